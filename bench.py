@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of the multilevel hot path on one B300 (or N replicas).
+
+A step is one multilevel measurement of the 24^3 x 8 FP32 workload (beta 0.98,
+slabs of 2, 100 sub-updates, r = 2..12, six field components at offsets
+0..8 for every r): k0 = 10 full compound sweeps, 100 slab sub-updates each
+followed by the accumulation of T^(2) and TO^(2), and the cross-slab products
+(Algorithm 1 of arXiv:1309.3859).  The lattice is thermalised (200 compound
+sweeps) before the warm-up steps.
+
+Metric: link updates per second over whole steps (every heatbath and
+overrelaxation link update of the step, divided by the step's device time),
+with multilevel measurements per second beside it.  L2 is flushed (a 512 MB
+write) before every timed step.  With --gpus N > 1 (torchrun) every rank runs
+its own lattice (independent Markov chains, weak scaling) and the value is the
+sum over ranks divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (one sub-update per step) on the host cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1309_3859_b300 import workloads  # noqa: E402
+
+METRIC = "multilevel link-updates/s"
+UNIT = "link-updates/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def link_updates_per_step(w) -> int:
+    """Heatbath + overrelaxation link updates of one measurement step."""
+    V = w.V
+    sweeps = 1 + w.n_or
+
+    def slab_links(d):  # temporal links always move; spatial ones on t = 0 mod d are frozen
+        return V + 3 * V * (d - 1) // d
+
+    n = w.k_between * 4 * V * sweeps
+    if w.outer_slab:
+        n += w.n_sub_outer * (slab_links(w.outer_slab) + w.n_sub * slab_links(w.slab)) * sweeps
+    else:
+        n += w.n_sub * slab_links(w.slab) * sweeps
+    return n
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- peaks
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- CPU baseline
+def oracle_sample(w, steps=1, threads=None):
+    """Time the FP64 oracle on a bounded sample of the workload: ``steps``
+    slab sub-updates with their accumulation and the cross-slab products."""
+    import oracle
+
+    threads = threads or os.cpu_count()
+    po = oracle.Params(L=w.L, Nt=w.Nt, beta=w.beta, seed=w.seed, n_or=w.n_or, slab=w.slab, n_sub=steps,
+                       k_between=0, r=w.r, rf=w.rf, probes=w.probes, comp_mask=w.comp_mask, threads=threads)
+    th = oracle.hot_start(po)
+    t0 = time.perf_counter()
+    oracle.measure(po, th, 0, 1)
+    dt = time.perf_counter() - t0
+    V = w.V
+    updates = steps * (V + 3 * V * (w.slab - 1) // w.slab) * (1 + w.n_or)
+    return updates / dt, threads, dt, updates
+
+
+def cpu_baseline(w):
+    rate, cores, dt, updates = oracle_sample(w, steps=6)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"six slab sub-updates (compound sweep + T/TO accumulation + products) of {w.name}: "
+                      f"{updates} link updates in {dt:.1f} s, FP64, OpenMP link updates"}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    rates = []
+    for _ in range(args.warmup):
+        oracle_sample(w, steps=1)
+    t0 = time.perf_counter()
+    tot_updates, tot_time, cores = 0, 0.0, None
+    for _ in range(args.steps):
+        rate, cores, dt, upd = oracle_sample(w, steps=1)
+        tot_updates += upd
+        tot_time += dt
+        rates.append(rate)
+    value = tot_updates / tot_time
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_time / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (hot start from the Philox stream)",
+            "config": {"workload": w.name, "L": w.L, "Nt": w.Nt, "beta": w.beta, "sample": "1 sub-update per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "one slab sub-update with accumulation and products per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def algorithmic_bytes(w, kernel):
+    """Bytes one launch of a kernel class must move at minimum (FP32 angles)."""
+    tsz = 8 if w.fp64 else 4
+    Ns, V = w.L ** 3, w.V
+    nslab = w.Nt // w.slab
+    nR = len(sorted(set(w.r) | set(w.rf)))
+    nc = bin(w.comp_mask).count("1")
+    if kernel == "update":
+        # a (mu, parity) pass reads U_mu at both parities (V), the other three
+        # directions everywhere (3V) and writes V/2 (frozen links included in
+        # the reads, as for a full pass)
+        return int(4.5 * V * tsz)
+    if kernel == "accumulate":
+        acc_o = nslab * len(w.rf) * len(w.probes) * nc * 2 * Ns
+        acc_t = nslab * nR * Ns
+        osum = nslab * nc * 2 * Ns * tsz
+        return 32 * (acc_o + acc_t) + osum + V * tsz  # complex FP64 read+write, slab sums, theta_0
+    raise ValueError(kernel)
+
+
+def run_gpu(args, w, rank, world):
+    import torch
+
+    from paper_1309_3859_b300 import ml
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist = dist_mod
+        dist.init_process_group("nccl")
+
+    p = ml.Params.from_workload(w, seed=w.seed + 1000 * rank)
+    lat = ml.Lattice(p)
+    st = lat.stream
+    lat.thermalize(w.n_therm)
+    rec = torch.empty((1, lat.rec_len), dtype=torch.float64, device=lat.device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=lat.device)
+    for _ in range(args.warmup):
+        lat.measure_device(1, rec)
+    lat.sync()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    launches0 = ml.kernel_launches()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(st):
+                flush.fill_(float(k))
+            starts[k].record(st)
+            lat.measure_device(1, rec)
+            ends[k].record(st)
+        lat.sync()
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    launches = ml.kernel_launches() - launches0
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=lat.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    upd = link_updates_per_step(w)
+    value = world * upd * args.steps / (ms * 1e-3)
+
+    # kernel classes: per-launch device time and launches per step
+    per_step = {
+        "heatbath": (ml.ML_K_HEATBATH, 8 * (w.k_between + w.n_sub)),
+        "overrelax": (ml.ML_K_OVERRELAX, 8 * w.n_or * (w.k_between + w.n_sub)),
+        "plaq_slab": (ml.ML_K_PLAQ_SLAB, w.n_sub),
+        "accumulate": (ml.ML_K_ACCUMULATE, w.n_sub),
+        "products": (ml.ML_K_PRODUCTS, 1),
+    }
+    kms = {name: lat.kernel_ms(kid, reps=20 if name != "products" else 3) for name, (kid, _) in per_step.items()}
+    share = {name: kms[name] * per_step[name][1] / (ms / args.steps) for name in per_step}
+    dominant = max(share, key=share.get)
+    peak, peak_kind = measured_peaks()
+    kname = "update" if dominant in ("heatbath", "overrelax") else dominant
+    if kname in ("update", "accumulate"):
+        nbytes = algorithmic_bytes(w, kname)
+        achieved = nbytes / (kms[dominant] * 1e-3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": nbytes, "launch_ms": kms[dominant]}
+    else:
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                "traffic": None}
+
+    # end to end through the public API with host buffers: upload this
+    # step's configuration from pinned memory, measure, read the record
+    theta_host = torch.from_numpy(lat.get_angles()).pin_memory()
+    out_host = np.zeros((1, lat.rec_len))
+    e2e_steps = max(1, min(args.steps, 5))
+    lat.set_angles(theta_host.numpy())
+    lat.measure(1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.set_angles(theta_host.numpy())
+        out_host[:] = lat.measure(1)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * upd * e2e_steps / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if w.fp64 else "f32 (FP64 slab accumulators and products)",
+        "data": "synthetic (hot start from the Philox stream, thermalised)",
+        "config": {"workload": w.name, "L": w.L, "Nt": w.Nt, "beta": w.beta, "n_sub": w.n_sub,
+                   "k_between": w.k_between, "n_or": w.n_or, "r": f"{w.r[0]}..{w.r[-1]}",
+                   "field_r": f"{w.rf[0]}..{w.rf[-1]}", "probes": len(w.probes), "components": 6,
+                   "link_updates_per_step": upd, "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": f"{world} independent lattice(s)"},
+        "measurements_per_s": world * args.steps / (ms * 1e-3),
+        "roofline": roof,
+        "kernel_ms": kms, "kernel_share": share,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
+                "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+        "wall_s": t_wall,
+    }
+    lat.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=workloads.SINGLE_24.name, choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus))
+    w = workloads.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, rank, world)
+    return run_gpu(args, w, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

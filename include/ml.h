@@ -1,0 +1,219 @@
+/*
+ * ml.h -- C ABI of the B300 multilevel Monte Carlo library (libml.so) for
+ * d = 3+1 compact U(1) Wilson-action lattice gauge theory.
+ *
+ * The library runs the Luescher-Weisz multilevel algorithm as used by Amado,
+ * Cardoso & Bicudo, arXiv:1309.3859 (Section II.C and Algorithm 1):
+ * checkerboard heatbath + overrelaxation sweeps with the spatial links of slab
+ * boundaries frozen, per-slab averages of two-link Polyakov factors with and
+ * without a plaquette field insertion, and cross-slab products that give the
+ * Polyakov-loop correlator P(r) and the flux-tube field profile.
+ *
+ * Conventions used by every entry point:
+ *   site index  i = x + L*(y + L*(z + L*t)), periodic in all four directions;
+ *   direction   0 = t (the paper's U_0), 1 = x, 2 = y, 3 = z;
+ *   angles      U_mu(i) = exp(i theta_mu(i)); host angle buffers hold
+ *               theta[mu * V + i] in double precision (V = L^3 Nt);
+ *   components  c = 0..5 are Ex, Ey, Ez, Bx, By, Bz = the plaquettes
+ *               P_01, P_02, P_03, P_23, P_31, P_12 (Section II.B);
+ *   charges     static charge at x, anti-charge at x + r xhat.
+ *
+ * Errors: every function returns an ml_status (0 = ML_OK, negative = error).
+ * No function throws across the ABI.  After ML_ETIMEOUT or ML_EREJECT the
+ * handle stays valid for inspection and ml_destroy.
+ *
+ * Streams: all device work of a handle is enqueued on the stream given to
+ * ml_create.  Functions documented as blocking synchronise that stream.
+ */
+#ifndef ML_H
+#define ML_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ML_OK = 0,
+  ML_EINVAL = -1,   /* invalid argument or parameter set                      */
+  ML_ENOMEM = -2,   /* the allocator returned NULL                            */
+  ML_ECUDA = -3,    /* a CUDA runtime call failed                             */
+  ML_ETIMEOUT = -4, /* a bounded device wait gave up                          */
+  ML_EREJECT = -5,  /* the von Mises rejection loop reached its trial cap     */
+  ML_EBUSY = -6,    /* resource in use (e.g. server at capacity)              */
+  ML_ESTATE = -7    /* call not allowed in the handle's state                 */
+} ml_status;
+
+typedef enum {
+  ML_FP64 = 0, /* link angles and update arithmetic in double precision       */
+  ML_FP32 = 1  /* link angles and update arithmetic in single precision; slab
+                  averages, products and final ratios stay in double          */
+} ml_precision;
+
+/* Transverse offset (dy, dz) of a field probe from the mid-point of the
+ * charges (the paper's mediator plane, Section III.B). */
+typedef struct {
+  int dy, dz;
+} ml_offset;
+
+/* Run parameters.  Validation (ML_EINVAL): L and Nt even and >= 2; slab >= 1
+ * dividing Nt; n_sub >= 1; outer_slab = 0, or a multiple of slab that divides
+ * Nt and differs from slab, with n_sub_outer >= 1; 1 <= r, rf <= L-1;
+ * |dy|, |dz| <= L-1; beta >= 0; k_between >= 0; n_or >= 0; comp_mask < 64;
+ * at least one r.  The lists are copied by ml_create. */
+typedef struct {
+  int L, Nt;            /* spatial and temporal extent                         */
+  double beta;          /* inverse coupling 1/g^2 of the Wilson action         */
+  uint64_t seed;        /* key of the Philox stream                            */
+  int prec;             /* ml_precision                                        */
+  int n_or;             /* overrelaxation sweeps per heatbath sweep (paper: 3) */
+  int slab;             /* inner slab thickness d (paper: 2)                   */
+  int n_sub;            /* inner sub-updates n2 per (outer) iteration          */
+  int outer_slab;       /* 0: one level; else outer thickness (paper: 4)       */
+  int n_sub_outer;      /* outer sub-updates n4                                */
+  int k_between;        /* full compound sweeps before each measurement, k0    */
+  int nr;               /* number of P(r) separations                          */
+  const int *r;         /* P(r) separations along x                            */
+  int nrf;              /* number of field-profile separations                 */
+  const int *rf;        /* separations of the field profile                    */
+  int nprobe;           /* number of probe offsets                             */
+  const ml_offset *probe; /* probe offsets on the mediator plane               */
+  uint32_t comp_mask;   /* bit c selects field component c                     */
+} ml_params;
+
+/* Device-memory allocator supplied by the caller (the Python binding passes
+ * PyTorch's caching allocator).  alloc returns device memory of at least
+ * `bytes` bytes aligned to 256 bytes, or NULL; free releases it. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *ctx);
+  void (*free)(void *ptr, void *ctx);
+  void *ctx;
+} ml_allocator;
+
+typedef struct ml_lattice ml_lattice;
+
+/* ------------------------------------------------------------------------ */
+/* Lattice lifecycle                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Validates *p, allocates the lattice through *alloc (NULL: cudaMalloc) on
+ * the current device, and enqueues the hot start theta = -pi + 2 pi u on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).  u is the
+ * 52-bit uniform of Philox block (i, mu, 0, 0) keyed by the seed.  Sweep
+ * numbering starts at 1 with the first heatbath sweep.  Ownership of the
+ * handle passes to the caller; release it with ml_destroy. */
+int ml_create(const ml_params *p, const ml_allocator *alloc, void *cuda_stream, ml_lattice **out);
+
+/* Synchronises the handle's stream and frees everything it owns. */
+int ml_destroy(ml_lattice *h);
+
+/* n_sweeps compound sweeps (one heatbath sweep + n_or overrelaxation sweeps,
+ * Section II) with no frozen links: thermalisation (Section II, Algorithm 1's
+ * k0 loop).  Asynchronous; errors surface at the next blocking call. */
+int ml_thermalize(ml_lattice *h, int n_sweeps);
+
+/* n_meas multilevel measurements (Algorithm 1).  Each one runs k_between full
+ * compound sweeps, then the slab sub-updates with frozen boundary spatial
+ * links (one level: n_sub sub-updates of thickness `slab`; two levels:
+ * n_sub_outer iterations of one outer sweep plus n_sub inner sub-updates),
+ * accumulating the slab averages of T^(d) and TO^(d) (Section II.C), then the
+ * cross-slab products.  Blocks until the records are in out_host.
+ * out_host receives n_meas records of ml_record_len doubles (layout below);
+ * out_len is its capacity in doubles. */
+int ml_measure(ml_lattice *h, int n_meas, double *out_host, size_t out_len);
+
+/* Same as ml_measure but leaves the records in device memory out_dev
+ * (n_meas * record_len doubles) and does not synchronise. */
+int ml_measure_device(ml_lattice *h, int n_meas, double *out_dev, size_t out_len);
+
+/* Doubles of one measurement record for parameter set *p:
+ *   P      [nr][2]               (Re, Im) (1/Ns) sum_x prod_s [T]_s(x, r)
+ *   Pf     [nrf][2]              the same at the field separations
+ *   W      [nrf][nprobe][6][2][2] for component c and insertion k (0: Re P_c,
+ *                                1: Im P_c), (Re, Im) of (1/(Ns Nt)) sum_x
+ *                                sum_s [TO]_s prod_{s' != s} [T]_{s'}
+ *   vac    [6][2]                mean Re P_c, Im P_c over sites and the
+ *                                sub-update configurations
+ *   naive  [nr][2]               (1/Ns) sum_x P(x)^* P(x + r) on the first
+ *                                configuration of the measurement
+ *   plaq   [1]                   mean plaquette of that configuration
+ * Unselected components are zero.  Ns = L^3. */
+int ml_record_len(const ml_params *p, size_t *len);
+
+/* Connected field profile from n_meas records already in device memory
+ * (Section II.D): with means over measurements,
+ *   F   = sqrt(beta) ( <Re W_{c,1}> / <Re Pf> - <vac_{c,1}> )
+ *   F^2 = -2 beta   ( <Re W_{c,0}> / <Re Pf> - <vac_{c,0}> )
+ * written as out_dev[nrf][nprobe][6][2] (F, F^2), computed in double
+ * precision on the device.  Asynchronous on the handle's stream. */
+int ml_connected_device(ml_lattice *h, const double *records_dev, int n_meas, double *out_dev, size_t out_len);
+
+/* ------------------------------------------------------------------------ */
+/* Configuration access and single steps (checkpointing, tests)              */
+/* ------------------------------------------------------------------------ */
+
+/* Copies the angles to / from host memory theta[4 * V] (double, canonical
+ * layout above).  Blocking.  ml_set_angles wraps values into [-pi, pi). */
+int ml_get_angles(ml_lattice *h, double *theta_host, size_t n);
+int ml_set_angles(ml_lattice *h, const double *theta_host, size_t n);
+
+/* Number of heatbath sweeps done so far (the Philox sweep counter); setting
+ * it with the saved angles resumes a run bit-exactly. */
+int ml_get_sweep(ml_lattice *h, uint64_t *n);
+int ml_set_sweep(ml_lattice *h, uint64_t n);
+
+/* One pass over the links U_mu(x) of parity `parity` (0 even, 1 odd) that
+ * are not frozen (slab_d > 0 freezes spatial links on t = 0 mod slab_d):
+ * kind 0 = heatbath with sweep number n, kind 1 = overrelaxation.
+ * Asynchronous.  Does not change the sweep counter. */
+int ml_update_pass(ml_lattice *h, int mu, int parity, int slab_d, uint64_t n, int kind);
+
+/* n compound sweeps with slab mask slab_d (0 = none). Asynchronous. */
+int ml_compound_sweeps(ml_lattice *h, int n, int slab_d);
+
+/* Record (layout of ml_record_len) of the current configuration alone, as a
+ * measurement with one sub-update and no sweep.  Blocking. */
+int ml_observe(ml_lattice *h, double *out_host, size_t out_len);
+
+/* Waits for the handle's stream and reports deferred device errors. */
+int ml_sync(ml_lattice *h);
+
+/* ------------------------------------------------------------------------ */
+/* Utilities                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Philox4x32-10 (Salmon et al., SC'11) evaluated on the device for n
+ * counters ctr[4n] and keys key[2n] (host arrays); out[4n] on the host.
+ * Blocking.  Used to check the device generator bit for bit. */
+int ml_philox(const uint32_t *ctr, const uint32_t *key, size_t n, uint32_t *out);
+
+/* Kernel classes of ml_kernel_timing. */
+typedef enum {
+  ML_K_HEATBATH = 0,   /* one heatbath pass (mu = 1, even sites, slab mask)      */
+  ML_K_OVERRELAX = 1,  /* one overrelaxation pass (same links)                   */
+  ML_K_PLAQ_SLAB = 2,  /* per-slab plaquette sums of the selected components     */
+  ML_K_ACCUMULATE = 3, /* accumulation of T^(d) and TO^(d) for one configuration  */
+  ML_K_PRODUCTS = 4    /* cross-slab products and their reduction over sites     */
+} ml_kernel_class;
+
+/* Average device time in milliseconds of `reps` back-to-back launches of one
+ * kernel class, bracketed by CUDA events on the handle's stream, in the
+ * launch configuration ml_measure uses.  Update passes run on a scratch copy
+ * of the angles, so the Markov chain is unchanged; the slab accumulators are
+ * left undefined (every measurement clears them first).  Blocking. */
+int ml_kernel_timing(ml_lattice *h, int kernel, int reps, double *avg_ms);
+
+/* Static text for a status code. */
+const char *ml_error_string(int status);
+
+/* Number of kernels the library has launched in this process (including
+ * those replayed from CUDA graphs). */
+uint64_t ml_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ML_H */

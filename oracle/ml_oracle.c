@@ -497,6 +497,7 @@ static void slab_two_link(const geom *g, const double *th, int64_t xs, int t0, i
 
 /* Length of one measurement record:
  *   P      [nr][2]                 (Re, Im) of (1/N_s) sum_x prod_s [T]_s
+ *   Pf     [nrf][2]                the same at the field separations rf
  *   W      [nrf][nprobe][6][2][2]  component c, insertion k (Re P / Im P),
  *                                  (Re, Im) of (1/(N_s N_t)) sum_x sum_s
  *                                  [TO]_s prod_{s' != s} [T]_{s'}
@@ -505,7 +506,7 @@ static void slab_two_link(const geom *g, const double *th, int64_t xs, int t0, i
  *   naive  [nr][2]                 naive P+P on the measurement's first config
  *   plaq   [1]                     mean plaquette of that configuration       */
 int64_t orc_record_len(const orc_params *p) {
-  return (int64_t)p->nr * 2 + (int64_t)p->nrf * p->nprobe * 24 + 12 + (int64_t)p->nr * 2 + 1;
+  return (int64_t)p->nr * 2 + (int64_t)p->nrf * 2 + (int64_t)p->nrf * p->nprobe * 24 + 12 + (int64_t)p->nr * 2 + 1;
 }
 
 typedef struct {
@@ -704,7 +705,24 @@ static void cross_slab(const orc_params *p, const geom *g, const slab_sums *S, d
     rec[2 * a] = sr / (double)g->Ns;
     rec[2 * a + 1] = si / (double)g->Ns;
   }
-  double *w = rec + 2 * p->nr;
+  double *pf = rec + 2 * p->nr;
+  for (int a = 0; a < p->nrf; ++a) {
+    double sr = 0.0, si = 0.0;
+    for (int64_t xs = 0; xs < g->Ns; ++xs) {
+      cplx prod = {1.0, 0.0};
+      for (int sl = 0; sl < S->nslab; ++sl) {
+        cplx t = T_FR(S, sl, a, xs);
+        t.re *= inv;
+        t.im *= inv;
+        prod = cmul(prod, t);
+      }
+      sr += prod.re;
+      si += prod.im;
+    }
+    pf[2 * a] = sr / (double)g->Ns;
+    pf[2 * a + 1] = si / (double)g->Ns;
+  }
+  double *w = pf + 2 * p->nrf;
   for (int a = 0; a < p->nrf; ++a)
     for (int b = 0; b < p->nprobe; ++b)
       for (int c = 0; c < 6; ++c)
@@ -761,7 +779,7 @@ int orc_measure(const orc_params *p, double *th, uint64_t *counter, int n_meas, 
       if (orc_compound_sweep(p, th, 0, counter) != ORC_OK) status = ORC_EREJECT;
 
     /* naive estimator and plaquette of the measurement's first configuration */
-    double *naive = out + 2 * p->nr + (size_t)p->nrf * p->nprobe * 24 + 12;
+    double *naive = out + 2 * p->nr + 2 * p->nrf + (size_t)p->nrf * p->nprobe * 24 + 12;
     for (int a = 0; a < p->nr; ++a) naive_correlator(&g, th, p->r[a], &naive[2 * a], &naive[2 * a + 1]);
     naive[2 * p->nr] = orc_plaquette_mean(p->L, p->Nt, th);
 
@@ -789,7 +807,7 @@ int orc_measure(const orc_params *p, double *th, uint64_t *counter, int n_meas, 
       }
       cross_slab(p, &g, &outer, (double)p->n_sub_outer, out);
     }
-    double *v = out + 2 * p->nr + (size_t)p->nrf * p->nprobe * 24;
+    double *v = out + 2 * p->nr + 2 * p->nrf + (size_t)p->nrf * p->nprobe * 24;
     for (int c = 0; c < 12; ++c) v[c] = vac[c] / (double)n_cfg;
   }
   free(pf);

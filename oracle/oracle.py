@@ -255,11 +255,13 @@ def measure(p: Params, th: np.ndarray, counter: int, n_meas: int):
 
 
 def split_record(p: Params, rec: np.ndarray) -> dict:
-    """Views of a record array ``[..., record_len]``: P, W, vac, naive, plaq."""
+    """Views of a record array ``[..., record_len]``: P, Pf, W, vac, naive, plaq."""
     nr, nrf, npb = len(p.r), len(p.rf), len(p.probes)
     o = 0
     P = rec[..., o:o + 2 * nr].reshape(rec.shape[:-1] + (nr, 2))
     o += 2 * nr
+    Pf = rec[..., o:o + 2 * nrf].reshape(rec.shape[:-1] + (nrf, 2))
+    o += 2 * nrf
     W = rec[..., o:o + nrf * npb * 24].reshape(rec.shape[:-1] + (nrf, npb, 6, 2, 2))
     o += nrf * npb * 24
     vac = rec[..., o:o + 12].reshape(rec.shape[:-1] + (6, 2))
@@ -267,4 +269,4 @@ def split_record(p: Params, rec: np.ndarray) -> dict:
     naive = rec[..., o:o + 2 * nr].reshape(rec.shape[:-1] + (nr, 2))
     o += 2 * nr
     plaq = rec[..., o]
-    return {"P": P, "W": W, "vac": vac, "naive": naive, "plaq": plaq}
+    return {"P": P, "Pf": Pf, "W": W, "vac": vac, "naive": naive, "plaq": plaq}

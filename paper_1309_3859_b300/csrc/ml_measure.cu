@@ -1,0 +1,491 @@
+// Multilevel measurement kernels (arXiv:1309.3859, Section II.C and
+// Algorithm 1; field operators of Section II.B/II.D).
+//
+//   T^(d)(x, s, r)   = prod_{t in slab s} U_0(x, t)^* U_0(x + r xhat, t)
+//                    = exp(i [Theta_s(x + r) - Theta_s(x)]),
+//                      Theta_s(x) = sum_{t in slab s} theta_0(x, t)
+//   TO^(d)(x, s, rf) = T^(d)(x, s, rf) sum_{t in slab s} O(x0, t),
+//                      x0 = x + floor(rf / 2) xhat + dy yhat + dz zhat,
+//                      O in {Re P_c, Im P_c}
+//   P(r)   = (1/Ns) sum_x prod_s [T]_s(x, r)
+//   W      = (1/(Ns Nt)) sum_x sum_s [TO]_s(x) prod_{s' != s} [T]_{s'}(x)
+//
+// Slab sums live in double-precision complex accumulators laid out with the
+// spatial site x fastest, so one warp touches 32 consecutive sites.  All
+// reductions over sites are warp-shuffle trees writing per-warp partials,
+// followed by fixed-order sums: results do not depend on scheduling.
+#include "ml_internal.h"
+
+namespace ml {
+
+__constant__ int c_plane_mu[6] = {0, 0, 0, 2, 3, 1};
+__constant__ int c_plane_nu[6] = {1, 2, 3, 3, 1, 2};
+
+static inline int blocks_for(long long n, int t) { return static_cast<int>((n + t - 1) / t); }
+
+// spatial coordinates of spatial site x
+__device__ __forceinline__ void spatial_coords(const Geom& g, int x, int* cx, int* cy, int* cz) {
+  int rest = x / g.L;
+  *cx = x - rest * g.L;
+  *cy = rest % g.L;
+  *cz = rest / g.L;
+}
+
+// theta_0 at spatial site (cx, cy, cz) and time t
+template <typename T>
+__device__ __forceinline__ double theta0(const T* __restrict__ th, const Geom& g, int cx, int cy, int cz, int t) {
+  const int i = cx + g.L * (cy + g.L * (cz + g.L * t));
+  return static_cast<double>(th[soa(g, 0, i, (cx + cy + cz + t) & 1)]);
+}
+
+// plaquette angle of plane (mu, nu) at site coordinates c = (t, x, y, z)
+template <typename T>
+__device__ __forceinline__ T plaquette_angle(const T* __restrict__ th, const Geom& g, const int c[4], int mu, int nu) {
+  const int i = site_index(g, c[0], c[1], c[2], c[3]);
+  const int p = parity_of_coords(c);
+  const int ipmu = shifted(g, c, mu, 1, nu, 0);
+  const int ipnu = shifted(g, c, nu, 1, mu, 0);
+  return th[soa(g, mu, i, p)] + th[soa(g, nu, ipmu, p ^ 1)] - th[soa(g, mu, ipnu, p ^ 1)] - th[soa(g, nu, i, p)];
+}
+
+// e^{i phi} for a phase known in double precision, evaluated in T
+template <typename T>
+__device__ __forceinline__ double2 unit_phase(double phi) {
+  if constexpr (Prec<T>::fp64) {
+    double s, c;
+    sincos(phi, &s, &c);
+    return make_double2(c, s);
+  } else {
+    const float r = static_cast<float>(phi - kTwoPi * rint(phi * (1.0 / kTwoPi)));
+    float s, c;
+    __sincosf(r, &s, &c);
+    return make_double2(static_cast<double>(c), static_cast<double>(s));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-slab plaquette sums O[s][ci][k][x] = sum_{t in slab} (Re, Im) P_c(x, t)
+// and warp partials of the site sums of Re / Im P_c (vacuum).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_plaq_slab(const T* __restrict__ th, Geom g, int d, int nslab, int nc,
+                                                   const int* __restrict__ comp, T* __restrict__ osum,
+                                                   double* __restrict__ vac_part) {
+  using P = Prec<T>;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = idx < g.Ns * nslab;
+  const int s = live ? idx / g.Ns : 0;
+  const int x = live ? idx - s * g.Ns : 0;
+  int c[4];
+  spatial_coords(g, x, &c[1], &c[2], &c[3]);
+  double vac[12];
+#pragma unroll
+  for (int j = 0; j < 12; ++j) vac[j] = 0.0;
+  for (int ci = 0; ci < nc; ++ci) {
+    const int cc = comp[ci];
+    const int mu = c_plane_mu[cc], nu = c_plane_nu[cc];
+    T re = T(0), im = T(0);
+    if (live) {
+      for (int t = s * d; t < s * d + d; ++t) {
+        c[0] = t;
+        T sn, cs;
+        P::sincos_(plaquette_angle(th, g, c, mu, nu), &sn, &cs);
+        re += cs;
+        im += sn;
+      }
+      osum[(static_cast<size_t>(s * nc + ci) * 2 + 0) * g.Ns + x] = re;
+      osum[(static_cast<size_t>(s * nc + ci) * 2 + 1) * g.Ns + x] = im;
+    }
+    vac[2 * cc] = static_cast<double>(re);
+    vac[2 * cc + 1] = static_cast<double>(im);
+  }
+  const int warp = idx >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 12; ++j) {
+    const double v = warp_sum(vac[j]);
+    if (lane == 0) vac_part[static_cast<size_t>(warp) * 12 + j] = v;
+  }
+}
+
+// vac_acc[j] += scale * sum_w vac_part[w][j], fixed order (one block per j)
+__global__ void __launch_bounds__(256) k_vac_accumulate(const double* __restrict__ part, int nparts,
+                                                        double* __restrict__ acc, double scale) {
+  __shared__ double sh[8];
+  const int j = blockIdx.x;
+  double v = 0.0;
+  for (int w = threadIdx.x; w < nparts; w += blockDim.x) v += part[static_cast<size_t>(w) * 12 + j];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    acc[j] += s * scale;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Accumulation of T^(d) and TO^(d) for one configuration (one thread per
+// spatial site x and slab s).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_accumulate(const T* __restrict__ th, Geom g, int d, int nslab, MeasLayout m,
+                                                    const T* __restrict__ osum, double2* __restrict__ accT,
+                                                    double2* __restrict__ accO) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.Ns * nslab) return;
+  const int s = idx / g.Ns;
+  const int x = idx - s * g.Ns;
+  int cx, cy, cz;
+  spatial_coords(g, x, &cx, &cy, &cz);
+  double theta_x = 0.0;
+  for (int t = s * d; t < s * d + d; ++t) theta_x += theta0(th, g, cx, cy, cz, t);
+
+  for (int a = 0; a < m.nR; ++a) {
+    const int xr = wrapc(cx + m.R[a], g.L);
+    double theta_r = 0.0;
+    for (int t = s * d; t < s * d + d; ++t) theta_r += theta0(th, g, xr, cy, cz, t);
+    const double2 e = unit_phase<T>(theta_r - theta_x);
+    double2* p = accT + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
+    *p = cadd(*p, e);
+  }
+  for (int f = 0; f < m.nrf; ++f) {
+    const int rf = m.rf[f];
+    const int xr = wrapc(cx + rf, g.L);
+    double theta_r = 0.0;
+    for (int t = s * d; t < s * d + d; ++t) theta_r += theta0(th, g, xr, cy, cz, t);
+    const double2 e = unit_phase<T>(theta_r - theta_x);
+    const int x0x = wrapc(cx + rf / 2, g.L);
+    for (int b = 0; b < m.np; ++b) {
+      const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
+      for (int ci = 0; ci < m.nc; ++ci) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const double o = static_cast<double>(osum[(static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0]);
+          double2* p = accO + ((((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
+          *p = cadd(*p, cscale(e, o));
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Two-level combination: for outer slab S with inner slabs j = q S + jj,
+//   acc4T += prod_jj [T]_j ,  acc4O += sum_jj [TO]_j prod_{jj' != jj} [T]_j'
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, MeasLayout m,
+                                                 const double2* __restrict__ accT, const double2* __restrict__ accO,
+                                                 double inv_n, double2* __restrict__ acc4T,
+                                                 double2* __restrict__ acc4O) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= g.Ns * n_outer) return;
+  const int S = idx / g.Ns;
+  const int x = idx - S * g.Ns;
+  for (int a = 0; a < m.nR; ++a) {
+    double2 prod = make_double2(1.0, 0.0);
+    for (int jj = 0; jj < q; ++jj)
+      prod = cmul(prod, cscale(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x], inv_n));
+    double2* p = acc4T + (static_cast<size_t>(S) * m.nR + a) * g.Ns + x;
+    *p = cadd(*p, prod);
+  }
+  double2 tj[kMaxSlabs], rest[kMaxSlabs];
+  for (int f = 0; f < m.nrf; ++f) {
+    const int a = m.rf_idx[f];
+    for (int jj = 0; jj < q; ++jj) tj[jj] = cscale(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x], inv_n);
+    double2 run = make_double2(1.0, 0.0);
+    for (int jj = 0; jj < q; ++jj) {  // prefix products
+      rest[jj] = run;
+      run = cmul(run, tj[jj]);
+    }
+    run = make_double2(1.0, 0.0);
+    for (int jj = q - 1; jj >= 0; --jj) {  // times suffix products
+      rest[jj] = cmul(rest[jj], run);
+      run = cmul(run, tj[jj]);
+    }
+    for (int b = 0; b < m.np; ++b)
+      for (int ci = 0; ci < m.nc; ++ci)
+        for (int k = 0; k < 2; ++k) {
+          double2 sum = make_double2(0.0, 0.0);
+          for (int jj = 0; jj < q; ++jj) {
+            const double2 o =
+                accO[((((static_cast<size_t>(q * S + jj) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x];
+            sum = cadd(sum, cmul(cscale(o, inv_n), rest[jj]));
+          }
+          double2* p = acc4O + ((((static_cast<size_t>(S) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
+          *p = cadd(*p, sum);
+        }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cross-slab products, one thread per spatial site, warp partials per output:
+//   o in [0, nr)            P(r)
+//   o in [nr, nr+nrf)       P at the field separations
+//   o in [nr+nrf, ...)      W(f, b, ci, k)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_products(Geom g, int nslab, MeasLayout m, const double2* __restrict__ accT,
+                                                  const double2* __restrict__ accO, double inv_n,
+                                                  double2* __restrict__ partial, int nwarps) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = x < g.Ns;
+  const int warp = x >> 5, lane = threadIdx.x & 31;
+  for (int a = 0; a < m.nr; ++a) {
+    double2 prod = make_double2(live ? 1.0 : 0.0, 0.0);
+    if (live)
+      for (int s = 0; s < nslab; ++s)
+        prod = cmul(prod, cscale(accT[(static_cast<size_t>(s) * m.nR + m.r_idx[a]) * g.Ns + x], inv_n));
+    prod = warp_sum(prod);
+    if (lane == 0) partial[static_cast<size_t>(a) * nwarps + warp] = prod;
+  }
+  double2 ts[kMaxSlabs], rest[kMaxSlabs];
+  const int nW = m.np * m.nc * 2;
+  for (int f = 0; f < m.nrf; ++f) {
+    double2 full = make_double2(0.0, 0.0);
+    if (live) {
+      const int a = m.rf_idx[f];
+      for (int s = 0; s < nslab; ++s) ts[s] = cscale(accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x], inv_n);
+      double2 run = make_double2(1.0, 0.0);
+      for (int s = 0; s < nslab; ++s) {
+        rest[s] = run;
+        run = cmul(run, ts[s]);
+      }
+      full = run;
+      run = make_double2(1.0, 0.0);
+      for (int s = nslab - 1; s >= 0; --s) {
+        rest[s] = cmul(rest[s], run);
+        run = cmul(run, ts[s]);
+      }
+    }
+    full = warp_sum(full);
+    if (lane == 0) partial[static_cast<size_t>(m.nr + f) * nwarps + warp] = full;
+    for (int j = 0; j < nW; ++j) {  // j = (b * nc + ci) * 2 + k
+      double2 sum = make_double2(0.0, 0.0);
+      if (live)
+        for (int s = 0; s < nslab; ++s) {
+          const double2 o = accO[((static_cast<size_t>(s) * m.nrf + f) * nW + j) * g.Ns + x];
+          sum = cadd(sum, cmul(cscale(o, inv_n), rest[s]));
+        }
+      sum = warp_sum(sum);
+      if (lane == 0) partial[static_cast<size_t>(m.nr + m.nrf + f * nW + j) * nwarps + warp] = sum;
+    }
+  }
+}
+
+// Fixed-order sum of the warp partials of each output into the record.
+__global__ void k_finalize_products(const double2* __restrict__ partial, int nwarps, Geom g, MeasLayout m,
+                                    double* __restrict__ rec) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nW = m.np * m.nc * 2;
+  const int nout = m.nr + m.nrf + m.nrf * nW;
+  if (o >= nout) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int w = 0; w < nwarps; ++w) s = cadd(s, partial[static_cast<size_t>(o) * nwarps + w]);
+  size_t off;
+  double scale;
+  if (o < m.nr) {
+    off = m.off_P + 2 * o;
+    scale = 1.0 / g.Ns;
+  } else if (o < m.nr + m.nrf) {
+    off = m.off_Pf + 2 * (o - m.nr);
+    scale = 1.0 / g.Ns;
+  } else {
+    const int q = o - m.nr - m.nrf;
+    const int f = q / nW, j = q - f * nW;
+    const int b = j / (m.nc * 2), ci = (j / 2) % m.nc, k = j & 1;
+    off = m.off_W + ((((static_cast<size_t>(f) * m.np + b) * 6 + m.comp[ci]) * 2 + k) * 2);
+    scale = 1.0 / (static_cast<double>(g.Ns) * g.Nt);
+  }
+  rec[off] = s.x * scale;
+  rec[off + 1] = s.y * scale;
+}
+
+// ---------------------------------------------------------------------------
+// Naive P(x)^* P(x + r) and the mean plaquette of the current configuration.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_naive(const T* __restrict__ th, Geom g, MeasLayout m,
+                                               double2* __restrict__ partial, int nwarps) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = x < g.Ns;
+  int cx = 0, cy = 0, cz = 0;
+  if (live) spatial_coords(g, x, &cx, &cy, &cz);
+  double tx = 0.0;
+  if (live)
+    for (int t = 0; t < g.Nt; ++t) tx += theta0(th, g, cx, cy, cz, t);
+  const int warp = x >> 5, lane = threadIdx.x & 31;
+  for (int a = 0; a < m.nr; ++a) {
+    double2 e = make_double2(0.0, 0.0);
+    if (live) {
+      const int xr = wrapc(cx + m.R[m.r_idx[a]], g.L);
+      double tr = 0.0;
+      for (int t = 0; t < g.Nt; ++t) tr += theta0(th, g, xr, cy, cz, t);
+      double sn, cs;
+      sincos(tr - tx, &sn, &cs);
+      e = make_double2(cs, sn);
+    }
+    e = warp_sum(e);
+    if (lane == 0) partial[static_cast<size_t>(a) * nwarps + warp] = e;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_plaq_mean(const T* __restrict__ th, Geom g, double* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double v = 0.0;
+  if (i < g.V) {
+    int rest = i / g.L;
+    int c[4];
+    c[1] = i - rest * g.L;
+    c[2] = rest % g.L;
+    rest /= g.L;
+    c[3] = rest % g.L;
+    c[0] = rest / g.L;
+    for (int mu = 0; mu < 4; ++mu)
+      for (int nu = mu + 1; nu < 4; ++nu) v += cos(static_cast<double>(plaquette_angle(th, g, c, mu, nu)));
+  }
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) part[i >> 5] = v;
+}
+
+__global__ void k_finalize_naive(const double2* __restrict__ partial, int nwarps, const double* __restrict__ ppart,
+                                 int npw, Geom g, MeasLayout m, double* __restrict__ rec) {
+  for (int o = threadIdx.x; o <= m.nr; o += blockDim.x) {
+    if (o < m.nr) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int w = 0; w < nwarps; ++w) s = cadd(s, partial[static_cast<size_t>(o) * nwarps + w]);
+      rec[m.off_naive + 2 * o] = s.x / g.Ns;
+      rec[m.off_naive + 2 * o + 1] = s.y / g.Ns;
+    } else {
+      double s = 0.0;
+      for (int w = 0; w < npw; ++w) s += ppart[w];
+      rec[m.off_plaq] = s / (6.0 * g.V);
+    }
+  }
+}
+
+__global__ void k_write_vac(const double* __restrict__ acc, double inv, MeasLayout m, double* __restrict__ rec) {
+  const int ci = threadIdx.x;
+  if (ci >= m.nc) return;
+  const int c = m.comp[ci];
+  rec[m.off_vac + 2 * c] = acc[2 * c] * inv;
+  rec[m.off_vac + 2 * c + 1] = acc[2 * c + 1] * inv;
+}
+
+// Connected field (Section II.D): F = sqrt(beta) (<W_{c,Im}> / <Pf> - <vac_Im>),
+// F^2 = -2 beta (<W_{c,Re}> / <Pf> - <vac_Re>), means over measurements.
+__global__ void k_connected(const double* __restrict__ recs, int n_meas, MeasLayout m, double beta,
+                            double* __restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m.nrf * m.np * 6) return;
+  const int c = idx % 6;
+  const int b = (idx / 6) % m.np;
+  const int f = idx / (6 * m.np);
+  double pf = 0.0, w0 = 0.0, w1 = 0.0, v0 = 0.0, v1 = 0.0;
+  for (int j = 0; j < n_meas; ++j) {
+    const double* r = recs + static_cast<size_t>(j) * m.rec_len;
+    pf += r[m.off_Pf + 2 * f];
+    const size_t wo = m.off_W + (((static_cast<size_t>(f) * m.np + b) * 6 + c) * 2) * 2;
+    w0 += r[wo];
+    w1 += r[wo + 2];
+    v0 += r[m.off_vac + 2 * c];
+    v1 += r[m.off_vac + 2 * c + 1];
+  }
+  const double inv = 1.0 / n_meas;
+  bool sel = false;
+  for (int ci = 0; ci < m.nc; ++ci) sel |= (m.comp[ci] == c);
+  double F = 0.0, F2 = 0.0;
+  if (sel) {
+    F = sqrt(beta) * (w1 / pf - v1 * inv);
+    F2 = -2.0 * beta * (w0 / pf - v0 * inv);
+  }
+  out[2 * idx] = F;
+  out[2 * idx + 1] = F2;
+}
+
+// ---------------------------------------------------------------------------
+int vac_part_count(const Geom& g, int d) {
+  const int nslab = g.Nt / d;
+  return blocks_for(static_cast<long long>(g.Ns) * nslab, 256) * 8;
+}
+
+int product_partial_count(const Geom& g) { return blocks_for(g.Ns, 256) * 8; }
+
+void launch_plaq_slab(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, void* osum,
+                      double* vac_part, cudaStream_t s) {
+  const int nslab = g.Nt / d;
+  const int nb = blocks_for(static_cast<long long>(g.Ns) * nslab, 256);
+  if (fp64)
+    k_plaq_slab<double><<<nb, 256, 0, s>>>(static_cast<const double*>(theta), g, d, nslab, m.nc, m.comp,
+                                           static_cast<double*>(osum), vac_part);
+  else
+    k_plaq_slab<float><<<nb, 256, 0, s>>>(static_cast<const float*>(theta), g, d, nslab, m.nc, m.comp,
+                                          static_cast<float*>(osum), vac_part);
+  count_launches(1);
+}
+
+void launch_vac_accumulate(const double* vac_part, int nparts, double* vac_acc, double scale, cudaStream_t s) {
+  k_vac_accumulate<<<12, 256, 0, s>>>(vac_part, nparts, vac_acc, scale);
+  count_launches(1);
+}
+
+void launch_accumulate(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, const void* osum,
+                       double2* accT, double2* accO, cudaStream_t s) {
+  const int nslab = g.Nt / d;
+  const int nb = blocks_for(static_cast<long long>(g.Ns) * nslab, 256);
+  if (fp64)
+    k_accumulate<double><<<nb, 256, 0, s>>>(static_cast<const double*>(theta), g, d, nslab, m,
+                                            static_cast<const double*>(osum), accT, accO);
+  else
+    k_accumulate<float><<<nb, 256, 0, s>>>(static_cast<const float*>(theta), g, d, nslab, m,
+                                           static_cast<const float*>(osum), accT, accO);
+  count_launches(1);
+}
+
+void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, const double2* accT, const double2* accO,
+                    double inv_n, double2* acc4T, double2* acc4O, cudaStream_t s) {
+  const int nb = blocks_for(static_cast<long long>(g.Ns) * n_outer, 256);
+  k_combine<<<nb, 256, 0, s>>>(g, n_outer, q, m, accT, accO, inv_n, acc4T, acc4O);
+  count_launches(1);
+}
+
+void launch_products(const Geom& g, int nslab, const MeasLayout& m, const double2* accT, const double2* accO,
+                     double inv_n, double2* partial, double* rec, cudaStream_t s) {
+  const int nb = blocks_for(g.Ns, 256);
+  const int nwarps = nb * 8;
+  k_products<<<nb, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps);
+  const int nout = m.nr + m.nrf + m.nrf * m.np * m.nc * 2;
+  k_finalize_products<<<blocks_for(nout, 128), 128, 0, s>>>(partial, nwarps, g, m, rec);
+  count_launches(2);
+}
+
+void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,
+                                double* rec, cudaStream_t s) {
+  const int nb = blocks_for(g.Ns, 256);
+  const int nwarps = nb * 8;
+  const int nbv = blocks_for(g.V, 256);
+  double* ppart = reinterpret_cast<double*>(partial + static_cast<size_t>(m.nr) * nwarps);
+  if (fp64) {
+    k_naive<double><<<nb, 256, 0, s>>>(static_cast<const double*>(theta), g, m, partial, nwarps);
+    k_plaq_mean<double><<<nbv, 256, 0, s>>>(static_cast<const double*>(theta), g, ppart);
+  } else {
+    k_naive<float><<<nb, 256, 0, s>>>(static_cast<const float*>(theta), g, m, partial, nwarps);
+    k_plaq_mean<float><<<nbv, 256, 0, s>>>(static_cast<const float*>(theta), g, ppart);
+  }
+  k_finalize_naive<<<1, 128, 0, s>>>(partial, nwarps, ppart, nbv * 8, g, m, rec);
+  count_launches(3);
+}
+
+void launch_write_vac(const double* vac_acc, double inv_ncfg, const MeasLayout& m, double* rec, cudaStream_t s) {
+  k_write_vac<<<1, 32, 0, s>>>(vac_acc, inv_ncfg, m, rec);
+  count_launches(1);
+}
+
+void launch_connected(const double* recs, int n_meas, const MeasLayout& m, double beta, double* out, cudaStream_t s) {
+  const int n = m.nrf * m.np * 6;
+  if (n == 0) return;
+  k_connected<<<blocks_for(n, 128), 128, 0, s>>>(recs, n_meas, m, beta, out);
+  count_launches(1);
+}
+
+}  // namespace ml

@@ -1,0 +1,309 @@
+"""Python binding of ``libml.so`` (include/ml.h): argument marshalling only.
+
+Every step of the multilevel path runs in the library's CUDA kernels; this
+module converts Python arguments to the C ABI, supplies PyTorch's caching
+allocator and a PyTorch stream, and raises :class:`MLError` on a non-zero
+status.  There is no CPU fallback: without the built library or a CUDA
+device the calls fail.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+ML_OK, ML_EINVAL, ML_ENOMEM, ML_ECUDA, ML_ETIMEOUT, ML_EREJECT, ML_EBUSY, ML_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+ML_FP64, ML_FP32 = 0, 1
+ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_PLAQ_SLAB, ML_K_ACCUMULATE, ML_K_PRODUCTS = range(5)
+COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
+
+
+class MLError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = _lib.ml_error_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} (status {status})" if what else f"{msg} (status {status})")
+
+
+class _Offset(ctypes.Structure):
+    _fields_ = [("dy", ctypes.c_int), ("dz", ctypes.c_int)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int), ("Nt", ctypes.c_int), ("beta", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("prec", ctypes.c_int), ("n_or", ctypes.c_int), ("slab", ctypes.c_int), ("n_sub", ctypes.c_int),
+        ("outer_slab", ctypes.c_int), ("n_sub_outer", ctypes.c_int), ("k_between", ctypes.c_int),
+        ("nr", ctypes.c_int), ("r", ctypes.POINTER(ctypes.c_int)),
+        ("nrf", ctypes.c_int), ("rf", ctypes.POINTER(ctypes.c_int)),
+        ("nprobe", ctypes.c_int), ("probe", ctypes.POINTER(_Offset)),
+        ("comp_mask", ctypes.c_uint32),
+    ]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_U32 = ctypes.POINTER(ctypes.c_uint32)
+_H = ctypes.c_void_p
+
+# name -> (restype, argtypes) for every entry point declared in include/ml.h
+SIGNATURES = {
+    "ml_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.POINTER(_Allocator), ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_void_p)]),
+    "ml_destroy": (ctypes.c_int, [_H]),
+    "ml_thermalize": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ml_measure": (ctypes.c_int, [_H, ctypes.c_int, _D, ctypes.c_size_t]),
+    "ml_measure_device": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "ml_record_len": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.POINTER(ctypes.c_size_t)]),
+    "ml_connected_device": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "ml_get_angles": (ctypes.c_int, [_H, _D, ctypes.c_size_t]),
+    "ml_set_angles": (ctypes.c_int, [_H, _D, ctypes.c_size_t]),
+    "ml_get_sweep": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint64)]),
+    "ml_set_sweep": (ctypes.c_int, [_H, ctypes.c_uint64]),
+    "ml_update_pass": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.c_int]),
+    "ml_compound_sweeps": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    "ml_observe": (ctypes.c_int, [_H, _D, ctypes.c_size_t]),
+    "ml_sync": (ctypes.c_int, [_H]),
+    "ml_philox": (ctypes.c_int, [_U32, _U32, ctypes.c_size_t, _U32]),
+    "ml_kernel_timing": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "ml_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ml_kernel_launches": (ctypes.c_uint64, []),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load ``libml.so`` (building it with nvcc first when it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing and _build.stale():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is not built; run paper_1309_3859_b300.build.build()")
+        L = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != ML_OK:
+        raise MLError(status, what)
+
+
+@dataclass
+class Params:
+    """Run parameters of one lattice (mirrors ``ml_params``)."""
+
+    L: int
+    Nt: int
+    beta: float
+    seed: int = 1
+    fp64: bool = True
+    n_or: int = 3
+    slab: int = 2
+    n_sub: int = 1
+    outer_slab: int = 0
+    n_sub_outer: int = 0
+    k_between: int = 0
+    r: tuple = (1,)
+    rf: tuple = ()
+    probes: tuple = ()
+    comp_mask: int = 0
+    _keep: list = field(default_factory=list, repr=False, compare=False)
+
+    @property
+    def V(self) -> int:
+        return self.L ** 3 * self.Nt
+
+    @property
+    def Ns(self) -> int:
+        return self.L ** 3
+
+    def c(self) -> _Params:
+        r = (ctypes.c_int * max(1, len(self.r)))(*self.r)
+        rf = (ctypes.c_int * max(1, len(self.rf)))(*self.rf)
+        pr = (_Offset * max(1, len(self.probes)))(*[_Offset(int(a), int(b)) for a, b in self.probes])
+        self._keep[:] = [r, rf, pr]
+        return _Params(self.L, self.Nt, float(self.beta), int(self.seed) & (2 ** 64 - 1),
+                       ML_FP64 if self.fp64 else ML_FP32, self.n_or, self.slab, self.n_sub, self.outer_slab,
+                       self.n_sub_outer, self.k_between, len(self.r), r, len(self.rf), rf, len(self.probes), pr,
+                       self.comp_mask)
+
+    @classmethod
+    def from_workload(cls, w, **kw) -> "Params":
+        d = dict(L=w.L, Nt=w.Nt, beta=w.beta, seed=w.seed, fp64=w.fp64, n_or=w.n_or, slab=w.slab, n_sub=w.n_sub,
+                 outer_slab=w.outer_slab, n_sub_outer=w.n_sub_outer, k_between=w.k_between, r=tuple(w.r),
+                 rf=tuple(w.rf), probes=tuple(w.probes), comp_mask=w.comp_mask)
+        d.update(kw)
+        return cls(**d)
+
+
+def record_len(p: Params) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().ml_record_len(ctypes.byref(p.c()), ctypes.byref(n)), "ml_record_len")
+    return n.value
+
+
+def split_record(p: Params, rec: np.ndarray) -> dict:
+    """Views of records ``[..., record_len]`` by block: P, Pf, W, vac, naive, plaq."""
+    nr, nrf, npb = len(p.r), len(p.rf), len(p.probes)
+    sizes = [("P", 2 * nr, (nr, 2)), ("Pf", 2 * nrf, (nrf, 2)), ("W", 24 * nrf * npb, (nrf, npb, 6, 2, 2)),
+             ("vac", 12, (6, 2)), ("naive", 2 * nr, (nr, 2)), ("plaq", 1, ())]
+    out, o = {}, 0
+    lead = rec.shape[:-1]
+    for name, n, shape in sizes:
+        out[name] = rec[..., o:o + n].reshape(lead + shape)
+        o += n
+    return out
+
+
+def philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    """Philox4x32-10 blocks evaluated on the device."""
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.empty_like(ctr)
+    _check(lib().ml_philox(ctr.ctypes.data_as(_U32), key.ctypes.data_as(_U32), ctr.shape[0],
+                           out.ctypes.data_as(_U32)), "ml_philox")
+    return out
+
+
+def kernel_launches() -> int:
+    return int(lib().ml_kernel_launches())
+
+
+class Lattice:
+    """One lattice resident on the GPU (``ml_create`` ... ``ml_destroy``).
+
+    Device memory comes from PyTorch's caching allocator and all work runs on
+    a dedicated PyTorch stream (``self.stream``)."""
+
+    def __init__(self, p: Params, stream=None, device=None):
+        import torch
+
+        self.p = p
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        dev, st = self.device, self.stream
+
+        def _alloc(size, ctx):
+            return torch.cuda.caching_allocator_alloc(int(size), dev, st)
+
+        def _free(ptr, ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+        self._alloc = _Allocator(self._cb[0], self._cb[1], None)
+        self._cp = p.c()
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().ml_create(ctypes.byref(self._cp), ctypes.byref(self._alloc),
+                                   ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)), "ml_create")
+        self.h = h
+        self.rec_len = record_len(p)
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().ml_destroy(self.h), "ml_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- Algorithm 1
+    def thermalize(self, n: int):
+        _check(lib().ml_thermalize(self.h, int(n)), "ml_thermalize")
+
+    def measure(self, n_meas: int) -> np.ndarray:
+        out = np.zeros((n_meas, self.rec_len), dtype=np.float64)
+        _check(lib().ml_measure(self.h, int(n_meas), out.ctypes.data_as(_D), out.size), "ml_measure")
+        return out
+
+    def measure_device(self, n_meas: int, out=None):
+        """Enqueue measurements whose records stay in a device tensor."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty((n_meas, self.rec_len), dtype=torch.float64, device=self.device)
+        assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+        _check(lib().ml_measure_device(self.h, int(n_meas), ctypes.c_void_p(out.data_ptr()), out.numel()),
+               "ml_measure_device")
+        return out
+
+    def connected(self, records_dev):
+        """Connected F and F^2 profile [nrf][nprobe][6][2] from device records."""
+        torch = self._torch
+        out = torch.empty((len(self.p.rf), len(self.p.probes), 6, 2), dtype=torch.float64, device=self.device)
+        _check(lib().ml_connected_device(self.h, ctypes.c_void_p(records_dev.data_ptr()), records_dev.shape[0],
+                                         ctypes.c_void_p(out.data_ptr()), out.numel()), "ml_connected_device")
+        return out
+
+    def observe(self) -> np.ndarray:
+        out = np.zeros(self.rec_len, dtype=np.float64)
+        _check(lib().ml_observe(self.h, out.ctypes.data_as(_D), out.size), "ml_observe")
+        return out
+
+    # -- configuration access
+    def get_angles(self) -> np.ndarray:
+        out = np.empty((4, self.p.V), dtype=np.float64)
+        _check(lib().ml_get_angles(self.h, out.ctypes.data_as(_D), out.size), "ml_get_angles")
+        return out
+
+    def set_angles(self, theta: np.ndarray):
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(4, self.p.V)
+        _check(lib().ml_set_angles(self.h, th.ctypes.data_as(_D), th.size), "ml_set_angles")
+
+    @property
+    def sweep(self) -> int:
+        n = ctypes.c_uint64()
+        _check(lib().ml_get_sweep(self.h, ctypes.byref(n)), "ml_get_sweep")
+        return n.value
+
+    @sweep.setter
+    def sweep(self, n: int):
+        _check(lib().ml_set_sweep(self.h, int(n)), "ml_set_sweep")
+
+    def update_pass(self, mu: int, parity: int, slab_d: int, n: int, kind: int):
+        _check(lib().ml_update_pass(self.h, mu, parity, slab_d, int(n), kind), "ml_update_pass")
+
+    def compound_sweeps(self, n: int, slab_d: int = 0):
+        _check(lib().ml_compound_sweeps(self.h, int(n), int(slab_d)), "ml_compound_sweeps")
+
+    def kernel_ms(self, kernel: int, reps: int = 20) -> float:
+        """Average event-timed duration of one kernel class (ml_kernel_timing)."""
+        ms = ctypes.c_double()
+        _check(lib().ml_kernel_timing(self.h, int(kernel), int(reps), ctypes.byref(ms)), "ml_kernel_timing")
+        return ms.value
+
+    def sync(self):
+        _check(lib().ml_sync(self.h), "ml_sync")

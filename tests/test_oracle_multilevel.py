@@ -56,6 +56,8 @@ def test_single_sub_update_identity(two_level):
     s = oracle.split_record(p, rec[0])
     Pexp, Wexp = _identity_expectation(p, th)
     assert np.abs(s["P"][:, 0] + 1j * s["P"][:, 1] - Pexp).max() < 1e-13
+    Pf = s["Pf"][:, 0] + 1j * s["Pf"][:, 1]
+    assert np.abs(Pf - Pexp[[p.r.index(r) for r in p.rf]]).max() < 1e-13
     Wgot = s["W"][..., 0] + 1j * s["W"][..., 1]
     assert np.abs(Wgot - Wexp).max() < 1e-13
     # vacuum sums: one configuration, site means of Re / Im P_c
