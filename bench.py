@@ -177,24 +177,50 @@ def run_reference(args, w, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def algorithmic_bytes(w, kernel):
-    """Bytes one launch of a kernel class must move at minimum (FP32 angles)."""
+def algorithmic_bytes(w, kernel, n_batch=1):
+    """Bytes one launch of a kernel class must move at minimum.
+
+    update pass: a (mu, parity) pass reads U_mu at both parities (V angles),
+    the other three directions everywhere (3V) and writes V/2: 4.5 V angles;
+    the persistent kernel runs 4 (1 + n_or) ... = 8 (1 + n_or) passes per
+    compound sweep.  fold: every slab accumulator is read and written once
+    (complex FP64, 32 bytes) and every record of the batch is read once."""
     tsz = 8 if w.fp64 else 4
     Ns, V = w.L ** 3, w.V
     nslab = w.Nt // w.slab
-    nR = len(sorted(set(w.r) | set(w.rf)))
+    nR = len(set(w.r) | set(w.rf))
     nc = bin(w.comp_mask).count("1")
-    if kernel == "update":
-        # a (mu, parity) pass reads U_mu at both parities (V), the other three
-        # directions everywhere (3V) and writes V/2 (frozen links included in
-        # the reads, as for a full pass)
+    if kernel == "pass":
         return int(4.5 * V * tsz)
+    if kernel == "sweep":
+        return int(8 * (1 + w.n_or) * 4.5 * V * tsz)
     if kernel == "accumulate":
         acc_o = nslab * len(w.rf) * len(w.probes) * nc * 2 * Ns
         acc_t = nslab * nR * Ns
-        osum = nslab * nc * 2 * Ns * tsz
-        return 32 * (acc_o + acc_t) + osum + V * tsz  # complex FP64 read+write, slab sums, theta_0
+        records = n_batch * nslab * Ns * (1 + nc * 2) * tsz
+        return 32 * (acc_o + acc_t) + records
     raise ValueError(kernel)
+
+
+def hbm_sweep_point(ml, peak):
+    """Persistent compound sweep on a 64^4 FP32 lattice (268 MB of angles,
+    beyond L2): link updates/s and effective bandwidth against HBM."""
+    p = ml.Params(L=64, Nt=64, beta=0.98, seed=5, fp64=False, slab=2, n_sub=1, r=(1,))
+    with ml.Lattice(p) as lat:
+        lat.thermalize(2)
+        ms_sweep = lat.kernel_ms(ml.ML_K_SWEEP, reps=5)
+        ms_or = lat.kernel_ms(ml.ML_K_OVERRELAX, reps=10)
+        ms_hb = lat.kernel_ms(ml.ML_K_HEATBATH, reps=10)
+    V = p.V
+    # slab mask 2: temporal links all move, spatial links on half the slices
+    moved = (V + 3 * V // 2) * 4
+    pass_bytes = 4.5 * V * 4
+    return {"workload": "sweep-64x64x64x64-fp32", "angle_bytes": 16 * V,
+            "compound_sweep_ms": ms_sweep, "link_updates_per_s": moved / (ms_sweep * 1e-3),
+            "sweep_achieved_gbs": 32 * pass_bytes / (ms_sweep * 1e-3) / 1e9,
+            "sweep_frac": 32 * pass_bytes / (ms_sweep * 1e-3) / 1e9 / peak,
+            "or_pass_ms": ms_or, "or_pass_gbs": pass_bytes / (ms_or * 1e-3) / 1e9,
+            "hb_pass_ms": ms_hb, "hb_pass_gbs": pass_bytes / (ms_hb * 1e-3) / 1e9}
 
 
 def run_gpu(args, w, rank, world):
@@ -251,27 +277,25 @@ def run_gpu(args, w, rank, world):
     value = world * upd * args.steps / (ms * 1e-3)
 
     # kernel classes: per-launch device time and launches per step
+    nB = lat.batch_slots
+    n_folds = -(-w.n_sub // nB)
     per_step = {
-        "heatbath": (ml.ML_K_HEATBATH, 8 * (w.k_between + w.n_sub)),
-        "overrelax": (ml.ML_K_OVERRELAX, 8 * w.n_or * (w.k_between + w.n_sub)),
-        "plaq_slab": (ml.ML_K_PLAQ_SLAB, w.n_sub),
-        "accumulate": (ml.ML_K_ACCUMULATE, w.n_sub),
+        "sweep": (ml.ML_K_SWEEP, w.k_between + w.n_sub),
+        "record": (ml.ML_K_RECORD, w.n_sub),
+        "accumulate": (ml.ML_K_ACCUMULATE, n_folds),
         "products": (ml.ML_K_PRODUCTS, 1),
     }
     kms = {name: lat.kernel_ms(kid, reps=20 if name != "products" else 3) for name, (kid, _) in per_step.items()}
     share = {name: kms[name] * per_step[name][1] / (ms / args.steps) for name in per_step}
-    dominant = max(share, key=share.get)
+    dominant = max(("sweep", "accumulate"), key=share.get)
     peak, peak_kind = measured_peaks()
-    kname = "update" if dominant in ("heatbath", "overrelax") else dominant
-    if kname in ("update", "accumulate"):
-        nbytes = algorithmic_bytes(w, kname)
-        achieved = nbytes / (kms[dominant] * 1e-3) / 1e9
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-                "algorithmic_bytes_per_launch": nbytes, "launch_ms": kms[dominant]}
-    else:
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-                "traffic": None}
+    nbytes = algorithmic_bytes(w, dominant, nB)
+    achieved = nbytes / (kms[dominant] * 1e-3) / 1e9
+    roof = {"kernel": {"sweep": "k_sweeps", "accumulate": "k_accum_T + k_accum_O"}[dominant], "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
+            "launch_ms": kms[dominant], "batch_slots": nB}
+    hbm_point = hbm_sweep_point(ml, peak) if rank == 0 and not args.no_extra else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -306,6 +330,7 @@ def run_gpu(args, w, rank, world):
         "measurements_per_s": world * args.steps / (ms * 1e-3),
         "roofline": roof,
         "kernel_ms": kms, "kernel_share": share,
+        "sweep_hbm_point": hbm_point,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
         "gpu_launches": int(launches),
@@ -329,6 +354,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=workloads.SINGLE_24.name, choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 64^4 HBM sweep point")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus))

@@ -191,11 +191,12 @@ int ml_philox(const uint32_t *ctr, const uint32_t *key, size_t n, uint32_t *out)
 
 /* Kernel classes of ml_kernel_timing. */
 typedef enum {
-  ML_K_HEATBATH = 0,   /* one heatbath pass (mu = 1, even sites, slab mask)      */
-  ML_K_OVERRELAX = 1,  /* one overrelaxation pass (same links)                   */
-  ML_K_PLAQ_SLAB = 2,  /* per-slab plaquette sums of the selected components     */
-  ML_K_ACCUMULATE = 3, /* accumulation of T^(d) and TO^(d) for one configuration  */
-  ML_K_PRODUCTS = 4    /* cross-slab products and their reduction over sites     */
+  ML_K_HEATBATH = 0,   /* one heatbath pass kernel (mu = 1, even sites, slab mask) */
+  ML_K_OVERRELAX = 1,  /* one overrelaxation pass kernel (same links)             */
+  ML_K_RECORD = 2,     /* record of one sub-update: slab phase and plaquette sums */
+  ML_K_ACCUMULATE = 3, /* fold of a full batch of records into the slab sums      */
+  ML_K_PRODUCTS = 4,   /* cross-slab products and their reduction over sites      */
+  ML_K_SWEEP = 5       /* one compound slab sweep in the persistent sweep kernel  */
 } ml_kernel_class;
 
 /* Average device time in milliseconds of `reps` back-to-back launches of one
@@ -204,6 +205,10 @@ typedef enum {
  * of the angles, so the Markov chain is unchanged; the slab accumulators are
  * left undefined (every measurement clears them first).  Blocking. */
 int ml_kernel_timing(ml_lattice *h, int kernel, int reps, double *avg_ms);
+
+/* Number of sub-update records the handle folds into its slab sums per
+ * accumulation pass (chosen at ml_create from the record size, at most 16). */
+int ml_batch_slots(ml_lattice *h, int *n);
 
 /* Static text for a status code. */
 const char *ml_error_string(int status);

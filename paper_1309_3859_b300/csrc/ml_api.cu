@@ -54,7 +54,11 @@ struct ml_lattice {
   MeasLayout meas{};
   double2 *accT = nullptr, *accO = nullptr, *acc4T = nullptr, *acc4O = nullptr;
   size_t accT_bytes = 0, accO_bytes = 0, acc4T_bytes = 0, acc4O_bytes = 0;
-  void* osum = nullptr;
+  void* osum = nullptr;       // [nslab][nc][2][Ns][kBatch] plaquette slab sums
+  void* theta_rec = nullptr;  // [nslab][Ns][kBatch] slab phase sums
+  int nB = kBatch;            // sub-update records folded per accumulation pass
+  unsigned long long* bar = nullptr;  // arrival counter of the persistent sweep kernel's grid barrier
+  unsigned long long* scratch_n = nullptr;
   double* vac_part = nullptr;
   double* vac_acc = nullptr;
   double2* partial = nullptr;
@@ -63,7 +67,8 @@ struct ml_lattice {
   void* scratch_theta = nullptr;
   double* rec_buf = nullptr;
   size_t rec_cap = 0;
-  Graph g_full, g_sub, g_outer;
+  Graph g_full, g_outer, g_flush;
+  Graph g_sub[kBatch];
 };
 
 namespace {
@@ -128,23 +133,30 @@ size_t record_len(int nr, int nrf, int np) {
          static_cast<size_t>(nr) * 2 + 1;
 }
 
-// one compound sweep: sweep number += 1, heatbath sweep, n_or OR sweeps
-void enqueue_compound_sweep(ml_lattice* h, int d) {
-  launch_sweep_begin(h->d_n, h->stream);
-  for (int mu = 0; mu < 4; ++mu)
-    for (int par = 0; par < 2; ++par)
-      launch_update_pass(h->fp64, h->theta, h->g, mu, par, d, 0, h->d_n, 0, h->seed, h->beta, h->d_err, h->stream);
-  for (int o = 0; o < h->n_or; ++o)
-    for (int mu = 0; mu < 4; ++mu)
-      for (int par = 0; par < 2; ++par)
-        launch_update_pass(h->fp64, h->theta, h->g, mu, par, d, 1, h->d_n, 0, h->seed, h->beta, h->d_err, h->stream);
+// n compound sweeps (heatbath + n_or overrelaxation sweeps) with slab mask d
+// in one cooperative launch of the persistent sweep kernel
+int enqueue_sweeps(ml_lattice* h, int n, int d) {
+  if (n <= 0) return ML_OK;
+  return launch_sweeps(h->fp64, h->theta, h->g, d, h->n_or, n, h->d_n, h->seed, h->beta, h->d_err, h->bar,
+                       h->stream)
+             ? ML_ECUDA
+             : ML_OK;
 }
 
-// accumulation of the current configuration into the inner slab sums
-void enqueue_accumulate(ml_lattice* h) {
-  launch_plaq_slab(h->fp64, h->theta, h->g, h->slab, h->meas, h->osum, h->vac_part, h->stream);
+// one slab sub-update: compound sweep with the inner mask, then the record of
+// the new configuration into ring slot `slot` and its vacuum sums
+int enqueue_sub_update(ml_lattice* h, int slot) {
+  int st = enqueue_sweeps(h, 1, h->slab);
+  if (st) return st;
+  launch_record(h->fp64, h->theta, h->g, h->slab, h->meas, slot, h->theta_rec, h->osum, h->vac_part, h->stream);
   launch_vac_accumulate(h->vac_part, h->nparts_inner, h->vac_acc, 1.0 / h->g.V, h->stream);
-  launch_accumulate(h->fp64, h->theta, h->g, h->slab, h->meas, h->osum, h->accT, h->accO, h->stream);
+  return ML_OK;
+}
+
+// fold the first nrec ring slots into the inner slab sums
+void enqueue_fold(ml_lattice* h, int nrec) {
+  launch_accumulate_batch(h->fp64, h->g, h->slab, h->meas, h->theta_rec, h->osum, nrec, h->accT, h->accO,
+                          h->stream);
 }
 
 template <typename F>
@@ -153,10 +165,13 @@ int capture(ml_lattice* h, Graph* out, F&& body) {
   ML_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   tl_capturing = 1;
   tl_captured = 0;
-  body();
+  const int body_status = body();
   tl_capturing = 0;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-  if (e != cudaSuccess) return ML_ECUDA;
+  if (e != cudaSuccess || body_status != ML_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return body_status != ML_OK ? body_status : ML_ECUDA;
+  }
   e = cudaGraphInstantiate(&out->exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return ML_ECUDA;
@@ -184,11 +199,29 @@ int check_errors(ml_lattice* h) {
 }
 
 void destroy_graphs(ml_lattice* h) {
-  for (Graph* gr : {&h->g_full, &h->g_sub, &h->g_outer})
+  std::vector<Graph*> all = {&h->g_full, &h->g_outer, &h->g_flush};
+  for (int j = 0; j < kBatch; ++j) all.push_back(&h->g_sub[j]);
+  for (Graph* gr : all)
     if (gr->exec) {
       cudaGraphExecDestroy(gr->exec);
       gr->exec = nullptr;
     }
+}
+
+// inner loop of n_sub slab sub-updates, folding the records every nB
+int run_inner_loop(ml_lattice* h) {
+  int slot = 0;
+  for (int i = 0; i < h->n_sub; ++i) {
+    int st = launch_graph(h, h->g_sub[slot]);
+    if (st) return st;
+    if (++slot == h->nB) {
+      st = launch_graph(h, h->g_flush);
+      if (st) return st;
+      slot = 0;
+    }
+  }
+  if (slot > 0) enqueue_fold(h, slot);
+  return ML_OK;
 }
 
 int zero_inner(ml_lattice* h) {
@@ -213,7 +246,7 @@ int enqueue_measurements(ml_lattice* h, int n_meas, double* rec) {
   for (int j = 0; j < n_meas; ++j) {
     double* out = rec + static_cast<size_t>(j) * m.rec_len;
     ML_CUDA(cudaMemsetAsync(out, 0, m.rec_len * sizeof(double), h->stream));
-    for (int s = 0; s < h->k_between; ++s) {
+    if (h->k_between > 0) {
       int st = launch_graph(h, h->g_full);
       if (st) return st;
     }
@@ -222,11 +255,8 @@ int enqueue_measurements(ml_lattice* h, int n_meas, double* rec) {
     int ncfg = 0;
     if (h->outer_slab == 0) {
       int st = zero_inner(h);
+      if (!st) st = run_inner_loop(h);
       if (st) return st;
-      for (int i = 0; i < h->n_sub; ++i) {
-        st = launch_graph(h, h->g_sub);
-        if (st) return st;
-      }
       launch_products(h->g, nslab_in, m, h->accT, h->accO, 1.0 / h->n_sub, h->partial, out, h->stream);
       ncfg = h->n_sub;
     } else {
@@ -237,11 +267,8 @@ int enqueue_measurements(ml_lattice* h, int n_meas, double* rec) {
         int st = launch_graph(h, h->g_outer);
         if (st) return st;
         st = zero_inner(h);
+        if (!st) st = run_inner_loop(h);
         if (st) return st;
-        for (int i = 0; i < h->n_sub; ++i) {
-          st = launch_graph(h, h->g_sub);
-          if (st) return st;
-        }
         launch_combine(h->g, nslab_out, h->outer_slab / h->slab, m, h->accT, h->accO, 1.0 / h->n_sub, h->acc4T,
                        h->acc4O, h->stream);
       }
@@ -371,7 +398,10 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
     h->acc4T = static_cast<double2*>(dev_alloc(h, h->acc4T_bytes));
     h->acc4O = static_cast<double2*>(dev_alloc(h, h->acc4O_bytes));
   }
-  h->osum = dev_alloc(h, static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * tsz);
+  h->osum = dev_alloc(h, static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * kBatch * tsz);
+  h->theta_rec = dev_alloc(h, static_cast<size_t>(nslab_in) * g.Ns * kBatch * tsz);
+  h->bar = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long)));
+  h->scratch_n = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long)));
   h->nparts_inner = vac_part_count(g, h->slab);
   h->vac_part = static_cast<double*>(dev_alloc(h, static_cast<size_t>(h->nparts_inner) * 12 * sizeof(double)));
   h->vac_acc = static_cast<double*>(dev_alloc(h, 12 * sizeof(double)));
@@ -380,7 +410,8 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
   const size_t nvw = static_cast<size_t>((g.V + 255) / 256) * 8;
   const size_t part = std::max(nout * nw, static_cast<size_t>(nr) * nw + nvw / 2 + 1);
   h->partial = static_cast<double2*>(dev_alloc(h, part * sizeof(double2)));
-  bool ok = h->theta && h->d_n && h->d_err && h->d_lists && h->accT && h->accO && h->osum && h->vac_part &&
+  bool ok = h->theta && h->d_n && h->d_err && h->d_lists && h->accT && h->accO && h->osum && h->theta_rec &&
+            h->bar && h->scratch_n && h->vac_part &&
             h->vac_acc && h->partial && (!nslab_out || (h->acc4T && h->acc4O));
   if (!ok) {
     free_all(h);
@@ -416,16 +447,25 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_n, 0, sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->vac_acc, 0, 12 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream);
+  // ring slots not yet written in a batch are multiplied by zero: keep them finite
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->osum, 0, static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * kBatch * tsz, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->theta_rec, 0, static_cast<size_t>(nslab_in) * g.Ns * kBatch * tsz, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->vac_part, 0, static_cast<size_t>(h->nparts_inner) * 12 * sizeof(double), h->stream);
   if (e == cudaSuccess) launch_hot_start(h->fp64, h->theta, g, h->seed, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // lists are host temporaries
   if (e == cudaSuccess) e = cudaGetLastError();
   st = e == cudaSuccess ? ML_OK : ML_ECUDA;
-  if (!st) st = capture(h, &h->g_full, [&] { enqueue_compound_sweep(h, 0); });
-  if (!st) st = capture(h, &h->g_sub, [&] {
-    enqueue_compound_sweep(h, h->slab);
-    enqueue_accumulate(h);
+  if (!st && h->k_between > 0) st = capture(h, &h->g_full, [&] { return enqueue_sweeps(h, h->k_between, 0); });
+  for (int j = 0; j < h->nB && !st; ++j) st = capture(h, &h->g_sub[j], [&] { return enqueue_sub_update(h, j); });
+  if (!st) st = capture(h, &h->g_flush, [&] {
+    enqueue_fold(h, h->nB);
+    return ML_OK;
   });
-  if (!st && h->outer_slab) st = capture(h, &h->g_outer, [&] { enqueue_compound_sweep(h, h->outer_slab); });
+  if (!st && h->outer_slab) st = capture(h, &h->g_outer, [&] { return enqueue_sweeps(h, 1, h->outer_slab); });
   if (st) {
     destroy_graphs(h);
     free_all(h);
@@ -454,19 +494,18 @@ int ml_sync(ml_lattice* h) {
 
 int ml_thermalize(ml_lattice* h, int n_sweeps) {
   if (!h || n_sweeps < 0) return ML_EINVAL;
-  for (int s = 0; s < n_sweeps; ++s) {
-    int st = launch_graph(h, h->g_full);
-    if (st) return st;
-  }
+  int st = enqueue_sweeps(h, n_sweeps, 0);
+  if (st) return st;
   h->h_n += static_cast<uint64_t>(n_sweeps);
   return ML_OK;
 }
 
 int ml_compound_sweeps(ml_lattice* h, int n, int slab_d) {
   if (!h || n < 0 || slab_d < 0) return ML_EINVAL;
-  for (int s = 0; s < n; ++s) enqueue_compound_sweep(h, slab_d);
+  int st = enqueue_sweeps(h, n, slab_d);
+  if (st) return st;
   h->h_n += static_cast<uint64_t>(n);
-  return cuda_status(cudaGetLastError());
+  return ML_OK;
 }
 
 int ml_update_pass(ml_lattice* h, int mu, int parity, int slab_d, uint64_t n, int kind) {
@@ -505,7 +544,9 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
   ML_CUDA(cudaMemsetAsync(h->vac_acc, 0, 12 * sizeof(double), h->stream));
   st = zero_inner(h);
   if (st) return st;
-  enqueue_accumulate(h);
+  launch_record(h->fp64, h->theta, h->g, h->slab, m, 0, h->theta_rec, h->osum, h->vac_part, h->stream);
+  launch_vac_accumulate(h->vac_part, h->nparts_inner, h->vac_acc, 1.0 / h->g.V, h->stream);
+  enqueue_fold(h, 1);
   launch_products(h->g, h->g.Nt / h->slab, m, h->accT, h->accO, 1.0, h->partial, out, h->stream);
   launch_write_vac(h->vac_acc, 1.0, m, out, h->stream);
   ML_CUDA(cudaGetLastError());
@@ -561,7 +602,7 @@ int ml_set_sweep(ml_lattice* h, uint64_t n) {
 }
 
 int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
-  if (!h || !avg_ms || reps < 1 || kernel < ML_K_HEATBATH || kernel > ML_K_PRODUCTS) return ML_EINVAL;
+  if (!h || !avg_ms || reps < 1 || kernel < ML_K_HEATBATH || kernel > ML_K_SWEEP) return ML_EINVAL;
   const size_t tbytes = 4ull * h->g.V * (h->fp64 ? sizeof(double) : sizeof(float));
   if (!h->scratch_theta) {
     h->scratch_theta = dev_alloc(h, tbytes);
@@ -570,25 +611,31 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   int st = ensure_rec(h, h->meas.rec_len);
   if (st) return st;
   ML_CUDA(cudaMemcpyAsync(h->scratch_theta, h->theta, tbytes, cudaMemcpyDeviceToDevice, h->stream));
+  ML_CUDA(cudaMemcpyAsync(h->scratch_n, h->d_n, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->stream));
   cudaEvent_t e0, e1;
   ML_CUDA(cudaEventCreate(&e0));
   ML_CUDA(cudaEventCreate(&e1));
   ML_CUDA(cudaEventRecord(e0, h->stream));
-  for (int i = 0; i < reps; ++i) {
+  for (int i = 0; i < reps && !st; ++i) {
     switch (kernel) {
       case ML_K_HEATBATH:
       case ML_K_OVERRELAX:
         launch_update_pass(h->fp64, h->scratch_theta, h->g, 1, 0, h->slab, kernel == ML_K_HEATBATH ? 0 : 1, nullptr,
                            h->h_n + 1, h->seed, h->beta, h->d_err, h->stream);
         break;
-      case ML_K_PLAQ_SLAB:
-        launch_plaq_slab(h->fp64, h->theta, h->g, h->slab, h->meas, h->osum, h->vac_part, h->stream);
+      case ML_K_RECORD:
+        launch_record(h->fp64, h->theta, h->g, h->slab, h->meas, 0, h->theta_rec, h->osum, h->vac_part, h->stream);
         break;
       case ML_K_ACCUMULATE:
-        launch_accumulate(h->fp64, h->theta, h->g, h->slab, h->meas, h->osum, h->accT, h->accO, h->stream);
+        enqueue_fold(h, h->nB);
+        break;
+      case ML_K_PRODUCTS:
+        launch_products(h->g, h->g.Nt / h->slab, h->meas, h->accT, h->accO, 1.0, h->partial, h->rec_buf, h->stream);
         break;
       default:
-        launch_products(h->g, h->g.Nt / h->slab, h->meas, h->accT, h->accO, 1.0, h->partial, h->rec_buf, h->stream);
+        if (launch_sweeps(h->fp64, h->scratch_theta, h->g, h->slab, h->n_or, 1, h->scratch_n, h->seed, h->beta,
+                          h->d_err, h->bar, h->stream))
+          st = ML_ECUDA;
     }
   }
   ML_CUDA(cudaEventRecord(e1, h->stream));
@@ -598,7 +645,14 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   *avg_ms = static_cast<double>(ms) / reps;
+  if (st) return st;
   return check_errors(h);
+}
+
+int ml_batch_slots(ml_lattice* h, int* n) {
+  if (!h || !n) return ML_EINVAL;
+  *n = h->nB;
+  return ML_OK;
 }
 
 int ml_philox(const uint32_t* ctr, const uint32_t* key, size_t n, uint32_t* out) {

@@ -30,22 +30,31 @@ struct MeasLayout {
 void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parity, int slab_d, int kind,
                         const unsigned long long* n_dev, unsigned long long n_fixed, uint64_t seed, double beta,
                         int* err, cudaStream_t s);
-void launch_sweep_begin(unsigned long long* n_dev, cudaStream_t s);
+// n_compound compound sweeps in one cooperative launch (grid barrier between
+// passes on the monotonic counter *bar, zeroed once at creation).  Returns 0,
+// or -1 when the launch fails.
+int launch_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
+                  unsigned long long* n_dev, uint64_t seed, double beta, int* err, unsigned long long* bar,
+                  cudaStream_t s);
 void launch_hot_start(bool fp64, void* theta, const Geom& g, uint64_t seed, cudaStream_t s);
 void launch_angles_to_soa(bool fp64, const double* canon, void* theta, const Geom& g, cudaStream_t s);
 void launch_angles_from_soa(bool fp64, const void* theta, double* canon, const Geom& g, cudaStream_t s);
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n, cudaStream_t s);
 
 // ---- measurement (ml_measure.cu) ----
-// Per-slab plaquette sums O[s][ci][k][x] for slabs of thickness d, and warp
-// partial sums of Re/Im P_c over all sites for the vacuum.
-void launch_plaq_slab(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, void* osum,
-                      double* vac_part, cudaStream_t s);
+// Record of one sub-update configuration into ring slot `slot`: slab phase
+// sums theta_rec[s][x][kBatch] and plaquette slab sums
+// osum[s][ci][k][x][kBatch] (slabs of thickness d), plus warp partials of the
+// site sums of Re/Im P_c for the vacuum.
+void launch_record(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, int slot,
+                   void* theta_rec, void* osum, double* vac_part, cudaStream_t s);
 int vac_part_count(const Geom& g, int d);
 void launch_vac_accumulate(const double* vac_part, int nparts, double* vac_acc, double scale, cudaStream_t s);
-// accT[s][iR][x] += T_s(x, R); accO[s][irf][b][ci][k][x] += T_s(x, rf) O[s][ci][k][x0]
-void launch_accumulate(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, const void* osum,
-                       double2* accT, double2* accO, cudaStream_t s);
+// Fold ring slots 0 .. nrec-1 (nrec <= kBatch) into the slab sums:
+// accT[s][iR][x] += sum_j T_j(x, s, R); accO[s][f][b][ci][k][x] += sum_j
+// T_j(x, s, rf) O_j[s][ci][k](x0)
+void launch_accumulate_batch(bool fp64, const Geom& g, int d, const MeasLayout& m, const void* theta_rec,
+                             const void* osum, int nrec, double2* accT, double2* accO, cudaStream_t s);
 // two-level combination of inner averages (sum / n_inner) into outer sums
 void launch_combine(const Geom& g, int n_inner_slabs, int q, const MeasLayout& m, const double2* accT,
                     const double2* accO, double inv_n, double2* acc4T, double2* acc4O, cudaStream_t s);

@@ -64,13 +64,45 @@ __device__ __forceinline__ double2 unit_phase(double phi) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-slab plaquette sums O[s][ci][k][x] = sum_{t in slab} (Re, Im) P_c(x, t)
-// and warp partials of the site sums of Re / Im P_c (vacuum).
+// Ring of sub-update records, slot-fastest: element (slot j) of
+//   theta_rec[s][x][kBatch]          Theta_s(x) = sum_{t in slab} theta_0(x, t)
+//                                    (FP32: summed in double, reduced to
+//                                    [-pi, pi) and rounded)
+//   osum[s][ci][k][x][kBatch]        sum_{t in slab} (Re, Im) P_c(x, t)
+// so the fold reads all records of one site as one contiguous vector.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_plaq_slab(const T* __restrict__ th, Geom g, int d, int nslab, int nc,
-                                                   const int* __restrict__ comp, T* __restrict__ osum,
-                                                   double* __restrict__ vac_part) {
+__device__ __forceinline__ void load_batch(const T* __restrict__ p, T v[kBatch]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int j = 0; j < kBatch / 4; ++j) {
+      const float4 a = q[j];
+      v[4 * j] = a.x;
+      v[4 * j + 1] = a.y;
+      v[4 * j + 2] = a.z;
+      v[4 * j + 3] = a.w;
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int j = 0; j < kBatch / 2; ++j) {
+      const double2 a = q[j];
+      v[2 * j] = a.x;
+      v[2 * j + 1] = a.y;
+    }
+  }
+}
+
+// Record of one configuration into ring slot `slot`; grid (sites x slabs,
+// nc + 1): blockIdx.y < nc handles component ci = blockIdx.y, blockIdx.y = nc
+// the slab phase sums.  Component blocks also write warp partials of the site
+// sums of Re / Im P_c (vac_part[warp][c][k]; entries of unselected components
+// stay zero).
+template <typename T>
+__global__ void __launch_bounds__(256) k_record(const T* __restrict__ th, Geom g, int d, int nslab, int nc,
+                                                const int* __restrict__ comp, int slot, T* __restrict__ theta_rec,
+                                                T* __restrict__ osum, double* __restrict__ vac_part) {
   using P = Prec<T>;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = idx < g.Ns * nslab;
@@ -78,32 +110,36 @@ __global__ void __launch_bounds__(256) k_plaq_slab(const T* __restrict__ th, Geo
   const int x = live ? idx - s * g.Ns : 0;
   int c[4];
   spatial_coords(g, x, &c[1], &c[2], &c[3]);
-  double vac[12];
-#pragma unroll
-  for (int j = 0; j < 12; ++j) vac[j] = 0.0;
-  for (int ci = 0; ci < nc; ++ci) {
-    const int cc = comp[ci];
-    const int mu = c_plane_mu[cc], nu = c_plane_nu[cc];
-    T re = T(0), im = T(0);
+  const int ci = blockIdx.y;
+  if (ci == nc) {
     if (live) {
-      for (int t = s * d; t < s * d + d; ++t) {
-        c[0] = t;
-        T sn, cs;
-        P::sincos_(plaquette_angle(th, g, c, mu, nu), &sn, &cs);
-        re += cs;
-        im += sn;
-      }
-      osum[(static_cast<size_t>(s * nc + ci) * 2 + 0) * g.Ns + x] = re;
-      osum[(static_cast<size_t>(s * nc + ci) * 2 + 1) * g.Ns + x] = im;
+      double tsum = 0.0;
+      for (int t = s * d; t < s * d + d; ++t) tsum += theta0(th, g, c[1], c[2], c[3], t);
+      theta_rec[(static_cast<size_t>(s) * g.Ns + x) * kBatch + slot] =
+          static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
     }
-    vac[2 * cc] = static_cast<double>(re);
-    vac[2 * cc + 1] = static_cast<double>(im);
+    return;  // the whole block takes this branch
   }
-  const int warp = idx >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < 12; ++j) {
-    const double v = warp_sum(vac[j]);
-    if (lane == 0) vac_part[static_cast<size_t>(warp) * 12 + j] = v;
+  const int cc = comp[ci];
+  const int mu = c_plane_mu[cc], nu = c_plane_nu[cc];
+  T re = T(0), im = T(0);
+  if (live) {
+    for (int t = s * d; t < s * d + d; ++t) {
+      c[0] = t;
+      T sn, cs;
+      P::sincos_(plaquette_angle(th, g, c, mu, nu), &sn, &cs);
+      re += cs;
+      im += sn;
+    }
+    osum[((static_cast<size_t>(s * nc + ci) * 2 + 0) * g.Ns + x) * kBatch + slot] = re;
+    osum[((static_cast<size_t>(s * nc + ci) * 2 + 1) * g.Ns + x) * kBatch + slot] = im;
+  }
+  const double vr = warp_sum(static_cast<double>(re));
+  const double vi = warp_sum(static_cast<double>(im));
+  if ((threadIdx.x & 31) == 0) {
+    const size_t w = idx >> 5;
+    vac_part[w * 12 + 2 * cc] = vr;
+    vac_part[w * 12 + 2 * cc + 1] = vi;
   }
 }
 
@@ -124,47 +160,85 @@ __global__ void __launch_bounds__(256) k_vac_accumulate(const double* __restrict
   }
 }
 
+// e^{i (Theta(x + r) - Theta(x))} for the first nrec records, zero beyond
+template <typename T>
+__device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const T* __restrict__ rec_xr, int nrec,
+                                             T er[kBatch], T ei[kBatch]) {
+  T a[kBatch], b[kBatch];
+  load_batch<T>(rec_x, a);
+  load_batch<T>(rec_xr, b);
+#pragma unroll
+  for (int j = 0; j < kBatch; ++j) {
+    er[j] = T(0);
+    ei[j] = T(0);
+    if (j < nrec) Prec<T>::sincos_(b[j] - a[j], &ei[j], &er[j]);
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Accumulation of T^(d) and TO^(d) for one configuration (one thread per
-// spatial site x and slab s).
+// Fold of nrec <= kBatch records into the double-precision slab sums:
+//   accT[s][a][x]              += sum_j T_j(x, s, R_a)
+//   accO[s][f][b][ci][k][x]    += sum_j T_j(x, s, rf_f) O_j[s][ci][k](x0)
+// The sum over the batch is formed in the records' precision and added once,
+// so each accumulator is read and written once per batch.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_accumulate(const T* __restrict__ th, Geom g, int d, int nslab, MeasLayout m,
-                                                    const T* __restrict__ osum, double2* __restrict__ accT,
-                                                    double2* __restrict__ accO) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= g.Ns * nslab) return;
-  const int s = idx / g.Ns;
-  const int x = idx - s * g.Ns;
+__global__ void __launch_bounds__(256) k_accum_T(Geom g, MeasLayout m, const T* __restrict__ theta_rec, int nrec,
+                                                 double2* __restrict__ accT) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.Ns) return;
+  const int s = blockIdx.y / m.nR, a = blockIdx.y - s * m.nR;
   int cx, cy, cz;
   spatial_coords(g, x, &cx, &cy, &cz);
-  double theta_x = 0.0;
-  for (int t = s * d; t < s * d + d; ++t) theta_x += theta0(th, g, cx, cy, cz, t);
-
-  for (int a = 0; a < m.nR; ++a) {
-    const int xr = wrapc(cx + m.R[a], g.L);
-    double theta_r = 0.0;
-    for (int t = s * d; t < s * d + d; ++t) theta_r += theta0(th, g, xr, cy, cz, t);
-    const double2 e = unit_phase<T>(theta_r - theta_x);
-    double2* p = accT + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
-    *p = cadd(*p, e);
-  }
-  for (int f = 0; f < m.nrf; ++f) {
-    const int rf = m.rf[f];
-    const int xr = wrapc(cx + rf, g.L);
-    double theta_r = 0.0;
-    for (int t = s * d; t < s * d + d; ++t) theta_r += theta0(th, g, xr, cy, cz, t);
-    const double2 e = unit_phase<T>(theta_r - theta_x);
-    const int x0x = wrapc(cx + rf / 2, g.L);
-    for (int b = 0; b < m.np; ++b) {
-      const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
-      for (int ci = 0; ci < m.nc; ++ci) {
+  const int xr = wrapc(cx + m.R[a], g.L) + g.L * (cy + g.L * cz);
+  const T* rec = theta_rec + static_cast<size_t>(s) * g.Ns * kBatch;
+  T er[kBatch], ei[kBatch];
+  batch_phases<T>(rec + static_cast<size_t>(x) * kBatch, rec + static_cast<size_t>(xr) * kBatch, nrec, er, ei);
+  T sr = T(0), si = T(0);
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const double o = static_cast<double>(osum[(static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0]);
-          double2* p = accO + ((((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
-          *p = cadd(*p, cscale(e, o));
+  for (int j = 0; j < kBatch; ++j) {
+    sr += er[j];
+    si += ei[j];
+  }
+  double2* p = accT + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
+  *p = make_double2(p->x + static_cast<double>(sr), p->y + static_cast<double>(si));
+}
+
+constexpr int kProbesPerThread = 3;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_accum_O(Geom g, MeasLayout m, const T* __restrict__ theta_rec,
+                                                 const T* __restrict__ osum, int nrec, double2* __restrict__ accO) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.Ns) return;
+  const int nbg = (m.np + kProbesPerThread - 1) / kProbesPerThread;
+  const int bg = blockIdx.y % nbg;
+  const int sf = blockIdx.y / nbg;
+  const int s = sf / m.nrf, f = sf - s * m.nrf;
+  int cx, cy, cz;
+  spatial_coords(g, x, &cx, &cy, &cz);
+  const int rf = m.rf[f];
+  const int xr = wrapc(cx + rf, g.L) + g.L * (cy + g.L * cz);
+  const T* trec = theta_rec + static_cast<size_t>(s) * g.Ns * kBatch;
+  T er[kBatch], ei[kBatch];
+  batch_phases<T>(trec + static_cast<size_t>(x) * kBatch, trec + static_cast<size_t>(xr) * kBatch, nrec, er, ei);
+  const int x0x = wrapc(cx + rf / 2, g.L);
+  const int b_end = min(m.np, (bg + 1) * kProbesPerThread);
+  for (int b = bg * kProbesPerThread; b < b_end; ++b) {
+    const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
+    for (int ci = 0; ci < m.nc; ++ci) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        T o[kBatch];
+        load_batch<T>(osum + ((static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0) * kBatch, o);
+        T sr = T(0), si = T(0);
+#pragma unroll
+        for (int j = 0; j < kBatch; ++j) {
+          sr += er[j] * o[j];
+          si += ei[j] * o[j];
         }
+        double2* p = accO + ((((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
+        *p = make_double2(p->x + static_cast<double>(sr), p->y + static_cast<double>(si));
       }
     }
   }
@@ -219,56 +293,68 @@ __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, Mea
 }
 
 // ---------------------------------------------------------------------------
-// Cross-slab products, one thread per spatial site, warp partials per output:
-//   o in [0, nr)            P(r)
-//   o in [nr, nr+nrf)       P at the field separations
-//   o in [nr+nrf, ...)      W(f, b, ci, k)
+// Cross-slab products with per-warp partial sums over sites:
+//   o in [0, nr)            P(r)      = sum_x prod_s [T]_s(x, r)
+//   o in [nr, nr+nrf)       P(rf)
+//   o in [nr+nrf, ...)      W(f, j)   = sum_x sum_s [TO]_s(x, f, j) R_s(x, f),
+//                           R_s = prod_{s' != s} [T]_{s'} (prefix x suffix),
+//                           j = (b * nc + ci) * 2 + k
+// k_products_P: grid (sites, nr + nrf); k_products_W: grid (sites, nrf,
+// chunks of kWChunk values of j).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_products(Geom g, int nslab, MeasLayout m, const double2* __restrict__ accT,
-                                                  const double2* __restrict__ accO, double inv_n,
-                                                  double2* __restrict__ partial, int nwarps) {
+constexpr int kWChunk = 12;
+
+__global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayout m, const double2* __restrict__ accT,
+                                                    double inv_n, double2* __restrict__ partial, int nwarps) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = x < g.Ns;
-  const int warp = x >> 5, lane = threadIdx.x & 31;
-  for (int a = 0; a < m.nr; ++a) {
-    double2 prod = make_double2(live ? 1.0 : 0.0, 0.0);
-    if (live)
-      for (int s = 0; s < nslab; ++s)
-        prod = cmul(prod, cscale(accT[(static_cast<size_t>(s) * m.nR + m.r_idx[a]) * g.Ns + x], inv_n));
-    prod = warp_sum(prod);
-    if (lane == 0) partial[static_cast<size_t>(a) * nwarps + warp] = prod;
-  }
-  double2 ts[kMaxSlabs], rest[kMaxSlabs];
+  const int o = blockIdx.y;
+  const int a = o < m.nr ? m.r_idx[o] : m.rf_idx[o - m.nr];
+  double2 prod = make_double2(live ? 1.0 : 0.0, 0.0);
+  if (live)
+    for (int s = 0; s < nslab; ++s) prod = cmul(prod, accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]);
+  // (1/n)^nslab applied once
+  double scale = 1.0;
+  for (int s = 0; s < nslab; ++s) scale *= inv_n;
+  prod = warp_sum(cscale(prod, scale));
+  if ((threadIdx.x & 31) == 0) partial[static_cast<size_t>(o) * nwarps + (x >> 5)] = prod;
+}
+
+__global__ void __launch_bounds__(256) k_products_W(Geom g, int nslab, MeasLayout m, const double2* __restrict__ accT,
+                                                    const double2* __restrict__ accO, double inv_n,
+                                                    double2* __restrict__ partial, int nwarps) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = x < g.Ns;
+  const int f = blockIdx.y;
   const int nW = m.np * m.nc * 2;
-  for (int f = 0; f < m.nrf; ++f) {
-    double2 full = make_double2(0.0, 0.0);
-    if (live) {
-      const int a = m.rf_idx[f];
-      for (int s = 0; s < nslab; ++s) ts[s] = cscale(accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x], inv_n);
-      double2 run = make_double2(1.0, 0.0);
+  const int j0 = blockIdx.z * kWChunk;
+  const int j1 = min(nW, j0 + kWChunk);
+  double2 rest[kMaxSlabs];
+  if (live) {
+    const int a = m.rf_idx[f];
+    double2 run = make_double2(1.0, 0.0);
+    for (int s = 0; s < nslab; ++s) {  // prefix products
+      rest[s] = run;
+      run = cmul(run, accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]);
+    }
+    run = make_double2(1.0, 0.0);
+    for (int s = nslab - 1; s >= 0; --s) {  // times suffix products
+      rest[s] = cmul(rest[s], run);
+      run = cmul(run, accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]);
+    }
+  }
+  double scale = 1.0;  // [TO] and nslab - 1 factors [T]: (1/n)^nslab
+  for (int s = 0; s < nslab; ++s) scale *= inv_n;
+  for (int j = j0; j < j1; ++j) {
+    double2 sum = make_double2(0.0, 0.0);
+    if (live)
       for (int s = 0; s < nslab; ++s) {
-        rest[s] = run;
-        run = cmul(run, ts[s]);
+        const double2 o = accO[((static_cast<size_t>(s) * m.nrf + f) * nW + j) * g.Ns + x];
+        sum = cadd(sum, cmul(o, rest[s]));
       }
-      full = run;
-      run = make_double2(1.0, 0.0);
-      for (int s = nslab - 1; s >= 0; --s) {
-        rest[s] = cmul(rest[s], run);
-        run = cmul(run, ts[s]);
-      }
-    }
-    full = warp_sum(full);
-    if (lane == 0) partial[static_cast<size_t>(m.nr + f) * nwarps + warp] = full;
-    for (int j = 0; j < nW; ++j) {  // j = (b * nc + ci) * 2 + k
-      double2 sum = make_double2(0.0, 0.0);
-      if (live)
-        for (int s = 0; s < nslab; ++s) {
-          const double2 o = accO[((static_cast<size_t>(s) * m.nrf + f) * nW + j) * g.Ns + x];
-          sum = cadd(sum, cmul(cscale(o, inv_n), rest[s]));
-        }
-      sum = warp_sum(sum);
-      if (lane == 0) partial[static_cast<size_t>(m.nr + m.nrf + f * nW + j) * nwarps + warp] = sum;
-    }
+    sum = warp_sum(cscale(sum, scale));
+    if ((threadIdx.x & 31) == 0)
+      partial[static_cast<size_t>(m.nr + m.nrf + f * nW + j) * nwarps + (x >> 5)] = sum;
   }
 }
 
@@ -411,16 +497,16 @@ int vac_part_count(const Geom& g, int d) {
 
 int product_partial_count(const Geom& g) { return blocks_for(g.Ns, 256) * 8; }
 
-void launch_plaq_slab(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, void* osum,
-                      double* vac_part, cudaStream_t s) {
+void launch_record(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, int slot,
+                   void* theta_rec, void* osum, double* vac_part, cudaStream_t s) {
   const int nslab = g.Nt / d;
-  const int nb = blocks_for(static_cast<long long>(g.Ns) * nslab, 256);
+  const dim3 grid(blocks_for(static_cast<long long>(g.Ns) * nslab, 256), m.nc + 1);
   if (fp64)
-    k_plaq_slab<double><<<nb, 256, 0, s>>>(static_cast<const double*>(theta), g, d, nslab, m.nc, m.comp,
-                                           static_cast<double*>(osum), vac_part);
+    k_record<double><<<grid, 256, 0, s>>>(static_cast<const double*>(theta), g, d, nslab, m.nc, m.comp, slot,
+                                          static_cast<double*>(theta_rec), static_cast<double*>(osum), vac_part);
   else
-    k_plaq_slab<float><<<nb, 256, 0, s>>>(static_cast<const float*>(theta), g, d, nslab, m.nc, m.comp,
-                                          static_cast<float*>(osum), vac_part);
+    k_record<float><<<grid, 256, 0, s>>>(static_cast<const float*>(theta), g, d, nslab, m.nc, m.comp, slot,
+                                         static_cast<float*>(theta_rec), static_cast<float*>(osum), vac_part);
   count_launches(1);
 }
 
@@ -429,17 +515,26 @@ void launch_vac_accumulate(const double* vac_part, int nparts, double* vac_acc, 
   count_launches(1);
 }
 
-void launch_accumulate(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, const void* osum,
-                       double2* accT, double2* accO, cudaStream_t s) {
+void launch_accumulate_batch(bool fp64, const Geom& g, int d, const MeasLayout& m, const void* theta_rec,
+                             const void* osum, int nrec, double2* accT, double2* accO, cudaStream_t s) {
   const int nslab = g.Nt / d;
-  const int nb = blocks_for(static_cast<long long>(g.Ns) * nslab, 256);
+  const dim3 gt(blocks_for(g.Ns, 256), nslab * m.nR);
   if (fp64)
-    k_accumulate<double><<<nb, 256, 0, s>>>(static_cast<const double*>(theta), g, d, nslab, m,
-                                            static_cast<const double*>(osum), accT, accO);
+    k_accum_T<double><<<gt, 256, 0, s>>>(g, m, static_cast<const double*>(theta_rec), nrec, accT);
   else
-    k_accumulate<float><<<nb, 256, 0, s>>>(static_cast<const float*>(theta), g, d, nslab, m,
-                                           static_cast<const float*>(osum), accT, accO);
+    k_accum_T<float><<<gt, 256, 0, s>>>(g, m, static_cast<const float*>(theta_rec), nrec, accT);
   count_launches(1);
+  if (m.nrf > 0 && m.np > 0 && m.nc > 0) {
+    const int nbg = (m.np + kProbesPerThread - 1) / kProbesPerThread;
+    const dim3 go(blocks_for(g.Ns, 256), nslab * m.nrf * nbg);
+    if (fp64)
+      k_accum_O<double><<<go, 256, 0, s>>>(g, m, static_cast<const double*>(theta_rec),
+                                           static_cast<const double*>(osum), nrec, accO);
+    else
+      k_accum_O<float><<<go, 256, 0, s>>>(g, m, static_cast<const float*>(theta_rec), static_cast<const float*>(osum),
+                                          nrec, accO);
+    count_launches(1);
+  }
 }
 
 void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, const double2* accT, const double2* accO,
@@ -453,10 +548,17 @@ void launch_products(const Geom& g, int nslab, const MeasLayout& m, const double
                      double inv_n, double2* partial, double* rec, cudaStream_t s) {
   const int nb = blocks_for(g.Ns, 256);
   const int nwarps = nb * 8;
-  k_products<<<nb, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps);
-  const int nout = m.nr + m.nrf + m.nrf * m.np * m.nc * 2;
+  k_products_P<<<dim3(nb, m.nr + m.nrf), 256, 0, s>>>(g, nslab, m, accT, inv_n, partial, nwarps);
+  count_launches(1);
+  const int nW = m.np * m.nc * 2;
+  if (m.nrf > 0 && nW > 0) {
+    k_products_W<<<dim3(nb, m.nrf, (nW + kWChunk - 1) / kWChunk), 256, 0, s>>>(g, nslab, m, accT, accO, inv_n,
+                                                                               partial, nwarps);
+    count_launches(1);
+  }
+  const int nout = m.nr + m.nrf + m.nrf * nW;
   k_finalize_products<<<blocks_for(nout, 128), 128, 0, s>>>(partial, nwarps, g, m, rec);
-  count_launches(2);
+  count_launches(1);
 }
 
 void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,

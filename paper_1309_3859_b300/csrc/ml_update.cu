@@ -106,21 +106,36 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
   }
 }
 
-// One (mu, parity) pass, one thread per link.  The links of one pass share no
-// plaquette, so all of them update independently and in place.
+constexpr int kSweepThreads = 384;  // block size of the persistent sweep kernel
+
+// Site index of the neighbour one step along direction mu (sign +1 or -1)
+// of the site with index i and coordinates c = (t, x, y, z).  No division:
+// the wrap is a compare.
+__device__ __forceinline__ int step_index(const Geom& g, int i, const int c[4], int mu, int sign) {
+  const int ext = mu == 0 ? g.Nt : g.L;
+  const int stride = mu == 0 ? g.Ns : (mu == 1 ? 1 : (mu == 2 ? g.L : g.L * g.L));
+  if (sign > 0) return c[mu] == ext - 1 ? i - (ext - 1) * stride : i + stride;
+  return c[mu] == 0 ? i + (ext - 1) * stride : i - stride;
+}
+
+// Update of the link U_mu at half index h of parity `parity` (heatbath for
+// KIND 0 with sweep number n, overrelaxation for KIND 1).  Frozen links (slab
+// mode, spatial mu on t = 0 mod slab_d) are left unchanged.
+// `th` carries no __restrict__: inside the persistent sweep kernel other blocks
+// rewrite the angles between passes, so every load must be a plain coherent
+// global load (never the read-only path).
 template <typename T, int KIND>
-__global__ void __launch_bounds__(128) k_update_pass(T* __restrict__ th, Geom g, int mu, int parity, int slab_d,
-                                                      const unsigned long long* __restrict__ n_dev,
-                                                      unsigned long long n_fixed, uint32_t k0, uint32_t k1, T beta,
-                                                      int* __restrict__ err) {
+__device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int parity, int slab_d, int h,
+                                            unsigned long long n, uint32_t k0, uint32_t k1, T beta,
+                                            int* __restrict__ err) {
   using P = Prec<T>;
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= g.Vh) return;
   int c[4];
   half_site_coords(g, h, parity, c);
   if (slab_d > 0 && mu != 0 && (c[0] % slab_d) == 0) return;  // frozen boundary link
   const int i = site_index(g, c[0], c[1], c[2], c[3]);
   const int op = parity ^ 1;
+  const int ipmu = step_index(g, i, c, mu, +1);
+  const T* th_mu_op = th + static_cast<size_t>(mu * 2 + op) * g.Vh;
 
   // staple sum W = sum_{nu != mu} [ e^{i(th_nu(x+mu) - th_mu(x+nu) - th_nu(x))}
   //                               + e^{i(-th_nu(x+mu-nu) - th_mu(x-nu) + th_nu(x-nu))} ]
@@ -128,12 +143,14 @@ __global__ void __launch_bounds__(128) k_update_pass(T* __restrict__ th, Geom g,
 #pragma unroll
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
-    const int ipmu = shifted(g, c, mu, 1, nu, 0);
-    const int ipnu = shifted(g, c, nu, 1, mu, 0);
-    const int imnu = shifted(g, c, nu, -1, mu, 0);
-    const int ipmu_mnu = shifted(g, c, mu, 1, nu, -1);
-    const T a = th[soa(g, nu, ipmu, op)] - th[soa(g, mu, ipnu, op)] - th[soa(g, nu, i, parity)];
-    const T b = -th[soa(g, nu, ipmu_mnu, parity)] - th[soa(g, mu, imnu, op)] + th[soa(g, nu, imnu, op)];
+    const T* th_nu_p = th + static_cast<size_t>(nu * 2 + parity) * g.Vh;
+    const T* th_nu_op = th + static_cast<size_t>(nu * 2 + op) * g.Vh;
+    const int ipnu = step_index(g, i, c, nu, +1);
+    const int imnu = step_index(g, i, c, nu, -1);
+    // x + mu - nu: the coordinate along nu of x + mu is c[nu]
+    const int ipmu_mnu = step_index(g, ipmu, c, nu, -1);
+    const T a = th_nu_op[ipmu >> 1] - th_mu_op[ipnu >> 1] - th_nu_p[i >> 1];
+    const T b = -th_nu_p[ipmu_mnu >> 1] - th_mu_op[imnu >> 1] + th_nu_op[imnu >> 1];
     T sa, ca, sb, cb;
     P::sincos_(a, &sa, &ca);
     P::sincos_(b, &sb, &cb);
@@ -142,22 +159,99 @@ __global__ void __launch_bounds__(128) k_update_pass(T* __restrict__ th, Geom g,
   }
   const T k = P::sqrt_(wr * wr + wi * wi);
   const T alpha = P::atan2_(wi, wr);
-  const size_t self = soa(g, mu, i, parity);
+  T* self = th + static_cast<size_t>(mu * 2 + parity) * g.Vh + (i >> 1);
   if (KIND == 0) {
-    const unsigned long long n = n_dev ? *n_dev : n_fixed;
     T psi;
     if (!von_mises<T>(beta * k, static_cast<uint32_t>(i), mu, n, k0, k1, &psi)) {
       atomicOr(err, kErrReject);
       return;
     }
-    th[self] = P::wrap(psi - alpha);
+    *self = P::wrap(psi - alpha);
   } else {
     if (k == T(0)) return;
-    th[self] = P::wrap(T(-2) * alpha - th[self]);
+    *self = P::wrap(T(-2) * alpha - *self);
   }
 }
 
-__global__ void k_sweep_begin(unsigned long long* n) { *n += 1ull; }
+// One (mu, parity) pass, one thread per link.  The links of one pass share no
+// plaquette, so all of them update independently and in place.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(128) k_update_pass(T* __restrict__ th, Geom g, int mu, int parity, int slab_d,
+                                                      const unsigned long long* __restrict__ n_dev,
+                                                      unsigned long long n_fixed, uint32_t k0, uint32_t k1, T beta,
+                                                      int* __restrict__ err) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= g.Vh) return;
+  const unsigned long long n = n_dev ? *n_dev : n_fixed;
+  update_link<T, KIND>(th, g, mu, parity, slab_d, h, n, k0, k1, beta, err);
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident), on a
+// monotonic 64-bit arrival counter: block b's k-th arrival returns old, and
+// the barrier opens when the counter reaches the next multiple of the grid
+// size.  Arrival is a release atomic, polling an acquire load.  The spin is
+// bounded: after kSpinLimit polls the block records kErrTimeout and reports
+// failure, so a lost block cannot hang the device.
+constexpr unsigned kSpinLimit = 1u << 28;
+
+__device__ __forceinline__ unsigned long long atom_add_release(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, int* err) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    const unsigned long long nb = gridDim.x;
+    const unsigned long long old = atom_add_release(count, 1ull);
+    const unsigned long long target = (old / nb + 1ull) * nb;
+    unsigned polls = 0;
+    while (ld_acquire(count) < target) {
+      if (++polls > kSpinLimit) {
+        atomicOr(err, kErrTimeout);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// n_compound compound sweeps (heatbath + n_or overrelaxation sweeps, each
+// sweep mu = 0..3 x parity even, odd) in one cooperative launch, with a grid
+// barrier between passes.  The heatbath sweep numbers are *n_dev + 1 ..
+// *n_dev + n_compound; block 0 stores the last one at the end.
+template <typename T>
+__global__ void __launch_bounds__(kSweepThreads) k_sweeps(T* th, Geom g, int slab_d, int n_or, int n_compound,
+                                                          unsigned long long* __restrict__ n_dev, uint32_t k0,
+                                                          uint32_t k1, T beta, int* __restrict__ err,
+                                                          unsigned long long* __restrict__ bar) {
+  const unsigned long long base = *n_dev;
+  const int stride = gridDim.x * blockDim.x;
+  for (int s = 0; s < n_compound; ++s) {
+    const unsigned long long n = base + 1 + s;
+    for (int sweep = 0; sweep <= n_or; ++sweep)
+      for (int mu = 0; mu < 4; ++mu)
+        for (int par = 0; par < 2; ++par) {
+          for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += stride) {
+            if (sweep == 0)
+              update_link<T, 0>(th, g, mu, par, slab_d, h, n, k0, k1, beta, err);
+            else
+              update_link<T, 1>(th, g, mu, par, slab_d, h, n, k0, k1, beta, err);
+          }
+          if (!grid_barrier(bar, err)) return;
+        }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_dev = base + n_compound;
+}
 
 // Hot start theta = -pi + 2 pi u, u = 52-bit uniform of block (i, mu, 0, 0).
 template <typename T>
@@ -240,10 +334,52 @@ void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parit
   count_launches(1);
 }
 
-void launch_sweep_begin(unsigned long long* n_dev, cudaStream_t s) {
-  k_sweep_begin<<<1, 1, 0, s>>>(n_dev);
-  count_launches(1);
+// Persistent sweep grid: one link per thread per pass when the pass fits the
+// co-resident grid, else a grid-stride loop over the co-resident grid.
+template <typename T>
+static int sweeps_grid(const Geom& g) {
+  static int cached[2] = {0, 0};
+  int& blocks_per_sm = cached[sizeof(T) == 8 ? 1 : 0];
+  if (!blocks_per_sm) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_sweeps<T>, kSweepThreads, 0);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int need = blocks_for(g.Vh, kSweepThreads);
+  const int cap = blocks_per_sm * sms;
+  return need < cap ? need : cap;
 }
+
+template <typename T>
+static cudaError_t launch_sweeps_t(void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
+                                   unsigned long long* n_dev, uint64_t seed, double beta, int* err,
+                                   unsigned long long* bar, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(sweeps_grid<T>(g));
+  cfg.blockDim = dim3(kSweepThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_sweeps<T>, static_cast<T*>(theta), g, slab_d, n_or, n_compound, n_dev,
+                            static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), static_cast<T>(beta), err,
+                            bar);
+}
+
+int launch_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
+                  unsigned long long* n_dev, uint64_t seed, double beta, int* err, unsigned long long* bar,
+                  cudaStream_t s) {
+  if (n_compound <= 0) return 0;
+  cudaError_t e = fp64 ? launch_sweeps_t<double>(theta, g, slab_d, n_or, n_compound, n_dev, seed, beta, err, bar, s)
+                       : launch_sweeps_t<float>(theta, g, slab_d, n_or, n_compound, n_dev, seed, beta, err, bar, s);
+  count_launches(1);
+  return e == cudaSuccess ? 0 : -1;
+}
+
 
 void launch_hot_start(bool fp64, void* theta, const Geom& g, uint64_t seed, cudaStream_t s) {
   const int nt = 256, nb = blocks_for(4ll * g.V, nt);

@@ -19,7 +19,7 @@ from . import build as _build
 
 ML_OK, ML_EINVAL, ML_ENOMEM, ML_ECUDA, ML_ETIMEOUT, ML_EREJECT, ML_EBUSY, ML_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 ML_FP64, ML_FP32 = 0, 1
-ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_PLAQ_SLAB, ML_K_ACCUMULATE, ML_K_PRODUCTS = range(5)
+ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP = range(6)
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
@@ -78,6 +78,7 @@ SIGNATURES = {
     "ml_sync": (ctypes.c_int, [_H]),
     "ml_philox": (ctypes.c_int, [_U32, _U32, ctypes.c_size_t, _U32]),
     "ml_kernel_timing": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "ml_batch_slots": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     "ml_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ml_kernel_launches": (ctypes.c_uint64, []),
 }
@@ -304,6 +305,12 @@ class Lattice:
         ms = ctypes.c_double()
         _check(lib().ml_kernel_timing(self.h, int(kernel), int(reps), ctypes.byref(ms)), "ml_kernel_timing")
         return ms.value
+
+    @property
+    def batch_slots(self) -> int:
+        n = ctypes.c_int()
+        _check(lib().ml_batch_slots(self.h, ctypes.byref(n)), "ml_batch_slots")
+        return n.value
 
     def sync(self):
         _check(lib().ml_sync(self.h), "ml_sync")

@@ -223,9 +223,10 @@ def test_observe_fp32_component_subset():
 
 
 # ----------------------------------------------------------------------------- whole runs, ordered phase
-@pytest.mark.parametrize("two_level", [False, True])
-def test_multilevel_run_fp64_ordered_phase(two_level):
-    kw = dict(slab=2, n_sub=3, k_between=2, r=(1, 2, 3), rf=(1, 2), probes=((0, 0), (1, 0), (2, 1)),
+@pytest.mark.parametrize("two_level,n_sub", [(False, 3), (True, 3), (False, 37), (True, 18)])
+def test_multilevel_run_fp64_ordered_phase(two_level, n_sub):
+    """n_sub > 16 exercises full folds of the record ring plus a ragged tail."""
+    kw = dict(slab=2, n_sub=n_sub, k_between=2, r=(1, 2, 3), rf=(1, 2), probes=((0, 0), (1, 0), (2, 1)),
               comp_mask=0x3F)
     if two_level:
         kw.update(outer_slab=4, n_sub_outer=2)
