@@ -143,7 +143,7 @@ int ml_measure_device(ml_lattice *h, int n_meas, double *out_dev, size_t out_len
 int ml_record_len(const ml_params *p, size_t *len);
 
 /* Connected field profile from n_meas records already in device memory
- * (Section II.D): with means over measurements,
+ * (Section II.C, electromagnetic-field equations): with means over measurements,
  *   F   = sqrt(beta) ( <Re W_{c,1}> / <Re Pf> - <vac_{c,1}> )
  *   F^2 = -2 beta   ( <Re W_{c,0}> / <Re Pf> - <vac_{c,0}> )
  * written as out_dev[nrf][nprobe][6][2] (F, F^2), computed in double

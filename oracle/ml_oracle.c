@@ -398,8 +398,8 @@ int orc_update_pass(const orc_params *p, double *th, int mu, int par, int d, uin
 
 /* Compound sweep (Section II: one update + n_or overrelaxations): heatbath
  * sweep number ++(*counter), then n_or overrelaxation sweeps.  Each sweep
- * visits mu = 0, 1, 2, 3 and within each direction the even then the odd
- * sites (Section II.D, "first the even points and then the odd points"). */
+ * visits mu = 0, 1, 2, 3 and within each direction the even sites before the
+ * odd ones (Section II.D: in-place even/odd update). */
 int orc_compound_sweep(const orc_params *p, double *th, int d, uint64_t *counter) {
   int status = ORC_OK;
   uint64_t n = ++(*counter);

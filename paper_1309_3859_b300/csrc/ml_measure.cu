@@ -1,5 +1,6 @@
 // Multilevel measurement kernels (arXiv:1309.3859, Section II.C and
-// Algorithm 1; field operators of Section II.B/II.D).
+// Algorithm 1; field operators of Section II.B and of the electromagnetic-field
+// part of Section II.C).
 //
 //   T^(d)(x, s, r)   = prod_{t in slab s} U_0(x, t)^* U_0(x + r xhat, t)
 //                    = exp(i [Theta_s(x + r) - Theta_s(x)]),
@@ -458,7 +459,7 @@ __global__ void k_write_vac(const double* __restrict__ acc, double inv, MeasLayo
   rec[m.off_vac + 2 * c + 1] = acc[2 * c + 1] * inv;
 }
 
-// Connected field (Section II.D): F = sqrt(beta) (<W_{c,Im}> / <Pf> - <vac_Im>),
+// Connected field (Section II.C, electromagnetic field): F = sqrt(beta) (<W_{c,Im}> / <Pf> - <vac_Im>),
 // F^2 = -2 beta (<W_{c,Re}> / <Pf> - <vac_Re>), means over measurements.
 __global__ void k_connected(const double* __restrict__ recs, int n_meas, MeasLayout m, double beta,
                             double* __restrict__ out) {
