@@ -54,9 +54,18 @@ struct ml_lattice {
   MeasLayout meas{};
   double2 *accT = nullptr, *accO = nullptr, *acc4T = nullptr, *acc4O = nullptr;
   size_t accT_bytes = 0, accO_bytes = 0, acc4T_bytes = 0, acc4O_bytes = 0;
-  void* osum = nullptr;       // [nslab][nc][2][Ns][kBatch] plaquette slab sums
-  void* theta_rec = nullptr;  // [nslab][Ns][kBatch] slab phase sums
+  // double-buffered ring of sub-update records (buffer b, slot j):
+  void* osum[2] = {nullptr, nullptr};       // [nslab][nc][2][Ns][kBatch] plaquette slab sums
+  void* theta_rec[2] = {nullptr, nullptr};  // [nslab][Ns][kBatch] slab phase sums
   int nB = kBatch;            // sub-update records folded per accumulation pass
+  int cur_buf = 0;            // ring buffer the next sub-update records into
+  // accumulation stream: folds, clears, level combination and products run
+  // there, overlapping the latency-bound sweeps on the main stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr};   // buffer b fully recorded (main)
+  cudaEvent_t ev_fold[2] = {nullptr, nullptr};  // buffer b folded, free again (side)
+  cudaEvent_t ev_main = nullptr, ev_side = nullptr;
+  double2* partial_naive = nullptr;
   unsigned long long* bar = nullptr;  // arrival counter of the persistent sweep kernel's grid barrier
   unsigned long long* scratch_n = nullptr;
   double* vac_part = nullptr;
@@ -67,8 +76,9 @@ struct ml_lattice {
   void* scratch_theta = nullptr;
   double* rec_buf = nullptr;
   size_t rec_cap = 0;
-  Graph g_full, g_outer, g_flush;
-  Graph g_sub[kBatch];
+  Graph g_full, g_outer;
+  Graph g_flush[2];
+  Graph g_sub[2][kBatch];
 };
 
 namespace {
@@ -144,19 +154,28 @@ int enqueue_sweeps(ml_lattice* h, int n, int d) {
 }
 
 // one slab sub-update: compound sweep with the inner mask, then the record of
-// the new configuration into ring slot `slot` and its vacuum sums
-int enqueue_sub_update(ml_lattice* h, int slot) {
+// the new configuration into slot `slot` of ring buffer `buf` and its vacuum
+// sums (main stream)
+int enqueue_sub_update(ml_lattice* h, int buf, int slot) {
   int st = enqueue_sweeps(h, 1, h->slab);
   if (st) return st;
-  launch_record(h->fp64, h->theta, h->g, h->slab, h->meas, slot, h->theta_rec, h->osum, h->vac_part, h->stream);
+  launch_record(h->fp64, h->theta, h->g, h->slab, h->meas, slot, h->theta_rec[buf], h->osum[buf], h->vac_part,
+                h->stream);
   launch_vac_accumulate(h->vac_part, h->nparts_inner, h->vac_acc, 1.0 / h->g.V, h->stream);
   return ML_OK;
 }
 
-// fold the first nrec ring slots into the inner slab sums
-void enqueue_fold(ml_lattice* h, int nrec) {
-  launch_accumulate_batch(h->fp64, h->g, h->slab, h->meas, h->theta_rec, h->osum, nrec, h->accT, h->accO,
-                          h->stream);
+// fold the first nrec slots of ring buffer `buf` into the inner slab sums
+void enqueue_fold(ml_lattice* h, int buf, int nrec, cudaStream_t s) {
+  launch_accumulate_batch(h->fp64, h->g, h->slab, h->meas, h->theta_rec[buf], h->osum[buf], nrec, h->accT, h->accO,
+                          s);
+}
+
+// make stream `to` wait for everything enqueued so far on stream `from`
+int join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+  ML_CUDA(cudaEventRecord(ev, from));
+  ML_CUDA(cudaStreamWaitEvent(to, ev, 0));
+  return ML_OK;
 }
 
 template <typename F>
@@ -179,13 +198,14 @@ int capture(ml_lattice* h, Graph* out, F&& body) {
   return ML_OK;
 }
 
-int launch_graph(ml_lattice* h, const Graph& gr) {
-  ML_CUDA(cudaGraphLaunch(gr.exec, h->stream));
+int launch_graph(ml_lattice* h, const Graph& gr, cudaStream_t s = nullptr) {
+  ML_CUDA(cudaGraphLaunch(gr.exec, s ? s : h->stream));
   g_launches.fetch_add(gr.kernels, std::memory_order_relaxed);
   return ML_OK;
 }
 
 int check_errors(ml_lattice* h) {
+  if (h->side) ML_CUDA(cudaStreamSynchronize(h->side));
   ML_CUDA(cudaStreamSynchronize(h->stream));
   int err = 0;
   ML_CUDA(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -199,8 +219,9 @@ int check_errors(ml_lattice* h) {
 }
 
 void destroy_graphs(ml_lattice* h) {
-  std::vector<Graph*> all = {&h->g_full, &h->g_outer, &h->g_flush};
-  for (int j = 0; j < kBatch; ++j) all.push_back(&h->g_sub[j]);
+  std::vector<Graph*> all = {&h->g_full, &h->g_outer, &h->g_flush[0], &h->g_flush[1]};
+  for (int b = 0; b < 2; ++b)
+    for (int j = 0; j < kBatch; ++j) all.push_back(&h->g_sub[b][j]);
   for (Graph* gr : all)
     if (gr->exec) {
       cudaGraphExecDestroy(gr->exec);
@@ -208,25 +229,64 @@ void destroy_graphs(ml_lattice* h) {
     }
 }
 
-// inner loop of n_sub slab sub-updates, folding the records every nB
-int run_inner_loop(ml_lattice* h) {
-  int slot = 0;
-  for (int i = 0; i < h->n_sub; ++i) {
-    int st = launch_graph(h, h->g_sub[slot]);
-    if (st) return st;
-    if (++slot == h->nB) {
-      st = launch_graph(h, h->g_flush);
-      if (st) return st;
-      slot = 0;
+void destroy_streams(ml_lattice* h) {
+  for (cudaEvent_t* e : {&h->ev_rec[0], &h->ev_rec[1], &h->ev_fold[0], &h->ev_fold[1], &h->ev_main, &h->ev_side})
+    if (*e) {
+      cudaEventDestroy(*e);
+      *e = nullptr;
     }
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+    h->side = nullptr;
   }
-  if (slot > 0) enqueue_fold(h, slot);
+}
+
+// hand ring buffer `buf` (nrec records) from the main stream to the fold on
+// the accumulation stream
+int hand_over(ml_lattice* h, int buf, int nrec) {
+  ML_CUDA(cudaEventRecord(h->ev_rec[buf], h->stream));
+  ML_CUDA(cudaStreamWaitEvent(h->side, h->ev_rec[buf], 0));
+  if (nrec == h->nB) {
+    int st = launch_graph(h, h->g_flush[buf], h->side);
+    if (st) return st;
+  } else {
+    enqueue_fold(h, buf, nrec, h->side);
+  }
+  ML_CUDA(cudaEventRecord(h->ev_fold[buf], h->side));
   return ML_OK;
 }
 
-int zero_inner(ml_lattice* h) {
-  ML_CUDA(cudaMemsetAsync(h->accT, 0, h->accT_bytes, h->stream));
-  if (h->accO_bytes) ML_CUDA(cudaMemsetAsync(h->accO, 0, h->accO_bytes, h->stream));
+// inner loop of n_sub slab sub-updates (main stream), folding every nB
+// records on the accumulation stream while the sweeps continue; a ring
+// buffer is reused only after its previous fold has finished
+int run_inner_loop(ml_lattice* h) {
+  int buf = h->cur_buf, slot = 0;
+  ML_CUDA(cudaStreamWaitEvent(h->stream, h->ev_fold[buf], 0));
+  for (int i = 0; i < h->n_sub; ++i) {
+    int st = launch_graph(h, h->g_sub[buf][slot]);
+    if (st) return st;
+    if (++slot == h->nB) {
+      st = hand_over(h, buf, slot);
+      if (st) return st;
+      buf ^= 1;
+      slot = 0;
+      if (i + 1 < h->n_sub) ML_CUDA(cudaStreamWaitEvent(h->stream, h->ev_fold[buf], 0));
+    }
+  }
+  if (slot > 0) {
+    int st = hand_over(h, buf, slot);
+    if (st) return st;
+    buf ^= 1;
+  }
+  h->cur_buf = buf;
+  return ML_OK;
+}
+
+// clear the inner slab sums (accumulation stream)
+int zero_inner(ml_lattice* h, cudaStream_t s) {
+  ML_CUDA(cudaMemsetAsync(h->accT, 0, h->accT_bytes, s));
+  if (h->accO_bytes) ML_CUDA(cudaMemsetAsync(h->accO, 0, h->accO_bytes, s));
   return ML_OK;
 }
 
@@ -239,40 +299,45 @@ int ensure_rec(ml_lattice* h, size_t doubles) {
   return ML_OK;
 }
 
-// Algorithm 1 for n_meas measurements into device records rec
+// Algorithm 1 for n_meas measurements into device records rec.  Sweeps,
+// records and the vacuum run on the main stream; clears, folds, the level
+// combination and the products on the accumulation stream.
 int enqueue_measurements(ml_lattice* h, int n_meas, double* rec) {
   const MeasLayout& m = h->meas;
   const int nslab_in = h->g.Nt / h->slab;
+  int st = join(h->stream, h->side, h->ev_main);
+  if (st) return st;
   for (int j = 0; j < n_meas; ++j) {
     double* out = rec + static_cast<size_t>(j) * m.rec_len;
     ML_CUDA(cudaMemsetAsync(out, 0, m.rec_len * sizeof(double), h->stream));
     if (h->k_between > 0) {
-      int st = launch_graph(h, h->g_full);
+      st = launch_graph(h, h->g_full);
       if (st) return st;
     }
-    launch_naive_and_plaquette(h->fp64, h->theta, h->g, m, h->partial, out, h->stream);
+    launch_naive_and_plaquette(h->fp64, h->theta, h->g, m, h->partial_naive, out, h->stream);
     ML_CUDA(cudaMemsetAsync(h->vac_acc, 0, 12 * sizeof(double), h->stream));
+    st = join(h->stream, h->side, h->ev_main);  // the record `out` is cleared before the products
+    if (st) return st;
     int ncfg = 0;
     if (h->outer_slab == 0) {
-      int st = zero_inner(h);
+      st = zero_inner(h, h->side);
       if (!st) st = run_inner_loop(h);
       if (st) return st;
-      launch_products(h->g, nslab_in, m, h->accT, h->accO, 1.0 / h->n_sub, h->partial, out, h->stream);
+      launch_products(h->g, nslab_in, m, h->accT, h->accO, 1.0 / h->n_sub, h->partial, out, h->side);
       ncfg = h->n_sub;
     } else {
       const int nslab_out = h->g.Nt / h->outer_slab;
-      ML_CUDA(cudaMemsetAsync(h->acc4T, 0, h->acc4T_bytes, h->stream));
-      if (h->acc4O_bytes) ML_CUDA(cudaMemsetAsync(h->acc4O, 0, h->acc4O_bytes, h->stream));
+      ML_CUDA(cudaMemsetAsync(h->acc4T, 0, h->acc4T_bytes, h->side));
+      if (h->acc4O_bytes) ML_CUDA(cudaMemsetAsync(h->acc4O, 0, h->acc4O_bytes, h->side));
       for (int o = 0; o < h->n_sub_outer; ++o) {
-        int st = launch_graph(h, h->g_outer);
-        if (st) return st;
-        st = zero_inner(h);
+        st = launch_graph(h, h->g_outer);
+        if (!st) st = zero_inner(h, h->side);
         if (!st) st = run_inner_loop(h);
         if (st) return st;
         launch_combine(h->g, nslab_out, h->outer_slab / h->slab, m, h->accT, h->accO, 1.0 / h->n_sub, h->acc4T,
-                       h->acc4O, h->stream);
+                       h->acc4O, h->side);
       }
-      launch_products(h->g, nslab_out, m, h->acc4T, h->acc4O, 1.0 / h->n_sub_outer, h->partial, out, h->stream);
+      launch_products(h->g, nslab_out, m, h->acc4T, h->acc4O, 1.0 / h->n_sub_outer, h->partial, out, h->side);
       ncfg = h->n_sub * h->n_sub_outer;
     }
     launch_write_vac(h->vac_acc, 1.0 / ncfg, m, out, h->stream);
@@ -280,6 +345,8 @@ int enqueue_measurements(ml_lattice* h, int n_meas, double* rec) {
                                                           ? static_cast<uint64_t>(h->n_sub)
                                                           : static_cast<uint64_t>(h->n_sub_outer) * (1 + h->n_sub));
   }
+  st = join(h->side, h->stream, h->ev_side);  // results complete in stream order on the main stream
+  if (st) return st;
   return cuda_status(cudaGetLastError());
 }
 
@@ -398,8 +465,12 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
     h->acc4T = static_cast<double2*>(dev_alloc(h, h->acc4T_bytes));
     h->acc4O = static_cast<double2*>(dev_alloc(h, h->acc4O_bytes));
   }
-  h->osum = dev_alloc(h, static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * kBatch * tsz);
-  h->theta_rec = dev_alloc(h, static_cast<size_t>(nslab_in) * g.Ns * kBatch * tsz);
+  const size_t osum_bytes = static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * kBatch * tsz;
+  const size_t trec_bytes = static_cast<size_t>(nslab_in) * g.Ns * kBatch * tsz;
+  for (int b = 0; b < 2; ++b) {
+    h->osum[b] = dev_alloc(h, osum_bytes);
+    h->theta_rec[b] = dev_alloc(h, trec_bytes);
+  }
   h->bar = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long)));
   h->scratch_n = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long)));
   h->nparts_inner = vac_part_count(g, h->slab);
@@ -410,7 +481,9 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
   const size_t nvw = static_cast<size_t>((g.V + 255) / 256) * 8;
   const size_t part = std::max(nout * nw, static_cast<size_t>(nr) * nw + nvw / 2 + 1);
   h->partial = static_cast<double2*>(dev_alloc(h, part * sizeof(double2)));
-  bool ok = h->theta && h->d_n && h->d_err && h->d_lists && h->accT && h->accO && h->osum && h->theta_rec &&
+  h->partial_naive = static_cast<double2*>(dev_alloc(h, (static_cast<size_t>(nr) * nw + nvw / 2 + 1) * sizeof(double2)));
+  bool ok = h->theta && h->d_n && h->d_err && h->d_lists && h->accT && h->accO && h->osum[0] && h->osum[1] &&
+            h->theta_rec[0] && h->theta_rec[1] && h->partial_naive &&
             h->bar && h->scratch_n && h->vac_part &&
             h->vac_acc && h->partial && (!nslab_out || (h->acc4T && h->acc4O));
   if (!ok) {
@@ -449,10 +522,17 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
   if (e == cudaSuccess) e = cudaMemsetAsync(h->vac_acc, 0, 12 * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream);
   // ring slots not yet written in a batch are multiplied by zero: keep them finite
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(h->osum, 0, static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * kBatch * tsz, h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(h->theta_rec, 0, static_cast<size_t>(nslab_in) * g.Ns * kBatch * tsz, h->stream);
+  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+    e = cudaMemsetAsync(h->osum[b], 0, osum_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->theta_rec[b], 0, trec_bytes, h->stream);
+  }
+  if (e == cudaSuccess) {
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo);
+  }
+  for (cudaEvent_t* ev : {&h->ev_rec[0], &h->ev_rec[1], &h->ev_fold[0], &h->ev_fold[1], &h->ev_main, &h->ev_side})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(h->vac_part, 0, static_cast<size_t>(h->nparts_inner) * 12 * sizeof(double), h->stream);
   if (e == cudaSuccess) launch_hot_start(h->fp64, h->theta, g, h->seed, h->stream);
@@ -460,14 +540,18 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
   if (e == cudaSuccess) e = cudaGetLastError();
   st = e == cudaSuccess ? ML_OK : ML_ECUDA;
   if (!st && h->k_between > 0) st = capture(h, &h->g_full, [&] { return enqueue_sweeps(h, h->k_between, 0); });
-  for (int j = 0; j < h->nB && !st; ++j) st = capture(h, &h->g_sub[j], [&] { return enqueue_sub_update(h, j); });
-  if (!st) st = capture(h, &h->g_flush, [&] {
-    enqueue_fold(h, h->nB);
-    return ML_OK;
-  });
+  for (int b = 0; b < 2; ++b) {
+    for (int j = 0; j < h->nB && !st; ++j)
+      st = capture(h, &h->g_sub[b][j], [&] { return enqueue_sub_update(h, b, j); });
+    if (!st) st = capture(h, &h->g_flush[b], [&] {
+      enqueue_fold(h, b, h->nB, h->stream);
+      return ML_OK;
+    });
+  }
   if (!st && h->outer_slab) st = capture(h, &h->g_outer, [&] { return enqueue_sweeps(h, 1, h->outer_slab); });
   if (st) {
     destroy_graphs(h);
+    destroy_streams(h);
     free_all(h);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -479,8 +563,10 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
 
 int ml_destroy(ml_lattice* h) {
   if (!h) return ML_EINVAL;
+  if (h->side) cudaStreamSynchronize(h->side);
   cudaStreamSynchronize(h->stream);
   destroy_graphs(h);
+  destroy_streams(h);
   free_all(h);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -540,13 +626,16 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
   double* out = h->rec_buf;
   const MeasLayout& m = h->meas;
   ML_CUDA(cudaMemsetAsync(out, 0, m.rec_len * sizeof(double), h->stream));
-  launch_naive_and_plaquette(h->fp64, h->theta, h->g, m, h->partial, out, h->stream);
+  launch_naive_and_plaquette(h->fp64, h->theta, h->g, m, h->partial_naive, out, h->stream);
   ML_CUDA(cudaMemsetAsync(h->vac_acc, 0, 12 * sizeof(double), h->stream));
-  st = zero_inner(h);
+  st = join(h->side, h->stream, h->ev_side);
+  if (!st) st = zero_inner(h, h->stream);
   if (st) return st;
-  launch_record(h->fp64, h->theta, h->g, h->slab, m, 0, h->theta_rec, h->osum, h->vac_part, h->stream);
+  const int buf = h->cur_buf;
+  ML_CUDA(cudaStreamWaitEvent(h->stream, h->ev_fold[buf], 0));
+  launch_record(h->fp64, h->theta, h->g, h->slab, m, 0, h->theta_rec[buf], h->osum[buf], h->vac_part, h->stream);
   launch_vac_accumulate(h->vac_part, h->nparts_inner, h->vac_acc, 1.0 / h->g.V, h->stream);
-  enqueue_fold(h, 1);
+  enqueue_fold(h, buf, 1, h->stream);
   launch_products(h->g, h->g.Nt / h->slab, m, h->accT, h->accO, 1.0, h->partial, out, h->stream);
   launch_write_vac(h->vac_acc, 1.0, m, out, h->stream);
   ML_CUDA(cudaGetLastError());
@@ -610,6 +699,8 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   }
   int st = ensure_rec(h, h->meas.rec_len);
   if (st) return st;
+  st = join(h->side, h->stream, h->ev_side);
+  if (st) return st;
   ML_CUDA(cudaMemcpyAsync(h->scratch_theta, h->theta, tbytes, cudaMemcpyDeviceToDevice, h->stream));
   ML_CUDA(cudaMemcpyAsync(h->scratch_n, h->d_n, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->stream));
   cudaEvent_t e0, e1;
@@ -624,10 +715,11 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
                            h->h_n + 1, h->seed, h->beta, h->d_err, h->stream);
         break;
       case ML_K_RECORD:
-        launch_record(h->fp64, h->theta, h->g, h->slab, h->meas, 0, h->theta_rec, h->osum, h->vac_part, h->stream);
+        launch_record(h->fp64, h->theta, h->g, h->slab, h->meas, 0, h->theta_rec[0], h->osum[0], h->vac_part,
+                      h->stream);
         break;
       case ML_K_ACCUMULATE:
-        enqueue_fold(h, h->nB);
+        enqueue_fold(h, 0, h->nB, h->stream);
         break;
       case ML_K_PRODUCTS:
         launch_products(h->g, h->g.Nt / h->slab, h->meas, h->accT, h->accO, 1.0, h->partial, h->rec_buf, h->stream);
