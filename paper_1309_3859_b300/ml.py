@@ -252,10 +252,15 @@ class Lattice:
         return out
 
     def measure_device(self, n_meas: int, out=None):
-        """Enqueue measurements whose records stay in a device tensor."""
+        """Enqueue measurements whose records stay in a device tensor.
+
+        The work runs on ``self.stream``; wait for it (``sync()`` or
+        ``torch.cuda.current_stream().wait_stream(self.stream)``) before
+        reading the tensor on another stream."""
         torch = self._torch
         if out is None:
-            out = torch.empty((n_meas, self.rec_len), dtype=torch.float64, device=self.device)
+            with torch.cuda.stream(self.stream):
+                out = torch.empty((n_meas, self.rec_len), dtype=torch.float64, device=self.device)
         assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
         _check(lib().ml_measure_device(self.h, int(n_meas), ctypes.c_void_p(out.data_ptr()), out.numel()),
                "ml_measure_device")
@@ -264,7 +269,8 @@ class Lattice:
     def connected(self, records_dev):
         """Connected F and F^2 profile [nrf][nprobe][6][2] from device records."""
         torch = self._torch
-        out = torch.empty((len(self.p.rf), len(self.p.probes), 6, 2), dtype=torch.float64, device=self.device)
+        with torch.cuda.stream(self.stream):
+            out = torch.empty((len(self.p.rf), len(self.p.probes), 6, 2), dtype=torch.float64, device=self.device)
         _check(lib().ml_connected_device(self.h, ctypes.c_void_p(records_dev.data_ptr()), records_dev.shape[0],
                                          ctypes.c_void_p(out.data_ptr()), out.numel()), "ml_connected_device")
         return out

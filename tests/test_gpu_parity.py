@@ -246,15 +246,14 @@ def test_multilevel_run_fp64_ordered_phase(two_level, n_sub):
 
 
 def test_connected_profile_on_device():
-    import torch
-
     po, pm = pair(L=4, Nt=4, beta=2.5, seed=91, slab=2, n_sub=2, k_between=1, r=(1, 2), rf=(2,),
                   probes=((0, 0), (1, 0)), comp_mask=0x3F)
     with ml.Lattice(pm) as lat:
         lat.thermalize(3)
         recs = lat.measure_device(3)
-        out = lat.connected(recs).cpu().numpy()
-        torch.cuda.synchronize()
+        out_dev = lat.connected(recs)
+        lat.sync()  # the results are complete in the lattice stream's order
+        out = out_dev.cpu().numpy()
         r = recs.cpu().numpy()
     s = ml.split_record(pm, r)
     pf = s["Pf"][:, 0, 0].mean()
