@@ -210,6 +210,47 @@ int ml_kernel_timing(ml_lattice *h, int kernel, int reps, double *avg_ms);
  * accumulation pass (chosen at ml_create from the record size, at most 16). */
 int ml_batch_slots(ml_lattice *h, int *n);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free entry point (no counterpart in the paper)                  */
+/* ------------------------------------------------------------------------ */
+
+/* Some callers cannot allocate device memory: code embedded in a host
+ * application or framework whose memory manager has already claimed the
+ * device memory it may use (a cudaMalloc there fails or fragments its pool),
+ * and latency-bound serving loops, where cudaMalloc / cudaFree may
+ * synchronise the device and stall every stream.  For them this computes the
+ * same values as the `naive` and `plaq` blocks of ml_observe from angles the
+ * caller already holds on the device, and allocates nothing: its scratch is
+ * one fixed array of ML_NOALLOC_SCRATCH_BYTES (2 MiB) inside the library,
+ * which every GPU that loads the library keeps until the process exits.
+ *
+ *   theta_dev    device angles in the library's layout,
+ *                theta[(mu * 2 + parity) * V/2 + (i >> 1)], i and parity as
+ *                above; double for prec = ML_FP64, float for ML_FP32
+ *   r, nr        host array of nr separations, 1 <= r <= L-1,
+ *                1 <= nr <= ML_NOALLOC_MAX_R
+ *   out_dev      device output, 2 nr + 1 doubles: (Re, Im) of
+ *                (1/L^3) sum_x P(x)^* P(x + r xhat) for each r, then the mean
+ *                plaquette
+ *   cuda_stream  stream the work is enqueued on (cudaStream_t; NULL = legacy
+ *                default stream); the call does not synchronise
+ *
+ * Size limit: a call uses 2 nr W + Wv doubles of the scratch array, with
+ * W = 8 ceil(L^3 / 256) and Wv = 8 ceil(L^3 Nt / 256); a call that would need
+ * more than ML_NOALLOC_SCRATCH_BYTES / 8 doubles returns ML_EINVAL (24^3 x 8
+ * with nr = 11 uses 12960 of the 262144).
+ * Set-up: the first call on each device looks up the device address of the
+ * scratch array with that device current; make that first call before any
+ * stream capture.
+ * Sharing: every call on a device uses the same array and it keeps the last
+ * call's contents; each call writes every value it later reads, so nothing
+ * needs clearing, but calls that may overlap on the GPU (different streams
+ * or host threads) race and must be serialised by the caller. */
+#define ML_NOALLOC_SCRATCH_BYTES (2 * 1024 * 1024)
+#define ML_NOALLOC_MAX_R 64
+int ml_naive_noalloc(const void *theta_dev, int L, int Nt, int prec, const int *r, int nr, double *out_dev,
+                     void *cuda_stream);
+
 /* Static text for a status code. */
 const char *ml_error_string(int status);
 

@@ -79,6 +79,9 @@ SIGNATURES = {
     "ml_philox": (ctypes.c_int, [_U32, _U32, ctypes.c_size_t, _U32]),
     "ml_kernel_timing": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ml_batch_slots": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
+    "ml_naive_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p]),
     "ml_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ml_kernel_launches": (ctypes.c_uint64, []),
 }
