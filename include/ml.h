@@ -206,6 +206,20 @@ typedef enum {
  * left undefined (every measurement clears them first).  Blocking. */
 int ml_kernel_timing(ml_lattice *h, int kernel, int reps, double *avg_ms);
 
+/* Implementations of the compound sweep.  ml_create times both on the
+ * handle's lattice and keeps the faster; results are identical. */
+typedef enum {
+  ML_SWEEP_PERSISTENT = 0, /* one cooperative persistent kernel, grid barrier
+                              (bounded spin) between passes                   */
+  ML_SWEEP_PASSES = 1      /* one kernel per (direction, parity) pass, replayed
+                              from a CUDA graph                               */
+} ml_sweep_impl;
+
+/* Query or force the compound-sweep implementation (forcing re-captures the
+ * handle's graphs; blocking). */
+int ml_sweep_mode(ml_lattice *h, int *mode);
+int ml_set_sweep_mode(ml_lattice *h, int mode);
+
 /* Number of sub-update records the handle folds into its slab sums per
  * accumulation pass (chosen at ml_create from the record size, at most 16). */
 int ml_batch_slots(ml_lattice *h, int *n);

@@ -76,7 +76,8 @@ struct ml_lattice {
   void* scratch_theta = nullptr;
   double* rec_buf = nullptr;
   size_t rec_cap = 0;
-  Graph g_full, g_outer;
+  int sweep_mode = ML_SWEEP_PERSISTENT;
+  Graph g_full, g_outer, g_one_full;
   Graph g_flush[2];
   Graph g_sub[2][kBatch];
 };
@@ -145,13 +146,17 @@ size_t record_len(int nr, int nrf, int np) {
 
 // n compound sweeps (heatbath + n_or overrelaxation sweeps) with slab mask d
 // in one cooperative launch of the persistent sweep kernel
-int enqueue_sweeps(ml_lattice* h, int n, int d) {
+int enqueue_sweeps_on(ml_lattice* h, int mode, void* theta, unsigned long long* n_dev, int n, int d) {
   if (n <= 0) return ML_OK;
-  return launch_sweeps(h->fp64, h->theta, h->g, d, h->n_or, n, h->d_n, h->seed, h->beta, h->d_err, h->bar,
-                       h->stream)
-             ? ML_ECUDA
-             : ML_OK;
+  const int rc = mode == ML_SWEEP_PERSISTENT
+                     ? launch_sweeps(h->fp64, theta, h->g, d, h->n_or, n, n_dev, h->seed, h->beta, h->d_err, h->bar,
+                                     h->stream)
+                     : launch_pass_sweeps(h->fp64, theta, h->g, d, h->n_or, n, n_dev, h->seed, h->beta, h->d_err,
+                                          h->stream);
+  return rc ? ML_ECUDA : ML_OK;
 }
+
+int enqueue_sweeps(ml_lattice* h, int n, int d) { return enqueue_sweeps_on(h, h->sweep_mode, h->theta, h->d_n, n, d); }
 
 // one slab sub-update: compound sweep with the inner mask, then the record of
 // the new configuration into slot `slot` of ring buffer `buf` and its vacuum
@@ -219,7 +224,7 @@ int check_errors(ml_lattice* h) {
 }
 
 void destroy_graphs(ml_lattice* h) {
-  std::vector<Graph*> all = {&h->g_full, &h->g_outer, &h->g_flush[0], &h->g_flush[1]};
+  std::vector<Graph*> all = {&h->g_full, &h->g_outer, &h->g_one_full, &h->g_flush[0], &h->g_flush[1]};
   for (int b = 0; b < 2; ++b)
     for (int j = 0; j < kBatch; ++j) all.push_back(&h->g_sub[b][j]);
   for (Graph* gr : all)
@@ -350,9 +355,93 @@ int enqueue_measurements(ml_lattice* h, int n_meas, double* rec) {
   return cuda_status(cudaGetLastError());
 }
 
+// Capture every graph of the measurement schedule for the current sweep mode.
+int capture_graphs(ml_lattice* h) {
+  int st = ML_OK;
+  if (h->k_between > 0) st = capture(h, &h->g_full, [&] { return enqueue_sweeps(h, h->k_between, 0); });
+  if (!st) st = capture(h, &h->g_one_full, [&] { return enqueue_sweeps(h, 1, 0); });
+  for (int b = 0; b < 2; ++b) {
+    for (int j = 0; j < h->nB && !st; ++j)
+      st = capture(h, &h->g_sub[b][j], [&] { return enqueue_sub_update(h, b, j); });
+    if (!st) st = capture(h, &h->g_flush[b], [&] {
+      enqueue_fold(h, b, h->nB, h->stream);
+      return ML_OK;
+    });
+  }
+  if (!st && h->outer_slab) st = capture(h, &h->g_outer, [&] { return enqueue_sweeps(h, 1, h->outer_slab); });
+  return st;
+}
+
+int ensure_scratch_theta(ml_lattice* h) {
+  if (h->scratch_theta) return ML_OK;
+  h->scratch_theta = dev_alloc(h, 4ull * h->g.V * (h->fp64 ? sizeof(double) : sizeof(float)));
+  return h->scratch_theta ? ML_OK : ML_ENOMEM;
+}
+
+// Autotuning of the sweep implementation: time one compound slab sweep as the
+// persistent cooperative kernel and as a captured graph of per-pass kernels
+// (on a scratch copy of the angles) and keep the faster.  Small lattices are
+// latency-bound and favour the persistent kernel; large ones favour the
+// per-pass kernels' full occupancy.
+int choose_sweep_mode(ml_lattice* h) {
+  int st = ensure_scratch_theta(h);
+  if (st) return st;
+  const size_t tbytes = 4ull * h->g.V * (h->fp64 ? sizeof(double) : sizeof(float));
+  ML_CUDA(cudaMemcpyAsync(h->scratch_theta, h->theta, tbytes, cudaMemcpyDeviceToDevice, h->stream));
+  ML_CUDA(cudaMemsetAsync(h->scratch_n, 0, sizeof(unsigned long long), h->stream));
+  Graph pp;
+  st = capture(h, &pp, [&] { return enqueue_sweeps_on(h, ML_SWEEP_PASSES, h->scratch_theta, h->scratch_n, 1, h->slab); });
+  if (st) return st;
+  // alternate the candidates over several rounds (the clocks may still be
+  // ramping up when a handle is created) and keep each one's best round
+  cudaEvent_t ev[3];
+  for (cudaEvent_t& e : ev) ML_CUDA(cudaEventCreate(&e));
+  const int rounds = 4, reps = 2;
+  float best[2] = {1e30f, 1e30f};
+  st = enqueue_sweeps_on(h, ML_SWEEP_PERSISTENT, h->scratch_theta, h->scratch_n, 2, h->slab);  // warm-up
+  if (!st) st = launch_graph(h, pp);
+  for (int r = 0; r < rounds && !st; ++r) {
+    st = cuda_status(cudaEventRecord(ev[0], h->stream));
+    for (int i = 0; i < reps && !st; ++i)
+      st = enqueue_sweeps_on(h, ML_SWEEP_PERSISTENT, h->scratch_theta, h->scratch_n, 1, h->slab);
+    if (!st) st = cuda_status(cudaEventRecord(ev[1], h->stream));
+    for (int i = 0; i < reps && !st; ++i) st = launch_graph(h, pp);
+    if (!st) st = cuda_status(cudaEventRecord(ev[2], h->stream));
+    if (!st) st = cuda_status(cudaEventSynchronize(ev[2]));
+    if (!st) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b, ev[1], ev[2]);
+      best[0] = a < best[0] ? a : best[0];
+      best[1] = b < best[1] ? b : best[1];
+    }
+  }
+  if (!st) h->sweep_mode = best[1] < best[0] ? ML_SWEEP_PASSES : ML_SWEEP_PERSISTENT;
+  for (cudaEvent_t& e : ev) cudaEventDestroy(e);
+  cudaGraphExecDestroy(pp.exec);
+  if (st) return st;
+  return check_errors(h);
+}
+
 }  // namespace
 
 extern "C" {
+
+int ml_sweep_mode(ml_lattice* h, int* mode) {
+  if (!h || !mode) return ML_EINVAL;
+  *mode = h->sweep_mode;
+  return ML_OK;
+}
+
+int ml_set_sweep_mode(ml_lattice* h, int mode) {
+  if (!h || (mode != ML_SWEEP_PERSISTENT && mode != ML_SWEEP_PASSES)) return ML_EINVAL;
+  int st = check_errors(h);
+  if (st) return st;
+  if (mode == h->sweep_mode) return ML_OK;
+  destroy_graphs(h);
+  h->sweep_mode = mode;
+  return capture_graphs(h);
+}
 
 const char* ml_error_string(int status) {
   switch (status) {
@@ -539,16 +628,8 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // lists are host temporaries
   if (e == cudaSuccess) e = cudaGetLastError();
   st = e == cudaSuccess ? ML_OK : ML_ECUDA;
-  if (!st && h->k_between > 0) st = capture(h, &h->g_full, [&] { return enqueue_sweeps(h, h->k_between, 0); });
-  for (int b = 0; b < 2; ++b) {
-    for (int j = 0; j < h->nB && !st; ++j)
-      st = capture(h, &h->g_sub[b][j], [&] { return enqueue_sub_update(h, b, j); });
-    if (!st) st = capture(h, &h->g_flush[b], [&] {
-      enqueue_fold(h, b, h->nB, h->stream);
-      return ML_OK;
-    });
-  }
-  if (!st && h->outer_slab) st = capture(h, &h->g_outer, [&] { return enqueue_sweeps(h, 1, h->outer_slab); });
+  if (!st) st = choose_sweep_mode(h);
+  if (!st) st = capture_graphs(h);
   if (st) {
     destroy_graphs(h);
     destroy_streams(h);
@@ -580,7 +661,11 @@ int ml_sync(ml_lattice* h) {
 
 int ml_thermalize(ml_lattice* h, int n_sweeps) {
   if (!h || n_sweeps < 0) return ML_EINVAL;
-  int st = enqueue_sweeps(h, n_sweeps, 0);
+  int st = ML_OK;
+  if (h->sweep_mode == ML_SWEEP_PERSISTENT)
+    st = enqueue_sweeps(h, n_sweeps, 0);
+  else
+    for (int i = 0; i < n_sweeps && !st; ++i) st = launch_graph(h, h->g_one_full);
   if (st) return st;
   h->h_n += static_cast<uint64_t>(n_sweeps);
   return ML_OK;
@@ -693,11 +778,8 @@ int ml_set_sweep(ml_lattice* h, uint64_t n) {
 int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   if (!h || !avg_ms || reps < 1 || kernel < ML_K_HEATBATH || kernel > ML_K_SWEEP) return ML_EINVAL;
   const size_t tbytes = 4ull * h->g.V * (h->fp64 ? sizeof(double) : sizeof(float));
-  if (!h->scratch_theta) {
-    h->scratch_theta = dev_alloc(h, tbytes);
-    if (!h->scratch_theta) return ML_ENOMEM;
-  }
-  int st = ensure_rec(h, h->meas.rec_len);
+  int st = ensure_scratch_theta(h);
+  if (!st) st = ensure_rec(h, h->meas.rec_len);
   if (st) return st;
   st = join(h->side, h->stream, h->ev_side);
   if (st) return st;
@@ -725,9 +807,7 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
         launch_products(h->g, h->g.Nt / h->slab, h->meas, h->accT, h->accO, 1.0, h->partial, h->rec_buf, h->stream);
         break;
       default:
-        if (launch_sweeps(h->fp64, h->scratch_theta, h->g, h->slab, h->n_or, 1, h->scratch_n, h->seed, h->beta,
-                          h->d_err, h->bar, h->stream))
-          st = ML_ECUDA;
+        st = enqueue_sweeps_on(h, h->sweep_mode, h->scratch_theta, h->scratch_n, 1, h->slab);
     }
   }
   ML_CUDA(cudaEventRecord(e1, h->stream));

@@ -36,6 +36,11 @@ void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parit
 int launch_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
                   unsigned long long* n_dev, uint64_t seed, double beta, int* err, unsigned long long* bar,
                   cudaStream_t s);
+// The same n_compound compound sweeps as one kernel per (direction, parity)
+// pass: *n_dev is incremented by a one-thread kernel before each compound
+// sweep and read by its heatbath passes.  Returns 0 or -1.
+int launch_pass_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
+                       unsigned long long* n_dev, uint64_t seed, double beta, int* err, cudaStream_t s);
 void launch_hot_start(bool fp64, void* theta, const Geom& g, uint64_t seed, cudaStream_t s);
 void launch_angles_to_soa(bool fp64, const double* canon, void* theta, const Geom& g, cudaStream_t s);
 void launch_angles_from_soa(bool fp64, const void* theta, double* canon, const Geom& g, cudaStream_t s);

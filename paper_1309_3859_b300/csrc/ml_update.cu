@@ -84,11 +84,14 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
       *psi = kPiF * (2.0f * uniform23(o.x) - 1.0f);
       return true;
     }
-    const float root = sqrtf(1.0f + 4.0f * kappa * kappa);
+    // single-precision set-up with hardware reciprocals (a few ulp); every
+    // operand is well inside the normal range for kappa >= kappa_tiny
+    const float k2 = kappa * kappa;
+    const float root = sqrtf(fmaf(4.0f, k2, 1.0f));
     const float tau = 1.0f + root;
-    const float tau_minus_2 = 4.0f * kappa * kappa / (1.0f + root);
-    const float rho = tau * tau_minus_2 / (tau + sqrtf(2.0f * tau)) / (2.0f * kappa);
-    const float s = (1.0f + rho * rho) / (2.0f * rho);
+    const float tau_minus_2 = __fdividef(4.0f * k2, 1.0f + root);
+    const float rho = __fdividef(tau * tau_minus_2, (tau + sqrtf(2.0f * tau)) * (2.0f * kappa));
+    const float s = __fdividef(fmaf(rho, rho, 1.0f), 2.0f * rho);
     for (int m = 0; m < kMaxTrials; ++m) {
       const U4 o = Draws<float>::block(site, mu, n, m, k0, k1);
       const float u1 = uniform23(o.x), u2 = uniform23(o.y);
@@ -96,7 +99,8 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
       float f = __fdividef(fmaf(s, z, 1.0f), s + z);
       f = fminf(fmaxf(f, -1.0f), 1.0f);
       const float c = kappa * (s - f);
-      if ((c * (2.0f - c) - u2 > 0.0f) || (__logf(c / u2) + 1.0f - c >= 0.0f)) {
+      // log(c / u2) as a difference of hardware logarithms (c > 0, u2 > 0)
+      if ((c * (2.0f - c) - u2 > 0.0f) || (__logf(c) - __logf(u2) + 1.0f - c >= 0.0f)) {
         const float a = acosf(f);
         *psi = (uniform23(o.z) > 0.5f) ? a : -a;
         return true;
@@ -380,6 +384,21 @@ int launch_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, i
   return e == cudaSuccess ? 0 : -1;
 }
 
+
+__global__ void k_sweep_begin(unsigned long long* n) { *n += 1ull; }
+
+int launch_pass_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
+                       unsigned long long* n_dev, uint64_t seed, double beta, int* err, cudaStream_t s) {
+  for (int c = 0; c < n_compound; ++c) {
+    k_sweep_begin<<<1, 1, 0, s>>>(n_dev);
+    count_launches(1);
+    for (int sweep = 0; sweep <= n_or; ++sweep)
+      for (int mu = 0; mu < 4; ++mu)
+        for (int par = 0; par < 2; ++par)
+          launch_update_pass(fp64, theta, g, mu, par, slab_d, sweep == 0 ? 0 : 1, n_dev, 0, seed, beta, err, s);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
 
 void launch_hot_start(bool fp64, void* theta, const Geom& g, uint64_t seed, cudaStream_t s) {
   const int nt = 256, nb = blocks_for(4ll * g.V, nt);

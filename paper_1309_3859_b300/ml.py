@@ -19,6 +19,7 @@ from . import build as _build
 
 ML_OK, ML_EINVAL, ML_ENOMEM, ML_ECUDA, ML_ETIMEOUT, ML_EREJECT, ML_EBUSY, ML_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 ML_FP64, ML_FP32 = 0, 1
+ML_SWEEP_PERSISTENT, ML_SWEEP_PASSES = 0, 1
 ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP = range(6)
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
@@ -79,6 +80,8 @@ SIGNATURES = {
     "ml_philox": (ctypes.c_int, [_U32, _U32, ctypes.c_size_t, _U32]),
     "ml_kernel_timing": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ml_batch_slots": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
+    "ml_sweep_mode": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
+    "ml_set_sweep_mode": (ctypes.c_int, [_H, ctypes.c_int]),
     "ml_naive_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
@@ -314,6 +317,16 @@ class Lattice:
         ms = ctypes.c_double()
         _check(lib().ml_kernel_timing(self.h, int(kernel), int(reps), ctypes.byref(ms)), "ml_kernel_timing")
         return ms.value
+
+    @property
+    def sweep_mode(self) -> int:
+        m = ctypes.c_int()
+        _check(lib().ml_sweep_mode(self.h, ctypes.byref(m)), "ml_sweep_mode")
+        return m.value
+
+    @sweep_mode.setter
+    def sweep_mode(self, mode: int):
+        _check(lib().ml_set_sweep_mode(self.h, int(mode)), "ml_set_sweep_mode")
 
     @property
     def batch_slots(self) -> int:

@@ -303,3 +303,23 @@ def test_full_size_observe_fp32_single_24():
     scale = {k: np.abs(ref[k]).max() for k in ("P", "Pf", "W", "vac")}
     for key in ("P", "Pf", "W", "vac"):
         assert np.abs(got[key] - ref[key]).max() < 3e-5 * max(scale[key], 1e-3), key
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_sweep_implementations_agree(fp64):
+    """The persistent kernel and the per-pass kernels run the same link
+    updates in the same order: identical chains and records."""
+    p = ml.Params(L=8, Nt=4, beta=0.95, seed=5, fp64=fp64, slab=2, n_sub=3, k_between=1, r=(1, 2), rf=(2,),
+                  probes=((0, 0), (1, 0)), comp_mask=0x3F)
+    out = {}
+    for mode in (ml.ML_SWEEP_PERSISTENT, ml.ML_SWEEP_PASSES):
+        with ml.Lattice(p) as lat:
+            lat.sweep_mode = mode
+            assert lat.sweep_mode == mode
+            lat.thermalize(3)
+            rec = lat.measure(2)
+            out[mode] = (rec, lat.get_angles(), lat.sweep)
+    a, b = out[ml.ML_SWEEP_PERSISTENT], out[ml.ML_SWEEP_PASSES]
+    assert a[2] == b[2]
+    assert np.array_equal(a[1], b[1])
+    assert np.array_equal(a[0], b[0])
