@@ -225,6 +225,37 @@ int ml_set_sweep_mode(ml_lattice *h, int mode);
 int ml_batch_slots(ml_lattice *h, int *n);
 
 /* ------------------------------------------------------------------------ */
+/* Batches: many independent lattices advanced together                      */
+/* ------------------------------------------------------------------------ */
+
+/* A batch holds n independent lattices (different L, Nt, beta, seed,
+ * separations, probes and components) that share one schedule: precision,
+ * n_or, slab, outer_slab, n_sub, n_sub_outer and k_between must be equal
+ * (else ML_EINVAL).  Every sweep, record and fold of the batch is one kernel
+ * launch over all its lattices (the multi-lattice kernels a single lattice
+ * also runs), so each lattice's results are identical to those of the same
+ * parameters run alone with ml_create.  Memory and stream as for ml_create. */
+typedef struct ml_batch ml_batch;
+int ml_batch_create(const ml_params *ps, int n, const ml_allocator *alloc, void *cuda_stream, ml_batch **out);
+int ml_batch_destroy(ml_batch *b);
+int ml_batch_size(ml_batch *b, int *n);
+/* n_sweeps full compound sweeps of every lattice.  Asynchronous. */
+int ml_batch_thermalize(ml_batch *b, int n_sweeps);
+/* n_meas measurements of every lattice (Algorithm 1).  Output layout:
+ * lattice-major, [lattice][measurement][record of that lattice], total
+ * length from ml_batch_result_len, lattice offsets from
+ * ml_batch_record_offset.  ml_batch_measure blocks; the _device variant
+ * writes device memory asynchronously. */
+int ml_batch_result_len(ml_batch *b, int n_meas, size_t *len);
+int ml_batch_record_offset(ml_batch *b, int lattice, int n_meas, size_t *offset);
+int ml_batch_measure(ml_batch *b, int n_meas, double *out_host, size_t out_len);
+int ml_batch_measure_device(ml_batch *b, int n_meas, double *out_dev, size_t out_len);
+int ml_batch_get_angles(ml_batch *b, int lattice, double *theta_host, size_t n);
+int ml_batch_sync(ml_batch *b);
+int ml_batch_sweep_mode(ml_batch *b, int *mode);
+int ml_batch_set_sweep_mode(ml_batch *b, int mode);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free entry point (no counterpart in the paper)                  */
 /* ------------------------------------------------------------------------ */
 

@@ -1,13 +1,20 @@
 // C ABI of libml (declared in include/ml.h): lattice lifecycle, Algorithm 1
 // of arXiv:1309.3859 as a host-side schedule of CUDA graphs, configuration
-// access and utilities.
+// access, batches of lattices advanced together, and utilities.
+//
+// Internally every handle is an Engine: a set of lattices (one for
+// ml_lattice, many for ml_batch) described by a device table of LatDesc, whose
+// sweeps, records and folds each run as one launch over the whole table.  A
+// lattice therefore goes through exactly the same kernels alone and in a
+// batch.
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "ml.h"
-#include "ml_internal.h"
+#include "ml_engine.h"
 
 namespace ml {
 
@@ -22,96 +29,55 @@ void count_launches(uint64_t n) {
     g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 
-struct Graph {
-  cudaGraphExec_t exec = nullptr;
-  uint64_t kernels = 0;
-};
-
 }  // namespace ml
 
 using namespace ml;
 
-struct ml_lattice {
-  // parameters
-  Geom g{};
-  bool fp64 = true;
-  double beta = 0.0;
-  uint64_t seed = 0;
-  int n_or = 3, slab = 2, n_sub = 1, outer_slab = 0, n_sub_outer = 0, k_between = 0;
-  std::vector<int> r, rf, pdy, pdz, comps, R, r_idx, rf_idx;
-  uint32_t comp_mask = 0;
-  // device state
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  ml_allocator alloc{};
-  bool use_alloc = false;
-  std::vector<void*> blocks;
-  void* theta = nullptr;
-  unsigned long long* d_n = nullptr;
-  int* d_err = nullptr;
-  uint64_t h_n = 0;
-  int* d_lists = nullptr;
-  MeasLayout meas{};
-  double2 *accT = nullptr, *accO = nullptr, *acc4T = nullptr, *acc4O = nullptr;
-  size_t accT_bytes = 0, accO_bytes = 0, acc4T_bytes = 0, acc4O_bytes = 0;
-  // double-buffered ring of sub-update records (buffer b, slot j):
-  void* osum[2] = {nullptr, nullptr};       // [nslab][nc][2][Ns][kBatch] plaquette slab sums
-  void* theta_rec[2] = {nullptr, nullptr};  // [nslab][Ns][kBatch] slab phase sums
-  int nB = kBatch;            // sub-update records folded per accumulation pass
-  int cur_buf = 0;            // ring buffer the next sub-update records into
-  // accumulation stream: folds, clears, level combination and products run
-  // there, overlapping the latency-bound sweeps on the main stream
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_rec[2] = {nullptr, nullptr};   // buffer b fully recorded (main)
-  cudaEvent_t ev_fold[2] = {nullptr, nullptr};  // buffer b folded, free again (side)
-  cudaEvent_t ev_main = nullptr, ev_side = nullptr;
-  double2* partial_naive = nullptr;
-  unsigned long long* bar = nullptr;  // arrival counter of the persistent sweep kernel's grid barrier
-  unsigned long long* scratch_n = nullptr;
-  double* vac_part = nullptr;
-  double* vac_acc = nullptr;
-  double2* partial = nullptr;
-  int nparts_inner = 0;
-  double* staging = nullptr;
-  void* scratch_theta = nullptr;
-  double* rec_buf = nullptr;
-  size_t rec_cap = 0;
-  int sweep_mode = ML_SWEEP_PERSISTENT;
-  Graph g_full, g_outer, g_one_full;
-  Graph g_flush[2];
-  Graph g_sub[2][kBatch];
-};
+namespace ml {
+namespace eng {
 
-namespace {
+#define ML_CUDA(call)                       \
+  do {                                      \
+    cudaError_t e_ = (call);                \
+    if (e_ != cudaSuccess) return ML_ECUDA; \
+  } while (0)
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? ML_OK : ML_ECUDA; }
 
-#define ML_CUDA(call)                              \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return ML_ECUDA;        \
-  } while (0)
-
-void* dev_alloc(ml_lattice* h, size_t bytes) {
+void* raw_alloc(Engine* e, size_t bytes) {
   if (bytes == 0) bytes = 256;
   void* p = nullptr;
-  if (h->use_alloc) {
-    p = h->alloc.alloc(bytes, h->alloc.ctx);
+  if (e->use_alloc) {
+    p = e->alloc.alloc(bytes, e->alloc.ctx);
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     p = nullptr;
   }
-  if (p) h->blocks.push_back(p);
   return p;
 }
 
-void free_all(ml_lattice* h) {
-  for (void* p : h->blocks) {
-    if (h->use_alloc)
-      h->alloc.free(p, h->alloc.ctx);
-    else
-      cudaFree(p);
-  }
-  h->blocks.clear();
+void raw_free(Engine* e, void* p) {
+  if (e->use_alloc)
+    e->alloc.free(p, e->alloc.ctx);
+  else
+    cudaFree(p);
+}
+
+void* dev_alloc(Engine* e, size_t bytes) {
+  void* p = raw_alloc(e, bytes);
+  if (p) e->blocks.push_back(p);
+  return p;
+}
+
+void* lat_alloc(Engine* e, LatState* L, size_t bytes) {
+  void* p = raw_alloc(e, bytes);
+  if (p) L->blocks.push_back(p);
+  return p;
+}
+
+void free_lattice(Engine* e, LatState* L) {
+  for (void* p : L->blocks) raw_free(e, p);
+  L->blocks.clear();
+  delete L;
 }
 
 int validate(const ml_params* p) {
@@ -144,39 +110,170 @@ size_t record_len(int nr, int nrf, int np) {
          static_cast<size_t>(nr) * 2 + 1;
 }
 
-// n compound sweeps (heatbath + n_or overrelaxation sweeps) with slab mask d
-// in one cooperative launch of the persistent sweep kernel
-int enqueue_sweeps_on(ml_lattice* h, int mode, void* theta, unsigned long long* n_dev, int n, int d) {
-  if (n <= 0) return ML_OK;
-  const int rc = mode == ML_SWEEP_PERSISTENT
-                     ? launch_sweeps(h->fp64, theta, h->g, d, h->n_or, n, n_dev, h->seed, h->beta, h->d_err, h->bar,
-                                     h->stream)
-                     : launch_pass_sweeps(h->fp64, theta, h->g, d, h->n_or, n, n_dev, h->seed, h->beta, h->d_err,
-                                          h->stream);
-  return rc ? ML_ECUDA : ML_OK;
+// --------------------------------------------------------------------------- lattice state
+int make_lattice(Engine* e, const ml_params* p, LatState** out) {
+  LatState* L = new (std::nothrow) LatState();
+  if (!L) return ML_ENOMEM;
+  *out = L;  // the caller owns L (and its buffers) from here on, also on failure
+  L->g.L = p->L;
+  L->g.Nt = p->Nt;
+  L->g.Ns = p->L * p->L * p->L;
+  L->g.V = L->g.Ns * p->Nt;
+  L->g.Vh = L->g.V / 2;
+  L->beta = p->beta;
+  L->seed = p->seed;
+  L->r.assign(p->r, p->r + p->nr);
+  if (p->nrf) L->rf.assign(p->rf, p->rf + p->nrf);
+  for (int b = 0; b < p->nprobe; ++b) {
+    L->pdy.push_back(p->probe[b].dy);
+    L->pdz.push_back(p->probe[b].dz);
+  }
+  for (int c = 0; c < 6; ++c)
+    if (p->comp_mask & (1u << c)) L->comps.push_back(c);
+  for (int v : L->r) {  // union of separations, with each list entry's index in it
+    int a = 0;
+    while (a < (int)L->R.size() && L->R[a] != v) ++a;
+    if (a == (int)L->R.size()) L->R.push_back(v);
+    L->r_idx.push_back(a);
+  }
+  for (int v : L->rf) {
+    int a = 0;
+    while (a < (int)L->R.size() && L->R[a] != v) ++a;
+    if (a == (int)L->R.size()) L->R.push_back(v);
+    L->rf_idx.push_back(a);
+  }
+  const Geom& g = L->g;
+  const size_t tsz = e->fp64 ? sizeof(double) : sizeof(float);
+  const int nR = static_cast<int>(L->R.size()), nr = p->nr, nrf = p->nrf, np = p->nprobe;
+  const int nc = static_cast<int>(L->comps.size());
+  const int nslab_in = g.Nt / p->slab;
+  const int nslab_out = p->outer_slab ? g.Nt / p->outer_slab : 0;
+
+  std::vector<int> lists;
+  auto push = [&](const std::vector<int>& v) {
+    size_t o = lists.size();
+    lists.insert(lists.end(), v.begin(), v.end());
+    return o;
+  };
+  const size_t oR = push(L->R), or_ = push(L->r_idx), orf_idx = push(L->rf_idx), orf = push(L->rf),
+               ody = push(L->pdy), odz = push(L->pdz), oc = push(L->comps);
+
+  L->theta = lat_alloc(e, L, 4ull * g.V * tsz);
+  L->d_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
+  L->d_lists = static_cast<int*>(lat_alloc(e, L, (lists.size() + 1) * sizeof(int)));
+  L->accT_bytes = static_cast<size_t>(nslab_in) * nR * g.Ns * sizeof(double2);
+  L->accO_bytes = static_cast<size_t>(nslab_in) * nrf * np * nc * 2 * g.Ns * sizeof(double2);
+  L->accT = static_cast<double2*>(lat_alloc(e, L, L->accT_bytes));
+  L->accO = static_cast<double2*>(lat_alloc(e, L, L->accO_bytes));
+  if (nslab_out) {
+    L->acc4T_bytes = static_cast<size_t>(nslab_out) * nR * g.Ns * sizeof(double2);
+    L->acc4O_bytes = static_cast<size_t>(nslab_out) * nrf * np * nc * 2 * g.Ns * sizeof(double2);
+    L->acc4T = static_cast<double2*>(lat_alloc(e, L, L->acc4T_bytes));
+    L->acc4O = static_cast<double2*>(lat_alloc(e, L, L->acc4O_bytes));
+  }
+  L->osum_bytes = static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * kBatch * tsz;
+  L->trec_bytes = static_cast<size_t>(nslab_in) * g.Ns * kBatch * tsz;
+  for (int b = 0; b < 2; ++b) {
+    L->osum[b] = lat_alloc(e, L, L->osum_bytes);
+    L->theta_rec[b] = lat_alloc(e, L, L->trec_bytes);
+  }
+  L->nparts = vac_part_count(g, p->slab);
+  L->vac_part = static_cast<double*>(lat_alloc(e, L, static_cast<size_t>(L->nparts) * 12 * sizeof(double)));
+  L->vac_acc = static_cast<double*>(lat_alloc(e, L, 12 * sizeof(double)));
+  const size_t nw = static_cast<size_t>(product_partial_count(g));
+  const size_t nout = static_cast<size_t>(nr) + nrf + static_cast<size_t>(nrf) * np * nc * 2;
+  const size_t nvw = static_cast<size_t>((g.V + 255) / 256) * 8;
+  L->partial = static_cast<double2*>(lat_alloc(e, L, nout * nw * sizeof(double2)));
+  L->partial_naive =
+      static_cast<double2*>(lat_alloc(e, L, (static_cast<size_t>(nr) * nw + nvw / 2 + 1) * sizeof(double2)));
+  L->scratch_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
+  const bool ok = L->theta && L->d_n && L->d_lists && L->accT && L->accO && L->osum[0] && L->osum[1] &&
+                  L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->vac_acc && L->partial &&
+                  L->partial_naive && L->scratch_n && (!nslab_out || (L->acc4T && L->acc4O));
+  if (!ok) return ML_ENOMEM;
+
+  MeasLayout& m = L->meas;
+  m.nR = nR;
+  m.nr = nr;
+  m.nrf = nrf;
+  m.np = np;
+  m.nc = nc;
+  m.R = L->d_lists + oR;
+  m.r_idx = L->d_lists + or_;
+  m.rf_idx = L->d_lists + orf_idx;
+  m.rf = L->d_lists + orf;
+  m.pdy = L->d_lists + ody;
+  m.pdz = L->d_lists + odz;
+  m.comp = L->d_lists + oc;
+  m.rec_len = static_cast<int>(record_len(nr, nrf, np));
+  m.off_P = 0;
+  m.off_Pf = 2 * nr;
+  m.off_W = m.off_Pf + 2 * nrf;
+  m.off_vac = m.off_W + nrf * np * 24;
+  m.off_naive = m.off_vac + 12;
+  m.off_plaq = m.off_naive + 2 * nr;
+
+  LatDesc& d = L->desc;
+  d.g = g;
+  d.m = m;
+  d.theta = L->theta;
+  d.n_dev = L->d_n;
+  d.k0 = static_cast<uint32_t>(p->seed);
+  d.k1 = static_cast<uint32_t>(p->seed >> 32);
+  d.beta = p->beta;
+  d.slab = p->slab;
+  d.nslab = nslab_in;
+  d.tiles = (g.Vh + kSweepTile - 1) / kSweepTile;
+  for (int b = 0; b < 2; ++b) {
+    d.theta_rec[b] = L->theta_rec[b];
+    d.osum[b] = L->osum[b];
+  }
+  d.accT = L->accT;
+  d.accO = L->accO;
+  d.vac_part = L->vac_part;
+  d.nparts = L->nparts;
+  d.vac_acc = L->vac_acc;
+
+  cudaStream_t s = e->stream;
+  cudaError_t ce = cudaSuccess;
+  if (!lists.empty())
+    ce = cudaMemcpyAsync(L->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(L->d_n, 0, sizeof(unsigned long long), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), s);
+  if (ce == cudaSuccess)
+    ce = cudaMemsetAsync(L->vac_part, 0, static_cast<size_t>(L->nparts) * 12 * sizeof(double), s);
+  // ring slots not yet written in a batch are multiplied by zero: keep them finite
+  for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
+    ce = cudaMemsetAsync(L->osum[b], 0, L->osum_bytes, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(L->theta_rec[b], 0, L->trec_bytes, s);
+  }
+  if (ce == cudaSuccess) launch_hot_start(e->fp64, L->theta, g, p->seed, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);  // `lists` is a host temporary
+  if (ce == cudaSuccess) ce = cudaGetLastError();
+  return cuda_status(ce);
 }
 
-int enqueue_sweeps(ml_lattice* h, int n, int d) { return enqueue_sweeps_on(h, h->sweep_mode, h->theta, h->d_n, n, d); }
+// --------------------------------------------------------------------------- schedule pieces
+int enqueue_sweeps_table(Engine* e, const LatDesc* table, int n, int mask, int mode) {
+  if (n <= 0) return ML_OK;
+  return launch_sweeps_table(e->fp64, mode == ML_SWEEP_PERSISTENT, table, e->d_tile_lat, e->td, nullptr, mask,
+                             e->n_or, n, e->d_err, e->bar, e->stream)
+             ? ML_ECUDA
+             : ML_OK;
+}
 
-// one slab sub-update: compound sweep with the inner mask, then the record of
-// the new configuration into slot `slot` of ring buffer `buf` and its vacuum
-// sums (main stream)
-int enqueue_sub_update(ml_lattice* h, int buf, int slot) {
-  int st = enqueue_sweeps(h, 1, h->slab);
+int enqueue_sweeps(Engine* e, int n, int mask) { return enqueue_sweeps_table(e, e->d_desc, n, mask, e->sweep_mode); }
+
+// one slab sub-update of every lattice: compound sweep with the inner mask,
+// then the record of the new configuration into slot (buf, slot) and its
+// vacuum sums (main stream)
+int enqueue_sub_update(Engine* e, int buf, int slot) {
+  int st = enqueue_sweeps(e, 1, e->slab);
   if (st) return st;
-  launch_record(h->fp64, h->theta, h->g, h->slab, h->meas, slot, h->theta_rec[buf], h->osum[buf], h->vac_part,
-                h->stream);
-  launch_vac_accumulate(h->vac_part, h->nparts_inner, h->vac_acc, 1.0 / h->g.V, h->stream);
+  launch_record_table(e->fp64, e->d_desc, e->td, nullptr, buf, slot, e->stream);
   return ML_OK;
 }
 
-// fold the first nrec slots of ring buffer `buf` into the inner slab sums
-void enqueue_fold(ml_lattice* h, int buf, int nrec, cudaStream_t s) {
-  launch_accumulate_batch(h->fp64, h->g, h->slab, h->meas, h->theta_rec[buf], h->osum[buf], nrec, h->accT, h->accO,
-                          s);
-}
-
-// make stream `to` wait for everything enqueued so far on stream `from`
 int join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
   ML_CUDA(cudaEventRecord(ev, from));
   ML_CUDA(cudaStreamWaitEvent(to, ev, 0));
@@ -184,49 +281,49 @@ int join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
 }
 
 template <typename F>
-int capture(ml_lattice* h, Graph* out, F&& body) {
+int capture(Engine* e, Graph* out, F&& body) {
   cudaGraph_t graph = nullptr;
-  ML_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  ML_CUDA(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
   tl_capturing = 1;
   tl_captured = 0;
   const int body_status = body();
   tl_capturing = 0;
-  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
-  if (e != cudaSuccess || body_status != ML_OK) {
+  cudaError_t ce = cudaStreamEndCapture(e->stream, &graph);
+  if (ce != cudaSuccess || body_status != ML_OK) {
     if (graph) cudaGraphDestroy(graph);
     return body_status != ML_OK ? body_status : ML_ECUDA;
   }
-  e = cudaGraphInstantiate(&out->exec, graph, 0);
+  ce = cudaGraphInstantiate(&out->exec, graph, 0);
   cudaGraphDestroy(graph);
-  if (e != cudaSuccess) return ML_ECUDA;
+  if (ce != cudaSuccess) return ML_ECUDA;
   out->kernels = tl_captured;
   return ML_OK;
 }
 
-int launch_graph(ml_lattice* h, const Graph& gr, cudaStream_t s = nullptr) {
-  ML_CUDA(cudaGraphLaunch(gr.exec, s ? s : h->stream));
+int launch_graph(Engine* e, const Graph& gr, cudaStream_t s = nullptr) {
+  ML_CUDA(cudaGraphLaunch(gr.exec, s ? s : e->stream));
   g_launches.fetch_add(gr.kernels, std::memory_order_relaxed);
   return ML_OK;
 }
 
-int check_errors(ml_lattice* h) {
-  if (h->side) ML_CUDA(cudaStreamSynchronize(h->side));
-  ML_CUDA(cudaStreamSynchronize(h->stream));
+int check_errors(Engine* e) {
+  if (e->side) ML_CUDA(cudaStreamSynchronize(e->side));
+  ML_CUDA(cudaStreamSynchronize(e->stream));
   int err = 0;
-  ML_CUDA(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  ML_CUDA(cudaMemcpy(&err, e->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (err) {
-    ML_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
-    ML_CUDA(cudaStreamSynchronize(h->stream));
+    ML_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(int), e->stream));
+    ML_CUDA(cudaStreamSynchronize(e->stream));
     if (err & kErrTimeout) return ML_ETIMEOUT;
     if (err & kErrReject) return ML_EREJECT;
   }
   return ML_OK;
 }
 
-void destroy_graphs(ml_lattice* h) {
-  std::vector<Graph*> all = {&h->g_full, &h->g_outer, &h->g_one_full, &h->g_flush[0], &h->g_flush[1]};
+void destroy_graphs(Engine* e) {
+  std::vector<Graph*> all = {&e->g_full, &e->g_outer, &e->g_one_full, &e->g_flush[0], &e->g_flush[1]};
   for (int b = 0; b < 2; ++b)
-    for (int j = 0; j < kBatch; ++j) all.push_back(&h->g_sub[b][j]);
+    for (int j = 0; j < kBatch; ++j) all.push_back(&e->g_sub[b][j]);
   for (Graph* gr : all)
     if (gr->exec) {
       cudaGraphExecDestroy(gr->exec);
@@ -234,214 +331,378 @@ void destroy_graphs(ml_lattice* h) {
     }
 }
 
-void destroy_streams(ml_lattice* h) {
-  for (cudaEvent_t* e : {&h->ev_rec[0], &h->ev_rec[1], &h->ev_fold[0], &h->ev_fold[1], &h->ev_main, &h->ev_side})
-    if (*e) {
-      cudaEventDestroy(*e);
-      *e = nullptr;
-    }
-  if (h->side) {
-    cudaStreamSynchronize(h->side);
-    cudaStreamDestroy(h->side);
-    h->side = nullptr;
-  }
-}
-
 // hand ring buffer `buf` (nrec records) from the main stream to the fold on
 // the accumulation stream
-int hand_over(ml_lattice* h, int buf, int nrec) {
-  ML_CUDA(cudaEventRecord(h->ev_rec[buf], h->stream));
-  ML_CUDA(cudaStreamWaitEvent(h->side, h->ev_rec[buf], 0));
-  if (nrec == h->nB) {
-    int st = launch_graph(h, h->g_flush[buf], h->side);
+int hand_over(Engine* e, int buf, int nrec) {
+  ML_CUDA(cudaEventRecord(e->ev_rec[buf], e->stream));
+  ML_CUDA(cudaStreamWaitEvent(e->side, e->ev_rec[buf], 0));
+  if (nrec == e->nB) {
+    int st = launch_graph(e, e->g_flush[buf], e->side);
     if (st) return st;
   } else {
-    enqueue_fold(h, buf, nrec, h->side);
+    launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, nrec, e->side);
   }
-  ML_CUDA(cudaEventRecord(h->ev_fold[buf], h->side));
+  ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
   return ML_OK;
 }
 
 // inner loop of n_sub slab sub-updates (main stream), folding every nB
 // records on the accumulation stream while the sweeps continue; a ring
 // buffer is reused only after its previous fold has finished
-int run_inner_loop(ml_lattice* h) {
-  int buf = h->cur_buf, slot = 0;
-  ML_CUDA(cudaStreamWaitEvent(h->stream, h->ev_fold[buf], 0));
-  for (int i = 0; i < h->n_sub; ++i) {
-    int st = launch_graph(h, h->g_sub[buf][slot]);
+int run_inner_loop(Engine* e) {
+  int buf = e->cur_buf, slot = 0;
+  ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
+  for (int i = 0; i < e->n_sub; ++i) {
+    int st = launch_graph(e, e->g_sub[buf][slot]);
     if (st) return st;
-    if (++slot == h->nB) {
-      st = hand_over(h, buf, slot);
+    if (++slot == e->nB) {
+      st = hand_over(e, buf, slot);
       if (st) return st;
       buf ^= 1;
       slot = 0;
-      if (i + 1 < h->n_sub) ML_CUDA(cudaStreamWaitEvent(h->stream, h->ev_fold[buf], 0));
+      if (i + 1 < e->n_sub) ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
     }
   }
   if (slot > 0) {
-    int st = hand_over(h, buf, slot);
+    int st = hand_over(e, buf, slot);
     if (st) return st;
     buf ^= 1;
   }
-  h->cur_buf = buf;
+  e->cur_buf = buf;
   return ML_OK;
 }
 
-// clear the inner slab sums (accumulation stream)
-int zero_inner(ml_lattice* h, cudaStream_t s) {
-  ML_CUDA(cudaMemsetAsync(h->accT, 0, h->accT_bytes, s));
-  if (h->accO_bytes) ML_CUDA(cudaMemsetAsync(h->accO, 0, h->accO_bytes, s));
+int zero_inner(Engine* e, cudaStream_t s) {
+  for (LatState* L : e->lats) {
+    ML_CUDA(cudaMemsetAsync(L->accT, 0, L->accT_bytes, s));
+    if (L->accO_bytes) ML_CUDA(cudaMemsetAsync(L->accO, 0, L->accO_bytes, s));
+  }
   return ML_OK;
 }
 
-int ensure_rec(ml_lattice* h, size_t doubles) {
-  if (doubles <= h->rec_cap) return ML_OK;
-  double* p = static_cast<double*>(dev_alloc(h, doubles * sizeof(double)));
+int ensure_rec(Engine* e, size_t doubles) {
+  if (doubles <= e->rec_cap) return ML_OK;
+  double* p = static_cast<double*>(dev_alloc(e, doubles * sizeof(double)));
   if (!p) return ML_ENOMEM;
-  h->rec_buf = p;  // the previous buffer stays owned until destroy
-  h->rec_cap = doubles;
+  e->rec_buf = p;  // the previous buffer stays owned until destroy
+  e->rec_cap = doubles;
   return ML_OK;
 }
 
-// Algorithm 1 for n_meas measurements into device records rec.  Sweeps,
-// records and the vacuum run on the main stream; clears, folds, the level
-// combination and the products on the accumulation stream.
-int enqueue_measurements(ml_lattice* h, int n_meas, double* rec) {
-  const MeasLayout& m = h->meas;
-  const int nslab_in = h->g.Nt / h->slab;
-  int st = join(h->stream, h->side, h->ev_main);
+// offset (doubles) of lattice li's first record in an output of n_meas
+// measurements: lattice-major, [lattice][measurement][record]
+size_t record_offset(const Engine* e, int li, int n_meas) {
+  size_t o = 0;
+  for (int k = 0; k < li; ++k) o += static_cast<size_t>(n_meas) * e->lats[k]->meas.rec_len;
+  return o;
+}
+
+size_t total_len(const Engine* e, int n_meas) { return record_offset(e, static_cast<int>(e->lats.size()), n_meas); }
+
+// Algorithm 1 for n_meas measurements of every lattice.  Sweeps, records and
+// the vacuum run on the main stream; clears, folds, the level combination and
+// the products on the accumulation stream.
+int enqueue_measurements(Engine* e, int n_meas, double* rec) {
+  int st = join(e->stream, e->side, e->ev_main);
   if (st) return st;
+  const int nlat = static_cast<int>(e->lats.size());
+  std::vector<double*> out(nlat);
   for (int j = 0; j < n_meas; ++j) {
-    double* out = rec + static_cast<size_t>(j) * m.rec_len;
-    ML_CUDA(cudaMemsetAsync(out, 0, m.rec_len * sizeof(double), h->stream));
-    if (h->k_between > 0) {
-      st = launch_graph(h, h->g_full);
+    for (int li = 0; li < nlat; ++li) {
+      LatState* L = e->lats[li];
+      out[li] = rec + record_offset(e, li, n_meas) + static_cast<size_t>(j) * L->meas.rec_len;
+      ML_CUDA(cudaMemsetAsync(out[li], 0, L->meas.rec_len * sizeof(double), e->stream));
+    }
+    if (e->k_between > 0) {
+      st = launch_graph(e, e->g_full);
       if (st) return st;
     }
-    launch_naive_and_plaquette(h->fp64, h->theta, h->g, m, h->partial_naive, out, h->stream);
-    ML_CUDA(cudaMemsetAsync(h->vac_acc, 0, 12 * sizeof(double), h->stream));
-    st = join(h->stream, h->side, h->ev_main);  // the record `out` is cleared before the products
+    for (int li = 0; li < nlat; ++li) {
+      LatState* L = e->lats[li];
+      launch_naive_and_plaquette(e->fp64, L->theta, L->g, L->meas, L->partial_naive, out[li], e->stream);
+      ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->stream));
+    }
+    st = join(e->stream, e->side, e->ev_main);  // records cleared before the products write them
     if (st) return st;
     int ncfg = 0;
-    if (h->outer_slab == 0) {
-      st = zero_inner(h, h->side);
-      if (!st) st = run_inner_loop(h);
+    if (e->outer_slab == 0) {
+      st = zero_inner(e, e->side);
+      if (!st) st = run_inner_loop(e);
       if (st) return st;
-      launch_products(h->g, nslab_in, m, h->accT, h->accO, 1.0 / h->n_sub, h->partial, out, h->side);
-      ncfg = h->n_sub;
-    } else {
-      const int nslab_out = h->g.Nt / h->outer_slab;
-      ML_CUDA(cudaMemsetAsync(h->acc4T, 0, h->acc4T_bytes, h->side));
-      if (h->acc4O_bytes) ML_CUDA(cudaMemsetAsync(h->acc4O, 0, h->acc4O_bytes, h->side));
-      for (int o = 0; o < h->n_sub_outer; ++o) {
-        st = launch_graph(h, h->g_outer);
-        if (!st) st = zero_inner(h, h->side);
-        if (!st) st = run_inner_loop(h);
-        if (st) return st;
-        launch_combine(h->g, nslab_out, h->outer_slab / h->slab, m, h->accT, h->accO, 1.0 / h->n_sub, h->acc4T,
-                       h->acc4O, h->side);
+      for (int li = 0; li < nlat; ++li) {
+        LatState* L = e->lats[li];
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, L->accT, L->accO, 1.0 / e->n_sub, L->partial, out[li],
+                        e->side);
       }
-      launch_products(h->g, nslab_out, m, h->acc4T, h->acc4O, 1.0 / h->n_sub_outer, h->partial, out, h->side);
-      ncfg = h->n_sub * h->n_sub_outer;
+      ncfg = e->n_sub;
+    } else {
+      for (LatState* L : e->lats) {
+        ML_CUDA(cudaMemsetAsync(L->acc4T, 0, L->acc4T_bytes, e->side));
+        if (L->acc4O_bytes) ML_CUDA(cudaMemsetAsync(L->acc4O, 0, L->acc4O_bytes, e->side));
+      }
+      for (int o = 0; o < e->n_sub_outer; ++o) {
+        st = launch_graph(e, e->g_outer);
+        if (!st) st = zero_inner(e, e->side);
+        if (!st) st = run_inner_loop(e);
+        if (st) return st;
+        for (LatState* L : e->lats)
+          launch_combine(L->g, L->g.Nt / e->outer_slab, e->outer_slab / e->slab, L->meas, L->accT, L->accO,
+                         1.0 / e->n_sub, L->acc4T, L->acc4O, e->side);
+      }
+      for (int li = 0; li < nlat; ++li) {
+        LatState* L = e->lats[li];
+        launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, L->acc4T, L->acc4O, 1.0 / e->n_sub_outer,
+                        L->partial, out[li], e->side);
+      }
+      ncfg = e->n_sub * e->n_sub_outer;
     }
-    launch_write_vac(h->vac_acc, 1.0 / ncfg, m, out, h->stream);
-    h->h_n += static_cast<uint64_t>(h->k_between) + (h->outer_slab == 0
-                                                          ? static_cast<uint64_t>(h->n_sub)
-                                                          : static_cast<uint64_t>(h->n_sub_outer) * (1 + h->n_sub));
+    for (int li = 0; li < nlat; ++li)
+      launch_write_vac(e->lats[li]->vac_acc, 1.0 / ncfg, e->lats[li]->meas, out[li], e->stream);
   }
-  st = join(h->side, h->stream, h->ev_side);  // results complete in stream order on the main stream
+  st = join(e->side, e->stream, e->ev_side);  // results complete in stream order on the main stream
   if (st) return st;
   return cuda_status(cudaGetLastError());
 }
 
 // Capture every graph of the measurement schedule for the current sweep mode.
-int capture_graphs(ml_lattice* h) {
+int capture_graphs(Engine* e) {
   int st = ML_OK;
-  if (h->k_between > 0) st = capture(h, &h->g_full, [&] { return enqueue_sweeps(h, h->k_between, 0); });
-  if (!st) st = capture(h, &h->g_one_full, [&] { return enqueue_sweeps(h, 1, 0); });
+  if (e->k_between > 0) st = capture(e, &e->g_full, [&] { return enqueue_sweeps(e, e->k_between, 0); });
+  if (!st) st = capture(e, &e->g_one_full, [&] { return enqueue_sweeps(e, 1, 0); });
   for (int b = 0; b < 2; ++b) {
-    for (int j = 0; j < h->nB && !st; ++j)
-      st = capture(h, &h->g_sub[b][j], [&] { return enqueue_sub_update(h, b, j); });
-    if (!st) st = capture(h, &h->g_flush[b], [&] {
-      enqueue_fold(h, b, h->nB, h->stream);
+    for (int j = 0; j < e->nB && !st; ++j)
+      st = capture(e, &e->g_sub[b][j], [&] { return enqueue_sub_update(e, b, j); });
+    if (!st) st = capture(e, &e->g_flush[b], [&] {
+      launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, b, e->nB, e->stream);
       return ML_OK;
     });
   }
-  if (!st && h->outer_slab) st = capture(h, &h->g_outer, [&] { return enqueue_sweeps(h, 1, h->outer_slab); });
+  if (!st && e->outer_slab) st = capture(e, &e->g_outer, [&] { return enqueue_sweeps(e, 1, e->outer_slab); });
   return st;
 }
 
-int ensure_scratch_theta(ml_lattice* h) {
-  if (h->scratch_theta) return ML_OK;
-  h->scratch_theta = dev_alloc(h, 4ull * h->g.V * (h->fp64 ? sizeof(double) : sizeof(float)));
-  return h->scratch_theta ? ML_OK : ML_ENOMEM;
+// timing copies of every lattice's angles and sweep counter, and a table that
+// points at them
+int ensure_scratch(Engine* e) {
+  if (e->d_desc_scratch) return ML_OK;
+  const size_t tsz = e->fp64 ? sizeof(double) : sizeof(float);
+  std::vector<LatDesc> tab;
+  for (LatState* L : e->lats) {
+    L->scratch_theta = lat_alloc(e, L, 4ull * L->g.V * tsz);
+    if (!L->scratch_theta) return ML_ENOMEM;
+    LatDesc d = L->desc;
+    d.theta = L->scratch_theta;
+    d.n_dev = L->scratch_n;
+    tab.push_back(d);
+  }
+  e->d_desc_scratch = static_cast<LatDesc*>(dev_alloc(e, tab.size() * sizeof(LatDesc)));
+  if (!e->d_desc_scratch) return ML_ENOMEM;
+  ML_CUDA(cudaMemcpyAsync(e->d_desc_scratch, tab.data(), tab.size() * sizeof(LatDesc), cudaMemcpyHostToDevice,
+                          e->stream));
+  ML_CUDA(cudaStreamSynchronize(e->stream));
+  return ML_OK;
 }
 
-// Autotuning of the sweep implementation: time one compound slab sweep as the
-// persistent cooperative kernel and as a captured graph of per-pass kernels
-// (on a scratch copy of the angles) and keep the faster.  Small lattices are
-// latency-bound and favour the persistent kernel; large ones favour the
-// per-pass kernels' full occupancy.
-int choose_sweep_mode(ml_lattice* h) {
-  int st = ensure_scratch_theta(h);
+int refresh_scratch(Engine* e) {
+  const size_t tsz = e->fp64 ? sizeof(double) : sizeof(float);
+  for (LatState* L : e->lats) {
+    ML_CUDA(cudaMemcpyAsync(L->scratch_theta, L->theta, 4ull * L->g.V * tsz, cudaMemcpyDeviceToDevice, e->stream));
+    ML_CUDA(cudaMemcpyAsync(L->scratch_n, L->d_n, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, e->stream));
+  }
+  return ML_OK;
+}
+
+// Autotuning of the sweep implementation: time one compound slab sweep of the
+// table as the persistent cooperative kernel and as a captured graph of
+// per-pass kernels (on the timing copies), alternating the candidates over
+// several rounds (the clocks may still be ramping up), and keep the faster.
+// Small tables are latency-bound and favour the persistent kernel; large ones
+// favour the per-pass kernels' full occupancy.
+int choose_sweep_mode(Engine* e) {
+  int st = ensure_scratch(e);
+  if (!st) st = refresh_scratch(e);
   if (st) return st;
-  const size_t tbytes = 4ull * h->g.V * (h->fp64 ? sizeof(double) : sizeof(float));
-  ML_CUDA(cudaMemcpyAsync(h->scratch_theta, h->theta, tbytes, cudaMemcpyDeviceToDevice, h->stream));
-  ML_CUDA(cudaMemsetAsync(h->scratch_n, 0, sizeof(unsigned long long), h->stream));
   Graph pp;
-  st = capture(h, &pp, [&] { return enqueue_sweeps_on(h, ML_SWEEP_PASSES, h->scratch_theta, h->scratch_n, 1, h->slab); });
+  st = capture(e, &pp, [&] { return enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, ML_SWEEP_PASSES); });
   if (st) return st;
-  // alternate the candidates over several rounds (the clocks may still be
-  // ramping up when a handle is created) and keep each one's best round
   cudaEvent_t ev[3];
-  for (cudaEvent_t& e : ev) ML_CUDA(cudaEventCreate(&e));
+  for (cudaEvent_t& x : ev) ML_CUDA(cudaEventCreate(&x));
   const int rounds = 4, reps = 2;
   float best[2] = {1e30f, 1e30f};
-  st = enqueue_sweeps_on(h, ML_SWEEP_PERSISTENT, h->scratch_theta, h->scratch_n, 2, h->slab);  // warm-up
-  if (!st) st = launch_graph(h, pp);
+  st = enqueue_sweeps_table(e, e->d_desc_scratch, 2, e->slab, ML_SWEEP_PERSISTENT);  // warm-up
+  if (!st) st = launch_graph(e, pp);
   for (int r = 0; r < rounds && !st; ++r) {
-    st = cuda_status(cudaEventRecord(ev[0], h->stream));
+    st = cuda_status(cudaEventRecord(ev[0], e->stream));
     for (int i = 0; i < reps && !st; ++i)
-      st = enqueue_sweeps_on(h, ML_SWEEP_PERSISTENT, h->scratch_theta, h->scratch_n, 1, h->slab);
-    if (!st) st = cuda_status(cudaEventRecord(ev[1], h->stream));
-    for (int i = 0; i < reps && !st; ++i) st = launch_graph(h, pp);
-    if (!st) st = cuda_status(cudaEventRecord(ev[2], h->stream));
+      st = enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, ML_SWEEP_PERSISTENT);
+    if (!st) st = cuda_status(cudaEventRecord(ev[1], e->stream));
+    for (int i = 0; i < reps && !st; ++i) st = launch_graph(e, pp);
+    if (!st) st = cuda_status(cudaEventRecord(ev[2], e->stream));
     if (!st) st = cuda_status(cudaEventSynchronize(ev[2]));
     if (!st) {
       float a = 0.f, b = 0.f;
       cudaEventElapsedTime(&a, ev[0], ev[1]);
       cudaEventElapsedTime(&b, ev[1], ev[2]);
-      best[0] = a < best[0] ? a : best[0];
-      best[1] = b < best[1] ? b : best[1];
+      best[0] = std::min(best[0], a);
+      best[1] = std::min(best[1], b);
     }
   }
-  if (!st) h->sweep_mode = best[1] < best[0] ? ML_SWEEP_PASSES : ML_SWEEP_PERSISTENT;
-  for (cudaEvent_t& e : ev) cudaEventDestroy(e);
+  if (!st) e->sweep_mode = best[1] < best[0] ? ML_SWEEP_PASSES : ML_SWEEP_PERSISTENT;
+  for (cudaEvent_t& x : ev) cudaEventDestroy(x);
   cudaGraphExecDestroy(pp.exec);
   if (st) return st;
-  return check_errors(h);
+  return check_errors(e);
 }
 
-}  // namespace
+void destroy_engine(Engine* e) {
+  if (e->side) cudaStreamSynchronize(e->side);
+  if (e->stream) cudaStreamSynchronize(e->stream);
+  destroy_graphs(e);
+  for (cudaEvent_t* x : {&e->ev_rec[0], &e->ev_rec[1], &e->ev_fold[0], &e->ev_fold[1], &e->ev_main, &e->ev_side})
+    if (*x) cudaEventDestroy(*x);
+  if (e->side) cudaStreamDestroy(e->side);
+  for (LatState* L : e->lats) free_lattice(e, L);
+  e->lats.clear();
+  for (void* p : e->blocks) raw_free(e, p);
+  e->blocks.clear();
+  if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+}
+
+// Build an engine over n parameter sets that share one schedule (precision,
+// n_or, slab, outer_slab, n_sub, n_sub_outer, k_between).
+int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc, void* cuda_stream) {
+  if (!ps || n < 1) return ML_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    int st = validate(&ps[i]);
+    if (st) return st;
+    const ml_params& a = ps[0];
+    const ml_params& b = ps[i];
+    if (a.prec != b.prec || a.n_or != b.n_or || a.slab != b.slab || a.outer_slab != b.outer_slab ||
+        a.n_sub != b.n_sub || a.k_between != b.k_between || (a.outer_slab && a.n_sub_outer != b.n_sub_outer))
+      return ML_EINVAL;
+  }
+  e->fp64 = ps[0].prec == ML_FP64;
+  e->n_or = ps[0].n_or;
+  e->slab = ps[0].slab;
+  e->outer_slab = ps[0].outer_slab;
+  e->n_sub = ps[0].n_sub;
+  e->n_sub_outer = ps[0].n_sub_outer;
+  e->k_between = ps[0].k_between;
+  if (alloc && alloc->alloc && alloc->free) {
+    e->alloc = *alloc;
+    e->use_alloc = true;
+  }
+  if (cuda_stream) {
+    e->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    ML_CUDA(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+    e->own_stream = true;
+  }
+  int lo = 0, hi = 0;
+  ML_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  ML_CUDA(cudaStreamCreateWithPriority(&e->side, cudaStreamNonBlocking, lo));
+  for (cudaEvent_t* x : {&e->ev_rec[0], &e->ev_rec[1], &e->ev_fold[0], &e->ev_fold[1], &e->ev_main, &e->ev_side})
+    ML_CUDA(cudaEventCreateWithFlags(x, cudaEventDisableTiming));
+  e->d_err = static_cast<int*>(dev_alloc(e, sizeof(int)));
+  e->bar = static_cast<unsigned long long*>(dev_alloc(e, sizeof(unsigned long long)));
+  if (!e->d_err || !e->bar) return ML_ENOMEM;
+  ML_CUDA(cudaMemsetAsync(e->d_err, 0, sizeof(int), e->stream));
+  ML_CUDA(cudaMemsetAsync(e->bar, 0, sizeof(unsigned long long), e->stream));
+
+  std::vector<LatDesc> tab;
+  std::vector<int> tile_lat;
+  TableDims& td = e->td;
+  td = TableDims{};
+  for (int i = 0; i < n; ++i) {
+    LatState* L = nullptr;
+    int st = make_lattice(e, &ps[i], &L);
+    if (L) e->lats.push_back(L);  // owned by the engine from here on
+    if (st) return st;
+    LatDesc& d = L->desc;
+    d.tile_start = static_cast<int>(tile_lat.size());
+    tile_lat.insert(tile_lat.end(), d.tiles, i);
+    tab.push_back(d);
+    const MeasLayout& m = d.m;
+    td.max_blocks_rec = std::max(td.max_blocks_rec, record_blocks(d.g, d.slab));
+    td.max_nc1 = std::max(td.max_nc1, m.nc + 1);
+    td.max_blocks_site = std::max(td.max_blocks_site, (d.g.Ns + 255) / 256);
+    td.max_y_T = std::max(td.max_y_T, d.nslab * m.nR);
+    if (m.nrf > 0 && m.np > 0 && m.nc > 0)
+      td.max_y_O = std::max(td.max_y_O, d.nslab * m.nrf * fold_probe_groups(m.np));
+  }
+  td.nlat = n;
+  td.total_tiles = static_cast<int>(tile_lat.size());
+  e->d_desc = static_cast<LatDesc*>(dev_alloc(e, tab.size() * sizeof(LatDesc)));
+  e->d_tile_lat = static_cast<int*>(dev_alloc(e, tile_lat.size() * sizeof(int)));
+  if (!e->d_desc || !e->d_tile_lat) return ML_ENOMEM;
+  ML_CUDA(cudaMemcpyAsync(e->d_desc, tab.data(), tab.size() * sizeof(LatDesc), cudaMemcpyHostToDevice, e->stream));
+  ML_CUDA(cudaMemcpyAsync(e->d_tile_lat, tile_lat.data(), tile_lat.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          e->stream));
+  ML_CUDA(cudaStreamSynchronize(e->stream));
+  int st = choose_sweep_mode(e);
+  if (!st) st = capture_graphs(e);
+  return st;
+}
+
+int thermalize_engine(Engine* e, int n_sweeps) {
+  if (n_sweeps < 0) return ML_EINVAL;
+  int st = ML_OK;
+  if (e->sweep_mode == ML_SWEEP_PERSISTENT)
+    st = enqueue_sweeps(e, n_sweeps, 0);
+  else
+    for (int i = 0; i < n_sweeps && !st; ++i) st = launch_graph(e, e->g_one_full);
+  return st;
+}
+
+int measure_host(Engine* e, int n_meas, double* out_host, size_t out_len) {
+  if (n_meas < 0 || (n_meas > 0 && !out_host)) return ML_EINVAL;
+  const size_t need = total_len(e, n_meas);
+  if (out_len < need) return ML_EINVAL;
+  int st = ensure_rec(e, need);
+  if (st) return st;
+  st = enqueue_measurements(e, n_meas, e->rec_buf);
+  if (st) return st;
+  ML_CUDA(cudaMemcpyAsync(out_host, e->rec_buf, need * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+  return check_errors(e);
+}
+
+int get_angles(Engine* e, LatState* L, double* theta_host, size_t n) {
+  if (!theta_host || n < 4ull * L->g.V) return ML_EINVAL;
+  if (!L->staging) {
+    L->staging = static_cast<double*>(lat_alloc(e, L, 4ull * L->g.V * sizeof(double)));
+    if (!L->staging) return ML_ENOMEM;
+  }
+  ML_CUDA(cudaStreamSynchronize(e->side));
+  launch_angles_from_soa(e->fp64, L->theta, L->staging, L->g, e->stream);
+  ML_CUDA(cudaMemcpyAsync(theta_host, L->staging, 4ull * L->g.V * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+  return check_errors(e);
+}
+
+int set_sweep_mode(Engine* e, int mode) {
+  if (mode != ML_SWEEP_PERSISTENT && mode != ML_SWEEP_PASSES) return ML_EINVAL;
+  int st = check_errors(e);
+  if (st) return st;
+  if (mode == e->sweep_mode) return ML_OK;
+  destroy_graphs(e);
+  e->sweep_mode = mode;
+  return capture_graphs(e);
+}
+
+}  // namespace eng
+}  // namespace ml
+
+using namespace ml::eng;
+
+struct ml_lattice {
+  Engine e;
+  LatState* L() { return e.lats[0]; }
+};
+
+struct ml_batch {
+  Engine e;
+};
 
 extern "C" {
-
-int ml_sweep_mode(ml_lattice* h, int* mode) {
-  if (!h || !mode) return ML_EINVAL;
-  *mode = h->sweep_mode;
-  return ML_OK;
-}
-
-int ml_set_sweep_mode(ml_lattice* h, int mode) {
-  if (!h || (mode != ML_SWEEP_PERSISTENT && mode != ML_SWEEP_PASSES)) return ML_EINVAL;
-  int st = check_errors(h);
-  if (st) return st;
-  if (mode == h->sweep_mode) return ML_OK;
-  destroy_graphs(h);
-  h->sweep_mode = mode;
-  return capture_graphs(h);
-}
 
 const char* ml_error_string(int status) {
   switch (status) {
@@ -466,6 +727,7 @@ int ml_record_len(const ml_params* p, size_t* len) {
   return ML_OK;
 }
 
+// --------------------------------------------------------------------------- single lattice
 int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, ml_lattice** out) {
   if (!out) return ML_EINVAL;
   *out = nullptr;
@@ -473,168 +735,9 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
   if (st) return st;
   ml_lattice* h = new (std::nothrow) ml_lattice();
   if (!h) return ML_ENOMEM;
-  h->g.L = p->L;
-  h->g.Nt = p->Nt;
-  h->g.Ns = p->L * p->L * p->L;
-  h->g.V = h->g.Ns * p->Nt;
-  h->g.Vh = h->g.V / 2;
-  h->fp64 = p->prec == ML_FP64;
-  h->beta = p->beta;
-  h->seed = p->seed;
-  h->n_or = p->n_or;
-  h->slab = p->slab;
-  h->n_sub = p->n_sub;
-  h->outer_slab = p->outer_slab;
-  h->n_sub_outer = p->n_sub_outer;
-  h->k_between = p->k_between;
-  h->r.assign(p->r, p->r + p->nr);
-  if (p->nrf) h->rf.assign(p->rf, p->rf + p->nrf);
-  for (int b = 0; b < p->nprobe; ++b) {
-    h->pdy.push_back(p->probe[b].dy);
-    h->pdz.push_back(p->probe[b].dz);
-  }
-  h->comp_mask = p->comp_mask;
-  for (int c = 0; c < 6; ++c)
-    if (p->comp_mask & (1u << c)) h->comps.push_back(c);
-  // union of separations, with the index of every list entry in it
-  for (int v : h->r) {
-    int a = 0;
-    while (a < (int)h->R.size() && h->R[a] != v) ++a;
-    if (a == (int)h->R.size()) h->R.push_back(v);
-    h->r_idx.push_back(a);
-  }
-  for (int v : h->rf) {
-    int a = 0;
-    while (a < (int)h->R.size() && h->R[a] != v) ++a;
-    if (a == (int)h->R.size()) h->R.push_back(v);
-    h->rf_idx.push_back(a);
-  }
-  if (alloc && alloc->alloc && alloc->free) {
-    h->alloc = *alloc;
-    h->use_alloc = true;
-  }
-  if (cuda_stream) {
-    h->stream = static_cast<cudaStream_t>(cuda_stream);
-  } else {
-    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
-      delete h;
-      return ML_ECUDA;
-    }
-    h->own_stream = true;
-  }
-
-  const Geom& g = h->g;
-  const size_t tsz = h->fp64 ? sizeof(double) : sizeof(float);
-  const int nR = static_cast<int>(h->R.size()), nr = p->nr, nrf = p->nrf, np = p->nprobe;
-  const int nc = static_cast<int>(h->comps.size());
-  const int nslab_in = g.Nt / h->slab;
-  const int nslab_out = h->outer_slab ? g.Nt / h->outer_slab : 0;
-
-  // device lists: R, r_idx, rf_idx, rf, pdy, pdz, comp
-  std::vector<int> lists;
-  auto push = [&](const std::vector<int>& v) {
-    size_t o = lists.size();
-    lists.insert(lists.end(), v.begin(), v.end());
-    return o;
-  };
-  const size_t oR = push(h->R), or_ = push(h->r_idx), orf_idx = push(h->rf_idx), orf = push(h->rf),
-               ody = push(h->pdy), odz = push(h->pdz), oc = push(h->comps);
-
-  h->theta = dev_alloc(h, 4ull * g.V * tsz);
-  h->d_n = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long)));
-  h->d_err = static_cast<int*>(dev_alloc(h, sizeof(int)));
-  h->d_lists = static_cast<int*>(dev_alloc(h, (lists.size() + 1) * sizeof(int)));
-  h->accT_bytes = static_cast<size_t>(nslab_in) * nR * g.Ns * sizeof(double2);
-  h->accO_bytes = static_cast<size_t>(nslab_in) * nrf * np * nc * 2 * g.Ns * sizeof(double2);
-  h->accT = static_cast<double2*>(dev_alloc(h, h->accT_bytes));
-  h->accO = static_cast<double2*>(dev_alloc(h, h->accO_bytes));
-  if (nslab_out) {
-    h->acc4T_bytes = static_cast<size_t>(nslab_out) * nR * g.Ns * sizeof(double2);
-    h->acc4O_bytes = static_cast<size_t>(nslab_out) * nrf * np * nc * 2 * g.Ns * sizeof(double2);
-    h->acc4T = static_cast<double2*>(dev_alloc(h, h->acc4T_bytes));
-    h->acc4O = static_cast<double2*>(dev_alloc(h, h->acc4O_bytes));
-  }
-  const size_t osum_bytes = static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * kBatch * tsz;
-  const size_t trec_bytes = static_cast<size_t>(nslab_in) * g.Ns * kBatch * tsz;
-  for (int b = 0; b < 2; ++b) {
-    h->osum[b] = dev_alloc(h, osum_bytes);
-    h->theta_rec[b] = dev_alloc(h, trec_bytes);
-  }
-  h->bar = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long)));
-  h->scratch_n = static_cast<unsigned long long*>(dev_alloc(h, sizeof(unsigned long long)));
-  h->nparts_inner = vac_part_count(g, h->slab);
-  h->vac_part = static_cast<double*>(dev_alloc(h, static_cast<size_t>(h->nparts_inner) * 12 * sizeof(double)));
-  h->vac_acc = static_cast<double*>(dev_alloc(h, 12 * sizeof(double)));
-  const size_t nw = static_cast<size_t>(product_partial_count(g));
-  const size_t nout = static_cast<size_t>(nr) + nrf + static_cast<size_t>(nrf) * np * nc * 2;
-  const size_t nvw = static_cast<size_t>((g.V + 255) / 256) * 8;
-  const size_t part = std::max(nout * nw, static_cast<size_t>(nr) * nw + nvw / 2 + 1);
-  h->partial = static_cast<double2*>(dev_alloc(h, part * sizeof(double2)));
-  h->partial_naive = static_cast<double2*>(dev_alloc(h, (static_cast<size_t>(nr) * nw + nvw / 2 + 1) * sizeof(double2)));
-  bool ok = h->theta && h->d_n && h->d_err && h->d_lists && h->accT && h->accO && h->osum[0] && h->osum[1] &&
-            h->theta_rec[0] && h->theta_rec[1] && h->partial_naive &&
-            h->bar && h->scratch_n && h->vac_part &&
-            h->vac_acc && h->partial && (!nslab_out || (h->acc4T && h->acc4O));
-  if (!ok) {
-    free_all(h);
-    if (h->own_stream) cudaStreamDestroy(h->stream);
-    delete h;
-    return ML_ENOMEM;
-  }
-
-  MeasLayout& m = h->meas;
-  m.nR = nR;
-  m.nr = nr;
-  m.nrf = nrf;
-  m.np = np;
-  m.nc = nc;
-  m.R = h->d_lists + oR;
-  m.r_idx = h->d_lists + or_;
-  m.rf_idx = h->d_lists + orf_idx;
-  m.rf = h->d_lists + orf;
-  m.pdy = h->d_lists + ody;
-  m.pdz = h->d_lists + odz;
-  m.comp = h->d_lists + oc;
-  m.rec_len = static_cast<int>(record_len(nr, nrf, np));
-  m.off_P = 0;
-  m.off_Pf = 2 * nr;
-  m.off_W = m.off_Pf + 2 * nrf;
-  m.off_vac = m.off_W + nrf * np * 24;
-  m.off_naive = m.off_vac + 12;
-  m.off_plaq = m.off_naive + 2 * nr;
-
-  cudaError_t e = cudaSuccess;
-  if (!lists.empty())
-    e = cudaMemcpyAsync(h->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_n, 0, sizeof(unsigned long long), h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->vac_acc, 0, 12 * sizeof(double), h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->bar, 0, sizeof(unsigned long long), h->stream);
-  // ring slots not yet written in a batch are multiplied by zero: keep them finite
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-    e = cudaMemsetAsync(h->osum[b], 0, osum_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->theta_rec[b], 0, trec_bytes, h->stream);
-  }
-  if (e == cudaSuccess) {
-    int lo = 0, hi = 0;
-    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, lo);
-  }
-  for (cudaEvent_t* ev : {&h->ev_rec[0], &h->ev_rec[1], &h->ev_fold[0], &h->ev_fold[1], &h->ev_main, &h->ev_side})
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(h->vac_part, 0, static_cast<size_t>(h->nparts_inner) * 12 * sizeof(double), h->stream);
-  if (e == cudaSuccess) launch_hot_start(h->fp64, h->theta, g, h->seed, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // lists are host temporaries
-  if (e == cudaSuccess) e = cudaGetLastError();
-  st = e == cudaSuccess ? ML_OK : ML_ECUDA;
-  if (!st) st = choose_sweep_mode(h);
-  if (!st) st = capture_graphs(h);
+  st = init_engine(&h->e, p, 1, alloc, cuda_stream);
   if (st) {
-    destroy_graphs(h);
-    destroy_streams(h);
-    free_all(h);
-    if (h->own_stream) cudaStreamDestroy(h->stream);
+    destroy_engine(&h->e);
     delete h;
     return st;
   }
@@ -644,124 +747,105 @@ int ml_create(const ml_params* p, const ml_allocator* alloc, void* cuda_stream, 
 
 int ml_destroy(ml_lattice* h) {
   if (!h) return ML_EINVAL;
-  if (h->side) cudaStreamSynchronize(h->side);
-  cudaStreamSynchronize(h->stream);
-  destroy_graphs(h);
-  destroy_streams(h);
-  free_all(h);
-  if (h->own_stream) cudaStreamDestroy(h->stream);
+  destroy_engine(&h->e);
   delete h;
   return ML_OK;
 }
 
 int ml_sync(ml_lattice* h) {
   if (!h) return ML_EINVAL;
-  return check_errors(h);
+  return check_errors(&h->e);
 }
 
 int ml_thermalize(ml_lattice* h, int n_sweeps) {
-  if (!h || n_sweeps < 0) return ML_EINVAL;
-  int st = ML_OK;
-  if (h->sweep_mode == ML_SWEEP_PERSISTENT)
-    st = enqueue_sweeps(h, n_sweeps, 0);
-  else
-    for (int i = 0; i < n_sweeps && !st; ++i) st = launch_graph(h, h->g_one_full);
-  if (st) return st;
-  h->h_n += static_cast<uint64_t>(n_sweeps);
-  return ML_OK;
+  if (!h) return ML_EINVAL;
+  return thermalize_engine(&h->e, n_sweeps);
 }
 
 int ml_compound_sweeps(ml_lattice* h, int n, int slab_d) {
   if (!h || n < 0 || slab_d < 0) return ML_EINVAL;
-  int st = enqueue_sweeps(h, n, slab_d);
-  if (st) return st;
-  h->h_n += static_cast<uint64_t>(n);
-  return ML_OK;
+  return enqueue_sweeps(&h->e, n, slab_d);
 }
 
 int ml_update_pass(ml_lattice* h, int mu, int parity, int slab_d, uint64_t n, int kind) {
   if (!h || mu < 0 || mu > 3 || parity < 0 || parity > 1 || slab_d < 0 || kind < 0 || kind > 1) return ML_EINVAL;
-  launch_update_pass(h->fp64, h->theta, h->g, mu, parity, slab_d, kind, nullptr, n, h->seed, h->beta, h->d_err,
-                     h->stream);
+  LatState* L = h->L();
+  launch_update_pass(h->e.fp64, L->theta, L->g, mu, parity, slab_d, kind, nullptr, n, L->seed, L->beta, h->e.d_err,
+                     h->e.stream);
   return cuda_status(cudaGetLastError());
 }
 
 int ml_measure_device(ml_lattice* h, int n_meas, double* out_dev, size_t out_len) {
   if (!h || n_meas < 0 || (n_meas > 0 && !out_dev)) return ML_EINVAL;
-  if (out_len < static_cast<size_t>(n_meas) * h->meas.rec_len) return ML_EINVAL;
-  return enqueue_measurements(h, n_meas, out_dev);
+  if (out_len < total_len(&h->e, n_meas)) return ML_EINVAL;
+  return enqueue_measurements(&h->e, n_meas, out_dev);
 }
 
 int ml_measure(ml_lattice* h, int n_meas, double* out_host, size_t out_len) {
-  if (!h || n_meas < 0 || (n_meas > 0 && !out_host)) return ML_EINVAL;
-  const size_t need = static_cast<size_t>(n_meas) * h->meas.rec_len;
-  if (out_len < need) return ML_EINVAL;
-  int st = ensure_rec(h, need);
-  if (st) return st;
-  st = enqueue_measurements(h, n_meas, h->rec_buf);
-  if (st) return st;
-  ML_CUDA(cudaMemcpyAsync(out_host, h->rec_buf, need * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  return check_errors(h);
+  if (!h) return ML_EINVAL;
+  return measure_host(&h->e, n_meas, out_host, out_len);
 }
 
 int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
-  if (!h || !out_host || out_len < static_cast<size_t>(h->meas.rec_len)) return ML_EINVAL;
-  int st = ensure_rec(h, h->meas.rec_len);
+  if (!h || !out_host) return ML_EINVAL;
+  Engine* e = &h->e;
+  LatState* L = h->L();
+  const MeasLayout& m = L->meas;
+  if (out_len < static_cast<size_t>(m.rec_len)) return ML_EINVAL;
+  int st = ensure_rec(e, m.rec_len);
   if (st) return st;
-  double* out = h->rec_buf;
-  const MeasLayout& m = h->meas;
-  ML_CUDA(cudaMemsetAsync(out, 0, m.rec_len * sizeof(double), h->stream));
-  launch_naive_and_plaquette(h->fp64, h->theta, h->g, m, h->partial_naive, out, h->stream);
-  ML_CUDA(cudaMemsetAsync(h->vac_acc, 0, 12 * sizeof(double), h->stream));
-  st = join(h->side, h->stream, h->ev_side);
-  if (!st) st = zero_inner(h, h->stream);
+  double* out = e->rec_buf;
+  st = join(e->side, e->stream, e->ev_side);
   if (st) return st;
-  const int buf = h->cur_buf;
-  ML_CUDA(cudaStreamWaitEvent(h->stream, h->ev_fold[buf], 0));
-  launch_record(h->fp64, h->theta, h->g, h->slab, m, 0, h->theta_rec[buf], h->osum[buf], h->vac_part, h->stream);
-  launch_vac_accumulate(h->vac_part, h->nparts_inner, h->vac_acc, 1.0 / h->g.V, h->stream);
-  enqueue_fold(h, buf, 1, h->stream);
-  launch_products(h->g, h->g.Nt / h->slab, m, h->accT, h->accO, 1.0, h->partial, out, h->stream);
-  launch_write_vac(h->vac_acc, 1.0, m, out, h->stream);
+  const int buf = e->cur_buf;
+  ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
+  ML_CUDA(cudaMemsetAsync(out, 0, m.rec_len * sizeof(double), e->stream));
+  launch_naive_and_plaquette(e->fp64, L->theta, L->g, m, L->partial_naive, out, e->stream);
+  ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->stream));
+  st = zero_inner(e, e->stream);
+  if (st) return st;
+  launch_record_table(e->fp64, e->d_desc, e->td, nullptr, buf, 0, e->stream);
+  launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream);
+  launch_products(L->g, L->g.Nt / e->slab, m, L->accT, L->accO, 1.0, L->partial, out, e->stream);
+  launch_write_vac(L->vac_acc, 1.0, m, out, e->stream);
   ML_CUDA(cudaGetLastError());
-  ML_CUDA(cudaMemcpyAsync(out_host, out, m.rec_len * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  return check_errors(h);
+  ML_CUDA(cudaMemcpyAsync(out_host, out, m.rec_len * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
+  return check_errors(e);
 }
 
 int ml_connected_device(ml_lattice* h, const double* records_dev, int n_meas, double* out_dev, size_t out_len) {
   if (!h || !records_dev || !out_dev || n_meas < 1) return ML_EINVAL;
-  if (out_len < static_cast<size_t>(h->meas.nrf) * h->meas.np * 12) return ML_EINVAL;
-  launch_connected(records_dev, n_meas, h->meas, h->beta, out_dev, h->stream);
+  LatState* L = h->L();
+  if (out_len < static_cast<size_t>(L->meas.nrf) * L->meas.np * 12) return ML_EINVAL;
+  launch_connected(records_dev, n_meas, L->meas, L->beta, out_dev, h->e.stream);
   return cuda_status(cudaGetLastError());
 }
 
 int ml_get_angles(ml_lattice* h, double* theta_host, size_t n) {
-  if (!h || !theta_host || n < 4ull * h->g.V) return ML_EINVAL;
-  if (!h->staging) {
-    h->staging = static_cast<double*>(dev_alloc(h, 4ull * h->g.V * sizeof(double)));
-    if (!h->staging) return ML_ENOMEM;
-  }
-  launch_angles_from_soa(h->fp64, h->theta, h->staging, h->g, h->stream);
-  ML_CUDA(cudaMemcpyAsync(theta_host, h->staging, 4ull * h->g.V * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  return check_errors(h);
+  if (!h) return ML_EINVAL;
+  return get_angles(&h->e, h->L(), theta_host, n);
 }
 
 int ml_set_angles(ml_lattice* h, const double* theta_host, size_t n) {
-  if (!h || !theta_host || n < 4ull * h->g.V) return ML_EINVAL;
-  if (!h->staging) {
-    h->staging = static_cast<double*>(dev_alloc(h, 4ull * h->g.V * sizeof(double)));
-    if (!h->staging) return ML_ENOMEM;
+  if (!h) return ML_EINVAL;
+  Engine* e = &h->e;
+  LatState* L = h->L();
+  if (!theta_host || n < 4ull * L->g.V) return ML_EINVAL;
+  if (!L->staging) {
+    L->staging = static_cast<double*>(lat_alloc(e, L, 4ull * L->g.V * sizeof(double)));
+    if (!L->staging) return ML_ENOMEM;
   }
-  ML_CUDA(cudaMemcpyAsync(h->staging, theta_host, 4ull * h->g.V * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-  launch_angles_to_soa(h->fp64, h->staging, h->theta, h->g, h->stream);
-  return check_errors(h);
+  ML_CUDA(cudaStreamSynchronize(e->side));
+  ML_CUDA(cudaMemcpyAsync(L->staging, theta_host, 4ull * L->g.V * sizeof(double), cudaMemcpyHostToDevice, e->stream));
+  launch_angles_to_soa(e->fp64, L->staging, L->theta, L->g, e->stream);
+  return check_errors(e);
 }
 
 int ml_get_sweep(ml_lattice* h, uint64_t* n) {
   if (!h || !n) return ML_EINVAL;
   unsigned long long v = 0;
-  ML_CUDA(cudaMemcpyAsync(&v, h->d_n, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
-  ML_CUDA(cudaStreamSynchronize(h->stream));
+  ML_CUDA(cudaMemcpyAsync(&v, h->L()->d_n, sizeof(v), cudaMemcpyDeviceToHost, h->e.stream));
+  ML_CUDA(cudaStreamSynchronize(h->e.stream));
   *n = v;
   return ML_OK;
 }
@@ -769,48 +853,62 @@ int ml_get_sweep(ml_lattice* h, uint64_t* n) {
 int ml_set_sweep(ml_lattice* h, uint64_t n) {
   if (!h) return ML_EINVAL;
   unsigned long long v = n;
-  ML_CUDA(cudaMemcpyAsync(h->d_n, &v, sizeof(v), cudaMemcpyHostToDevice, h->stream));
-  ML_CUDA(cudaStreamSynchronize(h->stream));
-  h->h_n = n;
+  ML_CUDA(cudaMemcpyAsync(h->L()->d_n, &v, sizeof(v), cudaMemcpyHostToDevice, h->e.stream));
+  ML_CUDA(cudaStreamSynchronize(h->e.stream));
+  return ML_OK;
+}
+
+int ml_sweep_mode(ml_lattice* h, int* mode) {
+  if (!h || !mode) return ML_EINVAL;
+  *mode = h->e.sweep_mode;
+  return ML_OK;
+}
+
+int ml_set_sweep_mode(ml_lattice* h, int mode) {
+  if (!h) return ML_EINVAL;
+  return set_sweep_mode(&h->e, mode);
+}
+
+int ml_batch_slots(ml_lattice* h, int* n) {
+  if (!h || !n) return ML_EINVAL;
+  *n = h->e.nB;
   return ML_OK;
 }
 
 int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   if (!h || !avg_ms || reps < 1 || kernel < ML_K_HEATBATH || kernel > ML_K_SWEEP) return ML_EINVAL;
-  const size_t tbytes = 4ull * h->g.V * (h->fp64 ? sizeof(double) : sizeof(float));
-  int st = ensure_scratch_theta(h);
-  if (!st) st = ensure_rec(h, h->meas.rec_len);
+  Engine* e = &h->e;
+  LatState* L = h->L();
+  int st = ensure_scratch(e);
+  if (!st) st = ensure_rec(e, L->meas.rec_len);
+  if (!st) st = join(e->side, e->stream, e->ev_side);
+  if (!st) st = refresh_scratch(e);
   if (st) return st;
-  st = join(h->side, h->stream, h->ev_side);
-  if (st) return st;
-  ML_CUDA(cudaMemcpyAsync(h->scratch_theta, h->theta, tbytes, cudaMemcpyDeviceToDevice, h->stream));
-  ML_CUDA(cudaMemcpyAsync(h->scratch_n, h->d_n, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, h->stream));
   cudaEvent_t e0, e1;
   ML_CUDA(cudaEventCreate(&e0));
   ML_CUDA(cudaEventCreate(&e1));
-  ML_CUDA(cudaEventRecord(e0, h->stream));
+  ML_CUDA(cudaEventRecord(e0, e->stream));
   for (int i = 0; i < reps && !st; ++i) {
     switch (kernel) {
       case ML_K_HEATBATH:
       case ML_K_OVERRELAX:
-        launch_update_pass(h->fp64, h->scratch_theta, h->g, 1, 0, h->slab, kernel == ML_K_HEATBATH ? 0 : 1, nullptr,
-                           h->h_n + 1, h->seed, h->beta, h->d_err, h->stream);
+        launch_update_pass(e->fp64, L->scratch_theta, L->g, 1, 0, e->slab, kernel == ML_K_HEATBATH ? 0 : 1, nullptr,
+                           1000000ull + i, L->seed, L->beta, e->d_err, e->stream);
         break;
       case ML_K_RECORD:
-        launch_record(h->fp64, h->theta, h->g, h->slab, h->meas, 0, h->theta_rec[0], h->osum[0], h->vac_part,
-                      h->stream);
+        launch_record_table(e->fp64, e->d_desc, e->td, nullptr, 0, 0, e->stream);
         break;
       case ML_K_ACCUMULATE:
-        enqueue_fold(h, 0, h->nB, h->stream);
+        launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, 0, e->nB, e->stream);
         break;
       case ML_K_PRODUCTS:
-        launch_products(h->g, h->g.Nt / h->slab, h->meas, h->accT, h->accO, 1.0, h->partial, h->rec_buf, h->stream);
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, L->accT, L->accO, 1.0, L->partial, e->rec_buf, e->stream);
         break;
       default:
-        st = enqueue_sweeps_on(h, h->sweep_mode, h->scratch_theta, h->scratch_n, 1, h->slab);
+        st = enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, e->sweep_mode);
     }
   }
-  ML_CUDA(cudaEventRecord(e1, h->stream));
+  ML_CUDA(cudaEventRecord(e1, e->stream));
   ML_CUDA(cudaEventSynchronize(e1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
@@ -818,33 +916,109 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   cudaEventDestroy(e1);
   *avg_ms = static_cast<double>(ms) / reps;
   if (st) return st;
-  return check_errors(h);
-}
-
-int ml_batch_slots(ml_lattice* h, int* n) {
-  if (!h || !n) return ML_EINVAL;
-  *n = h->nB;
-  return ML_OK;
+  return check_errors(e);
 }
 
 int ml_philox(const uint32_t* ctr, const uint32_t* key, size_t n, uint32_t* out) {
   if (!ctr || !key || !out) return ML_EINVAL;
   if (n == 0) return ML_OK;
   uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
-  cudaError_t e = cudaMalloc(&dc, n * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&dk, n * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&dout, n * 16);
-  if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, n * 16, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(dk, key, n * 8, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
+  cudaError_t ce = cudaMalloc(&dc, n * 16);
+  if (ce == cudaSuccess) ce = cudaMalloc(&dk, n * 8);
+  if (ce == cudaSuccess) ce = cudaMalloc(&dout, n * 16);
+  if (ce == cudaSuccess) ce = cudaMemcpy(dc, ctr, n * 16, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(dk, key, n * 8, cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) {
     launch_philox(dc, dk, dout, n, nullptr);
-    e = cudaGetLastError();
+    ce = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemcpy(out, dout, n * 16, cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess) ce = cudaMemcpy(out, dout, n * 16, cudaMemcpyDeviceToHost);
   cudaFree(dc);
   cudaFree(dk);
   cudaFree(dout);
-  return e == cudaSuccess ? ML_OK : ML_ECUDA;
+  return ce == cudaSuccess ? ML_OK : ML_ECUDA;
+}
+
+// --------------------------------------------------------------------------- batches
+int ml_batch_create(const ml_params* ps, int n, const ml_allocator* alloc, void* cuda_stream, ml_batch** out) {
+  if (!out || !ps || n < 1) return ML_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    int st = validate(&ps[i]);
+    if (st) return st;
+  }
+  ml_batch* b = new (std::nothrow) ml_batch();
+  if (!b) return ML_ENOMEM;
+  int st = init_engine(&b->e, ps, n, alloc, cuda_stream);
+  if (st) {
+    destroy_engine(&b->e);
+    delete b;
+    return st;
+  }
+  *out = b;
+  return ML_OK;
+}
+
+int ml_batch_destroy(ml_batch* b) {
+  if (!b) return ML_EINVAL;
+  destroy_engine(&b->e);
+  delete b;
+  return ML_OK;
+}
+
+int ml_batch_size(ml_batch* b, int* n) {
+  if (!b || !n) return ML_EINVAL;
+  *n = static_cast<int>(b->e.lats.size());
+  return ML_OK;
+}
+
+int ml_batch_thermalize(ml_batch* b, int n_sweeps) {
+  if (!b) return ML_EINVAL;
+  return thermalize_engine(&b->e, n_sweeps);
+}
+
+int ml_batch_result_len(ml_batch* b, int n_meas, size_t* len) {
+  if (!b || !len || n_meas < 0) return ML_EINVAL;
+  *len = total_len(&b->e, n_meas);
+  return ML_OK;
+}
+
+int ml_batch_record_offset(ml_batch* b, int lattice, int n_meas, size_t* offset) {
+  if (!b || !offset || n_meas < 0 || lattice < 0 || lattice >= static_cast<int>(b->e.lats.size())) return ML_EINVAL;
+  *offset = record_offset(&b->e, lattice, n_meas);
+  return ML_OK;
+}
+
+int ml_batch_measure(ml_batch* b, int n_meas, double* out_host, size_t out_len) {
+  if (!b) return ML_EINVAL;
+  return measure_host(&b->e, n_meas, out_host, out_len);
+}
+
+int ml_batch_measure_device(ml_batch* b, int n_meas, double* out_dev, size_t out_len) {
+  if (!b || n_meas < 0 || (n_meas > 0 && !out_dev)) return ML_EINVAL;
+  if (out_len < total_len(&b->e, n_meas)) return ML_EINVAL;
+  return enqueue_measurements(&b->e, n_meas, out_dev);
+}
+
+int ml_batch_get_angles(ml_batch* b, int lattice, double* theta_host, size_t n) {
+  if (!b || lattice < 0 || lattice >= static_cast<int>(b->e.lats.size())) return ML_EINVAL;
+  return get_angles(&b->e, b->e.lats[lattice], theta_host, n);
+}
+
+int ml_batch_sync(ml_batch* b) {
+  if (!b) return ML_EINVAL;
+  return check_errors(&b->e);
+}
+
+int ml_batch_sweep_mode(ml_batch* b, int* mode) {
+  if (!b || !mode) return ML_EINVAL;
+  *mode = b->e.sweep_mode;
+  return ML_OK;
+}
+
+int ml_batch_set_sweep_mode(ml_batch* b, int mode) {
+  if (!b) return ML_EINVAL;
+  return set_sweep_mode(&b->e, mode);
 }
 
 }  // extern "C"

@@ -1,0 +1,85 @@
+// Internal engine shared by the C ABI layer (ml_api.cu) and the request
+// server (ml_server.cu): per-lattice state, the lockstep schedule of a set of
+// lattices, and the helpers that build and run them.
+#pragma once
+
+#include <vector>
+
+#include "ml.h"
+#include "ml_internal.h"
+
+namespace ml {
+namespace eng {
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;
+};
+
+// One lattice: parameters, device buffers and its descriptor.
+struct LatState {
+  Geom g{};
+  double beta = 0.0;
+  uint64_t seed = 0;
+  std::vector<int> r, rf, pdy, pdz, comps, R, r_idx, rf_idx;
+  MeasLayout meas{};
+  void* theta = nullptr;
+  unsigned long long* d_n = nullptr;
+  int* d_lists = nullptr;
+  double2 *accT = nullptr, *accO = nullptr, *acc4T = nullptr, *acc4O = nullptr;
+  size_t accT_bytes = 0, accO_bytes = 0, acc4T_bytes = 0, acc4O_bytes = 0;
+  void* osum[2] = {nullptr, nullptr};       // record ring [nslab][nc][2][Ns][kBatch]
+  void* theta_rec[2] = {nullptr, nullptr};  // record ring [nslab][Ns][kBatch]
+  size_t osum_bytes = 0, trec_bytes = 0;
+  double* vac_part = nullptr;
+  int nparts = 0;
+  double* vac_acc = nullptr;
+  double2* partial = nullptr;        // product partials (accumulation stream)
+  double2* partial_naive = nullptr;  // naive / plaquette partials (main stream)
+  double* staging = nullptr;         // canonical angles for get / set
+  void* scratch_theta = nullptr;     // timing copies
+  unsigned long long* scratch_n = nullptr;
+  LatDesc desc{};
+  std::vector<void*> blocks;  // this lattice's device allocations
+};
+
+// A set of lattices advanced by one schedule (Algorithm 1 in lockstep).
+struct Engine {
+  bool fp64 = true;
+  int n_or = 3, slab = 2, outer_slab = 0, n_sub = 1, n_sub_outer = 0, k_between = 0;
+  std::vector<LatState*> lats;
+  cudaStream_t stream = nullptr, side = nullptr;
+  bool own_stream = false;
+  ml_allocator alloc{};
+  bool use_alloc = false;
+  std::vector<void*> blocks;
+  LatDesc* d_desc = nullptr;          // table
+  LatDesc* d_desc_scratch = nullptr;  // the same lattices on their timing copies
+  int* d_tile_lat = nullptr;
+  TableDims td{};
+  int* d_err = nullptr;
+  unsigned long long* bar = nullptr;  // grid-barrier counter of the persistent sweeps
+  int sweep_mode = ML_SWEEP_PERSISTENT;
+  int nB = kBatch, cur_buf = 0;
+  cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_fold[2] = {nullptr, nullptr};
+  cudaEvent_t ev_main = nullptr, ev_side = nullptr;
+  Graph g_full, g_outer, g_one_full, g_flush[2], g_sub[2][kBatch];
+  double* rec_buf = nullptr;
+  size_t rec_cap = 0;
+};
+
+int cuda_status(cudaError_t e);
+int validate(const ml_params* p);
+size_t record_len(int nr, int nrf, int np);
+// allocation through the engine's allocator (or cudaMalloc)
+void* raw_alloc(Engine* e, size_t bytes);
+void raw_free(Engine* e, void* p);
+void* dev_alloc(Engine* e, size_t bytes);  // owned by the engine
+// one lattice with all its buffers, hot-started on e->stream; *out is set
+// (and owned by the caller) even when the call fails
+int make_lattice(Engine* e, const ml_params* p, LatState** out);
+void free_lattice(Engine* e, LatState* L);
+int check_errors(Engine* e);
+
+}  // namespace eng
+}  // namespace ml

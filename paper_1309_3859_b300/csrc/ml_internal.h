@@ -24,42 +24,83 @@ struct MeasLayout {
   int off_P, off_Pf, off_W, off_vac, off_naive, off_plaq;
 };
 
+// Per-lattice descriptor read by the multi-lattice ("table") kernels.  A
+// table holds one or more lattices of one precision; one launch covers all of
+// them, each with its own geometry, coupling, seed and buffers.
+struct LatDesc {
+  Geom g;
+  MeasLayout m;
+  void* theta;                // angles, structure-of-arrays
+  unsigned long long* n_dev;  // heatbath sweep counter
+  uint32_t k0, k1;            // Philox key (seed)
+  double beta;
+  int slab, nslab;            // inner slab thickness d and Nt / d
+  int tile_start, tiles;      // sweep tiles of kSweepTile links
+  void* theta_rec[2];         // record ring buffers [nslab][Ns][kBatch]
+  void* osum[2];              // [nslab][nc][2][Ns][kBatch]
+  double2* accT;              // inner slab sums
+  double2* accO;
+  double* vac_part;           // [nparts][12] warp partials of the vacuum sums
+  int nparts;
+  double* vac_acc;            // [12]
+};
+
+// Per-lattice control of one step of the request-serving engine; schedules
+// that advance every lattice of a table in lockstep pass null and uniform
+// arguments instead.
+struct LatCtl {
+  int mask;    // slab thickness of this step's sweep (0: no frozen links)
+  int record;  // 1: record the configuration into slot `slot` of buffer `buf`
+  int buf, slot;
+  int fold;    // 1: fold slots 0 .. nrec-1 of buffer `fold_buf`
+  int fold_buf, nrec;
+};
+
+// Launch geometry of a table (maxima over its lattices).
+struct TableDims {
+  int nlat;
+  int total_tiles;
+  int max_blocks_rec;   // ceil(Ns * nslab / 256)
+  int max_nc1;          // nc + 1
+  int max_blocks_site;  // ceil(Ns / 256)
+  int max_y_T;          // nslab * nR
+  int max_y_O;          // nslab * nrf * probe groups
+};
+
+constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep kernels)
+
+// ---- multi-lattice kernels (ml_update.cu, ml_measure.cu) ----
+// n_compound compound sweeps of every lattice of the table (mask: slab
+// thickness, or per lattice from ctl), either in one cooperative persistent
+// launch with a grid barrier between passes (bar: monotonic counter) or as one
+// kernel per pass.  tile_lat[t] is the lattice of sweep tile t.  Returns 0 or
+// -1 when a launch fails.
+int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int* tile_lat, const TableDims& td,
+                        const LatCtl* ctl, int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
+                        cudaStream_t s);
+// record of each lattice's configuration into ring slot (buf, slot) and its
+// vacuum partials; then vac_acc += site means
+void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
+                         cudaStream_t s);
+// fold slots 0 .. nrec-1 of ring buffer buf into each lattice's slab sums
+void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
+                       cudaStream_t s);
+int record_blocks(const Geom& g, int d);
+int fold_probe_groups(int np);
+
 // ---- link updates (ml_update.cu) ----
 // kind: 0 heatbath, 1 overrelaxation.  The heatbath sweep number is *n_dev
 // when n_dev is not null, else n_fixed.
 void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parity, int slab_d, int kind,
                         const unsigned long long* n_dev, unsigned long long n_fixed, uint64_t seed, double beta,
                         int* err, cudaStream_t s);
-// n_compound compound sweeps in one cooperative launch (grid barrier between
-// passes on the monotonic counter *bar, zeroed once at creation).  Returns 0,
-// or -1 when the launch fails.
-int launch_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
-                  unsigned long long* n_dev, uint64_t seed, double beta, int* err, unsigned long long* bar,
-                  cudaStream_t s);
-// The same n_compound compound sweeps as one kernel per (direction, parity)
-// pass: *n_dev is incremented by a one-thread kernel before each compound
-// sweep and read by its heatbath passes.  Returns 0 or -1.
-int launch_pass_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
-                       unsigned long long* n_dev, uint64_t seed, double beta, int* err, cudaStream_t s);
 void launch_hot_start(bool fp64, void* theta, const Geom& g, uint64_t seed, cudaStream_t s);
 void launch_angles_to_soa(bool fp64, const double* canon, void* theta, const Geom& g, cudaStream_t s);
 void launch_angles_from_soa(bool fp64, const void* theta, double* canon, const Geom& g, cudaStream_t s);
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n, cudaStream_t s);
 
 // ---- measurement (ml_measure.cu) ----
-// Record of one sub-update configuration into ring slot `slot`: slab phase
-// sums theta_rec[s][x][kBatch] and plaquette slab sums
-// osum[s][ci][k][x][kBatch] (slabs of thickness d), plus warp partials of the
-// site sums of Re/Im P_c for the vacuum.
-void launch_record(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, int slot,
-                   void* theta_rec, void* osum, double* vac_part, cudaStream_t s);
 int vac_part_count(const Geom& g, int d);
-void launch_vac_accumulate(const double* vac_part, int nparts, double* vac_acc, double scale, cudaStream_t s);
-// Fold ring slots 0 .. nrec-1 (nrec <= kBatch) into the slab sums:
-// accT[s][iR][x] += sum_j T_j(x, s, R); accO[s][f][b][ci][k][x] += sum_j
-// T_j(x, s, rf) O_j[s][ci][k](x0)
-void launch_accumulate_batch(bool fp64, const Geom& g, int d, const MeasLayout& m, const void* theta_rec,
-                             const void* osum, int nrec, double2* accT, double2* accO, cudaStream_t s);
 // two-level combination of inner averages (sum / n_inner) into outer sums
 void launch_combine(const Geom& g, int n_inner_slabs, int q, const MeasLayout& m, const double2* accT,
                     const double2* accO, double inv_n, double2* acc4T, double2* acc4O, cudaStream_t s);

@@ -95,16 +95,26 @@ __device__ __forceinline__ void load_batch(const T* __restrict__ p, T v[kBatch])
   }
 }
 
-// Record of one configuration into ring slot `slot`; grid (sites x slabs,
-// nc + 1): blockIdx.y < nc handles component ci = blockIdx.y, blockIdx.y = nc
-// the slab phase sums.  Component blocks also write warp partials of the site
-// sums of Re / Im P_c (vac_part[warp][c][k]; entries of unselected components
-// stay zero).
+// Record of each lattice's configuration into ring slot `slot` of buffer
+// `buf`; grid (sites x slabs, nc + 1, lattices): blockIdx.y < nc handles
+// component ci = blockIdx.y, blockIdx.y = nc the slab phase sums.  Component
+// blocks also write warp partials of the site sums of Re / Im P_c
+// (vac_part[warp][c][k]; entries of unselected components stay zero).
 template <typename T>
-__global__ void __launch_bounds__(256) k_record(const T* __restrict__ th, Geom g, int d, int nslab, int nc,
-                                                const int* __restrict__ comp, int slot, T* __restrict__ theta_rec,
-                                                T* __restrict__ osum, double* __restrict__ vac_part) {
+__global__ void __launch_bounds__(256) k_record_table(const LatDesc* __restrict__ desc,
+                                                      const LatCtl* __restrict__ ctl, int buf, int slot) {
   using P = Prec<T>;
+  const int li = blockIdx.z;
+  if (ctl) {
+    if (!ctl[li].record) return;
+    buf = ctl[li].buf;
+    slot = ctl[li].slot;
+  }
+  const LatDesc& L = desc[li];
+  const Geom g = L.g;
+  const int d = L.slab, nslab = L.nslab, nc = L.m.nc;
+  if (blockIdx.x * blockDim.x >= g.Ns * nslab || static_cast<int>(blockIdx.y) > nc) return;  // whole block
+  const T* __restrict__ th = static_cast<const T*>(L.theta);
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = idx < g.Ns * nslab;
   const int s = live ? idx / g.Ns : 0;
@@ -116,12 +126,12 @@ __global__ void __launch_bounds__(256) k_record(const T* __restrict__ th, Geom g
     if (live) {
       double tsum = 0.0;
       for (int t = s * d; t < s * d + d; ++t) tsum += theta0(th, g, c[1], c[2], c[3], t);
-      theta_rec[(static_cast<size_t>(s) * g.Ns + x) * kBatch + slot] =
+      static_cast<T*>(L.theta_rec[buf])[(static_cast<size_t>(s) * g.Ns + x) * kBatch + slot] =
           static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
     }
     return;  // the whole block takes this branch
   }
-  const int cc = comp[ci];
+  const int cc = L.m.comp[ci];
   const int mu = c_plane_mu[cc], nu = c_plane_nu[cc];
   T re = T(0), im = T(0);
   if (live) {
@@ -132,6 +142,7 @@ __global__ void __launch_bounds__(256) k_record(const T* __restrict__ th, Geom g
       re += cs;
       im += sn;
     }
+    T* osum = static_cast<T*>(L.osum[buf]);
     osum[((static_cast<size_t>(s * nc + ci) * 2 + 0) * g.Ns + x) * kBatch + slot] = re;
     osum[((static_cast<size_t>(s * nc + ci) * 2 + 1) * g.Ns + x) * kBatch + slot] = im;
   }
@@ -139,25 +150,28 @@ __global__ void __launch_bounds__(256) k_record(const T* __restrict__ th, Geom g
   const double vi = warp_sum(static_cast<double>(im));
   if ((threadIdx.x & 31) == 0) {
     const size_t w = idx >> 5;
-    vac_part[w * 12 + 2 * cc] = vr;
-    vac_part[w * 12 + 2 * cc + 1] = vi;
+    L.vac_part[w * 12 + 2 * cc] = vr;
+    L.vac_part[w * 12 + 2 * cc + 1] = vi;
   }
 }
 
-// vac_acc[j] += scale * sum_w vac_part[w][j], fixed order (one block per j)
-__global__ void __launch_bounds__(256) k_vac_accumulate(const double* __restrict__ part, int nparts,
-                                                        double* __restrict__ acc, double scale) {
+// vac_acc[j] += (1/V) sum_w vac_part[w][j] in a fixed order; grid (12, lattices)
+__global__ void __launch_bounds__(256) k_vac_accumulate_table(const LatDesc* __restrict__ desc,
+                                                              const LatCtl* __restrict__ ctl) {
   __shared__ double sh[8];
+  const int li = blockIdx.y;
+  if (ctl && !ctl[li].record) return;
+  const LatDesc& L = desc[li];
   const int j = blockIdx.x;
   double v = 0.0;
-  for (int w = threadIdx.x; w < nparts; w += blockDim.x) v += part[static_cast<size_t>(w) * 12 + j];
+  for (int w = threadIdx.x; w < L.nparts; w += blockDim.x) v += L.vac_part[static_cast<size_t>(w) * 12 + j];
   v = warp_sum(v);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    acc[j] += s * scale;
+    L.vac_acc[j] += s * (1.0 / L.g.V);
   }
 }
 
@@ -184,15 +198,24 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 // so each accumulator is read and written once per batch.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_accum_T(Geom g, MeasLayout m, const T* __restrict__ theta_rec, int nrec,
-                                                 double2* __restrict__ accT) {
+__global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict__ desc,
+                                                       const LatCtl* __restrict__ ctl, int buf, int nrec) {
+  const int li = blockIdx.z;
+  if (ctl) {
+    if (!ctl[li].fold) return;
+    buf = ctl[li].fold_buf;
+    nrec = ctl[li].nrec;
+  }
+  const LatDesc& L = desc[li];
+  const Geom g = L.g;
+  const MeasLayout& m = L.m;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= g.Ns) return;
+  if (x >= g.Ns || static_cast<int>(blockIdx.y) >= L.nslab * m.nR) return;
   const int s = blockIdx.y / m.nR, a = blockIdx.y - s * m.nR;
   int cx, cy, cz;
   spatial_coords(g, x, &cx, &cy, &cz);
   const int xr = wrapc(cx + m.R[a], g.L) + g.L * (cy + g.L * cz);
-  const T* rec = theta_rec + static_cast<size_t>(s) * g.Ns * kBatch;
+  const T* rec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * kBatch;
   T er[kBatch], ei[kBatch];
   batch_phases<T>(rec + static_cast<size_t>(x) * kBatch, rec + static_cast<size_t>(xr) * kBatch, nrec, er, ei);
   T sr = T(0), si = T(0);
@@ -201,18 +224,28 @@ __global__ void __launch_bounds__(256) k_accum_T(Geom g, MeasLayout m, const T* 
     sr += er[j];
     si += ei[j];
   }
-  double2* p = accT + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
+  double2* p = L.accT + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
   *p = make_double2(p->x + static_cast<double>(sr), p->y + static_cast<double>(si));
 }
 
 constexpr int kProbesPerThread = 3;
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_accum_O(Geom g, MeasLayout m, const T* __restrict__ theta_rec,
-                                                 const T* __restrict__ osum, int nrec, double2* __restrict__ accO) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= g.Ns) return;
+__global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict__ desc,
+                                                       const LatCtl* __restrict__ ctl, int buf, int nrec) {
+  const int li = blockIdx.z;
+  if (ctl) {
+    if (!ctl[li].fold) return;
+    buf = ctl[li].fold_buf;
+    nrec = ctl[li].nrec;
+  }
+  const LatDesc& L = desc[li];
+  const Geom g = L.g;
+  const MeasLayout& m = L.m;
   const int nbg = (m.np + kProbesPerThread - 1) / kProbesPerThread;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.Ns || m.nrf == 0 || nbg == 0 || m.nc == 0 || static_cast<int>(blockIdx.y) >= L.nslab * m.nrf * nbg)
+    return;
   const int bg = blockIdx.y % nbg;
   const int sf = blockIdx.y / nbg;
   const int s = sf / m.nrf, f = sf - s * m.nrf;
@@ -220,7 +253,8 @@ __global__ void __launch_bounds__(256) k_accum_O(Geom g, MeasLayout m, const T* 
   spatial_coords(g, x, &cx, &cy, &cz);
   const int rf = m.rf[f];
   const int xr = wrapc(cx + rf, g.L) + g.L * (cy + g.L * cz);
-  const T* trec = theta_rec + static_cast<size_t>(s) * g.Ns * kBatch;
+  const T* trec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * kBatch;
+  const T* osum = static_cast<const T*>(L.osum[buf]);
   T er[kBatch], ei[kBatch];
   batch_phases<T>(trec + static_cast<size_t>(x) * kBatch, trec + static_cast<size_t>(xr) * kBatch, nrec, er, ei);
   const int x0x = wrapc(cx + rf / 2, g.L);
@@ -238,7 +272,7 @@ __global__ void __launch_bounds__(256) k_accum_O(Geom g, MeasLayout m, const T* 
           sr += er[j] * o[j];
           si += ei[j] * o[j];
         }
-        double2* p = accO + ((((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
+        double2* p = L.accO + ((((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
         *p = make_double2(p->x + static_cast<double>(sr), p->y + static_cast<double>(si));
       }
     }
@@ -491,49 +525,39 @@ __global__ void k_connected(const double* __restrict__ recs, int n_meas, MeasLay
 }
 
 // ---------------------------------------------------------------------------
-int vac_part_count(const Geom& g, int d) {
-  const int nslab = g.Nt / d;
-  return blocks_for(static_cast<long long>(g.Ns) * nslab, 256) * 8;
-}
+int vac_part_count(const Geom& g, int d) { return record_blocks(g, d) * 8; }
 
 int product_partial_count(const Geom& g) { return blocks_for(g.Ns, 256) * 8; }
 
-void launch_record(bool fp64, const void* theta, const Geom& g, int d, const MeasLayout& m, int slot,
-                   void* theta_rec, void* osum, double* vac_part, cudaStream_t s) {
-  const int nslab = g.Nt / d;
-  const dim3 grid(blocks_for(static_cast<long long>(g.Ns) * nslab, 256), m.nc + 1);
+int record_blocks(const Geom& g, int d) { return blocks_for(static_cast<long long>(g.Ns) * (g.Nt / d), 256); }
+
+int fold_probe_groups(int np) { return (np + kProbesPerThread - 1) / kProbesPerThread; }
+
+void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
+                         cudaStream_t s) {
+  const dim3 grid(td.max_blocks_rec, td.max_nc1, td.nlat);
   if (fp64)
-    k_record<double><<<grid, 256, 0, s>>>(static_cast<const double*>(theta), g, d, nslab, m.nc, m.comp, slot,
-                                          static_cast<double*>(theta_rec), static_cast<double*>(osum), vac_part);
+    k_record_table<double><<<grid, 256, 0, s>>>(d, ctl, buf, slot);
   else
-    k_record<float><<<grid, 256, 0, s>>>(static_cast<const float*>(theta), g, d, nslab, m.nc, m.comp, slot,
-                                         static_cast<float*>(theta_rec), static_cast<float*>(osum), vac_part);
-  count_launches(1);
+    k_record_table<float><<<grid, 256, 0, s>>>(d, ctl, buf, slot);
+  k_vac_accumulate_table<<<dim3(12, td.nlat), 256, 0, s>>>(d, ctl);
+  count_launches(2);
 }
 
-void launch_vac_accumulate(const double* vac_part, int nparts, double* vac_acc, double scale, cudaStream_t s) {
-  k_vac_accumulate<<<12, 256, 0, s>>>(vac_part, nparts, vac_acc, scale);
-  count_launches(1);
-}
-
-void launch_accumulate_batch(bool fp64, const Geom& g, int d, const MeasLayout& m, const void* theta_rec,
-                             const void* osum, int nrec, double2* accT, double2* accO, cudaStream_t s) {
-  const int nslab = g.Nt / d;
-  const dim3 gt(blocks_for(g.Ns, 256), nslab * m.nR);
+void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
+                       cudaStream_t s) {
+  const dim3 gt(td.max_blocks_site, td.max_y_T, td.nlat);
   if (fp64)
-    k_accum_T<double><<<gt, 256, 0, s>>>(g, m, static_cast<const double*>(theta_rec), nrec, accT);
+    k_accum_T_table<double><<<gt, 256, 0, s>>>(d, ctl, buf, nrec);
   else
-    k_accum_T<float><<<gt, 256, 0, s>>>(g, m, static_cast<const float*>(theta_rec), nrec, accT);
+    k_accum_T_table<float><<<gt, 256, 0, s>>>(d, ctl, buf, nrec);
   count_launches(1);
-  if (m.nrf > 0 && m.np > 0 && m.nc > 0) {
-    const int nbg = (m.np + kProbesPerThread - 1) / kProbesPerThread;
-    const dim3 go(blocks_for(g.Ns, 256), nslab * m.nrf * nbg);
+  if (td.max_y_O > 0) {
+    const dim3 go(td.max_blocks_site, td.max_y_O, td.nlat);
     if (fp64)
-      k_accum_O<double><<<go, 256, 0, s>>>(g, m, static_cast<const double*>(theta_rec),
-                                           static_cast<const double*>(osum), nrec, accO);
+      k_accum_O_table<double><<<go, 256, 0, s>>>(d, ctl, buf, nrec);
     else
-      k_accum_O<float><<<go, 256, 0, s>>>(g, m, static_cast<const float*>(theta_rec), static_cast<const float*>(osum),
-                                          nrec, accO);
+      k_accum_O_table<float><<<go, 256, 0, s>>>(d, ctl, buf, nrec);
     count_launches(1);
   }
 }

@@ -110,7 +110,7 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
   }
 }
 
-constexpr int kSweepThreads = 384;  // block size of the persistent sweep kernel
+constexpr int kSweepThreads = kSweepTile;  // block size of the sweep kernels
 
 // Site index of the neighbour one step along direction mu (sign +1 or -1)
 // of the site with index i and coordinates c = (t, x, y, z).  No division:
@@ -230,34 +230,93 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* count, int* err
 }
 
 // n_compound compound sweeps (heatbath + n_or overrelaxation sweeps, each
-// sweep mu = 0..3 x parity even, odd) in one cooperative launch, with a grid
-// barrier between passes.  The heatbath sweep numbers are *n_dev + 1 ..
-// *n_dev + n_compound; block 0 stores the last one at the end.
+// sweep mu = 0..3 x parity even, odd) of every lattice of a table in one
+// cooperative launch, with a grid barrier between passes.  Lattice i's
+// heatbath sweep numbers are *n_dev + 1 .. *n_dev + n_compound; block 0
+// advances the counters after the last barrier, when every block has read
+// them.
 template <typename T>
-__global__ void __launch_bounds__(kSweepThreads) k_sweeps(T* th, Geom g, int slab_d, int n_or, int n_compound,
-                                                          unsigned long long* __restrict__ n_dev, uint32_t k0,
-                                                          uint32_t k1, T beta, int* __restrict__ err,
-                                                          unsigned long long* __restrict__ bar) {
-  const unsigned long long base = *n_dev;
-  const int stride = gridDim.x * blockDim.x;
-  for (int s = 0; s < n_compound; ++s) {
-    const unsigned long long n = base + 1 + s;
+__global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* __restrict__ d,
+                                                                const int* __restrict__ tile_lat, int total_tiles,
+                                                                int nlat, const LatCtl* __restrict__ ctl, int mask,
+                                                                int n_or, int n_compound, int* __restrict__ err,
+                                                                unsigned long long* __restrict__ bar) {
+  // When every tile has its own block (the latency-bound case), the block's
+  // lattice parameters are read once into registers: the barrier's acquire
+  // fence would otherwise send each pass's descriptor loads back to L2.
+  const bool one_tile = total_tiles <= static_cast<int>(gridDim.x);
+  T* c_theta = nullptr;
+  Geom c_g{};
+  int c_h = 0, c_mask = 0;
+  uint32_t c_k0 = 0, c_k1 = 0;
+  T c_beta = T(0);
+  unsigned long long c_base = 0;
+  if (one_tile && static_cast<int>(blockIdx.x) < total_tiles) {
+    const int i = tile_lat[blockIdx.x];
+    const LatDesc& L = d[i];
+    c_theta = static_cast<T*>(L.theta);
+    c_g = L.g;
+    c_h = (static_cast<int>(blockIdx.x) - L.tile_start) * kSweepTile + threadIdx.x;
+    c_mask = ctl ? ctl[i].mask : mask;
+    c_k0 = L.k0;
+    c_k1 = L.k1;
+    c_beta = static_cast<T>(L.beta);
+    c_base = *L.n_dev;
+  }
+  for (int c = 0; c < n_compound; ++c) {
     for (int sweep = 0; sweep <= n_or; ++sweep)
       for (int mu = 0; mu < 4; ++mu)
         for (int par = 0; par < 2; ++par) {
-          for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < g.Vh; h += stride) {
-            if (sweep == 0)
-              update_link<T, 0>(th, g, mu, par, slab_d, h, n, k0, k1, beta, err);
-            else
-              update_link<T, 1>(th, g, mu, par, slab_d, h, n, k0, k1, beta, err);
+          if (one_tile) {
+            if (c_theta && c_h < c_g.Vh) {
+              if (sweep == 0)
+                update_link<T, 0>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err);
+              else
+                update_link<T, 1>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err);
+            }
+          } else {
+            for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+              const int i = tile_lat[t];
+              const LatDesc& L = d[i];
+              const int h = (t - L.tile_start) * kSweepTile + threadIdx.x;
+              if (h >= L.g.Vh) continue;
+              const int md = ctl ? ctl[i].mask : mask;
+              const unsigned long long n = *L.n_dev + 1 + c;
+              if (sweep == 0)
+                update_link<T, 0>(static_cast<T*>(L.theta), L.g, mu, par, md, h, n, L.k0, L.k1,
+                                  static_cast<T>(L.beta), err);
+              else
+                update_link<T, 1>(static_cast<T*>(L.theta), L.g, mu, par, md, h, n, L.k0, L.k1,
+                                  static_cast<T>(L.beta), err);
+            }
           }
           if (!grid_barrier(bar, err)) return;
         }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *n_dev = base + n_compound;
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nlat; i += blockDim.x) *d[i].n_dev += n_compound;
 }
 
-// Hot start theta = -pi + 2 pi u, u = 52-bit uniform of block (i, mu, 0, 0).
+// One (mu, parity) pass of every lattice of a table, one tile per block; the
+// heatbath sweep number is *n_dev (advanced by k_sweep_begin_table).
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kSweepThreads) k_pass_table(const LatDesc* __restrict__ d,
+                                                              const int* __restrict__ tile_lat,
+                                                              const LatCtl* __restrict__ ctl, int mask, int mu,
+                                                              int parity, int* __restrict__ err) {
+  const int i = tile_lat[blockIdx.x];
+  const LatDesc& L = d[i];
+  const int h = (blockIdx.x - L.tile_start) * kSweepTile + threadIdx.x;
+  if (h >= L.g.Vh) return;
+  const int md = ctl ? ctl[i].mask : mask;
+  update_link<T, KIND>(static_cast<T*>(L.theta), L.g, mu, parity, md, h, *L.n_dev, L.k0, L.k1,
+                       static_cast<T>(L.beta), err);
+}
+
+__global__ void k_sweep_begin_table(const LatDesc* __restrict__ d, int nlat) {
+  for (int i = threadIdx.x; i < nlat; i += blockDim.x) *d[i].n_dev += 1ull;
+}
+
 template <typename T>
 __global__ void k_hot_start(T* __restrict__ th, Geom g, uint32_t k0, uint32_t k1) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -338,30 +397,29 @@ void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parit
   count_launches(1);
 }
 
-// Persistent sweep grid: one link per thread per pass when the pass fits the
+// Persistent sweep grid: one tile per block per pass when the table fits the
 // co-resident grid, else a grid-stride loop over the co-resident grid.
 template <typename T>
-static int sweeps_grid(const Geom& g) {
+static int sweeps_grid(int total_tiles) {
   static int cached[2] = {0, 0};
   int& blocks_per_sm = cached[sizeof(T) == 8 ? 1 : 0];
   if (!blocks_per_sm) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_sweeps<T>, kSweepThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_sweeps_table<T>, kSweepThreads, 0);
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int need = blocks_for(g.Vh, kSweepThreads);
   const int cap = blocks_per_sm * sms;
-  return need < cap ? need : cap;
+  return total_tiles < cap ? total_tiles : cap;
 }
 
 template <typename T>
-static cudaError_t launch_sweeps_t(void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
-                                   unsigned long long* n_dev, uint64_t seed, double beta, int* err,
-                                   unsigned long long* bar, cudaStream_t s) {
+static cudaError_t launch_sweeps_table_t(const LatDesc* d, const int* tile_lat, const TableDims& td, const LatCtl* ctl,
+                                         int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
+                                         cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(sweeps_grid<T>(g));
+  cfg.gridDim = dim3(sweeps_grid<T>(td.total_tiles));
   cfg.blockDim = dim3(kSweepThreads);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -369,35 +427,45 @@ static cudaError_t launch_sweeps_t(void* theta, const Geom& g, int slab_d, int n
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_sweeps<T>, static_cast<T*>(theta), g, slab_d, n_or, n_compound, n_dev,
-                            static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), static_cast<T>(beta), err,
-                            bar);
+  return cudaLaunchKernelEx(&cfg, k_sweeps_table<T>, d, tile_lat, td.total_tiles, td.nlat, ctl, mask, n_or,
+                            n_compound, err, bar);
 }
 
-int launch_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
-                  unsigned long long* n_dev, uint64_t seed, double beta, int* err, unsigned long long* bar,
-                  cudaStream_t s) {
-  if (n_compound <= 0) return 0;
-  cudaError_t e = fp64 ? launch_sweeps_t<double>(theta, g, slab_d, n_or, n_compound, n_dev, seed, beta, err, bar, s)
-                       : launch_sweeps_t<float>(theta, g, slab_d, n_or, n_compound, n_dev, seed, beta, err, bar, s);
-  count_launches(1);
-  return e == cudaSuccess ? 0 : -1;
-}
-
-
-__global__ void k_sweep_begin(unsigned long long* n) { *n += 1ull; }
-
-int launch_pass_sweeps(bool fp64, void* theta, const Geom& g, int slab_d, int n_or, int n_compound,
-                       unsigned long long* n_dev, uint64_t seed, double beta, int* err, cudaStream_t s) {
+template <typename T>
+static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const TableDims& td, const LatCtl* ctl,
+                                  int mask, int n_or, int n_compound, int* err, cudaStream_t s) {
   for (int c = 0; c < n_compound; ++c) {
-    k_sweep_begin<<<1, 1, 0, s>>>(n_dev);
+    k_sweep_begin_table<<<1, 128, 0, s>>>(d, td.nlat);
     count_launches(1);
     for (int sweep = 0; sweep <= n_or; ++sweep)
       for (int mu = 0; mu < 4; ++mu)
-        for (int par = 0; par < 2; ++par)
-          launch_update_pass(fp64, theta, g, mu, par, slab_d, sweep == 0 ? 0 : 1, n_dev, 0, seed, beta, err, s);
+        for (int par = 0; par < 2; ++par) {
+          if (sweep == 0)
+            k_pass_table<T, 0><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
+          else
+            k_pass_table<T, 1><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
+          count_launches(1);
+        }
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int* tile_lat, const TableDims& td,
+                        const LatCtl* ctl, int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
+                        cudaStream_t s) {
+  if (n_compound <= 0 || td.total_tiles <= 0) return 0;
+  cudaError_t e = cudaSuccess;
+  if (persistent) {
+    e = fp64 ? launch_sweeps_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, bar, s)
+             : launch_sweeps_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, bar, s);
+    count_launches(1);
+  } else {
+    if (fp64)
+      launch_passes_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s);
+    else
+      launch_passes_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? 0 : -1;
 }
 
 void launch_hot_start(bool fp64, void* theta, const Geom& g, uint64_t seed, cudaStream_t s) {

@@ -85,6 +85,19 @@ SIGNATURES = {
     "ml_naive_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
+    "ml_batch_create": (ctypes.c_int, [ctypes.POINTER(_Params), ctypes.c_int, ctypes.POINTER(_Allocator),
+                                       ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "ml_batch_destroy": (ctypes.c_int, [_H]),
+    "ml_batch_size": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
+    "ml_batch_thermalize": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ml_batch_result_len": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "ml_batch_record_offset": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "ml_batch_measure": (ctypes.c_int, [_H, ctypes.c_int, _D, ctypes.c_size_t]),
+    "ml_batch_measure_device": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]),
+    "ml_batch_get_angles": (ctypes.c_int, [_H, ctypes.c_int, _D, ctypes.c_size_t]),
+    "ml_batch_sync": (ctypes.c_int, [_H]),
+    "ml_batch_sweep_mode": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
+    "ml_batch_set_sweep_mode": (ctypes.c_int, [_H, ctypes.c_int]),
     "ml_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ml_kernel_launches": (ctypes.c_uint64, []),
 }
@@ -212,16 +225,8 @@ class Lattice:
         self._torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
-        dev, st = self.device, self.stream
-
-        def _alloc(size, ctx):
-            return torch.cuda.caching_allocator_alloc(int(size), dev, st)
-
-        def _free(ptr, ctx):
-            torch.cuda.caching_allocator_delete(int(ptr))
-
-        self._cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
-        self._alloc = _Allocator(self._cb[0], self._cb[1], None)
+        self._cb, self._alloc = _torch_allocator(torch, self.device, self.stream)
+        st = self.stream
         self._cp = p.c()
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
@@ -336,3 +341,112 @@ class Lattice:
 
     def sync(self):
         _check(lib().ml_sync(self.h), "ml_sync")
+
+
+def _torch_allocator(torch, dev, st):
+    def _alloc(size, ctx):
+        return torch.cuda.caching_allocator_alloc(int(size), dev, st)
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    return cb, _Allocator(cb[0], cb[1], None)
+
+
+class Batch:
+    """Independent lattices advanced together (``ml_batch_*``).
+
+    All parameter sets must share one schedule (precision, n_or, slab,
+    outer_slab, n_sub, n_sub_outer, k_between)."""
+
+    def __init__(self, params, stream=None, device=None):
+        import torch
+
+        self.params = list(params)
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        self._cb, self._alloc = _torch_allocator(torch, self.device, self.stream)
+        arr = (_Params * len(self.params))(*[p.c() for p in self.params])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().ml_batch_create(arr, len(self.params), ctypes.byref(self._alloc),
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "ml_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().ml_batch_destroy(self.h), "ml_batch_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.params)
+
+    def thermalize(self, n: int):
+        _check(lib().ml_batch_thermalize(self.h, int(n)), "ml_batch_thermalize")
+
+    def result_len(self, n_meas: int) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ml_batch_result_len(self.h, int(n_meas), ctypes.byref(n)), "ml_batch_result_len")
+        return n.value
+
+    def offsets(self, n_meas: int):
+        out = []
+        for i in range(len(self.params)):
+            o = ctypes.c_size_t()
+            _check(lib().ml_batch_record_offset(self.h, i, int(n_meas), ctypes.byref(o)), "ml_batch_record_offset")
+            out.append(o.value)
+        return out
+
+    def split(self, flat: np.ndarray, n_meas: int):
+        """Per-lattice record arrays [n_meas][record_len] from a batch output."""
+        offs = self.offsets(n_meas) + [flat.shape[-1]]
+        return [flat[..., offs[i]:offs[i + 1]].reshape(flat.shape[:-1] + (n_meas, -1))
+                for i in range(len(self.params))]
+
+    def measure(self, n_meas: int):
+        flat = np.zeros(self.result_len(n_meas), dtype=np.float64)
+        _check(lib().ml_batch_measure(self.h, int(n_meas), flat.ctypes.data_as(_D), flat.size), "ml_batch_measure")
+        return self.split(flat, n_meas)
+
+    def measure_device(self, n_meas: int, out=None):
+        torch = self._torch
+        if out is None:
+            with torch.cuda.stream(self.stream):
+                out = torch.empty(self.result_len(n_meas), dtype=torch.float64, device=self.device)
+        _check(lib().ml_batch_measure_device(self.h, int(n_meas), ctypes.c_void_p(out.data_ptr()), out.numel()),
+               "ml_batch_measure_device")
+        return out
+
+    def get_angles(self, i: int) -> np.ndarray:
+        p = self.params[i]
+        out = np.empty((4, p.V), dtype=np.float64)
+        _check(lib().ml_batch_get_angles(self.h, int(i), out.ctypes.data_as(_D), out.size), "ml_batch_get_angles")
+        return out
+
+    @property
+    def sweep_mode(self) -> int:
+        m = ctypes.c_int()
+        _check(lib().ml_batch_sweep_mode(self.h, ctypes.byref(m)), "ml_batch_sweep_mode")
+        return m.value
+
+    @sweep_mode.setter
+    def sweep_mode(self, mode: int):
+        _check(lib().ml_batch_set_sweep_mode(self.h, int(mode)), "ml_batch_set_sweep_mode")
+
+    def sync(self):
+        _check(lib().ml_batch_sync(self.h), "ml_batch_sync")
