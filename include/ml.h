@@ -256,6 +256,57 @@ int ml_batch_sweep_mode(ml_batch *b, int *mode);
 int ml_batch_set_sweep_mode(ml_batch *b, int mode);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: measurement requests with continuous batching                     */
+/* ------------------------------------------------------------------------ */
+
+/* A server owns one device allocation of budget_bytes (the HBM budget) and a
+ * worker thread.  Requests (one lattice each: create, n_therm thermalisation
+ * sweeps, n_meas measurements) are admitted first-in first-out whenever their
+ * memory fits the budget and fewer than max_active (0: 1024) are running.
+ * All admitted lattices advance together: each worker tick is one compound
+ * sweep of every lattice in one launch (each with the slab mask of its own
+ * phase), one record and one fold launch over the lattices that need them,
+ * and the per-lattice steps of Algorithm 1.  Requests that arrive while others
+ * run join at the next tick; finished ones leave and free their memory.  Each
+ * request's records are identical to the same parameters run with ml_create.
+ * All requests of a server share prec and n_or. */
+typedef struct {
+  int prec;            /* ml_precision of every request                      */
+  int n_or;            /* overrelaxation sweeps per heatbath sweep           */
+  size_t budget_bytes; /* device memory for all resident requests (>= 1 MiB) */
+  int max_active;      /* bound on simultaneously resident requests (0: 1024) */
+} ml_server_config;
+
+typedef struct {
+  int queued, active;
+  uint64_t completed, failed, ticks;
+  size_t budget_bytes, used_bytes;
+} ml_server_info;
+
+typedef struct ml_server ml_server;
+/* Allocates the budget (cudaMalloc, current device) and starts the worker. */
+int ml_server_create(const ml_server_config *cfg, ml_server **out);
+/* Queues a request (parameters are copied); *job identifies it.  ML_EINVAL
+ * for invalid parameters or a precision / n_or different from the server's.
+ * A request that cannot fit the budget even alone completes with ML_ENOMEM. */
+int ml_submit(ml_server *s, const ml_params *p, int n_therm, int n_meas, uint64_t *job);
+/* Non-blocking: *done = 1 once the request has finished.  When done and
+ * out_host is not NULL, copies its n_meas records (ml_record_len layout).
+ * Returns the request's status (ML_OK, or the error that ended it). */
+int ml_poll(ml_server *s, uint64_t job, int *done, double *out_host, size_t out_len);
+/* Blocks until the request finishes (ML_ETIMEOUT after timeout_s seconds). */
+int ml_wait(ml_server *s, uint64_t job, double timeout_s);
+/* Host times (seconds since server creation) of submission, admission and
+ * completion (-1 while not reached). */
+int ml_job_times(ml_server *s, uint64_t job, double *t_submit, double *t_admit, double *t_done);
+/* Forgets a finished request (ML_EBUSY while it runs). */
+int ml_job_release(ml_server *s, uint64_t job);
+int ml_server_stats(ml_server *s, ml_server_info *out);
+/* Cancels queued requests, waits for the admitted ones, stops the worker
+ * and frees everything. */
+int ml_server_destroy(ml_server *s);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free entry point (no counterpart in the paper)                  */
 /* ------------------------------------------------------------------------ */
 

@@ -86,6 +86,8 @@ void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const
 void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
                        cudaStream_t s);
 int record_blocks(const Geom& g, int d);
+// co-resident blocks per SM of the persistent sweep kernel
+int sweep_blocks_per_sm(bool fp64);
 int fold_probe_groups(int np);
 
 // ---- link updates (ml_update.cu) ----

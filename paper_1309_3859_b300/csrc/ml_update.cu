@@ -414,6 +414,15 @@ static int sweeps_grid(int total_tiles) {
   return total_tiles < cap ? total_tiles : cap;
 }
 
+int sweep_blocks_per_sm(bool fp64) {
+  int n = 0;
+  if (fp64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweeps_table<double>, kSweepThreads, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweeps_table<float>, kSweepThreads, 0);
+  return n < 1 ? 1 : n;
+}
+
 template <typename T>
 static cudaError_t launch_sweeps_table_t(const LatDesc* d, const int* tile_lat, const TableDims& td, const LatCtl* ctl,
                                          int mask, int n_or, int n_compound, int* err, unsigned long long* bar,

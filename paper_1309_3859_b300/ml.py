@@ -98,6 +98,15 @@ SIGNATURES = {
     "ml_batch_sync": (ctypes.c_int, [_H]),
     "ml_batch_sweep_mode": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     "ml_batch_set_sweep_mode": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ml_server_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "ml_submit": (ctypes.c_int, [_H, ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_uint64)]),
+    "ml_poll": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), _D, ctypes.c_size_t]),
+    "ml_wait": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_double]),
+    "ml_job_times": (ctypes.c_int, [_H, ctypes.c_uint64, _D, _D, _D]),
+    "ml_job_release": (ctypes.c_int, [_H, ctypes.c_uint64]),
+    "ml_server_stats": (ctypes.c_int, [_H, ctypes.c_void_p]),
+    "ml_server_destroy": (ctypes.c_int, [_H]),
     "ml_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ml_kernel_launches": (ctypes.c_uint64, []),
 }
@@ -450,3 +459,78 @@ class Batch:
 
     def sync(self):
         _check(lib().ml_batch_sync(self.h), "ml_batch_sync")
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("n_or", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
+                ("max_active", ctypes.c_int)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int), ("active", ctypes.c_int), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("ticks", ctypes.c_uint64), ("budget_bytes", ctypes.c_size_t),
+                ("used_bytes", ctypes.c_size_t)]
+
+
+class Server:
+    """Request server with continuous batching (``ml_server_*``, ``ml_submit``)."""
+
+    def __init__(self, budget_bytes: int, fp64: bool = False, n_or: int = 3, max_active: int = 0):
+        import torch
+
+        torch.cuda.init()
+        cfg = _ServerConfig(ML_FP64 if fp64 else ML_FP32, n_or, int(budget_bytes), int(max_active))
+        h = ctypes.c_void_p()
+        _check(lib().ml_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ml_server_create")
+        self.h = h
+        self._params = {}
+
+    def submit(self, p: Params, n_therm: int, n_meas: int) -> int:
+        job = ctypes.c_uint64()
+        _check(lib().ml_submit(self.h, ctypes.byref(p.c()), int(n_therm), int(n_meas), ctypes.byref(job)),
+               "ml_submit")
+        self._params[job.value] = (p, n_meas)
+        return job.value
+
+    def poll(self, job: int):
+        """(done, records or None)"""
+        p, n_meas = self._params[job]
+        out = np.zeros((n_meas, record_len(p)), dtype=np.float64)
+        done = ctypes.c_int()
+        _check(lib().ml_poll(self.h, job, ctypes.byref(done), out.ctypes.data_as(_D), out.size), "ml_poll")
+        return (True, out) if done.value else (False, None)
+
+    def wait(self, job: int, timeout_s: float = 600.0):
+        _check(lib().ml_wait(self.h, job, float(timeout_s)), "ml_wait")
+        return self.poll(job)[1]
+
+    def times(self, job: int):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().ml_job_times(self.h, job, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "ml_job_times")
+        return a.value, b.value, c.value
+
+    def release(self, job: int):
+        _check(lib().ml_job_release(self.h, job), "ml_job_release")
+        self._params.pop(job, None)
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check(lib().ml_server_stats(self.h, ctypes.byref(st)), "ml_server_stats")
+        return {k: getattr(st, k) for k, _ in _ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(lib().ml_server_destroy(self.h), "ml_server_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
