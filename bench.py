@@ -36,7 +36,7 @@ import numpy as np  # noqa: E402
 
 from paper_1309_3859_b300 import workloads  # noqa: E402
 
-METRIC = "multilevel link-updates/s"
+METRIC = "multilevel link-updates/s"  # with HBM fraction (roofline) and serving p50/p99 beside it
 UNIT = "link-updates/s"
 L2_FLUSH_BYTES = 512 << 20
 
@@ -223,6 +223,93 @@ def hbm_sweep_point(ml, peak):
             "hb_pass_ms": ms_hb, "hb_pass_gbs": pass_bytes / (ms_hb * 1e-3) / 1e9}
 
 
+def batch_params(ml, n=64):
+    """The batched workload: 64 lattices, L from {12,16,20,24}, N_t from
+    {4,...,12}, beta in [0.94, 0.99], FP32, slabs of 2, 50 sub-updates,
+    P(r) r = 1..L/2, E_x on the mid-plane at r = L/4, offsets 0..L/4."""
+    out = []
+    for (L, Nt, beta, seed) in workloads.batch_mix(n):
+        out.append(ml.Params(L=L, Nt=Nt, beta=beta, seed=seed, fp64=False, slab=2, n_sub=50, k_between=10,
+                             r=tuple(range(1, L // 2 + 1)), rf=(L // 4,),
+                             probes=tuple((d, 0) for d in range(L // 4 + 1)), comp_mask=workloads.COMP_EX))
+    return out
+
+
+def batched_point(ml, steps=3, warmup=1):
+    import torch
+
+    ps = batch_params(ml)
+    with ml.Batch(ps) as b:
+        b.thermalize(200)
+        for _ in range(warmup):
+            b.measure_device(1)
+        b.sync()
+        st = b.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            b.measure_device(1)
+        e1.record(st)
+        b.sync()
+        ms = e0.elapsed_time(e1) / steps
+        mode = b.sweep_mode
+    upd = 0
+    for p in ps:
+        V = p.L ** 3 * p.Nt
+        upd += (p.k_between * 4 * V + p.n_sub * (V + 3 * V * (p.slab - 1) // p.slab)) * (1 + p.n_or)
+    return {"workload": "batched-64-lattices-fp32", "lattices": len(ps), "ms_per_step": ms,
+            "link_updates_per_s": upd / (ms * 1e-3), "measurements_per_s": len(ps) / (ms * 1e-3),
+            "sweep_impl": ["persistent", "per-pass"][mode], "step": "one measurement of every lattice"}
+
+
+def serving_request(ml, L, Nt, beta, seed):
+    """One serving request: thermalise 100 sweeps, one measurement of 50 slab
+    sub-updates, P(r) r = 1..L/2, E_x at r = L/4 over offsets 0..L/4."""
+    return ml.Params(L=L, Nt=Nt, beta=beta, seed=seed, fp64=False, slab=2, n_sub=50, k_between=0,
+                     r=tuple(range(1, L // 2 + 1)), rf=(max(1, L // 4),),
+                     probes=tuple((d, 0) for d in range(L // 4 + 1)), comp_mask=workloads.COMP_EX)
+
+
+def serving_point(ml, n_requests=1000, load=0.8, budget_gb=160):
+    """Poisson arrivals at `load` x the measured capacity; latency per size class."""
+    with ml.Server(budget_bytes=int(budget_gb) << 30, fp64=False) as srv:
+        # capacity: a burst of requests submitted at once
+        cal = workloads.request_stream(200, 1.0, seed=11)
+        t0 = time.perf_counter()
+        jobs = [srv.submit(serving_request(ml, L, Nt, beta, 10 ** 6 + sd), 100, 1) for (_, L, Nt, beta, sd) in cal]
+        for j in jobs:
+            srv.wait(j, 600)
+        capacity = len(jobs) / (time.perf_counter() - t0)
+        for j in jobs:
+            srv.release(j)
+        rate = load * capacity
+        stream = workloads.request_stream(n_requests, rate, seed=7)
+        start = time.perf_counter()
+        sub = []
+        for (t_arr, L, Nt, beta, sd) in stream:
+            delay = start + t_arr - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            sub.append((srv.submit(serving_request(ml, L, Nt, beta, sd), 100, 1), L, Nt))
+        lat, by_L, upd = [], {}, 0
+        for (j, L, Nt) in sub:
+            srv.wait(j, 600)
+            t_s, t_a, t_d = srv.times(j)
+            lat.append(t_d - t_s)
+            by_L.setdefault(L, []).append(t_d - t_s)
+            V = L ** 3 * Nt
+            upd += (100 * 4 * V + 50 * (V + 3 * V // 2)) * 4
+        span = time.perf_counter() - start
+        stats = srv.stats()
+    q = lambda a, f: float(np.percentile(np.asarray(a), f))  # noqa: E731
+    return {"workload": "serving-poisson-fp32", "requests": n_requests, "load": load,
+            "capacity_req_per_s": capacity, "arrival_rate_per_s": rate, "throughput_req_per_s": n_requests / span,
+            "link_updates_per_s": upd / span, "latency_s": {"p50": q(lat, 50), "p99": q(lat, 99)},
+            "latency_by_L_s": {str(L): {"n": len(v), "p50": q(v, 50), "p99": q(v, 99)} for L, v in sorted(by_L.items())},
+            "budget_gb": budget_gb, "ticks": stats["ticks"],
+            "request": "100 thermalisation sweeps + 1 measurement (50 sub-updates), L in 12..32, Nt in 4..12"}
+
+
 def run_gpu(args, w, rank, world):
     import torch
 
@@ -261,9 +348,15 @@ def run_gpu(args, w, rank, world):
         for k in range(args.steps):
             with torch.cuda.stream(st):
                 flush.fill_(float(k))
+            if args.profile and k == 0:
+                torch.cuda.synchronize()
+                torch.cuda.cudart().cudaProfilerStart()
             starts[k].record(st)
             lat.measure_device(1, rec)
             ends[k].record(st)
+            if args.profile and k == 0:
+                torch.cuda.synchronize()
+                torch.cuda.cudart().cudaProfilerStop()
         lat.sync()
         barrier()
         t_wall = time.perf_counter() - t_wall0
@@ -296,6 +389,7 @@ def run_gpu(args, w, rank, world):
             "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
             "launch_ms": kms[dominant], "batch_slots": nB}
     hbm_point = hbm_sweep_point(ml, peak) if rank == 0 and not args.no_extra else None
+    batch_point = batched_point(ml) if rank == 0 and not args.no_extra else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -316,6 +410,9 @@ def run_gpu(args, w, rank, world):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
+    serving = None
+    if rank == 0 and args.serving_requests > 0:
+        serving = serving_point(ml, n_requests=args.serving_requests)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -331,11 +428,13 @@ def run_gpu(args, w, rank, world):
         "roofline": roof,
         "kernel_ms": kms, "kernel_share": share,
         "sweep_hbm_point": hbm_point,
+        "batched": batch_point,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,
+        "serving": serving,
         "wall_s": t_wall,
     }
     lat.close()
@@ -354,7 +453,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=workloads.SINGLE_24.name, choices=sorted(workloads.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the 64^4 HBM sweep point")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 64^4 HBM sweep point and the batch")
+    ap.add_argument("--profile", action="store_true",
+                    help="bracket the first timed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--serving-requests", type=int, default=1000,
+                    help="requests of the serving measurement (0 skips it)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
