@@ -171,8 +171,9 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
     L->acc4T = static_cast<double2*>(lat_alloc(e, L, L->acc4T_bytes));
     L->acc4O = static_cast<double2*>(lat_alloc(e, L, L->acc4O_bytes));
   }
-  L->osum_bytes = static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * kBatch * tsz;
-  L->trec_bytes = static_cast<size_t>(nslab_in) * g.Ns * kBatch * tsz;
+  const int nB = rec_batch(e->fp64);
+  L->osum_bytes = static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * nB * tsz;
+  L->trec_bytes = static_cast<size_t>(nslab_in) * g.Ns * nB * tsz;
   for (int b = 0; b < 2; ++b) {
     L->osum[b] = lat_alloc(e, L, L->osum_bytes);
     L->theta_rec[b] = lat_alloc(e, L, L->trec_bytes);
@@ -268,10 +269,10 @@ int enqueue_sweeps(Engine* e, int n, int mask) { return enqueue_sweeps_table(e, 
 // then the record of the new configuration into slot (buf, slot) and its
 // vacuum sums (main stream)
 int enqueue_sub_update(Engine* e, int buf, int slot) {
-  int st = enqueue_sweeps(e, 1, e->slab);
-  if (st) return st;
-  launch_record_table(e->fp64, e->d_desc, e->td, nullptr, buf, slot, e->stream);
-  return ML_OK;
+  return launch_sweeps_table(e->fp64, e->sweep_mode == ML_SWEEP_PERSISTENT, e->d_desc, e->d_tile_lat, e->td, nullptr,
+                             e->slab, e->n_or, 1, e->d_err, e->bar, e->stream, true, buf, slot)
+             ? ML_ECUDA
+             : ML_OK;
 }
 
 int join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
@@ -323,7 +324,7 @@ int check_errors(Engine* e) {
 void destroy_graphs(Engine* e) {
   std::vector<Graph*> all = {&e->g_full, &e->g_outer, &e->g_one_full, &e->g_flush[0], &e->g_flush[1]};
   for (int b = 0; b < 2; ++b)
-    for (int j = 0; j < kBatch; ++j) all.push_back(&e->g_sub[b][j]);
+    for (int j = 0; j < kBatchMax; ++j) all.push_back(&e->g_sub[b][j]);
   for (Graph* gr : all)
     if (gr->exec) {
       cudaGraphExecDestroy(gr->exec);
@@ -582,6 +583,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
       return ML_EINVAL;
   }
   e->fp64 = ps[0].prec == ML_FP64;
+  e->nB = rec_batch(e->fp64);
   e->n_or = ps[0].n_or;
   e->slab = ps[0].slab;
   e->outer_slab = ps[0].outer_slab;

@@ -15,7 +15,13 @@ constexpr float kTwoPiF = 6.28318530717958647692f;
 constexpr float kInvTwoPiF = 0.15915494309189533577f;
 constexpr int kMaxTrials = 64;   // cap of the von Mises rejection loop
 constexpr int kMaxSlabs = 64;    // slabs per level handled by the product kernels
-constexpr int kBatch = 16;       // sub-update records folded per accumulation pass
+// Sub-update records folded per accumulation pass (ring slots).
+constexpr int kBatchMax = 16;
+template <typename T>
+struct RecBatch {
+  static constexpr int n = 16;
+};
+inline int rec_batch(bool) { return 16; }
 
 // Error bits written to the handle's device error word.
 constexpr int kErrReject = 1;

@@ -28,8 +28,8 @@ struct LatState {
   int* d_lists = nullptr;
   double2 *accT = nullptr, *accO = nullptr, *acc4T = nullptr, *acc4O = nullptr;
   size_t accT_bytes = 0, accO_bytes = 0, acc4T_bytes = 0, acc4O_bytes = 0;
-  void* osum[2] = {nullptr, nullptr};       // record ring [nslab][nc][2][Ns][kBatch]
-  void* theta_rec[2] = {nullptr, nullptr};  // record ring [nslab][Ns][kBatch]
+  void* osum[2] = {nullptr, nullptr};       // record ring [nslab][nc][2][Ns][slots]
+  void* theta_rec[2] = {nullptr, nullptr};  // record ring [nslab][Ns][slots]
   size_t osum_bytes = 0, trec_bytes = 0;
   double* vac_part = nullptr;
   int nparts = 0;
@@ -60,10 +60,10 @@ struct Engine {
   int* d_err = nullptr;
   unsigned long long* bar = nullptr;  // grid-barrier counter of the persistent sweeps
   int sweep_mode = ML_SWEEP_PERSISTENT;
-  int nB = kBatch, cur_buf = 0;
+  int nB = kBatchMax, cur_buf = 0;  // ring slots (rec_batch of the precision)
   cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_fold[2] = {nullptr, nullptr};
   cudaEvent_t ev_main = nullptr, ev_side = nullptr;
-  Graph g_full, g_outer, g_one_full, g_flush[2], g_sub[2][kBatch];
+  Graph g_full, g_outer, g_one_full, g_flush[2], g_sub[2][kBatchMax];
   double* rec_buf = nullptr;
   size_t rec_cap = 0;
 };

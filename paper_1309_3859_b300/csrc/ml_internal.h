@@ -36,8 +36,8 @@ struct LatDesc {
   double beta;
   int slab, nslab;            // inner slab thickness d and Nt / d
   int tile_start, tiles;      // sweep tiles of kSweepTile links
-  void* theta_rec[2];         // record ring buffers [nslab][Ns][kBatch]
-  void* osum[2];              // [nslab][nc][2][Ns][kBatch]
+  void* theta_rec[2];         // record ring buffers [nslab][Ns][slots]
+  void* osum[2];              // [nslab][nc][2][Ns][slots], slots = rec_batch(fp64)
   double2* accT;              // inner slab sums
   double2* accO;
   double* vac_part;           // [nparts][12] warp partials of the vacuum sums
@@ -75,9 +75,12 @@ constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep k
 // launch with a grid barrier between passes (bar: monotonic counter) or as one
 // kernel per pass.  tile_lat[t] is the lattice of sweep tile t.  Returns 0 or
 // -1 when a launch fails.
+// With `record`, the new configurations are then recorded into ring slot
+// (rec_buf, rec_slot) (or per lattice from ctl) and their vacuum sums
+// accumulated, exactly as launch_record_table does.
 int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int* tile_lat, const TableDims& td,
                         const LatCtl* ctl, int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
-                        cudaStream_t s);
+                        cudaStream_t s, bool record = false, int rec_buf = 0, int rec_slot = 0);
 // record of each lattice's configuration into ring slot (buf, slot) and its
 // vacuum partials; then vac_acc += site means
 void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,

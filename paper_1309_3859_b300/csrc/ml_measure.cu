@@ -15,39 +15,11 @@
 // spatial site x fastest, so one warp touches 32 consecutive sites.  All
 // reductions over sites are warp-shuffle trees writing per-warp partials,
 // followed by fixed-order sums: results do not depend on scheduling.
-#include "ml_internal.h"
+#include "ml_record.cuh"
 
 namespace ml {
 
-__constant__ int c_plane_mu[6] = {0, 0, 0, 2, 3, 1};
-__constant__ int c_plane_nu[6] = {1, 2, 3, 3, 1, 2};
-
 static inline int blocks_for(long long n, int t) { return static_cast<int>((n + t - 1) / t); }
-
-// spatial coordinates of spatial site x
-__device__ __forceinline__ void spatial_coords(const Geom& g, int x, int* cx, int* cy, int* cz) {
-  int rest = x / g.L;
-  *cx = x - rest * g.L;
-  *cy = rest % g.L;
-  *cz = rest / g.L;
-}
-
-// theta_0 at spatial site (cx, cy, cz) and time t
-template <typename T>
-__device__ __forceinline__ double theta0(const T* __restrict__ th, const Geom& g, int cx, int cy, int cz, int t) {
-  const int i = cx + g.L * (cy + g.L * (cz + g.L * t));
-  return static_cast<double>(th[soa(g, 0, i, (cx + cy + cz + t) & 1)]);
-}
-
-// plaquette angle of plane (mu, nu) at site coordinates c = (t, x, y, z)
-template <typename T>
-__device__ __forceinline__ T plaquette_angle(const T* __restrict__ th, const Geom& g, const int c[4], int mu, int nu) {
-  const int i = site_index(g, c[0], c[1], c[2], c[3]);
-  const int p = parity_of_coords(c);
-  const int ipmu = shifted(g, c, mu, 1, nu, 0);
-  const int ipnu = shifted(g, c, nu, 1, mu, 0);
-  return th[soa(g, mu, i, p)] + th[soa(g, nu, ipmu, p ^ 1)] - th[soa(g, mu, ipnu, p ^ 1)] - th[soa(g, nu, i, p)];
-}
 
 // e^{i phi} for a phase known in double precision, evaluated in T
 template <typename T>
@@ -66,19 +38,19 @@ __device__ __forceinline__ double2 unit_phase(double phi) {
 
 // ---------------------------------------------------------------------------
 // Ring of sub-update records, slot-fastest: element (slot j) of
-//   theta_rec[s][x][kBatch]          Theta_s(x) = sum_{t in slab} theta_0(x, t)
+//   theta_rec[s][x][slots]           Theta_s(x) = sum_{t in slab} theta_0(x, t)
 //                                    (FP32: summed in double, reduced to
 //                                    [-pi, pi) and rounded)
-//   osum[s][ci][k][x][kBatch]        sum_{t in slab} (Re, Im) P_c(x, t)
+//   osum[s][ci][k][x][slots]         sum_{t in slab} (Re, Im) P_c(x, t)
 // so the fold reads all records of one site as one contiguous vector.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void load_batch(const T* __restrict__ p, T v[kBatch]) {
+__device__ __forceinline__ void load_batch(const T* __restrict__ p, T v[RecBatch<T>::n]) {
   if constexpr (sizeof(T) == 4) {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int j = 0; j < kBatch / 4; ++j) {
-      const float4 a = q[j];
+    for (int j = 0; j < RecBatch<T>::n / 4; ++j) {
+      const float4 a = __ldg(q + j);
       v[4 * j] = a.x;
       v[4 * j + 1] = a.y;
       v[4 * j + 2] = a.z;
@@ -87,8 +59,8 @@ __device__ __forceinline__ void load_batch(const T* __restrict__ p, T v[kBatch])
   } else {
     const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
-    for (int j = 0; j < kBatch / 2; ++j) {
-      const double2 a = q[j];
+    for (int j = 0; j < RecBatch<T>::n / 2; ++j) {
+      const double2 a = __ldg(q + j);
       v[2 * j] = a.x;
       v[2 * j + 1] = a.y;
     }
@@ -103,7 +75,6 @@ __device__ __forceinline__ void load_batch(const T* __restrict__ p, T v[kBatch])
 template <typename T>
 __global__ void __launch_bounds__(256) k_record_table(const LatDesc* __restrict__ desc,
                                                       const LatCtl* __restrict__ ctl, int buf, int slot) {
-  using P = Prec<T>;
   const int li = blockIdx.z;
   if (ctl) {
     if (!ctl[li].record) return;
@@ -111,48 +82,9 @@ __global__ void __launch_bounds__(256) k_record_table(const LatDesc* __restrict_
     slot = ctl[li].slot;
   }
   const LatDesc& L = desc[li];
-  const Geom g = L.g;
-  const int d = L.slab, nslab = L.nslab, nc = L.m.nc;
-  if (blockIdx.x * blockDim.x >= g.Ns * nslab || static_cast<int>(blockIdx.y) > nc) return;  // whole block
-  const T* __restrict__ th = static_cast<const T*>(L.theta);
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = idx < g.Ns * nslab;
-  const int s = live ? idx / g.Ns : 0;
-  const int x = live ? idx - s * g.Ns : 0;
-  int c[4];
-  spatial_coords(g, x, &c[1], &c[2], &c[3]);
-  const int ci = blockIdx.y;
-  if (ci == nc) {
-    if (live) {
-      double tsum = 0.0;
-      for (int t = s * d; t < s * d + d; ++t) tsum += theta0(th, g, c[1], c[2], c[3], t);
-      static_cast<T*>(L.theta_rec[buf])[(static_cast<size_t>(s) * g.Ns + x) * kBatch + slot] =
-          static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
-    }
-    return;  // the whole block takes this branch
-  }
-  const int cc = L.m.comp[ci];
-  const int mu = c_plane_mu[cc], nu = c_plane_nu[cc];
-  T re = T(0), im = T(0);
-  if (live) {
-    for (int t = s * d; t < s * d + d; ++t) {
-      c[0] = t;
-      T sn, cs;
-      P::sincos_(plaquette_angle(th, g, c, mu, nu), &sn, &cs);
-      re += cs;
-      im += sn;
-    }
-    T* osum = static_cast<T*>(L.osum[buf]);
-    osum[((static_cast<size_t>(s * nc + ci) * 2 + 0) * g.Ns + x) * kBatch + slot] = re;
-    osum[((static_cast<size_t>(s * nc + ci) * 2 + 1) * g.Ns + x) * kBatch + slot] = im;
-  }
-  const double vr = warp_sum(static_cast<double>(re));
-  const double vi = warp_sum(static_cast<double>(im));
-  if ((threadIdx.x & 31) == 0) {
-    const size_t w = idx >> 5;
-    L.vac_part[w * 12 + 2 * cc] = vr;
-    L.vac_part[w * 12 + 2 * cc + 1] = vi;
-  }
+  if (blockIdx.x * blockDim.x >= L.g.Ns * L.nslab || static_cast<int>(blockIdx.y) > L.m.nc) return;  // whole block
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  record_warp<T>(L, buf, slot, blockIdx.y, w, threadIdx.x & 31);
 }
 
 // vac_acc[j] += (1/V) sum_w vac_part[w][j] in a fixed order; grid (12, lattices)
@@ -161,29 +93,40 @@ __global__ void __launch_bounds__(256) k_vac_accumulate_table(const LatDesc* __r
   __shared__ double sh[8];
   const int li = blockIdx.y;
   if (ctl && !ctl[li].record) return;
-  const LatDesc& L = desc[li];
-  const int j = blockIdx.x;
-  double v = 0.0;
-  for (int w = threadIdx.x; w < L.nparts; w += blockDim.x) v += L.vac_part[static_cast<size_t>(w) * 12 + j];
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    L.vac_acc[j] += s * (1.0 / L.g.V);
-  }
+  vac_block_sum(desc[li], blockIdx.x, sh);
 }
+
+// Exact float -> double widening with integer instructions only, keeping the
+// scarce double-precision pipe for the additions.  A binary32 value
+// (s, e, m) is the binary64 value (s, e - 127 + 1023, m << 29); zero and
+// subnormal inputs (|v| < 2^-126, far below any batch sum that is not zero)
+// widen to a signed zero, and infinities or NaNs keep their class.
+__device__ __forceinline__ double widen(float v) {
+  const unsigned int b = __float_as_uint(v);
+  const unsigned long long sign = static_cast<unsigned long long>(b >> 31) << 63;
+  const unsigned int e = (b >> 23) & 0xffu;
+  const unsigned long long m = static_cast<unsigned long long>(b & 0x7fffffu) << 29;
+  unsigned long long bits;
+  if (e == 0u)
+    bits = sign;
+  else if (e == 0xffu)
+    bits = sign | (0x7ffull << 52) | m;
+  else
+    bits = sign | (static_cast<unsigned long long>(e + (1023u - 127u)) << 52) | m;
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+__device__ __forceinline__ double widen(double v) { return v; }
 
 // e^{i (Theta(x + r) - Theta(x))} for the first nrec records, zero beyond
 template <typename T>
 __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const T* __restrict__ rec_xr, int nrec,
-                                             T er[kBatch], T ei[kBatch]) {
-  T a[kBatch], b[kBatch];
+                                             T er[RecBatch<T>::n], T ei[RecBatch<T>::n]) {
+  constexpr int B = RecBatch<T>::n;
+  T a[B], b[B];
   load_batch<T>(rec_x, a);
   load_batch<T>(rec_xr, b);
 #pragma unroll
-  for (int j = 0; j < kBatch; ++j) {
+  for (int j = 0; j < B; ++j) {
     er[j] = T(0);
     ei[j] = T(0);
     if (j < nrec) Prec<T>::sincos_(b[j] - a[j], &ei[j], &er[j]);
@@ -191,7 +134,7 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 }
 
 // ---------------------------------------------------------------------------
-// Fold of nrec <= kBatch records into the double-precision slab sums:
+// Fold of nrec <= slots records into the double-precision slab sums:
 //   accT[s][a][x]              += sum_j T_j(x, s, R_a)
 //   accO[s][f][b][ci][k][x]    += sum_j T_j(x, s, rf_f) O_j[s][ci][k](x0)
 // The sum over the batch is formed in the records' precision and added once,
@@ -215,17 +158,18 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
   int cx, cy, cz;
   spatial_coords(g, x, &cx, &cy, &cz);
   const int xr = wrapc(cx + m.R[a], g.L) + g.L * (cy + g.L * cz);
-  const T* rec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * kBatch;
-  T er[kBatch], ei[kBatch];
-  batch_phases<T>(rec + static_cast<size_t>(x) * kBatch, rec + static_cast<size_t>(xr) * kBatch, nrec, er, ei);
+  constexpr int B = RecBatch<T>::n;
+  const T* rec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
+  T er[B], ei[B];
+  batch_phases<T>(rec + static_cast<size_t>(x) * B, rec + static_cast<size_t>(xr) * B, nrec, er, ei);
   T sr = T(0), si = T(0);
 #pragma unroll
-  for (int j = 0; j < kBatch; ++j) {
+  for (int j = 0; j < B; ++j) {
     sr += er[j];
     si += ei[j];
   }
   double2* p = L.accT + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
-  *p = make_double2(p->x + static_cast<double>(sr), p->y + static_cast<double>(si));
+  *p = make_double2(p->x + widen(sr), p->y + widen(si));
 }
 
 constexpr int kProbesPerThread = 3;
@@ -233,6 +177,8 @@ constexpr int kProbesPerThread = 3;
 template <typename T>
 __global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict__ desc,
                                                        const LatCtl* __restrict__ ctl, int buf, int nrec) {
+  constexpr int B = RecBatch<T>::n;
+  constexpr int kMaxCK = 12;  // components x (Re, Im) insertions
   const int li = blockIdx.z;
   if (ctl) {
     if (!ctl[li].fold) return;
@@ -253,29 +199,40 @@ __global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict
   spatial_coords(g, x, &cx, &cy, &cz);
   const int rf = m.rf[f];
   const int xr = wrapc(cx + rf, g.L) + g.L * (cy + g.L * cz);
-  const T* trec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * kBatch;
-  const T* osum = static_cast<const T*>(L.osum[buf]);
-  T er[kBatch], ei[kBatch];
-  batch_phases<T>(trec + static_cast<size_t>(x) * kBatch, trec + static_cast<size_t>(xr) * kBatch, nrec, er, ei);
+  const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
+  const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
+  double2* __restrict__ acc = L.accO;
+  T er[B], ei[B];
+  batch_phases<T>(trec + static_cast<size_t>(x) * B, trec + static_cast<size_t>(xr) * B, nrec, er, ei);
   const int x0x = wrapc(cx + rf / 2, g.L);
+  const int nck = 2 * m.nc;
   const int b_end = min(m.np, (bg + 1) * kProbesPerThread);
   for (int b = bg * kProbesPerThread; b < b_end; ++b) {
     const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
-    for (int ci = 0; ci < m.nc; ++ci) {
+    const size_t abase = (((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * nck) * g.Ns + x;
+    // every accumulator of this probe is read before the arithmetic, so the
+    // loads of all components are in flight together
+    double2 a[kMaxCK];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        T o[kBatch];
-        load_batch<T>(osum + ((static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0) * kBatch, o);
-        T sr = T(0), si = T(0);
+    for (int q = 0; q < kMaxCK; ++q)
+      if (q < nck) a[q] = acc[abase + static_cast<size_t>(q) * g.Ns];
 #pragma unroll
-        for (int j = 0; j < kBatch; ++j) {
-          sr += er[j] * o[j];
-          si += ei[j] * o[j];
-        }
-        double2* p = L.accO + ((((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
-        *p = make_double2(p->x + static_cast<double>(sr), p->y + static_cast<double>(si));
+    for (int q = 0; q < kMaxCK; ++q) {
+      if (q >= nck) break;
+      const int ci = q >> 1, k = q & 1;
+      T o[B];
+      load_batch<T>(osum + ((static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0) * B, o);
+      T sr = T(0), si = T(0);
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        sr += er[j] * o[j];
+        si += ei[j] * o[j];
       }
+      a[q] = make_double2(a[q].x + widen(sr), a[q].y + widen(si));
     }
+#pragma unroll
+    for (int q = 0; q < kMaxCK; ++q)
+      if (q < nck) acc[abase + static_cast<size_t>(q) * g.Ns] = a[q];
   }
 }
 

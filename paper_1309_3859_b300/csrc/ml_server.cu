@@ -245,14 +245,14 @@ void advance(ml_server* s, Job* j) {
   }
 }
 
-LatCtl control_of(const Job* j) {
+LatCtl control_of(const Job* j, int nB) {
   LatCtl c{};
   if (j->phase == kOuter) c.mask = j->p.outer_slab;
   if (j->phase == kInner) {
     c.mask = j->p.slab;
     c.record = 1;
-    c.slot = j->sub % kBatch;
-    c.fold = (c.slot == kBatch - 1 || j->sub == j->p.n_sub - 1) ? 1 : 0;
+    c.slot = j->sub % nB;
+    c.fold = (c.slot == nB - 1 || j->sub == j->p.n_sub - 1) ? 1 : 0;
     c.nrec = c.slot + 1;
   }
   return c;
@@ -347,14 +347,13 @@ int run_tick(ml_server* s) {
   }
   const size_t n = s->active.size();
   s->h_ctl.resize(n);
-  for (size_t i = 0; i < n; ++i) s->h_ctl[i] = control_of(s->active[i]);
+  for (size_t i = 0; i < n; ++i) s->h_ctl[i] = control_of(s->active[i], rec_batch(e->fp64));
   SRV_CUDA(cudaMemcpyAsync(s->d_ctl, s->h_ctl.data(), n * sizeof(LatCtl), cudaMemcpyHostToDevice, e->stream));
   const bool persistent = s->td.total_tiles <= s->coresident_tiles;
   if (persistent) SRV_CUDA(cudaMemsetAsync(e->bar, 0, sizeof(unsigned long long), e->stream));
   if (launch_sweeps_table(e->fp64, persistent, s->d_desc, s->d_tile_lat, s->td, s->d_ctl, 0, e->n_or, 1, e->d_err,
-                          e->bar, e->stream))
+                          e->bar, e->stream, true, 0, 0))
     return ML_ECUDA;
-  launch_record_table(e->fp64, s->d_desc, s->td, s->d_ctl, 0, 0, e->stream);
   launch_fold_table(e->fp64, s->d_desc, s->td, s->d_ctl, 0, 0, e->stream);
   for (Job* j : s->active) advance(s, j);
   SRV_CUDA(cudaGetLastError());

@@ -8,7 +8,7 @@
 // theta (Section II, Creutz 1987), even/odd checkerboard in place (Section
 // II.D) and spatial links on t = 0 (mod d) frozen in slab mode (Section II.C,
 // Algorithm 1).
-#include "ml_internal.h"
+#include "ml_record.cuh"
 
 namespace ml {
 
@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
                                                                 const int* __restrict__ tile_lat, int total_tiles,
                                                                 int nlat, const LatCtl* __restrict__ ctl, int mask,
                                                                 int n_or, int n_compound, int* __restrict__ err,
-                                                                unsigned long long* __restrict__ bar) {
+                                                                unsigned long long* __restrict__ bar, int record,
+                                                                int rec_buf, int rec_slot) {
   // When every tile has its own block (the latency-bound case), the block's
   // lattice parameters are read once into registers: the barrier's acquire
   // fence would otherwise send each pass's descriptor loads back to L2.
@@ -292,6 +293,31 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
           }
           if (!grid_barrier(bar, err)) return;
         }
+  }
+  if (record) {
+    // record of the new configurations (the work of k_record_table, warp for
+    // warp), then the vacuum sums (the work of k_vac_accumulate_table)
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int li = 0; li < nlat; ++li) {
+      int buf = rec_buf, slot = rec_slot;
+      if (ctl) {
+        if (!ctl[li].record) continue;
+        buf = ctl[li].buf;
+        slot = ctl[li].slot;
+      }
+      const LatDesc& L = d[li];
+      const int nw = record_warps(L), items = (L.m.nc + 1) * nw;
+      for (int it = gw; it < items; it += nwarps) record_warp<T>(L, buf, slot, it / nw, it - (it / nw) * nw, lane);
+    }
+    if (!grid_barrier(bar, err)) return;
+    __shared__ double sh[8];
+    for (int pair = blockIdx.x; pair < nlat * 12; pair += gridDim.x) {
+      const int li = pair / 12;
+      if (ctl && !ctl[li].record) continue;
+      vac_block_sum(d[li], pair - li * 12, sh);
+    }
   }
   if (blockIdx.x == 0)
     for (int i = threadIdx.x; i < nlat; i += blockDim.x) *d[i].n_dev += n_compound;
@@ -426,7 +452,7 @@ int sweep_blocks_per_sm(bool fp64) {
 template <typename T>
 static cudaError_t launch_sweeps_table_t(const LatDesc* d, const int* tile_lat, const TableDims& td, const LatCtl* ctl,
                                          int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
-                                         cudaStream_t s) {
+                                         int record, int rec_buf, int rec_slot, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sweeps_grid<T>(td.total_tiles));
   cfg.blockDim = dim3(kSweepThreads);
@@ -437,7 +463,7 @@ static cudaError_t launch_sweeps_table_t(const LatDesc* d, const int* tile_lat, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_sweeps_table<T>, d, tile_lat, td.total_tiles, td.nlat, ctl, mask, n_or,
-                            n_compound, err, bar);
+                            n_compound, err, bar, record, rec_buf, rec_slot);
 }
 
 template <typename T>
@@ -460,18 +486,22 @@ static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const T
 
 int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int* tile_lat, const TableDims& td,
                         const LatCtl* ctl, int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool record, int rec_buf, int rec_slot) {
   if (n_compound <= 0 || td.total_tiles <= 0) return 0;
   cudaError_t e = cudaSuccess;
   if (persistent) {
-    e = fp64 ? launch_sweeps_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, bar, s)
-             : launch_sweeps_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, bar, s);
+    const int rec = record ? 1 : 0;
+    e = fp64 ? launch_sweeps_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, bar, rec, rec_buf,
+                                             rec_slot, s)
+             : launch_sweeps_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, bar, rec, rec_buf,
+                                            rec_slot, s);
     count_launches(1);
   } else {
     if (fp64)
       launch_passes_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s);
     else
       launch_passes_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s);
+    if (record) launch_record_table(fp64, d, td, ctl, rec_buf, rec_slot, s);
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? 0 : -1;
