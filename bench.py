@@ -372,19 +372,22 @@ def run_gpu(args, w, rank, world):
     # kernel classes: per-launch device time and launches per step
     nB = lat.batch_slots
     n_folds = -(-w.n_sub // nB)
+    # the k0 full sweeps run as one launch of k_between compound sweeps; a
+    # slab sub-update is one launch of the sweep kernel with the record fused
     per_step = {
-        "sweep": (ml.ML_K_SWEEP, w.k_between + w.n_sub),
-        "record": (ml.ML_K_RECORD, w.n_sub),
+        "subupdate": (ml.ML_K_SUBUPDATE, w.n_sub),
+        "full_sweeps": (ml.ML_K_SWEEP, w.k_between),
         "accumulate": (ml.ML_K_ACCUMULATE, n_folds),
         "products": (ml.ML_K_PRODUCTS, 1),
     }
     kms = {name: lat.kernel_ms(kid, reps=20 if name != "products" else 3) for name, (kid, _) in per_step.items()}
     share = {name: kms[name] * per_step[name][1] / (ms / args.steps) for name in per_step}
-    dominant = max(("sweep", "accumulate"), key=share.get)
+    dominant = max(("subupdate", "accumulate"), key=share.get)
     peak, peak_kind = measured_peaks()
-    nbytes = algorithmic_bytes(w, dominant, nB)
+    nbytes = algorithmic_bytes(w, "sweep" if dominant == "subupdate" else dominant, nB)
     achieved = nbytes / (kms[dominant] * 1e-3) / 1e9
-    roof = {"kernel": {"sweep": "k_sweeps", "accumulate": "k_accum_T + k_accum_O"}[dominant], "bound": "hbm",
+    impl = ["k_sweeps_table (persistent, record fused)", "k_pass_table + k_record_table"][lat.sweep_mode]
+    roof = {"kernel": {"subupdate": impl, "accumulate": "k_accum_T_table + k_accum_O_table"}[dominant], "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
             "launch_ms": kms[dominant], "batch_slots": nB}

@@ -196,7 +196,9 @@ typedef enum {
   ML_K_RECORD = 2,     /* record of one sub-update: slab phase and plaquette sums */
   ML_K_ACCUMULATE = 3, /* fold of a full batch of records into the slab sums      */
   ML_K_PRODUCTS = 4,   /* cross-slab products and their reduction over sites      */
-  ML_K_SWEEP = 5       /* one compound slab sweep in the persistent sweep kernel  */
+  ML_K_SWEEP = 5,      /* one compound slab sweep (the handle's implementation)   */
+  ML_K_SUBUPDATE = 6   /* one slab sub-update as measurements run it: compound
+                          sweep and record (fused in the persistent kernel)     */
 } ml_kernel_class;
 
 /* Average device time in milliseconds of `reps` back-to-back launches of one

@@ -878,7 +878,7 @@ int ml_batch_slots(ml_lattice* h, int* n) {
 }
 
 int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
-  if (!h || !avg_ms || reps < 1 || kernel < ML_K_HEATBATH || kernel > ML_K_SWEEP) return ML_EINVAL;
+  if (!h || !avg_ms || reps < 1 || kernel < ML_K_HEATBATH || kernel > ML_K_SUBUPDATE) return ML_EINVAL;
   Engine* e = &h->e;
   LatState* L = h->L();
   int st = ensure_scratch(e);
@@ -906,8 +906,14 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
       case ML_K_PRODUCTS:
         launch_products(L->g, L->g.Nt / e->slab, L->meas, L->accT, L->accO, 1.0, L->partial, e->rec_buf, e->stream);
         break;
-      default:
+      case ML_K_SWEEP:
         st = enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, e->sweep_mode);
+        break;
+      default:
+        st = launch_sweeps_table(e->fp64, e->sweep_mode == ML_SWEEP_PERSISTENT, e->d_desc_scratch, e->d_tile_lat,
+                                 e->td, nullptr, e->slab, e->n_or, 1, e->d_err, e->bar, e->stream, true, 0, 0)
+                 ? ML_ECUDA
+                 : ML_OK;
     }
   }
   ML_CUDA(cudaEventRecord(e1, e->stream));

@@ -20,7 +20,7 @@ from . import build as _build
 ML_OK, ML_EINVAL, ML_ENOMEM, ML_ECUDA, ML_ETIMEOUT, ML_EREJECT, ML_EBUSY, ML_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 ML_FP64, ML_FP32 = 0, 1
 ML_SWEEP_PERSISTENT, ML_SWEEP_PASSES = 0, 1
-ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP = range(6)
+ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP, ML_K_SUBUPDATE = range(7)
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
