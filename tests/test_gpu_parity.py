@@ -323,3 +323,34 @@ def test_sweep_implementations_agree(fp64):
     assert a[2] == b[2]
     assert np.array_equal(a[1], b[1])
     assert np.array_equal(a[0], b[0])
+
+
+def test_full_size_two_level_48():
+    """48^3 x 16 two-level workload in FP32: one overrelaxation pass of every
+    direction link by link, and the measurement of one configuration with its
+    full layout (r = 2..24, six components at r = 8, 16, 24, offsets 0..12)
+    against the oracle."""
+    w = workloads.LARGE_48
+    kw = dict(slab=2, n_sub=1, k_between=0, r=w.r, rf=w.rf, probes=w.probes, comp_mask=w.comp_mask)
+    po = oracle.Params(L=w.L, Nt=w.Nt, beta=w.beta, seed=6, draws=1, threads=0, **kw)
+    pm = ml.Params(L=w.L, Nt=w.Nt, beta=w.beta, seed=6, fp64=False, outer_slab=w.outer_slab,
+                   n_sub_outer=w.n_sub_outer, **kw)
+    th0 = oracle.hot_start(po).astype(np.float32).astype(np.float64)
+    with ml.Lattice(pm) as lat:
+        for mu in (0, 3):
+            ref = th0.copy()
+            oracle.update_pass(po, ref, mu, 0, 4, 1, 1)
+            lat.set_angles(th0)
+            lat.update_pass(mu, 0, 4, 1, 1)
+            err = wrapd(lat.get_angles()[mu] - ref[mu])
+            assert np.quantile(err, 0.999) < 1e-4 and np.median(err) < 1e-6
+        rec, _ = oracle.measure(po, th0.copy(), 0, 1)
+        ref = oracle.split_record(po, rec[0])
+        # the oracle swept once before measuring: measure that configuration
+        th1 = th0.copy()
+        oracle.compound_sweep(po, th1, 0, slab_d=2)
+        lat.set_angles(th1)
+        got = ml.split_record(pm, lat.observe())
+    for key in ("P", "Pf", "W", "vac"):
+        scale = max(np.abs(ref[key]).max(), 1e-3)
+        assert np.abs(got[key] - ref[key]).max() < 3e-5 * scale, key
