@@ -183,8 +183,9 @@ def algorithmic_bytes(w, kernel, n_batch=1):
     update pass: a (mu, parity) pass reads U_mu at both parities (V angles),
     the other three directions everywhere (3V) and writes V/2: 4.5 V angles;
     the persistent kernel runs 4 (1 + n_or) ... = 8 (1 + n_or) passes per
-    compound sweep.  fold: every slab accumulator is read and written once
-    (complex FP64, 32 bytes) and every record of the batch is read once."""
+    compound sweep.  fold: every slab accumulator (16 bytes per complex sum:
+    two doubles, or two float pairs) is read and written once (32 bytes) and
+    every record of the batch is read once."""
     tsz = 8 if w.fp64 else 4
     Ns, V = w.L ** 3, w.V
     nslab = w.Nt // w.slab
@@ -420,7 +421,7 @@ def run_gpu(args, w, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if w.fp64 else "f32 (FP64 slab accumulators and products)",
+        "vs_baseline": None, "dtype": "f64" if w.fp64 else "f32 (float-pair slab sums, FP64 products)",
         "data": "synthetic (hot start from the Philox stream, thermalised)",
         "config": {"workload": w.name, "L": w.L, "Nt": w.Nt, "beta": w.beta, "n_sub": w.n_sub,
                    "k_between": w.k_between, "n_or": w.n_or, "r": f"{w.r[0]}..{w.r[-1]}",

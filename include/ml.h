@@ -49,7 +49,8 @@ typedef enum {
 typedef enum {
   ML_FP64 = 0, /* link angles and update arithmetic in double precision       */
   ML_FP32 = 1  /* link angles and update arithmetic in single precision; slab
-                  averages, products and final ratios stay in double          */
+                  sums as double-length float pairs (about 47 bits), averages,
+                  products and final ratios in double                         */
 } ml_precision;
 
 /* Transverse offset (dy, dz) of a field probe from the mid-point of the

@@ -432,8 +432,8 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       if (st) return st;
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
-        launch_products(L->g, L->g.Nt / e->slab, L->meas, L->accT, L->accO, 1.0 / e->n_sub, L->partial, out[li],
-                        e->side);
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
+                        out[li], e->side);
       }
       ncfg = e->n_sub;
     } else {
@@ -447,13 +447,13 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
         if (!st) st = run_inner_loop(e);
         if (st) return st;
         for (LatState* L : e->lats)
-          launch_combine(L->g, L->g.Nt / e->outer_slab, e->outer_slab / e->slab, L->meas, L->accT, L->accO,
-                         1.0 / e->n_sub, L->acc4T, L->acc4O, e->side);
+          launch_combine(L->g, L->g.Nt / e->outer_slab, e->outer_slab / e->slab, L->meas, !e->fp64, L->accT,
+                         L->accO, 1.0 / e->n_sub, L->acc4T, L->acc4O, e->side);
       }
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
-        launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, L->acc4T, L->acc4O, 1.0 / e->n_sub_outer,
-                        L->partial, out[li], e->side);
+        launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, !e->fp64, L->acc4T, L->acc4O,
+                        1.0 / e->n_sub_outer, L->partial, out[li], e->side);
       }
       ncfg = e->n_sub * e->n_sub_outer;
     }
@@ -808,7 +808,7 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
   if (st) return st;
   launch_record_table(e->fp64, e->d_desc, e->td, nullptr, buf, 0, e->stream);
   launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream);
-  launch_products(L->g, L->g.Nt / e->slab, m, L->accT, L->accO, 1.0, L->partial, out, e->stream);
+  launch_products(L->g, L->g.Nt / e->slab, m, !e->fp64, L->accT, L->accO, 1.0, L->partial, out, e->stream);
   launch_write_vac(L->vac_acc, 1.0, m, out, e->stream);
   ML_CUDA(cudaGetLastError());
   ML_CUDA(cudaMemcpyAsync(out_host, out, m.rec_len * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
@@ -904,7 +904,8 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
         launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, 0, e->nB, e->stream);
         break;
       case ML_K_PRODUCTS:
-        launch_products(L->g, L->g.Nt / e->slab, L->meas, L->accT, L->accO, 1.0, L->partial, e->rec_buf, e->stream);
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, L->accO, 1.0, L->partial, e->rec_buf,
+                        e->stream);
         break;
       case ML_K_SWEEP:
         st = enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, e->sweep_mode);

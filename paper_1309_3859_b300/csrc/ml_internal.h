@@ -38,8 +38,8 @@ struct LatDesc {
   int tile_start, tiles;      // sweep tiles of kSweepTile links
   void* theta_rec[2];         // record ring buffers [nslab][Ns][slots]
   void* osum[2];              // [nslab][nc][2][Ns][slots], slots = rec_batch(fp64)
-  double2* accT;              // inner slab sums
-  double2* accO;
+  double2* accT;              // inner slab sums: double2 (re, im), or for FP32
+  double2* accO;              //   lattices float4 (re_hi, re_lo, im_hi, im_lo)
   double* vac_part;           // [nparts][12] warp partials of the vacuum sums
   int nparts;
   double* vac_acc;            // [12]
@@ -107,12 +107,13 @@ void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size
 // ---- measurement (ml_measure.cu) ----
 int vac_part_count(const Geom& g, int d);
 // two-level combination of inner averages (sum / n_inner) into outer sums
-void launch_combine(const Geom& g, int n_inner_slabs, int q, const MeasLayout& m, const double2* accT,
-                    const double2* accO, double inv_n, double2* acc4T, double2* acc4O, cudaStream_t s);
-// cross-slab products of the averages sum / n, reduced over x into the
-// record's P, Pf and W blocks
+// (pairs: all slab sums are the FP32 lattices' float-pair accumulators)
+void launch_combine(const Geom& g, int n_inner_slabs, int q, const MeasLayout& m, bool pairs, const void* accT,
+                    const void* accO, double inv_n, void* acc4T, void* acc4O, cudaStream_t s);
 int product_partial_count(const Geom& g);
-void launch_products(const Geom& g, int nslab, const MeasLayout& m, const double2* accT, const double2* accO,
+// cross-slab products of the averages sum / n, reduced over x into the
+// record's P, Pf and W blocks (pairs: as for launch_combine)
+void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, const void* accO,
                      double inv_n, double2* partial, double* rec, cudaStream_t s);
 // naive P+P and mean plaquette of the current configuration
 void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,

@@ -11,8 +11,8 @@
 //   P(r)   = (1/Ns) sum_x prod_s [T]_s(x, r)
 //   W      = (1/(Ns Nt)) sum_x sum_s [TO]_s(x) prod_{s' != s} [T]_{s'}(x)
 //
-// Slab sums live in double-precision complex accumulators laid out with the
-// spatial site x fastest, so one warp touches 32 consecutive sites.  All
+// Slab sums live in complex accumulators (double, or double-length float pairs
+// for FP32 lattices) laid out with the spatial site x fastest, so one warp touches 32 consecutive sites.  All
 // reductions over sites are warp-shuffle trees writing per-warp partials,
 // followed by fixed-order sums: results do not depend on scheduling.
 #include "ml_record.cuh"
@@ -96,26 +96,63 @@ __global__ void __launch_bounds__(256) k_vac_accumulate_table(const LatDesc* __r
   vac_block_sum(desc[li], blockIdx.x, sh);
 }
 
-// Exact float -> double widening with integer instructions only, keeping the
-// scarce double-precision pipe for the additions.  A binary32 value
-// (s, e, m) is the binary64 value (s, e - 127 + 1023, m << 29); zero and
-// subnormal inputs (|v| < 2^-126, far below any batch sum that is not zero)
-// widen to a signed zero, and infinities or NaNs keep their class.
-__device__ __forceinline__ double widen(float v) {
-  const unsigned int b = __float_as_uint(v);
-  const unsigned long long sign = static_cast<unsigned long long>(b >> 31) << 63;
-  const unsigned int e = (b >> 23) & 0xffu;
-  const unsigned long long m = static_cast<unsigned long long>(b & 0x7fffffu) << 29;
-  unsigned long long bits;
-  if (e == 0u)
-    bits = sign;
-  else if (e == 0xffu)
-    bits = sign | (0x7ffull << 52) | m;
-  else
-    bits = sign | (static_cast<unsigned long long>(e + (1023u - 127u)) << 52) | m;
-  return __longlong_as_double(static_cast<long long>(bits));
+// Slab sums (inner and outer).  FP64 lattices keep double2 (re, im) sums and
+// do all measurement arithmetic in double.  FP32 lattices keep each part as
+// an unevaluated sum hi + lo of two binary32 numbers (Dekker's double-length
+// representation, about 47 significant bits), packed as float4 (re_hi, re_lo,
+// im_hi, im_lo) in the same 16 bytes: a value enters with Knuth's error-free
+// TwoSum followed by a renormalisation, and products use the averages rounded
+// to binary32, the precision of the lattice's own link phases.  All of this
+// runs on the FP32 pipe, which retires far more operations per clock than the
+// double-precision pipe of this part.  The explicit _rn intrinsics keep the
+// compiler from contracting or reassociating the error terms.
+template <typename T>
+struct SlabAcc {
+  using type = double2;
+};
+template <>
+struct SlabAcc<float> {
+  using type = float4;
+};
+
+// arithmetic of the products formed from slab sums of type A
+template <typename A>
+struct AccMath;
+template <>
+struct AccMath<double2> {
+  static constexpr bool fp64 = true;
+  using real = double;
+  using cplx = double2;
+  __device__ static __forceinline__ double2 value(const double2& a) { return a; }
+  __device__ static __forceinline__ double2 make(double re, double im) { return make_double2(re, im); }
+};
+template <>
+struct AccMath<float4> {
+  static constexpr bool fp64 = false;
+  using real = float;
+  using cplx = float2;
+  __device__ static __forceinline__ float2 value(const float4& a) {
+    return make_float2(__fadd_rn(a.x, a.y), __fadd_rn(a.z, a.w));
+  }
+  __device__ static __forceinline__ float2 make(float re, float im) { return make_float2(re, im); }
+};
+
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float vb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, vb)), __fsub_rn(v, vb));  // hi + v = s + err exactly
+  const float l = __fadd_rn(lo, err);
+  hi = __fadd_rn(s, l);
+  lo = __fsub_rn(l, __fsub_rn(hi, s));
 }
-__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ void acc_add(double2& a, double re, double im) {
+  a.x += re;
+  a.y += im;
+}
+__device__ __forceinline__ void acc_add(float4& a, float re, float im) {
+  ff_add(a.x, a.y, re);
+  ff_add(a.z, a.w, im);
+}
 
 // e^{i (Theta(x + r) - Theta(x))} for the first nrec records, zero beyond
 template <typename T>
@@ -134,7 +171,7 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 }
 
 // ---------------------------------------------------------------------------
-// Fold of nrec <= slots records into the double-precision slab sums:
+// Fold of nrec <= slots records into the slab sums (SlabAcc<T>):
 //   accT[s][a][x]              += sum_j T_j(x, s, R_a)
 //   accO[s][f][b][ci][k][x]    += sum_j T_j(x, s, rf_f) O_j[s][ci][k](x0)
 // The sum over the batch is formed in the records' precision and added once,
@@ -168,8 +205,11 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
     sr += er[j];
     si += ei[j];
   }
-  double2* p = L.accT + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
-  *p = make_double2(p->x + widen(sr), p->y + widen(si));
+  using A = typename SlabAcc<T>::type;
+  A* p = reinterpret_cast<A*>(L.accT) + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
+  A v = *p;
+  acc_add(v, sr, si);
+  *p = v;
 }
 
 constexpr int kProbesPerThread = 3;
@@ -201,7 +241,8 @@ __global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict
   const int xr = wrapc(cx + rf, g.L) + g.L * (cy + g.L * cz);
   const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
   const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
-  double2* __restrict__ acc = L.accO;
+  using A = typename SlabAcc<T>::type;
+  A* __restrict__ acc = reinterpret_cast<A*>(L.accO);
   T er[B], ei[B];
   batch_phases<T>(trec + static_cast<size_t>(x) * B, trec + static_cast<size_t>(xr) * B, nrec, er, ei);
   const int x0x = wrapc(cx + rf / 2, g.L);
@@ -212,7 +253,7 @@ __global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict
     const size_t abase = (((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * nck) * g.Ns + x;
     // every accumulator of this probe is read before the arithmetic, so the
     // loads of all components are in flight together
-    double2 a[kMaxCK];
+    A a[kMaxCK];
 #pragma unroll
     for (int q = 0; q < kMaxCK; ++q)
       if (q < nck) a[q] = acc[abase + static_cast<size_t>(q) * g.Ns];
@@ -228,7 +269,7 @@ __global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict
         sr += er[j] * o[j];
         si += ei[j] * o[j];
       }
-      a[q] = make_double2(a[q].x + widen(sr), a[q].y + widen(si));
+      acc_add(a[q], sr, si);
     }
 #pragma unroll
     for (int q = 0; q < kMaxCK; ++q)
@@ -239,32 +280,40 @@ __global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict
 // ---------------------------------------------------------------------------
 // Two-level combination: for outer slab S with inner slabs j = q S + jj,
 //   acc4T += prod_jj [T]_j ,  acc4O += sum_jj [TO]_j prod_{jj' != jj} [T]_j'
+// with [.] = inner sum / n_inner, in the arithmetic of AccMath<A>.
 // ---------------------------------------------------------------------------
+template <typename A>
 __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, MeasLayout m,
-                                                 const double2* __restrict__ accT, const double2* __restrict__ accO,
-                                                 double inv_n, double2* __restrict__ acc4T,
-                                                 double2* __restrict__ acc4O) {
+                                                 const A* __restrict__ accT, const A* __restrict__ accO,
+                                                 double inv_n, A* __restrict__ acc4T, A* __restrict__ acc4O) {
+  using M = AccMath<A>;
+  using C = typename M::cplx;
+  using R = typename M::real;
+  const R in = static_cast<R>(inv_n);
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.Ns * n_outer) return;
   const int S = idx / g.Ns;
   const int x = idx - S * g.Ns;
   for (int a = 0; a < m.nR; ++a) {
-    double2 prod = make_double2(1.0, 0.0);
+    C prod = M::make(R(1), R(0));
     for (int jj = 0; jj < q; ++jj)
-      prod = cmul(prod, cscale(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x], inv_n));
-    double2* p = acc4T + (static_cast<size_t>(S) * m.nR + a) * g.Ns + x;
-    *p = cadd(*p, prod);
+      prod = cmul(prod, cscale(M::value(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x]), in));
+    A* p = acc4T + (static_cast<size_t>(S) * m.nR + a) * g.Ns + x;
+    A v = *p;
+    acc_add(v, prod.x, prod.y);
+    *p = v;
   }
-  double2 tj[kMaxSlabs], rest[kMaxSlabs];
+  C tj[kMaxSlabs], rest[kMaxSlabs];
   for (int f = 0; f < m.nrf; ++f) {
     const int a = m.rf_idx[f];
-    for (int jj = 0; jj < q; ++jj) tj[jj] = cscale(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x], inv_n);
-    double2 run = make_double2(1.0, 0.0);
+    for (int jj = 0; jj < q; ++jj)
+      tj[jj] = cscale(M::value(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x]), in);
+    C run = M::make(R(1), R(0));
     for (int jj = 0; jj < q; ++jj) {  // prefix products
       rest[jj] = run;
       run = cmul(run, tj[jj]);
     }
-    run = make_double2(1.0, 0.0);
+    run = M::make(R(1), R(0));
     for (int jj = q - 1; jj >= 0; --jj) {  // times suffix products
       rest[jj] = cmul(rest[jj], run);
       run = cmul(run, tj[jj]);
@@ -272,14 +321,16 @@ __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, Mea
     for (int b = 0; b < m.np; ++b)
       for (int ci = 0; ci < m.nc; ++ci)
         for (int k = 0; k < 2; ++k) {
-          double2 sum = make_double2(0.0, 0.0);
+          C sum = M::make(R(0), R(0));
           for (int jj = 0; jj < q; ++jj) {
-            const double2 o =
-                accO[((((static_cast<size_t>(q * S + jj) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x];
-            sum = cadd(sum, cmul(cscale(o, inv_n), rest[jj]));
+            const C o = M::value(
+                accO[((((static_cast<size_t>(q * S + jj) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x]);
+            sum = cadd(sum, cmul(cscale(o, in), rest[jj]));
           }
-          double2* p = acc4O + ((((static_cast<size_t>(S) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
-          *p = cadd(*p, sum);
+          A* p = acc4O + ((((static_cast<size_t>(S) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
+          A v = *p;
+          acc_add(v, sum.x, sum.y);
+          *p = v;
         }
   }
 }
@@ -292,61 +343,103 @@ __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, Mea
 //                           R_s = prod_{s' != s} [T]_{s'} (prefix x suffix),
 //                           j = (b * nc + ci) * 2 + k
 // k_products_P: grid (sites, nr + nrf); k_products_W: grid (sites, nrf,
-// chunks of kWChunk values of j).
+// chunks of kWChunk values of j).  FP64 sums: products of the raw sums, one
+// factor (1/n)^nslab at the end.  FP32 sums: every factor scaled by 1/n as it
+// is read, so no nslab over- or underflows binary32; the per-warp partials
+// are written in double.
 // ---------------------------------------------------------------------------
 constexpr int kWChunk = 12;
 
-__global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayout m, const double2* __restrict__ accT,
+template <typename M>
+__device__ __forceinline__ typename M::cplx slab_factor(typename M::cplx t, typename M::real in) {
+  if constexpr (M::fp64)
+    return t;
+  else
+    return cscale(t, in);
+}
+template <typename M>
+__device__ __forceinline__ typename M::real final_scale(int nslab, double inv_n) {
+  if constexpr (M::fp64) {
+    double scale = 1.0;
+    for (int s = 0; s < nslab; ++s) scale *= inv_n;
+    return scale;
+  } else {
+    return static_cast<float>(inv_n);  // the one factor of [TO] (W); P(r) passes 1
+  }
+}
+
+template <typename A>
+__global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT,
                                                     double inv_n, double2* __restrict__ partial, int nwarps) {
+  using M = AccMath<A>;
+  using C = typename M::cplx;
+  using R = typename M::real;
+  const R in = static_cast<R>(inv_n);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = x < g.Ns;
   const int o = blockIdx.y;
   const int a = o < m.nr ? m.r_idx[o] : m.rf_idx[o - m.nr];
-  double2 prod = make_double2(live ? 1.0 : 0.0, 0.0);
+  C prod = M::make(live ? R(1) : R(0), R(0));
   if (live)
-    for (int s = 0; s < nslab; ++s) prod = cmul(prod, accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]);
-  // (1/n)^nslab applied once
-  double scale = 1.0;
-  for (int s = 0; s < nslab; ++s) scale *= inv_n;
-  prod = warp_sum(cscale(prod, scale));
-  if ((threadIdx.x & 31) == 0) partial[static_cast<size_t>(o) * nwarps + (x >> 5)] = prod;
+    for (int s = 0; s < nslab; ++s)
+      prod = cmul(prod, slab_factor<M>(M::value(accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]), in));
+  if constexpr (M::fp64) prod = cscale(prod, final_scale<M>(nslab, inv_n));
+  prod = warp_sum(prod);
+  if ((threadIdx.x & 31) == 0)
+    partial[static_cast<size_t>(o) * nwarps + (x >> 5)] = make_double2(prod.x, prod.y);
 }
 
-__global__ void __launch_bounds__(256) k_products_W(Geom g, int nslab, MeasLayout m, const double2* __restrict__ accT,
-                                                    const double2* __restrict__ accO, double inv_n,
+// One thread: site x, field separation f, kWChunk values of j.  Suffix
+// products are formed once from the top slab down; the loop over slabs then
+// keeps the prefix product running and reads the kWChunk [TO] sums of each
+// slab together.
+template <typename A>
+__global__ void __launch_bounds__(256) k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT,
+                                                    const A* __restrict__ accO, double inv_n,
                                                     double2* __restrict__ partial, int nwarps) {
+  using M = AccMath<A>;
+  using C = typename M::cplx;
+  using R = typename M::real;
+  const R in = static_cast<R>(inv_n);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = x < g.Ns;
   const int f = blockIdx.y;
   const int nW = m.np * m.nc * 2;
   const int j0 = blockIdx.z * kWChunk;
-  const int j1 = min(nW, j0 + kWChunk);
-  double2 rest[kMaxSlabs];
+  const int nj = min(nW - j0, kWChunk);
+  C sum[kWChunk];
+#pragma unroll
+  for (int q = 0; q < kWChunk; ++q) sum[q] = M::make(R(0), R(0));
   if (live) {
-    const int a = m.rf_idx[f];
-    double2 run = make_double2(1.0, 0.0);
-    for (int s = 0; s < nslab; ++s) {  // prefix products
-      rest[s] = run;
-      run = cmul(run, accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]);
+    const size_t tstride = static_cast<size_t>(m.nR) * g.Ns;  // slab stride of accT
+    const A* tcol = accT + static_cast<size_t>(m.rf_idx[f]) * g.Ns + x;
+    C suf[kMaxSlabs];  // suf[s] = prod_{s' > s} [T]_{s'}
+    C run = M::make(R(1), R(0));
+    for (int s = nslab - 1; s >= 0; --s) {
+      suf[s] = run;
+      run = cmul(run, slab_factor<M>(M::value(tcol[s * tstride]), in));
     }
-    run = make_double2(1.0, 0.0);
-    for (int s = nslab - 1; s >= 0; --s) {  // times suffix products
-      rest[s] = cmul(rest[s], run);
-      run = cmul(run, accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]);
+    run = M::make(R(1), R(0));  // prod_{s' < s} [T]_{s'}
+    for (int s = 0; s < nslab; ++s) {
+      const C rest = cmul(run, suf[s]);
+      const A* ocol = accO + (static_cast<size_t>(s * m.nrf + f) * nW + j0) * g.Ns + x;
+      A o[kWChunk];
+#pragma unroll
+      for (int q = 0; q < kWChunk; ++q)
+        if (q < nj) o[q] = ocol[static_cast<size_t>(q) * g.Ns];
+#pragma unroll
+      for (int q = 0; q < kWChunk; ++q)
+        if (q < nj) sum[q] = cadd(sum[q], cmul(M::value(o[q]), rest));
+      run = cmul(run, slab_factor<M>(M::value(tcol[s * tstride]), in));
     }
   }
-  double scale = 1.0;  // [TO] and nslab - 1 factors [T]: (1/n)^nslab
-  for (int s = 0; s < nslab; ++s) scale *= inv_n;
-  for (int j = j0; j < j1; ++j) {
-    double2 sum = make_double2(0.0, 0.0);
-    if (live)
-      for (int s = 0; s < nslab; ++s) {
-        const double2 o = accO[((static_cast<size_t>(s) * m.nrf + f) * nW + j) * g.Ns + x];
-        sum = cadd(sum, cmul(o, rest[s]));
-      }
-    sum = warp_sum(cscale(sum, scale));
+  const R scale = final_scale<M>(nslab, inv_n);
+#pragma unroll
+  for (int q = 0; q < kWChunk; ++q) {
+    if (q >= nj) break;
+    const C w = warp_sum(cscale(sum[q], scale));
     if ((threadIdx.x & 31) == 0)
-      partial[static_cast<size_t>(m.nr + m.nrf + f * nW + j) * nwarps + (x >> 5)] = sum;
+      partial[static_cast<size_t>(m.nr + m.nrf + f * nW + j0 + q) * nwarps + (x >> 5)] = make_double2(w.x, w.y);
   }
 }
 
@@ -519,25 +612,44 @@ void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const L
   }
 }
 
-void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, const double2* accT, const double2* accO,
-                    double inv_n, double2* acc4T, double2* acc4O, cudaStream_t s) {
+void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, bool pairs, const void* accT,
+                    const void* accO, double inv_n, void* acc4T, void* acc4O, cudaStream_t s) {
   const int nb = blocks_for(static_cast<long long>(g.Ns) * n_outer, 256);
-  k_combine<<<nb, 256, 0, s>>>(g, n_outer, q, m, accT, accO, inv_n, acc4T, acc4O);
+  if (pairs)
+    k_combine<float4><<<nb, 256, 0, s>>>(g, n_outer, q, m, static_cast<const float4*>(accT),
+                                         static_cast<const float4*>(accO), inv_n, static_cast<float4*>(acc4T),
+                                         static_cast<float4*>(acc4O));
+  else
+    k_combine<double2><<<nb, 256, 0, s>>>(g, n_outer, q, m, static_cast<const double2*>(accT),
+                                          static_cast<const double2*>(accO), inv_n, static_cast<double2*>(acc4T),
+                                          static_cast<double2*>(acc4O));
   count_launches(1);
 }
 
-void launch_products(const Geom& g, int nslab, const MeasLayout& m, const double2* accT, const double2* accO,
-                     double inv_n, double2* partial, double* rec, cudaStream_t s) {
-  const int nb = blocks_for(g.Ns, 256);
-  const int nwarps = nb * 8;
-  k_products_P<<<dim3(nb, m.nr + m.nrf), 256, 0, s>>>(g, nslab, m, accT, inv_n, partial, nwarps);
+template <typename A>
+static void products_of(const Geom& g, int nslab, const MeasLayout& m, const A* accT, const A* accO, double inv_n,
+                        double2* partial, int nb, int nwarps, cudaStream_t s) {
+  k_products_P<A><<<dim3(nb, m.nr + m.nrf), 256, 0, s>>>(g, nslab, m, accT, inv_n, partial, nwarps);
   count_launches(1);
   const int nW = m.np * m.nc * 2;
   if (m.nrf > 0 && nW > 0) {
-    k_products_W<<<dim3(nb, m.nrf, (nW + kWChunk - 1) / kWChunk), 256, 0, s>>>(g, nslab, m, accT, accO, inv_n,
-                                                                               partial, nwarps);
+    k_products_W<A><<<dim3(nb, m.nrf, (nW + kWChunk - 1) / kWChunk), 256, 0, s>>>(g, nslab, m, accT, accO, inv_n,
+                                                                                  partial, nwarps);
     count_launches(1);
   }
+}
+
+void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, const void* accO,
+                     double inv_n, double2* partial, double* rec, cudaStream_t s) {
+  const int nb = blocks_for(g.Ns, 256);
+  const int nwarps = nb * 8;
+  if (pairs)
+    products_of(g, nslab, m, static_cast<const float4*>(accT), static_cast<const float4*>(accO), inv_n, partial, nb,
+                nwarps, s);
+  else
+    products_of(g, nslab, m, static_cast<const double2*>(accT), static_cast<const double2*>(accO), inv_n, partial,
+                nb, nwarps, s);
+  const int nW = m.np * m.nc * 2;
   const int nout = m.nr + m.nrf + m.nrf * nW;
   k_finalize_products<<<blocks_for(nout, 128), 128, 0, s>>>(partial, nwarps, g, m, rec);
   count_launches(1);

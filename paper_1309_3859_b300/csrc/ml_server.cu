@@ -194,12 +194,12 @@ void end_of_measurement(ml_server* s, Job* j) {
   double* out = j->rec_dev + static_cast<size_t>(j->meas) * L->meas.rec_len;
   int ncfg;
   if (j->p.outer_slab) {
-    launch_products(L->g, L->g.Nt / j->p.outer_slab, L->meas, L->acc4T, L->acc4O, 1.0 / j->p.n_sub_outer,
-                    L->partial, out, e->stream);
+    launch_products(L->g, L->g.Nt / j->p.outer_slab, L->meas, !e->fp64, L->acc4T, L->acc4O,
+                    1.0 / j->p.n_sub_outer, L->partial, out, e->stream);
     ncfg = j->p.n_sub * j->p.n_sub_outer;
   } else {
-    launch_products(L->g, L->g.Nt / j->p.slab, L->meas, L->accT, L->accO, 1.0 / j->p.n_sub, L->partial, out,
-                    e->stream);
+    launch_products(L->g, L->g.Nt / j->p.slab, L->meas, !e->fp64, L->accT, L->accO, 1.0 / j->p.n_sub, L->partial,
+                    out, e->stream);
     ncfg = j->p.n_sub;
   }
   launch_write_vac(L->vac_acc, 1.0 / ncfg, L->meas, out, e->stream);
@@ -229,8 +229,8 @@ void advance(ml_server* s, Job* j) {
     case kInner:
       if (++j->sub == j->p.n_sub) {
         if (j->p.outer_slab) {
-          launch_combine(L->g, L->g.Nt / j->p.outer_slab, j->p.outer_slab / j->p.slab, L->meas, L->accT, L->accO,
-                         1.0 / j->p.n_sub, L->acc4T, L->acc4O, e->stream);
+          launch_combine(L->g, L->g.Nt / j->p.outer_slab, j->p.outer_slab / j->p.slab, L->meas, !e->fp64,
+                         L->accT, L->accO, 1.0 / j->p.n_sub, L->acc4T, L->acc4O, e->stream);
           if (++j->outer < j->p.n_sub_outer)
             j->phase = kOuter;
           else
