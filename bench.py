@@ -260,7 +260,7 @@ def batched_point(ml, steps=3, warmup=1):
         upd += (p.k_between * 4 * V + p.n_sub * (V + 3 * V * (p.slab - 1) // p.slab)) * (1 + p.n_or)
     return {"workload": "batched-64-lattices-fp32", "lattices": len(ps), "ms_per_step": ms,
             "link_updates_per_s": upd / (ms * 1e-3), "measurements_per_s": len(ps) / (ms * 1e-3),
-            "sweep_impl": ["persistent", "per-pass"][mode], "step": "one measurement of every lattice"}
+            "sweep_impl": ["persistent", "per-pass", "resident"][mode], "step": "one measurement of every lattice"}
 
 
 def serving_request(ml, L, Nt, beta, seed):
@@ -377,7 +377,7 @@ def run_gpu(args, w, rank, world):
     # slab sub-update is one launch of the sweep kernel with the record fused
     per_step = {
         "subupdate": (ml.ML_K_SUBUPDATE, w.n_sub),
-        "full_sweeps": (ml.ML_K_SWEEP, w.k_between),
+        "full_sweeps": (ml.ML_K_FULLSWEEP, w.k_between),
         "accumulate": (ml.ML_K_ACCUMULATE, n_folds),
         "products": (ml.ML_K_PRODUCTS, 1),
     }
@@ -387,7 +387,8 @@ def run_gpu(args, w, rank, world):
     peak, peak_kind = measured_peaks()
     nbytes = algorithmic_bytes(w, "sweep" if dominant == "subupdate" else dominant, nB)
     achieved = nbytes / (kms[dominant] * 1e-3) / 1e9
-    impl = ["k_sweeps_table (persistent, record fused)", "k_pass_table + k_record_table"][lat.sweep_mode]
+    impl = ["k_sweeps_table (persistent, record fused)", "k_pass_table + k_record_table",
+            "k_sweeps_resident (cluster-resident slabs, record fused)"][lat.sweep_mode]
     roof = {"kernel": {"subupdate": impl, "accumulate": "k_accum_T_table + k_accum_O_table"}[dominant], "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,

@@ -198,8 +198,11 @@ typedef enum {
   ML_K_ACCUMULATE = 3, /* fold of a full batch of records into the slab sums      */
   ML_K_PRODUCTS = 4,   /* cross-slab products and their reduction over sites      */
   ML_K_SWEEP = 5,      /* one compound slab sweep (the handle's implementation)   */
-  ML_K_SUBUPDATE = 6   /* one slab sub-update as measurements run it: compound
-                          sweep and record (fused in the persistent kernel)     */
+  ML_K_SUBUPDATE = 6,  /* one slab sub-update as measurements run it: compound
+                          sweep and record (fused in the persistent and
+                          resident kernels)                                     */
+  ML_K_FULLSWEEP = 7   /* one compound sweep without frozen links, as between
+                          measurements and in ml_thermalize                     */
 } ml_kernel_class;
 
 /* Average device time in milliseconds of `reps` back-to-back launches of one
@@ -209,13 +212,21 @@ typedef enum {
  * left undefined (every measurement clears them first).  Blocking. */
 int ml_kernel_timing(ml_lattice *h, int kernel, int reps, double *avg_ms);
 
-/* Implementations of the compound sweep.  ml_create times both on the
- * handle's lattice and keeps the faster; results are identical. */
+/* Implementations of the compound sweep.  ml_create times the available
+ * ones on the handle's lattices and keeps the fastest; results are
+ * bit-identical. */
 typedef enum {
   ML_SWEEP_PERSISTENT = 0, /* one cooperative persistent kernel, grid barrier
                               (bounded spin) between passes                   */
-  ML_SWEEP_PASSES = 1      /* one kernel per (direction, parity) pass, replayed
+  ML_SWEEP_PASSES = 1,     /* one kernel per (direction, parity) pass, replayed
                               from a CUDA graph                               */
+  ML_SWEEP_RESIDENT = 2    /* slab sub-updates: one thread-block cluster per
+                              time slab keeps the slab's links in distributed
+                              shared memory, hardware cluster barrier between
+                              passes; available when a slab fits the cluster's
+                              shared memory (else ML_EINVAL when forced).
+                              Sweeps without frozen links run as the faster of
+                              the other two.                                  */
 } ml_sweep_impl;
 
 /* Query or force the compound-sweep implementation (forcing re-captures the

@@ -179,7 +179,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
     L->theta_rec[b] = lat_alloc(e, L, L->trec_bytes);
   }
   L->nparts = vac_part_count(g, p->slab);
-  L->vac_part = static_cast<double*>(lat_alloc(e, L, static_cast<size_t>(L->nparts) * 12 * sizeof(double)));
+  L->vac_part = static_cast<double*>(lat_alloc(e, L, static_cast<size_t>(L->nparts) * 2 * nc * sizeof(double)));
   L->vac_acc = static_cast<double*>(lat_alloc(e, L, 12 * sizeof(double)));
   const size_t nw = static_cast<size_t>(product_partial_count(g));
   const size_t nout = static_cast<size_t>(nr) + nrf + static_cast<size_t>(nrf) * np * nc * 2;
@@ -241,8 +241,6 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
     ce = cudaMemcpyAsync(L->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L->d_n, 0, sizeof(unsigned long long), s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), s);
-  if (ce == cudaSuccess)
-    ce = cudaMemsetAsync(L->vac_part, 0, static_cast<size_t>(L->nparts) * 12 * sizeof(double), s);
   // ring slots not yet written in a batch are multiplied by zero: keep them finite
   for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
     ce = cudaMemsetAsync(L->osum[b], 0, L->osum_bytes, s);
@@ -255,12 +253,33 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
 }
 
 // --------------------------------------------------------------------------- schedule pieces
-int enqueue_sweeps_table(Engine* e, const LatDesc* table, int n, int mask, int mode) {
+// the cluster-resident plan for slab thickness mask, if it is available
+const ResidentPlan* resident_plan(const Engine* e, int mask) {
+  if (mask > 0 && mask == e->res_inner.mask && e->res_inner.cs > 0) return &e->res_inner;
+  if (mask > 0 && mask == e->res_outer.mask && e->res_outer.cs > 0) return &e->res_outer;
+  return nullptr;
+}
+
+// n compound sweeps with frozen-link mask `mask` (0: none) of every lattice
+// of `table` in implementation `mode`, optionally recording the result into
+// ring slot (buf, slot) with its vacuum sums (main stream)
+int enqueue_sweeps_mode(Engine* e, const LatDesc* table, int n, int mask, int mode, bool record, int buf, int slot) {
   if (n <= 0) return ML_OK;
+  if (mode == ML_SWEEP_RESIDENT) {
+    if (const ResidentPlan* p = resident_plan(e, mask))
+      return launch_sweeps_resident(e->fp64, *p, table, e->td.nlat, e->n_or, n, e->d_err, e->stream, record, buf, slot)
+                 ? ML_ECUDA
+                 : ML_OK;
+    mode = e->full_mode;
+  }
   return launch_sweeps_table(e->fp64, mode == ML_SWEEP_PERSISTENT, table, e->d_tile_lat, e->td, nullptr, mask,
-                             e->n_or, n, e->d_err, e->bar, e->stream)
+                             e->n_or, n, e->d_err, e->bar, e->stream, record, buf, slot)
              ? ML_ECUDA
              : ML_OK;
+}
+
+int enqueue_sweeps_table(Engine* e, const LatDesc* table, int n, int mask, int mode) {
+  return enqueue_sweeps_mode(e, table, n, mask, mode, false, 0, 0);
 }
 
 int enqueue_sweeps(Engine* e, int n, int mask) { return enqueue_sweeps_table(e, e->d_desc, n, mask, e->sweep_mode); }
@@ -269,10 +288,7 @@ int enqueue_sweeps(Engine* e, int n, int mask) { return enqueue_sweeps_table(e, 
 // then the record of the new configuration into slot (buf, slot) and its
 // vacuum sums (main stream)
 int enqueue_sub_update(Engine* e, int buf, int slot) {
-  return launch_sweeps_table(e->fp64, e->sweep_mode == ML_SWEEP_PERSISTENT, e->d_desc, e->d_tile_lat, e->td, nullptr,
-                             e->slab, e->n_or, 1, e->d_err, e->bar, e->stream, true, buf, slot)
-             ? ML_ECUDA
-             : ML_OK;
+  return enqueue_sweeps_mode(e, e->d_desc, 1, e->slab, e->sweep_mode, true, buf, slot);
 }
 
 int join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
@@ -352,6 +368,23 @@ int hand_over(Engine* e, int buf, int nrec) {
 // buffer is reused only after its previous fold has finished
 int run_inner_loop(Engine* e) {
   int buf = e->cur_buf, slot = 0;
+  if (const ResidentPlan* p = e->sweep_mode == ML_SWEEP_RESIDENT ? resident_plan(e, e->slab) : nullptr) {
+    // one cluster-resident launch per ring buffer: the sweeps keep their
+    // SMs, the previous buffer's fold runs on the others
+    for (int i = 0; i < e->n_sub;) {
+      const int cnt = std::min(e->nB, e->n_sub - i);
+      ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
+      if (launch_sweeps_resident(e->fp64, *p, e->d_desc, e->td.nlat, e->n_or, 1, e->d_err, e->stream, true, buf, 0,
+                                 cnt))
+        return ML_ECUDA;
+      int st = hand_over(e, buf, cnt);
+      if (st) return st;
+      buf ^= 1;
+      i += cnt;
+    }
+    e->cur_buf = buf;
+    return ML_OK;
+  }
   ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
   for (int i = 0; i < e->n_sub; ++i) {
     int st = launch_graph(e, e->g_sub[buf][slot]);
@@ -421,10 +454,10 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
     for (int li = 0; li < nlat; ++li) {
       LatState* L = e->lats[li];
       launch_naive_and_plaquette(e->fp64, L->theta, L->g, L->meas, L->partial_naive, out[li], e->stream);
-      ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->stream));
     }
     st = join(e->stream, e->side, e->ev_main);  // records cleared before the products write them
     if (st) return st;
+    for (LatState* L : e->lats) ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->side));
     int ncfg = 0;
     if (e->outer_slab == 0) {
       st = zero_inner(e, e->side);
@@ -458,7 +491,7 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       ncfg = e->n_sub * e->n_sub_outer;
     }
     for (int li = 0; li < nlat; ++li)
-      launch_write_vac(e->lats[li]->vac_acc, 1.0 / ncfg, e->lats[li]->meas, out[li], e->stream);
+      launch_write_vac(e->lats[li]->vac_acc, 1.0 / ncfg, e->lats[li]->meas, out[li], e->side);
   }
   st = join(e->side, e->stream, e->ev_side);  // results complete in stream order on the main stream
   if (st) return st;
@@ -513,42 +546,71 @@ int refresh_scratch(Engine* e) {
   return ML_OK;
 }
 
-// Autotuning of the sweep implementation: time one compound slab sweep of the
-// table as the persistent cooperative kernel and as a captured graph of
-// per-pass kernels (on the timing copies), alternating the candidates over
-// several rounds (the clocks may still be ramping up), and keep the faster.
-// Small tables are latency-bound and favour the persistent kernel; large ones
-// favour the per-pass kernels' full occupancy.
+// Cluster-resident plans for the inner and the outer slab thickness, with
+// their unit lists and finished-unit counters on the device.
+int plan_resident_sweeps(Engine* e) {
+  std::vector<Geom> geoms;
+  for (LatState* L : e->lats) geoms.push_back(L->g);
+  for (ResidentPlan* p : {&e->res_inner, &e->res_outer}) {
+    const int mask = p == &e->res_inner ? e->slab : e->outer_slab;
+    std::vector<int4> units;
+    plan_resident(e->fp64, geoms.data(), static_cast<int>(geoms.size()), mask, p, &units);
+    if (p->cs == 0) continue;
+    int4* d_units = static_cast<int4*>(dev_alloc(e, units.size() * sizeof(int4)));
+    p->done = static_cast<unsigned long long*>(dev_alloc(e, sizeof(unsigned long long)));
+    if (!d_units || !p->done) return ML_ENOMEM;
+    ML_CUDA(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice, e->stream));
+    ML_CUDA(cudaMemsetAsync(p->done, 0, sizeof(unsigned long long), e->stream));
+    p->units = d_units;
+  }
+  ML_CUDA(cudaStreamSynchronize(e->stream));
+  return ML_OK;
+}
+
+// Autotuning of the sweep implementation: time one slab sub-update (compound
+// sweep and record) of the table as the persistent cooperative kernel, as a
+// captured graph of per-pass kernels and, when the slabs fit, as the
+// cluster-resident kernel (on the timing copies; the records land in ring
+// slots that every measurement rewrites before use), alternating the
+// candidates over several rounds (the clocks may still be ramping up), and
+// keep the fastest.  Small tables are latency-bound and favour the persistent
+// or resident kernels; large ones the per-pass kernels' full occupancy.
 int choose_sweep_mode(Engine* e) {
   int st = ensure_scratch(e);
   if (!st) st = refresh_scratch(e);
   if (st) return st;
+  const LatDesc* tab = e->d_desc_scratch;
+  const bool resident = resident_plan(e, e->slab) != nullptr;
   Graph pp;
-  st = capture(e, &pp, [&] { return enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, ML_SWEEP_PASSES); });
+  st = capture(e, &pp, [&] { return enqueue_sweeps_mode(e, tab, 1, e->slab, ML_SWEEP_PASSES, true, 0, 0); });
   if (st) return st;
-  cudaEvent_t ev[3];
+  auto run = [&](int mode) {
+    return mode == ML_SWEEP_PASSES ? launch_graph(e, pp)
+                                   : enqueue_sweeps_mode(e, tab, 1, e->slab, mode, true, 0, 0);
+  };
+  const int nmodes = resident ? 3 : 2;
+  cudaEvent_t ev[4];
   for (cudaEvent_t& x : ev) ML_CUDA(cudaEventCreate(&x));
   const int rounds = 4, reps = 2;
-  float best[2] = {1e30f, 1e30f};
-  st = enqueue_sweeps_table(e, e->d_desc_scratch, 2, e->slab, ML_SWEEP_PERSISTENT);  // warm-up
-  if (!st) st = launch_graph(e, pp);
+  float best[3] = {1e30f, 1e30f, 1e30f};
+  for (int m = 0; m < nmodes && !st; ++m) st = run(m);  // warm-up
   for (int r = 0; r < rounds && !st; ++r) {
     st = cuda_status(cudaEventRecord(ev[0], e->stream));
-    for (int i = 0; i < reps && !st; ++i)
-      st = enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, ML_SWEEP_PERSISTENT);
-    if (!st) st = cuda_status(cudaEventRecord(ev[1], e->stream));
-    for (int i = 0; i < reps && !st; ++i) st = launch_graph(e, pp);
-    if (!st) st = cuda_status(cudaEventRecord(ev[2], e->stream));
-    if (!st) st = cuda_status(cudaEventSynchronize(ev[2]));
-    if (!st) {
-      float a = 0.f, b = 0.f;
-      cudaEventElapsedTime(&a, ev[0], ev[1]);
-      cudaEventElapsedTime(&b, ev[1], ev[2]);
-      best[0] = std::min(best[0], a);
-      best[1] = std::min(best[1], b);
+    for (int m = 0; m < nmodes && !st; ++m) {
+      for (int i = 0; i < reps && !st; ++i) st = run(m);
+      if (!st) st = cuda_status(cudaEventRecord(ev[m + 1], e->stream));
+    }
+    if (!st) st = cuda_status(cudaEventSynchronize(ev[nmodes]));
+    for (int m = 0; m < nmodes && !st; ++m) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[m], ev[m + 1]);
+      best[m] = std::min(best[m], ms);
     }
   }
-  if (!st) e->sweep_mode = best[1] < best[0] ? ML_SWEEP_PASSES : ML_SWEEP_PERSISTENT;
+  if (!st) {
+    e->full_mode = best[ML_SWEEP_PASSES] < best[ML_SWEEP_PERSISTENT] ? ML_SWEEP_PASSES : ML_SWEEP_PERSISTENT;
+    e->sweep_mode = (resident && best[ML_SWEEP_RESIDENT] < best[e->full_mode]) ? ML_SWEEP_RESIDENT : e->full_mode;
+  }
   for (cudaEvent_t& x : ev) cudaEventDestroy(x);
   cudaGraphExecDestroy(pp.exec);
   if (st) return st;
@@ -594,14 +656,16 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
     e->alloc = *alloc;
     e->use_alloc = true;
   }
+  // the sweeps (main stream) own the critical path: highest priority; the
+  // folds (accumulation stream) fill the SMs the sweeps leave free
+  int lo = 0, hi = 0;
+  ML_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
   if (cuda_stream) {
     e->stream = static_cast<cudaStream_t>(cuda_stream);
   } else {
-    ML_CUDA(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+    ML_CUDA(cudaStreamCreateWithPriority(&e->stream, cudaStreamNonBlocking, hi));
     e->own_stream = true;
   }
-  int lo = 0, hi = 0;
-  ML_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
   ML_CUDA(cudaStreamCreateWithPriority(&e->side, cudaStreamNonBlocking, lo));
   for (cudaEvent_t* x : {&e->ev_rec[0], &e->ev_rec[1], &e->ev_fold[0], &e->ev_fold[1], &e->ev_main, &e->ev_side})
     ML_CUDA(cudaEventCreateWithFlags(x, cudaEventDisableTiming));
@@ -631,6 +695,8 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
     td.max_y_T = std::max(td.max_y_T, d.nslab * m.nR);
     if (m.nrf > 0 && m.np > 0 && m.nc > 0)
       td.max_y_O = std::max(td.max_y_O, d.nslab * m.nrf * fold_probe_groups(m.np));
+    td.max_vac_blocks = std::max(td.max_vac_blocks, d.nparts);
+    td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
   }
   td.nlat = n;
   td.total_tiles = static_cast<int>(tile_lat.size());
@@ -641,7 +707,8 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
   ML_CUDA(cudaMemcpyAsync(e->d_tile_lat, tile_lat.data(), tile_lat.size() * sizeof(int), cudaMemcpyHostToDevice,
                           e->stream));
   ML_CUDA(cudaStreamSynchronize(e->stream));
-  int st = choose_sweep_mode(e);
+  int st = plan_resident_sweeps(e);
+  if (!st) st = choose_sweep_mode(e);
   if (!st) st = capture_graphs(e);
   return st;
 }
@@ -649,7 +716,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
 int thermalize_engine(Engine* e, int n_sweeps) {
   if (n_sweeps < 0) return ML_EINVAL;
   int st = ML_OK;
-  if (e->sweep_mode == ML_SWEEP_PERSISTENT)
+  if (e->full_mode == ML_SWEEP_PERSISTENT)
     st = enqueue_sweeps(e, n_sweeps, 0);
   else
     for (int i = 0; i < n_sweeps && !st; ++i) st = launch_graph(e, e->g_one_full);
@@ -681,12 +748,14 @@ int get_angles(Engine* e, LatState* L, double* theta_host, size_t n) {
 }
 
 int set_sweep_mode(Engine* e, int mode) {
-  if (mode != ML_SWEEP_PERSISTENT && mode != ML_SWEEP_PASSES) return ML_EINVAL;
+  if (mode != ML_SWEEP_PERSISTENT && mode != ML_SWEEP_PASSES && mode != ML_SWEEP_RESIDENT) return ML_EINVAL;
+  if (mode == ML_SWEEP_RESIDENT && !resident_plan(e, e->slab)) return ML_EINVAL;
   int st = check_errors(e);
   if (st) return st;
   if (mode == e->sweep_mode) return ML_OK;
   destroy_graphs(e);
   e->sweep_mode = mode;
+  if (mode != ML_SWEEP_RESIDENT) e->full_mode = mode;
   return capture_graphs(e);
 }
 
@@ -878,7 +947,7 @@ int ml_batch_slots(ml_lattice* h, int* n) {
 }
 
 int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
-  if (!h || !avg_ms || reps < 1 || kernel < ML_K_HEATBATH || kernel > ML_K_SUBUPDATE) return ML_EINVAL;
+  if (!h || !avg_ms || reps < 1 || kernel < ML_K_HEATBATH || kernel > ML_K_FULLSWEEP) return ML_EINVAL;
   Engine* e = &h->e;
   LatState* L = h->L();
   int st = ensure_scratch(e);
@@ -910,11 +979,11 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
       case ML_K_SWEEP:
         st = enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, e->sweep_mode);
         break;
+      case ML_K_FULLSWEEP:
+        st = enqueue_sweeps_table(e, e->d_desc_scratch, 1, 0, e->full_mode);
+        break;
       default:
-        st = launch_sweeps_table(e->fp64, e->sweep_mode == ML_SWEEP_PERSISTENT, e->d_desc_scratch, e->d_tile_lat,
-                                 e->td, nullptr, e->slab, e->n_or, 1, e->d_err, e->bar, e->stream, true, 0, 0)
-                 ? ML_ECUDA
-                 : ML_OK;
+        st = enqueue_sweeps_mode(e, e->d_desc_scratch, 1, e->slab, e->sweep_mode, true, 0, 0);
     }
   }
   ML_CUDA(cudaEventRecord(e1, e->stream));

@@ -59,7 +59,9 @@ struct Engine {
   TableDims td{};
   int* d_err = nullptr;
   unsigned long long* bar = nullptr;  // grid-barrier counter of the persistent sweeps
-  int sweep_mode = ML_SWEEP_PERSISTENT;
+  int sweep_mode = ML_SWEEP_PERSISTENT;  // implementation of the slab sub-updates
+  int full_mode = ML_SWEEP_PERSISTENT;   // of sweeps the resident kernels cannot run (no frozen links)
+  ResidentPlan res_inner, res_outer;     // cluster-resident plans for slab and outer_slab
   int nB = kBatchMax, cur_buf = 0;  // ring slots (rec_batch of the precision)
   cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_fold[2] = {nullptr, nullptr};
   cudaEvent_t ev_main = nullptr, ev_side = nullptr;

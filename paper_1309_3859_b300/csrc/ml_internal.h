@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "ml_device.cuh"
 
 namespace ml {
@@ -40,9 +42,9 @@ struct LatDesc {
   void* osum[2];              // [nslab][nc][2][Ns][slots], slots = rec_batch(fp64)
   double2* accT;              // inner slab sums: double2 (re, im), or for FP32
   double2* accO;              //   lattices float4 (re_hi, re_lo, im_hi, im_lo)
-  double* vac_part;           // [nparts][12] warp partials of the vacuum sums
-  int nparts;
-  double* vac_acc;            // [12]
+  double* vac_part;           // [nc * 2][nparts] block partials of the vacuum sums of a fold
+  int nparts;                 // vacuum blocks per part (vac_part_count)
+  double* vac_acc;            // [12] vacuum sums of the folded configurations
 };
 
 // Per-lattice control of one step of the request-serving engine; schedules
@@ -60,11 +62,13 @@ struct LatCtl {
 struct TableDims {
   int nlat;
   int total_tiles;
-  int max_blocks_rec;   // ceil(Ns * nslab / 256)
+  int max_blocks_rec;   // blocks of 256 threads for record_warps() warps
   int max_nc1;          // nc + 1
   int max_blocks_site;  // ceil(Ns / 256)
   int max_y_T;          // nslab * nR
   int max_y_O;          // nslab * nrf * probe groups
+  int max_vac_blocks;   // vac_part_count
+  int max_vac_parts;    // nc * 2
 };
 
 constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep kernels)
@@ -76,16 +80,16 @@ constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep k
 // kernel per pass.  tile_lat[t] is the lattice of sweep tile t.  Returns 0 or
 // -1 when a launch fails.
 // With `record`, the new configurations are then recorded into ring slot
-// (rec_buf, rec_slot) (or per lattice from ctl) and their vacuum sums
-// accumulated, exactly as launch_record_table does.
+// (rec_buf, rec_slot) (or per lattice from ctl), exactly as
+// launch_record_table does.
 int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int* tile_lat, const TableDims& td,
                         const LatCtl* ctl, int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
                         cudaStream_t s, bool record = false, int rec_buf = 0, int rec_slot = 0);
-// record of each lattice's configuration into ring slot (buf, slot) and its
-// vacuum partials; then vac_acc += site means
+// record of each lattice's configuration into ring slot (buf, slot)
 void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
                          cudaStream_t s);
-// fold slots 0 .. nrec-1 of ring buffer buf into each lattice's slab sums
+// fold slots 0 .. nrec-1 of ring buffer buf into each lattice's slab sums,
+// and their vacuum sums into vac_acc
 void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
                        cudaStream_t s);
 int record_blocks(const Geom& g, int d);
@@ -121,6 +125,27 @@ void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, con
 void launch_write_vac(const double* vac_acc, double inv_ncfg, const MeasLayout& m, double* rec, cudaStream_t s);
 void launch_connected(const double* recs, int n_meas, const MeasLayout& m, double beta, double* out,
                       cudaStream_t s);
+
+// ---- cluster-resident slab sub-updates (ml_resident.cu) ----
+// One thread-block cluster per (lattice, slab) unit keeps the unit's links in
+// the shared memory of its CTAs for a whole launch of slab sweeps.
+struct ResidentPlan {
+  int mask = 0;                        // slab thickness d of the sweeps
+  int cs = 0;                          // CTAs per cluster; 0: the table does not fit
+  size_t smem = 0;                     // dynamic shared memory per CTA
+  int nunits = 0;                      // (lattice, slab) units = clusters launched
+  const int4* units = nullptr;         // device [nunits] (lattice, slab, ny, nz bricks)
+  unsigned long long* done = nullptr;  // finished-unit counter (zero between launches)
+};
+// Fills everything but the device pointers; the host list of units goes to
+// `units` (empty when cs = 0).
+void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, ResidentPlan* p, std::vector<int4>* units);
+// n_rec rounds of n_compound compound slab sweeps (mask p.mask) of every
+// lattice of the table, each optionally followed by the record into ring slot
+// (rec_buf, rec_slot + round): n_rec sub-updates as n_rec calls of
+// launch_sweeps_table would run them, in one launch.  Returns 0 or -1.
+int launch_sweeps_resident(bool fp64, const ResidentPlan& p, const LatDesc* d, int nlat, int n_or, int n_compound,
+                           int* err, cudaStream_t s, bool record, int rec_buf, int rec_slot, int n_rec = 1);
 
 // kernels launched so far (process-wide)
 void count_launches(uint64_t n);

@@ -1,0 +1,156 @@
+// The link update itself: heatbath and overrelaxation of one U(1) link from
+// its staple angles (arXiv:1309.3859, Section II; Best & Fisher 1979; Creutz
+// 1987), shared by the kernels that read the angles from global memory and
+// the cluster-resident kernels that read them from distributed shared memory,
+// so that every implementation produces bit-identical configurations.
+#pragma once
+
+#include "ml_device.cuh"
+
+namespace ml {
+
+// Random uniforms of rejection trial m for link (site, mu), sweep n.
+// FP64: blocks j = 2m (u1 = words 0,1; u2 = words 2,3) and 2m+1 (u3 = words
+// 0,1) with 52-bit uniforms.  FP32: block j = m, words 0, 1, 2 with 23-bit
+// uniforms.  Counter = (site, mu + 4 j, n lo, n hi), key = seed.
+template <typename T>
+struct Draws;
+
+template <>
+struct Draws<double> {
+  __device__ static __forceinline__ void trial(uint32_t site, int mu, unsigned long long n, int m, uint32_t k0,
+                                               uint32_t k1, double* u1, double* u2) {
+    const U4 o = philox4x32_10(U4{site, static_cast<uint32_t>(mu + 8 * m), static_cast<uint32_t>(n),
+                                  static_cast<uint32_t>(n >> 32)},
+                               k0, k1);
+    *u1 = uniform52(o.x, o.y);
+    *u2 = uniform52(o.z, o.w);
+  }
+  __device__ static __forceinline__ double sign_draw(uint32_t site, int mu, unsigned long long n, int m, uint32_t k0,
+                                                     uint32_t k1) {
+    const U4 o = philox4x32_10(U4{site, static_cast<uint32_t>(mu + 8 * m + 4), static_cast<uint32_t>(n),
+                                  static_cast<uint32_t>(n >> 32)},
+                               k0, k1);
+    return uniform52(o.x, o.y);
+  }
+};
+
+template <>
+struct Draws<float> {
+  __device__ static __forceinline__ U4 block(uint32_t site, int mu, unsigned long long n, int m, uint32_t k0,
+                                             uint32_t k1) {
+    return philox4x32_10(
+        U4{site, static_cast<uint32_t>(mu + 4 * m), static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)}, k0, k1);
+  }
+};
+
+// Best & Fisher (Applied Statistics 28 (1979) 152): psi with density
+// exp(kappa cos psi) / (2 pi I0(kappa)).  Returns false at the trial cap.
+template <typename T>
+__device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsigned long long n, uint32_t k0,
+                                          uint32_t k1, T* psi) {
+  using P = Prec<T>;
+  if constexpr (P::fp64) {
+    double u1, u2;
+    if (kappa < P::kappa_tiny) {
+      Draws<double>::trial(site, mu, n, 0, k0, k1, &u1, &u2);
+      *psi = kPi * (2.0 * u1 - 1.0);
+      return true;
+    }
+    const double root = sqrt(1.0 + 4.0 * kappa * kappa);
+    const double tau = 1.0 + root;
+    const double tau_minus_2 = 4.0 * kappa * kappa / (1.0 + root);
+    const double rho = tau * tau_minus_2 / (tau + sqrt(2.0 * tau)) / (2.0 * kappa);
+    const double s = (1.0 + rho * rho) / (2.0 * rho);
+    for (int m = 0; m < kMaxTrials; ++m) {
+      Draws<double>::trial(site, mu, n, m, k0, k1, &u1, &u2);
+      const double z = P::cos_pi_u(u1);
+      double f = (1.0 + s * z) / (s + z);
+      f = fmin(fmax(f, -1.0), 1.0);
+      const double c = kappa * (s - f);
+      if ((c * (2.0 - c) - u2 > 0.0) || (log(c / u2) + 1.0 - c >= 0.0)) {
+        const double a = acos(f);
+        *psi = (Draws<double>::sign_draw(site, mu, n, m, k0, k1) > 0.5) ? a : -a;
+        return true;
+      }
+    }
+    return false;
+  } else {
+    if (kappa < P::kappa_tiny) {
+      const U4 o = Draws<float>::block(site, mu, n, 0, k0, k1);
+      *psi = kPiF * (2.0f * uniform23(o.x) - 1.0f);
+      return true;
+    }
+    // single-precision set-up with hardware reciprocals (a few ulp); every
+    // operand is well inside the normal range for kappa >= kappa_tiny
+    const float k2 = kappa * kappa;
+    const float root = sqrtf(fmaf(4.0f, k2, 1.0f));
+    const float tau = 1.0f + root;
+    const float tau_minus_2 = __fdividef(4.0f * k2, 1.0f + root);
+    const float rho = __fdividef(tau * tau_minus_2, (tau + sqrtf(2.0f * tau)) * (2.0f * kappa));
+    const float s = __fdividef(fmaf(rho, rho, 1.0f), 2.0f * rho);
+    for (int m = 0; m < kMaxTrials; ++m) {
+      const U4 o = Draws<float>::block(site, mu, n, m, k0, k1);
+      const float u1 = uniform23(o.x), u2 = uniform23(o.y);
+      const float z = P::cos_pi_u(u1);
+      float f = __fdividef(fmaf(s, z, 1.0f), s + z);
+      f = fminf(fmaxf(f, -1.0f), 1.0f);
+      const float c = kappa * (s - f);
+      // log(c / u2) as a difference of hardware logarithms (c > 0, u2 > 0)
+      if ((c * (2.0f - c) - u2 > 0.0f) || (__logf(c) - __logf(u2) + 1.0f - c >= 0.0f)) {
+        const float a = acosf(f);
+        *psi = (uniform23(o.z) > 0.5f) ? a : -a;
+        return true;
+      }
+    }
+    return false;
+  }
+}
+
+// New angle of link U_mu from its staples.  staples(nu, v) fills the six
+// angles of the two plaquettes in the (mu, nu) plane that contain the link:
+//   v = theta_nu(x+mu), theta_mu(x+nu), theta_nu(x),
+//       theta_nu(x+mu-nu), theta_mu(x-nu), theta_nu(x-nu)
+// so that the staple sum is
+//   W = sum_{nu != mu} [ e^{i(v0 - v1 - v2)} + e^{i(-v3 - v4 + v5)} ]
+//     = k e^{i alpha}.
+// KIND 0: heatbath draw theta = psi - alpha with psi ~ exp(beta k cos psi);
+// KIND 1: overrelaxation theta -> -2 alpha - theta (self() is the current
+// angle).  Returns false when the link keeps its angle (k = 0 in
+// overrelaxation, or the heatbath trial cap, which also sets kErrReject).
+template <typename T, int KIND, typename Staples, typename Self>
+__device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&& self, uint32_t site,
+                                               unsigned long long n, uint32_t k0, uint32_t k1, T beta,
+                                               int* __restrict__ err, T* out) {
+  using P = Prec<T>;
+  T wr = T(0), wi = T(0);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    T v[6];
+    staples(nu, v);
+    const T a = v[0] - v[1] - v[2];
+    const T b = -v[3] - v[4] + v[5];
+    T sa, ca, sb, cb;
+    P::sincos_(a, &sa, &ca);
+    P::sincos_(b, &sb, &cb);
+    wr += ca + cb;
+    wi += sa + sb;
+  }
+  const T k = P::sqrt_(wr * wr + wi * wi);
+  const T alpha = P::atan2_(wi, wr);
+  if (KIND == 0) {
+    T psi;
+    if (!von_mises<T>(beta * k, site, mu, n, k0, k1, &psi)) {
+      atomicOr(err, kErrReject);
+      return false;
+    }
+    *out = P::wrap(psi - alpha);
+  } else {
+    if (k == T(0)) return false;
+    *out = P::wrap(T(-2) * alpha - self());
+  }
+  return true;
+}
+
+}  // namespace ml

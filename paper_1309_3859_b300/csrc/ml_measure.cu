@@ -15,6 +15,8 @@
 // for FP32 lattices) laid out with the spatial site x fastest, so one warp touches 32 consecutive sites.  All
 // reductions over sites are warp-shuffle trees writing per-warp partials,
 // followed by fixed-order sums: results do not depend on scheduling.
+#include <algorithm>
+
 #include "ml_record.cuh"
 
 namespace ml {
@@ -69,9 +71,7 @@ __device__ __forceinline__ void load_batch(const T* __restrict__ p, T v[RecBatch
 
 // Record of each lattice's configuration into ring slot `slot` of buffer
 // `buf`; grid (sites x slabs, nc + 1, lattices): blockIdx.y < nc handles
-// component ci = blockIdx.y, blockIdx.y = nc the slab phase sums.  Component
-// blocks also write warp partials of the site sums of Re / Im P_c
-// (vac_part[warp][c][k]; entries of unselected components stay zero).
+// component ci = blockIdx.y, blockIdx.y = nc the slab phase sums.
 template <typename T>
 __global__ void __launch_bounds__(256) k_record_table(const LatDesc* __restrict__ desc,
                                                       const LatCtl* __restrict__ ctl, int buf, int slot) {
@@ -82,18 +82,76 @@ __global__ void __launch_bounds__(256) k_record_table(const LatDesc* __restrict_
     slot = ctl[li].slot;
   }
   const LatDesc& L = desc[li];
-  if (blockIdx.x * blockDim.x >= L.g.Ns * L.nslab || static_cast<int>(blockIdx.y) > L.m.nc) return;  // whole block
+  if (blockIdx.x * blockDim.x >= 32 * record_warps(L) || static_cast<int>(blockIdx.y) > L.m.nc) return;  // whole block
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   record_warp<T>(L, buf, slot, blockIdx.y, w, threadIdx.x & 31);
 }
 
-// vac_acc[j] += (1/V) sum_w vac_part[w][j] in a fixed order; grid (12, lattices)
-__global__ void __launch_bounds__(256) k_vac_accumulate_table(const LatDesc* __restrict__ desc,
-                                                              const LatCtl* __restrict__ ctl) {
+// ---------------------------------------------------------------------------
+// Vacuum sums of the folded records (Section II.B: the field operators'
+// vacuum expectation values, estimated on every sub-update configuration):
+//   vac_acc[2 c + k] += (1/V) sum_{j < nrec} sum_{s, x} O_j[s][ci][k](x),
+// c = comp[ci], from the plaquette slab sums the records already hold.
+// k_vac_partial_table: grid (vac blocks, nc * 2 parts, lattices); block b of
+// a part sums a contiguous range of the part's (slab, site) pairs over the
+// folded slots into vac_part[part][b].  k_vac_final_table: one warp per part
+// adds the partials in a fixed order.  Entries of unselected components stay
+// zero.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_vac_partial_table(const LatDesc* __restrict__ desc,
+                                                           const LatCtl* __restrict__ ctl, int buf, int nrec) {
+  constexpr int B = RecBatch<T>::n;
+  const int li = blockIdx.z;
+  if (ctl) {
+    if (!ctl[li].fold) return;
+    buf = ctl[li].fold_buf;
+    nrec = ctl[li].nrec;
+  }
+  const LatDesc& L = desc[li];
+  const int part = blockIdx.y, b = blockIdx.x;
+  if (part >= 2 * L.m.nc || b >= L.nparts) return;
+  const int ci = part >> 1, k = part & 1;
+  const long long items = static_cast<long long>(L.nslab) * L.g.Ns;  // (slab, site) pairs
+  const long long per = (items + L.nparts - 1) / L.nparts;
+  const long long i0 = b * per, i1 = min(items, i0 + per);
+  const T* osum = static_cast<const T*>(L.osum[buf]);
+  double v = 0.0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const long long sl = i / L.g.Ns;
+    const long long x = i - sl * L.g.Ns;
+    const T* o = osum + (((sl * L.m.nc + ci) * 2 + k) * L.g.Ns + x) * B;
+    T a[B];
+    load_batch<T>(o, a);
+    T t = T(0);
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      if (j < nrec) t += a[j];
+    v += static_cast<double>(t);
+  }
   __shared__ double sh[8];
-  const int li = blockIdx.y;
-  if (ctl && !ctl[li].record) return;
-  vac_block_sum(desc[li], blockIdx.x, sh);
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < 8; ++w) tot += sh[w];
+    L.vac_part[static_cast<size_t>(part) * L.nparts + b] = tot;
+  }
+}
+
+// grid (lattices), 32 x 12 threads: warp q adds part q's partials
+__global__ void __launch_bounds__(384) k_vac_final_table(const LatDesc* __restrict__ desc,
+                                                         const LatCtl* __restrict__ ctl) {
+  const int li = blockIdx.x;
+  if (ctl && !ctl[li].fold) return;
+  const LatDesc& L = desc[li];
+  const int part = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (part >= 2 * L.m.nc) return;
+  double v = 0.0;
+  for (int b = lane; b < L.nparts; b += 32) v += L.vac_part[static_cast<size_t>(part) * L.nparts + b];
+  v = warp_sum(v);
+  if (lane == 0) L.vac_acc[2 * L.m.comp[part >> 1] + (part & 1)] += v * (1.0 / L.g.V);
 }
 
 // Slab sums (inner and outer).  FP64 lattices keep double2 (re, im) sums and
@@ -575,11 +633,16 @@ __global__ void k_connected(const double* __restrict__ recs, int n_meas, MeasLay
 }
 
 // ---------------------------------------------------------------------------
-int vac_part_count(const Geom& g, int d) { return record_blocks(g, d) * 8; }
+int vac_part_count(const Geom& g, int d) {
+  const long long items = static_cast<long long>(g.Ns) * (g.Nt / d);
+  return static_cast<int>(std::min<long long>(128, std::max<long long>(1, (items + 2047) / 2048)));
+}
 
 int product_partial_count(const Geom& g) { return blocks_for(g.Ns, 256) * 8; }
 
-int record_blocks(const Geom& g, int d) { return blocks_for(static_cast<long long>(g.Ns) * (g.Nt / d), 256); }
+int record_blocks(const Geom& g, int d) {
+  return blocks_for(32ll * ((g.Ns + 31) / 32) * (g.Nt / d), 256);  // record_warps() warps
+}
 
 int fold_probe_groups(int np) { return (np + kProbesPerThread - 1) / kProbesPerThread; }
 
@@ -590,8 +653,7 @@ void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const
     k_record_table<double><<<grid, 256, 0, s>>>(d, ctl, buf, slot);
   else
     k_record_table<float><<<grid, 256, 0, s>>>(d, ctl, buf, slot);
-  k_vac_accumulate_table<<<dim3(12, td.nlat), 256, 0, s>>>(d, ctl);
-  count_launches(2);
+  count_launches(1);
 }
 
 void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
@@ -609,6 +671,15 @@ void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const L
     else
       k_accum_O_table<float><<<go, 256, 0, s>>>(d, ctl, buf, nrec);
     count_launches(1);
+  }
+  if (td.max_vac_parts > 0) {
+    const dim3 gv(td.max_vac_blocks, td.max_vac_parts, td.nlat);
+    if (fp64)
+      k_vac_partial_table<double><<<gv, 256, 0, s>>>(d, ctl, buf, nrec);
+    else
+      k_vac_partial_table<float><<<gv, 256, 0, s>>>(d, ctl, buf, nrec);
+    k_vac_final_table<<<td.nlat, 384, 0, s>>>(d, ctl);
+    count_launches(2);
   }
 }
 

@@ -1,7 +1,7 @@
 // Record of a sub-update configuration (slab phase sums and plaquette slab
-// sums into the ring) and the vacuum sums, as device functions shared by the
-// standalone record kernels and the record phase of the persistent sweep
-// kernel, so that both produce bit-identical values.
+// sums into the ring), as device functions shared by the standalone record
+// kernels and the record phase of the persistent sweep kernel, so that both
+// produce bit-identical values.
 #pragma once
 
 #include "ml_internal.h"
@@ -46,20 +46,25 @@ __device__ __forceinline__ T plaquette_angle(const T* th, const Geom& g, const i
   return th[soa(g, mu, i, p)] + th[soa(g, nu, ipmu, p ^ 1)] - th[soa(g, mu, ipnu, p ^ 1)] - th[soa(g, nu, i, p)];
 }
 
-// Record warp w of row y (y < nc: component ci = y; y = nc: slab phase
-// sums) of lattice L into slot `slot` of ring buffer `buf`.  The warp covers
-// idx = 32 w .. 32 w + 31 with idx = s Ns + x; component rows also store the
-// warp's site sums of Re / Im P_c in vac_part[w][c][k].  All 32 lanes call.
+// Warps of the record of one slab: warp xw covers the spatial sites
+// x = 32 xw .. 32 xw + 31 (so no warp straddles two slabs).
+__device__ __forceinline__ int record_warps_per_slab(const Geom& g) { return (g.Ns + 31) / 32; }
+
+// Record warp w = s * record_warps_per_slab + xw of row y (y < nc: component
+// ci = y; y = nc: slab phase sums) of lattice L into slot `slot` of ring
+// buffer `buf`.
 template <typename T>
 __device__ __forceinline__ void record_warp(const LatDesc& L, int buf, int slot, int y, int w, int lane) {
   using P = Prec<T>;
   const Geom g = L.g;
   const int d = L.slab, nslab = L.nslab, nc = L.m.nc;
   const T* th = static_cast<const T*>(L.theta);
-  const int idx = 32 * w + lane;
-  const bool live = idx < g.Ns * nslab;
-  const int s = live ? idx / g.Ns : 0;
-  const int x = live ? idx - s * g.Ns : 0;
+  const int ws = record_warps_per_slab(g);
+  const int sw = w / ws;
+  const int xw = 32 * (w - sw * ws) + lane;
+  const bool live = sw < nslab && xw < g.Ns;
+  const int s = live ? sw : 0;
+  const int x = live ? xw : 0;
   int c[4];
   spatial_coords(g, x, &c[1], &c[2], &c[3]);
   if (y == nc) {
@@ -87,35 +92,9 @@ __device__ __forceinline__ void record_warp(const LatDesc& L, int buf, int slot,
     osum[((static_cast<size_t>(s * nc + y) * 2 + 0) * g.Ns + x) * RecBatch<T>::n + slot] = re;
     osum[((static_cast<size_t>(s * nc + y) * 2 + 1) * g.Ns + x) * RecBatch<T>::n + slot] = im;
   }
-  const double vr = warp_sum(static_cast<double>(re));
-  const double vi = warp_sum(static_cast<double>(im));
-  if (lane == 0) {
-    L.vac_part[static_cast<size_t>(w) * 12 + 2 * cc] = vr;
-    L.vac_part[static_cast<size_t>(w) * 12 + 2 * cc + 1] = vi;
-  }
 }
 
 // record warps of lattice L (rows y = 0..nc)
-__device__ __forceinline__ int record_warps(const LatDesc& L) { return (L.g.Ns * L.nslab + 31) / 32; }
-
-// vac_acc[j] += (1/V) sum_w vac_part[w][j] in a fixed order, by threads
-// 0..255 of a block (sh: 8 doubles of shared memory); every thread of the
-// block calls (it synchronises).
-__device__ __forceinline__ void vac_block_sum(const LatDesc& L, int j, double* sh) {
-  const int t = threadIdx.x;
-  if (t < 256) {
-    double v = 0.0;
-    for (int w = t; w < L.nparts; w += 256) v += L.vac_part[static_cast<size_t>(w) * 12 + j];
-    v = warp_sum(v);
-    if ((t & 31) == 0) sh[t >> 5] = v;
-  }
-  __syncthreads();
-  if (t == 0) {
-    double s = 0.0;
-    for (int w = 0; w < 8; ++w) s += sh[w];
-    L.vac_acc[j] += s * (1.0 / L.g.V);
-  }
-  __syncthreads();
-}
+__device__ __forceinline__ int record_warps(const LatDesc& L) { return L.nslab * record_warps_per_slab(L.g); }
 
 }  // namespace ml

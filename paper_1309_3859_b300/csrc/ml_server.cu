@@ -315,6 +315,8 @@ int rebuild_tables(ml_server* s) {
     td.max_y_T = std::max(td.max_y_T, d.nslab * m.nR);
     if (m.nrf > 0 && m.np > 0 && m.nc > 0)
       td.max_y_O = std::max(td.max_y_O, d.nslab * m.nrf * fold_probe_groups(m.np));
+    td.max_vac_blocks = std::max(td.max_vac_blocks, d.nparts);
+    td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
   }
   td.nlat = static_cast<int>(n);
   td.total_tiles = static_cast<int>(s->h_tile_lat.size());

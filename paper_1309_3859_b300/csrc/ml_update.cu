@@ -8,107 +8,11 @@
 // theta (Section II, Creutz 1987), even/odd checkerboard in place (Section
 // II.D) and spatial links on t = 0 (mod d) frozen in slab mode (Section II.C,
 // Algorithm 1).
+#include "ml_link.cuh"
 #include "ml_record.cuh"
+#include "ml_sync.cuh"
 
 namespace ml {
-
-// Random uniforms of rejection trial m for link (site, mu), sweep n.
-// FP64: blocks j = 2m (u1 = words 0,1; u2 = words 2,3) and 2m+1 (u3 = words
-// 0,1) with 52-bit uniforms.  FP32: block j = m, words 0, 1, 2 with 23-bit
-// uniforms.  Counter = (site, mu + 4 j, n lo, n hi), key = seed.
-template <typename T>
-struct Draws;
-
-template <>
-struct Draws<double> {
-  __device__ static __forceinline__ void trial(uint32_t site, int mu, unsigned long long n, int m, uint32_t k0,
-                                               uint32_t k1, double* u1, double* u2) {
-    const U4 o = philox4x32_10(U4{site, static_cast<uint32_t>(mu + 8 * m), static_cast<uint32_t>(n),
-                                  static_cast<uint32_t>(n >> 32)},
-                               k0, k1);
-    *u1 = uniform52(o.x, o.y);
-    *u2 = uniform52(o.z, o.w);
-  }
-  __device__ static __forceinline__ double sign_draw(uint32_t site, int mu, unsigned long long n, int m, uint32_t k0,
-                                                     uint32_t k1) {
-    const U4 o = philox4x32_10(U4{site, static_cast<uint32_t>(mu + 8 * m + 4), static_cast<uint32_t>(n),
-                                  static_cast<uint32_t>(n >> 32)},
-                               k0, k1);
-    return uniform52(o.x, o.y);
-  }
-};
-
-template <>
-struct Draws<float> {
-  __device__ static __forceinline__ U4 block(uint32_t site, int mu, unsigned long long n, int m, uint32_t k0,
-                                             uint32_t k1) {
-    return philox4x32_10(
-        U4{site, static_cast<uint32_t>(mu + 4 * m), static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)}, k0, k1);
-  }
-};
-
-// Best & Fisher (Applied Statistics 28 (1979) 152): psi with density
-// exp(kappa cos psi) / (2 pi I0(kappa)).  Returns false at the trial cap.
-template <typename T>
-__device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsigned long long n, uint32_t k0,
-                                          uint32_t k1, T* psi) {
-  using P = Prec<T>;
-  if constexpr (P::fp64) {
-    double u1, u2;
-    if (kappa < P::kappa_tiny) {
-      Draws<double>::trial(site, mu, n, 0, k0, k1, &u1, &u2);
-      *psi = kPi * (2.0 * u1 - 1.0);
-      return true;
-    }
-    const double root = sqrt(1.0 + 4.0 * kappa * kappa);
-    const double tau = 1.0 + root;
-    const double tau_minus_2 = 4.0 * kappa * kappa / (1.0 + root);
-    const double rho = tau * tau_minus_2 / (tau + sqrt(2.0 * tau)) / (2.0 * kappa);
-    const double s = (1.0 + rho * rho) / (2.0 * rho);
-    for (int m = 0; m < kMaxTrials; ++m) {
-      Draws<double>::trial(site, mu, n, m, k0, k1, &u1, &u2);
-      const double z = P::cos_pi_u(u1);
-      double f = (1.0 + s * z) / (s + z);
-      f = fmin(fmax(f, -1.0), 1.0);
-      const double c = kappa * (s - f);
-      if ((c * (2.0 - c) - u2 > 0.0) || (log(c / u2) + 1.0 - c >= 0.0)) {
-        const double a = acos(f);
-        *psi = (Draws<double>::sign_draw(site, mu, n, m, k0, k1) > 0.5) ? a : -a;
-        return true;
-      }
-    }
-    return false;
-  } else {
-    if (kappa < P::kappa_tiny) {
-      const U4 o = Draws<float>::block(site, mu, n, 0, k0, k1);
-      *psi = kPiF * (2.0f * uniform23(o.x) - 1.0f);
-      return true;
-    }
-    // single-precision set-up with hardware reciprocals (a few ulp); every
-    // operand is well inside the normal range for kappa >= kappa_tiny
-    const float k2 = kappa * kappa;
-    const float root = sqrtf(fmaf(4.0f, k2, 1.0f));
-    const float tau = 1.0f + root;
-    const float tau_minus_2 = __fdividef(4.0f * k2, 1.0f + root);
-    const float rho = __fdividef(tau * tau_minus_2, (tau + sqrtf(2.0f * tau)) * (2.0f * kappa));
-    const float s = __fdividef(fmaf(rho, rho, 1.0f), 2.0f * rho);
-    for (int m = 0; m < kMaxTrials; ++m) {
-      const U4 o = Draws<float>::block(site, mu, n, m, k0, k1);
-      const float u1 = uniform23(o.x), u2 = uniform23(o.y);
-      const float z = P::cos_pi_u(u1);
-      float f = __fdividef(fmaf(s, z, 1.0f), s + z);
-      f = fminf(fmaxf(f, -1.0f), 1.0f);
-      const float c = kappa * (s - f);
-      // log(c / u2) as a difference of hardware logarithms (c > 0, u2 > 0)
-      if ((c * (2.0f - c) - u2 > 0.0f) || (__logf(c) - __logf(u2) + 1.0f - c >= 0.0f)) {
-        const float a = acosf(f);
-        *psi = (uniform23(o.z) > 0.5f) ? a : -a;
-        return true;
-      }
-    }
-    return false;
-  }
-}
 
 constexpr int kSweepThreads = kSweepTile;  // block size of the sweep kernels
 
@@ -132,7 +36,6 @@ template <typename T, int KIND>
 __device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int parity, int slab_d, int h,
                                             unsigned long long n, uint32_t k0, uint32_t k1, T beta,
                                             int* __restrict__ err) {
-  using P = Prec<T>;
   int c[4];
   half_site_coords(g, h, parity, c);
   if (slab_d > 0 && mu != 0 && (c[0] % slab_d) == 0) return;  // frozen boundary link
@@ -140,41 +43,25 @@ __device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int pa
   const int op = parity ^ 1;
   const int ipmu = step_index(g, i, c, mu, +1);
   const T* th_mu_op = th + static_cast<size_t>(mu * 2 + op) * g.Vh;
-
-  // staple sum W = sum_{nu != mu} [ e^{i(th_nu(x+mu) - th_mu(x+nu) - th_nu(x))}
-  //                               + e^{i(-th_nu(x+mu-nu) - th_mu(x-nu) + th_nu(x-nu))} ]
-  T wr = T(0), wi = T(0);
-#pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == mu) continue;
+  T* self = th + static_cast<size_t>(mu * 2 + parity) * g.Vh + (i >> 1);
+  auto staples = [&](int nu, T v[6]) {
     const T* th_nu_p = th + static_cast<size_t>(nu * 2 + parity) * g.Vh;
     const T* th_nu_op = th + static_cast<size_t>(nu * 2 + op) * g.Vh;
     const int ipnu = step_index(g, i, c, nu, +1);
     const int imnu = step_index(g, i, c, nu, -1);
     // x + mu - nu: the coordinate along nu of x + mu is c[nu]
     const int ipmu_mnu = step_index(g, ipmu, c, nu, -1);
-    const T a = th_nu_op[ipmu >> 1] - th_mu_op[ipnu >> 1] - th_nu_p[i >> 1];
-    const T b = -th_nu_p[ipmu_mnu >> 1] - th_mu_op[imnu >> 1] + th_nu_op[imnu >> 1];
-    T sa, ca, sb, cb;
-    P::sincos_(a, &sa, &ca);
-    P::sincos_(b, &sb, &cb);
-    wr += ca + cb;
-    wi += sa + sb;
-  }
-  const T k = P::sqrt_(wr * wr + wi * wi);
-  const T alpha = P::atan2_(wi, wr);
-  T* self = th + static_cast<size_t>(mu * 2 + parity) * g.Vh + (i >> 1);
-  if (KIND == 0) {
-    T psi;
-    if (!von_mises<T>(beta * k, static_cast<uint32_t>(i), mu, n, k0, k1, &psi)) {
-      atomicOr(err, kErrReject);
-      return;
-    }
-    *self = P::wrap(psi - alpha);
-  } else {
-    if (k == T(0)) return;
-    *self = P::wrap(T(-2) * alpha - *self);
-  }
+    v[0] = th_nu_op[ipmu >> 1];
+    v[1] = th_mu_op[ipnu >> 1];
+    v[2] = th_nu_p[i >> 1];
+    v[3] = th_nu_p[ipmu_mnu >> 1];
+    v[4] = th_mu_op[imnu >> 1];
+    v[5] = th_nu_op[imnu >> 1];
+  };
+  T out;
+  if (new_link_angle<T, KIND>(mu, staples, [&] { return *self; }, static_cast<uint32_t>(i), n, k0, k1, beta, err,
+                              &out))
+    *self = out;
 }
 
 // One (mu, parity) pass, one thread per link.  The links of one pass share no
@@ -188,45 +75,6 @@ __global__ void __launch_bounds__(128) k_update_pass(T* __restrict__ th, Geom g,
   if (h >= g.Vh) return;
   const unsigned long long n = n_dev ? *n_dev : n_fixed;
   update_link<T, KIND>(th, g, mu, parity, slab_d, h, n, k0, k1, beta, err);
-}
-
-// Grid-wide barrier for a cooperative launch (all blocks co-resident), on a
-// monotonic 64-bit arrival counter: block b's k-th arrival returns old, and
-// the barrier opens when the counter reaches the next multiple of the grid
-// size.  Arrival is a release atomic, polling an acquire load.  The spin is
-// bounded: after kSpinLimit polls the block records kErrTimeout and reports
-// failure, so a lost block cannot hang the device.
-constexpr unsigned kSpinLimit = 1u << 28;
-
-__device__ __forceinline__ unsigned long long atom_add_release(unsigned long long* p, unsigned long long v) {
-  unsigned long long old;
-  asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-  return old;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ bool grid_barrier(unsigned long long* count, int* err) {
-  __syncthreads();
-  int ok = 1;
-  if (threadIdx.x == 0) {
-    const unsigned long long nb = gridDim.x;
-    const unsigned long long old = atom_add_release(count, 1ull);
-    const unsigned long long target = (old / nb + 1ull) * nb;
-    unsigned polls = 0;
-    while (ld_acquire(count) < target) {
-      if (++polls > kSpinLimit) {
-        atomicOr(err, kErrTimeout);
-        ok = 0;
-        break;
-      }
-    }
-  }
-  return __syncthreads_and(ok) != 0;
 }
 
 // n_compound compound sweeps (heatbath + n_or overrelaxation sweeps, each
@@ -296,7 +144,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
   }
   if (record) {
     // record of the new configurations (the work of k_record_table, warp for
-    // warp), then the vacuum sums (the work of k_vac_accumulate_table)
+    // warp)
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -310,13 +158,6 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
       const LatDesc& L = d[li];
       const int nw = record_warps(L), items = (L.m.nc + 1) * nw;
       for (int it = gw; it < items; it += nwarps) record_warp<T>(L, buf, slot, it / nw, it - (it / nw) * nw, lane);
-    }
-    if (!grid_barrier(bar, err)) return;
-    __shared__ double sh[8];
-    for (int pair = blockIdx.x; pair < nlat * 12; pair += gridDim.x) {
-      const int li = pair / 12;
-      if (ctl && !ctl[li].record) continue;
-      vac_block_sum(d[li], pair - li * 12, sh);
     }
   }
   if (blockIdx.x == 0)

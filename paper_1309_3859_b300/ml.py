@@ -19,8 +19,9 @@ from . import build as _build
 
 ML_OK, ML_EINVAL, ML_ENOMEM, ML_ECUDA, ML_ETIMEOUT, ML_EREJECT, ML_EBUSY, ML_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 ML_FP64, ML_FP32 = 0, 1
-ML_SWEEP_PERSISTENT, ML_SWEEP_PASSES = 0, 1
-ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP, ML_K_SUBUPDATE = range(7)
+ML_SWEEP_PERSISTENT, ML_SWEEP_PASSES, ML_SWEEP_RESIDENT = 0, 1, 2
+(ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP, ML_K_SUBUPDATE,
+ ML_K_FULLSWEEP) = range(8)
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
@@ -233,7 +234,8 @@ class Lattice:
         self.p = p
         self._torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
-        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        # high priority: the sweeps own the critical path, folds fill the SMs they leave
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device, priority=-100)
         self._cb, self._alloc = _torch_allocator(torch, self.device, self.stream)
         st = self.stream
         self._cp = p.c()
@@ -375,7 +377,8 @@ class Batch:
         self.params = list(params)
         self._torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
-        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        # high priority: the sweeps own the critical path, folds fill the SMs they leave
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device, priority=-100)
         self._cb, self._alloc = _torch_allocator(torch, self.device, self.stream)
         arr = (_Params * len(self.params))(*[p.c() for p in self.params])
         self._arr = arr

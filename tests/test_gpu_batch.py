@@ -36,7 +36,7 @@ def run_alone(p, mode=None, n_therm=3, n_meas=2):
 
 
 @pytest.mark.parametrize("fp64", [True, False])
-@pytest.mark.parametrize("mode", [ml.ML_SWEEP_PERSISTENT, ml.ML_SWEEP_PASSES])
+@pytest.mark.parametrize("mode", [ml.ML_SWEEP_PERSISTENT, ml.ML_SWEEP_PASSES, ml.ML_SWEEP_RESIDENT])
 def test_batch_matches_alone(fp64, mode):
     ps = mixed_params(fp64, n_sub=20)
     alone = [run_alone(p, mode) for p in ps]
@@ -50,11 +50,12 @@ def test_batch_matches_alone(fp64, mode):
         assert np.array_equal(angles[i], alone[i][1]), i
 
 
-def test_batch_two_level_matches_alone():
+@pytest.mark.parametrize("mode", [ml.ML_SWEEP_PERSISTENT, ml.ML_SWEEP_RESIDENT])
+def test_batch_two_level_matches_alone(mode):
     ps = mixed_params(False, n_sub=3, outer=True)
     alone = [run_alone(p) for p in ps]
     with ml.Batch(ps) as b:
-        b.sweep_mode = ml.ML_SWEEP_PERSISTENT
+        b.sweep_mode = mode
         b.thermalize(3)
         recs = b.measure(2)
     for i in range(len(ps)):

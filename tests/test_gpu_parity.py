@@ -306,23 +306,47 @@ def test_full_size_observe_fp32_single_24():
 
 
 @pytest.mark.parametrize("fp64", [True, False])
-def test_sweep_implementations_agree(fp64):
-    """The persistent kernel and the per-pass kernels run the same link
-    updates in the same order: identical chains and records."""
-    p = ml.Params(L=8, Nt=4, beta=0.95, seed=5, fp64=fp64, slab=2, n_sub=3, k_between=1, r=(1, 2), rf=(2,),
-                  probes=((0, 0), (1, 0)), comp_mask=0x3F)
+@pytest.mark.parametrize("geom", [dict(L=8, Nt=4, n_sub=3), dict(L=6, Nt=8, n_sub=18, outer_slab=4, n_sub_outer=2)])
+def test_sweep_implementations_agree(fp64, geom):
+    """The persistent kernel, the per-pass kernels and the cluster-resident
+    kernels run the same link updates with the same random numbers: identical
+    chains and records.  L = 6 puts cluster boundaries and partial record
+    warps inside a slab; n_sub = 18 covers a full record ring and a tail; the
+    two-level run uses the resident kernels for both slab thicknesses."""
+    p = ml.Params(beta=0.95, seed=5, fp64=fp64, slab=2, k_between=1, r=(1, 2), rf=(2,), probes=((0, 0), (1, 0)),
+                  comp_mask=0x3F, **geom)
     out = {}
-    for mode in (ml.ML_SWEEP_PERSISTENT, ml.ML_SWEEP_PASSES):
+    modes = (ml.ML_SWEEP_PERSISTENT, ml.ML_SWEEP_PASSES, ml.ML_SWEEP_RESIDENT)
+    for mode in modes:
         with ml.Lattice(p) as lat:
             lat.sweep_mode = mode
             assert lat.sweep_mode == mode
             lat.thermalize(3)
             rec = lat.measure(2)
             out[mode] = (rec, lat.get_angles(), lat.sweep)
-    a, b = out[ml.ML_SWEEP_PERSISTENT], out[ml.ML_SWEEP_PASSES]
-    assert a[2] == b[2]
-    assert np.array_equal(a[1], b[1])
-    assert np.array_equal(a[0], b[0])
+    a = out[modes[0]]
+    for mode in modes[1:]:
+        b = out[mode]
+        assert a[2] == b[2], mode
+        assert np.array_equal(a[1], b[1]), mode
+        assert np.array_equal(a[0], b[0]), mode
+
+
+def test_resident_mode_needs_fitting_slabs():
+    """A 64^3 slab of thickness 2 needs more shared memory than a cluster
+    has: forcing the resident implementation is rejected, the handle keeps
+    working in its own mode."""
+    p = ml.Params(L=64, Nt=2, beta=1.0, seed=1, fp64=False, slab=2, n_sub=1, r=(1,), rf=(1,), probes=((0, 0),),
+                  comp_mask=0x01)
+    with ml.Lattice(p) as lat:
+        mode = lat.sweep_mode
+        assert mode != ml.ML_SWEEP_RESIDENT
+        with pytest.raises(ml.MLError) as exc:
+            lat.sweep_mode = ml.ML_SWEEP_RESIDENT
+        assert exc.value.status == ml.ML_EINVAL
+        assert lat.sweep_mode == mode
+        lat.thermalize(1)
+        assert np.all(np.isfinite(lat.measure(1)))
 
 
 def test_full_size_two_level_48():
