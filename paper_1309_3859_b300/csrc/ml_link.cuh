@@ -44,6 +44,36 @@ struct Draws<float> {
   }
 };
 
+// Best & Fisher (Applied Statistics 28 (1979) 152) in single precision: the
+// envelope parameter s of kappa, and trial m, which on acceptance returns
+// f = cos psi and the sign of psi.  The set-up uses hardware reciprocals (a
+// few ulp); every operand is well inside the normal range for kappa >=
+// kappa_tiny.
+__device__ __forceinline__ float bf_envelope(float kappa) {
+  const float k2 = kappa * kappa;
+  const float root = sqrtf(fmaf(4.0f, k2, 1.0f));
+  const float tau = 1.0f + root;
+  const float tau_minus_2 = __fdividef(4.0f * k2, 1.0f + root);
+  const float rho = __fdividef(tau * tau_minus_2, (tau + sqrtf(2.0f * tau)) * (2.0f * kappa));
+  return __fdividef(fmaf(rho, rho, 1.0f), 2.0f * rho);
+}
+__device__ __forceinline__ bool bf_trial(float kappa, float s, uint32_t site, int mu, unsigned long long n, int m,
+                                         uint32_t k0, uint32_t k1, float* f_out, bool* neg) {
+  const U4 o = Draws<float>::block(site, mu, n, m, k0, k1);
+  const float u1 = uniform23(o.x), u2 = uniform23(o.y);
+  const float z = Prec<float>::cos_pi_u(u1);
+  float f = __fdividef(fmaf(s, z, 1.0f), s + z);
+  f = fminf(fmaxf(f, -1.0f), 1.0f);
+  const float c = kappa * (s - f);
+  // log(c / u2) as a difference of hardware logarithms (c > 0, u2 > 0)
+  if ((c * (2.0f - c) - u2 > 0.0f) || (__logf(c) - __logf(u2) + 1.0f - c >= 0.0f)) {
+    *f_out = f;
+    *neg = !(uniform23(o.z) > 0.5f);
+    return true;
+  }
+  return false;
+}
+
 // Best & Fisher (Applied Statistics 28 (1979) 152): psi with density
 // exp(kappa cos psi) / (2 pi I0(kappa)).  Returns false at the trial cap.
 template <typename T>
@@ -81,25 +111,13 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
       *psi = kPiF * (2.0f * uniform23(o.x) - 1.0f);
       return true;
     }
-    // single-precision set-up with hardware reciprocals (a few ulp); every
-    // operand is well inside the normal range for kappa >= kappa_tiny
-    const float k2 = kappa * kappa;
-    const float root = sqrtf(fmaf(4.0f, k2, 1.0f));
-    const float tau = 1.0f + root;
-    const float tau_minus_2 = __fdividef(4.0f * k2, 1.0f + root);
-    const float rho = __fdividef(tau * tau_minus_2, (tau + sqrtf(2.0f * tau)) * (2.0f * kappa));
-    const float s = __fdividef(fmaf(rho, rho, 1.0f), 2.0f * rho);
+    const float s = bf_envelope(kappa);
     for (int m = 0; m < kMaxTrials; ++m) {
-      const U4 o = Draws<float>::block(site, mu, n, m, k0, k1);
-      const float u1 = uniform23(o.x), u2 = uniform23(o.y);
-      const float z = P::cos_pi_u(u1);
-      float f = __fdividef(fmaf(s, z, 1.0f), s + z);
-      f = fminf(fmaxf(f, -1.0f), 1.0f);
-      const float c = kappa * (s - f);
-      // log(c / u2) as a difference of hardware logarithms (c > 0, u2 > 0)
-      if ((c * (2.0f - c) - u2 > 0.0f) || (__logf(c) - __logf(u2) + 1.0f - c >= 0.0f)) {
+      float f;
+      bool neg;
+      if (bf_trial(kappa, s, site, mu, n, m, k0, k1, &f, &neg)) {
         const float a = acosf(f);
-        *psi = (uniform23(o.z) > 0.5f) ? a : -a;
+        *psi = neg ? -a : a;
         return true;
       }
     }
@@ -118,10 +136,8 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
 // KIND 1: overrelaxation theta -> -2 alpha - theta (self() is the current
 // angle).  Returns false when the link keeps its angle (k = 0 in
 // overrelaxation, or the heatbath trial cap, which also sets kErrReject).
-template <typename T, int KIND, typename Staples, typename Self>
-__device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&& self, uint32_t site,
-                                               unsigned long long n, uint32_t k0, uint32_t k1, T beta,
-                                               int* __restrict__ err, T* out) {
+template <typename T, typename Staples>
+__device__ __forceinline__ void staple_sum(int mu, Staples&& staples, T* k, T* alpha) {
   using P = Prec<T>;
   T wr = T(0), wi = T(0);
 #pragma unroll
@@ -137,8 +153,17 @@ __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&&
     wr += ca + cb;
     wi += sa + sb;
   }
-  const T k = P::sqrt_(wr * wr + wi * wi);
-  const T alpha = P::atan2_(wi, wr);
+  *k = P::sqrt_(wr * wr + wi * wi);
+  *alpha = P::atan2_(wi, wr);
+}
+
+template <typename T, int KIND, typename Staples, typename Self>
+__device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&& self, uint32_t site,
+                                               unsigned long long n, uint32_t k0, uint32_t k1, T beta,
+                                               int* __restrict__ err, T* out) {
+  using P = Prec<T>;
+  T k, alpha;
+  staple_sum<T>(mu, staples, &k, &alpha);
   if (KIND == 0) {
     T psi;
     if (!von_mises<T>(beta * k, site, mu, n, k0, k1, &psi)) {

@@ -36,7 +36,6 @@ namespace ml {
 
 constexpr int kResThreads = 1024;
 constexpr size_t kResSmemMax = 200 * 1024;  // per CTA
-constexpr uint32_t kInterior = 0xffffffffu;  // ghost-table entry of an owned cell
 
 // x / div for x div < 2^40 with mdiv = floor(2^40 / div) + 1
 __device__ __forceinline__ int fdiv(int x, unsigned long long mdiv) {
@@ -78,6 +77,7 @@ struct Box {
   __device__ __forceinline__ int cell(int ix, int iy, int iz) const { return ix + bx * (iy + by * iz); }
 };
 
+// Update of the link U_mu at box cell bi, local time tl.
 template <typename T, int KIND>
 __device__ __forceinline__ void box_link(const Box& b, T* buf, int mu, int tl, int bi, uint32_t site,
                                          unsigned long long n, uint32_t k0, uint32_t k1, T beta, int* err) {
@@ -135,30 +135,35 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const int K = 4 * d + 3;
   const bool active = rank < b.ny * nz;  // CTAs beyond the brick grid own nothing and mirror nothing
   T* buf = reinterpret_cast<T*>(res_smem);
-  uint32_t* tab = reinterpret_cast<uint32_t*>(buf + static_cast<size_t>(K) * b.vol);
+  // ghost list: (cell, owner's address of the same cell) for every mirrored
+  // cell; cells of spatial parity 0 from the front, parity 1 from the back
+  uint2* ghost = reinterpret_cast<uint2*>(buf + static_cast<size_t>(K) * b.vol);
+  __shared__ int nghost[2];
   const uint32_t base = shared_addr(buf);
   // magic divisors; every dividend times its divisor stays below 2^40 (the
   // box fits in shared memory, so all counts are far below 2^20)
-  const unsigned long long m_bx = fdiv_magic(b.bx), m_by = fdiv_magic(b.by), m_L = fdiv_magic(g.L),
-                           m_vol = fdiv_magic(b.vol);
+  const unsigned long long m_bx = fdiv_magic(b.bx), m_by = fdiv_magic(b.by), m_L = fdiv_magic(g.L);
   const int t0 = s * d;
   T* th = static_cast<T*>(Ld.theta);
 
-  // ghost table and the box's links from global memory
+  // ghost list and the box's links from global memory
+  if (threadIdx.x < 2) nghost[threadIdx.x] = 0;
+  __syncthreads();
   for (int c = threadIdx.x; active && c < b.vol; c += blockDim.x) {
     const int q = fdiv(c, m_bx), ix = c - q * b.bx;
     const int iz = fdiv(q, m_by), iy = q - iz * b.by;
     const int cx = wrapc(ix - 1, g.L), cy = wrapc(b.y0 + iy - 1, g.L), cz = wrapc(b.z0 + iz - 1, g.L);
     const bool own = ix >= 1 && ix <= g.L && iy >= 1 && iy <= b.ylen && iz >= 1 && iz <= b.zlen;
-    uint32_t e = kInterior;
     if (!own) {
       const int oy = cy / b.yl_full, oz = cz / b.zl_full;
       const int owner = oy + b.ny * oz;
       const int oc = b.cell(cx + 1, cy - oy * b.yl_full + 1, cz - oz * b.zl_full + 1);
-      e = map_to_rank(base + static_cast<uint32_t>(oc * sizeof(T)), static_cast<uint32_t>(owner)) |
-          static_cast<uint32_t>((cx + cy + cz) & 1);
+      const int sp = (cx + cy + cz) & 1;
+      const int i = atomicAdd(&nghost[sp], 1);
+      ghost[sp == 0 ? i : b.vol - 1 - i] =
+          make_uint2(static_cast<uint32_t>(c),
+                     map_to_rank(base + static_cast<uint32_t>(oc * sizeof(T)), static_cast<uint32_t>(owner)));
     }
-    tab[c] = e;
     const int x = cx + g.L * (cy + g.L * cz);
     for (int sl = 0; sl < K; ++sl) {
       int rho = 0, tl = sl;
@@ -207,15 +212,17 @@ __global__ void __launch_bounds__(kResThreads, 1)
             }
             cluster_sync();
             // ghost copies of the links this pass moved: slots of mu at tl in
-            // [tl_lo, d), cells of parity par
-            const int nsl = active ? d - tl_lo : 0;
-            for (int k = threadIdx.x; k < nsl * b.vol; k += blockDim.x) {
-              const int q = fdiv(k, m_vol), cc = k - q * b.vol;
-              const uint32_t e = tab[cc];
-              if (e == kInterior || static_cast<int>((e + t0 + tl_lo + q) & 1u) != par) continue;
-              const int sl = b.slot(mu, tl_lo + q);
-              buf[sl * b.vol + cc] =
-                  ld_cluster((e & ~3u) + static_cast<uint32_t>(sl * b.vol * sizeof(T)), static_cast<T*>(nullptr));
+            // [tl_lo, d), mirrored cells whose site has parity par at time t0 + tl
+            // (spatial parity par ^ (t & 1))
+            for (int tl = tl_lo; active && tl < d; ++tl) {
+              const int sp = par ^ ((t0 + tl) & 1);
+              const int cnt = nghost[sp], first = sp == 0 ? 0 : b.vol - cnt;
+              const int sl = b.slot(mu, tl);
+              const uint32_t soff = static_cast<uint32_t>(sl * b.vol * sizeof(T));
+              for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                const uint2 e = ghost[first + i];
+                buf[sl * b.vol + e.x] = ld_cluster(e.y + soff, static_cast<T*>(nullptr));
+              }
             }
             __syncthreads();
           }
@@ -327,7 +334,7 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, ResidentPlan*
       const Geom& g = geoms[i];
       split[i] = brick_split(g.L, cs);
       if (g.Nt % mask != 0 || g.L % 2 != 0) fits = false;
-      smem = std::max(smem, static_cast<size_t>(split[i].box) * ((4 * mask + 3) * sizeof(T) + sizeof(uint32_t)));
+      smem = std::max(smem, static_cast<size_t>(split[i].box) * ((4 * mask + 3) * sizeof(T) + sizeof(uint2)));
     }
     if (!fits || smem > kResSmemMax) continue;
     cudaLaunchAttribute at[1];
