@@ -15,9 +15,10 @@
 // (4d + 3 slots; U_i at tl = 0 and tl = d are the frozen boundary links), so
 // every neighbour of a site is at a constant offset (+-1, +-(L+2),
 // +-(L+2)(ylen+2)) and every staple load is a plain shared-memory load.
-// After each (direction, parity) pass a hardware cluster barrier makes the
-// updated links visible, and each CTA copies the ones its ghost frame mirrors
-// from their owners through the cluster's shared-memory window.  At the end
+// A thread that moves a link also stores the new angle into every box cell
+// that mirrors it (in its own or another CTA's shared memory, through the
+// cluster's shared-memory window), so after the hardware cluster barrier that
+// ends each (direction, parity) pass every box is current.  At the end
 // the updated links go back to global memory and the slab is recorded (phase
 // sums, plaquette sums) from shared memory.  No grid-wide synchronisation:
 // the last cluster to finish advances the sweep counters.
@@ -66,6 +67,66 @@ static BrickSplit brick_split(int L, int cs) {
   return best;
 }
 
+// Every box cell, other than the owner's own interior cell, that holds the
+// site (cx, cy, cz) owned by the brick (ry, rz): emit(rank, cell) for each.
+// Rows of brick q's box are (q ylen_full + iy - 1) mod L, iy in [0, ylen_full
+// + 2); a row can appear twice in one box when the box spans the whole
+// extent.  Shared by the device, which builds the mirror lists, and the host,
+// which sizes them.
+template <typename F>
+__host__ __device__ __forceinline__ void for_each_mirror(int L, int ny, int nz, int ylf, int zlf, int ry, int rz,
+                                                         int cx, int cy, int cz, F&& emit) {
+  const int bx = L + 2, by = ylf + 2, bz = zlf + 2;
+  int yq[6], yi[6], zq[6], zi[6], ny_hit = 0, nz_hit = 0;
+  for (int q = 0; q < ny; ++q)
+    for (int k = -1; k <= 1; ++k) {
+      const int iy = cy - q * ylf + 1 + k * L;
+      if (iy >= 0 && iy < by && ny_hit < 6) {
+        yq[ny_hit] = q;
+        yi[ny_hit++] = iy;
+      }
+    }
+  for (int q = 0; q < nz; ++q)
+    for (int k = -1; k <= 1; ++k) {
+      const int iz = cz - q * zlf + 1 + k * L;
+      if (iz >= 0 && iz < bz && nz_hit < 6) {
+        zq[nz_hit] = q;
+        zi[nz_hit++] = iz;
+      }
+    }
+  int xi[3] = {cx + 1, 0, 0}, nx_hit = 1;
+  if (cx == L - 1) xi[nx_hit++] = 0;
+  if (cx == 0) xi[nx_hit++] = L + 1;
+  const int own_y = cy - ry * ylf + 1, own_z = cz - rz * zlf + 1;
+  for (int a = 0; a < ny_hit; ++a)
+    for (int c = 0; c < nz_hit; ++c)
+      for (int e = 0; e < nx_hit; ++e) {
+        const int r = yq[a] + ny * zq[c];
+        if (r == ry + ny * rz && e == 0 && yi[a] == own_y && zi[c] == own_z) continue;  // the owner's own cell
+        emit(r, xi[e] + bx * (yi[a] + by * zi[c]));
+      }
+}
+
+struct MirrorCount {
+  int* n;
+  __host__ __device__ void operator()(int, int) const { ++*n; }
+};
+
+// Largest number of mirror cells of the sites of one brick.
+static int mirror_capacity(int L, const BrickSplit& sp) {
+  int cap = 0;
+  for (int rz = 0; rz < sp.nz; ++rz)
+    for (int ry = 0; ry < sp.ny; ++ry) {
+      int n = 0;
+      for (int cz = rz * sp.zlen; cz < std::min(L, (rz + 1) * sp.zlen); ++cz)
+        for (int cy = ry * sp.ylen; cy < std::min(L, (ry + 1) * sp.ylen); ++cy)
+          for (int cx = 0; cx < L; ++cx)
+            for_each_mirror(L, sp.ny, sp.nz, sp.ylen, sp.zlen, ry, rz, cx, cy, cz, MirrorCount{&n});
+      cap = std::max(cap, n);
+    }
+  return cap;
+}
+
 // Geometry of one CTA's box.
 struct Box {
   int L, bx, by, bxy, vol;  // box extents (bx = L + 2, by = ylen + 2) and volume
@@ -77,10 +138,19 @@ struct Box {
   __device__ __forceinline__ int cell(int ix, int iy, int iz) const { return ix + bx * (iy + by * iz); }
 };
 
-// Update of the link U_mu at box cell bi, local time tl.
+__device__ __forceinline__ void st_cluster(uint32_t a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(uint32_t a, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+// Update of the link U_mu at box cell bi, local time tl; the new angle also
+// goes to the mirrors mirror[m0 .. m1) of the cell (cluster addresses of slot 0).
 template <typename T, int KIND>
-__device__ __forceinline__ void box_link(const Box& b, T* buf, int mu, int tl, int bi, uint32_t site,
-                                         unsigned long long n, uint32_t k0, uint32_t k1, T beta, int* err) {
+__device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* mirror, int m0, int m1, int mu,
+                                         int tl, int bi, uint32_t site, unsigned long long n, uint32_t k0,
+                                         uint32_t k1, T beta, int* err) {
   const int tp = tl + (mu == 0);  // x + mu
   const int bp = bi + b.off(mu);
   auto at = [&](int rho, int t_, int c) { return buf[b.slot(rho, t_) * b.vol + c]; };
@@ -93,9 +163,14 @@ __device__ __forceinline__ void box_link(const Box& b, T* buf, int mu, int tl, i
     w[4] = at(mu, tl - dt, bi - o);   // theta_mu(x - nu)
     w[5] = at(nu, tl - dt, bi - o);   // theta_nu(x - nu)
   };
-  T* self = buf + b.slot(mu, tl) * b.vol + bi;
+  const int sl = b.slot(mu, tl);
+  T* self = buf + sl * b.vol + bi;
   T out;
-  if (new_link_angle<T, KIND>(mu, staples, [&] { return *self; }, site, n, k0, k1, beta, err, &out)) *self = out;
+  if (new_link_angle<T, KIND>(mu, staples, [&] { return *self; }, site, n, k0, k1, beta, err, &out)) {
+    *self = out;
+    const uint32_t soff = static_cast<uint32_t>(sl * b.vol * sizeof(T));
+    for (int m = m0; m < m1; ++m) st_cluster(mirror[m] + soff, out);
+  }
 }
 
 // Grid: one cluster of cs CTAs per unit (lattice, slab); mask d is the slab
@@ -127,18 +202,20 @@ __global__ void __launch_bounds__(kResThreads, 1)
   b.by = b.yl_full + 2;
   b.bxy = b.bx * b.by;
   b.vol = b.bxy * (b.zl_full + 2);
-  const int ry = rank % b.ny, rz = rank / b.ny;
-  b.y0 = ry * b.yl_full;
-  b.z0 = rz * b.zl_full;
-  b.ylen = rz < nz ? max(0, min(g.L, b.y0 + b.yl_full) - b.y0) : 0;
-  b.zlen = rz < nz ? max(0, min(g.L, b.z0 + b.zl_full) - b.z0) : 0;
+  const int bry = rank % b.ny, brz = rank / b.ny;  // this CTA's brick
+  b.y0 = bry * b.yl_full;
+  b.z0 = brz * b.zl_full;
+  b.ylen = brz < nz ? max(0, min(g.L, b.y0 + b.yl_full) - b.y0) : 0;
+  b.zlen = brz < nz ? max(0, min(g.L, b.z0 + b.zl_full) - b.z0) : 0;
   const int K = 4 * d + 3;
   const bool active = rank < b.ny * nz;  // CTAs beyond the brick grid own nothing and mirror nothing
+  const int own = g.L * b.ylen * b.zlen;  // owned sites, index j = cx + L (ry + ylen rz)
   T* buf = reinterpret_cast<T*>(res_smem);
-  // ghost list: (cell, owner's address of the same cell) for every mirrored
-  // cell; cells of spatial parity 0 from the front, parity 1 from the back
-  uint2* ghost = reinterpret_cast<uint2*>(buf + static_cast<size_t>(K) * b.vol);
-  __shared__ int nghost[2];
+  // mirror lists of the owned sites (compressed rows: site j's mirrors are
+  // mirror[mstart[j] .. mstart[j+1]), cluster addresses of their slot-0 cells)
+  int* mstart = reinterpret_cast<int*>(buf + static_cast<size_t>(K) * b.vol);
+  uint32_t* mirror = reinterpret_cast<uint32_t*>(mstart + b.L * b.yl_full * b.zl_full + 1);
+  __shared__ int wsum[kResThreads / 32];
   const uint32_t base = shared_addr(buf);
   // magic divisors; every dividend times its divisor stays below 2^40 (the
   // box fits in shared memory, so all counts are far below 2^20)
@@ -146,24 +223,11 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const int t0 = s * d;
   T* th = static_cast<T*>(Ld.theta);
 
-  // ghost list and the box's links from global memory
-  if (threadIdx.x < 2) nghost[threadIdx.x] = 0;
-  __syncthreads();
+  // the box's links from global memory
   for (int c = threadIdx.x; active && c < b.vol; c += blockDim.x) {
     const int q = fdiv(c, m_bx), ix = c - q * b.bx;
     const int iz = fdiv(q, m_by), iy = q - iz * b.by;
     const int cx = wrapc(ix - 1, g.L), cy = wrapc(b.y0 + iy - 1, g.L), cz = wrapc(b.z0 + iz - 1, g.L);
-    const bool own = ix >= 1 && ix <= g.L && iy >= 1 && iy <= b.ylen && iz >= 1 && iz <= b.zlen;
-    if (!own) {
-      const int oy = cy / b.yl_full, oz = cz / b.zl_full;
-      const int owner = oy + b.ny * oz;
-      const int oc = b.cell(cx + 1, cy - oy * b.yl_full + 1, cz - oz * b.zl_full + 1);
-      const int sp = (cx + cy + cz) & 1;
-      const int i = atomicAdd(&nghost[sp], 1);
-      ghost[sp == 0 ? i : b.vol - 1 - i] =
-          make_uint2(static_cast<uint32_t>(c),
-                     map_to_rank(base + static_cast<uint32_t>(oc * sizeof(T)), static_cast<uint32_t>(owner)));
-    }
     const int x = cx + g.L * (cy + g.L * cz);
     for (int sl = 0; sl < K; ++sl) {
       int rho = 0, tl = sl;
@@ -179,13 +243,71 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const unsigned long long nbase = *Ld.n_dev;
   const uint32_t k0 = Ld.k0, k1 = Ld.k1;
   const T beta = static_cast<T>(Ld.beta);
+  const unsigned long long m_yl = fdiv_magic(max(b.ylen, 1));
+
+  // mirror lists: counts, an exclusive scan over the owned sites (one chunk
+  // per thread), then the addresses
+  const int chunk = (own + blockDim.x - 1) / blockDim.x;
+  const int j_lo = min(own, static_cast<int>(threadIdx.x) * chunk), j_hi = min(own, j_lo + chunk);
+  auto site_of = [&](int j, int* cx, int* cy, int* cz) {
+    const int row = fdiv(j, m_L);
+    *cx = j - row * g.L;
+    const int rzz = fdiv(row, m_yl);
+    *cy = b.y0 + row - rzz * b.ylen;
+    *cz = b.z0 + rzz;
+  };
+  int total = 0;
+  for (int j = j_lo; j < j_hi; ++j) {
+    int cx, cy, cz, cnt = 0;
+    site_of(j, &cx, &cy, &cz);
+    for_each_mirror(g.L, b.ny, nz, b.yl_full, b.zl_full, bry, brz, cx, cy, cz, [&](int, int) { ++cnt; });
+    mstart[j] = cnt;
+    total += cnt;
+  }
+  {  // block-wide exclusive scan of the per-thread totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int w = lane < static_cast<int>(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += v;
+      }
+      wsum[lane] = w;  // inclusive warp prefix
+    }
+    __syncthreads();
+    int run = incl - total + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int j = j_lo; j < j_hi; ++j) {
+      const int cnt = mstart[j];
+      mstart[j] = run;
+      run += cnt;
+    }
+    if (j_hi == own && j_lo < j_hi) mstart[own] = run;
+    if (own == 0 && threadIdx.x == 0) mstart[0] = 0;
+  }
   __syncthreads();
+  for (int j = j_lo; j < j_hi; ++j) {
+    int cx, cy, cz, m = mstart[j];
+    site_of(j, &cx, &cy, &cz);
+    for_each_mirror(g.L, b.ny, nz, b.yl_full, b.zl_full, bry, brz, cx, cy, cz, [&](int r, int cell) {
+      mirror[m++] = map_to_rank(base + static_cast<uint32_t>(cell * sizeof(T)), static_cast<uint32_t>(r));
+    });
+  }
+  // every box is loaded before any CTA stores into another's
+  cluster_sync();
 
   const int hx = g.L / 2;  // site pairs per row
   const int half = hx * b.ylen * b.zlen;
-  const int own = g.L * b.ylen * b.zlen;
   const unsigned long long m_half = fdiv_magic(max(half, 1)), m_hx = fdiv_magic(hx),
-                           m_yl = fdiv_magic(max(b.ylen, 1)), m_own = fdiv_magic(max(own, 1));
+                           m_own = fdiv_magic(max(own, 1));
   for (int round = 0; round < n_rec; ++round) {
     for (int c = 0; c < n_compound; ++c) {
       const unsigned long long n = nbase + 1 + static_cast<unsigned long long>(round) * n_compound + c;
@@ -204,27 +326,15 @@ __global__ void __launch_bounds__(kResThreads, 1)
               const int cy = b.y0 + ry, cz = b.z0 + rz;
               const int cx = cx0 + (((cy + cz + t) & 1) ^ par);
               const int bi = b.cell(cx + 1, ry + 1, rz + 1);
+              const int jo = cx + g.L * row;  // owned-site index
               const uint32_t site = static_cast<uint32_t>(cx + g.L * (cy + g.L * cz) + g.Ns * t);
               if (sweep == 0)
-                box_link<T, 0>(b, buf, mu, tl, bi, site, n, k0, k1, beta, err);
+                box_link<T, 0>(b, buf, mirror, mstart[jo], mstart[jo + 1], mu, tl, bi, site, n, k0, k1, beta, err);
               else
-                box_link<T, 1>(b, buf, mu, tl, bi, site, n, k0, k1, beta, err);
+                box_link<T, 1>(b, buf, mirror, mstart[jo], mstart[jo + 1], mu, tl, bi, site, n, k0, k1, beta, err);
             }
+            // the pass's links and their mirrors are in place for every CTA
             cluster_sync();
-            // ghost copies of the links this pass moved: slots of mu at tl in
-            // [tl_lo, d), mirrored cells whose site has parity par at time t0 + tl
-            // (spatial parity par ^ (t & 1))
-            for (int tl = tl_lo; active && tl < d; ++tl) {
-              const int sp = par ^ ((t0 + tl) & 1);
-              const int cnt = nghost[sp], first = sp == 0 ? 0 : b.vol - cnt;
-              const int sl = b.slot(mu, tl);
-              const uint32_t soff = static_cast<uint32_t>(sl * b.vol * sizeof(T));
-              for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-                const uint2 e = ghost[first + i];
-                buf[sl * b.vol + e.x] = ld_cluster(e.y + soff, static_cast<T*>(nullptr));
-              }
-            }
-            __syncthreads();
           }
     }
     if (record) {
@@ -259,12 +369,11 @@ __global__ void __launch_bounds__(kResThreads, 1)
         osum[((static_cast<size_t>(s * nc + y) * 2 + 0) * g.Ns + x) * RecBatch<T>::n + slot] = re;
         osum[((static_cast<size_t>(s * nc + y) * 2 + 1) * g.Ns + x) * RecBatch<T>::n + slot] = im;
       }
-      // the record reads only this CTA's box; the next round's first pass
-      // writes it after this barrier
-      __syncthreads();
     }
+    // records read mirrored cells: no CTA stores into them before every
+    // record of this round is done
+    cluster_sync();
   }
-  cluster_sync();  // no CTA reads another's shared memory after this point
 
   // write back the updated links (U_0 at tl in [0, d), U_i at tl in [1, d))
   for (int k = threadIdx.x; k < K * own; k += blockDim.x) {
@@ -334,7 +443,10 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, ResidentPlan*
       const Geom& g = geoms[i];
       split[i] = brick_split(g.L, cs);
       if (g.Nt % mask != 0 || g.L % 2 != 0) fits = false;
-      smem = std::max(smem, static_cast<size_t>(split[i].box) * ((4 * mask + 3) * sizeof(T) + sizeof(uint2)));
+      const BrickSplit& sp = split[i];
+      smem = std::max(smem, static_cast<size_t>(sp.box) * (4 * mask + 3) * sizeof(T) +
+                                (static_cast<size_t>(g.L) * sp.ylen * sp.zlen + 1 + mirror_capacity(g.L, sp)) *
+                                    sizeof(uint32_t));
     }
     if (!fits || smem > kResSmemMax) continue;
     cudaLaunchAttribute at[1];
