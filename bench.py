@@ -326,6 +326,10 @@ def run_gpu(args, w, rank, world):
 
     p = ml.Params.from_workload(w, seed=w.seed + 1000 * rank)
     lat = ml.Lattice(p)
+    if args.sweep_mode == "resident":  # full sweeps in the persistent kernel
+        lat.sweep_mode = SWEEP_MODES["persistent"]
+    if args.sweep_mode != "auto":
+        lat.sweep_mode = SWEEP_MODES[args.sweep_mode]
     st = lat.stream
     lat.thermalize(w.n_therm)
     rec = torch.empty((1, lat.rec_len), dtype=torch.float64, device=lat.device)
@@ -375,6 +379,8 @@ def run_gpu(args, w, rank, world):
     n_folds = -(-w.n_sub // nB)
     # the k0 full sweeps run as one launch of k_between compound sweeps; a
     # slab sub-update is one launch of the sweep kernel with the record fused
+    # (the resident kernel runs a ring buffer of nB sub-updates per launch and
+    # its folds overlap on the SMs it leaves free, so shares can sum past 1)
     per_step = {
         "subupdate": (ml.ML_K_SUBUPDATE, w.n_sub),
         "full_sweeps": (ml.ML_K_FULLSWEEP, w.k_between),
@@ -385,14 +391,17 @@ def run_gpu(args, w, rank, world):
     share = {name: kms[name] * per_step[name][1] / (ms / args.steps) for name in per_step}
     dominant = max(("subupdate", "accumulate"), key=share.get)
     peak, peak_kind = measured_peaks()
-    nbytes = algorithmic_bytes(w, "sweep" if dominant == "subupdate" else dominant, nB)
-    achieved = nbytes / (kms[dominant] * 1e-3) / 1e9
+    resident = lat.sweep_mode == ml.ML_SWEEP_RESIDENT
+    per_launch = nB if (dominant == "subupdate" and resident) else 1  # sub-updates per launch
+    nbytes = algorithmic_bytes(w, "sweep" if dominant == "subupdate" else dominant, nB) * per_launch
+    launch_ms = kms[dominant] * per_launch
+    achieved = nbytes / (launch_ms * 1e-3) / 1e9
     impl = ["k_sweeps_table (persistent, record fused)", "k_pass_table + k_record_table",
             "k_sweeps_resident (cluster-resident slabs, record fused)"][lat.sweep_mode]
     roof = {"kernel": {"subupdate": impl, "accumulate": "k_accum_T_table + k_accum_O_table"}[dominant], "bound": "hbm",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
-            "launch_ms": kms[dominant], "batch_slots": nB}
+            "launch_ms": launch_ms, "sub_updates_per_launch": per_launch, "batch_slots": nB}
     hbm_point = hbm_sweep_point(ml, peak) if rank == 0 and not args.no_extra else None
     batch_point = batched_point(ml) if rank == 0 and not args.no_extra else None
 
@@ -450,6 +459,9 @@ def run_gpu(args, w, rank, world):
     return 0
 
 
+SWEEP_MODES = {"persistent": 0, "passes": 1, "resident": 2}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,6 +473,9 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the 64^4 HBM sweep point and the batch")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the first timed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--sweep-mode", default="auto", choices=["auto", "persistent", "passes", "resident"],
+                    help="force the single lattice's sweep implementation (default: autotuned; resident: "
+                         "sub-updates cluster-resident, full sweeps persistent)")
     ap.add_argument("--serving-requests", type=int, default=1000,
                     help="requests of the serving measurement (0 skips it)")
     args = ap.parse_args()

@@ -200,7 +200,9 @@ typedef enum {
   ML_K_SWEEP = 5,      /* one compound slab sweep (the handle's implementation)   */
   ML_K_SUBUPDATE = 6,  /* one slab sub-update as measurements run it: compound
                           sweep and record (fused in the persistent and
-                          resident kernels)                                     */
+                          resident kernels; the resident kernel runs a ring
+                          buffer of sub-updates per launch, and the time is
+                          that launch's divided by its sub-updates)           */
   ML_K_FULLSWEEP = 7   /* one compound sweep without frozen links, as between
                           measurements and in ml_thermalize                     */
 } ml_kernel_class;

@@ -567,52 +567,77 @@ int plan_resident_sweeps(Engine* e) {
   return ML_OK;
 }
 
-// Autotuning of the sweep implementation: time one slab sub-update (compound
-// sweep and record) of the table as the persistent cooperative kernel, as a
+// Autotuning of the sweep implementation, on the timing copies: one slab
+// sub-update (sweep and record) as the persistent cooperative kernel, as a
 // captured graph of per-pass kernels and, when the slabs fit, as the
-// cluster-resident kernel (on the timing copies; the records land in ring
-// slots that every measurement rewrites before use), alternating the
-// candidates over several rounds (the clocks may still be ramping up), and
-// keep the fastest.  Small tables are latency-bound and favour the persistent
-// or resident kernels; large ones the per-pass kernels' full occupancy.
+// cluster-resident kernel (timed as measurements run it, a ring buffer of nB
+// sub-updates per launch, per sub-update; the records land in ring slots
+// that every measurement rewrites before use); and one compound sweep without
+// frozen links as the persistent kernel and as the per-pass graph.  The
+// candidates alternate over several rounds (the clocks may still be ramping
+// up) and the fastest of each group is kept.  Small tables are latency-bound
+// and favour the persistent or resident kernels; large ones the per-pass
+// kernels' full occupancy.
 int choose_sweep_mode(Engine* e) {
   int st = ensure_scratch(e);
   if (!st) st = refresh_scratch(e);
   if (st) return st;
   const LatDesc* tab = e->d_desc_scratch;
-  const bool resident = resident_plan(e, e->slab) != nullptr;
-  Graph pp;
+  const ResidentPlan* res = resident_plan(e, e->slab);
+  Graph pp, pf;
   st = capture(e, &pp, [&] { return enqueue_sweeps_mode(e, tab, 1, e->slab, ML_SWEEP_PASSES, true, 0, 0); });
-  if (st) return st;
-  auto run = [&](int mode) {
-    return mode == ML_SWEEP_PASSES ? launch_graph(e, pp)
-                                   : enqueue_sweeps_mode(e, tab, 1, e->slab, mode, true, 0, 0);
+  if (!st) st = capture(e, &pf, [&] { return enqueue_sweeps_table(e, tab, 1, 0, ML_SWEEP_PASSES); });
+  if (st) {
+    if (pp.exec) cudaGraphExecDestroy(pp.exec);
+    return st;
+  }
+  // candidates: 0-2 sub-update (persistent, passes, resident), 3-4 full sweep
+  // (persistent, passes); per-launch sub-update counts divide the times
+  const int nc = 5;
+  const int per[nc] = {1, 1, e->nB, 1, 1};
+  auto run = [&](int c) -> int {
+    switch (c) {
+      case 0: return enqueue_sweeps_mode(e, tab, 1, e->slab, ML_SWEEP_PERSISTENT, true, 0, 0);
+      case 1: return launch_graph(e, pp);
+      case 2:
+        return launch_sweeps_resident(e->fp64, *res, tab, e->td.nlat, e->n_or, 1, e->d_err, e->stream, true, 0, 0,
+                                      e->nB)
+                   ? ML_ECUDA
+                   : ML_OK;
+      case 3: return enqueue_sweeps_table(e, tab, 1, 0, ML_SWEEP_PERSISTENT);
+      default: return launch_graph(e, pf);
+    }
   };
-  const int nmodes = resident ? 3 : 2;
-  cudaEvent_t ev[4];
+  auto live = [&](int c) { return c != 2 || res != nullptr; };
+  cudaEvent_t ev[nc + 1];
   for (cudaEvent_t& x : ev) ML_CUDA(cudaEventCreate(&x));
   const int rounds = 4, reps = 2;
-  float best[3] = {1e30f, 1e30f, 1e30f};
-  for (int m = 0; m < nmodes && !st; ++m) st = run(m);  // warm-up
+  float best[nc];
+  for (float& x : best) x = 1e30f;
+  for (int c = 0; c < nc && !st; ++c)
+    if (live(c)) st = run(c);  // warm-up
   for (int r = 0; r < rounds && !st; ++r) {
     st = cuda_status(cudaEventRecord(ev[0], e->stream));
-    for (int m = 0; m < nmodes && !st; ++m) {
-      for (int i = 0; i < reps && !st; ++i) st = run(m);
-      if (!st) st = cuda_status(cudaEventRecord(ev[m + 1], e->stream));
+    for (int c = 0; c < nc && !st; ++c) {
+      for (int i = 0; i < reps && !st && live(c); ++i) st = run(c);
+      if (!st) st = cuda_status(cudaEventRecord(ev[c + 1], e->stream));
     }
-    if (!st) st = cuda_status(cudaEventSynchronize(ev[nmodes]));
-    for (int m = 0; m < nmodes && !st; ++m) {
+    if (!st) st = cuda_status(cudaEventSynchronize(ev[nc]));
+    for (int c = 0; c < nc && !st; ++c) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[m], ev[m + 1]);
-      best[m] = std::min(best[m], ms);
+      cudaEventElapsedTime(&ms, ev[c], ev[c + 1]);
+      if (live(c)) best[c] = std::min(best[c], ms / per[c]);
     }
   }
   if (!st) {
-    e->full_mode = best[ML_SWEEP_PASSES] < best[ML_SWEEP_PERSISTENT] ? ML_SWEEP_PASSES : ML_SWEEP_PERSISTENT;
-    e->sweep_mode = (resident && best[ML_SWEEP_RESIDENT] < best[e->full_mode]) ? ML_SWEEP_RESIDENT : e->full_mode;
+    e->full_mode = best[4] < best[3] ? ML_SWEEP_PASSES : ML_SWEEP_PERSISTENT;
+    int m = best[1] < best[0] ? ML_SWEEP_PASSES : ML_SWEEP_PERSISTENT;
+    if (res && best[2] < best[m]) m = ML_SWEEP_RESIDENT;
+    e->sweep_mode = m;
   }
   for (cudaEvent_t& x : ev) cudaEventDestroy(x);
   cudaGraphExecDestroy(pp.exec);
+  cudaGraphExecDestroy(pf.exec);
   if (st) return st;
   return check_errors(e);
 }
@@ -955,11 +980,22 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   if (!st) st = join(e->side, e->stream, e->ev_side);
   if (!st) st = refresh_scratch(e);
   if (st) return st;
+  // resident sub-updates run a ring buffer of nB per launch, as measurements
+  // do: time the launch and report per sub-update
+  const ResidentPlan* res =
+      kernel == ML_K_SUBUPDATE && e->sweep_mode == ML_SWEEP_RESIDENT ? resident_plan(e, e->slab) : nullptr;
   cudaEvent_t e0, e1;
   ML_CUDA(cudaEventCreate(&e0));
   ML_CUDA(cudaEventCreate(&e1));
   ML_CUDA(cudaEventRecord(e0, e->stream));
   for (int i = 0; i < reps && !st; ++i) {
+    if (res) {
+      st = launch_sweeps_resident(e->fp64, *res, e->d_desc_scratch, e->td.nlat, e->n_or, 1, e->d_err, e->stream, true,
+                                  0, 0, e->nB)
+               ? ML_ECUDA
+               : ML_OK;
+      continue;
+    }
     switch (kernel) {
       case ML_K_HEATBATH:
       case ML_K_OVERRELAX:
@@ -992,7 +1028,7 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  *avg_ms = static_cast<double>(ms) / reps;
+  *avg_ms = static_cast<double>(ms) / reps / (res ? e->nB : 1);
   if (st) return st;
   return check_errors(e);
 }

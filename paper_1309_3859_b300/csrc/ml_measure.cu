@@ -501,15 +501,18 @@ __global__ void __launch_bounds__(256) k_products_W(Geom g, int nslab, MeasLayou
   }
 }
 
-// Fixed-order sum of the warp partials of each output into the record.
-__global__ void k_finalize_products(const double2* __restrict__ partial, int nwarps, Geom g, MeasLayout m,
-                                    double* __restrict__ rec) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+// Fixed-order sum of the warp partials of each output into the record: one
+// warp per output, lane l adding partials l, l + 32, ..., then a shuffle tree.
+__global__ void __launch_bounds__(256) k_finalize_products(const double2* __restrict__ partial, int nwarps, Geom g,
+                                                           MeasLayout m, double* __restrict__ rec) {
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nW = m.np * m.nc * 2;
   const int nout = m.nr + m.nrf + m.nrf * nW;
-  if (o >= nout) return;
+  if (o >= nout) return;  // whole warp
   double2 s = make_double2(0.0, 0.0);
-  for (int w = 0; w < nwarps; ++w) s = cadd(s, partial[static_cast<size_t>(o) * nwarps + w]);
+  for (int w = lane; w < nwarps; w += 32) s = cadd(s, partial[static_cast<size_t>(o) * nwarps + w]);
+  s = warp_sum(s);
+  if (lane != 0) return;
   size_t off;
   double scale;
   if (o < m.nr) {
@@ -577,19 +580,30 @@ __global__ void __launch_bounds__(256) k_plaq_mean(const T* __restrict__ th, Geo
   if ((threadIdx.x & 31) == 0) part[i >> 5] = v;
 }
 
-__global__ void k_finalize_naive(const double2* __restrict__ partial, int nwarps, const double* __restrict__ ppart,
-                                 int npw, Geom g, MeasLayout m, double* __restrict__ rec) {
-  for (int o = threadIdx.x; o <= m.nr; o += blockDim.x) {
-    if (o < m.nr) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int w = 0; w < nwarps; ++w) s = cadd(s, partial[static_cast<size_t>(o) * nwarps + w]);
-      rec[m.off_naive + 2 * o] = s.x / g.Ns;
-      rec[m.off_naive + 2 * o + 1] = s.y / g.Ns;
-    } else {
-      double s = 0.0;
-      for (int w = 0; w < npw; ++w) s += ppart[w];
-      rec[m.off_plaq] = s / (6.0 * g.V);
-    }
+// Fixed-order sums of the naive and plaquette partials: block o < nr adds
+// output o's warp partials, block nr the plaquette partials; thread t adds
+// partials t, t + 256, ..., then warp trees and the 8 warp sums in order.
+__global__ void __launch_bounds__(256) k_finalize_naive(const double2* __restrict__ partial, int nwarps,
+                                                        const double* __restrict__ ppart, int npw, Geom g,
+                                                        MeasLayout m, double* __restrict__ rec) {
+  __shared__ double2 sh[8];
+  const int o = blockIdx.x, t = threadIdx.x;
+  double2 s = make_double2(0.0, 0.0);
+  if (o < m.nr)
+    for (int w = t; w < nwarps; w += blockDim.x) s = cadd(s, partial[static_cast<size_t>(o) * nwarps + w]);
+  else
+    for (int w = t; w < npw; w += blockDim.x) s.x += ppart[w];
+  s = warp_sum(s);
+  if ((t & 31) == 0) sh[t >> 5] = s;
+  __syncthreads();
+  if (t != 0) return;
+  s = make_double2(0.0, 0.0);
+  for (int w = 0; w < 8; ++w) s = cadd(s, sh[w]);
+  if (o < m.nr) {
+    rec[m.off_naive + 2 * o] = s.x / g.Ns;
+    rec[m.off_naive + 2 * o + 1] = s.y / g.Ns;
+  } else {
+    rec[m.off_plaq] = s.x / (6.0 * g.V);
   }
 }
 
@@ -722,7 +736,7 @@ void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, 
                 nb, nwarps, s);
   const int nW = m.np * m.nc * 2;
   const int nout = m.nr + m.nrf + m.nrf * nW;
-  k_finalize_products<<<blocks_for(nout, 128), 128, 0, s>>>(partial, nwarps, g, m, rec);
+  k_finalize_products<<<blocks_for(32ll * nout, 256), 256, 0, s>>>(partial, nwarps, g, m, rec);
   count_launches(1);
 }
 
@@ -739,7 +753,7 @@ void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, con
     k_naive<float><<<nb, 256, 0, s>>>(static_cast<const float*>(theta), g, m, partial, nwarps);
     k_plaq_mean<float><<<nbv, 256, 0, s>>>(static_cast<const float*>(theta), g, ppart);
   }
-  k_finalize_naive<<<1, 128, 0, s>>>(partial, nwarps, ppart, nbv * 8, g, m, rec);
+  k_finalize_naive<<<m.nr + 1, 256, 0, s>>>(partial, nwarps, ppart, nbv * 8, g, m, rec);
   count_launches(3);
 }
 
