@@ -57,7 +57,7 @@ typedef struct {
   uint64_t seed;
   int n_or;        /* overrelaxation sweeps per heatbath sweep (Section II: 3) */
   int draws;       /* 0: 52-bit uniforms, two Philox blocks per trial;
-                      1: 23-bit uniforms, one Philox block per trial         */
+                      1: 23-bit uniforms, two trials per Philox block        */
   int slab;        /* inner slab thickness d                                 */
   int n_sub;       /* inner sub-updates n2 (Algorithm 1)                     */
   int outer_slab;  /* 0 = single level, else outer slab thickness (Alg. 1: 4) */
@@ -123,7 +123,12 @@ double orc_uniform23(uint32_t a) {
 
 /* Uniforms (u1, u2, u3) of rejection trial m for link (site, mu) in heatbath
  * sweep number n.  key = (seed lo, seed hi), counter = (site, mu + 4 j, n lo,
- * n hi); trial m reads blocks j = 2m, 2m+1 (52-bit draws) or j = m (23-bit). */
+ * n hi).  52-bit draws: trial m reads blocks j = 2m (u1 = words 0,1; u2 =
+ * words 2,3) and 2m+1 (u3 = words 0,1).  23-bit draws: trials 2j and 2j+1
+ * share block j; trial 2j takes words 0 and 1, trial 2j+1 words 2 and 3, as
+ * u1 and u2, and u3 is the 23-bit uniform of u1's word shifted left by 23
+ * (its nine low bits, which u1 does not use, so u3 > 1/2 exactly when bit 8
+ * of that word is set). */
 static void link_uniforms(const orc_params *p, uint32_t site, int mu, uint64_t n, int m, double u[3]) {
   uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
   uint32_t out0[4], out1[4];
@@ -136,11 +141,12 @@ static void link_uniforms(const orc_params *p, uint32_t site, int mu, uint64_t n
     u[1] = orc_uniform52(out0[2], out0[3]);
     u[2] = orc_uniform52(out1[0], out1[1]);
   } else {
-    uint32_t c0[4] = {site, (uint32_t)(mu + 4 * m), (uint32_t)n, (uint32_t)(n >> 32)};
+    uint32_t c0[4] = {site, (uint32_t)(mu + 4 * (m >> 1)), (uint32_t)n, (uint32_t)(n >> 32)};
     orc_philox4x32_10(c0, key, out0);
-    u[0] = orc_uniform23(out0[0]);
-    u[1] = orc_uniform23(out0[1]);
-    u[2] = orc_uniform23(out0[2]);
+    const int w = 2 * (m & 1);
+    u[0] = orc_uniform23(out0[w]);
+    u[1] = orc_uniform23(out0[w + 1]);
+    u[2] = orc_uniform23(out0[w] << 23);
   }
 }
 

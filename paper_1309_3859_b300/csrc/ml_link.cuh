@@ -11,8 +11,10 @@ namespace ml {
 
 // Random uniforms of rejection trial m for link (site, mu), sweep n.
 // FP64: blocks j = 2m (u1 = words 0,1; u2 = words 2,3) and 2m+1 (u3 = words
-// 0,1) with 52-bit uniforms.  FP32: block j = m, words 0, 1, 2 with 23-bit
-// uniforms.  Counter = (site, mu + 4 j, n lo, n hi), key = seed.
+// 0,1) with 52-bit uniforms.  FP32: trials 2j and 2j+1 share block j, trial
+// 2j taking words 0, 1 and trial 2j+1 words 2, 3 as 23-bit u1, u2; the sign
+// draw u3 > 1/2 is bit 8 of u1's word (one of the nine bits u1 drops).
+// Counter = (site, mu + 4 j, n lo, n hi), key = seed.
 template <typename T>
 struct Draws;
 
@@ -37,10 +39,11 @@ struct Draws<double> {
 
 template <>
 struct Draws<float> {
-  __device__ static __forceinline__ U4 block(uint32_t site, int mu, unsigned long long n, int m, uint32_t k0,
+  // block j (trials 2j, 2j + 1)
+  __device__ static __forceinline__ U4 block(uint32_t site, int mu, unsigned long long n, int j, uint32_t k0,
                                              uint32_t k1) {
     return philox4x32_10(
-        U4{site, static_cast<uint32_t>(mu + 4 * m), static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)}, k0, k1);
+        U4{site, static_cast<uint32_t>(mu + 4 * j), static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32)}, k0, k1);
   }
 };
 
@@ -57,10 +60,10 @@ __device__ __forceinline__ float bf_envelope(float kappa) {
   const float rho = __fdividef(tau * tau_minus_2, (tau + sqrtf(2.0f * tau)) * (2.0f * kappa));
   return __fdividef(fmaf(rho, rho, 1.0f), 2.0f * rho);
 }
-__device__ __forceinline__ bool bf_trial(float kappa, float s, uint32_t site, int mu, unsigned long long n, int m,
-                                         uint32_t k0, uint32_t k1, float* f_out, bool* neg) {
-  const U4 o = Draws<float>::block(site, mu, n, m, k0, k1);
-  const float u1 = uniform23(o.x), u2 = uniform23(o.y);
+// One trial from words (a, b) of its Philox block: u1 = uniform23(a), u2 =
+// uniform23(b), sign from bit 8 of a.
+__device__ __forceinline__ bool bf_trial(float kappa, float s, uint32_t a, uint32_t b, float* f_out, bool* neg) {
+  const float u1 = uniform23(a), u2 = uniform23(b);
   const float z = Prec<float>::cos_pi_u(u1);
   float f = __fdividef(fmaf(s, z, 1.0f), s + z);
   f = fminf(fmaxf(f, -1.0f), 1.0f);
@@ -68,7 +71,7 @@ __device__ __forceinline__ bool bf_trial(float kappa, float s, uint32_t site, in
   // log(c / u2) as a difference of hardware logarithms (c > 0, u2 > 0)
   if ((c * (2.0f - c) - u2 > 0.0f) || (__logf(c) - __logf(u2) + 1.0f - c >= 0.0f)) {
     *f_out = f;
-    *neg = !(uniform23(o.z) > 0.5f);
+    *neg = ((a >> 8) & 1u) == 0u;  // u3 = uniform23(a << 23) > 1/2 exactly when bit 8 of a is set
     return true;
   }
   return false;
@@ -112,10 +115,12 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
       return true;
     }
     const float s = bf_envelope(kappa);
-    for (int m = 0; m < kMaxTrials; ++m) {
+    static_assert(kMaxTrials % 2 == 0, "trials come in pairs per Philox block");
+    for (int j = 0; j < kMaxTrials / 2; ++j) {
+      const U4 o = Draws<float>::block(site, mu, n, j, k0, k1);
       float f;
       bool neg;
-      if (bf_trial(kappa, s, site, mu, n, m, k0, k1, &f, &neg)) {
+      if (bf_trial(kappa, s, o.x, o.y, &f, &neg) || bf_trial(kappa, s, o.z, o.w, &f, &neg)) {
         const float a = acosf(f);
         *psi = neg ? -a : a;
         return true;
