@@ -271,10 +271,16 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
 }
 
 constexpr int kProbesPerThread = 3;
+constexpr int kAccGroup = 2;       // slab sums of a probe loaded together (components x (Re, Im))
+// launch bound of the fold, blocks per SM: FP32 64 registers, FP64 128, no spills
+template <typename T>
+constexpr int fold_min_blocks() {
+  return sizeof(T) == 4 ? 4 : 2;
+}
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict__ desc,
-                                                       const LatCtl* __restrict__ ctl, int buf, int nrec) {
+__global__ void __launch_bounds__(256, fold_min_blocks<T>())
+    k_accum_O_table(const LatDesc* __restrict__ desc, const LatCtl* __restrict__ ctl, int buf, int nrec) {
   constexpr int B = RecBatch<T>::n;
   constexpr int kMaxCK = 12;  // components x (Re, Im) insertions
   const int li = blockIdx.z;
@@ -309,29 +315,32 @@ __global__ void __launch_bounds__(256) k_accum_O_table(const LatDesc* __restrict
   for (int b = bg * kProbesPerThread; b < b_end; ++b) {
     const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
     const size_t abase = (((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * nck) * g.Ns + x;
-    // every accumulator of this probe is read before the arithmetic, so the
-    // loads of all components are in flight together
-    A a[kMaxCK];
+    // the slab sums of a group are read before its arithmetic, so their
+    // loads are in flight together
+    for (int q0 = 0; q0 < nck; q0 += kAccGroup) {
+      A a[kAccGroup];
 #pragma unroll
-    for (int q = 0; q < kMaxCK; ++q)
-      if (q < nck) a[q] = acc[abase + static_cast<size_t>(q) * g.Ns];
+      for (int i = 0; i < kAccGroup; ++i)
+        if (q0 + i < nck) a[i] = acc[abase + static_cast<size_t>(q0 + i) * g.Ns];
 #pragma unroll
-    for (int q = 0; q < kMaxCK; ++q) {
-      if (q >= nck) break;
-      const int ci = q >> 1, k = q & 1;
-      T o[B];
-      load_batch<T>(osum + ((static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0) * B, o);
-      T sr = T(0), si = T(0);
+      for (int i = 0; i < kAccGroup; ++i) {
+        const int q = q0 + i;
+        if (q >= nck) break;
+        const int ci = q >> 1, k = q & 1;
+        T o[B];
+        load_batch<T>(osum + ((static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0) * B, o);
+        T sr = T(0), si = T(0);
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        sr += er[j] * o[j];
-        si += ei[j] * o[j];
+        for (int j = 0; j < B; ++j) {
+          sr += er[j] * o[j];
+          si += ei[j] * o[j];
+        }
+        acc_add(a[i], sr, si);
       }
-      acc_add(a[q], sr, si);
-    }
 #pragma unroll
-    for (int q = 0; q < kMaxCK; ++q)
-      if (q < nck) acc[abase + static_cast<size_t>(q) * g.Ns] = a[q];
+      for (int i = 0; i < kAccGroup; ++i)
+        if (q0 + i < nck) acc[abase + static_cast<size_t>(q0 + i) * g.Ns] = a[i];
+    }
   }
 }
 
@@ -406,7 +415,8 @@ __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, Mea
 // is read, so no nslab over- or underflows binary32; the per-warp partials
 // are written in double.
 // ---------------------------------------------------------------------------
-constexpr int kWChunk = 12;
+constexpr int kWChunk = 6;         // values of j per thread
+constexpr int kProdMinBlocks = 3;  // launch bound: blocks per SM (80 registers, no spills)
 
 template <typename M>
 __device__ __forceinline__ typename M::cplx slab_factor(typename M::cplx t, typename M::real in) {
@@ -452,9 +462,9 @@ __global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayou
 // keeps the prefix product running and reads the kWChunk [TO] sums of each
 // slab together.
 template <typename A>
-__global__ void __launch_bounds__(256) k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT,
-                                                    const A* __restrict__ accO, double inv_n,
-                                                    double2* __restrict__ partial, int nwarps) {
+__global__ void __launch_bounds__(256, kProdMinBlocks)
+    k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT, const A* __restrict__ accO,
+                 double inv_n, double2* __restrict__ partial, int nwarps) {
   using M = AccMath<A>;
   using C = typename M::cplx;
   using R = typename M::real;
