@@ -338,7 +338,7 @@ int check_errors(Engine* e) {
 }
 
 void destroy_graphs(Engine* e) {
-  std::vector<Graph*> all = {&e->g_full, &e->g_outer, &e->g_one_full, &e->g_flush[0], &e->g_flush[1]};
+  std::vector<Graph*> all = {&e->g_full, &e->g_outer, &e->g_one_full};
   for (int b = 0; b < 2; ++b)
     for (int j = 0; j < kBatchMax; ++j) all.push_back(&e->g_sub[b][j]);
   for (Graph* gr : all)
@@ -349,25 +349,41 @@ void destroy_graphs(Engine* e) {
 }
 
 // hand ring buffer `buf` (nrec records) from the main stream to the fold on
-// the accumulation stream
-int hand_over(Engine* e, int buf, int nrec) {
+// the accumulation stream.  defer_O: the field-insertion part of this fold is
+// left to the products (the buffer's tail); the caller marks the buffer free
+// (ev_fold) after them.  first: the inner loop's first fold, which starts the
+// slab sums from zero.
+int hand_over(Engine* e, int buf, int nrec, bool defer_O, bool first) {
   ML_CUDA(cudaEventRecord(e->ev_rec[buf], e->stream));
   ML_CUDA(cudaStreamWaitEvent(e->side, e->ev_rec[buf], 0));
-  if (nrec == e->nB) {
-    int st = launch_graph(e, e->g_flush[buf], e->side);
-    if (st) return st;
-  } else {
-    launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, nrec, e->side);
-  }
-  ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
+  launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, nrec, e->side, defer_O, first);
+  if (!defer_O) ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
   return ML_OK;
 }
 
 // inner loop of n_sub slab sub-updates (main stream), folding every nB
 // records on the accumulation stream while the sweeps continue; a ring
-// buffer is reused only after its previous fold has finished
-int run_inner_loop(Engine* e) {
+// buffer is reused only after its previous fold has finished.  With tail_buf,
+// the last buffer's field-insertion fold is deferred to the products and
+// (*tail_buf, *tail_nrec) name it.
+int run_inner_loop(Engine* e, int* tail_buf = nullptr, int* tail_nrec = nullptr, bool* tail_first = nullptr) {
   int buf = e->cur_buf, slot = 0;
+  bool first = true;  // the slab sums are not cleared: the first fold starts them from zero
+  auto fold = [&](int buf_, int nrec_) {
+    const int st = hand_over(e, buf_, nrec_, false, first);
+    first = false;
+    return st;
+  };
+  auto last = [&](int buf_, int nrec_) {
+    if (tail_buf) {
+      *tail_buf = buf_;
+      *tail_nrec = nrec_;
+      *tail_first = first;
+    }
+    const int st = hand_over(e, buf_, nrec_, tail_buf != nullptr, first);
+    first = false;
+    return st;
+  };
   if (const ResidentPlan* p = e->sweep_mode == ML_SWEEP_RESIDENT ? resident_plan(e, e->slab) : nullptr) {
     // one cluster-resident launch per ring buffer: the sweeps keep their
     // SMs, the previous buffer's fold runs on the others
@@ -377,7 +393,7 @@ int run_inner_loop(Engine* e) {
       if (launch_sweeps_resident(e->fp64, *p, e->d_desc, e->td.nlat, e->n_or, 1, e->d_err, e->stream, true, buf, 0,
                                  cnt))
         return ML_ECUDA;
-      int st = hand_over(e, buf, cnt);
+      int st = i + cnt == e->n_sub ? last(buf, cnt) : fold(buf, cnt);
       if (st) return st;
       buf ^= 1;
       i += cnt;
@@ -390,7 +406,7 @@ int run_inner_loop(Engine* e) {
     int st = launch_graph(e, e->g_sub[buf][slot]);
     if (st) return st;
     if (++slot == e->nB) {
-      st = hand_over(e, buf, slot);
+      st = i + 1 == e->n_sub ? last(buf, slot) : fold(buf, slot);
       if (st) return st;
       buf ^= 1;
       slot = 0;
@@ -398,19 +414,11 @@ int run_inner_loop(Engine* e) {
     }
   }
   if (slot > 0) {
-    int st = hand_over(e, buf, slot);
+    int st = last(buf, slot);
     if (st) return st;
     buf ^= 1;
   }
   e->cur_buf = buf;
-  return ML_OK;
-}
-
-int zero_inner(Engine* e, cudaStream_t s) {
-  for (LatState* L : e->lats) {
-    ML_CUDA(cudaMemsetAsync(L->accT, 0, L->accT_bytes, s));
-    if (L->accO_bytes) ML_CUDA(cudaMemsetAsync(L->accO, 0, L->accO_bytes, s));
-  }
   return ML_OK;
 }
 
@@ -460,14 +468,17 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
     for (LatState* L : e->lats) ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->side));
     int ncfg = 0;
     if (e->outer_slab == 0) {
-      st = zero_inner(e, e->side);
-      if (!st) st = run_inner_loop(e);
+      // the last ring buffer's field insertions are folded by the products
+      int tb = 0, tn = 0;
+      bool tfirst = false;
+      st = run_inner_loop(e, &tb, &tn, &tfirst);
       if (st) return st;
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
         launch_products(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
-                        out[li], e->side);
+                        out[li], e->side, ProductTail{L->theta_rec[tb], L->osum[tb], tn, tfirst ? 1 : 0});
       }
+      ML_CUDA(cudaEventRecord(e->ev_fold[tb], e->side));  // the tail buffer is free after the products
       ncfg = e->n_sub;
     } else {
       for (LatState* L : e->lats) {
@@ -476,7 +487,6 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       }
       for (int o = 0; o < e->n_sub_outer; ++o) {
         st = launch_graph(e, e->g_outer);
-        if (!st) st = zero_inner(e, e->side);
         if (!st) st = run_inner_loop(e);
         if (st) return st;
         for (LatState* L : e->lats)
@@ -506,10 +516,6 @@ int capture_graphs(Engine* e) {
   for (int b = 0; b < 2; ++b) {
     for (int j = 0; j < e->nB && !st; ++j)
       st = capture(e, &e->g_sub[b][j], [&] { return enqueue_sub_update(e, b, j); });
-    if (!st) st = capture(e, &e->g_flush[b], [&] {
-      launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, b, e->nB, e->stream);
-      return ML_OK;
-    });
   }
   if (!st && e->outer_slab) st = capture(e, &e->g_outer, [&] { return enqueue_sweeps(e, 1, e->outer_slab); });
   return st;
@@ -898,10 +904,8 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
   ML_CUDA(cudaMemsetAsync(out, 0, m.rec_len * sizeof(double), e->stream));
   launch_naive_and_plaquette(e->fp64, L->theta, L->g, m, L->partial_naive, out, e->stream);
   ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->stream));
-  st = zero_inner(e, e->stream);
-  if (st) return st;
   launch_record_table(e->fp64, e->d_desc, e->td, nullptr, buf, 0, e->stream);
-  launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream);
+  launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream, false, true);
   launch_products(L->g, L->g.Nt / e->slab, m, !e->fp64, L->accT, L->accO, 1.0, L->partial, out, e->stream);
   launch_write_vac(L->vac_acc, 1.0, m, out, e->stream);
   ML_CUDA(cudaGetLastError());

@@ -65,7 +65,7 @@ struct Engine {
   int nB = kBatchMax, cur_buf = 0;  // ring slots (rec_batch of the precision)
   cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_fold[2] = {nullptr, nullptr};
   cudaEvent_t ev_main = nullptr, ev_side = nullptr;
-  Graph g_full, g_outer, g_one_full, g_flush[2], g_sub[2][kBatchMax];
+  Graph g_full, g_outer, g_one_full, g_sub[2][kBatchMax];
   double* rec_buf = nullptr;
   size_t rec_cap = 0;
 };

@@ -89,9 +89,11 @@ int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int*
 void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
                          cudaStream_t s);
 // fold slots 0 .. nrec-1 of ring buffer buf into each lattice's slab sums,
-// and their vacuum sums into vac_acc
+// and their vacuum sums into vac_acc (skip_O: leave the field-insertion sums
+// to a products launch with that buffer as its tail; overwrite: the slab sums
+// start from zero instead of their stored values)
 void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
-                       cudaStream_t s);
+                       cudaStream_t s, bool skip_O = false, bool overwrite = false);
 int record_blocks(const Geom& g, int d);
 // co-resident blocks per SM of the persistent sweep kernel
 int sweep_blocks_per_sm(bool fp64);
@@ -115,10 +117,18 @@ int vac_part_count(const Geom& g, int d);
 void launch_combine(const Geom& g, int n_inner_slabs, int q, const MeasLayout& m, bool pairs, const void* accT,
                     const void* accO, double inv_n, void* acc4T, void* acc4O, cudaStream_t s);
 int product_partial_count(const Geom& g);
+// records not yet folded into the field-insertion slab sums: the products
+// add them on the fly (nrec = 0: none)
+struct ProductTail {
+  const void* trec = nullptr;  // ring buffer theta_rec[buf] of the lattice
+  const void* osum = nullptr;  // ring buffer osum[buf]
+  int nrec = 0;
+  int overwrite = 0;  // the stored field-insertion sums are not yet written: start from zero
+};
 // cross-slab products of the averages sum / n, reduced over x into the
 // record's P, Pf and W blocks (pairs: as for launch_combine)
 void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, const void* accO,
-                     double inv_n, double2* partial, double* rec, cudaStream_t s);
+                     double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail = {});
 // naive P+P and mean plaquette of the current configuration
 void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,
                                 double* rec, cudaStream_t s);

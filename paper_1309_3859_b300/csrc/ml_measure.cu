@@ -229,7 +229,9 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 }
 
 // ---------------------------------------------------------------------------
-// Fold of nrec <= slots records into the slab sums (SlabAcc<T>):
+// Fold of nrec <= slots records into the slab sums (SlabAcc<T>); with
+// `overwrite` the sums start from zero (the first fold of an inner loop), so
+// they need no clearing and are not read:
 //   accT[s][a][x]              += sum_j T_j(x, s, R_a)
 //   accO[s][f][b][ci][k][x]    += sum_j T_j(x, s, rf_f) O_j[s][ci][k](x0)
 // The sum over the batch is formed in the records' precision and added once,
@@ -237,7 +239,8 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict__ desc,
-                                                       const LatCtl* __restrict__ ctl, int buf, int nrec) {
+                                                       const LatCtl* __restrict__ ctl, int buf, int nrec,
+                                                       int overwrite) {
   const int li = blockIdx.z;
   if (ctl) {
     if (!ctl[li].fold) return;
@@ -265,7 +268,7 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
   }
   using A = typename SlabAcc<T>::type;
   A* p = reinterpret_cast<A*>(L.accT) + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
-  A v = *p;
+  A v = overwrite ? A{} : *p;  // a first fold adds to zero sums without reading them
   acc_add(v, sr, si);
   *p = v;
 }
@@ -280,7 +283,8 @@ constexpr int fold_min_blocks() {
 
 template <typename T>
 __global__ void __launch_bounds__(256, fold_min_blocks<T>())
-    k_accum_O_table(const LatDesc* __restrict__ desc, const LatCtl* __restrict__ ctl, int buf, int nrec) {
+    k_accum_O_table(const LatDesc* __restrict__ desc, const LatCtl* __restrict__ ctl, int buf, int nrec,
+                    int overwrite) {
   constexpr int B = RecBatch<T>::n;
   constexpr int kMaxCK = 12;  // components x (Re, Im) insertions
   const int li = blockIdx.z;
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
       A a[kAccGroup];
 #pragma unroll
       for (int i = 0; i < kAccGroup; ++i)
-        if (q0 + i < nck) a[i] = acc[abase + static_cast<size_t>(q0 + i) * g.Ns];
+        if (q0 + i < nck) a[i] = overwrite ? A{} : acc[abase + static_cast<size_t>(q0 + i) * g.Ns];
 #pragma unroll
       for (int i = 0; i < kAccGroup; ++i) {
         const int q = q0 + i;
@@ -460,14 +464,29 @@ __global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayou
 // One thread: site x, field separation f, kWChunk values of j.  Suffix
 // products are formed once from the top slab down; the loop over slabs then
 // keeps the prefix product running and reads the kWChunk [TO] sums of each
-// slab together.
+// slab together.  With TAIL, the [TO] sums first take in the last nrec
+// records of ring buffer (trec, osum) exactly as k_accum_O_table would have
+// (same batch sum, same accumulator update), without writing them back: the
+// measurement's final fold of the field insertions and the products in one
+// pass over the slab sums.
 template <typename A>
-__global__ void __launch_bounds__(256, kProdMinBlocks)
+struct RecOf {
+  using type = double;
+};
+template <>
+struct RecOf<float4> {
+  using type = float;
+};
+
+template <typename A, bool TAIL>
+__global__ void __launch_bounds__(256, TAIL ? 2 : kProdMinBlocks)
     k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT, const A* __restrict__ accO,
-                 double inv_n, double2* __restrict__ partial, int nwarps) {
+                 double inv_n, double2* __restrict__ partial, int nwarps, ProductTail tail) {
   using M = AccMath<A>;
   using C = typename M::cplx;
   using R = typename M::real;
+  using T = typename RecOf<A>::type;
+  constexpr int B = RecBatch<T>::n;
   const R in = static_cast<R>(inv_n);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = x < g.Ns;
@@ -487,6 +506,12 @@ __global__ void __launch_bounds__(256, kProdMinBlocks)
       suf[s] = run;
       run = cmul(run, slab_factor<M>(M::value(tcol[s * tstride]), in));
     }
+    int cx = 0, cy = 0, cz = 0, xr = 0, x0x = 0;
+    if constexpr (TAIL) {
+      spatial_coords(g, x, &cx, &cy, &cz);
+      xr = wrapc(cx + m.rf[f], g.L) + g.L * (cy + g.L * cz);
+      x0x = wrapc(cx + m.rf[f] / 2, g.L);
+    }
     run = M::make(R(1), R(0));  // prod_{s' < s} [T]_{s'}
     for (int s = 0; s < nslab; ++s) {
       const C rest = cmul(run, suf[s]);
@@ -494,7 +519,28 @@ __global__ void __launch_bounds__(256, kProdMinBlocks)
       A o[kWChunk];
 #pragma unroll
       for (int q = 0; q < kWChunk; ++q)
-        if (q < nj) o[q] = ocol[static_cast<size_t>(q) * g.Ns];
+        if (q < nj) o[q] = (TAIL && tail.overwrite) ? A{} : ocol[static_cast<size_t>(q) * g.Ns];
+      if constexpr (TAIL) {
+        const T* trec = static_cast<const T*>(tail.trec) + static_cast<size_t>(s) * g.Ns * B;
+        const T* osum = static_cast<const T*>(tail.osum);
+        T er[B], ei[B];
+        batch_phases<T>(trec + static_cast<size_t>(x) * B, trec + static_cast<size_t>(xr) * B, tail.nrec, er, ei);
+#pragma unroll
+        for (int q = 0; q < kWChunk; ++q) {
+          if (q >= nj) break;
+          const int j = j0 + q, b = j / (2 * m.nc), ci = (j >> 1) % m.nc, k = j & 1;
+          const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
+          T ov[B];
+          load_batch<T>(osum + ((static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0) * B, ov);
+          T sr = T(0), si = T(0);
+#pragma unroll
+          for (int r = 0; r < B; ++r) {
+            sr += er[r] * ov[r];
+            si += ei[r] * ov[r];
+          }
+          acc_add(o[q], sr, si);
+        }
+      }
 #pragma unroll
       for (int q = 0; q < kWChunk; ++q)
         if (q < nj) sum[q] = cadd(sum[q], cmul(M::value(o[q]), rest));
@@ -681,19 +727,20 @@ void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const
 }
 
 void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool skip_O, bool overwrite) {
+  const int ow = overwrite ? 1 : 0;
   const dim3 gt(td.max_blocks_site, td.max_y_T, td.nlat);
   if (fp64)
-    k_accum_T_table<double><<<gt, 256, 0, s>>>(d, ctl, buf, nrec);
+    k_accum_T_table<double><<<gt, 256, 0, s>>>(d, ctl, buf, nrec, ow);
   else
-    k_accum_T_table<float><<<gt, 256, 0, s>>>(d, ctl, buf, nrec);
+    k_accum_T_table<float><<<gt, 256, 0, s>>>(d, ctl, buf, nrec, ow);
   count_launches(1);
-  if (td.max_y_O > 0) {
+  if (td.max_y_O > 0 && !skip_O) {
     const dim3 go(td.max_blocks_site, td.max_y_O, td.nlat);
     if (fp64)
-      k_accum_O_table<double><<<go, 256, 0, s>>>(d, ctl, buf, nrec);
+      k_accum_O_table<double><<<go, 256, 0, s>>>(d, ctl, buf, nrec, ow);
     else
-      k_accum_O_table<float><<<go, 256, 0, s>>>(d, ctl, buf, nrec);
+      k_accum_O_table<float><<<go, 256, 0, s>>>(d, ctl, buf, nrec, ow);
     count_launches(1);
   }
   if (td.max_vac_parts > 0) {
@@ -723,27 +770,30 @@ void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, bool
 
 template <typename A>
 static void products_of(const Geom& g, int nslab, const MeasLayout& m, const A* accT, const A* accO, double inv_n,
-                        double2* partial, int nb, int nwarps, cudaStream_t s) {
+                        double2* partial, int nb, int nwarps, const ProductTail& tail, cudaStream_t s) {
   k_products_P<A><<<dim3(nb, m.nr + m.nrf), 256, 0, s>>>(g, nslab, m, accT, inv_n, partial, nwarps);
   count_launches(1);
   const int nW = m.np * m.nc * 2;
   if (m.nrf > 0 && nW > 0) {
-    k_products_W<A><<<dim3(nb, m.nrf, (nW + kWChunk - 1) / kWChunk), 256, 0, s>>>(g, nslab, m, accT, accO, inv_n,
-                                                                                  partial, nwarps);
+    const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
+    if (tail.nrec > 0)
+      k_products_W<A, true><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
+    else
+      k_products_W<A, false><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
     count_launches(1);
   }
 }
 
 void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, const void* accO,
-                     double inv_n, double2* partial, double* rec, cudaStream_t s) {
+                     double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail) {
   const int nb = blocks_for(g.Ns, 256);
   const int nwarps = nb * 8;
   if (pairs)
     products_of(g, nslab, m, static_cast<const float4*>(accT), static_cast<const float4*>(accO), inv_n, partial, nb,
-                nwarps, s);
+                nwarps, tail, s);
   else
     products_of(g, nslab, m, static_cast<const double2*>(accT), static_cast<const double2*>(accO), inv_n, partial,
-                nb, nwarps, s);
+                nb, nwarps, tail, s);
   const int nW = m.np * m.nc * 2;
   const int nout = m.nr + m.nrf + m.nrf * nW;
   k_finalize_products<<<blocks_for(32ll * nout, 256), 256, 0, s>>>(partial, nwarps, g, m, rec);
