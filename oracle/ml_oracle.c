@@ -71,6 +71,10 @@ typedef struct {
   const int *probe_dy, *probe_dz; /* transverse probe offsets                */
   unsigned comp_mask; /* bit c set: component c of (Ex,Ey,Ez,Bx,By,Bz)       */
   int threads;     /* OpenMP threads for link updates, 0 = runtime default   */
+  int update;      /* update of the first sweep of a compound sweep:
+                      0 heatbath, 1 Metropolis (Section II)                  */
+  int metro_hits;  /* Metropolis hits per link visit                         */
+  double metro_width; /* Metropolis proposal half-width w (radians)          */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -362,6 +366,25 @@ static int parity_of(const geom *g, int64_t i) {
   return (c[0] + c[1] + c[2] + c[3]) & 1;
 }
 
+/* Metropolis update of one link (Section II: the standard Metropolis
+ * algorithm; the paper does not give its proposal, so it is a parameter): for
+ * hit h = 0 .. metro_hits-1 with the uniforms (u1, u2) of trial h of the
+ * heatbath stream, propose theta' = wrap(theta + w (2 u1 - 1)) and accept it
+ * when u2 < exp(beta k [cos(theta' + alpha) - cos(theta + alpha)]), the ratio
+ * of the link's weights exp(beta k cos(theta + alpha)) under the Wilson
+ * action (always when the exponent is not negative). */
+static double metropolis(const orc_params *p, double k, double alpha, uint32_t site, int mu, uint64_t n,
+                         double theta) {
+  for (int h = 0; h < p->metro_hits; ++h) {
+    double u[3];
+    link_uniforms(p, site, mu, n, h, u);
+    double prop = wrap(theta + p->metro_width * (2.0 * u[0] - 1.0));
+    double ds = p->beta * k * (cos(prop + alpha) - cos(theta + alpha));
+    if (ds >= 0.0 || u[1] < exp(ds)) theta = prop;
+  }
+  return theta;
+}
+
 /* A spatial link on a time slice t = 0 (mod d) is frozen in slab mode d > 0. */
 static int frozen(const geom *g, int64_t i, int mu, int d) {
   if (d <= 0 || mu == 0) return 0;
@@ -372,8 +395,9 @@ static int frozen(const geom *g, int64_t i, int mu, int d) {
 
 /* One pass over the links U_mu(x) with parity(x) = par that are not frozen.
  * kind 0: heatbath theta <- wrap(psi - alpha), psi ~ vonMises(beta k);
- * kind 1: overrelaxation theta <- wrap(-2 alpha - theta) (k = 0: unchanged).
- * n is the heatbath sweep number that keys the random stream. */
+ * kind 1: overrelaxation theta <- wrap(-2 alpha - theta) (k = 0: unchanged);
+ * kind 2: Metropolis (metro_hits hits of half-width metro_width).
+ * n is the update sweep number that keys the random stream. */
 int orc_update_pass(const orc_params *p, double *th, int mu, int par, int d, uint64_t n, int kind) {
   geom g = make_geom(p);
   int bad = 0;
@@ -394,6 +418,8 @@ int orc_update_pass(const orc_params *p, double *th, int mu, int par, int d, uin
         continue;
       }
       th[mu * g.V + i] = wrap(psi - alpha);
+    } else if (kind == 2) {
+      th[mu * g.V + i] = metropolis(p, k, alpha, (uint32_t)i, mu, n, th[mu * g.V + i]);
     } else {
       if (k == 0.0) continue;
       th[mu * g.V + i] = wrap(-2.0 * alpha - th[mu * g.V + i]);
@@ -402,16 +428,18 @@ int orc_update_pass(const orc_params *p, double *th, int mu, int par, int d, uin
   return bad ? ORC_EREJECT : ORC_OK;
 }
 
-/* Compound sweep (Section II: one update + n_or overrelaxations): heatbath
- * sweep number ++(*counter), then n_or overrelaxation sweeps.  Each sweep
- * visits mu = 0, 1, 2, 3 and within each direction the even sites before the
- * odd ones (Section II.D: in-place even/odd update). */
+/* Compound sweep (Section II: one update + n_or overrelaxations): update
+ * sweep number ++(*counter) (heatbath, or Metropolis with update = 1), then
+ * n_or overrelaxation sweeps.  Each sweep visits mu = 0, 1, 2, 3 and within
+ * each direction the even sites before the odd ones (Section II.D: in-place
+ * even/odd update). */
 int orc_compound_sweep(const orc_params *p, double *th, int d, uint64_t *counter) {
   int status = ORC_OK;
   uint64_t n = ++(*counter);
+  const int kind = p->update == 1 ? 2 : 0;
   for (int mu = 0; mu < 4; ++mu)
     for (int par = 0; par < 2; ++par)
-      if (orc_update_pass(p, th, mu, par, d, n, 0) != ORC_OK) status = ORC_EREJECT;
+      if (orc_update_pass(p, th, mu, par, d, n, kind) != ORC_OK) status = ORC_EREJECT;
   for (int o = 0; o < p->n_or; ++o)
     for (int mu = 0; mu < 4; ++mu)
       for (int par = 0; par < 2; ++par) orc_update_pass(p, th, mu, par, d, n, 1);
@@ -527,6 +555,10 @@ static cplx cmul(cplx a, cplx b) {
 static int validate(const orc_params *p) {
   if (p->L < 2 || p->Nt < 2 || (p->L & 1) || (p->Nt & 1)) return ORC_EINVAL;
   if (p->beta < 0.0 || p->n_or < 0 || p->draws < 0 || p->draws > 1) return ORC_EINVAL;
+  if (p->update < 0 || p->update > 1) return ORC_EINVAL;
+  if (p->update == 1 && (p->metro_hits < 1 || p->metro_hits > ORC_MAX_TRIALS || !(p->metro_width > 0.0) ||
+                         p->metro_width > ORC_PI))
+    return ORC_EINVAL;
   if (p->slab < 1 || p->Nt % p->slab != 0 || p->n_sub < 1 || p->k_between < 0) return ORC_EINVAL;
   if (p->outer_slab != 0) {
     if (p->outer_slab % p->slab != 0 || p->Nt % p->outer_slab != 0 || p->outer_slab == p->slab) return ORC_EINVAL;

@@ -58,6 +58,7 @@ class _Params(ctypes.Structure):
         ("nprobe", ctypes.c_int), ("probe_dy", ctypes.POINTER(ctypes.c_int)),
         ("probe_dz", ctypes.POINTER(ctypes.c_int)),
         ("comp_mask", ctypes.c_uint), ("threads", ctypes.c_int),
+        ("update", ctypes.c_int), ("metro_hits", ctypes.c_int), ("metro_width", ctypes.c_double),
     ]
 
 
@@ -112,6 +113,9 @@ class Params:
     probes: tuple = ()      # ((dy, dz), ...)
     comp_mask: int = 0
     threads: int = 0
+    update: int = 0         # first sweep of a compound sweep: 0 heatbath, 1 Metropolis
+    metro_hits: int = 1     # Metropolis hits per link visit
+    metro_width: float = 1.0  # Metropolis proposal half-width (radians)
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -130,7 +134,8 @@ class Params:
         self._keep[:] = [r, rf, dy, dz]
         return _Params(self.L, self.Nt, float(self.beta), int(self.seed) & (2**64 - 1), self.n_or, self.draws,
                        self.slab, self.n_sub, self.outer_slab, self.n_sub_outer, self.k_between,
-                       len(self.r), r, len(self.rf), rf, len(self.probes), dy, dz, self.comp_mask, self.threads)
+                       len(self.r), r, len(self.rf), rf, len(self.probes), dy, dz, self.comp_mask, self.threads,
+                       self.update, self.metro_hits, float(self.metro_width))
 
 
 def _dp(a: np.ndarray):
@@ -181,12 +186,13 @@ def staple(p: Params, th: np.ndarray, mu: int, i: int) -> complex:
 
 
 def update_pass(p: Params, th: np.ndarray, mu: int, parity: int, slab_d: int, n: int, kind: int) -> int:
-    """One heatbath (kind 0) or overrelaxation (kind 1) pass, in place."""
+    """One heatbath (kind 0), overrelaxation (kind 1) or Metropolis (kind 2) pass, in place."""
     return lib().orc_update_pass(ctypes.byref(p.c()), _dp(th), mu, parity, slab_d, n, kind)
 
 
 def compound_sweep(p: Params, th: np.ndarray, counter: int, slab_d: int = 0) -> int:
-    """One heatbath + n_or overrelaxation sweeps in place; returns the new sweep counter."""
+    """One update sweep (heatbath or Metropolis) + n_or overrelaxation sweeps in place; returns the new sweep
+    counter."""
     c = ctypes.c_uint64(counter)
     st = lib().orc_compound_sweep(ctypes.byref(p.c()), _dp(th), slab_d, ctypes.byref(c))
     if st != 0:

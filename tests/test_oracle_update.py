@@ -6,6 +6,10 @@
 * Overrelaxation: local action unchanged, involution, total action unchanged.
 * Heatbath: theta + alpha follows the von Mises law of kappa = beta k, tested
   by the probability-integral transform through scipy's von Mises CDF.
+* Metropolis (the paper's update, Section II): the conditional law is
+  stationary under a Metropolis pass (links drawn from it by the heatbath stay
+  distributed by it), the pass moves links at a sane rate, and a Metropolis
+  chain reaches the strong-coupling plaquette.
 * Slab freezing and checkerboard parity of the passes.
 * The whole chain against the strong-coupling plaquette I1(beta)/I0(beta).
 * Gauge covariance of the chain and invariance of the observables.
@@ -150,6 +154,63 @@ def test_heatbath_conditional_law(draws):
     assert st.chisquare(counts).pvalue > 1e-4
 
 
+# --------------------------------------------------------------------------- Metropolis
+@pytest.mark.parametrize("draws", [0, 1])
+def test_metropolis_keeps_the_conditional_law(draws):
+    """Links drawn from their conditional law exp(beta k cos(theta + alpha))
+    (by a heatbath pass) still follow it after a Metropolis pass of the same
+    links with fresh random numbers: the law is stationary.  An inverted or
+    mis-scaled acceptance ratio shifts the distribution and fails."""
+    L, Nt = 4, 4
+    p = oracle.Params(L=L, Nt=Nt, beta=1.3, draws=draws, seed=31, update=1, metro_hits=3, metro_width=1.7)
+    th0 = workloads.random_angles(L, Nt, seed=8)
+    t, x, y, z = coords(L, Nt)
+    par = (t + x + y + z) % 2
+    us, moved = [], []
+    for mu, parity in ((1, 0), (0, 1)):
+        idx = np.flatnonzero(par == parity)
+        W = np.array([oracle.staple(p, th0, mu, int(i)) for i in idx])
+        kappa, alpha = p.beta * np.abs(W), np.angle(W)
+        for n in range(1, 201):
+            th = th0.copy()
+            oracle.update_pass(p, th, mu, parity, 0, n, 0)           # exact draw
+            before = th[mu, idx].copy()
+            oracle.update_pass(p, th, mu, parity, 0, 100000 + n, 2)  # Metropolis
+            psi = (th[mu, idx] + alpha + np.pi) % TWO_PI - np.pi
+            us.append(st.vonmises.cdf(psi, kappa))
+            moved.append(wrapd(th[mu, idx] - before) > 0)
+    u = np.concatenate(us)
+    counts, _ = np.histogram(u, bins=40, range=(0, 1))
+    assert st.chisquare(counts).pvalue > 1e-4
+    rate = np.concatenate(moved).mean()
+    assert 0.3 < rate < 0.99, rate
+
+
+def test_metropolis_pass_matches_its_definition():
+    """One Metropolis hit per link, recomputed in numpy from the Philox
+    draws: proposal theta + w (2 u1 - 1), accepted when u2 < exp(beta k
+    (cos(theta' + alpha) - cos(theta + alpha)))."""
+    L, Nt = 4, 4
+    p = oracle.Params(L=L, Nt=Nt, beta=0.9, draws=0, seed=41, update=1, metro_hits=1, metro_width=0.8)
+    th0 = workloads.random_angles(L, Nt, seed=12)
+    t, x, y, z = coords(L, Nt)
+    par = (t + x + y + z) % 2
+    mu, parity, n = 2, 0, 7
+    th = th0.copy()
+    oracle.update_pass(p, th, mu, parity, 0, n, 2)
+    key = np.array([p.seed & 0xFFFFFFFF, p.seed >> 32], dtype=np.uint32)
+    for i in np.flatnonzero(par == parity)[:40]:
+        W = oracle.staple(p, th0, mu, int(i))
+        k, alpha = abs(W), np.angle(W)
+        o = oracle.philox(np.array([[i, mu, n, 0]], dtype=np.uint32), key[None, :])[0]
+        u1 = oracle.uniform52(int(o[0]), int(o[1]))
+        u2 = oracle.uniform52(int(o[2]), int(o[3]))
+        prop = (th0[mu, i] + 0.8 * (2 * u1 - 1) + np.pi) % TWO_PI - np.pi
+        ds = 0.9 * k * (np.cos(prop + alpha) - np.cos(th0[mu, i] + alpha))
+        want = prop if (ds >= 0 or u2 < np.exp(ds)) else th0[mu, i]
+        assert wrapd(th[mu, i] - want) < 1e-13, i
+
+
 # --------------------------------------------------------------------------- sweep structure
 @pytest.mark.parametrize("d", [2, 4])
 def test_slab_mask_freezes_boundary_spatial_links(d):
@@ -175,10 +236,13 @@ def test_hot_start_uniform():
 
 
 # --------------------------------------------------------------------------- whole chain
+@pytest.mark.parametrize("update", [0, 1])
 @pytest.mark.parametrize("beta", [0.05, 0.1, 0.2, 0.3])
-def test_strong_coupling_plaquette(beta):
-    """<cos theta_p> = u + O(u^5), u = I1(beta)/I0(beta)."""
-    p = oracle.Params(L=4, Nt=4, beta=beta, seed=100 + int(beta * 100), threads=4)
+def test_strong_coupling_plaquette(beta, update):
+    """<cos theta_p> = u + O(u^5), u = I1(beta)/I0(beta), for heatbath and
+    Metropolis chains."""
+    p = oracle.Params(L=4, Nt=4, beta=beta, seed=100 + int(beta * 100), threads=4, update=update, metro_hits=2,
+                      metro_width=2.5)
     th = oracle.hot_start(p)
     c = oracle.thermalize(p, th, 0, 20)
     vals = []
