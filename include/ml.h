@@ -59,11 +59,21 @@ typedef struct {
   int dy, dz;
 } ml_offset;
 
+/* Update of the first sweep of every compound sweep. */
+typedef enum {
+  ML_UPDATE_HEATBATH = 0,  /* exact draw of the link's conditional law (Best & Fisher sampler) */
+  ML_UPDATE_METROPOLIS = 1 /* Section II's Metropolis: metro_hits hits per link, proposal
+                              theta + w (2 u1 - 1) with w = metro_width, accepted when
+                              u2 < exp(beta k [cos(theta' + alpha) - cos(theta + alpha)]);
+                              (u1, u2) are those of heatbath trial h of the same stream */
+} ml_update;
+
 /* Run parameters.  Validation (ML_EINVAL): L and Nt even and >= 2; slab >= 1
  * dividing Nt; n_sub >= 1; outer_slab = 0, or a multiple of slab that divides
  * Nt and differs from slab, with n_sub_outer >= 1; 1 <= r, rf <= L-1;
  * |dy|, |dz| <= L-1; beta >= 0; k_between >= 0; n_or >= 0; comp_mask < 64;
- * at least one r.  The lists are copied by ml_create. */
+ * at least one r; update an ml_update, and for Metropolis 1 <= metro_hits <= 64
+ * and 0 < metro_width <= pi.  The lists are copied by ml_create. */
 typedef struct {
   int L, Nt;            /* spatial and temporal extent                         */
   double beta;          /* inverse coupling 1/g^2 of the Wilson action         */
@@ -82,6 +92,9 @@ typedef struct {
   int nprobe;           /* number of probe offsets                             */
   const ml_offset *probe; /* probe offsets on the mediator plane               */
   uint32_t comp_mask;   /* bit c selects field component c                     */
+  int update;           /* ml_update of the first sweep of a compound sweep    */
+  int metro_hits;       /* Metropolis hits per link visit                      */
+  double metro_width;   /* Metropolis proposal half-width (radians)            */
 } ml_params;
 
 /* Device-memory allocator supplied by the caller (the Python binding passes
@@ -167,8 +180,10 @@ int ml_set_sweep(ml_lattice *h, uint64_t n);
 
 /* One pass over the links U_mu(x) of parity `parity` (0 even, 1 odd) that
  * are not frozen (slab_d > 0 freezes spatial links on t = 0 mod slab_d):
- * kind 0 = heatbath with sweep number n, kind 1 = overrelaxation.
- * Asynchronous.  Does not change the sweep counter. */
+ * kind 0 = the handle's update (heatbath or Metropolis) with sweep number n,
+ * kind 1 = overrelaxation, kind 2 = Metropolis (handles created with
+ * ML_UPDATE_METROPOLIS only, else ML_EINVAL).  Asynchronous.  Does not change
+ * the sweep counter. */
 int ml_update_pass(ml_lattice *h, int mu, int parity, int slab_d, uint64_t n, int kind);
 
 /* n compound sweeps with slab mask slab_d (0 = none). Asynchronous. */

@@ -102,6 +102,10 @@ int validate(const ml_params* p) {
     if (p->probe[a].dy <= -p->L || p->probe[a].dy >= p->L || p->probe[a].dz <= -p->L || p->probe[a].dz >= p->L)
       return ML_EINVAL;
   if (p->comp_mask >= 64u) return ML_EINVAL;
+  if (p->update != ML_UPDATE_HEATBATH && p->update != ML_UPDATE_METROPOLIS) return ML_EINVAL;
+  if (p->update == ML_UPDATE_METROPOLIS &&
+      (p->metro_hits < 1 || p->metro_hits > kMaxTrials || !(p->metro_width > 0.0) || p->metro_width > kPi))
+    return ML_EINVAL;
   return ML_OK;
 }
 
@@ -222,6 +226,9 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   d.k0 = static_cast<uint32_t>(p->seed);
   d.k1 = static_cast<uint32_t>(p->seed >> 32);
   d.beta = p->beta;
+  d.update = p->update;
+  d.metro_hits = p->update == ML_UPDATE_METROPOLIS ? p->metro_hits : 0;
+  d.metro_width = p->update == ML_UPDATE_METROPOLIS ? p->metro_width : 0.0;
   d.slab = p->slab;
   d.nslab = nslab_in;
   d.tiles = (g.Vh + kSweepTile - 1) / kSweepTile;
@@ -870,10 +877,12 @@ int ml_compound_sweeps(ml_lattice* h, int n, int slab_d) {
 }
 
 int ml_update_pass(ml_lattice* h, int mu, int parity, int slab_d, uint64_t n, int kind) {
-  if (!h || mu < 0 || mu > 3 || parity < 0 || parity > 1 || slab_d < 0 || kind < 0 || kind > 1) return ML_EINVAL;
+  if (!h || mu < 0 || mu > 3 || parity < 0 || parity > 1 || slab_d < 0 || kind < 0 || kind > 2) return ML_EINVAL;
   LatState* L = h->L();
+  const UpdateRule rule = update_rule(L->desc);
+  if (kind == 2 && !rule.metropolis) return ML_EINVAL;  // needs the handle's Metropolis parameters
   launch_update_pass(h->e.fp64, L->theta, L->g, mu, parity, slab_d, kind, nullptr, n, L->seed, L->beta, h->e.d_err,
-                     h->e.stream);
+                     h->e.stream, rule);
   return cuda_status(cudaGetLastError());
 }
 
@@ -1004,7 +1013,7 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
       case ML_K_HEATBATH:
       case ML_K_OVERRELAX:
         launch_update_pass(e->fp64, L->scratch_theta, L->g, 1, 0, e->slab, kernel == ML_K_HEATBATH ? 0 : 1, nullptr,
-                           1000000ull + i, L->seed, L->beta, e->d_err, e->stream);
+                           1000000ull + i, L->seed, L->beta, e->d_err, e->stream, update_rule(L->desc));
         break;
       case ML_K_RECORD:
         launch_record_table(e->fp64, e->d_desc, e->td, nullptr, 0, 0, e->stream);

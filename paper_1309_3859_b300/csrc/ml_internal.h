@@ -36,6 +36,9 @@ struct LatDesc {
   unsigned long long* n_dev;  // heatbath sweep counter
   uint32_t k0, k1;            // Philox key (seed)
   double beta;
+  int update;                 // ml_update of the first sweep of a compound sweep
+  int metro_hits;             // Metropolis hits per link visit
+  double metro_width;         // Metropolis proposal half-width
   int slab, nslab;            // inner slab thickness d and Nt / d
   int tile_start, tiles;      // sweep tiles of kSweepTile links
   void* theta_rec[2];         // record ring buffers [nslab][Ns][slots]
@@ -46,6 +49,16 @@ struct LatDesc {
   int nparts;                 // vacuum blocks per part (vac_part_count)
   double* vac_acc;            // [12] vacuum sums of the folded configurations
 };
+
+// Update of the first sweep of a compound sweep, per lattice.
+struct UpdateRule {
+  int metropolis;  // 0: heatbath, 1: Metropolis
+  int hits;        // Metropolis hits per link visit
+  double width;    // Metropolis proposal half-width
+};
+__host__ __device__ inline UpdateRule update_rule(const LatDesc& L) {
+  return UpdateRule{L.update, L.metro_hits, L.metro_width};
+}
 
 // Per-lattice control of one step of the request-serving engine; schedules
 // that advance every lattice of a table in lockstep pass null and uniform
@@ -102,9 +115,11 @@ int fold_probe_groups(int np);
 // ---- link updates (ml_update.cu) ----
 // kind: 0 heatbath, 1 overrelaxation.  The heatbath sweep number is *n_dev
 // when n_dev is not null, else n_fixed.
+// kind 2: the update sweep's pass with the Metropolis rule (hits and width
+// from `rule`)
 void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parity, int slab_d, int kind,
                         const unsigned long long* n_dev, unsigned long long n_fixed, uint64_t seed, double beta,
-                        int* err, cudaStream_t s);
+                        int* err, cudaStream_t s, const UpdateRule& rule);
 void launch_hot_start(bool fp64, void* theta, const Geom& g, uint64_t seed, cudaStream_t s);
 void launch_angles_to_soa(bool fp64, const double* canon, void* theta, const Geom& g, cudaStream_t s);
 void launch_angles_from_soa(bool fp64, const void* theta, double* canon, const Geom& g, cudaStream_t s);

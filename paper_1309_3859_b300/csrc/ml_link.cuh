@@ -5,7 +5,7 @@
 // so that every implementation produces bit-identical configurations.
 #pragma once
 
-#include "ml_device.cuh"
+#include "ml_internal.h"
 
 namespace ml {
 
@@ -130,6 +130,42 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
   }
 }
 
+// Metropolis (Section II): `hits` hits on the angle theta of a link whose
+// staple sum is k e^{i alpha}.  Hit h takes (u1, u2) of heatbath trial h of
+// the same stream, proposes theta' = wrap(theta + w (2 u1 - 1)) and accepts
+// it when u2 < exp(beta k [cos(theta' + alpha) - cos(theta + alpha)]) (always
+// when the exponent is not negative).
+template <typename T>
+__device__ __forceinline__ T metropolis(T theta, T k, T alpha, T beta, T w, int hits, uint32_t site, int mu,
+                                        unsigned long long n, uint32_t k0, uint32_t k1) {
+  using P = Prec<T>;
+  if constexpr (P::fp64) {
+    for (int h = 0; h < hits; ++h) {
+      double u1, u2;
+      Draws<double>::trial(site, mu, n, h, k0, k1, &u1, &u2);
+      const double prop = P::wrap(theta + w * (2.0 * u1 - 1.0));
+      const double ds = beta * k * (cos(prop + alpha) - cos(theta + alpha));
+      if (ds >= 0.0 || u2 < exp(ds)) theta = prop;
+    }
+  } else {
+    auto hit = [&](uint32_t a, uint32_t b) {
+      const float u1 = uniform23(a), u2 = uniform23(b);
+      const float prop = P::wrap(theta + w * (2.0f * u1 - 1.0f));
+      float s0, c0, s1, c1;
+      P::sincos_(prop + alpha, &s1, &c1);
+      P::sincos_(theta + alpha, &s0, &c0);
+      const float ds = beta * k * (c1 - c0);
+      if (ds >= 0.0f || u2 < __expf(ds)) theta = prop;
+    };
+    for (int h = 0; h < hits; h += 2) {  // hits 2j and 2j + 1 share Philox block j
+      const U4 o = Draws<float>::block(site, mu, n, h >> 1, k0, k1);
+      hit(o.x, o.y);
+      if (h + 1 < hits) hit(o.z, o.w);
+    }
+  }
+  return theta;
+}
+
 // New angle of link U_mu from its staples.  staples(nu, v) fills the six
 // angles of the two plaquettes in the (mu, nu) plane that contain the link:
 //   v = theta_nu(x+mu), theta_mu(x+nu), theta_nu(x),
@@ -139,8 +175,9 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
 //     = k e^{i alpha}.
 // KIND 0: heatbath draw theta = psi - alpha with psi ~ exp(beta k cos psi);
 // KIND 1: overrelaxation theta -> -2 alpha - theta (self() is the current
-// angle).  Returns false when the link keeps its angle (k = 0 in
-// overrelaxation, or the heatbath trial cap, which also sets kErrReject).
+// angle); KIND 2: Metropolis with `hits` hits of half-width w.  Returns false
+// when the link keeps its angle (k = 0 in overrelaxation, or the heatbath
+// trial cap, which also sets kErrReject).
 template <typename T, typename Staples>
 __device__ __forceinline__ void staple_sum(int mu, Staples&& staples, T* k, T* alpha) {
   using P = Prec<T>;
@@ -165,7 +202,7 @@ __device__ __forceinline__ void staple_sum(int mu, Staples&& staples, T* k, T* a
 template <typename T, int KIND, typename Staples, typename Self>
 __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&& self, uint32_t site,
                                                unsigned long long n, uint32_t k0, uint32_t k1, T beta,
-                                               int* __restrict__ err, T* out) {
+                                               int* __restrict__ err, T* out, T w = T(0), int hits = 0) {
   using P = Prec<T>;
   T k, alpha;
   staple_sum<T>(mu, staples, &k, &alpha);
@@ -176,6 +213,8 @@ __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&&
       return false;
     }
     *out = P::wrap(psi - alpha);
+  } else if (KIND == 2) {
+    *out = metropolis<T>(self(), k, alpha, beta, w, hits, site, mu, n, k0, k1);
   } else {
     if (k == T(0)) return false;
     *out = P::wrap(T(-2) * alpha - self());

@@ -150,7 +150,7 @@ __device__ __forceinline__ void st_cluster(uint32_t a, double v) {
 template <typename T, int KIND>
 __device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* mirror, int m0, int m1, int mu,
                                          int tl, int bi, uint32_t site, unsigned long long n, uint32_t k0,
-                                         uint32_t k1, T beta, int* err) {
+                                         uint32_t k1, T beta, int* err, const UpdateRule& rule) {
   const int tp = tl + (mu == 0);  // x + mu
   const int bp = bi + b.off(mu);
   auto at = [&](int rho, int t_, int c) { return buf[b.slot(rho, t_) * b.vol + c]; };
@@ -166,7 +166,13 @@ __device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* m
   const int sl = b.slot(mu, tl);
   T* self = buf + sl * b.vol + bi;
   T out;
-  if (new_link_angle<T, KIND>(mu, staples, [&] { return *self; }, site, n, k0, k1, beta, err, &out)) {
+  auto cur = [&] { return *self; };
+  const bool moved =
+      (KIND == 0 && rule.metropolis)
+          ? new_link_angle<T, 2>(mu, staples, cur, site, n, k0, k1, beta, err, &out, static_cast<T>(rule.width),
+                                 rule.hits)
+          : new_link_angle<T, KIND>(mu, staples, cur, site, n, k0, k1, beta, err, &out);
+  if (moved) {
     *self = out;
     const uint32_t soff = static_cast<uint32_t>(sl * b.vol * sizeof(T));
     for (int m = m0; m < m1; ++m) st_cluster(mirror[m] + soff, out);
@@ -243,6 +249,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const unsigned long long nbase = *Ld.n_dev;
   const uint32_t k0 = Ld.k0, k1 = Ld.k1;
   const T beta = static_cast<T>(Ld.beta);
+  const UpdateRule rule = update_rule(Ld);
   const unsigned long long m_yl = fdiv_magic(max(b.ylen, 1));
 
   // mirror lists: counts, an exclusive scan over the owned sites (one chunk
@@ -329,9 +336,11 @@ __global__ void __launch_bounds__(kResThreads, 1)
               const int jo = cx + g.L * row;  // owned-site index
               const uint32_t site = static_cast<uint32_t>(cx + g.L * (cy + g.L * cz) + g.Ns * t);
               if (sweep == 0)
-                box_link<T, 0>(b, buf, mirror, mstart[jo], mstart[jo + 1], mu, tl, bi, site, n, k0, k1, beta, err);
+                box_link<T, 0>(b, buf, mirror, mstart[jo], mstart[jo + 1], mu, tl, bi, site, n, k0, k1, beta, err,
+                               rule);
               else
-                box_link<T, 1>(b, buf, mirror, mstart[jo], mstart[jo + 1], mu, tl, bi, site, n, k0, k1, beta, err);
+                box_link<T, 1>(b, buf, mirror, mstart[jo], mstart[jo + 1], mu, tl, bi, site, n, k0, k1, beta, err,
+                               rule);
             }
             // the pass's links and their mirrors are in place for every CTA
             cluster_sync();

@@ -26,8 +26,9 @@ __device__ __forceinline__ int step_index(const Geom& g, int i, const int c[4], 
   return c[mu] == 0 ? i + (ext - 1) * stride : i - stride;
 }
 
-// Update of the link U_mu at half index h of parity `parity` (heatbath for
-// KIND 0 with sweep number n, overrelaxation for KIND 1).  Frozen links (slab
+// Update of the link U_mu at half index h of parity `parity` (the update
+// sweep's rule for KIND 0 — heatbath or Metropolis — with sweep number n,
+// overrelaxation for KIND 1).  Frozen links (slab
 // mode, spatial mu on t = 0 mod slab_d) are left unchanged.
 // `th` carries no __restrict__: inside the persistent sweep kernel other blocks
 // rewrite the angles between passes, so every load must be a plain coherent
@@ -35,7 +36,7 @@ __device__ __forceinline__ int step_index(const Geom& g, int i, const int c[4], 
 template <typename T, int KIND>
 __device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int parity, int slab_d, int h,
                                             unsigned long long n, uint32_t k0, uint32_t k1, T beta,
-                                            int* __restrict__ err) {
+                                            int* __restrict__ err, const UpdateRule& rule) {
   int c[4];
   half_site_coords(g, h, parity, c);
   if (slab_d > 0 && mu != 0 && (c[0] % slab_d) == 0) return;  // frozen boundary link
@@ -59,9 +60,14 @@ __device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int pa
     v[5] = th_nu_op[imnu >> 1];
   };
   T out;
-  if (new_link_angle<T, KIND>(mu, staples, [&] { return *self; }, static_cast<uint32_t>(i), n, k0, k1, beta, err,
-                              &out))
+  auto cur = [&] { return *self; };
+  if (KIND == 0 && rule.metropolis) {
+    if (new_link_angle<T, 2>(mu, staples, cur, static_cast<uint32_t>(i), n, k0, k1, beta, err, &out,
+                             static_cast<T>(rule.width), rule.hits))
+      *self = out;
+  } else if (new_link_angle<T, KIND>(mu, staples, cur, static_cast<uint32_t>(i), n, k0, k1, beta, err, &out)) {
     *self = out;
+  }
 }
 
 // One (mu, parity) pass, one thread per link.  The links of one pass share no
@@ -70,11 +76,11 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(128) k_update_pass(T* __restrict__ th, Geom g, int mu, int parity, int slab_d,
                                                       const unsigned long long* __restrict__ n_dev,
                                                       unsigned long long n_fixed, uint32_t k0, uint32_t k1, T beta,
-                                                      int* __restrict__ err) {
+                                                      int* __restrict__ err, UpdateRule rule) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= g.Vh) return;
   const unsigned long long n = n_dev ? *n_dev : n_fixed;
-  update_link<T, KIND>(th, g, mu, parity, slab_d, h, n, k0, k1, beta, err);
+  update_link<T, KIND>(th, g, mu, parity, slab_d, h, n, k0, k1, beta, err, rule);
 }
 
 // n_compound compound sweeps (heatbath + n_or overrelaxation sweeps, each
@@ -99,6 +105,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
   int c_h = 0, c_mask = 0;
   uint32_t c_k0 = 0, c_k1 = 0;
   T c_beta = T(0);
+  UpdateRule c_rule{};
   unsigned long long c_base = 0;
   if (one_tile && static_cast<int>(blockIdx.x) < total_tiles) {
     const int i = tile_lat[blockIdx.x];
@@ -110,6 +117,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
     c_k0 = L.k0;
     c_k1 = L.k1;
     c_beta = static_cast<T>(L.beta);
+    c_rule = update_rule(L);
     c_base = *L.n_dev;
   }
   for (int c = 0; c < n_compound; ++c) {
@@ -119,9 +127,11 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
           if (one_tile) {
             if (c_theta && c_h < c_g.Vh) {
               if (sweep == 0)
-                update_link<T, 0>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err);
+                update_link<T, 0>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err,
+                                  c_rule);
               else
-                update_link<T, 1>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err);
+                update_link<T, 1>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err,
+                                  c_rule);
             }
           } else {
             for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
@@ -133,10 +143,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
               const unsigned long long n = *L.n_dev + 1 + c;
               if (sweep == 0)
                 update_link<T, 0>(static_cast<T*>(L.theta), L.g, mu, par, md, h, n, L.k0, L.k1,
-                                  static_cast<T>(L.beta), err);
+                                  static_cast<T>(L.beta), err, update_rule(L));
               else
                 update_link<T, 1>(static_cast<T*>(L.theta), L.g, mu, par, md, h, n, L.k0, L.k1,
-                                  static_cast<T>(L.beta), err);
+                                  static_cast<T>(L.beta), err, update_rule(L));
             }
           }
           if (!grid_barrier(bar, err)) return;
@@ -177,7 +187,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_pass_table(const LatDesc* __r
   if (h >= L.g.Vh) return;
   const int md = ctl ? ctl[i].mask : mask;
   update_link<T, KIND>(static_cast<T*>(L.theta), L.g, mu, parity, md, h, *L.n_dev, L.k0, L.k1,
-                       static_cast<T>(L.beta), err);
+                       static_cast<T>(L.beta), err, update_rule(L));
 }
 
 __global__ void k_sweep_begin_table(const LatDesc* __restrict__ d, int nlat) {
@@ -243,23 +253,25 @@ static inline int blocks_for(long long n, int t) { return static_cast<int>((n + 
 
 void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parity, int slab_d, int kind,
                         const unsigned long long* n_dev, unsigned long long n_fixed, uint64_t seed, double beta,
-                        int* err, cudaStream_t s) {
+                        int* err, cudaStream_t s, const UpdateRule& rule) {
   const int nt = 128, nb = blocks_for(g.Vh, nt);
   const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+  // kind 2: the update sweep with the Metropolis rule
+  const UpdateRule r{kind == 2 ? 1 : 0, rule.hits, rule.width};
   if (fp64) {
-    if (kind == 0)
+    if (kind != 1)
       k_update_pass<double, 0><<<nb, nt, 0, s>>>(static_cast<double*>(theta), g, mu, parity, slab_d, n_dev, n_fixed,
-                                                 k0, k1, beta, err);
+                                                 k0, k1, beta, err, r);
     else
       k_update_pass<double, 1><<<nb, nt, 0, s>>>(static_cast<double*>(theta), g, mu, parity, slab_d, n_dev, n_fixed,
-                                                 k0, k1, beta, err);
+                                                 k0, k1, beta, err, r);
   } else {
-    if (kind == 0)
+    if (kind != 1)
       k_update_pass<float, 0><<<nb, nt, 0, s>>>(static_cast<float*>(theta), g, mu, parity, slab_d, n_dev, n_fixed, k0,
-                                                k1, static_cast<float>(beta), err);
+                                                k1, static_cast<float>(beta), err, r);
     else
       k_update_pass<float, 1><<<nb, nt, 0, s>>>(static_cast<float*>(theta), g, mu, parity, slab_d, n_dev, n_fixed, k0,
-                                                k1, static_cast<float>(beta), err);
+                                                k1, static_cast<float>(beta), err, r);
   }
   count_launches(1);
 }

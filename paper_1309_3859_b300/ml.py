@@ -20,6 +20,7 @@ from . import build as _build
 ML_OK, ML_EINVAL, ML_ENOMEM, ML_ECUDA, ML_ETIMEOUT, ML_EREJECT, ML_EBUSY, ML_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 ML_FP64, ML_FP32 = 0, 1
 ML_SWEEP_PERSISTENT, ML_SWEEP_PASSES, ML_SWEEP_RESIDENT = 0, 1, 2
+ML_UPDATE_HEATBATH, ML_UPDATE_METROPOLIS = 0, 1
 (ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP, ML_K_SUBUPDATE,
  ML_K_FULLSWEEP) = range(8)
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
@@ -45,6 +46,7 @@ class _Params(ctypes.Structure):
         ("nrf", ctypes.c_int), ("rf", ctypes.POINTER(ctypes.c_int)),
         ("nprobe", ctypes.c_int), ("probe", ctypes.POINTER(_Offset)),
         ("comp_mask", ctypes.c_uint32),
+        ("update", ctypes.c_int), ("metro_hits", ctypes.c_int), ("metro_width", ctypes.c_double),
     ]
 
 
@@ -160,6 +162,9 @@ class Params:
     rf: tuple = ()
     probes: tuple = ()
     comp_mask: int = 0
+    update: int = 0           # ML_UPDATE_HEATBATH or ML_UPDATE_METROPOLIS
+    metro_hits: int = 1
+    metro_width: float = 1.0
     _keep: list = field(default_factory=list, repr=False, compare=False)
 
     @property
@@ -178,7 +183,7 @@ class Params:
         return _Params(self.L, self.Nt, float(self.beta), int(self.seed) & (2 ** 64 - 1),
                        ML_FP64 if self.fp64 else ML_FP32, self.n_or, self.slab, self.n_sub, self.outer_slab,
                        self.n_sub_outer, self.k_between, len(self.r), r, len(self.rf), rf, len(self.probes), pr,
-                       self.comp_mask)
+                       self.comp_mask, self.update, self.metro_hits, float(self.metro_width))
 
     @classmethod
     def from_workload(cls, w, **kw) -> "Params":

@@ -182,6 +182,77 @@ def test_heatbath_pass_fp32_same_draws():
     assert close >= total - max(2, total // 2000)
 
 
+# ----------------------------------------------------------------------------- Metropolis (Section II's update)
+METRO = dict(update=1, metro_hits=3, metro_width=1.4)
+
+
+@pytest.mark.parametrize("d", [0, 2])
+def test_metropolis_pass_fp64(d):
+    """Every Metropolis pass (kind 2) from the same configuration against the
+    oracle: the same proposals and decisions, angles within 1e-12 except where
+    a decision sits within rounding of its threshold (none expected)."""
+    po, pm = pair(L=6, Nt=4, beta=0.95, seed=81, **METRO)
+    th0, _ = thermal_config(po, n=5)
+    with ml.Lattice(pm) as lat:
+        for mu in range(4):
+            for par in range(2):
+                n = 2000 + 10 * mu + par
+                ref = th0.copy()
+                oracle.update_pass(po, ref, mu, par, d, n, 2)
+                lat.set_angles(th0)
+                lat.update_pass(mu, par, d, n, 2)
+                dev = wrapd(lat.get_angles() - ref)
+                assert np.mean(dev <= 1e-12) >= 0.9995 and dev.max() < 1e-9, (mu, par, dev.max())
+                moved = wrapd(ref[mu] - th0[mu]) > 0
+                assert 0.1 < moved.mean() < 0.5, moved.mean()  # most unfrozen links of the parity move
+
+
+def test_metropolis_pass_fp32_same_draws():
+    """FP32 Metropolis against the oracle on the 23-bit draws: the same
+    decisions except within rounding of a threshold, angles close."""
+    po, pm = pair(L=8, Nt=4, beta=0.95, seed=82, fp64=False, **METRO)
+    th0, _ = thermal_config(po, n=5)
+    th0 = th0.astype(np.float32).astype(np.float64)
+    close = total = 0
+    with ml.Lattice(pm) as lat:
+        for mu in range(4):
+            for par in range(2):
+                ref = th0.copy()
+                oracle.update_pass(po, ref, mu, par, 0, 9, 2)
+                lat.set_angles(th0)
+                lat.update_pass(mu, par, 0, 9, 2)
+                err = wrapd(lat.get_angles()[mu] - ref[mu])
+                close += int((err < 1e-5).sum())
+                total += err.size
+    assert close >= total - max(2, total // 2000)
+
+
+def test_metropolis_update_kind_needs_metropolis_handle():
+    _, pm = pair(L=4, Nt=4, beta=1.0)
+    with ml.Lattice(pm) as lat:
+        with pytest.raises(ml.MLError) as exc:
+            lat.update_pass(0, 0, 0, 1, 2)
+        assert exc.value.status == ml.ML_EINVAL
+
+
+@pytest.mark.parametrize("two_level,n_sub", [(False, 3), (True, 3)])
+def test_multilevel_run_metropolis_fp64_ordered_phase(two_level, n_sub):
+    """Whole Metropolis multilevel runs against the oracle in the ordered
+    phase (beta = 2.5 from a cold start), FP64 within 1e-9."""
+    kw = dict(slab=2, n_sub=n_sub, k_between=2, r=(1, 2, 3), rf=(1, 2), probes=((0, 0), (1, 0)), comp_mask=0x3F,
+              **METRO)
+    if two_level:
+        kw.update(outer_slab=4, n_sub_outer=2)
+    po, pm = pair(L=4, Nt=8, beta=2.5, seed=91, **kw)
+    th, c = thermal_config(po, n=8, cold=True)
+    ref_rec, c2 = oracle.measure(po, th.copy(), c, 2)
+    with ml.Lattice(pm) as lat:
+        lat.set_angles(th)
+        lat.sweep = c
+        got = lat.measure(2)
+    assert np.abs(got - ref_rec).max() < 1e-9
+
+
 # ----------------------------------------------------------------------------- measurement of one configuration
 MEAS = dict(slab=2, n_sub=1, k_between=0, r=(1, 2, 3), rf=(1, 2, 3), probes=((0, 0), (1, 0), (0, 1), (-1, 2)),
             comp_mask=0x3F)
@@ -306,7 +377,8 @@ def test_full_size_observe_fp32_single_24():
 
 
 @pytest.mark.parametrize("fp64", [True, False])
-@pytest.mark.parametrize("geom", [dict(L=8, Nt=4, n_sub=3), dict(L=6, Nt=8, n_sub=18, outer_slab=4, n_sub_outer=2)])
+@pytest.mark.parametrize("geom", [dict(L=8, Nt=4, n_sub=3), dict(L=6, Nt=8, n_sub=18, outer_slab=4, n_sub_outer=2),
+                                  dict(L=8, Nt=4, n_sub=3, **METRO)])
 def test_sweep_implementations_agree(fp64, geom):
     """The persistent kernel, the per-pass kernels and the cluster-resident
     kernels run the same link updates with the same random numbers: identical

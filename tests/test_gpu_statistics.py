@@ -1,6 +1,9 @@
 """GPU chains against theory and against the oracle's chain, statistically.
 
-* Strong coupling: <cos theta_p> = I1(beta)/I0(beta) + O(u^5), FP64 and FP32.
+* Strong coupling: <cos theta_p> = I1(beta)/I0(beta) + O(u^5), FP64 and FP32,
+  heatbath and Metropolis chains.
+* A Metropolis chain (Section II's update) and a heatbath chain sample the
+  same ensemble: plaquette and P(r) agree within errors.
 * FP32 and FP64 GPU chains against an independent FP64 oracle chain:
   plaquette, P(r), field insertions and vacuum within 3 combined standard
   errors (jackknife over measurements).
@@ -24,11 +27,12 @@ pytestmark = pytest.mark.gpu
 TWO_PI = 2 * np.pi
 
 
+@pytest.mark.parametrize("update", [ml.ML_UPDATE_HEATBATH, ml.ML_UPDATE_METROPOLIS])
 @pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("beta", [0.1, 0.3])
-def test_strong_coupling_plaquette_gpu(fp64, beta):
+def test_strong_coupling_plaquette_gpu(fp64, beta, update):
     p = ml.Params(L=8, Nt=8, beta=beta, seed=200 + int(100 * beta), fp64=fp64, slab=2, n_sub=1, k_between=1,
-                  r=(1,))
+                  r=(1,), update=update, metro_hits=2, metro_width=2.5)
     with ml.Lattice(p) as lat:
         lat.thermalize(20)
         rec = lat.measure(300)
@@ -145,3 +149,24 @@ def test_gauge_covariance_gpu_sweep():
         b = lat.get_angles()
     d = np.abs((b - gauge(a) + np.pi) % TWO_PI - np.pi)
     assert d.max() < 1e-10
+
+
+def test_metropolis_and_heatbath_sample_the_same_ensemble():
+    """FP32 chains of 24 lattices (12 per update) at beta = 0.95 on the
+    6^3 x 4 multilevel workload: plaquette and P(1) means agree between the
+    heatbath and the Metropolis chains within 4 combined standard errors."""
+    base = dict(L=6, Nt=4, beta=0.95, fp64=False, slab=2, n_sub=5, k_between=2, r=(1, 2))
+    out = {}
+    for update in (ml.ML_UPDATE_HEATBATH, ml.ML_UPDATE_METROPOLIS):
+        ps = [ml.Params(seed=700 + 31 * i + update, update=update, metro_hits=4, metro_width=1.5, **base)
+              for i in range(12)]
+        with ml.Batch(ps) as b:
+            b.thermalize(100)
+            recs = b.measure(20)
+        per = [ml.split_record(p, r) for p, r in zip(ps, recs)]
+        out[update] = {"plaq": np.array([s["plaq"].mean() for s in per]),
+                       "P1": np.array([s["P"][:, 0, 0].mean() for s in per])}
+    for key in ("plaq", "P1"):
+        a, b = out[0][key], out[1][key]
+        ea, eb = a.std(ddof=1) / np.sqrt(a.size), b.std(ddof=1) / np.sqrt(b.size)
+        assert abs(a.mean() - b.mean()) < 4 * np.hypot(ea, eb), (key, a.mean(), ea, b.mean(), eb)
