@@ -75,6 +75,8 @@ typedef struct {
                       0 heatbath, 1 Metropolis (Section II)                  */
   int metro_hits;  /* Metropolis hits per link visit                         */
   double metro_width; /* Metropolis proposal half-width w (radians)          */
+  int multihit;    /* 1: P(r) at r >= 2 from the analytic multihit of the
+                      temporal links (Section II.C)                          */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -525,6 +527,58 @@ static void slab_two_link(const geom *g, const double *th, int64_t xs, int t0, i
   *im = pi;
 }
 
+/* Modified Bessel functions of the first kind from their power series,
+ * I_n(x) = sum_k (x/2)^(2k+n) / (k! (k+n)!), summed until the terms stop
+ * changing the sum (x >= 0). */
+static double bessel_i(int n, double x) {
+  const double h = 0.5 * x, h2 = h * h;
+  double term = 1.0;
+  for (int j = 1; j <= n; ++j) term *= h / j; /* (x/2)^n / n! */
+  double sum = term;
+  for (int k = 1; k < 100000; ++k) {
+    term *= h2 / ((double)k * (double)(k + n));
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+double orc_bessel_i0(double x) { return bessel_i(0, x); }
+double orc_bessel_i1(double x) { return bessel_i(1, x); }
+
+/* Analytic multihit (Section II.C: the innermost average of a temporal link
+ * with every other link fixed): the conditional mean of U_0(x, t) under the
+ * weight exp(beta k cos(theta + alpha)) of its staple sum k e^{i alpha},
+ *   <U_0> = e^{-i alpha} I1(beta k) / I0(beta k). */
+static void multihit_link(const orc_params *p, const double *th, int64_t i, double *re, double *im) {
+  double wr, wi;
+  orc_staple(p->L, p->Nt, th, 0, i, &wr, &wi);
+  const double k = sqrt(wr * wr + wi * wi);
+  const double alpha = atan2(wi, wr);
+  const double ratio = k > 0.0 ? orc_bessel_i1(p->beta * k) / orc_bessel_i0(p->beta * k) : 0.0;
+  *re = ratio * cos(alpha);
+  *im = -ratio * sin(alpha);
+}
+
+void orc_multihit_link(const orc_params *p, const double *th, int64_t i, double out[2]) {
+  multihit_link(p, th, i, &out[0], &out[1]);
+}
+
+/* Slab product of the multihit temporal links, prod_{t in slab} <U_0(x, t)>. */
+static void slab_multihit(const orc_params *p, const geom *g, const double *th, int64_t xs, int t0, int d,
+                          double *re, double *im) {
+  double pr = 1.0, pi = 0.0;
+  for (int t = t0; t < t0 + d; ++t) {
+    double ur, ui;
+    multihit_link(p, th, xs + g->Ns * t, &ur, &ui);
+    const double nr = pr * ur - pi * ui, ni = pr * ui + pi * ur;
+    pr = nr;
+    pi = ni;
+  }
+  *re = pr;
+  *im = pi;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Multilevel measurement (Algorithm 1; Section II.C)                        */
 /* ------------------------------------------------------------------------ */
@@ -555,7 +609,8 @@ static cplx cmul(cplx a, cplx b) {
 static int validate(const orc_params *p) {
   if (p->L < 2 || p->Nt < 2 || (p->L & 1) || (p->Nt & 1)) return ORC_EINVAL;
   if (p->beta < 0.0 || p->n_or < 0 || p->draws < 0 || p->draws > 1) return ORC_EINVAL;
-  if (p->update < 0 || p->update > 1) return ORC_EINVAL;
+  if (p->update < 0 || p->update > 1 || p->multihit < 0 || p->multihit > 1) return ORC_EINVAL;
+  if (p->multihit && p->beta > 100.0) return ORC_EINVAL; /* I0(beta k) stays finite for k <= 6 */
   if (p->update == 1 && (p->metro_hits < 1 || p->metro_hits > ORC_MAX_TRIALS || !(p->metro_width > 0.0) ||
                          p->metro_width > ORC_PI))
     return ORC_EINVAL;
@@ -636,7 +691,18 @@ static void accumulate_inner(const orc_params *p, const geom *g, const double *t
       int t0 = sl * d;
       for (int a = 0; a < p->nr; ++a) {
         cplx t;
-        slab_two_link(g, th, xs, t0, d, p->r[a], &t.re, &t.im);
+        if (p->multihit && p->r[a] >= 2 && p->L - p->r[a] >= 2) {
+          /* lines two or more sites apart (both ways round the torus) share
+           * no plaquette: each link is replaced by its multihit mean,
+           * conj(prod <U_0>(x)) prod <U_0>(x + r) */
+          double ar, ai, br, bi;
+          slab_multihit(p, g, th, xs, t0, d, &ar, &ai);
+          slab_multihit(p, g, th, shift(g, xs, 0, p->r[a], 0, 0), t0, d, &br, &bi);
+          t.re = ar * br + ai * bi;
+          t.im = ar * bi - ai * br;
+        } else {
+          slab_two_link(g, th, xs, t0, d, p->r[a], &t.re, &t.im);
+        }
         T_PR(S, sl, a, xs).re += t.re;
         T_PR(S, sl, a, xs).im += t.im;
       }

@@ -59,6 +59,7 @@ class _Params(ctypes.Structure):
         ("probe_dz", ctypes.POINTER(ctypes.c_int)),
         ("comp_mask", ctypes.c_uint), ("threads", ctypes.c_int),
         ("update", ctypes.c_int), ("metro_hits", ctypes.c_int), ("metro_width", ctypes.c_double),
+        ("multihit", ctypes.c_int),
     ]
 
 
@@ -69,6 +70,11 @@ _P = ctypes.POINTER(_Params)
 
 
 def _declare(L):
+    L.orc_bessel_i0.argtypes = [ctypes.c_double]
+    L.orc_bessel_i0.restype = ctypes.c_double
+    L.orc_bessel_i1.argtypes = [ctypes.c_double]
+    L.orc_bessel_i1.restype = ctypes.c_double
+    L.orc_multihit_link.argtypes = [_P, _D, ctypes.c_int64, _D]
     L.orc_philox_batch.argtypes = [ctypes.c_int64, _U32, _U32, _U32]
     L.orc_uniform52.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
     L.orc_uniform52.restype = ctypes.c_double
@@ -116,6 +122,7 @@ class Params:
     update: int = 0         # first sweep of a compound sweep: 0 heatbath, 1 Metropolis
     metro_hits: int = 1     # Metropolis hits per link visit
     metro_width: float = 1.0  # Metropolis proposal half-width (radians)
+    multihit: int = 0       # 1: P(r >= 2) from multihit temporal links
     _keep: list = field(default_factory=list, repr=False)
 
     @property
@@ -135,7 +142,7 @@ class Params:
         return _Params(self.L, self.Nt, float(self.beta), int(self.seed) & (2**64 - 1), self.n_or, self.draws,
                        self.slab, self.n_sub, self.outer_slab, self.n_sub_outer, self.k_between,
                        len(self.r), r, len(self.rf), rf, len(self.probes), dy, dz, self.comp_mask, self.threads,
-                       self.update, self.metro_hits, float(self.metro_width))
+                       self.update, self.metro_hits, float(self.metro_width), self.multihit)
 
 
 def _dp(a: np.ndarray):
@@ -276,3 +283,18 @@ def split_record(p: Params, rec: np.ndarray) -> dict:
     o += 2 * nr
     plaq = rec[..., o]
     return {"P": P, "Pf": Pf, "W": W, "vac": vac, "naive": naive, "plaq": plaq}
+
+
+def bessel_i0(x: float) -> float:
+    return lib().orc_bessel_i0(float(x))
+
+
+def bessel_i1(x: float) -> float:
+    return lib().orc_bessel_i1(float(x))
+
+
+def multihit_link(p: Params, th: np.ndarray, i: int) -> complex:
+    """Multihit mean e^{-i alpha} I1(beta k) / I0(beta k) of the temporal link at site i."""
+    out = np.zeros(2)
+    lib().orc_multihit_link(ctypes.byref(p.c()), _dp(th), int(i), _dp(out))
+    return complex(out[0], out[1])
