@@ -73,7 +73,8 @@ typedef enum {
  * Nt and differs from slab, with n_sub_outer >= 1; 1 <= r, rf <= L-1;
  * |dy|, |dz| <= L-1; beta >= 0; k_between >= 0; n_or >= 0; comp_mask < 64;
  * at least one r; update an ml_update, and for Metropolis 1 <= metro_hits <= 64
- * and 0 < metro_width <= pi.  The lists are copied by ml_create. */
+ * and 0 < metro_width <= pi; multihit 0 or 1, with multihit beta <= 100.  The
+ * lists are copied by ml_create. */
 typedef struct {
   int L, Nt;            /* spatial and temporal extent                         */
   double beta;          /* inverse coupling 1/g^2 of the Wilson action         */
@@ -95,6 +96,12 @@ typedef struct {
   int update;           /* ml_update of the first sweep of a compound sweep    */
   int metro_hits;       /* Metropolis hits per link visit                      */
   double metro_width;   /* Metropolis proposal half-width (radians)            */
+  int multihit;         /* 1: analytic multihit of the temporal links in P(r)
+                           at 2 <= r <= L-2 (Section II.C): each link of the
+                           two lines in a slab is replaced by its conditional
+                           mean e^{-i alpha} I1(beta k) / I0(beta k), k e^{i alpha}
+                           its staple sum; the field profile keeps the plain
+                           links                                               */
 } ml_params;
 
 /* Device-memory allocator supplied by the caller (the Python binding passes

@@ -106,6 +106,7 @@ int validate(const ml_params* p) {
   if (p->update == ML_UPDATE_METROPOLIS &&
       (p->metro_hits < 1 || p->metro_hits > kMaxTrials || !(p->metro_width > 0.0) || p->metro_width > kPi))
     return ML_EINVAL;
+  if (p->multihit < 0 || p->multihit > 1 || (p->multihit && p->beta > 100.0)) return ML_EINVAL;
   return ML_OK;
 }
 
@@ -134,18 +135,22 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   }
   for (int c = 0; c < 6; ++c)
     if (p->comp_mask & (1u << c)) L->comps.push_back(c);
-  for (int v : L->r) {  // union of separations, with each list entry's index in it
+  // union of the separations, with each list entry's index in it; P(r)
+  // entries whose two lines share no plaquette (2 <= r <= L-2) come from the
+  // multihit products when multihit is on, the rest from the plain links
+  auto entry = [&](int v, int mh) {
     int a = 0;
-    while (a < (int)L->R.size() && L->R[a] != v) ++a;
-    if (a == (int)L->R.size()) L->R.push_back(v);
-    L->r_idx.push_back(a);
-  }
-  for (int v : L->rf) {
-    int a = 0;
-    while (a < (int)L->R.size() && L->R[a] != v) ++a;
-    if (a == (int)L->R.size()) L->R.push_back(v);
-    L->rf_idx.push_back(a);
-  }
+    while (a < (int)L->R.size() && !(L->R[a] == v && L->Rmh[a] == mh)) ++a;
+    if (a == (int)L->R.size()) {
+      L->R.push_back(v);
+      L->Rmh.push_back(mh);
+    }
+    return a;
+  };
+  for (int v : L->r) L->r_idx.push_back(entry(v, p->multihit && v >= 2 && p->L - v >= 2 ? 1 : 0));
+  for (int v : L->rf) L->rf_idx.push_back(entry(v, 0));
+  bool any_mh = false;
+  for (int f : L->Rmh) any_mh = any_mh || f;
   const Geom& g = L->g;
   const size_t tsz = e->fp64 ? sizeof(double) : sizeof(float);
   const int nR = static_cast<int>(L->R.size()), nr = p->nr, nrf = p->nrf, np = p->nprobe;
@@ -159,7 +164,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
     lists.insert(lists.end(), v.begin(), v.end());
     return o;
   };
-  const size_t oR = push(L->R), or_ = push(L->r_idx), orf_idx = push(L->rf_idx), orf = push(L->rf),
+  const size_t oR = push(L->R), oRmh = push(L->Rmh), or_ = push(L->r_idx), orf_idx = push(L->rf_idx), orf = push(L->rf),
                ody = push(L->pdy), odz = push(L->pdz), oc = push(L->comps);
 
   L->theta = lat_alloc(e, L, 4ull * g.V * tsz);
@@ -181,6 +186,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   for (int b = 0; b < 2; ++b) {
     L->osum[b] = lat_alloc(e, L, L->osum_bytes);
     L->theta_rec[b] = lat_alloc(e, L, L->trec_bytes);
+    if (any_mh) L->mh_rec[b] = lat_alloc(e, L, 2 * L->trec_bytes);
   }
   L->nparts = vac_part_count(g, p->slab);
   L->vac_part = static_cast<double*>(lat_alloc(e, L, static_cast<size_t>(L->nparts) * 2 * nc * sizeof(double)));
@@ -194,7 +200,8 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   L->scratch_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
   const bool ok = L->theta && L->d_n && L->d_lists && L->accT && L->accO && L->osum[0] && L->osum[1] &&
                   L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->vac_acc && L->partial &&
-                  L->partial_naive && L->scratch_n && (!nslab_out || (L->acc4T && L->acc4O));
+                  L->partial_naive && L->scratch_n && (!nslab_out || (L->acc4T && L->acc4O)) &&
+                  (!any_mh || (L->mh_rec[0] && L->mh_rec[1]));
   if (!ok) return ML_ENOMEM;
 
   MeasLayout& m = L->meas;
@@ -204,6 +211,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   m.np = np;
   m.nc = nc;
   m.R = L->d_lists + oR;
+  m.Rmh = L->d_lists + oRmh;
   m.r_idx = L->d_lists + or_;
   m.rf_idx = L->d_lists + orf_idx;
   m.rf = L->d_lists + orf;
@@ -234,6 +242,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   d.tiles = (g.Vh + kSweepTile - 1) / kSweepTile;
   for (int b = 0; b < 2; ++b) {
     d.theta_rec[b] = L->theta_rec[b];
+    d.mh_rec[b] = L->mh_rec[b];
     d.osum[b] = L->osum[b];
   }
   d.accT = L->accT;
@@ -252,6 +261,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
     ce = cudaMemsetAsync(L->osum[b], 0, L->osum_bytes, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(L->theta_rec[b], 0, L->trec_bytes, s);
+    if (ce == cudaSuccess && L->mh_rec[b]) ce = cudaMemsetAsync(L->mh_rec[b], 0, 2 * L->trec_bytes, s);
   }
   if (ce == cudaSuccess) launch_hot_start(e->fp64, L->theta, g, p->seed, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);  // `lists` is a host temporary
@@ -567,7 +577,7 @@ int plan_resident_sweeps(Engine* e) {
   for (ResidentPlan* p : {&e->res_inner, &e->res_outer}) {
     const int mask = p == &e->res_inner ? e->slab : e->outer_slab;
     std::vector<int4> units;
-    plan_resident(e->fp64, geoms.data(), static_cast<int>(geoms.size()), mask, p, &units);
+    plan_resident(e->fp64, geoms.data(), static_cast<int>(geoms.size()), mask, e->td.max_blocks_mh > 0, p, &units);
     if (p->cs == 0) continue;
     int4* d_units = static_cast<int4*>(dev_alloc(e, units.size() * sizeof(int4)));
     p->done = static_cast<unsigned long long*>(dev_alloc(e, sizeof(unsigned long long)));
@@ -735,6 +745,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
       td.max_y_O = std::max(td.max_y_O, d.nslab * m.nrf * fold_probe_groups(m.np));
     td.max_vac_blocks = std::max(td.max_vac_blocks, d.nparts);
     td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
+    if (d.mh_rec[0]) td.max_blocks_mh = std::max(td.max_blocks_mh, (d.nslab * d.g.Ns + 255) / 256);
   }
   td.nlat = n;
   td.total_tiles = static_cast<int>(tile_lat.size());

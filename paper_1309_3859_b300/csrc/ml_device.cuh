@@ -135,6 +135,8 @@ struct Prec<double> {
   __device__ static __forceinline__ double cos_pi_u(double u) { return cos(kPi * u); }
   __device__ static __forceinline__ double wrap(double a) { return a - kTwoPi * floor((a + kPi) / kTwoPi); }
   __device__ static __forceinline__ double pi() { return kPi; }
+  // I1(x) / I0(x), the multihit mean modulus at x = beta k
+  __device__ static __forceinline__ double bessel_ratio(double x) { return cyl_bessel_i1(x) / cyl_bessel_i0(x); }
   static constexpr double kappa_tiny = 1e-150;
 };
 
@@ -152,6 +154,7 @@ struct Prec<float> {
   __device__ static __forceinline__ float cos_pi_u(float u) { return __cosf(kPiF * u); }
   __device__ static __forceinline__ float wrap(float a) { return fmaf(-kTwoPiF, floorf((a + kPiF) * kInvTwoPiF), a); }
   __device__ static __forceinline__ float pi() { return kPiF; }
+  __device__ static __forceinline__ float bessel_ratio(float x) { return cyl_bessel_i1f(x) / cyl_bessel_i0f(x); }
   static constexpr float kappa_tiny = 1e-15f;
 };
 

@@ -21,7 +21,7 @@ struct LatState {
   Geom g{};
   double beta = 0.0;
   uint64_t seed = 0;
-  std::vector<int> r, rf, pdy, pdz, comps, R, r_idx, rf_idx;
+  std::vector<int> r, rf, pdy, pdz, comps, R, Rmh, r_idx, rf_idx;
   MeasLayout meas{};
   void* theta = nullptr;
   unsigned long long* d_n = nullptr;
@@ -30,6 +30,7 @@ struct LatState {
   size_t accT_bytes = 0, accO_bytes = 0, acc4T_bytes = 0, acc4O_bytes = 0;
   void* osum[2] = {nullptr, nullptr};       // record ring [nslab][nc][2][Ns][slots]
   void* theta_rec[2] = {nullptr, nullptr};  // record ring [nslab][Ns][slots]
+  void* mh_rec[2] = {nullptr, nullptr};     // multihit ring [nslab][2][Ns][slots], or none
   size_t osum_bytes = 0, trec_bytes = 0;
   double* vac_part = nullptr;
   int nparts = 0;

@@ -16,6 +16,7 @@ struct MeasLayout {
   int nR;            // separations in the union of the P(r) and field lists
   int nr, nrf, np, nc;
   const int* R;      // [nR] separations of the union
+  const int* Rmh;    // [nR] 1: entry from the multihit slab products (P(r) only)
   const int* r_idx;  // [nr] index into R of each P(r) separation
   const int* rf_idx; // [nrf] index into R of each field separation
   const int* rf;     // [nrf] field separations
@@ -42,6 +43,7 @@ struct LatDesc {
   int slab, nslab;            // inner slab thickness d and Nt / d
   int tile_start, tiles;      // sweep tiles of kSweepTile links
   void* theta_rec[2];         // record ring buffers [nslab][Ns][slots]
+  void* mh_rec[2];            // multihit ring [nslab][2][Ns][slots] (modulus, phase); null: none
   void* osum[2];              // [nslab][nc][2][Ns][slots], slots = rec_batch(fp64)
   double2* accT;              // inner slab sums: double2 (re, im), or for FP32
   double2* accO;              //   lattices float4 (re_hi, re_lo, im_hi, im_lo)
@@ -82,6 +84,7 @@ struct TableDims {
   int max_y_O;          // nslab * nrf * probe groups
   int max_vac_blocks;   // vac_part_count
   int max_vac_parts;    // nc * 2
+  int max_blocks_mh;    // ceil(nslab * Ns / 256) of the multihit lattices; 0: none
 };
 
 constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep kernels)
@@ -98,9 +101,13 @@ constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep k
 int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int* tile_lat, const TableDims& td,
                         const LatCtl* ctl, int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
                         cudaStream_t s, bool record = false, int rec_buf = 0, int rec_slot = 0);
-// record of each lattice's configuration into ring slot (buf, slot)
+// record of each lattice's configuration into ring slot (buf, slot), with
+// the multihit record of the multihit lattices
 void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
                          cudaStream_t s);
+// the multihit record alone (after a sweep launch that recorded the rest)
+void launch_mh_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
+                            cudaStream_t s);
 // fold slots 0 .. nrec-1 of ring buffer buf into each lattice's slab sums,
 // and their vacuum sums into vac_acc (skip_O: leave the field-insertion sums
 // to a products launch with that buffer as its tail; overwrite: the slab sums
@@ -161,10 +168,12 @@ struct ResidentPlan {
   int nunits = 0;                      // (lattice, slab) units = clusters launched
   const int4* units = nullptr;         // device [nunits] (lattice, slab, ny, nz bricks)
   unsigned long long* done = nullptr;  // finished-unit counter (zero between launches)
+  bool mh = false;                     // the records include the multihit products
 };
 // Fills everything but the device pointers; the host list of units goes to
-// `units` (empty when cs = 0).
-void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, ResidentPlan* p, std::vector<int4>* units);
+// `units` (empty when cs = 0).  mh: the table has multihit lattices.
+void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, bool mh, ResidentPlan* p,
+                   std::vector<int4>* units);
 // n_rec rounds of n_compound compound slab sweeps (mask p.mask) of every
 // lattice of the table, each optionally followed by the record into ring slot
 // (rec_buf, rec_slot + round): n_rec sub-updates as n_rec calls of

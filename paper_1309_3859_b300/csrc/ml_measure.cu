@@ -87,6 +87,38 @@ __global__ void __launch_bounds__(256) k_record_table(const LatDesc* __restrict_
   record_warp<T>(L, buf, slot, blockIdx.y, w, threadIdx.x & 31);
 }
 
+// Multihit record of each multihit lattice's configuration into ring slot
+// `slot` of buffer `buf` (after the configuration's own record, in stream
+// order); grid (sites x slabs, 1, lattices), one thread per (slab, site).
+template <typename T>
+__global__ void __launch_bounds__(256) k_mh_record_table(const LatDesc* __restrict__ desc,
+                                                         const LatCtl* __restrict__ ctl, int buf, int slot) {
+  const int li = blockIdx.z;
+  if (ctl) {
+    if (!ctl[li].record) return;
+    buf = ctl[li].buf;
+    slot = ctl[li].slot;
+  }
+  const LatDesc& L = desc[li];
+  const Geom g = L.g;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (!L.mh_rec[buf] || k >= L.nslab * g.Ns) return;
+  const int s = k / g.Ns, x = k - s * g.Ns;
+  const T* th = static_cast<const T*>(L.theta);
+  int c[4];
+  spatial_coords(g, x, &c[1], &c[2], &c[3]);
+  T mod, ph;
+  multihit_slab<T>(s * L.slab, L.slab, static_cast<T>(L.beta),
+                   [&](int t, int nu, T v[6]) {
+                     c[0] = t;
+                     temporal_staples<T>(th, g, c, nu, v);
+                   },
+                   &mod, &ph);
+  T* mh = static_cast<T*>(L.mh_rec[buf]);
+  mh[mh_index<T>(g, s, 0, x, slot)] = mod;
+  mh[mh_index<T>(g, s, 1, x, slot)] = ph;
+}
+
 // ---------------------------------------------------------------------------
 // Vacuum sums of the folded records (Section II.B: the field operators'
 // vacuum expectation values, estimated on every sub-update configuration):
@@ -237,7 +269,7 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 // The sum over the batch is formed in the records' precision and added once,
 // so each accumulator is read and written once per batch.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, bool MH>
 __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict__ desc,
                                                        const LatCtl* __restrict__ ctl, int buf, int nrec,
                                                        int overwrite) {
@@ -257,9 +289,24 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
   spatial_coords(g, x, &cx, &cy, &cz);
   const int xr = wrapc(cx + m.R[a], g.L) + g.L * (cy + g.L * cz);
   constexpr int B = RecBatch<T>::n;
-  const T* rec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
   T er[B], ei[B];
-  batch_phases<T>(rec + static_cast<size_t>(x) * B, rec + static_cast<size_t>(xr) * B, nrec, er, ei);
+  if (MH && m.Rmh[a]) {
+    // multihit slab products: conj(mod_x e^{i ph_x}) mod_xr e^{i ph_xr}
+    const T* mh = static_cast<const T*>(L.mh_rec[buf]);
+    T mx[B], mr[B];
+    load_batch<T>(mh + mh_index<T>(g, s, 0, x, 0), mx);
+    load_batch<T>(mh + mh_index<T>(g, s, 0, xr, 0), mr);
+    batch_phases<T>(mh + mh_index<T>(g, s, 1, x, 0), mh + mh_index<T>(g, s, 1, xr, 0), nrec, er, ei);
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const T w = mx[j] * mr[j];
+      er[j] *= w;
+      ei[j] *= w;
+    }
+  } else {
+    const T* rec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
+    batch_phases<T>(rec + static_cast<size_t>(x) * B, rec + static_cast<size_t>(xr) * B, nrec, er, ei);
+  }
   T sr = T(0), si = T(0);
 #pragma unroll
   for (int j = 0; j < B; ++j) {
@@ -286,7 +333,6 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
     k_accum_O_table(const LatDesc* __restrict__ desc, const LatCtl* __restrict__ ctl, int buf, int nrec,
                     int overwrite) {
   constexpr int B = RecBatch<T>::n;
-  constexpr int kMaxCK = 12;  // components x (Re, Im) insertions
   const int li = blockIdx.z;
   if (ctl) {
     if (!ctl[li].fold) return;
@@ -724,16 +770,31 @@ void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const
   else
     k_record_table<float><<<grid, 256, 0, s>>>(d, ctl, buf, slot);
   count_launches(1);
+  launch_mh_record_table(fp64, d, td, ctl, buf, slot, s);
+}
+
+void launch_mh_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
+                            cudaStream_t s) {
+  if (td.max_blocks_mh <= 0) return;
+  const dim3 grid(td.max_blocks_mh, 1, td.nlat);
+  if (fp64)
+    k_mh_record_table<double><<<grid, 256, 0, s>>>(d, ctl, buf, slot);
+  else
+    k_mh_record_table<float><<<grid, 256, 0, s>>>(d, ctl, buf, slot);
+  count_launches(1);
 }
 
 void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
                        cudaStream_t s, bool skip_O, bool overwrite) {
   const int ow = overwrite ? 1 : 0;
   const dim3 gt(td.max_blocks_site, td.max_y_T, td.nlat);
+  // the multihit variant (more registers) only for tables with multihit lattices
   if (fp64)
-    k_accum_T_table<double><<<gt, 256, 0, s>>>(d, ctl, buf, nrec, ow);
+    (td.max_blocks_mh > 0 ? k_accum_T_table<double, true> : k_accum_T_table<double, false>)<<<gt, 256, 0, s>>>(
+        d, ctl, buf, nrec, ow);
   else
-    k_accum_T_table<float><<<gt, 256, 0, s>>>(d, ctl, buf, nrec, ow);
+    (td.max_blocks_mh > 0 ? k_accum_T_table<float, true> : k_accum_T_table<float, false>)<<<gt, 256, 0, s>>>(
+        d, ctl, buf, nrec, ow);
   count_launches(1);
   if (td.max_y_O > 0 && !skip_O) {
     const dim3 go(td.max_blocks_site, td.max_y_O, td.nlat);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "ml_internal.h"
+#include "ml_link.cuh"
 
 namespace ml {
 
@@ -44,6 +45,50 @@ __device__ __forceinline__ T plaquette_angle(const T* th, const Geom& g, const i
   const int ipmu = shifted(g, c, mu, 1, nu, 0);
   const int ipnu = shifted(g, c, nu, 1, mu, 0);
   return th[soa(g, mu, i, p)] + th[soa(g, nu, ipmu, p ^ 1)] - th[soa(g, mu, ipnu, p ^ 1)] - th[soa(g, nu, i, p)];
+}
+
+// Analytic multihit of the slab's temporal links at one spatial site
+// (Section II.C): each U_0(x, t) with every other link fixed averages to
+// e^{-i alpha_t} I1(beta k_t) / I0(beta k_t), k_t e^{i alpha_t} its staple sum,
+// and the links of one line share no plaquette, so the slab product of the
+// means is mod e^{i phase} with mod = prod_t I1/I0 and phase = -sum_t alpha_t.
+// staples_at(t, nu, v) gives U_0(x, t)'s six staple angles of plane (0, nu)
+// in the order of the link update, so k_t and alpha_t are bit-identical to
+// the update's.
+template <typename T, typename StaplesAt>
+__device__ __forceinline__ void multihit_slab(int t0, int d, T beta, StaplesAt&& staples_at, T* mod, T* phase) {
+  using P = Prec<T>;
+  T m = T(1);
+  double ph = 0.0;
+  for (int t = t0; t < t0 + d; ++t) {
+    T k, alpha;
+    staple_sum<T>(0, [&](int nu, T v[6]) { staples_at(t, nu, v); }, &k, &alpha);
+    m *= P::bessel_ratio(beta * k);
+    ph -= static_cast<double>(alpha);
+  }
+  *mod = m;
+  *phase = static_cast<T>(P::fp64 ? ph : ph - kTwoPi * floor((ph + kPi) * (1.0 / kTwoPi)));
+}
+
+// Staple angles of U_0 at coordinates c (t, x, y, z) for plane (0, nu), in
+// the order of the link update: theta_nu(x + 0), theta_0(x + nu),
+// theta_nu(x), theta_nu(x + 0 - nu), theta_0(x - nu), theta_nu(x - nu).
+template <typename T>
+__device__ __forceinline__ void temporal_staples(const T* th, const Geom& g, const int c[4], int nu, T v[6]) {
+  const int p = parity_of_coords(c), op = p ^ 1;
+  const int i = site_index(g, c[0], c[1], c[2], c[3]);
+  v[0] = th[soa(g, nu, shifted(g, c, 0, 1, nu, 0), op)];
+  v[1] = th[soa(g, 0, shifted(g, c, nu, 1, 0, 0), op)];
+  v[2] = th[soa(g, nu, i, p)];
+  v[3] = th[soa(g, nu, shifted(g, c, 0, 1, nu, -1), p)];
+  v[4] = th[soa(g, 0, shifted(g, c, nu, -1, 0, 0), op)];
+  v[5] = th[soa(g, nu, shifted(g, c, nu, -1, 0, 0), op)];
+}
+
+// Multihit ring slot of slab s, site x: modulus at part 0, phase at part 1.
+template <typename T>
+__device__ __forceinline__ size_t mh_index(const Geom& g, int s, int part, int x, int slot) {
+  return ((static_cast<size_t>(s) * 2 + part) * g.Ns + x) * RecBatch<T>::n + slot;
 }
 
 // Warps of the record of one slab: warp xw covers the spatial sites

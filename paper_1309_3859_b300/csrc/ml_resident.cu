@@ -145,24 +145,29 @@ __device__ __forceinline__ void st_cluster(uint32_t a, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
+// Staple angles of U_mu at box cell bi, local time tl, for plane (mu, nu),
+// in the order of the link update.
+template <typename T>
+__device__ __forceinline__ void box_staples(const Box& b, const T* buf, int mu, int tl, int bi, int nu, T w[6]) {
+  const int tp = tl + (mu == 0);  // x + mu
+  const int bp = bi + b.off(mu);
+  auto at = [&](int rho, int t_, int c) { return buf[b.slot(rho, t_) * b.vol + c]; };
+  const int dt = nu == 0, o = b.off(nu);
+  w[0] = at(nu, tp, bp);            // theta_nu(x + mu)
+  w[1] = at(mu, tl + dt, bi + o);   // theta_mu(x + nu)
+  w[2] = at(nu, tl, bi);            // theta_nu(x)
+  w[3] = at(nu, tp - dt, bp - o);   // theta_nu(x + mu - nu)
+  w[4] = at(mu, tl - dt, bi - o);   // theta_mu(x - nu)
+  w[5] = at(nu, tl - dt, bi - o);   // theta_nu(x - nu)
+}
+
 // Update of the link U_mu at box cell bi, local time tl; the new angle also
 // goes to the mirrors mirror[m0 .. m1) of the cell (cluster addresses of slot 0).
 template <typename T, int KIND>
 __device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* mirror, int m0, int m1, int mu,
                                          int tl, int bi, uint32_t site, unsigned long long n, uint32_t k0,
                                          uint32_t k1, T beta, int* err, const UpdateRule& rule) {
-  const int tp = tl + (mu == 0);  // x + mu
-  const int bp = bi + b.off(mu);
-  auto at = [&](int rho, int t_, int c) { return buf[b.slot(rho, t_) * b.vol + c]; };
-  auto staples = [&](int nu, T w[6]) {
-    const int dt = nu == 0, o = b.off(nu);
-    w[0] = at(nu, tp, bp);            // theta_nu(x + mu)
-    w[1] = at(mu, tl + dt, bi + o);   // theta_mu(x + nu)
-    w[2] = at(nu, tl, bi);            // theta_nu(x)
-    w[3] = at(nu, tp - dt, bp - o);   // theta_nu(x + mu - nu)
-    w[4] = at(mu, tl - dt, bi - o);   // theta_mu(x - nu)
-    w[5] = at(nu, tl - dt, bi - o);   // theta_nu(x - nu)
-  };
+  auto staples = [&](int nu, T w[6]) { box_staples<T>(b, buf, mu, tl, bi, nu, w); };
   const int sl = b.slot(mu, tl);
   T* self = buf + sl * b.vol + bi;
   T out;
@@ -185,7 +190,7 @@ __device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* m
 // record into ring slot rec_slot + round.  done: counter of finished units;
 // the last one advances every lattice's sweep counter by n_rec n_compound and
 // resets it.
-template <typename T>
+template <typename T, bool MH>
 __global__ void __launch_bounds__(kResThreads, 1)
     k_sweeps_resident(const LatDesc* __restrict__ desc, const int4* __restrict__ units, int nunits, int nlat, int d,
                       int n_or, int n_compound, int* __restrict__ err, unsigned long long* __restrict__ done,
@@ -361,6 +366,14 @@ __global__ void __launch_bounds__(kResThreads, 1)
           for (int tl = 0; tl < d; ++tl) tsum += static_cast<double>(buf[tl * b.vol + bi]);
           static_cast<T*>(Ld.theta_rec[rec_buf])[(static_cast<size_t>(s) * g.Ns + x) * RecBatch<T>::n + slot] =
               static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
+          if (MH && Ld.mh_rec[rec_buf]) {
+            T mod, ph;
+            multihit_slab<T>(0, d, beta, [&](int tl, int nu, T v[6]) { box_staples<T>(b, buf, 0, tl, bi, nu, v); },
+                             &mod, &ph);
+            T* mh = static_cast<T*>(Ld.mh_rec[rec_buf]);
+            mh[mh_index<T>(g, s, 0, x, slot)] = mod;
+            mh[mh_index<T>(g, s, 1, x, slot)] = ph;
+          }
           continue;
         }
         int mu, nu;
@@ -428,13 +441,21 @@ static cudaLaunchConfig_t resident_config(int cs, size_t smem, int clusters, cud
   return cfg;
 }
 
+// the multihit variant records the multihit products too (more registers)
 template <typename T>
-static void plan_resident_t(const Geom* geoms, int nlat, int mask, ResidentPlan* p, std::vector<int4>* units) {
+static auto resident_kernel(bool mh) {
+  return mh ? k_sweeps_resident<T, true> : k_sweeps_resident<T, false>;
+}
+
+template <typename T>
+static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, ResidentPlan* p,
+                            std::vector<int4>* units) {
   *p = ResidentPlan{};
   p->mask = mask;
+  p->mh = mh;
   units->clear();
   if (mask < 1) return;
-  auto kern = k_sweeps_resident<T>;
+  auto kern = resident_kernel<T>(mh);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kResSmemMax)) !=
       cudaSuccess) {
     cudaGetLastError();
@@ -474,11 +495,12 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, ResidentPlan*
   }
 }
 
-void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, ResidentPlan* p, std::vector<int4>* units) {
+void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, bool mh, ResidentPlan* p,
+                   std::vector<int4>* units) {
   if (fp64)
-    plan_resident_t<double>(geoms, nlat, mask, p, units);
+    plan_resident_t<double>(geoms, nlat, mask, mh, p, units);
   else
-    plan_resident_t<float>(geoms, nlat, mask, p, units);
+    plan_resident_t<float>(geoms, nlat, mask, mh, p, units);
 }
 
 int launch_sweeps_resident(bool fp64, const ResidentPlan& p, const LatDesc* d, int nlat, int n_or, int n_compound,
@@ -490,11 +512,11 @@ int launch_sweeps_resident(bool fp64, const ResidentPlan& p, const LatDesc* d, i
   const int rec = record ? 1 : 0;
   if (fp64) {
     cudaLaunchConfig_t cfg = resident_config<double>(p.cs, p.smem, p.nunits, s, at);
-    e = cudaLaunchKernelEx(&cfg, k_sweeps_resident<double>, d, p.units, p.nunits, nlat, p.mask, n_or, n_compound,
+    e = cudaLaunchKernelEx(&cfg, resident_kernel<double>(p.mh), d, p.units, p.nunits, nlat, p.mask, n_or, n_compound,
                            err, p.done, rec, rec_buf, rec_slot, n_rec);
   } else {
     cudaLaunchConfig_t cfg = resident_config<float>(p.cs, p.smem, p.nunits, s, at);
-    e = cudaLaunchKernelEx(&cfg, k_sweeps_resident<float>, d, p.units, p.nunits, nlat, p.mask, n_or, n_compound, err,
+    e = cudaLaunchKernelEx(&cfg, resident_kernel<float>(p.mh), d, p.units, p.nunits, nlat, p.mask, n_or, n_compound, err,
                            p.done, rec, rec_buf, rec_slot, n_rec);
   }
   count_launches(1);

@@ -317,6 +317,7 @@ int rebuild_tables(ml_server* s) {
       td.max_y_O = std::max(td.max_y_O, d.nslab * m.nrf * fold_probe_groups(m.np));
     td.max_vac_blocks = std::max(td.max_vac_blocks, d.nparts);
     td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
+    if (d.mh_rec[0]) td.max_blocks_mh = std::max(td.max_blocks_mh, (d.nslab * d.g.Ns + 255) / 256);
   }
   td.nlat = static_cast<int>(n);
   td.total_tiles = static_cast<int>(s->h_tile_lat.size());

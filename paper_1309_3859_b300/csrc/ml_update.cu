@@ -349,6 +349,7 @@ int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int*
              : launch_sweeps_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, bar, rec, rec_buf,
                                             rec_slot, s);
     count_launches(1);
+    if (record) launch_mh_record_table(fp64, d, td, ctl, rec_buf, rec_slot, s);
   } else {
     if (fp64)
       launch_passes_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s);

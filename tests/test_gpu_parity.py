@@ -11,6 +11,9 @@ Deterministic comparisons (same inputs, same Philox stream):
   same configuration within 1e-5 relative on the plaquette.
 * Whole multilevel runs (one and two levels) in the ordered phase, where
   rounding differences are not amplified by the chain: FP64 within 1e-9.
+* Analytic multihit (Section II.C): the multihit P(r) of one configuration and
+  of whole ordered-phase runs against the oracle; on the same chain only the
+  multihit entries differ from the plain run's records.
 
 Chains near the transition amplify rounding by ~100x per sweep, so there
 the comparison is statistical (test_gpu_statistics.py).
@@ -293,6 +296,55 @@ def test_observe_fp32_component_subset():
     _observe_parity(6, 4, False, 2e-5, comp_mask=0b010010)
 
 
+# ----------------------------------------------------------------------------- analytic multihit (Section II.C)
+@pytest.mark.parametrize("L,Nt", [(4, 8), (6, 4)])
+def test_observe_multihit_fp64(L, Nt):
+    """P(r) at 2 <= r <= L-2 from the multihit products, r = 1 and r = L-1
+    (adjacent lines) and the field records from the plain links."""
+    _observe_parity(L, Nt, True, 1e-12, multihit=1, r=tuple(r for r in (1, 2, 3, 5) if r < L))
+
+
+def test_observe_multihit_fp32():
+    _observe_parity(6, 4, False, 2e-5, multihit=1, r=(1, 2, 3, 5))
+
+
+@pytest.mark.parametrize("two_level,n_sub", [(False, 37), (True, 3)])
+def test_multilevel_run_multihit_fp64_ordered_phase(two_level, n_sub):
+    kw = dict(slab=2, n_sub=n_sub, k_between=2, r=(1, 2, 3), rf=(1, 2), probes=((0, 0), (1, 0)), comp_mask=0x3F,
+              multihit=1)
+    if two_level:
+        kw.update(outer_slab=4, n_sub_outer=2)
+    po, pm = pair(L=6, Nt=8, beta=2.5, seed=92, **kw)
+    th, c = thermal_config(po, n=8, cold=True)
+    ref_rec, _ = oracle.measure(po, th.copy(), c, 2)
+    with ml.Lattice(pm) as lat:
+        lat.set_angles(th)
+        lat.sweep = c
+        got = lat.measure(2)
+    assert np.abs(got - ref_rec).max() < 1e-9
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_multihit_changes_only_the_multihit_entries(fp64):
+    """Multihit is a different estimator on the same chain: with the same seed
+    the angles, P(r) at adjacent lines, the field records, the vacuum and the
+    naive estimator are bit-identical to the plain run's; P(r >= 2) differs."""
+    base = dict(L=8, Nt=8, beta=1.0, seed=17, fp64=fp64, slab=2, n_sub=20, k_between=2, r=(1, 2, 4, 7), rf=(2, 3),
+                probes=((0, 0), (1, 1)), comp_mask=0x3F)
+    out = {}
+    for mh in (0, 1):
+        with ml.Lattice(ml.Params(multihit=mh, **base)) as lat:
+            lat.thermalize(4)
+            out[mh] = (ml.split_record(lat.p, lat.measure(3)), lat.get_angles())
+    (a, tha), (b, thb) = out[0], out[1]
+    assert np.array_equal(tha, thb)
+    for key in ("Pf", "W", "vac", "naive", "plaq"):
+        assert np.array_equal(a[key], b[key]), key
+    for i, r in enumerate(base["r"]):
+        same = np.array_equal(a["P"][:, i], b["P"][:, i])
+        assert same == (r in (1, 7)), r
+
+
 # ----------------------------------------------------------------------------- whole runs, ordered phase
 @pytest.mark.parametrize("two_level,n_sub", [(False, 3), (True, 3), (False, 37), (True, 18)])
 def test_multilevel_run_fp64_ordered_phase(two_level, n_sub):
@@ -356,11 +408,14 @@ def test_full_size_pass_fp32_single_24():
             assert np.quantile(err, 0.999) < 1e-4 and np.median(err) < 1e-6
 
 
-def test_full_size_observe_fp32_single_24():
+@pytest.mark.parametrize("multihit", [0, 1])
+def test_full_size_observe_fp32_single_24(multihit):
     """24^3 x 8 with the full r = 2..12, six components, offsets 0..8 layout:
-    measurement of one configuration against the oracle."""
+    measurement of one configuration against the oracle (with multihit every
+    P(r) entry comes from the multihit products)."""
     w = workloads.SINGLE_24
-    kw = dict(slab=2, n_sub=1, k_between=0, r=w.r, rf=w.rf, probes=w.probes, comp_mask=w.comp_mask, threads=0)
+    kw = dict(slab=2, n_sub=1, k_between=0, r=w.r, rf=w.rf, probes=w.probes, comp_mask=w.comp_mask, threads=0,
+              multihit=multihit)
     po = oracle.Params(L=w.L, Nt=w.Nt, beta=w.beta, seed=4, draws=1, **kw)
     kw.pop("threads")
     pm = ml.Params(L=w.L, Nt=w.Nt, beta=w.beta, seed=4, fp64=False, **kw)
@@ -378,7 +433,7 @@ def test_full_size_observe_fp32_single_24():
 
 @pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("geom", [dict(L=8, Nt=4, n_sub=3), dict(L=6, Nt=8, n_sub=18, outer_slab=4, n_sub_outer=2),
-                                  dict(L=8, Nt=4, n_sub=3, **METRO)])
+                                  dict(L=8, Nt=4, n_sub=3, **METRO), dict(L=6, Nt=4, n_sub=18, multihit=1)])
 def test_sweep_implementations_agree(fp64, geom):
     """The persistent kernel, the per-pass kernels and the cluster-resident
     kernels run the same link updates with the same random numbers: identical
