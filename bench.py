@@ -311,6 +311,40 @@ def serving_point(ml, n_requests=1000, load=0.8, budget_gb=160):
             "request": "100 thermalisation sweeps + 1 measurement (50 sub-updates), L in 12..32, Nt in 4..12"}
 
 
+def multihit_point(ml, w, n_meas=40):
+    """The step's workload with Section II.C's analytic multihit for P(r)
+    against the plain estimator on the same chain (same seed): time per step
+    and the jackknife error of every P(r) entry, so the error reduction per
+    unit of device time can be read off."""
+    import torch
+
+    from paper_1309_3859_b300.stats import jackknife
+
+    out = {"workload": w.name + "-multihit", "measurements": n_meas}
+    errs = {}
+    for mh in (0, 1):
+        p = ml.Params.from_workload(w, seed=w.seed + 7, multihit=mh)
+        with ml.Lattice(p) as lat:
+            lat.thermalize(w.n_therm)
+            rec = torch.empty((n_meas, lat.rec_len), dtype=torch.float64, device=lat.device)
+            lat.measure_device(1, rec[:1])
+            lat.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(lat.stream)
+            lat.measure_device(n_meas, rec)
+            e1.record(lat.stream)
+            lat.sync()
+            ms = e0.elapsed_time(e1) / n_meas
+            P = ml.split_record(p, rec.cpu().numpy())["P"][:, :, 0]
+        errs[mh] = np.array([jackknife(P[:, a])[1] for a in range(P.shape[1])])
+        out["ms_per_step" if mh else "plain_ms_per_step"] = ms
+    ratio = errs[0] / errs[1]
+    out["error_ratio_plain_over_multihit"] = {f"r={r}": float(x) for r, x in zip(w.r, ratio)}
+    # (error ratio)^2 x (time ratio): measurements needed for equal error, per unit time
+    out["efficiency_gain_median"] = float(np.median(ratio ** 2) * out["plain_ms_per_step"] / out["ms_per_step"])
+    return out
+
+
 def run_gpu(args, w, rank, world):
     import torch
 
@@ -404,6 +438,7 @@ def run_gpu(args, w, rank, world):
             "launch_ms": launch_ms, "sub_updates_per_launch": per_launch, "batch_slots": nB}
     hbm_point = hbm_sweep_point(ml, peak) if rank == 0 and not args.no_extra else None
     batch_point = batched_point(ml) if rank == 0 and not args.no_extra else None
+    mh_point = multihit_point(ml, w) if rank == 0 and not args.no_extra else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -443,6 +478,7 @@ def run_gpu(args, w, rank, world):
         "kernel_ms": kms, "kernel_share": share,
         "sweep_hbm_point": hbm_point,
         "batched": batch_point,
+        "multihit": mh_point,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
         "gpu_launches": int(launches),

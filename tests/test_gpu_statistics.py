@@ -8,6 +8,8 @@
   plaquette, P(r), field insertions and vacuum within 3 combined standard
   errors (jackknife over measurements).
 * Multilevel P(r) against the naive estimator on the small workload.
+* Multihit P(r) against the plain estimator on the same chain (paired
+  differences) and its smaller error.
 * beta = 0: zero means.
 * Gauge covariance of one GPU heatbath sweep.
 All seeds are fixed and the GPU reductions run in a fixed order, so each of
@@ -104,6 +106,26 @@ def test_multilevel_matches_naive_small_workload():
     for a in range(4):
         mi, ei = jackknife(ml_bins(s["P"][:, a, 1]))
         assert abs(mi) < 4 * ei + 1e-15
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_multihit_unbiased_and_reduces_the_error_gpu(fp64):
+    """Section II.C's multihit on the same chain as the plain estimator: the
+    paired differences of P(r >= 2) average to zero, and the multihit error
+    is smaller."""
+    base = dict(L=8, Nt=8, beta=1.0, seed=77, fp64=fp64, slab=2, n_sub=20, k_between=2, r=(2, 3, 4))
+    s = {}
+    for mh in (0, 1):
+        p = ml.Params(multihit=mh, **base)
+        with ml.Lattice(p) as lat:
+            lat.thermalize(40)
+            s[mh] = ml.split_record(p, lat.measure(100))["P"][:, :, 0]
+    for a in range(3):
+        md, ed = jackknife(ml_bins(s[1][:, a] - s[0][:, a]))
+        assert abs(md) < 3 * ed, (a, md, ed)
+        _, e0 = jackknife(ml_bins(s[0][:, a]))
+        _, e1 = jackknife(ml_bins(s[1][:, a]))
+        assert e1 < e0, (a, e1, e0)
 
 
 @pytest.mark.parametrize("fp64", [True, False])
