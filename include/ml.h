@@ -73,8 +73,9 @@ typedef enum {
  * Nt and differs from slab, with n_sub_outer >= 1; 1 <= r, rf <= L-1;
  * |dy|, |dz| <= L-1; beta >= 0; k_between >= 0; n_or >= 0; comp_mask < 64;
  * at least one r; update an ml_update, and for Metropolis 1 <= metro_hits <= 64
- * and 0 < metro_width <= pi; multihit 0 or 1, with multihit beta <= 100.  The
- * lists are copied by ml_create. */
+ * and 0 < metro_width <= pi; multihit 0 or 1, with multihit beta <= 100;
+ * replay 0 or 1, with replay outer_slab = 0.  The lists are copied by
+ * ml_create. */
 typedef struct {
   int L, Nt;            /* spatial and temporal extent                         */
   double beta;          /* inverse coupling 1/g^2 of the Wilson action         */
@@ -102,6 +103,13 @@ typedef struct {
                            mean e^{-i alpha} I1(beta k) / I0(beta k), k e^{i alpha}
                            its staple sum; the field profile keeps the plain
                            links                                               */
+  int replay;           /* 1: field insertions by replay (one level only): the
+                           inner loop runs twice from the same configuration
+                           and sweep numbers, first forming the slab averages
+                           [T], then adding every sub-update's T O times the
+                           other slabs' [T] straight into the products, so no
+                           per-site [TO] sums are kept (same estimator, the
+                           field-insertion memory for twice the slab sweeps) */
 } ml_params;
 
 /* Device-memory allocator supplied by the caller (the Python binding passes
@@ -268,8 +276,8 @@ int ml_batch_slots(ml_lattice *h, int *n);
 
 /* A batch holds n independent lattices (different L, Nt, beta, seed,
  * separations, probes and components) that share one schedule: precision,
- * n_or, slab, outer_slab, n_sub, n_sub_outer and k_between must be equal
- * (else ML_EINVAL).  Every sweep, record and fold of the batch is one kernel
+ * n_or, slab, outer_slab, n_sub, n_sub_outer, k_between and replay must be
+ * equal (else ML_EINVAL).  Every sweep, record and fold of the batch is one kernel
  * launch over all its lattices (the multi-lattice kernels a single lattice
  * also runs), so each lattice's results are identical to those of the same
  * parameters run alone with ml_create.  Memory and stream as for ml_create. */
@@ -325,7 +333,8 @@ typedef struct ml_server ml_server;
 /* Allocates the budget (cudaMalloc, current device) and starts the worker. */
 int ml_server_create(const ml_server_config *cfg, ml_server **out);
 /* Queues a request (parameters are copied); *job identifies it.  ML_EINVAL
- * for invalid parameters or a precision / n_or different from the server's.
+ * for invalid parameters, a precision / n_or different from the server's, or
+ * replay (the server folds every record as it comes).
  * A request that cannot fit the budget even alone completes with ML_ENOMEM. */
 int ml_submit(ml_server *s, const ml_params *p, int n_therm, int n_meas, uint64_t *job);
 /* Non-blocking: *done = 1 once the request has finished.  When done and

@@ -107,6 +107,7 @@ int validate(const ml_params* p) {
       (p->metro_hits < 1 || p->metro_hits > kMaxTrials || !(p->metro_width > 0.0) || p->metro_width > kPi))
     return ML_EINVAL;
   if (p->multihit < 0 || p->multihit > 1 || (p->multihit && p->beta > 100.0)) return ML_EINVAL;
+  if (p->replay < 0 || p->replay > 1 || (p->replay && p->outer_slab != 0)) return ML_EINVAL;
   return ML_OK;
 }
 
@@ -171,9 +172,14 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   L->d_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
   L->d_lists = static_cast<int*>(lat_alloc(e, L, (lists.size() + 1) * sizeof(int)));
   L->accT_bytes = static_cast<size_t>(nslab_in) * nR * g.Ns * sizeof(double2);
-  L->accO_bytes = static_cast<size_t>(nslab_in) * nrf * np * nc * 2 * g.Ns * sizeof(double2);
+  // replay keeps no per-site field-insertion sums
+  L->accO_bytes = p->replay ? 0 : static_cast<size_t>(nslab_in) * nrf * np * nc * 2 * g.Ns * sizeof(double2);
   L->accT = static_cast<double2*>(lat_alloc(e, L, L->accT_bytes));
-  L->accO = static_cast<double2*>(lat_alloc(e, L, L->accO_bytes));
+  L->accO = L->accO_bytes ? static_cast<double2*>(lat_alloc(e, L, L->accO_bytes)) : nullptr;
+  if (p->replay) {
+    L->replay_theta = lat_alloc(e, L, 4ull * g.V * tsz);
+    L->replay_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
+  }
   if (nslab_out) {
     L->acc4T_bytes = static_cast<size_t>(nslab_out) * nR * g.Ns * sizeof(double2);
     L->acc4O_bytes = static_cast<size_t>(nslab_out) * nrf * np * nc * 2 * g.Ns * sizeof(double2);
@@ -198,7 +204,8 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   L->partial_naive =
       static_cast<double2*>(lat_alloc(e, L, (static_cast<size_t>(nr) * nw + nvw / 2 + 1) * sizeof(double2)));
   L->scratch_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
-  const bool ok = L->theta && L->d_n && L->d_lists && L->accT && L->accO && L->osum[0] && L->osum[1] &&
+  const bool ok = L->theta && L->d_n && L->d_lists && L->accT && (L->accO || !L->accO_bytes) && L->osum[0] &&
+                  L->osum[1] && (!p->replay || (L->replay_theta && L->replay_n)) &&
                   L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->vac_acc && L->partial &&
                   L->partial_naive && L->scratch_n && (!nslab_out || (L->acc4T && L->acc4O)) &&
                   (!any_mh || (L->mh_rec[0] && L->mh_rec[1]));
@@ -373,7 +380,18 @@ void destroy_graphs(Engine* e) {
 int hand_over(Engine* e, int buf, int nrec, bool defer_O, bool first) {
   ML_CUDA(cudaEventRecord(e->ev_rec[buf], e->stream));
   ML_CUDA(cudaStreamWaitEvent(e->side, e->ev_rec[buf], 0));
-  launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, nrec, e->side, defer_O, first);
+  if (e->pass == 2) {
+    // replay: this buffer's field insertions times the final slab averages
+    // straight into the products' partial sums
+    for (LatState* L : e->lats)
+      launch_replay_W(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, 1.0 / e->n_sub, L->partial,
+                      ProductTail{L->theta_rec[buf], L->osum[buf], nrec, 1, first ? 0 : 1}, e->side);
+    ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
+    return ML_OK;
+  }
+  // the replay's first pass forms the slab averages [T] (and the vacuum) only
+  const bool skip_O = defer_O || e->pass == 1;
+  launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, nrec, e->side, skip_O, first);
   if (!defer_O) ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
   return ML_OK;
 }
@@ -484,7 +502,39 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
     if (st) return st;
     for (LatState* L : e->lats) ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->side));
     int ncfg = 0;
-    if (e->outer_slab == 0) {
+    if (e->replay) {
+      // Replay (one level): pass 1 forms the slab averages from the inner
+      // loop; the configuration and sweep counter are then put back and
+      // pass 2 reruns the same sub-updates (same sweep numbers, so the same
+      // configurations) adding each record's insertions times the other
+      // slabs' averages into the products; both passes end in the same state.
+      for (LatState* L : e->lats) {
+        ML_CUDA(cudaMemcpyAsync(L->replay_theta, L->theta, 4ull * L->g.V * (e->fp64 ? 8 : 4),
+                                cudaMemcpyDeviceToDevice, e->stream));
+        ML_CUDA(cudaMemcpyAsync(L->replay_n, L->d_n, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                e->stream));
+      }
+      e->pass = 1;
+      st = run_inner_loop(e);
+      if (!st) {
+        for (LatState* L : e->lats) {
+          ML_CUDA(cudaMemcpyAsync(L->theta, L->replay_theta, 4ull * L->g.V * (e->fp64 ? 8 : 4),
+                                  cudaMemcpyDeviceToDevice, e->stream));
+          ML_CUDA(cudaMemcpyAsync(L->d_n, L->replay_n, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                                  e->stream));
+        }
+        e->pass = 2;
+        st = run_inner_loop(e);
+      }
+      e->pass = 0;
+      if (st) return st;
+      for (int li = 0; li < nlat; ++li) {
+        LatState* L = e->lats[li];
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, nullptr, 1.0 / e->n_sub, L->partial,
+                        out[li], e->side, ProductTail{}, true);
+      }
+      ncfg = e->n_sub;
+    } else if (e->outer_slab == 0) {
       // the last ring buffer's field insertions are folded by the products
       int tb = 0, tn = 0;
       bool tfirst = false;
@@ -689,9 +739,11 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
     const ml_params& a = ps[0];
     const ml_params& b = ps[i];
     if (a.prec != b.prec || a.n_or != b.n_or || a.slab != b.slab || a.outer_slab != b.outer_slab ||
-        a.n_sub != b.n_sub || a.k_between != b.k_between || (a.outer_slab && a.n_sub_outer != b.n_sub_outer))
+        a.n_sub != b.n_sub || a.k_between != b.k_between || (a.outer_slab && a.n_sub_outer != b.n_sub_outer) ||
+        a.replay != b.replay)
       return ML_EINVAL;
   }
+  e->replay = ps[0].replay != 0;
   e->fp64 = ps[0].prec == ML_FP64;
   e->nB = rec_batch(e->fp64);
   e->n_or = ps[0].n_or;
@@ -741,7 +793,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
     td.max_nc1 = std::max(td.max_nc1, m.nc + 1);
     td.max_blocks_site = std::max(td.max_blocks_site, (d.g.Ns + 255) / 256);
     td.max_y_T = std::max(td.max_y_T, d.nslab * m.nR);
-    if (m.nrf > 0 && m.np > 0 && m.nc > 0)
+    if (m.nrf > 0 && m.np > 0 && m.nc > 0 && !e->replay)  // replay keeps no insertion sums to fold
       td.max_y_O = std::max(td.max_y_O, d.nslab * m.nrf * fold_probe_groups(m.np));
     td.max_vac_blocks = std::max(td.max_vac_blocks, d.nparts);
     td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
@@ -925,8 +977,15 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
   launch_naive_and_plaquette(e->fp64, L->theta, L->g, m, L->partial_naive, out, e->stream);
   ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->stream));
   launch_record_table(e->fp64, e->d_desc, e->td, nullptr, buf, 0, e->stream);
-  launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream, false, true);
-  launch_products(L->g, L->g.Nt / e->slab, m, !e->fp64, L->accT, L->accO, 1.0, L->partial, out, e->stream);
+  if (e->replay) {
+    // no stored insertion sums: the products take the one record as their tail
+    launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream, true, true);
+    launch_products(L->g, L->g.Nt / e->slab, m, !e->fp64, L->accT, nullptr, 1.0, L->partial, out, e->stream,
+                    ProductTail{L->theta_rec[buf], L->osum[buf], 1, 1, 0});
+  } else {
+    launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream, false, true);
+    launch_products(L->g, L->g.Nt / e->slab, m, !e->fp64, L->accT, L->accO, 1.0, L->partial, out, e->stream);
+  }
   launch_write_vac(L->vac_acc, 1.0, m, out, e->stream);
   ML_CUDA(cudaGetLastError());
   ML_CUDA(cudaMemcpyAsync(out_host, out, m.rec_len * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
@@ -1029,12 +1088,16 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
       case ML_K_RECORD:
         launch_record_table(e->fp64, e->d_desc, e->td, nullptr, 0, 0, e->stream);
         break;
-      case ML_K_ACCUMULATE:
+      case ML_K_ACCUMULATE:  // replay: the first pass's fold and the second pass's insertions of one buffer
         launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, 0, e->nB, e->stream);
+        if (e->replay)
+          for (LatState* Lr : e->lats)
+            launch_replay_W(Lr->g, Lr->g.Nt / e->slab, Lr->meas, !e->fp64, Lr->accT, 1.0, Lr->partial,
+                            ProductTail{Lr->theta_rec[0], Lr->osum[0], e->nB, 1, 1}, e->stream);
         break;
       case ML_K_PRODUCTS:
         launch_products(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, L->accO, 1.0, L->partial, e->rec_buf,
-                        e->stream);
+                        e->stream, ProductTail{}, e->replay);
         break;
       case ML_K_SWEEP:
         st = enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, e->sweep_mode);

@@ -39,6 +39,8 @@ struct LatState {
   double2* partial_naive = nullptr;  // naive / plaquette partials (main stream)
   double* staging = nullptr;         // canonical angles for get / set
   void* scratch_theta = nullptr;     // timing copies
+  void* replay_theta = nullptr;      // replay: configuration at the start of the inner loop
+  unsigned long long* replay_n = nullptr;  // and its sweep counter
   unsigned long long* scratch_n = nullptr;
   LatDesc desc{};
   std::vector<void*> blocks;  // this lattice's device allocations
@@ -48,6 +50,8 @@ struct LatState {
 struct Engine {
   bool fp64 = true;
   int n_or = 3, slab = 2, outer_slab = 0, n_sub = 1, n_sub_outer = 0, k_between = 0;
+  bool replay = false;  // field insertions by replay of the inner loop
+  int pass = 0;         // inner loop being run: 0 direct, 1 replay's slab averages, 2 replay's insertions
   std::vector<LatState*> lats;
   cudaStream_t stream = nullptr, side = nullptr;
   bool own_stream = false;

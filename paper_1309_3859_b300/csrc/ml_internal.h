@@ -146,11 +146,18 @@ struct ProductTail {
   const void* osum = nullptr;  // ring buffer osum[buf]
   int nrec = 0;
   int overwrite = 0;  // the stored field-insertion sums are not yet written: start from zero
+  int add = 0;        // add the W partials to the stored ones (later batches of a replay)
 };
 // cross-slab products of the averages sum / n, reduced over x into the
 // record's P, Pf and W blocks (pairs: as for launch_combine)
 void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, const void* accO,
-                     double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail = {});
+                     double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail = {},
+                     bool W_done = false);
+// replay: the W partials of one ring buffer's records (tail.nrec of them)
+// times the final slab averages, stored (tail.add = 0) or added to the stored
+// partials; W_done in the final launch_products then only adds P and finalises
+void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, double inv_n,
+                     double2* partial, const ProductTail& tail, cudaStream_t s);
 // naive P+P and mean plaquette of the current configuration
 void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,
                                 double* rec, cudaStream_t s);

@@ -561,11 +561,12 @@ __global__ void __launch_bounds__(256, TAIL ? 2 : kProdMinBlocks)
     run = M::make(R(1), R(0));  // prod_{s' < s} [T]_{s'}
     for (int s = 0; s < nslab; ++s) {
       const C rest = cmul(run, suf[s]);
-      const A* ocol = accO + (static_cast<size_t>(s * m.nrf + f) * nW + j0) * g.Ns + x;
+      const bool fresh = TAIL && tail.overwrite;  // no stored sums (replay: accO is null)
+      const A* ocol = fresh ? nullptr : accO + (static_cast<size_t>(s * m.nrf + f) * nW + j0) * g.Ns + x;
       A o[kWChunk];
 #pragma unroll
       for (int q = 0; q < kWChunk; ++q)
-        if (q < nj) o[q] = (TAIL && tail.overwrite) ? A{} : ocol[static_cast<size_t>(q) * g.Ns];
+        if (q < nj) o[q] = fresh ? A{} : ocol[static_cast<size_t>(q) * g.Ns];
       if constexpr (TAIL) {
         const T* trec = static_cast<const T*>(tail.trec) + static_cast<size_t>(s) * g.Ns * B;
         const T* osum = static_cast<const T*>(tail.osum);
@@ -598,8 +599,11 @@ __global__ void __launch_bounds__(256, TAIL ? 2 : kProdMinBlocks)
   for (int q = 0; q < kWChunk; ++q) {
     if (q >= nj) break;
     const C w = warp_sum(cscale(sum[q], scale));
-    if ((threadIdx.x & 31) == 0)
-      partial[static_cast<size_t>(m.nr + m.nrf + f * nW + j0 + q) * nwarps + (x >> 5)] = make_double2(w.x, w.y);
+    if ((threadIdx.x & 31) == 0) {
+      double2* p = partial + static_cast<size_t>(m.nr + m.nrf + f * nW + j0 + q) * nwarps + (x >> 5);
+      const double2 v = make_double2(w.x, w.y);
+      *p = (TAIL && tail.add) ? cadd(*p, v) : v;
+    }
   }
 }
 
@@ -831,11 +835,12 @@ void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, bool
 
 template <typename A>
 static void products_of(const Geom& g, int nslab, const MeasLayout& m, const A* accT, const A* accO, double inv_n,
-                        double2* partial, int nb, int nwarps, const ProductTail& tail, cudaStream_t s) {
+                        double2* partial, int nb, int nwarps, const ProductTail& tail, bool W_done,
+                        cudaStream_t s) {
   k_products_P<A><<<dim3(nb, m.nr + m.nrf), 256, 0, s>>>(g, nslab, m, accT, inv_n, partial, nwarps);
   count_launches(1);
   const int nW = m.np * m.nc * 2;
-  if (m.nrf > 0 && nW > 0) {
+  if (m.nrf > 0 && nW > 0 && !W_done) {
     const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
     if (tail.nrec > 0)
       k_products_W<A, true><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
@@ -846,18 +851,36 @@ static void products_of(const Geom& g, int nslab, const MeasLayout& m, const A* 
 }
 
 void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, const void* accO,
-                     double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail) {
+                     double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail,
+                     bool W_done) {
   const int nb = blocks_for(g.Ns, 256);
   const int nwarps = nb * 8;
   if (pairs)
     products_of(g, nslab, m, static_cast<const float4*>(accT), static_cast<const float4*>(accO), inv_n, partial, nb,
-                nwarps, tail, s);
+                nwarps, tail, W_done, s);
   else
     products_of(g, nslab, m, static_cast<const double2*>(accT), static_cast<const double2*>(accO), inv_n, partial,
-                nb, nwarps, tail, s);
+                nb, nwarps, tail, W_done, s);
   const int nW = m.np * m.nc * 2;
   const int nout = m.nr + m.nrf + m.nrf * nW;
   k_finalize_products<<<blocks_for(32ll * nout, 256), 256, 0, s>>>(partial, nwarps, g, m, rec);
+  count_launches(1);
+}
+
+void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, double inv_n,
+                     double2* partial, const ProductTail& tail, cudaStream_t s) {
+  const int nW = m.np * m.nc * 2;
+  if (m.nrf == 0 || nW == 0 || tail.nrec <= 0) return;
+  const int nb = blocks_for(g.Ns, 256);
+  const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
+  ProductTail t = tail;
+  t.overwrite = 1;  // this buffer's records alone
+  if (pairs)
+    k_products_W<float4, true><<<grid, 256, 0, s>>>(g, nslab, m, static_cast<const float4*>(accT), nullptr, inv_n,
+                                                    partial, nb * 8, t);
+  else
+    k_products_W<double2, true><<<grid, 256, 0, s>>>(g, nslab, m, static_cast<const double2*>(accT), nullptr, inv_n,
+                                                     partial, nb * 8, t);
   count_launches(1);
 }
 

@@ -496,7 +496,8 @@ int ml_submit(ml_server* s, const ml_params* p, int n_therm, int n_meas, uint64_
   if (!s || !p || !job || n_therm < 0 || n_meas < 1) return ML_EINVAL;
   int st = validate(p);
   if (st) return st;
-  if ((p->prec == ML_FP64) != s->e.fp64 || p->n_or != s->e.n_or) return ML_EINVAL;
+  // the server's step machine folds every record as it comes: no replay
+  if ((p->prec == ML_FP64) != s->e.fp64 || p->n_or != s->e.n_or || p->replay) return ML_EINVAL;
   Job* j = new (std::nothrow) Job();
   if (!j) return ML_ENOMEM;
   j->p = *p;

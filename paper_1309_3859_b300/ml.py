@@ -47,7 +47,7 @@ class _Params(ctypes.Structure):
         ("nprobe", ctypes.c_int), ("probe", ctypes.POINTER(_Offset)),
         ("comp_mask", ctypes.c_uint32),
         ("update", ctypes.c_int), ("metro_hits", ctypes.c_int), ("metro_width", ctypes.c_double),
-        ("multihit", ctypes.c_int),
+        ("multihit", ctypes.c_int), ("replay", ctypes.c_int),
     ]
 
 
@@ -167,6 +167,7 @@ class Params:
     metro_hits: int = 1
     metro_width: float = 1.0
     multihit: int = 0         # 1: P(r) at 2 <= r <= L-2 from multihit temporal links
+    replay: int = 0           # 1: field insertions by replay of the inner loop (one level)
     _keep: list = field(default_factory=list, repr=False, compare=False)
 
     @property
@@ -185,7 +186,8 @@ class Params:
         return _Params(self.L, self.Nt, float(self.beta), int(self.seed) & (2 ** 64 - 1),
                        ML_FP64 if self.fp64 else ML_FP32, self.n_or, self.slab, self.n_sub, self.outer_slab,
                        self.n_sub_outer, self.k_between, len(self.r), r, len(self.rf), rf, len(self.probes), pr,
-                       self.comp_mask, self.update, self.metro_hits, float(self.metro_width), self.multihit)
+                       self.comp_mask, self.update, self.metro_hits, float(self.metro_width), self.multihit,
+                       self.replay)
 
     @classmethod
     def from_workload(cls, w, **kw) -> "Params":

@@ -11,6 +11,8 @@ Deterministic comparisons (same inputs, same Philox stream):
   same configuration within 1e-5 relative on the plaquette.
 * Whole multilevel runs (one and two levels) in the ordered phase, where
   rounding differences are not amplified by the chain: FP64 within 1e-9.
+* Replay of the field insertions: same chain as the direct scheme bit for bit,
+  records to rounding; whole ordered-phase runs against the oracle.
 * Analytic multihit (Section II.C): the multihit P(r) of one configuration and
   of whole ordered-phase runs against the oracle; on the same chain only the
   multihit entries differ from the plain run's records.
@@ -37,8 +39,9 @@ def wrapd(a):
 def pair(**kw):
     """(oracle params, library params) for the same run."""
     fp64 = kw.pop("fp64", True)
+    replay = kw.pop("replay", 0)  # the same estimator as the oracle's direct sums
     po = oracle.Params(draws=0 if fp64 else 1, **kw)
-    pm = ml.Params(fp64=fp64, **kw)
+    pm = ml.Params(fp64=fp64, replay=replay, **kw)
     return po, pm
 
 
@@ -345,6 +348,68 @@ def test_multihit_changes_only_the_multihit_entries(fp64):
         assert same == (r in (1, 7)), r
 
 
+# ----------------------------------------------------------------------------- replay of the field insertions
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("n_sub", [3, 37])
+def test_replay_matches_the_direct_scheme(fp64, n_sub):
+    """The replay scheme runs the inner loop twice from the same configuration
+    and sweep numbers: the chain ends where the direct scheme's ends (bit for
+    bit) and the records agree to rounding (the same sums in another order)."""
+    base = dict(L=6, Nt=8, beta=1.0, seed=23, fp64=fp64, slab=2, n_sub=n_sub, k_between=2, r=(1, 2, 3),
+                rf=(1, 2, 3), probes=((0, 0), (1, 0), (0, 1), (-1, 2)), comp_mask=0x3F)
+    out = {}
+    for rp in (0, 1):
+        p = ml.Params(replay=rp, **base)
+        with ml.Lattice(p) as lat:
+            lat.thermalize(5)
+            rec = lat.measure(2)
+            out[rp] = (ml.split_record(p, rec), lat.get_angles(), lat.sweep)
+    (a, tha, na), (b, thb, nb) = out[0], out[1]
+    assert na == nb and np.array_equal(tha, thb)
+    for key in ("P", "Pf", "vac", "naive", "plaq"):
+        assert np.array_equal(a[key], b[key]), key
+    scale = np.abs(a["W"]).max()
+    assert np.abs(a["W"] - b["W"]).max() < (1e-13 if fp64 else 2e-6) * scale
+
+
+@pytest.mark.parametrize("fp64,tol", [(True, 1e-12), (False, 2e-5)])
+def test_observe_replay(fp64, tol):
+    _observe_parity(6, 4, fp64, tol, replay=1)
+
+
+def test_multilevel_run_replay_fp64_ordered_phase():
+    kw = dict(slab=2, n_sub=37, k_between=2, r=(1, 2, 3), rf=(1, 2), probes=((0, 0), (1, 0), (2, 1)),
+              comp_mask=0x3F)
+    po = oracle.Params(L=4, Nt=8, beta=2.5, seed=93, draws=0, **kw)
+    pm = ml.Params(L=4, Nt=8, beta=2.5, seed=93, fp64=True, replay=1, **kw)
+    th, c = thermal_config(po, n=8, cold=True)
+    ref_rec, c2 = oracle.measure(po, th.copy(), c, 2)
+    with ml.Lattice(pm) as lat:
+        lat.set_angles(th)
+        lat.sweep = c
+        got = lat.measure(2)
+        assert lat.sweep == c2
+    assert np.abs(got - ref_rec).max() < 1e-9
+
+
+def test_replay_refusals():
+    """Replay is one level only, uniform within a batch, and not served."""
+    base = dict(L=4, Nt=8, beta=1.0, seed=1, slab=2, n_sub=2, r=(1,), rf=(1,), probes=((0, 0),), comp_mask=1)
+    with pytest.raises(ml.MLError) as exc:
+        ml.Lattice(ml.Params(replay=1, outer_slab=4, n_sub_outer=2, **base))
+    assert exc.value.status == ml.ML_EINVAL
+    with pytest.raises(ml.MLError) as exc:
+        ml.Batch([ml.Params(replay=1, **base), ml.Params(replay=0, **base)])
+    assert exc.value.status == ml.ML_EINVAL
+    with ml.Batch([ml.Params(replay=1, **base), ml.Params(replay=1, **dict(base, seed=2))]) as b:
+        b.thermalize(1)
+        assert np.all(np.isfinite(b.measure(1)))
+    with ml.Server(budget_bytes=64 << 20, fp64=True) as srv:
+        with pytest.raises(ml.MLError) as exc:
+            srv.submit(ml.Params(replay=1, **base), 1, 1)
+        assert exc.value.status == ml.ML_EINVAL
+
+
 # ----------------------------------------------------------------------------- whole runs, ordered phase
 @pytest.mark.parametrize("two_level,n_sub", [(False, 3), (True, 3), (False, 37), (True, 18)])
 def test_multilevel_run_fp64_ordered_phase(two_level, n_sub):
@@ -433,7 +498,8 @@ def test_full_size_observe_fp32_single_24(multihit):
 
 @pytest.mark.parametrize("fp64", [True, False])
 @pytest.mark.parametrize("geom", [dict(L=8, Nt=4, n_sub=3), dict(L=6, Nt=8, n_sub=18, outer_slab=4, n_sub_outer=2),
-                                  dict(L=8, Nt=4, n_sub=3, **METRO), dict(L=6, Nt=4, n_sub=18, multihit=1)])
+                                  dict(L=8, Nt=4, n_sub=3, **METRO), dict(L=6, Nt=4, n_sub=18, multihit=1),
+                                  dict(L=6, Nt=4, n_sub=18, replay=1)])
 def test_sweep_implementations_agree(fp64, geom):
     """The persistent kernel, the per-pass kernels and the cluster-resident
     kernels run the same link updates with the same random numbers: identical
