@@ -345,6 +345,32 @@ def multihit_point(ml, w, n_meas=40):
     return out
 
 
+def replay_point(ml, w, steps=3):
+    """The step's workload with the field insertions by replay: the inner
+    loop runs twice, and no per-site insertion sums are kept."""
+    import torch
+
+    p = ml.Params.from_workload(w, seed=w.seed + 11, replay=1)
+    with ml.Lattice(p) as lat:
+        lat.thermalize(w.n_therm)
+        rec = torch.empty((1, lat.rec_len), dtype=torch.float64, device=lat.device)
+        lat.measure_device(1, rec)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(lat.stream)
+        for _ in range(steps):
+            lat.measure_device(1, rec)
+        e1.record(lat.stream)
+        lat.sync()
+        ms = e0.elapsed_time(e1) / steps
+    nslab = w.Nt // w.slab
+    direct_bytes = nslab * len(w.rf) * len(w.probes) * bin(w.comp_mask).count("1") * 2 * w.L ** 3 * 16
+    upd = link_updates_per_step(w)
+    return {"workload": w.name + "-replay", "ms_per_step": ms, "link_updates_per_s": upd / (ms * 1e-3),
+            "insertion_sums_bytes_direct": direct_bytes, "insertion_sums_bytes_replay": 0,
+            "note": "link updates of the chain; the replay executes the inner loop's updates twice"}
+
+
 def run_gpu(args, w, rank, world):
     import torch
 
@@ -439,6 +465,7 @@ def run_gpu(args, w, rank, world):
     hbm_point = hbm_sweep_point(ml, peak) if rank == 0 and not args.no_extra else None
     batch_point = batched_point(ml) if rank == 0 and not args.no_extra else None
     mh_point = multihit_point(ml, w) if rank == 0 and not args.no_extra else None
+    rp_point = replay_point(ml, w) if rank == 0 and not args.no_extra and not w.outer_slab else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -479,6 +506,7 @@ def run_gpu(args, w, rank, world):
         "sweep_hbm_point": hbm_point,
         "batched": batch_point,
         "multihit": mh_point,
+        "replay": rp_point,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
         "gpu_launches": int(launches),
