@@ -68,7 +68,8 @@ typedef enum {
                               (u1, u2) are those of heatbath trial h of the same stream */
 } ml_update;
 
-/* Run parameters.  Validation (ML_EINVAL): L and Nt even and >= 2; slab >= 1
+/* Run parameters.  Validation (ML_EINVAL): L and Nt even and >= 2, L^3 Nt <=
+ * 2^30, Nt <= 2^20; slab >= 1
  * dividing Nt; n_sub >= 1; outer_slab = 0, or a multiple of slab that divides
  * Nt and differs from slab, with n_sub_outer >= 1; 1 <= r, rf <= L-1;
  * |dy|, |dz| <= L-1; beta >= 0; k_between >= 0; n_or >= 0; comp_mask < 64;

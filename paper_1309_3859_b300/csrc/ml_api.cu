@@ -83,7 +83,7 @@ void free_lattice(Engine* e, LatState* L) {
 int validate(const ml_params* p) {
   if (!p) return ML_EINVAL;
   if (p->L < 2 || p->Nt < 2 || (p->L & 1) || (p->Nt & 1)) return ML_EINVAL;
-  if (static_cast<long long>(p->L) * p->L * p->L * p->Nt > (1ll << 30)) return ML_EINVAL;
+  if (static_cast<long long>(p->L) * p->L * p->L * p->Nt > (1ll << 30) || p->Nt > (1 << 20)) return ML_EINVAL;
   if (!(p->beta >= 0.0) || p->n_or < 0 || p->k_between < 0) return ML_EINVAL;
   if (p->prec != ML_FP64 && p->prec != ML_FP32) return ML_EINVAL;
   if (p->slab < 1 || p->Nt % p->slab != 0 || p->n_sub < 1) return ML_EINVAL;
@@ -121,11 +121,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   LatState* L = new (std::nothrow) LatState();
   if (!L) return ML_ENOMEM;
   *out = L;  // the caller owns L (and its buffers) from here on, also on failure
-  L->g.L = p->L;
-  L->g.Nt = p->Nt;
-  L->g.Ns = p->L * p->L * p->L;
-  L->g.V = L->g.Ns * p->Nt;
-  L->g.Vh = L->g.V / 2;
+  L->g = make_geom(p->L, p->Nt);
   L->beta = p->beta;
   L->seed = p->seed;
   L->r.assign(p->r, p->r + p->nr);

@@ -71,7 +71,42 @@ struct Geom {
   int Ns;  // L^3
   int V;   // Ns * Nt
   int Vh;  // V / 2
+  unsigned long long m_L, m_hx;  // division magics of L and L / 2 (div_magic)
 };
+
+// Division by an invariant d >= 1 as a 64-bit multiply-high: for 0 <= x <
+// 2^32, floor(x M / 2^64) = floor(x / d) with M = floor((2^64 - 1) / d) + 1,
+// since x M / 2^64 = x / d + x e / 2^64 with 0 <= e <= 1 and x e / 2^64 <
+// 1 / d.  d = 1 is M = 0 (quotient x).
+__host__ __device__ __forceinline__ unsigned long long div_magic(int d) {
+  return d <= 1 ? 0ull : ~0ull / static_cast<unsigned long long>(d) + 1ull;
+}
+__device__ __forceinline__ int udiv(int x, unsigned long long m) {
+  return m ? static_cast<int>(__umul64hi(static_cast<unsigned long long>(x), m)) : x;
+}
+
+// t mod d for 0 <= t < 2^22, 1 <= d: a float quotient within one of the
+// true one, corrected by one compare each way.
+__device__ __forceinline__ int small_mod(int t, int d) {
+  const int q = static_cast<int>(static_cast<float>(t) * __frcp_rn(static_cast<float>(d)));
+  int r = t - q * d;
+  r += r < 0 ? d : 0;
+  r -= r >= d ? d : 0;
+  return r;
+}
+
+// Geometry of an L^3 x Nt lattice.
+__host__ __device__ inline Geom make_geom(int L, int Nt) {
+  Geom g{};
+  g.L = L;
+  g.Nt = Nt;
+  g.Ns = L * L * L;
+  g.V = g.Ns * Nt;
+  g.Vh = g.V / 2;
+  g.m_L = div_magic(L);
+  g.m_hx = div_magic(L / 2);
+  return g;
+}
 
 __host__ __device__ __forceinline__ int wrapc(int v, int n) {
   v %= n;
@@ -86,15 +121,15 @@ __device__ __forceinline__ size_t soa(const Geom& g, int mu, int i, int parity) 
   return static_cast<size_t>(mu * 2 + parity) * g.Vh + static_cast<size_t>(i >> 1);
 }
 
-// coordinates (t, x, y, z) of the site with half index h and parity p
+// coordinates (t, x, y, z) of the site with half index h and parity p: h =
+// x / 2 + (L / 2)(y + L (z + L t)) (site 2h has an even x coordinate)
 __device__ __forceinline__ void half_site_coords(const Geom& g, int h, int p, int c[4]) {
-  const int i0 = 2 * h;  // even, so its x coordinate is even
-  int rest = i0 / g.L;
-  int x = i0 - rest * g.L;
-  const int y = rest % g.L;
-  rest /= g.L;
-  const int z = rest % g.L;
-  const int t = rest / g.L;
+  const int row = udiv(h, g.m_hx);  // y + L (z + L t)
+  int x = 2 * (h - row * (g.L >> 1));
+  const int zt = udiv(row, g.m_L);
+  const int y = row - zt * g.L;
+  const int t = udiv(zt, g.m_L);
+  const int z = zt - t * g.L;
   if (((y + z + t) & 1) != p) x += 1;
   c[0] = t;
   c[1] = x;

@@ -179,7 +179,7 @@ __device__ __forceinline__ T metropolis(T theta, T k, T alpha, T beta, T w, int 
 // when the link keeps its angle (k = 0 in overrelaxation, or the heatbath
 // trial cap, which also sets kErrReject).
 template <typename T, typename Staples>
-__device__ __forceinline__ void staple_sum(int mu, Staples&& staples, T* k, T* alpha) {
+__device__ __forceinline__ void staple_w(int mu, Staples&& staples, T* wr_out, T* wi_out) {
   using P = Prec<T>;
   T wr = T(0), wi = T(0);
 #pragma unroll
@@ -195,6 +195,14 @@ __device__ __forceinline__ void staple_sum(int mu, Staples&& staples, T* k, T* a
     wr += ca + cb;
     wi += sa + sb;
   }
+  *wr_out = wr;
+  *wi_out = wi;
+}
+template <typename T, typename Staples>
+__device__ __forceinline__ void staple_sum(int mu, Staples&& staples, T* k, T* alpha) {
+  using P = Prec<T>;
+  T wr, wi;
+  staple_w<T>(mu, staples, &wr, &wi);
   *k = P::sqrt_(wr * wr + wi * wi);
   *alpha = P::atan2_(wi, wr);
 }
@@ -204,6 +212,14 @@ __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&&
                                                unsigned long long n, uint32_t k0, uint32_t k1, T beta,
                                                int* __restrict__ err, T* out, T w = T(0), int hits = 0) {
   using P = Prec<T>;
+  if (KIND == 1) {
+    // overrelaxation needs only alpha; k = 0 exactly when wr^2 + wi^2 = 0
+    T wr, wi;
+    staple_w<T>(mu, staples, &wr, &wi);
+    if (wr * wr + wi * wi == T(0)) return false;
+    *out = P::wrap(T(-2) * P::atan2_(wi, wr) - self());
+    return true;
+  }
   T k, alpha;
   staple_sum<T>(mu, staples, &k, &alpha);
   if (KIND == 0) {
@@ -213,11 +229,8 @@ __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&&
       return false;
     }
     *out = P::wrap(psi - alpha);
-  } else if (KIND == 2) {
-    *out = metropolis<T>(self(), k, alpha, beta, w, hits, site, mu, n, k0, k1);
   } else {
-    if (k == T(0)) return false;
-    *out = P::wrap(T(-2) * alpha - self());
+    *out = metropolis<T>(self(), k, alpha, beta, w, hits, site, mu, n, k0, k1);
   }
   return true;
 }

@@ -672,13 +672,10 @@ __global__ void __launch_bounds__(256) k_plaq_mean(const T* __restrict__ th, Geo
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double v = 0.0;
   if (i < g.V) {
-    int rest = i / g.L;
     int c[4];
-    c[1] = i - rest * g.L;
-    c[2] = rest % g.L;
-    rest /= g.L;
-    c[3] = rest % g.L;
-    c[0] = rest / g.L;
+    spatial_coords(g, i, &c[1], &c[2], &c[3]);  // z comes out as z + L t
+    c[0] = udiv(c[3], g.m_L);
+    c[3] -= c[0] * g.L;
     for (int mu = 0; mu < 4; ++mu)
       for (int nu = mu + 1; nu < 4; ++nu) v += cos(static_cast<double>(plaquette_angle(th, g, c, mu, nu)));
   }

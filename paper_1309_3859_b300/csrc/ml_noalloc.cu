@@ -146,12 +146,7 @@ extern "C" int ml_naive_noalloc(const void* theta_dev, int L, int Nt, int prec, 
     if (r[a] < 1 || r[a] >= L) return ML_EINVAL;
     rl.r[a] = r[a];
   }
-  Geom g{};
-  g.L = L;
-  g.Nt = Nt;
-  g.Ns = L * L * L;
-  g.V = g.Ns * Nt;
-  g.Vh = g.V / 2;
+  const Geom g = make_geom(L, Nt);
   const int nbx = blocks_for(g.Ns, 256), nbv = blocks_for(g.V, 256);
   const int nwarps = nbx * 8, npw = nbv * 8;
   const long long need = 2ll * nr * nwarps + npw;  // doubles of scratch this call uses

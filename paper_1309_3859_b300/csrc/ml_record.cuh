@@ -24,10 +24,10 @@ __device__ __forceinline__ void plane_of(int c, int* mu, int* nu) {
 
 // spatial coordinates of spatial site x
 __device__ __forceinline__ void spatial_coords(const Geom& g, int x, int* cx, int* cy, int* cz) {
-  int rest = x / g.L;
+  const int rest = udiv(x, g.m_L);
   *cx = x - rest * g.L;
-  *cy = rest % g.L;
-  *cz = rest / g.L;
+  *cz = udiv(rest, g.m_L);
+  *cy = rest - *cz * g.L;
 }
 
 // theta_0 at spatial site (cx, cy, cz) and time t

@@ -27,6 +27,7 @@
 // implementation (new_link_angle), so configurations and records are
 // bit-identical to theirs.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "ml_link.cuh"
@@ -163,10 +164,13 @@ __device__ __forceinline__ void box_staples(const Box& b, const T* buf, int mu, 
 
 // Update of the link U_mu at box cell bi, local time tl; the new angle also
 // goes to the mirrors mirror[m0 .. m1) of the cell (cluster addresses of slot 0).
-template <typename T, int KIND>
-__device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* mirror, int m0, int m1, int mu,
-                                         int tl, int bi, uint32_t site, unsigned long long n, uint32_t k0,
-                                         uint32_t k1, T beta, int* err, const UpdateRule& rule) {
+// The direction is a template parameter, so the staple offsets and slots of
+// every plane resolve at compile time.
+template <typename T, int KIND, int MU>
+__device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* mirror, int m0, int m1, int tl,
+                                         int bi, uint32_t site, unsigned long long n, uint32_t k0, uint32_t k1,
+                                         T beta, int* err, const UpdateRule& rule) {
+  constexpr int mu = MU;
   auto staples = [&](int nu, T w[6]) { box_staples<T>(b, buf, mu, tl, bi, nu, w); };
   const int sl = b.slot(mu, tl);
   T* self = buf + sl * b.vol + bi;
@@ -320,32 +324,40 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const int half = hx * b.ylen * b.zlen;
   const unsigned long long m_half = fdiv_magic(max(half, 1)), m_hx = fdiv_magic(hx),
                            m_own = fdiv_magic(max(own, 1));
+  // one (mu, parity) pass of this CTA's links, mu a compile-time constant
+  auto pass = [&](auto mu_c, int sweep, int par, unsigned long long n) {
+    constexpr int mu = decltype(mu_c)::value;
+    constexpr int tl_lo = mu == 0 ? 0 : 1;  // spatial links at tl = 0 are frozen
+    const int items = (d - tl_lo) * half;
+    for (int k = threadIdx.x; k < items; k += blockDim.x) {
+      const int q = fdiv(k, m_half);
+      const int tl = tl_lo + q, t = t0 + tl;
+      const int j = k - q * half;
+      const int row = fdiv(j, m_hx);
+      const int cx0 = 2 * (j - row * hx);  // even
+      const int rz = fdiv(row, m_yl), ry = row - rz * b.ylen;
+      const int cy = b.y0 + ry, cz = b.z0 + rz;
+      const int cx = cx0 + (((cy + cz + t) & 1) ^ par);
+      const int bi = b.cell(cx + 1, ry + 1, rz + 1);
+      const int jo = cx + g.L * row;  // owned-site index
+      const uint32_t site = static_cast<uint32_t>(cx + g.L * (cy + g.L * cz) + g.Ns * t);
+      if (sweep == 0)
+        box_link<T, 0, mu>(b, buf, mirror, mstart[jo], mstart[jo + 1], tl, bi, site, n, k0, k1, beta, err, rule);
+      else
+        box_link<T, 1, mu>(b, buf, mirror, mstart[jo], mstart[jo + 1], tl, bi, site, n, k0, k1, beta, err, rule);
+    }
+  };
   for (int round = 0; round < n_rec; ++round) {
     for (int c = 0; c < n_compound; ++c) {
       const unsigned long long n = nbase + 1 + static_cast<unsigned long long>(round) * n_compound + c;
       for (int sweep = 0; sweep <= n_or; ++sweep)
         for (int mu = 0; mu < 4; ++mu)
           for (int par = 0; par < 2; ++par) {
-            const int tl_lo = mu == 0 ? 0 : 1;  // spatial links at tl = 0 are frozen
-            const int items = (d - tl_lo) * half;
-            for (int k = threadIdx.x; k < items; k += blockDim.x) {
-              const int q = fdiv(k, m_half);
-              const int tl = tl_lo + q, t = t0 + tl;
-              const int j = k - q * half;
-              const int row = fdiv(j, m_hx);
-              const int cx0 = 2 * (j - row * hx);  // even
-              const int rz = fdiv(row, m_yl), ry = row - rz * b.ylen;
-              const int cy = b.y0 + ry, cz = b.z0 + rz;
-              const int cx = cx0 + (((cy + cz + t) & 1) ^ par);
-              const int bi = b.cell(cx + 1, ry + 1, rz + 1);
-              const int jo = cx + g.L * row;  // owned-site index
-              const uint32_t site = static_cast<uint32_t>(cx + g.L * (cy + g.L * cz) + g.Ns * t);
-              if (sweep == 0)
-                box_link<T, 0>(b, buf, mirror, mstart[jo], mstart[jo + 1], mu, tl, bi, site, n, k0, k1, beta, err,
-                               rule);
-              else
-                box_link<T, 1>(b, buf, mirror, mstart[jo], mstart[jo + 1], mu, tl, bi, site, n, k0, k1, beta, err,
-                               rule);
+            switch (mu) {
+              case 0: pass(std::integral_constant<int, 0>{}, sweep, par, n); break;
+              case 1: pass(std::integral_constant<int, 1>{}, sweep, par, n); break;
+              case 2: pass(std::integral_constant<int, 2>{}, sweep, par, n); break;
+              default: pass(std::integral_constant<int, 3>{}, sweep, par, n); break;
             }
             // the pass's links and their mirrors are in place for every CTA
             cluster_sync();

@@ -33,13 +33,17 @@ __device__ __forceinline__ int step_index(const Geom& g, int i, const int c[4], 
 // `th` carries no __restrict__: inside the persistent sweep kernel other blocks
 // rewrite the angles between passes, so every load must be a plain coherent
 // global load (never the read-only path).
-template <typename T, int KIND>
-__device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int parity, int slab_d, int h,
-                                            unsigned long long n, uint32_t k0, uint32_t k1, T beta,
-                                            int* __restrict__ err, const UpdateRule& rule) {
+// The direction is a template parameter so that the loop over the planes
+// (mu, nu) unrolls with constant nu: coordinate and neighbour selects
+// resolve at compile time; update_link dispatches on the runtime direction.
+template <typename T, int KIND, int MU>
+__device__ __forceinline__ void update_link_mu(T* th, const Geom& g, int parity, int slab_d, int h,
+                                               unsigned long long n, uint32_t k0, uint32_t k1, T beta,
+                                               int* __restrict__ err, const UpdateRule& rule) {
+  constexpr int mu = MU;
   int c[4];
   half_site_coords(g, h, parity, c);
-  if (slab_d > 0 && mu != 0 && (c[0] % slab_d) == 0) return;  // frozen boundary link
+  if (slab_d > 0 && mu != 0 && small_mod(c[0], slab_d) == 0) return;  // frozen boundary link
   const int i = site_index(g, c[0], c[1], c[2], c[3]);
   const int op = parity ^ 1;
   const int ipmu = step_index(g, i, c, mu, +1);
@@ -70,6 +74,26 @@ __device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int pa
   }
 }
 
+template <typename T, int KIND>
+__device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int parity, int slab_d, int h,
+                                            unsigned long long n, uint32_t k0, uint32_t k1, T beta,
+                                            int* __restrict__ err, const UpdateRule& rule) {
+  switch (mu) {
+    case 0:
+      update_link_mu<T, KIND, 0>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
+      break;
+    case 1:
+      update_link_mu<T, KIND, 1>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
+      break;
+    case 2:
+      update_link_mu<T, KIND, 2>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
+      break;
+    default:
+      update_link_mu<T, KIND, 3>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
+      break;
+  }
+}
+
 // One (mu, parity) pass, one thread per link.  The links of one pass share no
 // plaquette, so all of them update independently and in place.
 template <typename T, int KIND>
@@ -90,7 +114,7 @@ __global__ void __launch_bounds__(128) k_update_pass(T* __restrict__ th, Geom g,
 // advances the counters after the last barrier, when every block has read
 // them.
 template <typename T>
-__global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* __restrict__ d,
+__global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc* __restrict__ d,
                                                                 const int* __restrict__ tile_lat, int total_tiles,
                                                                 int nlat, const LatCtl* __restrict__ ctl, int mask,
                                                                 int n_or, int n_compound, int* __restrict__ err,
@@ -177,7 +201,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweeps_table(const LatDesc* _
 // One (mu, parity) pass of every lattice of a table, one tile per block; the
 // heatbath sweep number is *n_dev (advanced by k_sweep_begin_table).
 template <typename T, int KIND>
-__global__ void __launch_bounds__(kSweepThreads) k_pass_table(const LatDesc* __restrict__ d,
+__global__ void __launch_bounds__(kSweepThreads, 4) k_pass_table(const LatDesc* __restrict__ d,
                                                               const int* __restrict__ tile_lat,
                                                               const LatCtl* __restrict__ ctl, int mask, int mu,
                                                               int parity, int* __restrict__ err) {
