@@ -292,8 +292,19 @@ int enqueue_sweeps_mode(Engine* e, const LatDesc* table, int n, int mask, int mo
                  : ML_OK;
     mode = e->full_mode;
   }
+  // a table of one lattice: its per-pass kernels take the descriptor's
+  // values as launch parameters (host copy of the same table entry)
+  LatDesc single{};
+  const bool one = e->lats.size() == 1;
+  if (one) {
+    single = e->lats[0]->desc;
+    if (table == e->d_desc_scratch) {
+      single.theta = e->lats[0]->scratch_theta;
+      single.n_dev = e->lats[0]->scratch_n;
+    }
+  }
   return launch_sweeps_table(e->fp64, mode == ML_SWEEP_PERSISTENT, table, e->d_tile_lat, e->td, nullptr, mask,
-                             e->n_or, n, e->d_err, e->bar, e->stream, record, buf, slot)
+                             e->n_or, n, e->d_err, e->bar, e->stream, record, buf, slot, one ? &single : nullptr)
              ? ML_ECUDA
              : ML_OK;
 }
@@ -1063,11 +1074,31 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   // do: time the launch and report per sub-update
   const ResidentPlan* res =
       kernel == ML_K_SUBUPDATE && e->sweep_mode == ML_SWEEP_RESIDENT ? resident_plan(e, e->slab) : nullptr;
+  // sweeps in the per-pass implementation run as CUDA graphs in the
+  // measurement schedule: time them the same way (direct launches of 33
+  // kernels would time the host's launch rate instead)
+  Graph tg;
+  const bool graph =
+      !res && ((kernel == ML_K_SWEEP && e->sweep_mode == ML_SWEEP_PASSES) ||
+               (kernel == ML_K_FULLSWEEP && e->full_mode == ML_SWEEP_PASSES) ||
+               (kernel == ML_K_SUBUPDATE && e->sweep_mode == ML_SWEEP_PASSES));
+  if (graph) {
+    st = capture(e, &tg, [&] {
+      if (kernel == ML_K_SWEEP) return enqueue_sweeps_table(e, e->d_desc_scratch, 1, e->slab, ML_SWEEP_PASSES);
+      if (kernel == ML_K_FULLSWEEP) return enqueue_sweeps_table(e, e->d_desc_scratch, 1, 0, ML_SWEEP_PASSES);
+      return enqueue_sweeps_mode(e, e->d_desc_scratch, 1, e->slab, ML_SWEEP_PASSES, true, 0, 0);
+    });
+    if (st) return st;
+  }
   cudaEvent_t e0, e1;
   ML_CUDA(cudaEventCreate(&e0));
   ML_CUDA(cudaEventCreate(&e1));
   ML_CUDA(cudaEventRecord(e0, e->stream));
   for (int i = 0; i < reps && !st; ++i) {
+    if (graph) {
+      st = launch_graph(e, tg);
+      continue;
+    }
     if (res) {
       st = launch_sweeps_resident(e->fp64, *res, e->d_desc_scratch, e->td.nlat, e->n_or, 1, e->d_err, e->stream, true,
                                   0, 0, e->nB)
@@ -1111,6 +1142,7 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (tg.exec) cudaGraphExecDestroy(tg.exec);
   *avg_ms = static_cast<double>(ms) / reps / (res ? e->nB : 1);
   if (st) return st;
   return check_errors(e);

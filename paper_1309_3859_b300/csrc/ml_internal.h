@@ -98,9 +98,12 @@ constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep k
 // With `record`, the new configurations are then recorded into ring slot
 // (rec_buf, rec_slot) (or per lattice from ctl), exactly as
 // launch_record_table does.
+// `single`: the host copy of the table's only entry (table of one lattice,
+// no ctl), whose per-pass kernels then take its values as launch parameters.
 int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int* tile_lat, const TableDims& td,
                         const LatCtl* ctl, int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
-                        cudaStream_t s, bool record = false, int rec_buf = 0, int rec_slot = 0);
+                        cudaStream_t s, bool record = false, int rec_buf = 0, int rec_slot = 0,
+                        const LatDesc* single = nullptr);
 // record of each lattice's configuration into ring slot (buf, slot), with
 // the multihit record of the multihit lattices
 void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,

@@ -96,8 +96,10 @@ __device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int pa
 
 // One (mu, parity) pass, one thread per link.  The links of one pass share no
 // plaquette, so all of them update independently and in place.
+constexpr int kUpdateThreads = 128;  // block of the single-lattice pass kernel
+
 template <typename T, int KIND>
-__global__ void __launch_bounds__(128) k_update_pass(T* __restrict__ th, Geom g, int mu, int parity, int slab_d,
+__global__ void __launch_bounds__(kUpdateThreads) k_update_pass(T* __restrict__ th, Geom g, int mu, int parity, int slab_d,
                                                       const unsigned long long* __restrict__ n_dev,
                                                       unsigned long long n_fixed, uint32_t k0, uint32_t k1, T beta,
                                                       int* __restrict__ err, UpdateRule rule) {
@@ -162,14 +164,15 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
               const int i = tile_lat[t];
               const LatDesc& L = d[i];
               const int h = (t - L.tile_start) * kSweepTile + threadIdx.x;
-              if (h >= L.g.Vh) continue;
+              const Geom g = L.g;  // registers, not loads from the table
+              if (h >= g.Vh) continue;
               const int md = ctl ? ctl[i].mask : mask;
               const unsigned long long n = *L.n_dev + 1 + c;
               if (sweep == 0)
-                update_link<T, 0>(static_cast<T*>(L.theta), L.g, mu, par, md, h, n, L.k0, L.k1,
+                update_link<T, 0>(static_cast<T*>(L.theta), g, mu, par, md, h, n, L.k0, L.k1,
                                   static_cast<T>(L.beta), err, update_rule(L));
               else
-                update_link<T, 1>(static_cast<T*>(L.theta), L.g, mu, par, md, h, n, L.k0, L.k1,
+                update_link<T, 1>(static_cast<T*>(L.theta), g, mu, par, md, h, n, L.k0, L.k1,
                                   static_cast<T>(L.beta), err, update_rule(L));
             }
           }
@@ -208,10 +211,16 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_pass_table(const LatDesc* 
   const int i = tile_lat[blockIdx.x];
   const LatDesc& L = d[i];
   const int h = (blockIdx.x - L.tile_start) * kSweepTile + threadIdx.x;
-  if (h >= L.g.Vh) return;
+  // the descriptor's fields in registers: by reference every geometry use
+  // would be a load from the table in global memory
+  const Geom g = L.g;
+  if (h >= g.Vh) return;
   const int md = ctl ? ctl[i].mask : mask;
-  update_link<T, KIND>(static_cast<T*>(L.theta), L.g, mu, parity, md, h, *L.n_dev, L.k0, L.k1,
-                       static_cast<T>(L.beta), err, update_rule(L));
+  T* const th = static_cast<T*>(L.theta);
+  const unsigned long long n = *L.n_dev;
+  const uint32_t k0 = L.k0, k1 = L.k1;
+  const T beta = static_cast<T>(L.beta);
+  update_link<T, KIND>(th, g, mu, parity, md, h, n, k0, k1, beta, err, update_rule(L));
 }
 
 __global__ void k_sweep_begin_table(const LatDesc* __restrict__ d, int nlat) {
@@ -278,7 +287,7 @@ static inline int blocks_for(long long n, int t) { return static_cast<int>((n + 
 void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parity, int slab_d, int kind,
                         const unsigned long long* n_dev, unsigned long long n_fixed, uint64_t seed, double beta,
                         int* err, cudaStream_t s, const UpdateRule& rule) {
-  const int nt = 128, nb = blocks_for(g.Vh, nt);
+  const int nt = kUpdateThreads, nb = blocks_for(g.Vh, nt);
   const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
   // kind 2: the update sweep with the Metropolis rule
   const UpdateRule r{kind == 2 ? 1 : 0, rule.hits, rule.width};
@@ -345,17 +354,33 @@ static cudaError_t launch_sweeps_table_t(const LatDesc* d, const int* tile_lat, 
 
 template <typename T>
 static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const TableDims& td, const LatCtl* ctl,
-                                  int mask, int n_or, int n_compound, int* err, cudaStream_t s) {
+                                  int mask, int n_or, int n_compound, int* err, cudaStream_t s,
+                                  const LatDesc* single) {
   for (int c = 0; c < n_compound; ++c) {
     k_sweep_begin_table<<<1, 128, 0, s>>>(d, td.nlat);
     count_launches(1);
     for (int sweep = 0; sweep <= n_or; ++sweep)
       for (int mu = 0; mu < 4; ++mu)
         for (int par = 0; par < 2; ++par) {
-          if (sweep == 0)
+          if (single && !ctl) {
+            // one lattice: geometry, key and coupling as launch parameters
+            // (constant bank) rather than loads from the table
+            const int nb = blocks_for(single->g.Vh, kUpdateThreads);
+            T* th = static_cast<T*>(single->theta);
+            const T beta = static_cast<T>(single->beta);
+            if (sweep == 0)
+              k_update_pass<T, 0><<<nb, kUpdateThreads, 0, s>>>(th, single->g, mu, par, mask, single->n_dev, 0,
+                                                                single->k0, single->k1, beta, err,
+                                                                update_rule(*single));
+            else
+              k_update_pass<T, 1><<<nb, kUpdateThreads, 0, s>>>(th, single->g, mu, par, mask, single->n_dev, 0,
+                                                                single->k0, single->k1, beta, err,
+                                                                update_rule(*single));
+          } else if (sweep == 0) {
             k_pass_table<T, 0><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
-          else
+          } else {
             k_pass_table<T, 1><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
+          }
           count_launches(1);
         }
   }
@@ -363,7 +388,7 @@ static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const T
 
 int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int* tile_lat, const TableDims& td,
                         const LatCtl* ctl, int mask, int n_or, int n_compound, int* err, unsigned long long* bar,
-                        cudaStream_t s, bool record, int rec_buf, int rec_slot) {
+                        cudaStream_t s, bool record, int rec_buf, int rec_slot, const LatDesc* single) {
   if (n_compound <= 0 || td.total_tiles <= 0) return 0;
   cudaError_t e = cudaSuccess;
   if (persistent) {
@@ -376,9 +401,9 @@ int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int*
     if (record) launch_mh_record_table(fp64, d, td, ctl, rec_buf, rec_slot, s);
   } else {
     if (fp64)
-      launch_passes_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s);
+      launch_passes_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s, single);
     else
-      launch_passes_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s);
+      launch_passes_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s, single);
     if (record) launch_record_table(fp64, d, td, ctl, rec_buf, rec_slot, s);
     e = cudaGetLastError();
   }
