@@ -345,6 +345,31 @@ def multihit_point(ml, w, n_meas=40):
     return out
 
 
+def fp64_point(ml, w, steps=3):
+    """The same workload on the FP64 GPU path (FP64 angles, update arithmetic
+    and slab sums): measurements/s of the single-lattice FP64 path against
+    which the FP32 path is compared."""
+    import torch
+
+    p = ml.Params.from_workload(w, fp64=True)
+    with ml.Lattice(p) as lat:
+        lat.thermalize(w.n_therm)
+        rec = torch.empty((1, lat.rec_len), dtype=torch.float64, device=lat.device)
+        lat.measure_device(1, rec)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(lat.stream)
+        for _ in range(steps):
+            lat.measure_device(1, rec)
+        e1.record(lat.stream)
+        lat.sync()
+        ms = e0.elapsed_time(e1) / steps
+        mode = ["persistent", "per-pass", "resident"][lat.sweep_mode]
+    return {"workload": w.name.replace("fp32", "fp64"), "ms_per_step": ms,
+            "measurements_per_s": 1e3 / ms, "link_updates_per_s": link_updates_per_step(w) / (ms * 1e-3),
+            "sweep_impl": mode}
+
+
 def replay_point(ml, w, steps=3):
     """The step's workload with the field insertions by replay: the inner
     loop runs twice, and no per-site insertion sums are kept."""
@@ -466,6 +491,7 @@ def run_gpu(args, w, rank, world):
     batch_point = batched_point(ml) if rank == 0 and not args.no_extra else None
     mh_point = multihit_point(ml, w) if rank == 0 and not args.no_extra else None
     rp_point = replay_point(ml, w) if rank == 0 and not args.no_extra and not w.outer_slab else None
+    f64_point = fp64_point(ml, w) if rank == 0 and not args.no_extra and not w.fp64 else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -507,6 +533,8 @@ def run_gpu(args, w, rank, world):
         "batched": batch_point,
         "multihit": mh_point,
         "replay": rp_point,
+        "fp64_path": f64_point,
+        "vs_fp64_path": (f64_point["ms_per_step"] / (ms / args.steps)) if f64_point else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
         "gpu_launches": int(launches),
