@@ -94,9 +94,132 @@ __device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int pa
   }
 }
 
+// Two links per thread: half indices h0 = 2 hp and h0 + 1 of one parity, for
+// L a multiple of 4.  They lie in one x row two sites apart (x1 = x0 + 2 <=
+// L - 1), so every neighbour displaced along t, y or z has consecutive half
+// indices for the two links starting at an even one (the strides and wrap
+// offsets L/2, L^2/2, L^3/2 times anything are even): one 2-vector load
+// serves both.  Neighbours displaced along x are loaded one by one.  Each
+// link's staple angles, arithmetic and draws are exactly those of
+// update_link_mu, and a link that does not move is stored back unchanged.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+template <typename T, int KIND, int MU>
+__device__ __forceinline__ void update_pair_mu(T* th, const Geom& g, int parity, int slab_d, int hp,
+                                               unsigned long long n, uint32_t k0, uint32_t k1, T beta,
+                                               int* __restrict__ err, const UpdateRule& rule) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int mu = MU;
+  const int h0 = 2 * hp;
+  int c0[4];
+  half_site_coords(g, h0, parity, c0);
+  if (slab_d > 0 && mu != 0 && small_mod(c0[0], slab_d) == 0) return;  // frozen boundary links (same t)
+  const int c1[4] = {c0[0], c0[1] + 2, c0[2], c0[3]};
+  const int i0 = site_index(g, c0[0], c0[1], c0[2], c0[3]);
+  const int i1 = i0 + 2;
+  const int op = parity ^ 1;
+  const T* arr_mu_op = th + static_cast<size_t>(mu * 2 + op) * g.Vh;
+  V2* self = reinterpret_cast<V2*>(th + static_cast<size_t>(mu * 2 + parity) * g.Vh + h0);
+  const V2 cur = *self;
+  const int ipmu0 = step_index(g, i0, c0, mu, +1);
+  const int ipmu1 = mu == 1 ? step_index(g, i1, c1, mu, +1) : ipmu0 + 2;
+  // both links' value at neighbour sites j0, j1 of one array (consecutive
+  // when `pair`, known at compile time)
+  auto load2 = [&](const T* arr, int j0, int j1, bool pair, T* a, T* b) {
+    if (pair) {
+      const V2 v = *reinterpret_cast<const V2*>(arr + (j0 >> 1));
+      *a = v.x;
+      *b = v.y;
+    } else {
+      *a = arr[j0 >> 1];
+      *b = arr[j1 >> 1];
+    }
+  };
+  T w0[4][6], w1[4][6];
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    const bool xnu = nu == 1, xmu = mu == 1;
+    const T* arr_nu_p = th + static_cast<size_t>(nu * 2 + parity) * g.Vh;
+    const T* arr_nu_op = th + static_cast<size_t>(nu * 2 + op) * g.Vh;
+    const int ipnu0 = step_index(g, i0, c0, nu, +1);
+    const int imnu0 = step_index(g, i0, c0, nu, -1);
+    const int ipnu1 = xnu ? step_index(g, i1, c1, nu, +1) : ipnu0 + 2;
+    const int imnu1 = xnu ? step_index(g, i1, c1, nu, -1) : imnu0 + 2;
+    // x + mu - nu: the coordinate along nu of x + mu is c[nu]
+    const int ipmu_mnu0 = step_index(g, ipmu0, c0, nu, -1);
+    const int ipmu_mnu1 = (xnu || xmu) ? step_index(g, ipmu1, c1, nu, -1) : ipmu_mnu0 + 2;
+    load2(arr_nu_op, ipmu0, ipmu1, !xmu, &w0[nu][0], &w1[nu][0]);
+    load2(arr_mu_op, ipnu0, ipnu1, !xnu, &w0[nu][1], &w1[nu][1]);
+    load2(arr_nu_p, i0, i1, true, &w0[nu][2], &w1[nu][2]);
+    load2(arr_nu_p, ipmu_mnu0, ipmu_mnu1, !xnu && !xmu, &w0[nu][3], &w1[nu][3]);
+    load2(arr_mu_op, imnu0, imnu1, !xnu, &w0[nu][4], &w1[nu][4]);
+    load2(arr_nu_op, imnu0, imnu1, !xnu, &w0[nu][5], &w1[nu][5]);
+  }
+  auto one = [&](const T (*w)[6], int i, T self_v, T* out) {
+    auto staples = [&](int nu, T v[6]) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[k] = w[nu][k];
+    };
+    auto curv = [&] { return self_v; };
+    if (KIND == 0 && rule.metropolis)
+      return new_link_angle<T, 2>(mu, staples, curv, static_cast<uint32_t>(i), n, k0, k1, beta, err, out,
+                                  static_cast<T>(rule.width), rule.hits);
+    return new_link_angle<T, KIND>(mu, staples, curv, static_cast<uint32_t>(i), n, k0, k1, beta, err, out);
+  };
+  V2 o = cur;
+  T out;
+  if (one(w0, i0, cur.x, &out)) o.x = out;
+  if (one(w1, i1, cur.y, &out)) o.y = out;
+  *self = o;
+}
+
+template <typename T, int KIND>
+__device__ __forceinline__ void update_pair(T* th, const Geom& g, int mu, int parity, int slab_d, int hp,
+                                            unsigned long long n, uint32_t k0, uint32_t k1, T beta,
+                                            int* __restrict__ err, const UpdateRule& rule) {
+  switch (mu) {
+    case 0:
+      update_pair_mu<T, KIND, 0>(th, g, parity, slab_d, hp, n, k0, k1, beta, err, rule);
+      break;
+    case 1:
+      update_pair_mu<T, KIND, 1>(th, g, parity, slab_d, hp, n, k0, k1, beta, err, rule);
+      break;
+    case 2:
+      update_pair_mu<T, KIND, 2>(th, g, parity, slab_d, hp, n, k0, k1, beta, err, rule);
+      break;
+    default:
+      update_pair_mu<T, KIND, 3>(th, g, parity, slab_d, hp, n, k0, k1, beta, err, rule);
+      break;
+  }
+}
+
 // One (mu, parity) pass, one thread per link.  The links of one pass share no
 // plaquette, so all of them update independently and in place.
 constexpr int kUpdateThreads = 128;  // block of the single-lattice pass kernel
+
+// The same pass with two links per thread (L a multiple of 4).
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kUpdateThreads) k_update_pass_pair(T* __restrict__ th, Geom g, int mu, int parity,
+                                                                     int slab_d,
+                                                                     const unsigned long long* __restrict__ n_dev,
+                                                                     unsigned long long n_fixed, uint32_t k0,
+                                                                     uint32_t k1, T beta, int* __restrict__ err,
+                                                                     UpdateRule rule) {
+  const int hp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (hp >= (g.Vh >> 1)) return;
+  const unsigned long long n = n_dev ? *n_dev : n_fixed;
+  update_pair<T, KIND>(th, g, mu, parity, slab_d, hp, n, k0, k1, beta, err, rule);
+}
 
 template <typename T, int KIND>
 __global__ void __launch_bounds__(kUpdateThreads) k_update_pass(T* __restrict__ th, Geom g, int mu, int parity, int slab_d,
@@ -284,29 +407,45 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, const uint32_t* __res
 // ---------------------------------------------------------------------------
 static inline int blocks_for(long long n, int t) { return static_cast<int>((n + t - 1) / t); }
 
+// One pass of one lattice with its values as launch parameters: two links
+// per thread when L is a multiple of 4, else one.  KIND 0: the update sweep's
+// rule (heatbath, or Metropolis with rule.metropolis); 1: overrelaxation.
+template <typename T, int KIND>
+static void launch_pass_t(T* th, const Geom& g, int mu, int parity, int slab_d, const unsigned long long* n_dev,
+                          unsigned long long n_fixed, uint32_t k0, uint32_t k1, T beta, int* err,
+                          const UpdateRule& rule, cudaStream_t s) {
+  if ((g.L & 3) == 0) {
+    const int nb = blocks_for(g.Vh / 2, kUpdateThreads);
+    k_update_pass_pair<T, KIND><<<nb, kUpdateThreads, 0, s>>>(th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1,
+                                                               beta, err, rule);
+  } else {
+    const int nb = blocks_for(g.Vh, kUpdateThreads);
+    k_update_pass<T, KIND><<<nb, kUpdateThreads, 0, s>>>(th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1, beta,
+                                                          err, rule);
+  }
+  count_launches(1);
+}
+
 void launch_update_pass(bool fp64, void* theta, const Geom& g, int mu, int parity, int slab_d, int kind,
                         const unsigned long long* n_dev, unsigned long long n_fixed, uint64_t seed, double beta,
                         int* err, cudaStream_t s, const UpdateRule& rule) {
-  const int nt = kUpdateThreads, nb = blocks_for(g.Vh, nt);
   const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
   // kind 2: the update sweep with the Metropolis rule
   const UpdateRule r{kind == 2 ? 1 : 0, rule.hits, rule.width};
   if (fp64) {
+    double* th = static_cast<double*>(theta);
     if (kind != 1)
-      k_update_pass<double, 0><<<nb, nt, 0, s>>>(static_cast<double*>(theta), g, mu, parity, slab_d, n_dev, n_fixed,
-                                                 k0, k1, beta, err, r);
+      launch_pass_t<double, 0>(th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1, beta, err, r, s);
     else
-      k_update_pass<double, 1><<<nb, nt, 0, s>>>(static_cast<double*>(theta), g, mu, parity, slab_d, n_dev, n_fixed,
-                                                 k0, k1, beta, err, r);
+      launch_pass_t<double, 1>(th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1, beta, err, r, s);
   } else {
+    float* th = static_cast<float*>(theta);
+    const float b = static_cast<float>(beta);
     if (kind != 1)
-      k_update_pass<float, 0><<<nb, nt, 0, s>>>(static_cast<float*>(theta), g, mu, parity, slab_d, n_dev, n_fixed, k0,
-                                                k1, static_cast<float>(beta), err, r);
+      launch_pass_t<float, 0>(th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1, b, err, r, s);
     else
-      k_update_pass<float, 1><<<nb, nt, 0, s>>>(static_cast<float*>(theta), g, mu, parity, slab_d, n_dev, n_fixed, k0,
-                                                k1, static_cast<float>(beta), err, r);
+      launch_pass_t<float, 1>(th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1, b, err, r, s);
   }
-  count_launches(1);
 }
 
 // Persistent sweep grid: one tile per block per pass when the table fits the
@@ -365,22 +504,20 @@ static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const T
           if (single && !ctl) {
             // one lattice: geometry, key and coupling as launch parameters
             // (constant bank) rather than loads from the table
-            const int nb = blocks_for(single->g.Vh, kUpdateThreads);
             T* th = static_cast<T*>(single->theta);
             const T beta = static_cast<T>(single->beta);
             if (sweep == 0)
-              k_update_pass<T, 0><<<nb, kUpdateThreads, 0, s>>>(th, single->g, mu, par, mask, single->n_dev, 0,
-                                                                single->k0, single->k1, beta, err,
-                                                                update_rule(*single));
+              launch_pass_t<T, 0>(th, single->g, mu, par, mask, single->n_dev, 0, single->k0, single->k1, beta, err,
+                                  update_rule(*single), s);
             else
-              k_update_pass<T, 1><<<nb, kUpdateThreads, 0, s>>>(th, single->g, mu, par, mask, single->n_dev, 0,
-                                                                single->k0, single->k1, beta, err,
-                                                                update_rule(*single));
-          } else if (sweep == 0) {
-            k_pass_table<T, 0><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
-          } else {
-            k_pass_table<T, 1><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
+              launch_pass_t<T, 1>(th, single->g, mu, par, mask, single->n_dev, 0, single->k0, single->k1, beta, err,
+                                  update_rule(*single), s);
+            continue;
           }
+          if (sweep == 0)
+            k_pass_table<T, 0><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
+          else
+            k_pass_table<T, 1><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
           count_launches(1);
         }
   }
