@@ -786,6 +786,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
   std::vector<int> tile_lat;
   TableDims& td = e->td;
   td = TableDims{};
+  td.all_l4 = true;  // cleared by any lattice with L not a multiple of 4
   for (int i = 0; i < n; ++i) {
     LatState* L = nullptr;
     int st = make_lattice(e, &ps[i], &L);
@@ -805,6 +806,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
     td.max_vac_blocks = std::max(td.max_vac_blocks, d.nparts);
     td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
     if (d.mh_rec[0]) td.max_blocks_mh = std::max(td.max_blocks_mh, (d.nslab * d.g.Ns + 255) / 256);
+    td.all_l4 = td.all_l4 && (d.g.L % 4 == 0);
   }
   td.nlat = n;
   td.total_tiles = static_cast<int>(tile_lat.size());

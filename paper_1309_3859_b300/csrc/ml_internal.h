@@ -85,6 +85,7 @@ struct TableDims {
   int max_vac_blocks;   // vac_part_count
   int max_vac_parts;    // nc * 2
   int max_blocks_mh;    // ceil(nslab * Ns / 256) of the multihit lattices; 0: none
+  bool all_l4;          // every lattice has L a multiple of 4 (two links per thread in the pass kernels)
 };
 
 constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep kernels)

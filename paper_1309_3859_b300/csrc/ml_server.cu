@@ -303,6 +303,7 @@ int rebuild_tables(ml_server* s) {
   s->h_tile_lat.clear();
   TableDims& td = s->td;
   td = TableDims{};
+  td.all_l4 = true;  // cleared by any lattice with L not a multiple of 4
   for (size_t i = 0; i < n; ++i) {
     LatDesc d = s->active[i]->L->desc;
     d.tile_start = static_cast<int>(s->h_tile_lat.size());
@@ -318,6 +319,7 @@ int rebuild_tables(ml_server* s) {
     td.max_vac_blocks = std::max(td.max_vac_blocks, d.nparts);
     td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
     if (d.mh_rec[0]) td.max_blocks_mh = std::max(td.max_blocks_mh, (d.nslab * d.g.Ns + 255) / 256);
+    td.all_l4 = td.all_l4 && (d.g.L % 4 == 0);
   }
   td.nlat = static_cast<int>(n);
   td.total_tiles = static_cast<int>(s->h_tile_lat.size());

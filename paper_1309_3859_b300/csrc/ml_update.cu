@@ -346,6 +346,24 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_pass_table(const LatDesc* 
   update_link<T, KIND>(th, g, mu, parity, md, h, n, k0, k1, beta, err, update_rule(L));
 }
 
+// The same pass with two links per thread, for tables whose lattices all
+// have L a multiple of 4: tile t's kSweepTile links go to kSweepTile / 2
+// threads.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kSweepThreads / 2) k_pass_table_pair(const LatDesc* __restrict__ d,
+                                                                       const int* __restrict__ tile_lat,
+                                                                       const LatCtl* __restrict__ ctl, int mask,
+                                                                       int mu, int parity, int* __restrict__ err) {
+  const int i = tile_lat[blockIdx.x];
+  const LatDesc& L = d[i];
+  const Geom g = L.g;
+  const int hp = (blockIdx.x - L.tile_start) * (kSweepTile / 2) + threadIdx.x;
+  if (2 * hp >= g.Vh) return;
+  const int md = ctl ? ctl[i].mask : mask;
+  update_pair<T, KIND>(static_cast<T*>(L.theta), g, mu, parity, md, hp, *L.n_dev, L.k0, L.k1,
+                       static_cast<T>(L.beta), err, update_rule(L));
+}
+
 __global__ void k_sweep_begin_table(const LatDesc* __restrict__ d, int nlat) {
   for (int i = threadIdx.x; i < nlat; i += blockDim.x) *d[i].n_dev += 1ull;
 }
@@ -514,10 +532,18 @@ static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const T
                                   update_rule(*single), s);
             continue;
           }
-          if (sweep == 0)
+          if (td.all_l4) {  // two links per thread
+            if (sweep == 0)
+              k_pass_table_pair<T, 0><<<td.total_tiles, kSweepThreads / 2, 0, s>>>(d, tile_lat, ctl, mask, mu, par,
+                                                                                    err);
+            else
+              k_pass_table_pair<T, 1><<<td.total_tiles, kSweepThreads / 2, 0, s>>>(d, tile_lat, ctl, mask, mu, par,
+                                                                                    err);
+          } else if (sweep == 0) {
             k_pass_table<T, 0><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
-          else
+          } else {
             k_pass_table<T, 1><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
+          }
           count_launches(1);
         }
   }
