@@ -267,6 +267,18 @@ typedef enum {
 int ml_sweep_mode(ml_lattice *h, int *mode);
 int ml_set_sweep_mode(ml_lattice *h, int mode);
 
+/* Implementation of the field-insertion fold (Section II.C's [TO] sums). */
+typedef enum {
+  ML_FOLD_SITE = 0, /* one thread per site reads each probe's recorded plaquette sums from global memory */
+  ML_FOLD_TILE = 1  /* a block stages the recorded plaquette sums its probes reach in shared memory once
+                       per component; available when every lattice has L <= 256 and a tile of at most
+                       96 KB (else ML_EINVAL when forced) */
+} ml_fold_impl;
+/* Query or force the fold implementation; ml_create picks the faster of the
+ * two on the handle's table.  Both give bit-identical sums. */
+int ml_fold_mode(ml_lattice *h, int *mode);
+int ml_set_fold_mode(ml_lattice *h, int mode);
+
 /* Number of sub-update records the handle folds into its slab sums per
  * accumulation pass (chosen at ml_create from the record size, at most 16). */
 int ml_batch_slots(ml_lattice *h, int *n);

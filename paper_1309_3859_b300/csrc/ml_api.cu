@@ -658,6 +658,36 @@ int plan_resident_sweeps(Engine* e) {
 // up) and the fastest of each group is kept.  Small tables are latency-bound
 // and favour the persistent or resident kernels; large ones the per-pass
 // kernels' full occupancy.
+// The field-insertion fold: the per-site kernel or the shared-memory tiled
+// one (when every lattice admits it), whichever folds a full ring buffer
+// faster on this table.  Timing folds touches only the slab sums, which every
+// measurement's first fold overwrites, and the vacuum sums, which every
+// measurement clears.
+int choose_fold_mode(Engine* e) {
+  e->td.fold_tile_on = false;
+  if (!e->td.fold_tile || e->td.max_y_O == 0) return ML_OK;
+  cudaEvent_t ev[3];
+  for (cudaEvent_t& x : ev) ML_CUDA(cudaEventCreate(&x));
+  float best[2] = {1e30f, 1e30f};
+  int st = ML_OK;
+  for (int round = 0; round < 3 && !st; ++round)
+    for (int mode = 0; mode < 2 && !st; ++mode) {
+      e->td.fold_tile_on = mode == 1;
+      st = cuda_status(cudaEventRecord(ev[0], e->stream));
+      for (int rep = 0; rep < 2 && !st; ++rep)
+        launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, 0, e->nB, e->stream, false, false);
+      if (!st) st = cuda_status(cudaEventRecord(ev[1], e->stream));
+      if (!st) st = cuda_status(cudaEventSynchronize(ev[1]));
+      float ms = 0.f;
+      if (!st) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (round > 0) best[mode] = std::min(best[mode], ms);  // round 0 warms up
+    }
+  for (cudaEvent_t& x : ev) cudaEventDestroy(x);
+  e->td.fold_tile_on = best[1] < best[0];
+  if (st) return st;
+  return cuda_status(cudaGetLastError());
+}
+
 int choose_sweep_mode(Engine* e) {
   int st = ensure_scratch(e);
   if (!st) st = refresh_scratch(e);
@@ -751,6 +781,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
       return ML_EINVAL;
   }
   e->replay = ps[0].replay != 0;
+  if (prepare_measure_kernels()) return ML_ECUDA;
   e->fp64 = ps[0].prec == ML_FP64;
   e->nB = rec_batch(e->fp64);
   e->n_or = ps[0].n_or;
@@ -787,6 +818,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
   TableDims& td = e->td;
   td = TableDims{};
   td.all_l4 = true;  // cleared by any lattice with L not a multiple of 4
+  td.fold_tile = true;  // cleared by any lattice the tiled fold does not take
   for (int i = 0; i < n; ++i) {
     LatState* L = nullptr;
     int st = make_lattice(e, &ps[i], &L);
@@ -807,6 +839,18 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
     td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
     if (d.mh_rec[0]) td.max_blocks_mh = std::max(td.max_blocks_mh, (d.nslab * d.g.Ns + 255) / 256);
     td.all_l4 = td.all_l4 && (d.g.L % 4 == 0);
+    if (m.nrf > 0 && m.np > 0 && m.nc > 0) {
+      int bx = 0;
+      size_t sm = 0;
+      const LatState* Ls = L;
+      if (fold_tile_plan(e->fp64, d.g.L, Ls->pdy.data(), Ls->pdz.data(), m.np, &bx, &sm)) {
+        td.fold_tile_bx = std::max(td.fold_tile_bx, bx);
+        td.fold_tile_smem = std::max(td.fold_tile_smem, sm);
+        td.max_y_T_O = std::max(td.max_y_T_O, d.nslab * m.nrf);
+      } else {
+        td.fold_tile = false;
+      }
+    }
   }
   td.nlat = n;
   td.total_tiles = static_cast<int>(tile_lat.size());
@@ -819,6 +863,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
   ML_CUDA(cudaStreamSynchronize(e->stream));
   int st = plan_resident_sweeps(e);
   if (!st) st = choose_sweep_mode(e);
+  if (!st) st = choose_fold_mode(e);
   if (!st) st = capture_graphs(e);
   return st;
 }
@@ -1055,6 +1100,24 @@ int ml_sweep_mode(ml_lattice* h, int* mode) {
 int ml_set_sweep_mode(ml_lattice* h, int mode) {
   if (!h) return ML_EINVAL;
   return set_sweep_mode(&h->e, mode);
+}
+
+int ml_fold_mode(ml_lattice* h, int* mode) {
+  if (!h || !mode) return ML_EINVAL;
+  *mode = h->e.td.fold_tile_on ? ML_FOLD_TILE : ML_FOLD_SITE;
+  return ML_OK;
+}
+
+int ml_set_fold_mode(ml_lattice* h, int mode) {
+  if (!h || (mode != ML_FOLD_SITE && mode != ML_FOLD_TILE)) return ML_EINVAL;
+  Engine* e = &h->e;
+  if (mode == ML_FOLD_TILE && !e->td.fold_tile) return ML_EINVAL;
+  // folds in flight on the accumulation stream finish first
+  int st = join(e->side, e->stream, e->ev_side);
+  if (!st) st = cuda_status(cudaStreamSynchronize(e->stream));
+  if (st) return st;
+  e->td.fold_tile_on = mode == ML_FOLD_TILE;
+  return ML_OK;
 }
 
 int ml_batch_slots(ml_lattice* h, int* n) {

@@ -86,6 +86,11 @@ struct TableDims {
   int max_vac_parts;    // nc * 2
   int max_blocks_mh;    // ceil(nslab * Ns / 256) of the multihit lattices; 0: none
   bool all_l4;          // every lattice has L a multiple of 4 (two links per thread in the pass kernels)
+  bool fold_tile;       // every lattice takes the shared-memory tiled fold (fold_tile_plan)
+  bool fold_tile_on;    // the fold runs tiled (the engine's autotuner; the server keeps the per-site fold)
+  int fold_tile_bx;     // its blocks per (slab, field separation): max over the lattices
+  size_t fold_tile_smem;  // its dynamic shared memory: max over the lattices
+  int max_y_T_O;        // nslab * nrf (blocks of the tiled fold)
 };
 
 constexpr int kSweepTile = 384;  // links per sweep tile (= block of the sweep kernels)
@@ -119,6 +124,10 @@ void launch_mh_record_table(bool fp64, const LatDesc* d, const TableDims& td, co
 void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
                        cudaStream_t s, bool skip_O = false, bool overwrite = false);
 int record_blocks(const Geom& g, int d);
+// kernel attributes of the measurement kernels (before any launch or capture); 0 or -1
+int prepare_measure_kernels();
+// tiled-fold plan of one lattice (L, probe offsets): false when it does not apply
+bool fold_tile_plan(bool fp64, int L, const int* pdy, const int* pdz, int np, int* blocks_x, size_t* smem);
 // co-resident blocks per SM of the persistent sweep kernel
 int sweep_blocks_per_sm(bool fp64);
 int fold_probe_groups(int np);

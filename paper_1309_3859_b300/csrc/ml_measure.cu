@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "ml_record.cuh"
+#include "ml_sync.cuh"
 
 namespace ml {
 
@@ -392,6 +393,175 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
         if (q0 + i < nck) acc[abase + static_cast<size_t>(q0 + i) * g.Ns] = a[i];
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// The same fold with the recorded plaquette sums staged in shared memory.
+// Every site's 16-record batch of one component is read once per (field
+// separation, probe) by the per-site kernel above; here a block owns whole x
+// rows (rows_per_block(L) of them, at one z) of one (slab, field
+// separation), copies the records of every site any of its probes reaches
+// (the block's rows widened by the probes' y and z extent) into shared memory
+// once per component, and serves all probes from there: the L2 traffic of
+// the records falls by about the number of probes.  Each site's records
+// take their 16 x sizeof(T) bytes plus 16 of padding in the tile (an odd
+// number of 16-byte chunks), so that the 16-byte reads of a warp's
+// consecutive sites fall in distinct banks.  The
+// arithmetic is that of the per-site kernel, operation for operation.
+// ---------------------------------------------------------------------------
+constexpr int kTileThreads = 256;
+// tile bytes per site: the 16 records and a 16-byte pad
+__host__ __device__ constexpr int tile_site_bytes(bool fp64) { return 16 * (fp64 ? 8 : 4) + 16; }
+constexpr int kTileProbes = 4;              // slab sums loaded together
+constexpr size_t kTileSmemMax = 96 * 1024;  // per block
+
+struct ProbeBox {
+  int dymin, dymax, dzmin, dzmax;
+};
+__host__ __device__ inline ProbeBox probe_box(const int* pdy, const int* pdz, int np) {
+  ProbeBox b{pdy[0], pdy[0], pdz[0], pdz[0]};
+  for (int i = 1; i < np; ++i) {
+    b.dymin = pdy[i] < b.dymin ? pdy[i] : b.dymin;
+    b.dymax = pdy[i] > b.dymax ? pdy[i] : b.dymax;
+    b.dzmin = pdz[i] < b.dzmin ? pdz[i] : b.dzmin;
+    b.dzmax = pdz[i] > b.dzmax ? pdz[i] : b.dzmax;
+  }
+  return b;
+}
+__host__ __device__ inline int tile_rows_per_block(int L) {
+  const int r = L >= kTileThreads ? 1 : kTileThreads / L;
+  return r < L ? r : L;
+}
+// tile rows: the block's rows widened by the y extent, times the z extent
+__host__ __device__ inline int tile_rows(int L, const ProbeBox& p) {
+  return (tile_rows_per_block(L) + p.dymax - p.dymin) * (p.dzmax - p.dzmin + 1);
+}
+
+// blocks per SM of the tiled fold: FP32 3 (85 registers), FP64 2
+template <typename T>
+constexpr int tile_min_blocks() {
+  return sizeof(T) == 4 ? 3 : 2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_tile(const LatDesc* __restrict__ desc,
+                                                               const LatCtl* __restrict__ ctl, int buf, int nrec,
+                                                               int overwrite) {
+  constexpr int B = RecBatch<T>::n;
+  constexpr int SE = tile_site_bytes(sizeof(T) == 8) / static_cast<int>(sizeof(T));  // site stride in the tile
+  constexpr int CH = 16 / static_cast<int>(sizeof(T));                               // elements per 16-byte chunk
+  constexpr int NCH = B / CH;                                                         // chunks of a site's records
+  using A = typename SlabAcc<T>::type;
+  extern __shared__ __align__(16) unsigned char tile_smem[];
+  T* const tile = reinterpret_cast<T*>(tile_smem);
+  const int li = blockIdx.z;
+  if (ctl) {
+    if (!ctl[li].fold) return;
+    buf = ctl[li].fold_buf;
+    nrec = ctl[li].nrec;
+  }
+  const LatDesc& L = desc[li];
+  const Geom g = L.g;
+  const MeasLayout& m = L.m;
+  if (m.nrf == 0 || m.np == 0 || m.nc == 0 || static_cast<int>(blockIdx.y) >= L.nslab * m.nrf) return;
+  const int ry = tile_rows_per_block(g.L);
+  const int nrb = (g.L + ry - 1) / ry;  // row blocks per z plane
+  if (static_cast<int>(blockIdx.x) >= nrb * g.L) return;
+  const int z0 = blockIdx.x / nrb, y0 = (blockIdx.x - z0 * nrb) * ry;
+  const int rows = min(ry, g.L - y0);
+  const ProbeBox pb = probe_box(m.pdy, m.pdz, m.np);
+  const int tyn = ry + pb.dymax - pb.dymin;
+  const int trows = tyn * (pb.dzmax - pb.dzmin + 1);
+  const int s = blockIdx.y / m.nrf, f = blockIdx.y - s * m.nrf;
+  const int nck = 2 * m.nc;
+  const int tid = threadIdx.x, yy = tid / g.L, xx = tid - yy * g.L;
+  const bool live = yy < rows;
+  const int cy = y0 + (live ? yy : 0), cz = z0;
+  const int x = xx + g.L * (cy + g.L * cz);
+  const int rf = m.rf[f];
+  const int xr = wrapc(xx + rf, g.L) + g.L * (cy + g.L * cz);
+  const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
+  const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
+  A* __restrict__ acc = reinterpret_cast<A*>(L.accO);
+  T er[B], ei[B];
+  batch_phases<T>(trec + static_cast<size_t>(x) * B, trec + static_cast<size_t>(xr) * B, nrec, er, ei);
+  const int col = wrapc(xx + rf / 2, g.L);
+  for (int q = 0; q < nck; ++q) {
+    const int ci = q >> 1, k = q & 1;
+    const T* src = osum + (static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns * B;
+    for (int r = 0; r < trows; ++r) {  // tile row r: y = y0 + dymin + r mod tyn, z = z0 + dzmin + r / tyn
+      const int tz = r / tyn, ty = r - tz * tyn;
+      const int yg = wrapc(y0 + pb.dymin + ty, g.L), zg = wrapc(z0 + pb.dzmin + tz, g.L);
+      const T* row_src = src + static_cast<size_t>(g.L) * (yg + g.L * zg) * B;
+      T* row_dst = tile + static_cast<size_t>(r) * g.L * SE;
+      for (int c = tid; c < g.L * NCH; c += blockDim.x)
+        cp_async16(row_dst + (c / NCH) * SE + (c % NCH) * CH, row_src + (c / NCH) * B + (c % NCH) * CH);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (live) {
+      for (int b0 = 0; b0 < m.np; b0 += kTileProbes) {
+        A a[kTileProbes];
+#pragma unroll
+        for (int i = 0; i < kTileProbes; ++i)
+          if (b0 + i < m.np)
+            a[i] = overwrite ? A{}
+                             : acc[(((static_cast<size_t>(s) * m.nrf + f) * m.np + b0 + i) * nck + q) * g.Ns + x];
+#pragma unroll
+        for (int i = 0; i < kTileProbes; ++i) {
+          const int b = b0 + i;
+          if (b >= m.np) break;
+          const int r = (yy + m.pdy[b] - pb.dymin) + tyn * (m.pdz[b] - pb.dzmin);
+          const T* o_s = tile + (static_cast<size_t>(r) * g.L + col) * SE;
+          T o[B];
+#pragma unroll
+          for (int c = 0; c < NCH; ++c) {
+            if constexpr (sizeof(T) == 4) {
+              const float4 v = *reinterpret_cast<const float4*>(o_s + c * CH);
+              o[4 * c] = v.x;
+              o[4 * c + 1] = v.y;
+              o[4 * c + 2] = v.z;
+              o[4 * c + 3] = v.w;
+            } else {
+              const double2 v = *reinterpret_cast<const double2*>(o_s + c * CH);
+              o[2 * c] = v.x;
+              o[2 * c + 1] = v.y;
+            }
+          }
+          T sr = T(0), si = T(0);
+#pragma unroll
+          for (int j = 0; j < B; ++j) {
+            sr += er[j] * o[j];
+            si += ei[j] * o[j];
+          }
+          acc_add(a[i], sr, si);
+        }
+#pragma unroll
+        for (int i = 0; i < kTileProbes; ++i)
+          if (b0 + i < m.np) acc[(((static_cast<size_t>(s) * m.nrf + f) * m.np + b0 + i) * nck + q) * g.Ns + x] = a[i];
+      }
+    }
+    __syncthreads();  // the tile is read before the next component's copies
+  }
+}
+
+// Tile plan of a lattice for k_accum_O_tile: false when it does not apply
+// (L above the block, or a tile above kTileSmemMax).
+bool fold_tile_plan(bool fp64, int L, const int* pdy, const int* pdz, int np, int* blocks_x, size_t* smem) {
+  if (np <= 0) {
+    *blocks_x = 0;
+    *smem = 0;
+    return true;
+  }
+  if (L > kTileThreads) return false;
+  const ProbeBox pb = probe_box(pdy, pdz, np);
+  const size_t bytes = static_cast<size_t>(tile_rows(L, pb)) * L * tile_site_bytes(fp64);
+  if (bytes > kTileSmemMax) return false;
+  const int ry = tile_rows_per_block(L);
+  *blocks_x = (L + ry - 1) / ry * L;
+  *smem = bytes;
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -785,6 +955,14 @@ void launch_mh_record_table(bool fp64, const LatDesc* d, const TableDims& td, co
   count_launches(1);
 }
 
+int prepare_measure_kernels() {
+  const int most = static_cast<int>(kTileSmemMax);  // above the 48 KB default of dynamic shared memory
+  cudaError_t e = cudaFuncSetAttribute(k_accum_O_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_accum_O_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  return e == cudaSuccess ? 0 : -1;
+}
+
 void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
                        cudaStream_t s, bool skip_O, bool overwrite) {
   const int ow = overwrite ? 1 : 0;
@@ -797,7 +975,14 @@ void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const L
     (td.max_blocks_mh > 0 ? k_accum_T_table<float, true> : k_accum_T_table<float, false>)<<<gt, 256, 0, s>>>(
         d, ctl, buf, nrec, ow);
   count_launches(1);
-  if (td.max_y_O > 0 && !skip_O) {
+  if (td.max_y_O > 0 && !skip_O && td.fold_tile && td.fold_tile_on) {
+    const dim3 go(td.fold_tile_bx, td.max_y_T_O, td.nlat);
+    if (fp64)
+      k_accum_O_tile<double><<<go, kTileThreads, td.fold_tile_smem, s>>>(d, ctl, buf, nrec, ow);
+    else
+      k_accum_O_tile<float><<<go, kTileThreads, td.fold_tile_smem, s>>>(d, ctl, buf, nrec, ow);
+    count_launches(1);
+  } else if (td.max_y_O > 0 && !skip_O) {
     const dim3 go(td.max_blocks_site, td.max_y_O, td.nlat);
     if (fp64)
       k_accum_O_table<double><<<go, 256, 0, s>>>(d, ctl, buf, nrec, ow);

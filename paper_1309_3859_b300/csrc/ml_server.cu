@@ -304,6 +304,7 @@ int rebuild_tables(ml_server* s) {
   TableDims& td = s->td;
   td = TableDims{};
   td.all_l4 = true;  // cleared by any lattice with L not a multiple of 4
+  td.fold_tile = true;  // cleared by any lattice the tiled fold does not take
   for (size_t i = 0; i < n; ++i) {
     LatDesc d = s->active[i]->L->desc;
     d.tile_start = static_cast<int>(s->h_tile_lat.size());
@@ -320,6 +321,18 @@ int rebuild_tables(ml_server* s) {
     td.max_vac_parts = std::max(td.max_vac_parts, 2 * m.nc);
     if (d.mh_rec[0]) td.max_blocks_mh = std::max(td.max_blocks_mh, (d.nslab * d.g.Ns + 255) / 256);
     td.all_l4 = td.all_l4 && (d.g.L % 4 == 0);
+    if (m.nrf > 0 && m.np > 0 && m.nc > 0) {
+      int bx = 0;
+      size_t sm = 0;
+      const LatState* Ls = s->active[i]->L;
+      if (fold_tile_plan(s->e.fp64, d.g.L, Ls->pdy.data(), Ls->pdz.data(), m.np, &bx, &sm)) {
+        td.fold_tile_bx = std::max(td.fold_tile_bx, bx);
+        td.fold_tile_smem = std::max(td.fold_tile_smem, sm);
+        td.max_y_T_O = std::max(td.max_y_T_O, d.nslab * m.nrf);
+      } else {
+        td.fold_tile = false;
+      }
+    }
   }
   td.nlat = static_cast<int>(n);
   td.total_tiles = static_cast<int>(s->h_tile_lat.size());
@@ -472,7 +485,8 @@ int ml_server_create(const ml_server_config* cfg, ml_server** out) {
   s->e.alloc.ctx = &s->arena;
   s->e.use_alloc = true;
   s->max_active = cfg->max_active > 0 ? cfg->max_active : 1024;
-  cudaError_t ce = cudaStreamCreateWithFlags(&s->e.stream, cudaStreamNonBlocking);
+  cudaError_t ce = prepare_measure_kernels() ? cudaErrorUnknown : cudaSuccess;
+  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->e.stream, cudaStreamNonBlocking);
   if (ce == cudaSuccess) s->e.own_stream = true;
   if (ce == cudaSuccess) ce = cudaMalloc(&s->e.d_err, sizeof(int));
   if (ce == cudaSuccess) ce = cudaMalloc(&s->e.bar, sizeof(unsigned long long));

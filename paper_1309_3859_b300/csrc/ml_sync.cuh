@@ -93,4 +93,13 @@ __device__ __forceinline__ double ld_cluster(uint32_t a, double*) {
   return v;
 }
 
+// ---- asynchronous global -> shared copies of 16 bytes (cp.async) ----
+// Each thread's copies form groups; cp_async_wait_all waits for the thread's
+// own groups, so a block barrier must follow before other threads read them.
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(shared_addr(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 }  // namespace ml

@@ -20,6 +20,7 @@ from . import build as _build
 ML_OK, ML_EINVAL, ML_ENOMEM, ML_ECUDA, ML_ETIMEOUT, ML_EREJECT, ML_EBUSY, ML_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 ML_FP64, ML_FP32 = 0, 1
 ML_SWEEP_PERSISTENT, ML_SWEEP_PASSES, ML_SWEEP_RESIDENT = 0, 1, 2
+ML_FOLD_SITE, ML_FOLD_TILE = 0, 1
 ML_UPDATE_HEATBATH, ML_UPDATE_METROPOLIS = 0, 1
 (ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP, ML_K_SUBUPDATE,
  ML_K_FULLSWEEP) = range(8)
@@ -86,6 +87,8 @@ SIGNATURES = {
     "ml_batch_slots": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     "ml_sweep_mode": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     "ml_set_sweep_mode": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ml_fold_mode": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
+    "ml_set_fold_mode": (ctypes.c_int, [_H, ctypes.c_int]),
     "ml_naive_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p]),
@@ -352,6 +355,16 @@ class Lattice:
     @sweep_mode.setter
     def sweep_mode(self, mode: int):
         _check(lib().ml_set_sweep_mode(self.h, int(mode)), "ml_set_sweep_mode")
+
+    @property
+    def fold_mode(self) -> int:
+        m = ctypes.c_int()
+        _check(lib().ml_fold_mode(self.h, ctypes.byref(m)), "ml_fold_mode")
+        return m.value
+
+    @fold_mode.setter
+    def fold_mode(self, mode: int):
+        _check(lib().ml_set_fold_mode(self.h, int(mode)), "ml_set_fold_mode")
 
     @property
     def batch_slots(self) -> int:

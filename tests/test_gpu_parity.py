@@ -525,6 +525,26 @@ def test_sweep_implementations_agree(fp64, geom):
         assert np.array_equal(a[0], b[0]), mode
 
 
+@pytest.mark.parametrize("fp64", [True, False])
+@pytest.mark.parametrize("geom", [dict(L=8, Nt=4, n_sub=20, probes=((0, 0), (1, 0), (-2, 1), (3, -2))),
+                                  dict(L=6, Nt=8, n_sub=18, outer_slab=4, n_sub_outer=2,
+                                       probes=((0, 0), (2, 0), (5, 5))),
+                                  dict(L=12, Nt=4, n_sub=3, probes=tuple((d, 0) for d in range(7)))])
+def test_fold_implementations_agree(fp64, geom):
+    """The per-site fold and the shared-memory tiled fold form the same sums
+    operation for operation: identical records.  The probe sets reach both
+    signs of y and z offsets and wrap around the lattice."""
+    p = ml.Params(beta=0.95, seed=8, fp64=fp64, slab=2, k_between=1, r=(1, 2), rf=(1, 2, 3), comp_mask=0x3F, **geom)
+    out = {}
+    for mode in (ml.ML_FOLD_SITE, ml.ML_FOLD_TILE):
+        with ml.Lattice(p) as lat:
+            lat.fold_mode = mode
+            assert lat.fold_mode == mode
+            lat.thermalize(2)
+            out[mode] = lat.measure(2)
+    assert np.array_equal(out[ml.ML_FOLD_SITE], out[ml.ML_FOLD_TILE])
+
+
 def test_resident_mode_needs_fitting_slabs():
     """A 64^3 slab of thickness 2 needs more shared memory than a cluster
     has: forcing the resident implementation is rejected, the handle keeps
