@@ -365,43 +365,55 @@ __global__ void __launch_bounds__(kResThreads, 1)
     }
     if (record) {
       // the slab's record from shared memory (ghosts are current): phase sums
-      // and plaquette sums of the selected components into slot rec_slot + round
+      // and plaquette sums of the selected components into slot rec_slot +
+      // round, one owned site per thread (its coordinates worked out once)
       const int nc = Ld.m.nc, slot = rec_slot + round;
-      for (int k = threadIdx.x; k < (nc + 1) * own; k += blockDim.x) {
-        const int y = fdiv(k, m_own), j = k - y * own;
+      T* osum = static_cast<T*>(Ld.osum[rec_buf]);
+      for (int j = threadIdx.x; j < own; j += blockDim.x) {
         const int row = fdiv(j, m_L), cx = j - row * g.L;
         const int rz = fdiv(row, m_yl), ry = row - rz * b.ylen;
         const int x = cx + g.L * (b.y0 + ry + g.L * (b.z0 + rz));
         const int bi = b.cell(cx + 1, ry + 1, rz + 1);
-        if (y == nc) {
-          double tsum = 0.0;
-          for (int tl = 0; tl < d; ++tl) tsum += static_cast<double>(buf[tl * b.vol + bi]);
-          static_cast<T*>(Ld.theta_rec[rec_buf])[(static_cast<size_t>(s) * g.Ns + x) * RecBatch<T>::n + slot] =
-              static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
-          if (MH && Ld.mh_rec[rec_buf]) {
-            T mod, ph;
-            multihit_slab<T>(0, d, beta, [&](int tl, int nu, T v[6]) { box_staples<T>(b, buf, 0, tl, bi, nu, v); },
-                             &mod, &ph);
-            T* mh = static_cast<T*>(Ld.mh_rec[rec_buf]);
-            mh[mh_index<T>(g, s, 0, x, slot)] = mod;
-            mh[mh_index<T>(g, s, 1, x, slot)] = ph;
+        double tsum = 0.0;
+        for (int tl = 0; tl < d; ++tl) tsum += static_cast<double>(buf[tl * b.vol + bi]);
+        static_cast<T*>(Ld.theta_rec[rec_buf])[(static_cast<size_t>(s) * g.Ns + x) * RecBatch<T>::n + slot] =
+            static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
+        if (MH && Ld.mh_rec[rec_buf]) {
+          T mod, ph;
+          multihit_slab<T>(0, d, beta, [&](int tl, int nu, T v[6]) { box_staples<T>(b, buf, 0, tl, bi, nu, v); },
+                           &mod, &ph);
+          T* mh = static_cast<T*>(Ld.mh_rec[rec_buf]);
+          mh[mh_index<T>(g, s, 0, x, slot)] = mod;
+          mh[mh_index<T>(g, s, 1, x, slot)] = ph;
+        }
+        // plaquette sums of plane (mu, nu) over the slab's times into row y
+        auto plane_sums = [&](int mu, int nu, int y) {
+          T re = T(0), im = T(0);
+          for (int tl = 0; tl < d; ++tl) {
+            const T a = buf[b.slot(mu, tl) * b.vol + bi] + buf[b.slot(nu, tl + (mu == 0)) * b.vol + bi + b.off(mu)] -
+                        buf[b.slot(mu, tl) * b.vol + bi + b.off(nu)] - buf[b.slot(nu, tl) * b.vol + bi];
+            T sn, cs;
+            P::sincos_(a, &sn, &cs);
+            re += cs;
+            im += sn;
           }
-          continue;
+          osum[((static_cast<size_t>(s * nc + y) * 2 + 0) * g.Ns + x) * RecBatch<T>::n + slot] = re;
+          osum[((static_cast<size_t>(s * nc + y) * 2 + 1) * g.Ns + x) * RecBatch<T>::n + slot] = im;
+        };
+        if (nc == 6) {  // all six components, rows in component order: planes known at compile time
+          plane_sums(0, 1, 0);
+          plane_sums(0, 2, 1);
+          plane_sums(0, 3, 2);
+          plane_sums(2, 3, 3);
+          plane_sums(3, 1, 4);
+          plane_sums(1, 2, 5);
+        } else {
+          for (int y = 0; y < nc; ++y) {
+            int mu, nu;
+            plane_of(Ld.m.comp[y], &mu, &nu);  // nu is spatial for every component
+            plane_sums(mu, nu, y);
+          }
         }
-        int mu, nu;
-        plane_of(Ld.m.comp[y], &mu, &nu);  // nu is spatial for every component
-        T re = T(0), im = T(0);
-        for (int tl = 0; tl < d; ++tl) {
-          const T a = buf[b.slot(mu, tl) * b.vol + bi] + buf[b.slot(nu, tl + (mu == 0)) * b.vol + bi + b.off(mu)] -
-                      buf[b.slot(mu, tl) * b.vol + bi + b.off(nu)] - buf[b.slot(nu, tl) * b.vol + bi];
-          T sn, cs;
-          P::sincos_(a, &sn, &cs);
-          re += cs;
-          im += sn;
-        }
-        T* osum = static_cast<T*>(Ld.osum[rec_buf]);
-        osum[((static_cast<size_t>(s * nc + y) * 2 + 0) * g.Ns + x) * RecBatch<T>::n + slot] = re;
-        osum[((static_cast<size_t>(s * nc + y) * 2 + 1) * g.Ns + x) * RecBatch<T>::n + slot] = im;
       }
     }
     // records read mirrored cells: no CTA stores into them before every
