@@ -40,34 +40,18 @@ __device__ __forceinline__ double2 unit_phase(double phi) {
 }
 
 // ---------------------------------------------------------------------------
-// Ring of sub-update records, slot-fastest: element (slot j) of
-//   theta_rec[s][x][slots]           Theta_s(x) = sum_{t in slab} theta_0(x, t)
+// Ring of sub-update records (layout: rec_index), element (slot j) of
+//   theta_rec[s][slots][x]           Theta_s(x) = sum_{t in slab} theta_0(x, t)
 //                                    (FP32: summed in double, reduced to
 //                                    [-pi, pi) and rounded)
-//   osum[s][ci][k][x][slots]         sum_{t in slab} (Re, Im) P_c(x, t)
-// so the fold reads all records of one site as one contiguous vector.
+//   osum[s][ci][k][slots][x]         sum_{t in slab} (Re, Im) P_c(x, t)
+// A site's batch: the slots at p, p + Ns, p + 2 Ns, ... (p = rec_index(.., 0)),
+// each load coalesced over a warp's consecutive sites.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void load_batch(const T* __restrict__ p, T v[RecBatch<T>::n]) {
-  if constexpr (sizeof(T) == 4) {
-    const float4* q = reinterpret_cast<const float4*>(p);
+__device__ __forceinline__ void load_batch(const T* __restrict__ p, int stride, T v[RecBatch<T>::n]) {
 #pragma unroll
-    for (int j = 0; j < RecBatch<T>::n / 4; ++j) {
-      const float4 a = __ldg(q + j);
-      v[4 * j] = a.x;
-      v[4 * j + 1] = a.y;
-      v[4 * j + 2] = a.z;
-      v[4 * j + 3] = a.w;
-    }
-  } else {
-    const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll
-    for (int j = 0; j < RecBatch<T>::n / 2; ++j) {
-      const double2 a = __ldg(q + j);
-      v[2 * j] = a.x;
-      v[2 * j + 1] = a.y;
-    }
-  }
+  for (int j = 0; j < RecBatch<T>::n; ++j) v[j] = __ldg(p + static_cast<size_t>(j) * stride);
 }
 
 // Record of each lattice's configuration into ring slot `slot` of buffer
@@ -153,9 +137,9 @@ __global__ void __launch_bounds__(256) k_vac_partial_table(const LatDesc* __rest
   for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const long long sl = i / L.g.Ns;
     const long long x = i - sl * L.g.Ns;
-    const T* o = osum + (((sl * L.m.nc + ci) * 2 + k) * L.g.Ns + x) * B;
+    const T* o = osum + rec_index(L.g, static_cast<size_t>((sl * L.m.nc + ci) * 2 + k), static_cast<int>(x), 0);
     T a[B];
-    load_batch<T>(o, a);
+    load_batch<T>(o, L.g.Ns, a);
     T t = T(0);
 #pragma unroll
     for (int j = 0; j < B; ++j)
@@ -247,12 +231,12 @@ __device__ __forceinline__ void acc_add(float4& a, float re, float im) {
 
 // e^{i (Theta(x + r) - Theta(x))} for the first nrec records, zero beyond
 template <typename T>
-__device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const T* __restrict__ rec_xr, int nrec,
-                                             T er[RecBatch<T>::n], T ei[RecBatch<T>::n]) {
+__device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const T* __restrict__ rec_xr, int stride,
+                                             int nrec, T er[RecBatch<T>::n], T ei[RecBatch<T>::n]) {
   constexpr int B = RecBatch<T>::n;
   T a[B], b[B];
-  load_batch<T>(rec_x, a);
-  load_batch<T>(rec_xr, b);
+  load_batch<T>(rec_x, stride, a);
+  load_batch<T>(rec_xr, stride, b);
 #pragma unroll
   for (int j = 0; j < B; ++j) {
     er[j] = T(0);
@@ -295,9 +279,9 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
     // multihit slab products: conj(mod_x e^{i ph_x}) mod_xr e^{i ph_xr}
     const T* mh = static_cast<const T*>(L.mh_rec[buf]);
     T mx[B], mr[B];
-    load_batch<T>(mh + mh_index<T>(g, s, 0, x, 0), mx);
-    load_batch<T>(mh + mh_index<T>(g, s, 0, xr, 0), mr);
-    batch_phases<T>(mh + mh_index<T>(g, s, 1, x, 0), mh + mh_index<T>(g, s, 1, xr, 0), nrec, er, ei);
+    load_batch<T>(mh + mh_index<T>(g, s, 0, x, 0), g.Ns, mx);
+    load_batch<T>(mh + mh_index<T>(g, s, 0, xr, 0), g.Ns, mr);
+    batch_phases<T>(mh + mh_index<T>(g, s, 1, x, 0), mh + mh_index<T>(g, s, 1, xr, 0), g.Ns, nrec, er, ei);
 #pragma unroll
     for (int j = 0; j < B; ++j) {
       const T w = mx[j] * mr[j];
@@ -305,8 +289,8 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
       ei[j] *= w;
     }
   } else {
-    const T* rec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
-    batch_phases<T>(rec + static_cast<size_t>(x) * B, rec + static_cast<size_t>(xr) * B, nrec, er, ei);
+    const T* rec = static_cast<const T*>(L.theta_rec[buf]);
+    batch_phases<T>(rec + rec_index(g, s, x, 0), rec + rec_index(g, s, xr, 0), g.Ns, nrec, er, ei);
   }
   T sr = T(0), si = T(0);
 #pragma unroll
@@ -354,12 +338,12 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
   spatial_coords(g, x, &cx, &cy, &cz);
   const int rf = m.rf[f];
   const int xr = wrapc(cx + rf, g.L) + g.L * (cy + g.L * cz);
-  const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
+  const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]);
   const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
   using A = typename SlabAcc<T>::type;
   A* __restrict__ acc = reinterpret_cast<A*>(L.accO);
   T er[B], ei[B];
-  batch_phases<T>(trec + static_cast<size_t>(x) * B, trec + static_cast<size_t>(xr) * B, nrec, er, ei);
+  batch_phases<T>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, nrec, er, ei);
   const int x0x = wrapc(cx + rf / 2, g.L);
   const int nck = 2 * m.nc;
   const int b_end = min(m.np, (bg + 1) * kProbesPerThread);
@@ -379,7 +363,7 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
         if (q >= nck) break;
         const int ci = q >> 1, k = q & 1;
         T o[B];
-        load_batch<T>(osum + ((static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0) * B, o);
+        load_batch<T>(osum + rec_index(g, static_cast<size_t>(s * m.nc + ci) * 2 + k, x0, 0), g.Ns, o);
         T sr = T(0), si = T(0);
 #pragma unroll
         for (int j = 0; j < B; ++j) {
@@ -403,15 +387,12 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
 // separation), copies the records of every site any of its probes reaches
 // (the block's rows widened by the probes' y and z extent) into shared memory
 // once per component, and serves all probes from there: the L2 traffic of
-// the records falls by about the number of probes.  Each site's records
-// take their 16 x sizeof(T) bytes plus 16 of padding in the tile (an odd
-// number of 16-byte chunks), so that the 16-byte reads of a warp's
-// consecutive sites fall in distinct banks.  The
-// arithmetic is that of the per-site kernel, operation for operation.
+// the records falls by about the number of probes.  The tile keeps the
+// ring's slot-major order, [slot][tile row][x], so a warp's reads of
+// consecutive sites fall in distinct banks.  The arithmetic is that of the
+// per-site kernel, operation for operation.
 // ---------------------------------------------------------------------------
 constexpr int kTileThreads = 256;
-// tile bytes per site: the 16 records and a 16-byte pad
-__host__ __device__ constexpr int tile_site_bytes(bool fp64) { return 16 * (fp64 ? 8 : 4) + 16; }
 constexpr int kTileProbes = 4;              // slab sums loaded together
 constexpr size_t kTileSmemMax = 96 * 1024;  // per block
 
@@ -445,12 +426,11 @@ constexpr int tile_min_blocks() {
 
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_tile(const LatDesc* __restrict__ desc,
-                                                               const LatCtl* __restrict__ ctl, int buf, int nrec,
-                                                               int overwrite) {
+                                                                                    const LatCtl* __restrict__ ctl,
+                                                                                    int buf, int nrec,
+                                                                                    int overwrite) {
   constexpr int B = RecBatch<T>::n;
-  constexpr int SE = tile_site_bytes(sizeof(T) == 8) / static_cast<int>(sizeof(T));  // site stride in the tile
-  constexpr int CH = 16 / static_cast<int>(sizeof(T));                               // elements per 16-byte chunk
-  constexpr int NCH = B / CH;                                                         // chunks of a site's records
+  constexpr int CH = 16 / static_cast<int>(sizeof(T));  // elements per 16-byte chunk
   using A = typename SlabAcc<T>::type;
   extern __shared__ __align__(16) unsigned char tile_smem[];
   T* const tile = reinterpret_cast<T*>(tile_smem);
@@ -480,22 +460,23 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
   const int x = xx + g.L * (cy + g.L * cz);
   const int rf = m.rf[f];
   const int xr = wrapc(xx + rf, g.L) + g.L * (cy + g.L * cz);
-  const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]) + static_cast<size_t>(s) * g.Ns * B;
+  const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]);
   const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
   A* __restrict__ acc = reinterpret_cast<A*>(L.accO);
   T er[B], ei[B];
-  batch_phases<T>(trec + static_cast<size_t>(x) * B, trec + static_cast<size_t>(xr) * B, nrec, er, ei);
+  batch_phases<T>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, nrec, er, ei);
   const int col = wrapc(xx + rf / 2, g.L);
+  const int row_chunks = g.L / CH;                    // 16-byte chunks of an x row (L a multiple of CH)
+  const int copies = B * trows * row_chunks;          // per component
   for (int q = 0; q < nck; ++q) {
-    const int ci = q >> 1, k = q & 1;
-    const T* src = osum + (static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns * B;
-    for (int r = 0; r < trows; ++r) {  // tile row r: y = y0 + dymin + r mod tyn, z = z0 + dzmin + r / tyn
+    const size_t rowck = static_cast<size_t>(s * m.nc + (q >> 1)) * 2 + (q & 1);
+    for (int c = tid; c < copies; c += blockDim.x) {  // chunk c: slot j, tile row r, chunk u of the row
+      const int u = c % row_chunks, jr = c / row_chunks;
+      const int r = jr % trows, j = jr / trows;
       const int tz = r / tyn, ty = r - tz * tyn;
       const int yg = wrapc(y0 + pb.dymin + ty, g.L), zg = wrapc(z0 + pb.dzmin + tz, g.L);
-      const T* row_src = src + static_cast<size_t>(g.L) * (yg + g.L * zg) * B;
-      T* row_dst = tile + static_cast<size_t>(r) * g.L * SE;
-      for (int c = tid; c < g.L * NCH; c += blockDim.x)
-        cp_async16(row_dst + (c / NCH) * SE + (c % NCH) * CH, row_src + (c / NCH) * B + (c % NCH) * CH);
+      cp_async16(tile + (static_cast<size_t>(j) * trows + r) * g.L + u * CH,
+                 osum + rec_index(g, rowck, g.L * (yg + g.L * zg), j) + u * CH);
     }
     cp_async_commit();
     cp_async_wait_all();
@@ -513,27 +494,14 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
           const int b = b0 + i;
           if (b >= m.np) break;
           const int r = (yy + m.pdy[b] - pb.dymin) + tyn * (m.pdz[b] - pb.dzmin);
-          const T* o_s = tile + (static_cast<size_t>(r) * g.L + col) * SE;
-          T o[B];
-#pragma unroll
-          for (int c = 0; c < NCH; ++c) {
-            if constexpr (sizeof(T) == 4) {
-              const float4 v = *reinterpret_cast<const float4*>(o_s + c * CH);
-              o[4 * c] = v.x;
-              o[4 * c + 1] = v.y;
-              o[4 * c + 2] = v.z;
-              o[4 * c + 3] = v.w;
-            } else {
-              const double2 v = *reinterpret_cast<const double2*>(o_s + c * CH);
-              o[2 * c] = v.x;
-              o[2 * c + 1] = v.y;
-            }
-          }
+          const T* o_s = tile + static_cast<size_t>(r) * g.L + col;
+          const size_t jstride = static_cast<size_t>(trows) * g.L;
           T sr = T(0), si = T(0);
 #pragma unroll
           for (int j = 0; j < B; ++j) {
-            sr += er[j] * o[j];
-            si += ei[j] * o[j];
+            const T o = o_s[j * jstride];
+            sr += er[j] * o;
+            si += ei[j] * o;
           }
           acc_add(a[i], sr, si);
         }
@@ -547,16 +515,18 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
 }
 
 // Tile plan of a lattice for k_accum_O_tile: false when it does not apply
-// (L above the block, or a tile above kTileSmemMax).
+// (L above the block or not a whole number of 16-byte chunks of a row, or a
+// tile above kTileSmemMax).
 bool fold_tile_plan(bool fp64, int L, const int* pdy, const int* pdz, int np, int* blocks_x, size_t* smem) {
   if (np <= 0) {
     *blocks_x = 0;
     *smem = 0;
     return true;
   }
-  if (L > kTileThreads) return false;
+  const int tsz = fp64 ? 8 : 4;
+  if (L > kTileThreads || (L * tsz) % 16 != 0) return false;
   const ProbeBox pb = probe_box(pdy, pdz, np);
-  const size_t bytes = static_cast<size_t>(tile_rows(L, pb)) * L * tile_site_bytes(fp64);
+  const size_t bytes = static_cast<size_t>(RecBatch<float>::n) * tile_rows(L, pb) * L * tsz;
   if (bytes > kTileSmemMax) return false;
   const int ry = tile_rows_per_block(L);
   *blocks_x = (L + ry - 1) / ry * L;
@@ -738,17 +708,17 @@ __global__ void __launch_bounds__(256, TAIL ? 2 : kProdMinBlocks)
       for (int q = 0; q < kWChunk; ++q)
         if (q < nj) o[q] = fresh ? A{} : ocol[static_cast<size_t>(q) * g.Ns];
       if constexpr (TAIL) {
-        const T* trec = static_cast<const T*>(tail.trec) + static_cast<size_t>(s) * g.Ns * B;
+        const T* trec = static_cast<const T*>(tail.trec);
         const T* osum = static_cast<const T*>(tail.osum);
         T er[B], ei[B];
-        batch_phases<T>(trec + static_cast<size_t>(x) * B, trec + static_cast<size_t>(xr) * B, tail.nrec, er, ei);
+        batch_phases<T>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, tail.nrec, er, ei);
 #pragma unroll
         for (int q = 0; q < kWChunk; ++q) {
           if (q >= nj) break;
           const int j = j0 + q, b = j / (2 * m.nc), ci = (j >> 1) % m.nc, k = j & 1;
           const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
           T ov[B];
-          load_batch<T>(osum + ((static_cast<size_t>(s * m.nc + ci) * 2 + k) * g.Ns + x0) * B, ov);
+          load_batch<T>(osum + rec_index(g, static_cast<size_t>(s * m.nc + ci) * 2 + k, x0, 0), g.Ns, ov);
           T sr = T(0), si = T(0);
 #pragma unroll
           for (int r = 0; r < B; ++r) {

@@ -85,10 +85,19 @@ __device__ __forceinline__ void temporal_staples(const T* th, const Geom& g, con
   v[5] = th[soa(g, nu, shifted(g, c, nu, -1, 0, 0), op)];
 }
 
+// Ring of sub-update records, slot-major: row r of a ring buffer (a slab of
+// theta_rec, a (slab, component, Re/Im) of osum, a (slab, part) of mh_rec)
+// holds its RecBatch::n slots one after another, each a run of Ns sites, so
+// the record of one sub-update is written by consecutive threads at
+// consecutive addresses and a site's batch is read with stride Ns.
+__host__ __device__ __forceinline__ size_t rec_index(const Geom& g, size_t row, int x, int slot) {
+  return (row * RecBatch<float>::n + slot) * static_cast<size_t>(g.Ns) + x;
+}
+
 // Multihit ring slot of slab s, site x: modulus at part 0, phase at part 1.
 template <typename T>
 __device__ __forceinline__ size_t mh_index(const Geom& g, int s, int part, int x, int slot) {
-  return ((static_cast<size_t>(s) * 2 + part) * g.Ns + x) * RecBatch<T>::n + slot;
+  return rec_index(g, static_cast<size_t>(s) * 2 + part, x, slot);
 }
 
 // Warps of the record of one slab: warp xw covers the spatial sites
@@ -116,7 +125,7 @@ __device__ __forceinline__ void record_warp(const LatDesc& L, int buf, int slot,
     if (live) {
       double tsum = 0.0;
       for (int t = s * d; t < s * d + d; ++t) tsum += theta0(th, g, c[1], c[2], c[3], t);
-      static_cast<T*>(L.theta_rec[buf])[(static_cast<size_t>(s) * g.Ns + x) * RecBatch<T>::n + slot] =
+      static_cast<T*>(L.theta_rec[buf])[rec_index(g, s, x, slot)] =
           static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
     }
     return;
@@ -134,8 +143,8 @@ __device__ __forceinline__ void record_warp(const LatDesc& L, int buf, int slot,
       im += sn;
     }
     T* osum = static_cast<T*>(L.osum[buf]);
-    osum[((static_cast<size_t>(s * nc + y) * 2 + 0) * g.Ns + x) * RecBatch<T>::n + slot] = re;
-    osum[((static_cast<size_t>(s * nc + y) * 2 + 1) * g.Ns + x) * RecBatch<T>::n + slot] = im;
+    osum[rec_index(g, static_cast<size_t>(s * nc + y) * 2 + 0, x, slot)] = re;
+    osum[rec_index(g, static_cast<size_t>(s * nc + y) * 2 + 1, x, slot)] = im;
   }
 }
 

@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
         const int bi = b.cell(cx + 1, ry + 1, rz + 1);
         double tsum = 0.0;
         for (int tl = 0; tl < d; ++tl) tsum += static_cast<double>(buf[tl * b.vol + bi]);
-        static_cast<T*>(Ld.theta_rec[rec_buf])[(static_cast<size_t>(s) * g.Ns + x) * RecBatch<T>::n + slot] =
+        static_cast<T*>(Ld.theta_rec[rec_buf])[rec_index(g, s, x, slot)] =
             static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
         if (MH && Ld.mh_rec[rec_buf]) {
           T mod, ph;
@@ -397,8 +397,8 @@ __global__ void __launch_bounds__(kResThreads, 1)
             re += cs;
             im += sn;
           }
-          osum[((static_cast<size_t>(s * nc + y) * 2 + 0) * g.Ns + x) * RecBatch<T>::n + slot] = re;
-          osum[((static_cast<size_t>(s * nc + y) * 2 + 1) * g.Ns + x) * RecBatch<T>::n + slot] = im;
+          osum[rec_index(g, static_cast<size_t>(s * nc + y) * 2 + 0, x, slot)] = re;
+          osum[rec_index(g, static_cast<size_t>(s * nc + y) * 2 + 1, x, slot)] = im;
         };
         if (nc == 6) {  // all six components, rows in component order: planes known at compile time
           plane_sums(0, 1, 0);
