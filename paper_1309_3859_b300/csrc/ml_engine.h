@@ -28,9 +28,9 @@ struct LatState {
   int* d_lists = nullptr;
   double2 *accT = nullptr, *accO = nullptr, *acc4T = nullptr, *acc4O = nullptr;
   size_t accT_bytes = 0, accO_bytes = 0, acc4T_bytes = 0, acc4O_bytes = 0;
-  void* osum[2] = {nullptr, nullptr};       // record ring [nslab][nc][2][Ns][slots]
-  void* theta_rec[2] = {nullptr, nullptr};  // record ring [nslab][Ns][slots]
-  void* mh_rec[2] = {nullptr, nullptr};     // multihit ring [nslab][2][Ns][slots], or none
+  void* osum[2] = {nullptr, nullptr};       // record ring [nslab][nc][2][slots][Ns]
+  void* theta_rec[2] = {nullptr, nullptr};  // record ring [nslab][slots][Ns]
+  void* mh_rec[2] = {nullptr, nullptr};     // multihit ring [nslab][2][slots][Ns], or none
   size_t osum_bytes = 0, trec_bytes = 0;
   double* vac_part = nullptr;
   int nparts = 0;

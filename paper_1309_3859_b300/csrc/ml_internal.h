@@ -42,9 +42,9 @@ struct LatDesc {
   double metro_width;         // Metropolis proposal half-width
   int slab, nslab;            // inner slab thickness d and Nt / d
   int tile_start, tiles;      // sweep tiles of kSweepTile links
-  void* theta_rec[2];         // record ring buffers [nslab][Ns][slots]
-  void* mh_rec[2];            // multihit ring [nslab][2][Ns][slots] (modulus, phase); null: none
-  void* osum[2];              // [nslab][nc][2][Ns][slots], slots = rec_batch(fp64)
+  void* theta_rec[2];         // record ring buffers [nslab][slots][Ns]
+  void* mh_rec[2];            // multihit ring [nslab][2][slots][Ns] (modulus, phase); null: none
+  void* osum[2];              // [nslab][nc][2][slots][Ns], slots = rec_batch(fp64)
   double2* accT;              // inner slab sums: double2 (re, im), or for FP32
   double2* accO;              //   lattices float4 (re_hi, re_lo, im_hi, im_lo)
   double* vac_part;           // [nc * 2][nparts] block partials of the vacuum sums of a fold
