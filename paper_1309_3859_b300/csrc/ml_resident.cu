@@ -36,7 +36,7 @@
 
 namespace ml {
 
-constexpr int kResThreads = 1024;
+constexpr int kResThreads = 512;
 constexpr size_t kResSmemMax = 200 * 1024;  // per CTA
 
 // x / div for x div < 2^40 with mdiv = floor(2^40 / div) + 1
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
   // mirror[mstart[j] .. mstart[j+1]), cluster addresses of their slot-0 cells)
   int* mstart = reinterpret_cast<int*>(buf + static_cast<size_t>(K) * b.vol);
   uint32_t* mirror = reinterpret_cast<uint32_t*>(mstart + b.L * b.yl_full * b.zl_full + 1);
-  __shared__ int wsum[kResThreads / 32];
+  __shared__ int wsum[32];  // one per warp; warp 0 scans all 32 entries
   const uint32_t base = shared_addr(buf);
   // magic divisors; every dividend times its divisor stays below 2^40 (the
   // box fits in shared memory, so all counts are far below 2^20)
