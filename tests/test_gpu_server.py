@@ -3,6 +3,7 @@
 * Each request's records are bit-identical to the same parameters run alone,
   with requests arriving while others run (different phases share ticks),
   mixed sizes, couplings, schedules and two-level requests.
+* Multihit and Metropolis requests in the mix, bit-identical to alone.
 * Admission by HBM budget: requests queue until memory frees up, all finish,
   usage never exceeds the budget; a request larger than the budget fails with
   ML_ENOMEM; mismatched precision is rejected.
@@ -61,6 +62,22 @@ def test_server_matches_alone(fp64):
     for i in range(n):
         ref = run_alone(ps[i], *SCHED[i])
         assert np.array_equal(results[i], ref), i
+
+
+def test_server_multihit_and_metropolis_requests_match_alone():
+    """Requests with the analytic multihit (Section II.C) and with the
+    Metropolis update, mixed with plain ones, give the records of the same
+    parameters run alone."""
+    ps = [job_params(i, False) for i in range(4)]
+    ps[0].multihit = 1
+    ps[1].multihit = 1
+    ps[2].update, ps[2].metro_hits, ps[2].metro_width = ml.ML_UPDATE_METROPOLIS, 3, 1.4
+    sched = [(2, 2), (1, 1), (2, 1), (0, 2)]
+    with ml.Server(budget_bytes=256 << 20, fp64=False) as srv:
+        jobs = [srv.submit(p, *sc) for p, sc in zip(ps, sched)]
+        results = [srv.wait(j, timeout_s=120) for j in jobs]
+    for i, p in enumerate(ps):
+        assert np.array_equal(results[i], run_alone(p, *sched[i])), i
 
 
 def test_server_budget_admission_and_limits():
