@@ -79,7 +79,11 @@ __device__ __forceinline__ bool bf_trial(float kappa, float s, uint32_t a, uint3
 
 // Best & Fisher (Applied Statistics 28 (1979) 152): psi with density
 // exp(kappa cos psi) / (2 pi I0(kappa)).  Returns false at the trial cap.
-template <typename T>
+// EAGER (FP32): Philox blocks 0 and 1 are drawn together before the first
+// trial, so their two dependent round chains overlap; the trials are still
+// taken in order, so the angle is the one-at-a-time sampler's.  For
+// latency-bound callers with idle issue slots.
+template <typename T, bool EAGER = false>
 __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsigned long long n, uint32_t k0,
                                           uint32_t k1, T* psi) {
   using P = Prec<T>;
@@ -116,7 +120,21 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
     }
     const float s = bf_envelope(kappa);
     static_assert(kMaxTrials % 2 == 0, "trials come in pairs per Philox block");
-    for (int j = 0; j < kMaxTrials / 2; ++j) {
+    int j0 = 0;
+    if constexpr (EAGER) {
+      const U4 o0 = Draws<float>::block(site, mu, n, 0, k0, k1);
+      const U4 o1 = Draws<float>::block(site, mu, n, 1, k0, k1);
+      float f;
+      bool neg;
+      if (bf_trial(kappa, s, o0.x, o0.y, &f, &neg) || bf_trial(kappa, s, o0.z, o0.w, &f, &neg) ||
+          bf_trial(kappa, s, o1.x, o1.y, &f, &neg) || bf_trial(kappa, s, o1.z, o1.w, &f, &neg)) {
+        const float a = acosf(f);
+        *psi = neg ? -a : a;
+        return true;
+      }
+      j0 = 2;
+    }
+    for (int j = j0; j < kMaxTrials / 2; ++j) {
       const U4 o = Draws<float>::block(site, mu, n, j, k0, k1);
       float f;
       bool neg;
@@ -207,7 +225,7 @@ __device__ __forceinline__ void staple_sum(int mu, Staples&& staples, T* k, T* a
   *alpha = P::atan2_(wi, wr);
 }
 
-template <typename T, int KIND, typename Staples, typename Self>
+template <typename T, int KIND, bool EAGER = false, typename Staples, typename Self>
 __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&& self, uint32_t site,
                                                unsigned long long n, uint32_t k0, uint32_t k1, T beta,
                                                int* __restrict__ err, T* out, T w = T(0), int hits = 0) {
@@ -224,7 +242,7 @@ __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&&
   staple_sum<T>(mu, staples, &k, &alpha);
   if (KIND == 0) {
     T psi;
-    if (!von_mises<T>(beta * k, site, mu, n, k0, k1, &psi)) {
+    if (!von_mises<T, EAGER>(beta * k, site, mu, n, k0, k1, &psi)) {
       atomicOr(err, kErrReject);
       return false;
     }
