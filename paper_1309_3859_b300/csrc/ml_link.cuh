@@ -83,9 +83,11 @@ __device__ __forceinline__ bool bf_trial(float kappa, float s, uint32_t a, uint3
 // trial, so their two dependent round chains overlap; the trials are still
 // taken in order, so the angle is the one-at-a-time sampler's.  For
 // latency-bound callers with idle issue slots.
-template <typename T, bool EAGER = false>
+// pre: EAGER > 0 only, the link's blocks 0 and 1 when the caller drew them
+// before its staple sum (so the rounds overlap that work too).
+template <typename T, int EAGER = 0>
 __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsigned long long n, uint32_t k0,
-                                          uint32_t k1, T* psi) {
+                                          uint32_t k1, T* psi, const U4* pre = nullptr) {
   using P = Prec<T>;
   if constexpr (P::fp64) {
     double u1, u2;
@@ -114,16 +116,16 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
     return false;
   } else {
     if (kappa < P::kappa_tiny) {
-      const U4 o = Draws<float>::block(site, mu, n, 0, k0, k1);
+      const U4 o = (EAGER > 0 && pre) ? pre[0] : Draws<float>::block(site, mu, n, 0, k0, k1);
       *psi = kPiF * (2.0f * uniform23(o.x) - 1.0f);
       return true;
     }
     const float s = bf_envelope(kappa);
     static_assert(kMaxTrials % 2 == 0, "trials come in pairs per Philox block");
     int j0 = 0;
-    if constexpr (EAGER) {
-      const U4 o0 = Draws<float>::block(site, mu, n, 0, k0, k1);
-      const U4 o1 = Draws<float>::block(site, mu, n, 1, k0, k1);
+    if constexpr (EAGER > 0) {
+      const U4 o0 = pre ? pre[0] : Draws<float>::block(site, mu, n, 0, k0, k1);
+      const U4 o1 = pre ? pre[1] : Draws<float>::block(site, mu, n, 1, k0, k1);
       float f;
       bool neg;
       if (bf_trial(kappa, s, o0.x, o0.y, &f, &neg) || bf_trial(kappa, s, o0.z, o0.w, &f, &neg) ||
@@ -225,7 +227,10 @@ __device__ __forceinline__ void staple_sum(int mu, Staples&& staples, T* k, T* a
   *alpha = P::atan2_(wi, wr);
 }
 
-template <typename T, int KIND, bool EAGER = false, typename Staples, typename Self>
+// EAGER: 0 one Philox block at a time; 1 the first two together (von_mises);
+// 2 those two drawn before the staple sum (latency-bound callers: the
+// cluster-resident kernel; issue-bound ones lose by the registers it takes)
+template <typename T, int KIND, int EAGER = 0, typename Staples, typename Self>
 __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&& self, uint32_t site,
                                                unsigned long long n, uint32_t k0, uint32_t k1, T beta,
                                                int* __restrict__ err, T* out, T w = T(0), int hits = 0) {
@@ -238,11 +243,19 @@ __device__ __forceinline__ bool new_link_angle(int mu, Staples&& staples, Self&&
     *out = P::wrap(T(-2) * P::atan2_(wi, wr) - self());
     return true;
   }
+  // the eager heatbath's first two blocks depend on (site, mu, n) only:
+  // drawn before the staple sum, their rounds overlap its loads and sincos
+  U4 pre[2];
+  constexpr bool kPre = EAGER == 2 && KIND == 0 && !Prec<T>::fp64;
+  if constexpr (kPre) {
+    pre[0] = Draws<float>::block(site, mu, n, 0, k0, k1);
+    pre[1] = Draws<float>::block(site, mu, n, 1, k0, k1);
+  }
   T k, alpha;
   staple_sum<T>(mu, staples, &k, &alpha);
   if (KIND == 0) {
     T psi;
-    if (!von_mises<T, EAGER>(beta * k, site, mu, n, k0, k1, &psi)) {
+    if (!von_mises<T, EAGER>(beta * k, site, mu, n, k0, k1, &psi, kPre ? pre : nullptr)) {
       atomicOr(err, kErrReject);
       return false;
     }

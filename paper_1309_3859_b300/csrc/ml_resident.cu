@@ -180,7 +180,7 @@ __device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* m
       (KIND == 0 && rule.metropolis)
           ? new_link_angle<T, 2>(mu, staples, cur, site, n, k0, k1, beta, err, &out, static_cast<T>(rule.width),
                                  rule.hits)
-          : new_link_angle<T, KIND, true>(mu, staples, cur, site, n, k0, k1, beta, err, &out);
+          : new_link_angle<T, KIND, 2>(mu, staples, cur, site, n, k0, k1, beta, err, &out);
   if (moved) {
     *self = out;
     const uint32_t soff = static_cast<uint32_t>(sl * b.vol * sizeof(T));

@@ -69,7 +69,7 @@ __device__ __forceinline__ void update_link_mu(T* th, const Geom& g, int parity,
     if (new_link_angle<T, 2>(mu, staples, cur, static_cast<uint32_t>(i), n, k0, k1, beta, err, &out,
                              static_cast<T>(rule.width), rule.hits))
       *self = out;
-  } else if (new_link_angle<T, KIND, true>(mu, staples, cur, static_cast<uint32_t>(i), n, k0, k1, beta, err, &out)) {
+  } else if (new_link_angle<T, KIND, 1>(mu, staples, cur, static_cast<uint32_t>(i), n, k0, k1, beta, err, &out)) {
     *self = out;
   }
 }
@@ -174,7 +174,7 @@ __device__ __forceinline__ void update_pair_mu(T* th, const Geom& g, int parity,
     if (KIND == 0 && rule.metropolis)
       return new_link_angle<T, 2>(mu, staples, curv, static_cast<uint32_t>(i), n, k0, k1, beta, err, out,
                                   static_cast<T>(rule.width), rule.hits);
-    return new_link_angle<T, KIND, true>(mu, staples, curv, static_cast<uint32_t>(i), n, k0, k1, beta, err, out);
+    return new_link_angle<T, KIND, 1>(mu, staples, curv, static_cast<uint32_t>(i), n, k0, k1, beta, err, out);
   };
   V2 o = cur;
   T out;
