@@ -4,17 +4,19 @@
 // II.C, Algorithm 1) the time slabs of a lattice evolve independently during
 // a sub-update.  One thread-block cluster owns one slab.  Its CTAs split the
 // slab's spatial volume into bricks (all x, a range of y, a range of z); each
-// CTA holds its brick plus a one-site ghost frame for every link the slab's
-// updates read, in shared memory, for the whole launch:
+// CTA holds its brick plus a one-row ghost frame in y and z for every link
+// the slab's updates read, in shared memory, for the whole launch:
 //
-//   box cell (ix, iy, iz), ix in [0, L+2), iy in [0, ylen+2), iz in [0, zlen+2)
-//   <-> site ((ix-1) mod L, (y0+iy-1) mod L, (z0+iz-1) mod L)
+//   box cell (ix, iy, iz), ix in [0, L), iy in [0, ylen+2), iz in [0, zlen+2)
+//   <-> site (ix, (y0+iy-1) mod L, (z0+iz-1) mod L)
 //   buf[slot][cell],  slot = tl              U_0 at local time tl in [0, d)
 //                     slot = d + 3 tl + i-1  U_i at local time tl in [0, d]
 //
 // (4d + 3 slots; U_i at tl = 0 and tl = d are the frozen boundary links), so
-// every neighbour of a site is at a constant offset (+-1, +-(L+2),
-// +-(L+2)(ylen+2)) and every staple load is a plain shared-memory load.
+// every neighbour of a site is at a constant offset in y (+-L) and z
+// (+-L(ylen+2)), and in x at +-1 or, across the periodic seam, -+(L-1): every
+// staple load is a plain shared-memory load.  Rows span the whole x extent,
+// so x needs no ghost cells (and no mirror stores).
 // A thread that moves a link also stores the new angle into every box cell
 // that mirrors it (in its own or another CTA's shared memory, through the
 // cluster's shared-memory window), so after the hardware cluster barrier that
@@ -59,7 +61,7 @@ static BrickSplit brick_split(int L, int cs) {
     for (int nz = 1; nz <= std::min(L, cs / ny); ++nz) {
       const int yl = (L + ny - 1) / ny, zl = (L + nz - 1) / nz;
       const long long vol = static_cast<long long>(yl) * zl;
-      const int box = (L + 2) * (yl + 2) * (zl + 2);
+      const int box = L * (yl + 2) * (zl + 2);
       if (best_vol < 0 || vol < best_vol || (vol == best_vol && box < best.box)) {
         best_vol = vol;
         best = BrickSplit{ny, nz, yl, zl, box};
@@ -77,7 +79,7 @@ static BrickSplit brick_split(int L, int cs) {
 template <typename F>
 __host__ __device__ __forceinline__ void for_each_mirror(int L, int ny, int nz, int ylf, int zlf, int ry, int rz,
                                                          int cx, int cy, int cz, F&& emit) {
-  const int bx = L + 2, by = ylf + 2, bz = zlf + 2;
+  const int bx = L, by = ylf + 2, bz = zlf + 2;
   int yq[6], yi[6], zq[6], zi[6], ny_hit = 0, nz_hit = 0;
   for (int q = 0; q < ny; ++q)
     for (int k = -1; k <= 1; ++k) {
@@ -95,17 +97,13 @@ __host__ __device__ __forceinline__ void for_each_mirror(int L, int ny, int nz, 
         zi[nz_hit++] = iz;
       }
     }
-  int xi[3] = {cx + 1, 0, 0}, nx_hit = 1;
-  if (cx == L - 1) xi[nx_hit++] = 0;
-  if (cx == 0) xi[nx_hit++] = L + 1;
   const int own_y = cy - ry * ylf + 1, own_z = cz - rz * zlf + 1;
   for (int a = 0; a < ny_hit; ++a)
-    for (int c = 0; c < nz_hit; ++c)
-      for (int e = 0; e < nx_hit; ++e) {
-        const int r = yq[a] + ny * zq[c];
-        if (r == ry + ny * rz && e == 0 && yi[a] == own_y && zi[c] == own_z) continue;  // the owner's own cell
-        emit(r, xi[e] + bx * (yi[a] + by * zi[c]));
-      }
+    for (int c = 0; c < nz_hit; ++c) {
+      const int r = yq[a] + ny * zq[c];
+      if (r == ry + ny * rz && yi[a] == own_y && zi[c] == own_z) continue;  // the owner's own cell
+      emit(r, cx + bx * (yi[a] + by * zi[c]));
+    }
 }
 
 struct MirrorCount {
@@ -130,12 +128,22 @@ static int mirror_capacity(int L, const BrickSplit& sp) {
 
 // Geometry of one CTA's box.
 struct Box {
-  int L, bx, by, bxy, vol;  // box extents (bx = L + 2, by = ylen + 2) and volume
+  int L, bx, by, bxy, vol;  // box extents (bx = L, by = ylen + 2) and volume
   int y0, z0, ylen, zlen;   // owned rows (ylen, zlen: this CTA's, may be 0)
   int ny, yl_full, zl_full; // brick grid (owner of row y: y / yl_full)
   int d;
   __device__ __forceinline__ int slot(int rho, int tl) const { return rho == 0 ? tl : d + 3 * tl + rho - 1; }
-  __device__ __forceinline__ int off(int rho) const { return rho == 0 ? 0 : (rho == 1 ? 1 : (rho == 2 ? bx : bxy)); }
+  // cell offsets of x + rho and x - rho (time: 0, the slot changes instead);
+  // xp, xm: the x offsets of the site's column (+1 and -1 inside the row)
+  __device__ __forceinline__ int fwd(int rho, int xp) const {
+    return rho == 0 ? 0 : (rho == 1 ? xp : (rho == 2 ? bx : bxy));
+  }
+  __device__ __forceinline__ int bwd(int rho, int xm) const {
+    return rho == 0 ? 0 : (rho == 1 ? xm : (rho == 2 ? -bx : -bxy));
+  }
+  // the x offsets of column cx: the periodic seam stays inside the row
+  __device__ __forceinline__ int xplus(int cx) const { return cx == L - 1 ? 1 - L : 1; }
+  __device__ __forceinline__ int xminus(int cx) const { return cx == 0 ? L - 1 : -1; }
   __device__ __forceinline__ int cell(int ix, int iy, int iz) const { return ix + bx * (iy + by * iz); }
 };
 
@@ -146,20 +154,22 @@ __device__ __forceinline__ void st_cluster(uint32_t a, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
-// Staple angles of U_mu at box cell bi, local time tl, for plane (mu, nu),
-// in the order of the link update.
+// Staple angles of U_mu at box cell bi (x offsets xp, xm), local time tl,
+// for plane (mu, nu), in the order of the link update.  x + mu - nu keeps
+// the x column of x whenever nu = 1 (mu != nu), so xm applies to it too.
 template <typename T>
-__device__ __forceinline__ void box_staples(const Box& b, const T* buf, int mu, int tl, int bi, int nu, T w[6]) {
+__device__ __forceinline__ void box_staples(const Box& b, const T* buf, int mu, int tl, int bi, int xp, int xm, int nu,
+                                            T w[6]) {
   const int tp = tl + (mu == 0);  // x + mu
-  const int bp = bi + b.off(mu);
+  const int bp = bi + b.fwd(mu, xp);
   auto at = [&](int rho, int t_, int c) { return buf[b.slot(rho, t_) * b.vol + c]; };
-  const int dt = nu == 0, o = b.off(nu);
-  w[0] = at(nu, tp, bp);            // theta_nu(x + mu)
-  w[1] = at(mu, tl + dt, bi + o);   // theta_mu(x + nu)
-  w[2] = at(nu, tl, bi);            // theta_nu(x)
-  w[3] = at(nu, tp - dt, bp - o);   // theta_nu(x + mu - nu)
-  w[4] = at(mu, tl - dt, bi - o);   // theta_mu(x - nu)
-  w[5] = at(nu, tl - dt, bi - o);   // theta_nu(x - nu)
+  const int dt = nu == 0, of = b.fwd(nu, xp), ob = b.bwd(nu, xm);
+  w[0] = at(nu, tp, bp);             // theta_nu(x + mu)
+  w[1] = at(mu, tl + dt, bi + of);   // theta_mu(x + nu)
+  w[2] = at(nu, tl, bi);             // theta_nu(x)
+  w[3] = at(nu, tp - dt, bp + ob);   // theta_nu(x + mu - nu)
+  w[4] = at(mu, tl - dt, bi + ob);   // theta_mu(x - nu)
+  w[5] = at(nu, tl - dt, bi + ob);   // theta_nu(x - nu)
 }
 
 // Update of the link U_mu at box cell bi, local time tl; the new angle also
@@ -168,10 +178,10 @@ __device__ __forceinline__ void box_staples(const Box& b, const T* buf, int mu, 
 // every plane resolve at compile time.
 template <typename T, int KIND, int MU>
 __device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* mirror, int m0, int m1, int tl,
-                                         int bi, uint32_t site, unsigned long long n, uint32_t k0, uint32_t k1,
+                                         int bi, int xp, int xm, uint32_t site, unsigned long long n, uint32_t k0, uint32_t k1,
                                          T beta, int* err, const UpdateRule& rule) {
   constexpr int mu = MU;
-  auto staples = [&](int nu, T w[6]) { box_staples<T>(b, buf, mu, tl, bi, nu, w); };
+  auto staples = [&](int nu, T w[6]) { box_staples<T>(b, buf, mu, tl, bi, xp, xm, nu, w); };
   const int sl = b.slot(mu, tl);
   T* self = buf + sl * b.vol + bi;
   T out;
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const int nz = units[u].w;
   b.yl_full = (g.L + b.ny - 1) / b.ny;
   b.zl_full = (g.L + nz - 1) / nz;
-  b.bx = g.L + 2;
+  b.bx = g.L;
   b.by = b.yl_full + 2;
   b.bxy = b.bx * b.by;
   b.vol = b.bxy * (b.zl_full + 2);
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
   for (int c = threadIdx.x; active && c < b.vol; c += blockDim.x) {
     const int q = fdiv(c, m_bx), ix = c - q * b.bx;
     const int iz = fdiv(q, m_by), iy = q - iz * b.by;
-    const int cx = wrapc(ix - 1, g.L), cy = wrapc(b.y0 + iy - 1, g.L), cz = wrapc(b.z0 + iz - 1, g.L);
+    const int cx = ix, cy = wrapc(b.y0 + iy - 1, g.L), cz = wrapc(b.z0 + iz - 1, g.L);
     const int x = cx + g.L * (cy + g.L * cz);
     for (int sl = 0; sl < K; ++sl) {
       int rho = 0, tl = sl;
@@ -338,13 +348,16 @@ __global__ void __launch_bounds__(kResThreads, 1)
       const int rz = fdiv(row, m_yl), ry = row - rz * b.ylen;
       const int cy = b.y0 + ry, cz = b.z0 + rz;
       const int cx = cx0 + (((cy + cz + t) & 1) ^ par);
-      const int bi = b.cell(cx + 1, ry + 1, rz + 1);
+      const int bi = b.cell(cx, ry + 1, rz + 1);
+      const int xp = b.xplus(cx), xm = b.xminus(cx);
       const int jo = cx + g.L * row;  // owned-site index
       const uint32_t site = static_cast<uint32_t>(cx + g.L * (cy + g.L * cz) + g.Ns * t);
       if (sweep == 0)
-        box_link<T, 0, mu>(b, buf, mirror, mstart[jo], mstart[jo + 1], tl, bi, site, n, k0, k1, beta, err, rule);
+        box_link<T, 0, mu>(b, buf, mirror, mstart[jo], mstart[jo + 1], tl, bi, xp, xm, site, n, k0, k1, beta, err,
+                           rule);
       else
-        box_link<T, 1, mu>(b, buf, mirror, mstart[jo], mstart[jo + 1], tl, bi, site, n, k0, k1, beta, err, rule);
+        box_link<T, 1, mu>(b, buf, mirror, mstart[jo], mstart[jo + 1], tl, bi, xp, xm, site, n, k0, k1, beta, err,
+                           rule);
     }
   };
   for (int round = 0; round < n_rec; ++round) {
@@ -373,14 +386,15 @@ __global__ void __launch_bounds__(kResThreads, 1)
         const int row = fdiv(j, m_L), cx = j - row * g.L;
         const int rz = fdiv(row, m_yl), ry = row - rz * b.ylen;
         const int x = cx + g.L * (b.y0 + ry + g.L * (b.z0 + rz));
-        const int bi = b.cell(cx + 1, ry + 1, rz + 1);
+        const int bi = b.cell(cx, ry + 1, rz + 1);
+        const int xp = b.xplus(cx), xm = b.xminus(cx);
         double tsum = 0.0;
         for (int tl = 0; tl < d; ++tl) tsum += static_cast<double>(buf[tl * b.vol + bi]);
         static_cast<T*>(Ld.theta_rec[rec_buf])[rec_index(g, s, x, slot)] =
             static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
         if (MH && Ld.mh_rec[rec_buf]) {
           T mod, ph;
-          multihit_slab<T>(0, d, beta, [&](int tl, int nu, T v[6]) { box_staples<T>(b, buf, 0, tl, bi, nu, v); },
+          multihit_slab<T>(0, d, beta, [&](int tl, int nu, T v[6]) { box_staples<T>(b, buf, 0, tl, bi, xp, xm, nu, v); },
                            &mod, &ph);
           T* mh = static_cast<T*>(Ld.mh_rec[rec_buf]);
           mh[mh_index<T>(g, s, 0, x, slot)] = mod;
@@ -390,8 +404,9 @@ __global__ void __launch_bounds__(kResThreads, 1)
         auto plane_sums = [&](int mu, int nu, int y) {
           T re = T(0), im = T(0);
           for (int tl = 0; tl < d; ++tl) {
-            const T a = buf[b.slot(mu, tl) * b.vol + bi] + buf[b.slot(nu, tl + (mu == 0)) * b.vol + bi + b.off(mu)] -
-                        buf[b.slot(mu, tl) * b.vol + bi + b.off(nu)] - buf[b.slot(nu, tl) * b.vol + bi];
+            const T a = buf[b.slot(mu, tl) * b.vol + bi] +
+                        buf[b.slot(nu, tl + (mu == 0)) * b.vol + bi + b.fwd(mu, xp)] -
+                        buf[b.slot(mu, tl) * b.vol + bi + b.fwd(nu, xp)] - buf[b.slot(nu, tl) * b.vol + bi];
             T sn, cs;
             P::sincos_(a, &sn, &cs);
             re += cs;
@@ -434,7 +449,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
     const int rz = fdiv(row, m_yl), ry = row - rz * b.ylen;
     const int cy = b.y0 + ry, cz = b.z0 + rz, t = t0 + tl;
     th[soa(g, rho, cx + g.L * (cy + g.L * cz) + g.Ns * t, (cx + cy + cz + t) & 1)] =
-        buf[sl * b.vol + b.cell(cx + 1, ry + 1, rz + 1)];
+        buf[sl * b.vol + b.cell(cx, ry + 1, rz + 1)];
   }
   // every CTA of every unit read the sweep counters before its cluster's
   // barriers; the last unit to arrive advances them
