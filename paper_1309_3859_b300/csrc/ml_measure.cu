@@ -48,10 +48,11 @@ __device__ __forceinline__ double2 unit_phase(double phi) {
 // A site's batch: the slots at p, p + Ns, p + 2 Ns, ... (p = rec_index(.., 0)),
 // each load coalesced over a warp's consecutive sites.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void load_batch(const T* __restrict__ p, int stride, T v[RecBatch<T>::n]) {
+// (the first NB slots: a batch known to hold fewer records loads fewer)
+template <typename T, int NB = RecBatch<T>::n>
+__device__ __forceinline__ void load_batch(const T* __restrict__ p, int stride, T v[NB]) {
 #pragma unroll
-  for (int j = 0; j < RecBatch<T>::n; ++j) v[j] = __ldg(p + static_cast<size_t>(j) * stride);
+  for (int j = 0; j < NB; ++j) v[j] = __ldg(p + static_cast<size_t>(j) * stride);
 }
 
 // Record of each lattice's configuration into ring slot `slot` of buffer
@@ -230,13 +231,14 @@ __device__ __forceinline__ void acc_add(float4& a, float re, float im) {
 }
 
 // e^{i (Theta(x + r) - Theta(x))} for the first nrec records, zero beyond
-template <typename T>
+// (of the first NB slots)
+template <typename T, int NB = RecBatch<T>::n>
 __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const T* __restrict__ rec_xr, int stride,
-                                             int nrec, T er[RecBatch<T>::n], T ei[RecBatch<T>::n]) {
-  constexpr int B = RecBatch<T>::n;
+                                             int nrec, T er[NB], T ei[NB]) {
+  constexpr int B = NB;
   T a[B], b[B];
-  load_batch<T>(rec_x, stride, a);
-  load_batch<T>(rec_xr, stride, b);
+  load_batch<T, B>(rec_x, stride, a);
+  load_batch<T, B>(rec_xr, stride, b);
 #pragma unroll
   for (int j = 0; j < B; ++j) {
     er[j] = T(0);
@@ -654,7 +656,9 @@ __global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayou
 // records of ring buffer (trec, osum) exactly as k_accum_O_table would have
 // (same batch sum, same accumulator update), without writing them back: the
 // measurement's final fold of the field insertions and the products in one
-// pass over the slab sums.
+// pass over the slab sums.  TB: 0 without a tail, else the ring slots read
+// (nrec rounded up to 4, 8 or 16; the slots beyond nrec add exact zeros, so
+// fewer of them leave every sum unchanged).
 template <typename A>
 struct RecOf {
   using type = double;
@@ -664,15 +668,17 @@ struct RecOf<float4> {
   using type = float;
 };
 
-template <typename A, bool TAIL>
-__global__ void __launch_bounds__(256, TAIL ? 2 : kProdMinBlocks)
+template <typename A, int TB>
+__global__ void __launch_bounds__(256, TB ? 2 : kProdMinBlocks)
     k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT, const A* __restrict__ accO,
                  double inv_n, double2* __restrict__ partial, int nwarps, ProductTail tail) {
   using M = AccMath<A>;
   using C = typename M::cplx;
   using R = typename M::real;
   using T = typename RecOf<A>::type;
-  constexpr int B = RecBatch<T>::n;
+  constexpr bool TAIL = TB > 0;
+  constexpr int B = TAIL ? TB : 1;
+  static_assert(B <= RecBatch<T>::n, "a tail holds at most one ring buffer");
   const R in = static_cast<R>(inv_n);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = x < g.Ns;
@@ -711,14 +717,14 @@ __global__ void __launch_bounds__(256, TAIL ? 2 : kProdMinBlocks)
         const T* trec = static_cast<const T*>(tail.trec);
         const T* osum = static_cast<const T*>(tail.osum);
         T er[B], ei[B];
-        batch_phases<T>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, tail.nrec, er, ei);
+        batch_phases<T, B>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, tail.nrec, er, ei);
 #pragma unroll
         for (int q = 0; q < kWChunk; ++q) {
           if (q >= nj) break;
           const int j = j0 + q, b = j / (2 * m.nc), ci = (j >> 1) % m.nc, k = j & 1;
           const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
           T ov[B];
-          load_batch<T>(osum + rec_index(g, static_cast<size_t>(s * m.nc + ci) * 2 + k, x0, 0), g.Ns, ov);
+          load_batch<T, B>(osum + rec_index(g, static_cast<size_t>(s * m.nc + ci) * 2 + k, x0, 0), g.Ns, ov);
           T sr = T(0), si = T(0);
 #pragma unroll
           for (int r = 0; r < B; ++r) {
@@ -985,6 +991,21 @@ void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, bool
   count_launches(1);
 }
 
+// k_products_W with the tail's slot count
+template <typename A>
+static void launch_products_W(dim3 grid, const Geom& g, int nslab, const MeasLayout& m, const A* accT, const A* accO,
+                              double inv_n, double2* partial, int nwarps, const ProductTail& tail, cudaStream_t s) {
+  if (tail.nrec <= 0)
+    k_products_W<A, 0><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
+  else if (tail.nrec <= 4)
+    k_products_W<A, 4><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
+  else if (tail.nrec <= 8)
+    k_products_W<A, 8><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
+  else
+    k_products_W<A, RecBatch<typename RecOf<A>::type>::n><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n,
+                                                                               partial, nwarps, tail);
+}
+
 template <typename A>
 static void products_of(const Geom& g, int nslab, const MeasLayout& m, const A* accT, const A* accO, double inv_n,
                         double2* partial, int nb, int nwarps, const ProductTail& tail, bool W_done,
@@ -994,10 +1015,7 @@ static void products_of(const Geom& g, int nslab, const MeasLayout& m, const A* 
   const int nW = m.np * m.nc * 2;
   if (m.nrf > 0 && nW > 0 && !W_done) {
     const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
-    if (tail.nrec > 0)
-      k_products_W<A, true><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
-    else
-      k_products_W<A, false><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
+    launch_products_W(grid, g, nslab, m, accT, accO, inv_n, partial, nwarps, tail, s);
     count_launches(1);
   }
 }
@@ -1028,11 +1046,11 @@ void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool pairs, 
   ProductTail t = tail;
   t.overwrite = 1;  // this buffer's records alone
   if (pairs)
-    k_products_W<float4, true><<<grid, 256, 0, s>>>(g, nslab, m, static_cast<const float4*>(accT), nullptr, inv_n,
-                                                    partial, nb * 8, t);
+    launch_products_W(grid, g, nslab, m, static_cast<const float4*>(accT), static_cast<const float4*>(nullptr), inv_n,
+                      partial, nb * 8, t, s);
   else
-    k_products_W<double2, true><<<grid, 256, 0, s>>>(g, nslab, m, static_cast<const double2*>(accT), nullptr, inv_n,
-                                                     partial, nb * 8, t);
+    launch_products_W(grid, g, nslab, m, static_cast<const double2*>(accT), static_cast<const double2*>(nullptr),
+                      inv_n, partial, nb * 8, t, s);
   count_launches(1);
 }
 
