@@ -16,6 +16,7 @@
 // reductions over sites are warp-shuffle trees writing per-warp partials,
 // followed by fixed-order sums: results do not depend on scheduling.
 #include <algorithm>
+#include <type_traits>
 
 #include "ml_record.cuh"
 #include "ml_sync.cuh"
@@ -669,7 +670,7 @@ struct RecOf<float4> {
 };
 
 template <typename A, int TB>
-__global__ void __launch_bounds__(256, TB ? 2 : kProdMinBlocks)
+__global__ void __launch_bounds__(256, TB == 0 || (TB == 4 && std::is_same<A, float4>::value) ? kProdMinBlocks : 2)
     k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT, const A* __restrict__ accO,
                  double inv_n, double2* __restrict__ partial, int nwarps, ProductTail tail) {
   using M = AccMath<A>;
@@ -698,11 +699,21 @@ __global__ void __launch_bounds__(256, TB ? 2 : kProdMinBlocks)
       suf[s] = run;
       run = cmul(run, slab_factor<M>(M::value(tcol[s * tstride]), in));
     }
-    int cx = 0, cy = 0, cz = 0, xr = 0, x0x = 0;
+    // tail: the partner site x + rf of the phases, and per value q its
+    // insertion site x0 (probe b) and osum row (ci, k) within a slab, all
+    // independent of the slab
+    int xr = 0, x0q[kWChunk], rowq[kWChunk];
     if constexpr (TAIL) {
+      int cx, cy, cz;
       spatial_coords(g, x, &cx, &cy, &cz);
       xr = wrapc(cx + m.rf[f], g.L) + g.L * (cy + g.L * cz);
-      x0x = wrapc(cx + m.rf[f] / 2, g.L);
+      const int x0x = wrapc(cx + m.rf[f] / 2, g.L);
+#pragma unroll
+      for (int q = 0; q < kWChunk; ++q) {
+        const int j = min(j0 + q, nW - 1), b = j / (2 * m.nc);
+        rowq[q] = j - b * (2 * m.nc);  // ci * 2 + k
+        x0q[q] = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
+      }
     }
     run = M::make(R(1), R(0));  // prod_{s' < s} [T]_{s'}
     for (int s = 0; s < nslab; ++s) {
@@ -721,10 +732,8 @@ __global__ void __launch_bounds__(256, TB ? 2 : kProdMinBlocks)
 #pragma unroll
         for (int q = 0; q < kWChunk; ++q) {
           if (q >= nj) break;
-          const int j = j0 + q, b = j / (2 * m.nc), ci = (j >> 1) % m.nc, k = j & 1;
-          const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
           T ov[B];
-          load_batch<T, B>(osum + rec_index(g, static_cast<size_t>(s * m.nc + ci) * 2 + k, x0, 0), g.Ns, ov);
+          load_batch<T, B>(osum + rec_index(g, static_cast<size_t>(s * m.nc) * 2 + rowq[q], x0q[q], 0), g.Ns, ov);
           T sr = T(0), si = T(0);
 #pragma unroll
           for (int r = 0; r < B; ++r) {
