@@ -17,13 +17,26 @@
 // (+-L(ylen+2)), and in x at +-1 or, across the periodic seam, -+(L-1): every
 // staple load is a plain shared-memory load.  Rows span the whole x extent,
 // so x needs no ghost cells (and no mirror stores).
-// A thread that moves a link also stores the new angle into every box cell
-// that mirrors it (in its own or another CTA's shared memory, through the
-// cluster's shared-memory window), so after the hardware cluster barrier that
-// ends each (direction, parity) pass every box is current.  At the end
-// the updated links go back to global memory and the slab is recorded (phase
-// sums, plaquette sums) from shared memory.  No grid-wide synchronisation:
-// the last cluster to finish advances the sweep counters.
+// A thread that updates a link also stores its angle into every box cell
+// that mirrors it: in another CTA's shared memory with st.async, which
+// completes its bytes on that CTA's exchange mbarrier for the pass, or in the
+// CTA's own ghost rows.  Each CTA knows how many mirror stores it receives in
+// every pass (counted when the mirror lists are built), so a pass ends with a
+// wait for this CTA's own incoming bytes and a block barrier, not with a
+// barrier of the whole cluster.  No CTA overwrites a cell a neighbour still
+// reads: a site that reads a link owned by CTA B lies in B's box, so its
+// update is one of the stores B waits for before B's next pass.  Every pass
+// also carries one 4-byte token from each CTA to each of its neighbours (the
+// CTAs its sites mirror into), sent once the previous pass is complete:
+// passes that move no mirrored link (the spatial passes of a slab of
+// thickness 1) would otherwise let a CTA run more than one pass ahead of a
+// neighbour and land its stores on the neighbour's barrier for another
+// pass.  With the tokens no CTA leads a neighbour by more than one pass, so
+// two barriers, used by alternate passes, suffice.  At the end
+// of a round the slab is recorded (phase sums, plaquette sums) from shared
+// memory between cluster barriers, and at the end of the launch the updated
+// links go back to global memory.  No grid-wide synchronisation: the last
+// cluster to finish advances the sweep counters.
 //
 // Link updates use the same arithmetic and random numbers as every other
 // implementation (new_link_angle), so configurations and records are
@@ -172,13 +185,17 @@ __device__ __forceinline__ void box_staples(const Box& b, const T* buf, int mu, 
   w[5] = at(nu, tl - dt, bi + ob);   // theta_nu(x - nu)
 }
 
-// Update of the link U_mu at box cell bi, local time tl; the new angle also
-// goes to the mirrors mirror[m0 .. m1) of the cell (cluster addresses of slot 0).
-// The direction is a template parameter, so the staple offsets and slots of
-// every plane resolve at compile time.
+// Update of the link U_mu at box cell bi, local time tl; its angle (new or
+// kept) also goes to the mirrors mirror[m0 .. m1) of the cell ((cluster
+// address of the slot-0 cell, CTA rank)): st.async onto the receiver's
+// exchange barrier `bar` (a local address, the same in every CTA), or a plain
+// store into this CTA's (rank `own`) ghost rows.  Every mirror is stored, moved
+// or not, so that the receivers' byte counts are fixed.  The direction is a
+// template parameter, so the staple offsets and slots of every plane resolve
+// at compile time.
 template <typename T, int KIND, int MU>
-__device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* mirror, int m0, int m1, int tl,
-                                         int bi, int xp, int xm, uint32_t site, unsigned long long n, uint32_t k0, uint32_t k1,
+__device__ __forceinline__ void box_link(const Box& b, T* buf, const uint2* mirror, uint32_t own, uint32_t bar,
+                                         int m0, int m1, int tl, int bi, int xp, int xm, uint32_t site, unsigned long long n, uint32_t k0, uint32_t k1,
                                          T beta, int* err, const UpdateRule& rule) {
   constexpr int mu = MU;
   auto staples = [&](int nu, T w[6]) { box_staples<T>(b, buf, mu, tl, bi, xp, xm, nu, w); };
@@ -191,10 +208,15 @@ __device__ __forceinline__ void box_link(const Box& b, T* buf, const uint32_t* m
           ? new_link_angle<T, 2>(mu, staples, cur, site, n, k0, k1, beta, err, &out, static_cast<T>(rule.width),
                                  rule.hits)
           : new_link_angle<T, KIND, 2>(mu, staples, cur, site, n, k0, k1, beta, err, &out);
-  if (moved) {
-    *self = out;
-    const uint32_t soff = static_cast<uint32_t>(sl * b.vol * sizeof(T));
-    for (int m = m0; m < m1; ++m) st_cluster(mirror[m] + soff, out);
+  const T v = moved ? out : *self;
+  if (moved) *self = out;
+  const uint32_t soff = static_cast<uint32_t>(sl * b.vol * sizeof(T));
+  for (int m = m0; m < m1; ++m) {
+    const uint2 e = mirror[m];
+    if (e.y == own)
+      st_cluster(e.x + soff, v);
+    else
+      st_async(e.x + soff, v, map_to_rank(bar, e.y));
   }
 }
 
@@ -237,10 +259,31 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const int own = g.L * b.ylen * b.zlen;  // owned sites, index j = cx + L (ry + ylen rz)
   T* buf = reinterpret_cast<T*>(res_smem);
   // mirror lists of the owned sites (compressed rows: site j's mirrors are
-  // mirror[mstart[j] .. mstart[j+1]), cluster addresses of their slot-0 cells)
+  // mirror[mstart[j] .. mstart[j+1]), (cluster address of the slot-0 cell,
+  // rank of its CTA))
   int* mstart = reinterpret_cast<int*>(buf + static_cast<size_t>(K) * b.vol);
-  uint32_t* mirror = reinterpret_cast<uint32_t*>(mstart + b.L * b.yl_full * b.zl_full + 1);
+  uint2* mirror = reinterpret_cast<uint2*>(
+      (reinterpret_cast<uintptr_t>(mstart + b.L * b.yl_full * b.zl_full + 1) + 7) & ~static_cast<uintptr_t>(7));
   __shared__ int wsum[32];  // one per warp; warp 0 scans all 32 entries
+  // exchange barriers of the passes (pass q uses xbar[q & 1]) and the counts
+  // of mirror stores this CTA receives from the other CTAs' sites, by the
+  // sites' spatial parity (cx + cy + cz) & 1
+  __shared__ __align__(8) unsigned long long xbar[2];
+  __shared__ unsigned int xcnt[2];
+  // tokens: the CTAs that send this one a token every pass, this CTA's
+  // neighbours (flags by rank, then the list) and the word tokens land in
+  __shared__ unsigned int xntok, xtok;
+  __shared__ int xflag[32], xnbr[32], xnnbr;
+  if (threadIdx.x < 32) xflag[threadIdx.x] = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(shared_addr(&xbar[0]), 1);
+    mbar_init(shared_addr(&xbar[1]), 1);
+    xcnt[0] = 0u;
+    xcnt[1] = 0u;
+    xntok = 0u;
+    xtok = 0u;
+    fence_mbar_init();
+  }
   const uint32_t base = shared_addr(buf);
   // magic divisors; every dividend times its divisor stays below 2^40 (the
   // box fits in shared memory, so all counts are far below 2^20)
@@ -319,23 +362,56 @@ __global__ void __launch_bounds__(kResThreads, 1)
     if (j_hi == own && j_lo < j_hi) mstart[own] = run;
     if (own == 0 && threadIdx.x == 0) mstart[0] = 0;
   }
-  __syncthreads();
+  // every CTA's exchange barriers and counts are initialised before any CTA
+  // counts into them
+  cluster_sync();
   for (int j = j_lo; j < j_hi; ++j) {
     int cx, cy, cz, m = mstart[j];
     site_of(j, &cx, &cy, &cz);
+    const uint32_t cnt = shared_addr(&xcnt[(cx + cy + cz) & 1]);
     for_each_mirror(g.L, b.ny, nz, b.yl_full, b.zl_full, bry, brz, cx, cy, cz, [&](int r, int cell) {
-      mirror[m++] = map_to_rank(base + static_cast<uint32_t>(cell * sizeof(T)), static_cast<uint32_t>(r));
+      const uint32_t ur = static_cast<uint32_t>(r);
+      mirror[m++] = make_uint2(map_to_rank(base + static_cast<uint32_t>(cell * sizeof(T)), ur), ur);
+      if (r != rank) {
+        red_add_cluster(map_to_rank(cnt, ur), 1u);
+        xflag[r] = 1;
+      }
     });
   }
-  // every box is loaded before any CTA stores into another's
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int r = 0; r < static_cast<int>(cluster_size()) && r < 32; ++r)
+      if (xflag[r]) {
+        xnbr[k++] = r;
+        red_add_cluster(map_to_rank(shared_addr(&xntok), static_cast<uint32_t>(r)), 1u);
+      }
+    xnnbr = k;
+  }
+  // every box is loaded and every count complete before any CTA stores into
+  // another's box
   cluster_sync();
 
   const int hx = g.L / 2;  // site pairs per row
   const int half = hx * b.ylen * b.zlen;
   const unsigned long long m_half = fdiv_magic(max(half, 1)), m_hx = fdiv_magic(hx),
                            m_own = fdiv_magic(max(own, 1));
-  // one (mu, parity) pass of this CTA's links, mu a compile-time constant
-  auto pass = [&](auto mu_c, int sweep, int par, unsigned long long n) {
+  // bytes of mirror stores this CTA receives in a pass of direction class
+  // (mu = 0, mu > 0) and parity par: sites of spatial parity par ^ (t & 1)
+  // at each updated local time
+  uint32_t xbytes[2][2];
+  for (int c = 0; c < 2; ++c)
+    for (int par = 0; par < 2; ++par) {
+      uint32_t nst = 0;
+      for (int tl = c; tl < d; ++tl) nst += xcnt[par ^ ((t0 + tl) & 1)];
+      xbytes[c][par] = nst * static_cast<uint32_t>(sizeof(T)) + xntok * 4u;  // + the tokens
+    }
+  const uint32_t xtok_addr = shared_addr(&xtok);
+  const uint32_t xbar0 = shared_addr(&xbar[0]);
+  const uint32_t urank = static_cast<uint32_t>(rank);
+  // one (mu, parity) pass of this CTA's links, mu a compile-time constant;
+  // bar: the pass's exchange barrier
+  auto pass = [&](auto mu_c, int sweep, int par, unsigned long long n, uint32_t bar) {
     constexpr int mu = decltype(mu_c)::value;
     constexpr int tl_lo = mu == 0 ? 0 : 1;  // spatial links at tl = 0 are frozen
     const int items = (d - tl_lo) * half;
@@ -353,27 +429,38 @@ __global__ void __launch_bounds__(kResThreads, 1)
       const int jo = cx + g.L * row;  // owned-site index
       const uint32_t site = static_cast<uint32_t>(cx + g.L * (cy + g.L * cz) + g.Ns * t);
       if (sweep == 0)
-        box_link<T, 0, mu>(b, buf, mirror, mstart[jo], mstart[jo + 1], tl, bi, xp, xm, site, n, k0, k1, beta, err,
-                           rule);
+        box_link<T, 0, mu>(b, buf, mirror, urank, bar, mstart[jo], mstart[jo + 1], tl, bi, xp, xm, site, n, k0, k1,
+                           beta, err, rule);
       else
-        box_link<T, 1, mu>(b, buf, mirror, mstart[jo], mstart[jo + 1], tl, bi, xp, xm, site, n, k0, k1, beta, err,
-                           rule);
+        box_link<T, 1, mu>(b, buf, mirror, urank, bar, mstart[jo], mstart[jo + 1], tl, bi, xp, xm, site, n, k0, k1,
+                           beta, err, rule);
     }
   };
+  uint32_t q = 0;  // passes of this launch so far
   for (int round = 0; round < n_rec; ++round) {
     for (int c = 0; c < n_compound; ++c) {
       const unsigned long long n = nbase + 1 + static_cast<unsigned long long>(round) * n_compound + c;
       for (int sweep = 0; sweep <= n_or; ++sweep)
         for (int mu = 0; mu < 4; ++mu)
           for (int par = 0; par < 2; ++par) {
-            switch (mu) {
-              case 0: pass(std::integral_constant<int, 0>{}, sweep, par, n); break;
-              case 1: pass(std::integral_constant<int, 1>{}, sweep, par, n); break;
-              case 2: pass(std::integral_constant<int, 2>{}, sweep, par, n); break;
-              default: pass(std::integral_constant<int, 3>{}, sweep, par, n); break;
+            const uint32_t bar = xbar0 + 8u * (q & 1u);
+            // the previous pass is complete here: tell the neighbours
+            if (static_cast<int>(threadIdx.x) < xnnbr) {
+              const uint32_t r = static_cast<uint32_t>(xnbr[threadIdx.x]);
+              st_async(map_to_rank(xtok_addr, r), 0u, map_to_rank(bar, r));
             }
-            // the pass's links and their mirrors are in place for every CTA
-            cluster_sync();
+            switch (mu) {
+              case 0: pass(std::integral_constant<int, 0>{}, sweep, par, n, bar); break;
+              case 1: pass(std::integral_constant<int, 1>{}, sweep, par, n, bar); break;
+              case 2: pass(std::integral_constant<int, 2>{}, sweep, par, n, bar); break;
+              default: pass(std::integral_constant<int, 3>{}, sweep, par, n, bar); break;
+            }
+            // this CTA's incoming mirror stores of the pass have landed, and
+            // its own threads' updates are done
+            if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, xbytes[mu > 0][par]);
+            mbar_wait_bounded(bar, (q >> 1) & 1u, err);
+            __syncthreads();
+            ++q;
           }
     }
     if (record) {
@@ -513,9 +600,10 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, Resi
       split[i] = brick_split(g.L, cs);
       if (g.Nt % mask != 0 || g.L % 2 != 0) fits = false;
       const BrickSplit& sp = split[i];
+      // box, mirror offsets, 8 bytes of alignment, mirror entries
       smem = std::max(smem, static_cast<size_t>(sp.box) * (4 * mask + 3) * sizeof(T) +
-                                (static_cast<size_t>(g.L) * sp.ylen * sp.zlen + 1 + mirror_capacity(g.L, sp)) *
-                                    sizeof(uint32_t));
+                                (static_cast<size_t>(g.L) * sp.ylen * sp.zlen + 1) * sizeof(int) + 8 +
+                                static_cast<size_t>(mirror_capacity(g.L, sp)) * sizeof(uint2));
     }
     if (!fits || smem > kResSmemMax) continue;
     cudaLaunchAttribute at[1];

@@ -93,6 +93,67 @@ __device__ __forceinline__ double ld_cluster(uint32_t a, double*) {
   return v;
 }
 
+// ---- neighbour exchange inside a cluster: remote stores that complete on
+// the receiver's mbarrier ----
+// An mbarrier phase completes when its pending arrivals and its transaction
+// count both reach zero.  The receiver arrives once per phase (expect_tx with
+// the bytes it will receive); each sender's st.async subtracts its bytes on
+// arrival.  Stores may land before the receiver's expect_tx (the count then
+// runs negative until it arrives), so the receiver needs no handshake with
+// the senders for a phase, only the counts.
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// the initialised barriers are visible cluster-wide (before a cluster barrier)
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_parity(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the completion of the phase with parity `parity`, for at most
+// kMbarWaitCycles SM cycles (about 33 ms); on timeout records kErrTimeout and
+// returns false, leaving the caller to carry on (so every CTA of the cluster
+// still reaches the kernel's closing cluster barrier).
+constexpr long long kMbarWaitCycles = 1ll << 26;
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int* err) {
+  if (mbar_try_wait_parity(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_parity(bar, parity)) {
+    if (clock64() - t0 > kMbarWaitCycles) {
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+// store v at cluster address a, completing sizeof(v) bytes on the mbarrier
+// at cluster address bar (in the same CTA as a)
+__device__ __forceinline__ void st_async(uint32_t a, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(a), "f"(v), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t a, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(a), "d"(v), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t a, uint32_t v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(a), "r"(v), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void red_add_cluster(uint32_t a, uint32_t v) {
+  asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
 // ---- asynchronous global -> shared copies of 16 bytes (cp.async) ----
 // Each thread's copies form groups; cp_async_wait_all waits for the thread's
 // own groups, so a block barrier must follow before other threads read them.
