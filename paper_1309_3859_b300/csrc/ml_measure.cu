@@ -255,7 +255,10 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 //   accT[s][a][x]              += sum_j T_j(x, s, R_a)
 //   accO[s][f][b][ci][k][x]    += sum_j T_j(x, s, rf_f) O_j[s][ci][k](x0)
 // The sum over the batch is formed in the records' precision and added once,
-// so each accumulator is read and written once per batch.
+// so each accumulator is read and written once per batch.  The field-insertion
+// sums stream through L2 (loads and stores marked evict-first) so that they
+// do not push out the ring buffer's records, which every (separation, probe)
+// reads again.
 // ---------------------------------------------------------------------------
 template <typename T, bool MH>
 __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict__ desc,
@@ -359,7 +362,7 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
       A a[kAccGroup];
 #pragma unroll
       for (int i = 0; i < kAccGroup; ++i)
-        if (q0 + i < nck) a[i] = overwrite ? A{} : acc[abase + static_cast<size_t>(q0 + i) * g.Ns];
+        if (q0 + i < nck) a[i] = overwrite ? A{} : __ldcs(acc + abase + static_cast<size_t>(q0 + i) * g.Ns);
 #pragma unroll
       for (int i = 0; i < kAccGroup; ++i) {
         const int q = q0 + i;
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
       }
 #pragma unroll
       for (int i = 0; i < kAccGroup; ++i)
-        if (q0 + i < nck) acc[abase + static_cast<size_t>(q0 + i) * g.Ns] = a[i];
+        if (q0 + i < nck) __stcs(acc + abase + static_cast<size_t>(q0 + i) * g.Ns, a[i]);
     }
   }
 }
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
         for (int i = 0; i < kTileProbes; ++i)
           if (b0 + i < m.np)
             a[i] = overwrite ? A{}
-                             : acc[(((static_cast<size_t>(s) * m.nrf + f) * m.np + b0 + i) * nck + q) * g.Ns + x];
+                             : __ldcs(acc + (((static_cast<size_t>(s) * m.nrf + f) * m.np + b0 + i) * nck + q) * g.Ns + x);
 #pragma unroll
         for (int i = 0; i < kTileProbes; ++i) {
           const int b = b0 + i;
@@ -510,7 +513,8 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
         }
 #pragma unroll
         for (int i = 0; i < kTileProbes; ++i)
-          if (b0 + i < m.np) acc[(((static_cast<size_t>(s) * m.nrf + f) * m.np + b0 + i) * nck + q) * g.Ns + x] = a[i];
+          if (b0 + i < m.np)
+            __stcs(acc + (((static_cast<size_t>(s) * m.nrf + f) * m.np + b0 + i) * nck + q) * g.Ns + x, a[i]);
       }
     }
     __syncthreads();  // the tile is read before the next component's copies
@@ -583,14 +587,14 @@ __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, Mea
         for (int k = 0; k < 2; ++k) {
           C sum = M::make(R(0), R(0));
           for (int jj = 0; jj < q; ++jj) {
-            const C o = M::value(
-                accO[((((static_cast<size_t>(q * S + jj) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x]);
+            const C o = M::value(__ldcs(
+                accO + ((((static_cast<size_t>(q * S + jj) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x));
             sum = cadd(sum, cmul(cscale(o, in), rest[jj]));
           }
           A* p = acc4O + ((((static_cast<size_t>(S) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
-          A v = *p;
+          A v = __ldcs(p);
           acc_add(v, sum.x, sum.y);
-          *p = v;
+          __stcs(p, v);
         }
   }
 }
@@ -723,7 +727,7 @@ __global__ void __launch_bounds__(256, TB == 0 || (TB == 4 && std::is_same<A, fl
       A o[kWChunk];
 #pragma unroll
       for (int q = 0; q < kWChunk; ++q)
-        if (q < nj) o[q] = fresh ? A{} : ocol[static_cast<size_t>(q) * g.Ns];
+        if (q < nj) o[q] = fresh ? A{} : __ldcs(ocol + static_cast<size_t>(q) * g.Ns);
       if constexpr (TAIL) {
         const T* trec = static_cast<const T*>(tail.trec);
         const T* osum = static_cast<const T*>(tail.osum);
