@@ -200,7 +200,8 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   L->partial_naive =
       static_cast<double2*>(lat_alloc(e, L, (static_cast<size_t>(nr) * nw + nvw / 2 + 1) * sizeof(double2)));
   L->scratch_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
-  const bool ok = L->theta && L->d_n && L->d_lists && L->accT && (L->accO || !L->accO_bytes) && L->osum[0] &&
+  L->naive_theta = lat_alloc(e, L, 4ull * g.V * tsz);
+  const bool ok = L->theta && L->naive_theta && L->d_n && L->d_lists && L->accT && (L->accO || !L->accO_bytes) && L->osum[0] &&
                   L->osum[1] && (!p->replay || (L->replay_theta && L->replay_n)) &&
                   L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->vac_acc && L->partial &&
                   L->partial_naive && L->scratch_n && (!nslab_out || (L->acc4T && L->acc4O)) &&
@@ -483,9 +484,10 @@ size_t record_offset(const Engine* e, int li, int n_meas) {
 
 size_t total_len(const Engine* e, int n_meas) { return record_offset(e, static_cast<int>(e->lats.size()), n_meas); }
 
-// Algorithm 1 for n_meas measurements of every lattice.  Sweeps, records and
-// the vacuum run on the main stream; clears, folds, the level combination and
-// the products on the accumulation stream.
+// Algorithm 1 for n_meas measurements of every lattice.  Sweeps and records
+// run on the main stream; clears, the naive correlator and plaquette (from a
+// copy of the configuration), folds, the level combination and the products
+// on the accumulation stream.
 int enqueue_measurements(Engine* e, int n_meas, double* rec) {
   int st = join(e->stream, e->side, e->ev_main);
   if (st) return st;
@@ -501,12 +503,17 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       st = launch_graph(e, e->g_full);
       if (st) return st;
     }
+    // the naive correlator and plaquette of this configuration run on the
+    // accumulation stream, from a copy, while the inner loop starts
+    for (LatState* L : e->lats)
+      ML_CUDA(cudaMemcpyAsync(L->naive_theta, L->theta, 4ull * L->g.V * (e->fp64 ? 8 : 4), cudaMemcpyDeviceToDevice,
+                              e->stream));
+    st = join(e->stream, e->side, e->ev_main);  // records cleared and copies made before the side stream uses them
+    if (st) return st;
     for (int li = 0; li < nlat; ++li) {
       LatState* L = e->lats[li];
-      launch_naive_and_plaquette(e->fp64, L->theta, L->g, L->meas, L->partial_naive, out[li], e->stream);
+      launch_naive_and_plaquette(e->fp64, L->naive_theta, L->g, L->meas, L->partial_naive, out[li], e->side);
     }
-    st = join(e->stream, e->side, e->ev_main);  // records cleared before the products write them
-    if (st) return st;
     for (LatState* L : e->lats) ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->side));
     int ncfg = 0;
     if (e->replay) {

@@ -36,7 +36,8 @@ struct LatState {
   int nparts = 0;
   double* vac_acc = nullptr;
   double2* partial = nullptr;        // product partials (accumulation stream)
-  double2* partial_naive = nullptr;  // naive / plaquette partials (main stream)
+  double2* partial_naive = nullptr;  // naive / plaquette partials (accumulation stream)
+  void* naive_theta = nullptr;       // the configuration the naive correlator and plaquette read
   double* staging = nullptr;         // canonical angles for get / set
   void* scratch_theta = nullptr;     // timing copies
   void* replay_theta = nullptr;      // replay: configuration at the start of the inner loop
