@@ -43,8 +43,8 @@ __device__ __forceinline__ double2 unit_phase(double phi) {
 // ---------------------------------------------------------------------------
 // Ring of sub-update records (layout: rec_index), element (slot j) of
 //   theta_rec[s][slots][x]           Theta_s(x) = sum_{t in slab} theta_0(x, t)
-//                                    (FP32: summed in double, reduced to
-//                                    [-pi, pi) and rounded)
+//                                    (FP32: summed in single precision and
+//                                    reduced to [-pi, pi); slab_phase_sum)
 //   osum[s][ci][k][slots][x]         sum_{t in slab} (Re, Im) P_c(x, t)
 // A site's batch: the slots at p, p + Ns, p + 2 Ns, ... (p = rec_index(.., 0)),
 // each load coalesced over a warp's consecutive sites.

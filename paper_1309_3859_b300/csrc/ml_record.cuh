@@ -37,6 +37,18 @@ __device__ __forceinline__ double theta0(const T* th, const Geom& g, int cx, int
   return static_cast<double>(th[soa(g, 0, i, (cx + cy + cz + t) & 1)]);
 }
 
+// Recorded slab phase sum Theta_s(x) = sum over the slab's d times of
+// theta_0(x, t), from angle(tl) for tl = 0 .. d-1 in order.  FP64: the plain
+// sum.  FP32: summed in single precision and reduced to [-pi, pi) (only its
+// phase is used), one rounding per term; every record path calls this, so
+// all of them agree bit for bit.
+template <typename T, typename Angle>
+__device__ __forceinline__ T slab_phase_sum(int d, Angle&& angle) {
+  T sum = T(0);
+  for (int tl = 0; tl < d; ++tl) sum += angle(tl);
+  return Prec<T>::fp64 ? sum : Prec<T>::wrap(sum);
+}
+
 // plaquette angle of plane (mu, nu) at site coordinates c = (t, x, y, z)
 template <typename T>
 __device__ __forceinline__ T plaquette_angle(const T* th, const Geom& g, const int c[4], int mu, int nu) {
@@ -123,10 +135,11 @@ __device__ __forceinline__ void record_warp(const LatDesc& L, int buf, int slot,
   spatial_coords(g, x, &c[1], &c[2], &c[3]);
   if (y == nc) {
     if (live) {
-      double tsum = 0.0;
-      for (int t = s * d; t < s * d + d; ++t) tsum += theta0(th, g, c[1], c[2], c[3], t);
-      static_cast<T*>(L.theta_rec[buf])[rec_index(g, s, x, slot)] =
-          static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
+      static_cast<T*>(L.theta_rec[buf])[rec_index(g, s, x, slot)] = slab_phase_sum<T>(d, [&](int tl) {
+        const int t = s * d + tl;
+        const int i = c[1] + g.L * (c[2] + g.L * (c[3] + g.L * t));
+        return th[soa(g, 0, i, (c[1] + c[2] + c[3] + t) & 1)];
+      });
     }
     return;
   }

@@ -475,10 +475,8 @@ __global__ void __launch_bounds__(kResThreads, 1)
         const int x = cx + g.L * (b.y0 + ry + g.L * (b.z0 + rz));
         const int bi = b.cell(cx, ry + 1, rz + 1);
         const int xp = b.xplus(cx), xm = b.xminus(cx);
-        double tsum = 0.0;
-        for (int tl = 0; tl < d; ++tl) tsum += static_cast<double>(buf[tl * b.vol + bi]);
         static_cast<T*>(Ld.theta_rec[rec_buf])[rec_index(g, s, x, slot)] =
-            static_cast<T>(P::fp64 ? tsum : tsum - kTwoPi * floor((tsum + kPi) * (1.0 / kTwoPi)));
+            slab_phase_sum<T>(d, [&](int tl) { return buf[tl * b.vol + bi]; });
         if (MH && Ld.mh_rec[rec_buf]) {
           T mod, ph;
           multihit_slab<T>(0, d, beta, [&](int tl, int nu, T v[6]) { box_staples<T>(b, buf, 0, tl, bi, xp, xm, nu, v); },
