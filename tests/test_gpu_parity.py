@@ -350,11 +350,13 @@ def test_multihit_changes_only_the_multihit_entries(fp64):
 
 # ----------------------------------------------------------------------------- replay of the field insertions
 @pytest.mark.parametrize("fp64", [True, False])
-@pytest.mark.parametrize("n_sub", [3, 37])
+@pytest.mark.parametrize("n_sub", [3, 29, 37])
 def test_replay_matches_the_direct_scheme(fp64, n_sub):
     """The replay scheme runs the inner loop twice from the same configuration
     and sweep numbers: the chain ends where the direct scheme's ends (bit for
-    bit) and the records agree to rounding (the same sums in another order)."""
+    bit) and the records agree to rounding (the same sums in another order).
+    The direct scheme's last ring buffer, folded by the products, holds 3, 13
+    and 5 records: the products read 4, 16 and 8 ring slots."""
     base = dict(L=6, Nt=8, beta=1.0, seed=23, fp64=fp64, slab=2, n_sub=n_sub, k_between=2, r=(1, 2, 3),
                 rf=(1, 2, 3), probes=((0, 0), (1, 0), (0, 1), (-1, 2)), comp_mask=0x3F)
     out = {}
