@@ -855,6 +855,111 @@ static void cross_slab(const orc_params *p, const geom *g, const slab_sums *S, d
         }
 }
 
+/* ------------------------------------------------------------------------ */
+/* One measurement from configurations the caller supplies (Algorithm 1's     */
+/* accumulation and products without its sweeps).  orc_measure below drives  */
+/* the same functions with its own sweeps; tests feed them configurations     */
+/* taken from elsewhere (another chain, or built by hand).                    */
+/* ------------------------------------------------------------------------ */
+typedef struct orc_acc orc_acc;
+struct orc_acc {
+  orc_params p;
+  geom g;
+  int two_level;
+  slab_sums inner, outer;
+  double *pf;    /* plaquette field of the configuration being accumulated */
+  double *rec;   /* the record being formed                                */
+  double vac[12];
+  int n_cfg;     /* sub-update configurations accumulated                  */
+  int n_inner;   /* of them since the last level combination               */
+  int n_outer;   /* level combinations done                                */
+};
+
+static double *naive_block(const orc_params *p, double *rec) {
+  return rec + 2 * p->nr + 2 * p->nrf + (size_t)p->nrf * p->nprobe * 24 + 12;
+}
+
+void orc_acc_free(orc_acc *a) {
+  if (!a) return;
+  free(a->pf);
+  free(a->rec);
+  free_sums(&a->inner);
+  if (a->two_level) free_sums(&a->outer);
+  free(a);
+}
+
+/* NULL when *p is invalid or memory runs out.  The lists of *p must outlive
+ * the accumulator. */
+orc_acc *orc_acc_create(const orc_params *p) {
+  if (validate(p) != ORC_OK) return NULL;
+  orc_acc *a = (orc_acc *)calloc(1, sizeof(orc_acc));
+  if (!a) return NULL;
+  a->p = *p;
+  a->g = make_geom(p);
+  a->two_level = p->outer_slab != 0;
+  a->pf = (double *)malloc(sizeof(double) * 12 * a->g.V);
+  a->rec = (double *)calloc((size_t)orc_record_len(p), sizeof(double));
+  int ok = a->pf && a->rec && alloc_sums(p, &a->g, p->Nt / p->slab, &a->inner) == ORC_OK;
+  if (ok && a->two_level) ok = alloc_sums(p, &a->g, p->Nt / p->outer_slab, &a->outer) == ORC_OK;
+  if (!ok) {
+    orc_acc_free(a);
+    return NULL;
+  }
+  return a;
+}
+
+/* Start a measurement: clear the sums; the naive estimator and the plaquette
+ * come from th_first, the configuration before the first sub-update. */
+int orc_acc_begin(orc_acc *a, const double *th_first) {
+  const orc_params *p = &a->p;
+  memset(a->rec, 0, sizeof(double) * (size_t)orc_record_len(p));
+  memset(a->vac, 0, sizeof a->vac);
+  zero_sums(p, &a->g, &a->inner);
+  if (a->two_level) zero_sums(p, &a->g, &a->outer);
+  a->n_cfg = a->n_inner = a->n_outer = 0;
+  double *naive = naive_block(p, a->rec);
+  for (int r = 0; r < p->nr; ++r) naive_correlator(&a->g, th_first, p->r[r], &naive[2 * r], &naive[2 * r + 1]);
+  naive[2 * p->nr] = orc_plaquette_mean(p->L, p->Nt, th_first);
+  return ORC_OK;
+}
+
+/* Accumulate T^(d) and TO^(d) of one (inner) sub-update configuration. */
+int orc_acc_add(orc_acc *a, const double *th) {
+  accumulate_inner(&a->p, &a->g, th, &a->inner, a->pf, a->vac);
+  ++a->n_cfg;
+  ++a->n_inner;
+  return ORC_OK;
+}
+
+/* Two levels: fold the inner averages of the n_sub configurations added since
+ * the last call into the outer sums (Algorithm 1's level combination) and
+ * clear the inner sums. */
+int orc_acc_end_outer(orc_acc *a) {
+  if (!a->two_level || a->n_inner != a->p.n_sub) return ORC_EINVAL;
+  combine_levels(&a->p, &a->g, &a->inner, &a->outer);
+  zero_sums(&a->p, &a->g, &a->inner);
+  a->n_inner = 0;
+  ++a->n_outer;
+  return ORC_OK;
+}
+
+/* Cross-slab products of the top-level averages (the P, Pf and W blocks),
+ * the vacuum means, and the naive block of orc_acc_begin into rec
+ * (orc_record_len doubles).  One level needs exactly n_sub added
+ * configurations, two levels exactly n_sub_outer combinations. */
+int orc_acc_finish(orc_acc *a, double *rec) {
+  const orc_params *p = &a->p;
+  if (a->two_level ? (a->n_outer != p->n_sub_outer || a->n_inner != 0) : a->n_inner != p->n_sub) return ORC_EINVAL;
+  if (a->two_level)
+    cross_slab(p, &a->g, &a->outer, (double)p->n_sub_outer, a->rec);
+  else
+    cross_slab(p, &a->g, &a->inner, (double)p->n_sub, a->rec);
+  double *v = a->rec + 2 * p->nr + 2 * p->nrf + (size_t)p->nrf * p->nprobe * 24;
+  for (int c = 0; c < 12; ++c) v[c] = a->vac[c] / (double)a->n_cfg;
+  memcpy(rec, a->rec, sizeof(double) * (size_t)orc_record_len(p));
+  return ORC_OK;
+}
+
 /* n_meas multilevel measurements (Algorithm 1).  Each one: k0 full compound
  * sweeps; then either
  *   single level: n2 slab sub-updates (spatial links frozen on t = 0 mod d),
@@ -867,55 +972,94 @@ static void cross_slab(const orc_params *p, const geom *g, const slab_sums *S, d
 int orc_measure(const orc_params *p, double *th, uint64_t *counter, int n_meas, double *rec) {
   int status = validate(p);
   if (status != ORC_OK) return status;
-  geom g = make_geom(p);
+  orc_acc *a = orc_acc_create(p);
+  if (!a) return ORC_ENOMEM;
   const int64_t len = orc_record_len(p);
-  const int two_level = p->outer_slab != 0;
-  slab_sums inner, outer;
-  memset(&outer, 0, sizeof outer);
-  double *pf = (double *)malloc(sizeof(double) * 12 * g.V);
-  if (!pf || alloc_sums(p, &g, p->Nt / p->slab, &inner) != ORC_OK) return ORC_ENOMEM;
-  if (two_level && alloc_sums(p, &g, p->Nt / p->outer_slab, &outer) != ORC_OK) return ORC_ENOMEM;
-
   for (int m = 0; m < n_meas; ++m) {
-    double *out = rec + (size_t)m * len;
-    memset(out, 0, sizeof(double) * len);
     for (int s = 0; s < p->k_between; ++s)
       if (orc_compound_sweep(p, th, 0, counter) != ORC_OK) status = ORC_EREJECT;
-
-    /* naive estimator and plaquette of the measurement's first configuration */
-    double *naive = out + 2 * p->nr + 2 * p->nrf + (size_t)p->nrf * p->nprobe * 24 + 12;
-    for (int a = 0; a < p->nr; ++a) naive_correlator(&g, th, p->r[a], &naive[2 * a], &naive[2 * a + 1]);
-    naive[2 * p->nr] = orc_plaquette_mean(p->L, p->Nt, th);
-
-    double vac[12] = {0};
-    int n_cfg = 0;
-    if (!two_level) {
-      zero_sums(p, &g, &inner);
+    orc_acc_begin(a, th);
+    const int n_outer = a->two_level ? p->n_sub_outer : 1;
+    for (int o = 0; o < n_outer; ++o) {
+      if (a->two_level && orc_compound_sweep(p, th, p->outer_slab, counter) != ORC_OK) status = ORC_EREJECT;
       for (int j = 0; j < p->n_sub; ++j) {
         if (orc_compound_sweep(p, th, p->slab, counter) != ORC_OK) status = ORC_EREJECT;
-        accumulate_inner(p, &g, th, &inner, pf, vac);
-        ++n_cfg;
+        orc_acc_add(a, th);
       }
-      cross_slab(p, &g, &inner, (double)p->n_sub, out);
-    } else {
-      zero_sums(p, &g, &outer);
-      for (int o = 0; o < p->n_sub_outer; ++o) {
-        if (orc_compound_sweep(p, th, p->outer_slab, counter) != ORC_OK) status = ORC_EREJECT;
-        zero_sums(p, &g, &inner);
-        for (int j = 0; j < p->n_sub; ++j) {
-          if (orc_compound_sweep(p, th, p->slab, counter) != ORC_OK) status = ORC_EREJECT;
-          accumulate_inner(p, &g, th, &inner, pf, vac);
-          ++n_cfg;
-        }
-        combine_levels(p, &g, &inner, &outer);
-      }
-      cross_slab(p, &g, &outer, (double)p->n_sub_outer, out);
+      if (a->two_level) orc_acc_end_outer(a);
     }
-    double *v = out + 2 * p->nr + 2 * p->nrf + (size_t)p->nrf * p->nprobe * 24;
-    for (int c = 0; c < 12; ++c) v[c] = vac[c] / (double)n_cfg;
+    orc_acc_finish(a, rec + (size_t)m * len);
   }
-  free(pf);
-  free_sums(&inner);
-  if (two_level) free_sums(&outer);
+  orc_acc_free(a);
   return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Connected field profile from n_meas records (Section II.C, the connected */
+/* expectation value of the field and the relations between the plaquette  */
+/* and the field): with sums over the measurements,                          */
+/*   <O>_{P+P} = (sum_m W_m) / (sum_m Re Pf_m) - (1/n) sum_m vac_m,          */
+/*   F   = sqrt(beta) <Im P_c>_{P+P}   (k = 1 insertion),                    */
+/*   F^2 = -2 beta <Re P_c>_{P+P}      (k = 0 insertion; the constant 1 of   */
+/*                                      2 beta (1 - Re P) cancels between    */
+/*                                      the two terms)                       */
+/* from the real parts of W (the imaginary parts average to zero).  Errors  */
+/* by the delete-one jackknife over measurements (Section III): the         */
+/* estimate recomputed without measurement m, and                           */
+/* err^2 = (n-1)/n sum_m (est_m - mean_m est_m)^2.                           */
+/* out[nrf][nprobe][6][4] = (F, F^2, err F, err F^2); unselected components */
+/* and n_meas < 2 give zero errors.                                          */
+/* ------------------------------------------------------------------------ */
+static void connected_of(const orc_params *p, const double *recs, int n_meas, int skip, int f, int b, int c,
+                         double *F, double *F2) {
+  const int64_t len = orc_record_len(p);
+  const size_t off_pf = 2 * (size_t)p->nr;
+  const size_t off_w = off_pf + 2 * (size_t)p->nrf;
+  const size_t off_vac = off_w + (size_t)p->nrf * p->nprobe * 24;
+  double pf = 0.0, w0 = 0.0, w1 = 0.0, v0 = 0.0, v1 = 0.0;
+  int n = 0;
+  for (int m = 0; m < n_meas; ++m) {
+    if (m == skip) continue;
+    const double *r = recs + (size_t)m * len;
+    pf += r[off_pf + 2 * f];
+    const size_t wo = off_w + ((((size_t)f * p->nprobe + b) * 6 + c) * 2) * 2;
+    w0 += r[wo];     /* Re W of the Re P_c insertion */
+    w1 += r[wo + 2]; /* Re W of the Im P_c insertion */
+    v0 += r[off_vac + 2 * c];
+    v1 += r[off_vac + 2 * c + 1];
+    ++n;
+  }
+  *F = sqrt(p->beta) * (w1 / pf - v1 / n);
+  *F2 = -2.0 * p->beta * (w0 / pf - v0 / n);
+}
+
+int orc_connected(const orc_params *p, const double *recs, int n_meas, double *out) {
+  if (validate(p) != ORC_OK || n_meas < 1) return ORC_EINVAL;
+  for (int f = 0; f < p->nrf; ++f)
+    for (int b = 0; b < p->nprobe; ++b)
+      for (int c = 0; c < 6; ++c) {
+        double *o = out + ((((size_t)f * p->nprobe + b) * 6 + c) * 4);
+        o[0] = o[1] = o[2] = o[3] = 0.0;
+        if (!(p->comp_mask & (1u << c))) continue;
+        connected_of(p, recs, n_meas, -1, f, b, c, &o[0], &o[1]);
+        if (n_meas < 2) continue;
+        double sF = 0.0, sF2 = 0.0;
+        for (int m = 0; m < n_meas; ++m) {
+          double F, F2;
+          connected_of(p, recs, n_meas, m, f, b, c, &F, &F2);
+          sF += F;
+          sF2 += F2;
+        }
+        const double mF = sF / n_meas, mF2 = sF2 / n_meas;
+        double eF = 0.0, eF2 = 0.0;
+        for (int m = 0; m < n_meas; ++m) {
+          double F, F2;
+          connected_of(p, recs, n_meas, m, f, b, c, &F, &F2);
+          eF += (F - mF) * (F - mF);
+          eF2 += (F2 - mF2) * (F2 - mF2);
+        }
+        o[2] = sqrt((n_meas - 1.0) / n_meas * eF);
+        o[3] = sqrt((n_meas - 1.0) / n_meas * eF2);
+      }
+  return ORC_OK;
 }

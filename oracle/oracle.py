@@ -11,6 +11,7 @@ Angles use the canonical layout ``theta[mu, i]`` with
 
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -46,6 +47,37 @@ def lib() -> ctypes.CDLL:
         _lib = ctypes.CDLL(_LIB)
         _declare(_lib)
     return _lib
+
+
+def source() -> str:
+    """Text of ``ml_oracle.c`` (the tests compile copies with planted mistakes)."""
+    with open(_SRC) as f:
+        return f.read()
+
+
+def build_variant(text: str, path: str) -> str:
+    """Compile C source ``text`` (a modified copy of ``ml_oracle.c``) into the
+    shared library ``path``, with the oracle's own flags."""
+    c = path + ".c"
+    with open(c, "w") as f:
+        f.write(text)
+    subprocess.run(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC", "-o", path, c,
+                    "-lm"], check=True)
+    return path
+
+
+@contextlib.contextmanager
+def using_library(path: str):
+    """Run every oracle function against another build (``build_variant``)."""
+    global _lib
+    saved = _lib
+    L = ctypes.CDLL(path)
+    _declare(L)
+    _lib = L
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 class _Params(ctypes.Structure):
@@ -97,6 +129,14 @@ def _declare(L):
     L.orc_record_len.restype = ctypes.c_int64
     L.orc_validate.argtypes = [_P]
     L.orc_measure.argtypes = [_P, _D, _U64, ctypes.c_int, _D]
+    L.orc_acc_create.argtypes = [_P]
+    L.orc_acc_create.restype = ctypes.c_void_p
+    L.orc_acc_free.argtypes = [ctypes.c_void_p]
+    L.orc_acc_begin.argtypes = [ctypes.c_void_p, _D]
+    L.orc_acc_add.argtypes = [ctypes.c_void_p, _D]
+    L.orc_acc_end_outer.argtypes = [ctypes.c_void_p]
+    L.orc_acc_finish.argtypes = [ctypes.c_void_p, _D]
+    L.orc_connected.argtypes = [_P, _D, ctypes.c_int, _D]
 
 
 @dataclass
@@ -265,6 +305,84 @@ def measure(p: Params, th: np.ndarray, counter: int, n_meas: int):
     if st != 0:
         raise RuntimeError(f"oracle measure failed with status {st}")
     return rec, c.value
+
+
+class Accumulator:
+    """One multilevel measurement from configurations the caller supplies
+    (Algorithm 1's accumulation, level combination and cross-slab products,
+    without its sweeps): ``begin(th_first)``, then ``add(th)`` for each
+    sub-update configuration (two levels: ``end_outer()`` after every n_sub of
+    them), then ``finish()`` returns the record.  ``measure`` runs the same
+    functions on its own chain."""
+
+    def __init__(self, p: Params):
+        self.p = p
+        self._cp = p.c()
+        self.h = lib().orc_acc_create(ctypes.byref(self._cp))
+        if not self.h:
+            raise RuntimeError("oracle accumulator: invalid parameters or out of memory")
+
+    def close(self):
+        if self.h:
+            lib().orc_acc_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        self.close()
+
+    @staticmethod
+    def _th(th):
+        return np.ascontiguousarray(th, dtype=np.float64).reshape(4, -1)
+
+    def begin(self, th_first: np.ndarray):
+        t = self._th(th_first)
+        lib().orc_acc_begin(self.h, _dp(t))
+
+    def add(self, th: np.ndarray):
+        t = self._th(th)
+        lib().orc_acc_add(self.h, _dp(t))
+
+    def end_outer(self):
+        st = lib().orc_acc_end_outer(self.h)
+        if st != 0:
+            raise RuntimeError("end_outer: one level, or not n_sub configurations since the last call")
+
+    def finish(self) -> np.ndarray:
+        rec = np.zeros(record_len(self.p), dtype=np.float64)
+        st = lib().orc_acc_finish(self.h, _dp(rec))
+        if st != 0:
+            raise RuntimeError("finish: the configurations added do not complete a measurement")
+        return rec
+
+
+def measure_configs(p: Params, th_first: np.ndarray, configs) -> np.ndarray:
+    """One record from ``th_first`` (naive estimator and plaquette) and the
+    sub-update configurations ``configs`` in order (two levels: n_sub_outer
+    groups of n_sub)."""
+    with Accumulator(p) as acc:
+        acc.begin(th_first)
+        for k, th in enumerate(configs):
+            acc.add(th)
+            if p.outer_slab and (k + 1) % p.n_sub == 0:
+                acc.end_outer()
+        return acc.finish()
+
+
+def connected(p: Params, recs: np.ndarray) -> np.ndarray:
+    """Connected field profile (Section II.C) from records ``recs[n_meas, record_len]``:
+    ``out[nrf, nprobe, 6, 4]`` = (F, F^2, jackknife error of F, of F^2)."""
+    recs = np.ascontiguousarray(recs, dtype=np.float64).reshape(-1, record_len(p))
+    out = np.zeros((max(1, len(p.rf)), max(1, len(p.probes)), 6, 4))
+    st = lib().orc_connected(ctypes.byref(p.c()), _dp(recs), recs.shape[0], _dp(out))
+    if st != 0:
+        raise RuntimeError(f"oracle connected failed with status {st}")
+    return out[:len(p.rf), :len(p.probes)]
 
 
 def split_record(p: Params, rec: np.ndarray) -> dict:

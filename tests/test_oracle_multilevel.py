@@ -15,35 +15,8 @@ import pytest
 import scipy.special as sp
 
 import oracle
+from ml_identity import _identity_expectation
 from paper_1309_3859_b300.stats import jackknife
-
-
-def _spatial(a, L, Nt):
-    """[..., V] -> [..., Nt, z, y, x]"""
-    return a.reshape(a.shape[:-1] + (Nt, L, L, L))
-
-
-def _identity_expectation(p, th):
-    """P and W records of one configuration from Polyakov loops and the
-    plaquette field, with numpy shifts for the separations and probes."""
-    L, Nt = p.L, p.Nt
-    P = oracle.polyakov(p, th).reshape(L, L, L)  # [z, y, x]
-    f = _spatial(oracle.plaquette_field(p, th), L, Nt)  # [c, k, t, z, y, x]
-    ft = f.sum(axis=2)  # time sum of Re / Im P_c
-    Pexp = []
-    for r in p.r:
-        Pexp.append((np.conj(P) * np.roll(P, -r, axis=2)).mean())
-    W = np.zeros((len(p.rf), len(p.probes), 6, 2), dtype=complex)
-    for a, rf in enumerate(p.rf):
-        pp = np.conj(P) * np.roll(P, -rf, axis=2)
-        for b, (dy, dz) in enumerate(p.probes):
-            for c in range(6):
-                if not (p.comp_mask >> c) & 1:
-                    continue
-                for k in range(2):
-                    o = np.roll(ft[c, k], shift=(-dz, -dy, -(rf // 2)), axis=(0, 1, 2))
-                    W[a, b, c, k] = (pp * o).sum() / (p.Ns * Nt)
-    return np.array(Pexp), W
 
 
 @pytest.mark.parametrize("two_level", [False, True])
