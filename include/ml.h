@@ -48,9 +48,13 @@ typedef enum {
 
 typedef enum {
   ML_FP64 = 0, /* link angles and update arithmetic in double precision       */
-  ML_FP32 = 1  /* link angles and update arithmetic in single precision; slab
-                  sums as double-length float pairs (about 47 bits), averages,
-                  products and final ratios in double                         */
+  ML_FP32 = 1  /* link angles, update arithmetic and the per-sub-update
+                  records (slab phase sums, plaquette slab sums) in single
+                  precision; each fold adds the single-precision sum of a
+                  batch of up to 16 sub-update terms to double-precision slab
+                  sums; slab averages, level combination, cross-slab products,
+                  reductions over sites and final ratios in double precision
+                  (pair_sums = 1 keeps the slab sums as float pairs instead)  */
 } ml_precision;
 
 /* Transverse offset (dy, dz) of a field probe from the mid-point of the
@@ -75,8 +79,8 @@ typedef enum {
  * |dy|, |dz| <= L-1; beta >= 0; k_between >= 0; n_or >= 0; comp_mask < 64;
  * at least one r; update an ml_update, and for Metropolis 1 <= metro_hits <= 64
  * and 0 < metro_width <= pi; multihit 0 or 1, with multihit beta <= 100;
- * replay 0 or 1, with replay outer_slab = 0.  The lists are copied by
- * ml_create. */
+ * replay 0 or 1, with replay outer_slab = 0; pair_sums 0, or 1 with prec =
+ * ML_FP32.  The lists are copied by ml_create. */
 typedef struct {
   int L, Nt;            /* spatial and temporal extent                         */
   double beta;          /* inverse coupling 1/g^2 of the Wilson action         */
@@ -111,6 +115,13 @@ typedef struct {
                            other slabs' [T] straight into the products, so no
                            per-site [TO] sums are kept (same estimator, the
                            field-insertion memory for twice the slab sweeps) */
+  int pair_sums;        /* ML_FP32 only.  0 (default): slab sums in double
+                           precision.  1: each slab sum kept as an unevaluated
+                           sum hi + lo of two binary32 numbers (about 47
+                           significant bits; error-free additions on the
+                           single-precision pipe, which this GPU runs far
+                           faster than its double-precision one); averages,
+                           products and reductions stay double precision      */
 } ml_params;
 
 /* Device-memory allocator supplied by the caller (the Python binding passes

@@ -108,6 +108,7 @@ int validate(const ml_params* p) {
     return ML_EINVAL;
   if (p->multihit < 0 || p->multihit > 1 || (p->multihit && p->beta > 100.0)) return ML_EINVAL;
   if (p->replay < 0 || p->replay > 1 || (p->replay && p->outer_slab != 0)) return ML_EINVAL;
+  if (p->pair_sums < 0 || p->pair_sums > 1 || (p->pair_sums && p->prec != ML_FP32)) return ML_EINVAL;
   return ML_OK;
 }
 
@@ -392,14 +393,14 @@ int hand_over(Engine* e, int buf, int nrec, bool defer_O, bool first) {
     // replay: this buffer's field insertions times the final slab averages
     // straight into the products' partial sums
     for (LatState* L : e->lats)
-      launch_replay_W(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, 1.0 / e->n_sub, L->partial,
+      launch_replay_W(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, 1.0 / e->n_sub, L->partial,
                       ProductTail{L->theta_rec[buf], L->osum[buf], nrec, 1, first ? 0 : 1}, e->side);
     ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
     return ML_OK;
   }
   // the replay's first pass forms the slab averages [T] (and the vacuum) only
   const bool skip_O = defer_O || e->pass == 1;
-  launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, nrec, e->side, skip_O, first);
+  launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, buf, nrec, e->side, skip_O, first);
   if (!defer_O) ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
   return ML_OK;
 }
@@ -544,7 +545,7 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       if (st) return st;
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
-        launch_products(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, nullptr, 1.0 / e->n_sub, L->partial,
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, nullptr, 1.0 / e->n_sub, L->partial,
                         out[li], e->side, ProductTail{}, true);
       }
       ncfg = e->n_sub;
@@ -556,7 +557,7 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       if (st) return st;
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
-        launch_products(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
                         out[li], e->side, ProductTail{L->theta_rec[tb], L->osum[tb], tn, tfirst ? 1 : 0});
       }
       ML_CUDA(cudaEventRecord(e->ev_fold[tb], e->side));  // the tail buffer is free after the products
@@ -571,12 +572,12 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
         if (!st) st = run_inner_loop(e);
         if (st) return st;
         for (LatState* L : e->lats)
-          launch_combine(L->g, L->g.Nt / e->outer_slab, e->outer_slab / e->slab, L->meas, !e->fp64, L->accT,
+          launch_combine(L->g, L->g.Nt / e->outer_slab, e->outer_slab / e->slab, L->meas, e->pairs, L->accT,
                          L->accO, 1.0 / e->n_sub, L->acc4T, L->acc4O, e->side);
       }
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
-        launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, !e->fp64, L->acc4T, L->acc4O,
+        launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, e->fp64, e->pairs, L->acc4T, L->acc4O,
                         1.0 / e->n_sub_outer, L->partial, out[li], e->side);
       }
       ncfg = e->n_sub * e->n_sub_outer;
@@ -682,7 +683,7 @@ int choose_fold_mode(Engine* e) {
       e->td.fold_tile_on = mode == 1;
       st = cuda_status(cudaEventRecord(ev[0], e->stream));
       for (int rep = 0; rep < 2 && !st; ++rep)
-        launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, 0, e->nB, e->stream, false, false);
+        launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, 0, e->nB, e->stream, false, false);
       if (!st) st = cuda_status(cudaEventRecord(ev[1], e->stream));
       if (!st) st = cuda_status(cudaEventSynchronize(ev[1]));
       float ms = 0.f;
@@ -784,12 +785,13 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
     const ml_params& b = ps[i];
     if (a.prec != b.prec || a.n_or != b.n_or || a.slab != b.slab || a.outer_slab != b.outer_slab ||
         a.n_sub != b.n_sub || a.k_between != b.k_between || (a.outer_slab && a.n_sub_outer != b.n_sub_outer) ||
-        a.replay != b.replay)
+        a.replay != b.replay || a.pair_sums != b.pair_sums)
       return ML_EINVAL;
   }
   e->replay = ps[0].replay != 0;
   if (prepare_measure_kernels()) return ML_ECUDA;
   e->fp64 = ps[0].prec == ML_FP64;
+  e->pairs = ps[0].pair_sums != 0;
   e->nB = rec_batch(e->fp64);
   e->n_or = ps[0].n_or;
   e->slab = ps[0].slab;
@@ -1040,12 +1042,12 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
   launch_record_table(e->fp64, e->d_desc, e->td, nullptr, buf, 0, e->stream);
   if (e->replay) {
     // no stored insertion sums: the products take the one record as their tail
-    launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream, true, true);
-    launch_products(L->g, L->g.Nt / e->slab, m, !e->fp64, L->accT, nullptr, 1.0, L->partial, out, e->stream,
+    launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, buf, 1, e->stream, true, true);
+    launch_products(L->g, L->g.Nt / e->slab, m, e->fp64, e->pairs, L->accT, nullptr, 1.0, L->partial, out, e->stream,
                     ProductTail{L->theta_rec[buf], L->osum[buf], 1, 1, 0});
   } else {
-    launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, buf, 1, e->stream, false, true);
-    launch_products(L->g, L->g.Nt / e->slab, m, !e->fp64, L->accT, L->accO, 1.0, L->partial, out, e->stream);
+    launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, buf, 1, e->stream, false, true);
+    launch_products(L->g, L->g.Nt / e->slab, m, e->fp64, e->pairs, L->accT, L->accO, 1.0, L->partial, out, e->stream);
   }
   launch_write_vac(L->vac_acc, 1.0, m, out, e->stream);
   ML_CUDA(cudaGetLastError());
@@ -1188,14 +1190,14 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
         launch_record_table(e->fp64, e->d_desc, e->td, nullptr, 0, 0, e->stream);
         break;
       case ML_K_ACCUMULATE:  // replay: the first pass's fold and the second pass's insertions of one buffer
-        launch_fold_table(e->fp64, e->d_desc, e->td, nullptr, 0, e->nB, e->stream);
+        launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, 0, e->nB, e->stream);
         if (e->replay)
           for (LatState* Lr : e->lats)
-            launch_replay_W(Lr->g, Lr->g.Nt / e->slab, Lr->meas, !e->fp64, Lr->accT, 1.0, Lr->partial,
+            launch_replay_W(Lr->g, Lr->g.Nt / e->slab, Lr->meas, e->fp64, e->pairs, Lr->accT, 1.0, Lr->partial,
                             ProductTail{Lr->theta_rec[0], Lr->osum[0], e->nB, 1, 1}, e->stream);
         break;
       case ML_K_PRODUCTS:
-        launch_products(L->g, L->g.Nt / e->slab, L->meas, !e->fp64, L->accT, L->accO, 1.0, L->partial, e->rec_buf,
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0, L->partial, e->rec_buf,
                         e->stream, ProductTail{}, e->replay);
         break;
       case ML_K_SWEEP:

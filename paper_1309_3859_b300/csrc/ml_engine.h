@@ -50,6 +50,7 @@ struct LatState {
 // A set of lattices advanced by one schedule (Algorithm 1 in lockstep).
 struct Engine {
   bool fp64 = true;
+  bool pairs = false;  // FP32 lattices with float-pair slab sums (ml_params.pair_sums)
   int n_or = 3, slab = 2, outer_slab = 0, n_sub = 1, n_sub_outer = 0, k_between = 0;
   bool replay = false;  // field insertions by replay of the inner loop
   int pass = 0;         // inner loop being run: 0 direct, 1 replay's slab averages, 2 replay's insertions

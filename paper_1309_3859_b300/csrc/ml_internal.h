@@ -46,7 +46,7 @@ struct LatDesc {
   void* mh_rec[2];            // multihit ring [nslab][2][slots][Ns] (modulus, phase); null: none
   void* osum[2];              // [nslab][nc][2][slots][Ns], slots = rec_batch(fp64)
   double2* accT;              // inner slab sums: double2 (re, im), or for FP32
-  double2* accO;              //   lattices float4 (re_hi, re_lo, im_hi, im_lo)
+  double2* accO;              //   lattices with float-pair sums float4 (re_hi, re_lo, im_hi, im_lo)
   double* vac_part;           // [nc * 2][nparts] block partials of the vacuum sums of a fold
   int nparts;                 // vacuum blocks per part (vac_part_count)
   double* vac_acc;            // [12] vacuum sums of the folded configurations
@@ -118,10 +118,11 @@ void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const
 void launch_mh_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
                             cudaStream_t s);
 // fold slots 0 .. nrec-1 of ring buffer buf into each lattice's slab sums,
-// and their vacuum sums into vac_acc (skip_O: leave the field-insertion sums
-// to a products launch with that buffer as its tail; overwrite: the slab sums
-// start from zero instead of their stored values)
-void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
+// and their vacuum sums into vac_acc (pairs: FP32 lattices with float-pair
+// slab sums; skip_O: leave the field-insertion sums to a products launch with
+// that buffer as its tail; overwrite: the slab sums start from zero instead of
+// their stored values)
+void launch_fold_table(bool fp64, bool pairs, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
                        cudaStream_t s, bool skip_O = false, bool overwrite = false);
 int record_blocks(const Geom& g, int d);
 // kernel attributes of the measurement kernels (before any launch or capture); 0 or -1
@@ -147,8 +148,8 @@ void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size
 
 // ---- measurement (ml_measure.cu) ----
 int vac_part_count(const Geom& g, int d);
-// two-level combination of inner averages (sum / n_inner) into outer sums
-// (pairs: all slab sums are the FP32 lattices' float-pair accumulators)
+// two-level combination of inner averages (sum / n_inner) into outer sums,
+// in double precision (pairs: all slab sums are float-pair accumulators)
 void launch_combine(const Geom& g, int n_inner_slabs, int q, const MeasLayout& m, bool pairs, const void* accT,
                     const void* accO, double inv_n, void* acc4T, void* acc4O, cudaStream_t s);
 int product_partial_count(const Geom& g);
@@ -161,16 +162,17 @@ struct ProductTail {
   int overwrite = 0;  // the stored field-insertion sums are not yet written: start from zero
   int add = 0;        // add the W partials to the stored ones (later batches of a replay)
 };
-// cross-slab products of the averages sum / n, reduced over x into the
-// record's P, Pf and W blocks (pairs: as for launch_combine)
-void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, const void* accO,
+// cross-slab products of the averages sum / n, in double precision, reduced
+// over x into the record's P, Pf and W blocks (fp64: the lattice's precision;
+// pairs: as for launch_fold_table)
+void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT, const void* accO,
                      double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail = {},
                      bool W_done = false);
 // replay: the W partials of one ring buffer's records (tail.nrec of them)
 // times the final slab averages, stored (tail.add = 0) or added to the stored
 // partials; W_done in the final launch_products then only adds P and finalises
-void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, double inv_n,
-                     double2* partial, const ProductTail& tail, cudaStream_t s);
+void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
+                     double inv_n, double2* partial, const ProductTail& tail, cudaStream_t s);
 // naive P+P and mean plaquette of the current configuration
 void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,
                                 double* rec, cudaStream_t s);

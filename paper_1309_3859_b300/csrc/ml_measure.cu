@@ -11,13 +11,16 @@
 //   P(r)   = (1/Ns) sum_x prod_s [T]_s(x, r)
 //   W      = (1/(Ns Nt)) sum_x sum_s [TO]_s(x) prod_{s' != s} [T]_{s'}(x)
 //
-// Slab sums live in complex accumulators (double, or double-length float pairs
-// for FP32 lattices) laid out with the spatial site x fastest, so one warp touches 32 consecutive sites.  All
-// reductions over sites are warp-shuffle trees writing per-warp partials,
-// followed by fixed-order sums: results do not depend on scheduling.
+// Slab sums live in complex accumulators (double, or on request double-length
+// float pairs for FP32 lattices) laid out with the spatial site x fastest, so
+// one warp touches 32 consecutive sites; averages, products and reductions are
+// formed in double precision.  All reductions over sites are warp-shuffle
+// trees writing per-warp partials, followed by fixed-order sums: results do
+// not depend on scheduling.
 #include <algorithm>
 #include <type_traits>
 
+#include "ml_convert.cuh"
 #include "ml_record.cuh"
 #include "ml_sync.cuh"
 
@@ -173,46 +176,34 @@ __global__ void __launch_bounds__(384) k_vac_final_table(const LatDesc* __restri
   if (lane == 0) L.vac_acc[2 * L.m.comp[part >> 1] + (part & 1)] += v * (1.0 / L.g.V);
 }
 
-// Slab sums (inner and outer).  FP64 lattices keep double2 (re, im) sums and
-// do all measurement arithmetic in double.  FP32 lattices keep each part as
-// an unevaluated sum hi + lo of two binary32 numbers (Dekker's double-length
-// representation, about 47 significant bits), packed as float4 (re_hi, re_lo,
-// im_hi, im_lo) in the same 16 bytes: a value enters with Knuth's error-free
-// TwoSum followed by a renormalisation, and products use the averages rounded
-// to binary32, the precision of the lattice's own link phases.  All of this
-// runs on the FP32 pipe, which retires far more operations per clock than the
-// double-precision pipe of this part.  The explicit _rn intrinsics keep the
-// compiler from contracting or reassociating the error terms.
-template <typename T>
-struct SlabAcc {
-  using type = double2;
-};
-template <>
-struct SlabAcc<float> {
-  using type = float4;
-};
+// Slab sums (inner and outer), 16 bytes per complex value.  The default for
+// every lattice is double2 (re, im): a fold adds each batch sum of 16
+// sub-update terms, formed in the records' precision, to the FP64 sums.  On
+// request (ml_params.pair_sums) FP32 lattices keep each part instead as an
+// unevaluated sum hi + lo of two binary32 numbers (Dekker's double-length
+// representation, about 47 significant bits), packed as float4 (re_hi,
+// re_lo, im_hi, im_lo): a value enters with Knuth's error-free TwoSum and a
+// renormalisation on the FP32 pipe, which retires far more operations per
+// clock than the double-precision pipe of this part.  The explicit _rn
+// intrinsics keep the compiler from contracting or reassociating the error
+// terms.  Either way the averages, the level combination, the cross-slab
+// products and every reduction over sites are formed in double precision
+// (Section II.C: the products fall as exp(-V(r) Nt)).
 
-// arithmetic of the products formed from slab sums of type A
-template <typename A>
-struct AccMath;
-template <>
-struct AccMath<double2> {
-  static constexpr bool fp64 = true;
-  using real = double;
-  using cplx = double2;
-  __device__ static __forceinline__ double2 value(const double2& a) { return a; }
-  __device__ static __forceinline__ double2 make(double re, double im) { return make_double2(re, im); }
-};
-template <>
-struct AccMath<float4> {
-  static constexpr bool fp64 = false;
-  using real = float;
-  using cplx = float2;
-  __device__ static __forceinline__ float2 value(const float4& a) {
-    return make_float2(__fadd_rn(a.x, a.y), __fadd_rn(a.z, a.w));
-  }
-  __device__ static __forceinline__ float2 make(float re, float im) { return make_float2(re, im); }
-};
+// the slab sum as a double-precision complex number
+__device__ __forceinline__ double2 acc_value(const double2& a) { return a; }
+__device__ __forceinline__ double2 acc_value(const float4& a) {
+  return make_double2(exact_double(a.x) + exact_double(a.y), exact_double(a.z) + exact_double(a.w));
+}
+// s + a b in four fused multiply-adds (the double-precision pipe is this
+// part's scarce resource in the products)
+__device__ __forceinline__ double2 cmac(double2 s, double2 a, double2 b) {
+  s.x = fma(a.x, b.x, s.x);
+  s.x = fma(-a.y, b.y, s.x);
+  s.y = fma(a.x, b.y, s.y);
+  s.y = fma(a.y, b.x, s.y);
+  return s;
+}
 
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
   const float s = __fadd_rn(hi, v);
@@ -226,9 +217,23 @@ __device__ __forceinline__ void acc_add(double2& a, double re, double im) {
   a.x += re;
   a.y += im;
 }
+// a single-precision batch sum into double-precision sums
+__device__ __forceinline__ void acc_add(double2& a, float re, float im) {
+  a.x += exact_double(re);
+  a.y += exact_double(im);
+}
 __device__ __forceinline__ void acc_add(float4& a, float re, float im) {
   ff_add(a.x, a.y, re);
   ff_add(a.z, a.w, im);
+}
+// a double-precision value into a float pair: its leading binary32 part,
+// then the binary32 rounding of the rest (the two parts carry 48 bits)
+__device__ __forceinline__ void acc_add(float4& a, double re, double im) {
+  const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+  ff_add(a.x, a.y, rh);
+  ff_add(a.x, a.y, __double2float_rn(re - static_cast<double>(rh)));
+  ff_add(a.z, a.w, ih);
+  ff_add(a.z, a.w, __double2float_rn(im - static_cast<double>(ih)));
 }
 
 // e^{i (Theta(x + r) - Theta(x))} for the first nrec records, zero beyond
@@ -249,7 +254,7 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 }
 
 // ---------------------------------------------------------------------------
-// Fold of nrec <= slots records into the slab sums (SlabAcc<T>); with
+// Fold of nrec <= slots records into the slab sums (type A); with
 // `overwrite` the sums start from zero (the first fold of an inner loop), so
 // they need no clearing and are not read:
 //   accT[s][a][x]              += sum_j T_j(x, s, R_a)
@@ -260,7 +265,7 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
 // do not push out the ring buffer's records, which every (separation, probe)
 // reads again.
 // ---------------------------------------------------------------------------
-template <typename T, bool MH>
+template <typename T, typename A, bool MH>
 __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict__ desc,
                                                        const LatCtl* __restrict__ ctl, int buf, int nrec,
                                                        int overwrite) {
@@ -304,7 +309,6 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
     sr += er[j];
     si += ei[j];
   }
-  using A = typename SlabAcc<T>::type;
   A* p = reinterpret_cast<A*>(L.accT) + (static_cast<size_t>(s) * m.nR + a) * g.Ns + x;
   A v = overwrite ? A{} : *p;  // a first fold adds to zero sums without reading them
   acc_add(v, sr, si);
@@ -319,7 +323,7 @@ constexpr int fold_min_blocks() {
   return sizeof(T) == 4 ? 4 : 2;
 }
 
-template <typename T>
+template <typename T, typename A>
 __global__ void __launch_bounds__(256, fold_min_blocks<T>())
     k_accum_O_table(const LatDesc* __restrict__ desc, const LatCtl* __restrict__ ctl, int buf, int nrec,
                     int overwrite) {
@@ -346,7 +350,6 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
   const int xr = wrapc(cx + rf, g.L) + g.L * (cy + g.L * cz);
   const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]);
   const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
-  using A = typename SlabAcc<T>::type;
   A* __restrict__ acc = reinterpret_cast<A*>(L.accO);
   T er[B], ei[B];
   batch_phases<T>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, nrec, er, ei);
@@ -430,14 +433,13 @@ constexpr int tile_min_blocks() {
   return sizeof(T) == 4 ? 3 : 2;
 }
 
-template <typename T>
+template <typename T, typename A>
 __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_tile(const LatDesc* __restrict__ desc,
                                                                                     const LatCtl* __restrict__ ctl,
                                                                                     int buf, int nrec,
                                                                                     int overwrite) {
   constexpr int B = RecBatch<T>::n;
   constexpr int CH = 16 / static_cast<int>(sizeof(T));  // elements per 16-byte chunk
-  using A = typename SlabAcc<T>::type;
   extern __shared__ __align__(16) unsigned char tile_smem[];
   T* const tile = reinterpret_cast<T*>(tile_smem);
   const int li = blockIdx.z;
@@ -544,40 +546,38 @@ bool fold_tile_plan(bool fp64, int L, const int* pdy, const int* pdz, int np, in
 // ---------------------------------------------------------------------------
 // Two-level combination: for outer slab S with inner slabs j = q S + jj,
 //   acc4T += prod_jj [T]_j ,  acc4O += sum_jj [TO]_j prod_{jj' != jj} [T]_j'
-// with [.] = inner sum / n_inner, in the arithmetic of AccMath<A>.
+// with [.] = inner sum / n_inner, in double precision (A: the slab sums' type,
+// inner and outer alike).
 // ---------------------------------------------------------------------------
 template <typename A>
 __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, MeasLayout m,
                                                  const A* __restrict__ accT, const A* __restrict__ accO,
                                                  double inv_n, A* __restrict__ acc4T, A* __restrict__ acc4O) {
-  using M = AccMath<A>;
-  using C = typename M::cplx;
-  using R = typename M::real;
-  const R in = static_cast<R>(inv_n);
+  const double in = inv_n;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.Ns * n_outer) return;
   const int S = idx / g.Ns;
   const int x = idx - S * g.Ns;
   for (int a = 0; a < m.nR; ++a) {
-    C prod = M::make(R(1), R(0));
+    double2 prod = make_double2(1.0, 0.0);
     for (int jj = 0; jj < q; ++jj)
-      prod = cmul(prod, cscale(M::value(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x]), in));
+      prod = cmul(prod, cscale(acc_value(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x]), in));
     A* p = acc4T + (static_cast<size_t>(S) * m.nR + a) * g.Ns + x;
     A v = *p;
     acc_add(v, prod.x, prod.y);
     *p = v;
   }
-  C tj[kMaxSlabs], rest[kMaxSlabs];
+  double2 tj[kMaxSlabs], rest[kMaxSlabs];
   for (int f = 0; f < m.nrf; ++f) {
     const int a = m.rf_idx[f];
     for (int jj = 0; jj < q; ++jj)
-      tj[jj] = cscale(M::value(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x]), in);
-    C run = M::make(R(1), R(0));
+      tj[jj] = cscale(acc_value(accT[(static_cast<size_t>(q * S + jj) * m.nR + a) * g.Ns + x]), in);
+    double2 run = make_double2(1.0, 0.0);
     for (int jj = 0; jj < q; ++jj) {  // prefix products
       rest[jj] = run;
       run = cmul(run, tj[jj]);
     }
-    run = M::make(R(1), R(0));
+    run = make_double2(in, 0.0);  // the 1/n_inner of [TO]_j
     for (int jj = q - 1; jj >= 0; --jj) {  // times suffix products
       rest[jj] = cmul(rest[jj], run);
       run = cmul(run, tj[jj]);
@@ -585,11 +585,11 @@ __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, Mea
     for (int b = 0; b < m.np; ++b)
       for (int ci = 0; ci < m.nc; ++ci)
         for (int k = 0; k < 2; ++k) {
-          C sum = M::make(R(0), R(0));
+          double2 sum = make_double2(0.0, 0.0);
           for (int jj = 0; jj < q; ++jj) {
-            const C o = M::value(__ldcs(
+            const double2 o = acc_value(__ldcs(
                 accO + ((((static_cast<size_t>(q * S + jj) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x));
-            sum = cadd(sum, cmul(cscale(o, in), rest[jj]));
+            sum = cmac(sum, o, rest[jj]);
           }
           A* p = acc4O + ((((static_cast<size_t>(S) * m.nrf + f) * m.np + b) * m.nc + ci) * 2 + k) * g.Ns + x;
           A v = __ldcs(p);
@@ -607,51 +607,26 @@ __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, Mea
 //                           R_s = prod_{s' != s} [T]_{s'} (prefix x suffix),
 //                           j = (b * nc + ci) * 2 + k
 // k_products_P: grid (sites, nr + nrf); k_products_W: grid (sites, nrf,
-// chunks of kWChunk values of j).  FP64 sums: products of the raw sums, one
-// factor (1/n)^nslab at the end.  FP32 sums: every factor scaled by 1/n as it
-// is read, so no nslab over- or underflows binary32; the per-warp partials
-// are written in double.
+// chunks of kWChunk values of j).  All in double precision: every [T] factor
+// is the average sum / n (scaled as it is read, so no product of many slabs
+// over- or underflows), [TO] is scaled by 1/n once at the end.
 // ---------------------------------------------------------------------------
 constexpr int kWChunk = 6;         // values of j per thread
-constexpr int kProdMinBlocks = 3;  // launch bound: blocks per SM (80 registers, no spills)
-
-template <typename M>
-__device__ __forceinline__ typename M::cplx slab_factor(typename M::cplx t, typename M::real in) {
-  if constexpr (M::fp64)
-    return t;
-  else
-    return cscale(t, in);
-}
-template <typename M>
-__device__ __forceinline__ typename M::real final_scale(int nslab, double inv_n) {
-  if constexpr (M::fp64) {
-    double scale = 1.0;
-    for (int s = 0; s < nslab; ++s) scale *= inv_n;
-    return scale;
-  } else {
-    return static_cast<float>(inv_n);  // the one factor of [TO] (W); P(r) passes 1
-  }
-}
+constexpr int kProdMinBlocks = 3;  // launch bound of the products without a tail: blocks per SM
 
 template <typename A>
 __global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT,
                                                     double inv_n, double2* __restrict__ partial, int nwarps) {
-  using M = AccMath<A>;
-  using C = typename M::cplx;
-  using R = typename M::real;
-  const R in = static_cast<R>(inv_n);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = x < g.Ns;
   const int o = blockIdx.y;
   const int a = o < m.nr ? m.r_idx[o] : m.rf_idx[o - m.nr];
-  C prod = M::make(live ? R(1) : R(0), R(0));
+  double2 prod = make_double2(live ? 1.0 : 0.0, 0.0);
   if (live)
     for (int s = 0; s < nslab; ++s)
-      prod = cmul(prod, slab_factor<M>(M::value(accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]), in));
-  if constexpr (M::fp64) prod = cscale(prod, final_scale<M>(nslab, inv_n));
+      prod = cmul(prod, cscale(acc_value(accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]), inv_n));
   prod = warp_sum(prod);
-  if ((threadIdx.x & 31) == 0)
-    partial[static_cast<size_t>(o) * nwarps + (x >> 5)] = make_double2(prod.x, prod.y);
+  if ((threadIdx.x & 31) == 0) partial[static_cast<size_t>(o) * nwarps + (x >> 5)] = prod;
 }
 
 // One thread: site x, field separation f, kWChunk values of j.  Suffix
@@ -661,47 +636,34 @@ __global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayou
 // records of ring buffer (trec, osum) exactly as k_accum_O_table would have
 // (same batch sum, same accumulator update), without writing them back: the
 // measurement's final fold of the field insertions and the products in one
-// pass over the slab sums.  TB: 0 without a tail, else the ring slots read
-// (nrec rounded up to 4, 8 or 16; the slots beyond nrec add exact zeros, so
-// fewer of them leave every sum unchanged).
-template <typename A>
-struct RecOf {
-  using type = double;
-};
-template <>
-struct RecOf<float4> {
-  using type = float;
-};
-
-template <typename A, int TB>
-__global__ void __launch_bounds__(256, TB == 0 || (TB == 4 && std::is_same<A, float4>::value) ? kProdMinBlocks : 2)
+// pass over the slab sums.  T: the records' type; A: the slab sums' type.
+// TB: 0 without a tail, else the ring slots read (nrec rounded up to 4, 8 or
+// 16; the slots beyond nrec add exact zeros, so fewer of them leave every sum
+// unchanged).
+template <typename T, typename A, int TB>
+__global__ void __launch_bounds__(256, TB == 0 ? kProdMinBlocks : 2)
     k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT, const A* __restrict__ accO,
                  double inv_n, double2* __restrict__ partial, int nwarps, ProductTail tail) {
-  using M = AccMath<A>;
-  using C = typename M::cplx;
-  using R = typename M::real;
-  using T = typename RecOf<A>::type;
   constexpr bool TAIL = TB > 0;
   constexpr int B = TAIL ? TB : 1;
   static_assert(B <= RecBatch<T>::n, "a tail holds at most one ring buffer");
-  const R in = static_cast<R>(inv_n);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = x < g.Ns;
   const int f = blockIdx.y;
   const int nW = m.np * m.nc * 2;
   const int j0 = blockIdx.z * kWChunk;
   const int nj = min(nW - j0, kWChunk);
-  C sum[kWChunk];
+  double2 sum[kWChunk];
 #pragma unroll
-  for (int q = 0; q < kWChunk; ++q) sum[q] = M::make(R(0), R(0));
+  for (int q = 0; q < kWChunk; ++q) sum[q] = make_double2(0.0, 0.0);
   if (live) {
     const size_t tstride = static_cast<size_t>(m.nR) * g.Ns;  // slab stride of accT
     const A* tcol = accT + static_cast<size_t>(m.rf_idx[f]) * g.Ns + x;
-    C suf[kMaxSlabs];  // suf[s] = prod_{s' > s} [T]_{s'}
-    C run = M::make(R(1), R(0));
+    double2 suf[kMaxSlabs];  // suf[s] = prod_{s' > s} [T]_{s'}
+    double2 run = make_double2(1.0, 0.0);
     for (int s = nslab - 1; s >= 0; --s) {
       suf[s] = run;
-      run = cmul(run, slab_factor<M>(M::value(tcol[s * tstride]), in));
+      run = cmul(run, cscale(acc_value(tcol[s * tstride]), inv_n));
     }
     // tail: the partner site x + rf of the phases, and per value q its
     // insertion site x0 (probe b) and osum row (ci, k) within a slab, all
@@ -719,9 +681,9 @@ __global__ void __launch_bounds__(256, TB == 0 || (TB == 4 && std::is_same<A, fl
         x0q[q] = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
       }
     }
-    run = M::make(R(1), R(0));  // prod_{s' < s} [T]_{s'}
+    run = make_double2(1.0, 0.0);  // prod_{s' < s} [T]_{s'}
     for (int s = 0; s < nslab; ++s) {
-      const C rest = cmul(run, suf[s]);
+      const double2 rest = cmul(run, suf[s]);
       const bool fresh = TAIL && tail.overwrite;  // no stored sums (replay: accO is null)
       const A* ocol = fresh ? nullptr : accO + (static_cast<size_t>(s * m.nrf + f) * nW + j0) * g.Ns + x;
       A o[kWChunk];
@@ -749,19 +711,17 @@ __global__ void __launch_bounds__(256, TB == 0 || (TB == 4 && std::is_same<A, fl
       }
 #pragma unroll
       for (int q = 0; q < kWChunk; ++q)
-        if (q < nj) sum[q] = cadd(sum[q], cmul(M::value(o[q]), rest));
-      run = cmul(run, slab_factor<M>(M::value(tcol[s * tstride]), in));
+        if (q < nj) sum[q] = cmac(sum[q], acc_value(o[q]), rest);
+      run = cmul(run, cscale(acc_value(tcol[s * tstride]), inv_n));
     }
   }
-  const R scale = final_scale<M>(nslab, inv_n);
 #pragma unroll
   for (int q = 0; q < kWChunk; ++q) {
     if (q >= nj) break;
-    const C w = warp_sum(cscale(sum[q], scale));
+    const double2 w = warp_sum(cscale(sum[q], inv_n));
     if ((threadIdx.x & 31) == 0) {
       double2* p = partial + static_cast<size_t>(m.nr + m.nrf + f * nW + j0 + q) * nwarps + (x >> 5);
-      const double2 v = make_double2(w.x, w.y);
-      *p = (TAIL && tail.add) ? cadd(*p, v) : v;
+      *p = (TAIL && tail.add) ? cadd(*p, w) : w;
     }
   }
 }
@@ -944,50 +904,58 @@ void launch_mh_record_table(bool fp64, const LatDesc* d, const TableDims& td, co
   count_launches(1);
 }
 
+// Calls f(T{}, A{}) with the records' type T and the slab sums' type A of a
+// table: FP64 lattices (double, double2); FP32 lattices (float, double2), or
+// (float, float4) with float-pair sums.
+template <typename F>
+static void with_sum_types(bool fp64, bool pairs, F&& f) {
+  if (fp64)
+    f(double{}, double2{});
+  else if (pairs)
+    f(float{}, float4{});
+  else
+    f(float{}, double2{});
+}
+
 int prepare_measure_kernels() {
   const int most = static_cast<int>(kTileSmemMax);  // above the 48 KB default of dynamic shared memory
-  cudaError_t e = cudaFuncSetAttribute(k_accum_O_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_accum_O_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+  cudaError_t e = cudaSuccess;
+  for (int v = 0; v < 3; ++v)
+    with_sum_types(v == 0, v == 2, [&](auto t, auto a) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_accum_O_tile<decltype(t), decltype(a)>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    });
   return e == cudaSuccess ? 0 : -1;
 }
 
-void launch_fold_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int nrec,
-                       cudaStream_t s, bool skip_O, bool overwrite) {
+void launch_fold_table(bool fp64, bool pairs, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf,
+                       int nrec, cudaStream_t s, bool skip_O, bool overwrite) {
   const int ow = overwrite ? 1 : 0;
-  const dim3 gt(td.max_blocks_site, td.max_y_T, td.nlat);
-  // the multihit variant (more registers) only for tables with multihit lattices
-  if (fp64)
-    (td.max_blocks_mh > 0 ? k_accum_T_table<double, true> : k_accum_T_table<double, false>)<<<gt, 256, 0, s>>>(
+  with_sum_types(fp64, pairs, [&](auto t, auto a) {
+    using T = decltype(t);
+    using A = decltype(a);
+    const dim3 gt(td.max_blocks_site, td.max_y_T, td.nlat);
+    // the multihit variant (more registers) only for tables with multihit lattices
+    (td.max_blocks_mh > 0 ? k_accum_T_table<T, A, true> : k_accum_T_table<T, A, false>)<<<gt, 256, 0, s>>>(
         d, ctl, buf, nrec, ow);
-  else
-    (td.max_blocks_mh > 0 ? k_accum_T_table<float, true> : k_accum_T_table<float, false>)<<<gt, 256, 0, s>>>(
-        d, ctl, buf, nrec, ow);
-  count_launches(1);
-  if (td.max_y_O > 0 && !skip_O && td.fold_tile && td.fold_tile_on) {
-    const dim3 go(td.fold_tile_bx, td.max_y_T_O, td.nlat);
-    if (fp64)
-      k_accum_O_tile<double><<<go, kTileThreads, td.fold_tile_smem, s>>>(d, ctl, buf, nrec, ow);
-    else
-      k_accum_O_tile<float><<<go, kTileThreads, td.fold_tile_smem, s>>>(d, ctl, buf, nrec, ow);
     count_launches(1);
-  } else if (td.max_y_O > 0 && !skip_O) {
-    const dim3 go(td.max_blocks_site, td.max_y_O, td.nlat);
-    if (fp64)
-      k_accum_O_table<double><<<go, 256, 0, s>>>(d, ctl, buf, nrec, ow);
-    else
-      k_accum_O_table<float><<<go, 256, 0, s>>>(d, ctl, buf, nrec, ow);
-    count_launches(1);
-  }
-  if (td.max_vac_parts > 0) {
-    const dim3 gv(td.max_vac_blocks, td.max_vac_parts, td.nlat);
-    if (fp64)
-      k_vac_partial_table<double><<<gv, 256, 0, s>>>(d, ctl, buf, nrec);
-    else
-      k_vac_partial_table<float><<<gv, 256, 0, s>>>(d, ctl, buf, nrec);
-    k_vac_final_table<<<td.nlat, 384, 0, s>>>(d, ctl);
-    count_launches(2);
-  }
+    if (td.max_y_O > 0 && !skip_O && td.fold_tile && td.fold_tile_on) {
+      const dim3 go(td.fold_tile_bx, td.max_y_T_O, td.nlat);
+      k_accum_O_tile<T, A><<<go, kTileThreads, td.fold_tile_smem, s>>>(d, ctl, buf, nrec, ow);
+      count_launches(1);
+    } else if (td.max_y_O > 0 && !skip_O) {
+      const dim3 go(td.max_blocks_site, td.max_y_O, td.nlat);
+      k_accum_O_table<T, A><<<go, 256, 0, s>>>(d, ctl, buf, nrec, ow);
+      count_launches(1);
+    }
+    if (td.max_vac_parts > 0) {
+      const dim3 gv(td.max_vac_blocks, td.max_vac_parts, td.nlat);
+      k_vac_partial_table<T><<<gv, 256, 0, s>>>(d, ctl, buf, nrec);
+      k_vac_final_table<<<td.nlat, 384, 0, s>>>(d, ctl);
+      count_launches(2);
+    }
+  });
 }
 
 void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, bool pairs, const void* accT,
@@ -1005,65 +973,57 @@ void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, bool
 }
 
 // k_products_W with the tail's slot count
-template <typename A>
+template <typename T, typename A>
 static void launch_products_W(dim3 grid, const Geom& g, int nslab, const MeasLayout& m, const A* accT, const A* accO,
                               double inv_n, double2* partial, int nwarps, const ProductTail& tail, cudaStream_t s) {
   if (tail.nrec <= 0)
-    k_products_W<A, 0><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
+    k_products_W<T, A, 0><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
   else if (tail.nrec <= 4)
-    k_products_W<A, 4><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
+    k_products_W<T, A, 4><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
   else if (tail.nrec <= 8)
-    k_products_W<A, 8><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
+    k_products_W<T, A, 8><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
   else
-    k_products_W<A, RecBatch<typename RecOf<A>::type>::n><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n,
-                                                                               partial, nwarps, tail);
+    k_products_W<T, A, RecBatch<T>::n><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail);
 }
 
-template <typename A>
-static void products_of(const Geom& g, int nslab, const MeasLayout& m, const A* accT, const A* accO, double inv_n,
-                        double2* partial, int nb, int nwarps, const ProductTail& tail, bool W_done,
-                        cudaStream_t s) {
-  k_products_P<A><<<dim3(nb, m.nr + m.nrf), 256, 0, s>>>(g, nslab, m, accT, inv_n, partial, nwarps);
-  count_launches(1);
-  const int nW = m.np * m.nc * 2;
-  if (m.nrf > 0 && nW > 0 && !W_done) {
-    const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
-    launch_products_W(grid, g, nslab, m, accT, accO, inv_n, partial, nwarps, tail, s);
-    count_launches(1);
-  }
-}
-
-void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, const void* accO,
-                     double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail,
-                     bool W_done) {
+void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
+                     const void* accO, double inv_n, double2* partial, double* rec, cudaStream_t s,
+                     const ProductTail& tail, bool W_done) {
   const int nb = blocks_for(g.Ns, 256);
   const int nwarps = nb * 8;
-  if (pairs)
-    products_of(g, nslab, m, static_cast<const float4*>(accT), static_cast<const float4*>(accO), inv_n, partial, nb,
-                nwarps, tail, W_done, s);
-  else
-    products_of(g, nslab, m, static_cast<const double2*>(accT), static_cast<const double2*>(accO), inv_n, partial,
-                nb, nwarps, tail, W_done, s);
   const int nW = m.np * m.nc * 2;
+  with_sum_types(fp64, pairs, [&](auto t, auto a) {
+    using T = decltype(t);
+    using A = decltype(a);
+    k_products_P<A><<<dim3(nb, m.nr + m.nrf), 256, 0, s>>>(g, nslab, m, static_cast<const A*>(accT), inv_n, partial,
+                                                           nwarps);
+    count_launches(1);
+    if (m.nrf > 0 && nW > 0 && !W_done) {
+      const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
+      launch_products_W<T, A>(grid, g, nslab, m, static_cast<const A*>(accT), static_cast<const A*>(accO), inv_n,
+                              partial, nwarps, tail, s);
+      count_launches(1);
+    }
+  });
   const int nout = m.nr + m.nrf + m.nrf * nW;
   k_finalize_products<<<blocks_for(32ll * nout, 256), 256, 0, s>>>(partial, nwarps, g, m, rec);
   count_launches(1);
 }
 
-void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool pairs, const void* accT, double inv_n,
-                     double2* partial, const ProductTail& tail, cudaStream_t s) {
+void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
+                     double inv_n, double2* partial, const ProductTail& tail, cudaStream_t s) {
   const int nW = m.np * m.nc * 2;
   if (m.nrf == 0 || nW == 0 || tail.nrec <= 0) return;
   const int nb = blocks_for(g.Ns, 256);
   const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
-  ProductTail t = tail;
-  t.overwrite = 1;  // this buffer's records alone
-  if (pairs)
-    launch_products_W(grid, g, nslab, m, static_cast<const float4*>(accT), static_cast<const float4*>(nullptr), inv_n,
-                      partial, nb * 8, t, s);
-  else
-    launch_products_W(grid, g, nslab, m, static_cast<const double2*>(accT), static_cast<const double2*>(nullptr),
-                      inv_n, partial, nb * 8, t, s);
+  ProductTail tl = tail;
+  tl.overwrite = 1;  // this buffer's records alone
+  with_sum_types(fp64, pairs, [&](auto t, auto a) {
+    using T = decltype(t);
+    using A = decltype(a);
+    launch_products_W<T, A>(grid, g, nslab, m, static_cast<const A*>(accT), static_cast<const A*>(nullptr), inv_n,
+                            partial, nb * 8, tl, s);
+  });
   count_launches(1);
 }
 

@@ -194,11 +194,11 @@ void end_of_measurement(ml_server* s, Job* j) {
   double* out = j->rec_dev + static_cast<size_t>(j->meas) * L->meas.rec_len;
   int ncfg;
   if (j->p.outer_slab) {
-    launch_products(L->g, L->g.Nt / j->p.outer_slab, L->meas, !e->fp64, L->acc4T, L->acc4O,
+    launch_products(L->g, L->g.Nt / j->p.outer_slab, L->meas, e->fp64, e->pairs, L->acc4T, L->acc4O,
                     1.0 / j->p.n_sub_outer, L->partial, out, e->stream);
     ncfg = j->p.n_sub * j->p.n_sub_outer;
   } else {
-    launch_products(L->g, L->g.Nt / j->p.slab, L->meas, !e->fp64, L->accT, L->accO, 1.0 / j->p.n_sub, L->partial,
+    launch_products(L->g, L->g.Nt / j->p.slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0 / j->p.n_sub, L->partial,
                     out, e->stream);
     ncfg = j->p.n_sub;
   }
@@ -229,7 +229,7 @@ void advance(ml_server* s, Job* j) {
     case kInner:
       if (++j->sub == j->p.n_sub) {
         if (j->p.outer_slab) {
-          launch_combine(L->g, L->g.Nt / j->p.outer_slab, j->p.outer_slab / j->p.slab, L->meas, !e->fp64,
+          launch_combine(L->g, L->g.Nt / j->p.outer_slab, j->p.outer_slab / j->p.slab, L->meas, e->pairs,
                          L->accT, L->accO, 1.0 / j->p.n_sub, L->acc4T, L->acc4O, e->stream);
           if (++j->outer < j->p.n_sub_outer)
             j->phase = kOuter;
@@ -372,7 +372,7 @@ int run_tick(ml_server* s) {
   if (launch_sweeps_table(e->fp64, persistent, s->d_desc, s->d_tile_lat, s->td, s->d_ctl, 0, e->n_or, 1, e->d_err,
                           e->bar, e->stream, true, 0, 0))
     return ML_ECUDA;
-  launch_fold_table(e->fp64, s->d_desc, s->td, s->d_ctl, 0, 0, e->stream);
+  launch_fold_table(e->fp64, e->pairs, s->d_desc, s->td, s->d_ctl, 0, 0, e->stream);
   for (Job* j : s->active) advance(s, j);
   SRV_CUDA(cudaGetLastError());
   // finished jobs: read their records back, then release their memory
@@ -512,8 +512,9 @@ int ml_submit(ml_server* s, const ml_params* p, int n_therm, int n_meas, uint64_
   if (!s || !p || !job || n_therm < 0 || n_meas < 1) return ML_EINVAL;
   int st = validate(p);
   if (st) return st;
-  // the server's step machine folds every record as it comes: no replay
-  if ((p->prec == ML_FP64) != s->e.fp64 || p->n_or != s->e.n_or || p->replay) return ML_EINVAL;
+  // the server's step machine folds every record as it comes: no replay;
+  // its slab sums are double precision: no float-pair sums
+  if ((p->prec == ML_FP64) != s->e.fp64 || p->n_or != s->e.n_or || p->replay || p->pair_sums) return ML_EINVAL;
   Job* j = new (std::nothrow) Job();
   if (!j) return ML_ENOMEM;
   j->p = *p;

@@ -48,7 +48,7 @@ class _Params(ctypes.Structure):
         ("nprobe", ctypes.c_int), ("probe", ctypes.POINTER(_Offset)),
         ("comp_mask", ctypes.c_uint32),
         ("update", ctypes.c_int), ("metro_hits", ctypes.c_int), ("metro_width", ctypes.c_double),
-        ("multihit", ctypes.c_int), ("replay", ctypes.c_int),
+        ("multihit", ctypes.c_int), ("replay", ctypes.c_int), ("pair_sums", ctypes.c_int),
     ]
 
 
@@ -171,6 +171,7 @@ class Params:
     metro_width: float = 1.0
     multihit: int = 0         # 1: P(r) at 2 <= r <= L-2 from multihit temporal links
     replay: int = 0           # 1: field insertions by replay of the inner loop (one level)
+    pair_sums: int = 0        # 1 (FP32 only): float-pair slab sums instead of double precision
     _keep: list = field(default_factory=list, repr=False, compare=False)
 
     @property
@@ -190,7 +191,7 @@ class Params:
                        ML_FP64 if self.fp64 else ML_FP32, self.n_or, self.slab, self.n_sub, self.outer_slab,
                        self.n_sub_outer, self.k_between, len(self.r), r, len(self.rf), rf, len(self.probes), pr,
                        self.comp_mask, self.update, self.metro_hits, float(self.metro_width), self.multihit,
-                       self.replay)
+                       self.replay, self.pair_sums)
 
     @classmethod
     def from_workload(cls, w, **kw) -> "Params":

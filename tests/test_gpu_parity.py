@@ -435,24 +435,23 @@ def test_multilevel_run_fp64_ordered_phase(two_level, n_sub):
     assert np.abs(got - ref_rec).max() < 1e-9
 
 
-def test_connected_profile_on_device():
-    po, pm = pair(L=4, Nt=4, beta=2.5, seed=91, slab=2, n_sub=2, k_between=1, r=(1, 2), rf=(2,),
-                  probes=((0, 0), (1, 0)), comp_mask=0x3F)
+@pytest.mark.parametrize("fp64", [True, False])
+def test_connected_profile_on_device(fp64):
+    """ml_connected_device (Section II.C's connected field, F and F^2) on the
+    device's own records against the oracle's orc_connected on the same
+    records."""
+    po, pm = pair(L=4, Nt=4, beta=2.5, seed=91, slab=2, n_sub=2, k_between=1, r=(1, 2), rf=(2, 1),
+                  probes=((0, 0), (1, 0)), comp_mask=0b101011, fp64=fp64)
     with ml.Lattice(pm) as lat:
         lat.thermalize(3)
-        recs = lat.measure_device(3)
+        recs = lat.measure_device(5)
         out_dev = lat.connected(recs)
         lat.sync()  # the results are complete in the lattice stream's order
         out = out_dev.cpu().numpy()
         r = recs.cpu().numpy()
-    s = ml.split_record(pm, r)
-    pf = s["Pf"][:, 0, 0].mean()
-    W = s["W"][..., 0].mean(axis=0)          # [nrf][np][6][2]
-    vac = s["vac"].mean(axis=0)              # [6][2]
-    F = np.sqrt(pm.beta) * (W[..., 1] / pf - vac[:, 1])
-    F2 = -2 * pm.beta * (W[..., 0] / pf - vac[:, 0])
-    assert np.allclose(out[..., 0], F, rtol=1e-12, atol=1e-14)
-    assert np.allclose(out[..., 1], F2, rtol=1e-12, atol=1e-14)
+    ref = oracle.connected(po, r)
+    assert np.abs(ref[..., :2]).max() > 0.01
+    assert np.allclose(out, ref[..., :2], rtol=1e-13, atol=1e-15)
 
 
 # ----------------------------------------------------------------------------- full-size sampled parity
@@ -613,3 +612,36 @@ def test_full_size_two_level_48():
     for key in ("P", "Pf", "W", "vac"):
         scale = max(np.abs(ref[key]).max(), 1e-3)
         assert np.abs(got[key] - ref[key]).max() < 3e-5 * scale, key
+
+
+# ----------------------------------------------------------------------------- slab-sum formats
+@pytest.mark.parametrize("two_level", [False, True])
+def test_pair_sums_same_chain_close_records(two_level):
+    """FP32 lattices with float-pair slab sums (pair_sums = 1) run the same
+    chain as with the default double-precision sums; the records agree to the
+    float pairs' ~47 bits relative to each block's scale, and the
+    double-precision default stays within the FP32 tolerance of the oracle
+    measurement of one configuration."""
+    kw = dict(L=8, Nt=8, beta=0.98, seed=41, slab=2, n_sub=37, k_between=2, r=(1, 2, 3, 4), rf=(2, 4),
+              probes=((0, 0), (1, 0), (2, 1)), comp_mask=0x3F)
+    if two_level:
+        kw.update(n_sub=18, outer_slab=4, n_sub_outer=2)
+    out = {}
+    for ps in (0, 1):
+        p = ml.Params(fp64=False, pair_sums=ps, **kw)
+        with ml.Lattice(p) as lat:
+            lat.thermalize(5)
+            rec = lat.measure(2)
+            out[ps] = (rec, lat.get_angles())
+    assert np.array_equal(out[0][1], out[1][1])
+    a, b = ml.split_record(p, out[0][0]), ml.split_record(p, out[1][0])
+    for key in ("P", "Pf", "W", "vac", "naive", "plaq"):
+        scale = max(np.abs(a[key]).max(), 1e-30)
+        assert np.abs(a[key] - b[key]).max() <= 1e-9 * scale, key
+
+
+def test_pair_sums_refused_for_fp64():
+    p = ml.Params(L=4, Nt=4, beta=1.0, fp64=True, pair_sums=1)
+    with pytest.raises(ml.MLError) as e:
+        ml.Lattice(p)
+    assert e.value.status == ml.ML_EINVAL
