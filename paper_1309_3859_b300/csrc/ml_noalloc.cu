@@ -89,23 +89,36 @@ __global__ void __launch_bounds__(256) k_plaq_noalloc(const T* __restrict__ th, 
   if ((threadIdx.x & 31) == 0) part[i >> 5] = v;
 }
 
-// fixed-order sums of the partials: out = [nr][2] naive, then the plaquette
-__global__ void k_finalize_noalloc(const double* __restrict__ part, int nwarps, const double* __restrict__ ppart,
-                                   int npw, Geom g, int nr, double* __restrict__ out) {
-  for (int o = threadIdx.x; o <= nr; o += blockDim.x) {
-    if (o < nr) {
-      double sr = 0.0, si = 0.0;
-      for (int w = 0; w < nwarps; ++w) {
-        sr += part[(static_cast<size_t>(o) * nwarps + w) * 2];
-        si += part[(static_cast<size_t>(o) * nwarps + w) * 2 + 1];
-      }
-      out[2 * o] = sr / g.Ns;
-      out[2 * o + 1] = si / g.Ns;
-    } else {
-      double s = 0.0;
-      for (int w = 0; w < npw; ++w) s += ppart[w];
-      out[2 * nr] = s / (6.0 * g.V);
+// fixed-order sums of the partials, one block per output (blockIdx.x < nr:
+// naive correlator r, nr: the plaquette): thread t adds partials t, t + 256,
+// ..., then a shuffle tree per warp and the eight warp sums in order, so the
+// result does not depend on scheduling.  out = [nr][2] naive, then the
+// plaquette.
+__global__ void __launch_bounds__(256) k_finalize_noalloc(const double* __restrict__ part, int nwarps,
+                                                          const double* __restrict__ ppart, int npw, Geom g, int nr,
+                                                          double* __restrict__ out) {
+  const int o = blockIdx.x;
+  __shared__ double2 sh[8];
+  double2 s = make_double2(0.0, 0.0);
+  if (o < nr) {
+    for (int w = threadIdx.x; w < nwarps; w += blockDim.x) {
+      s.x += part[(static_cast<size_t>(o) * nwarps + w) * 2];
+      s.y += part[(static_cast<size_t>(o) * nwarps + w) * 2 + 1];
     }
+  } else {
+    for (int w = threadIdx.x; w < npw; w += blockDim.x) s.x += ppart[w];
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double2 t = make_double2(0.0, 0.0);
+  for (int w = 0; w < 8; ++w) t = make_double2(t.x + sh[w].x, t.y + sh[w].y);
+  if (o < nr) {
+    out[2 * o] = t.x / g.Ns;
+    out[2 * o + 1] = t.y / g.Ns;
+  } else {
+    out[2 * nr] = t.x / (6.0 * g.V);
   }
 }
 
@@ -163,7 +176,7 @@ extern "C" int ml_naive_noalloc(const void* theta_dev, int L, int Nt, int prec, 
     k_naive_noalloc<float><<<nbx, 256, 0, s>>>(static_cast<const float*>(theta_dev), g, rl, scratch, nwarps);
     k_plaq_noalloc<float><<<nbv, 256, 0, s>>>(static_cast<const float*>(theta_dev), g, ppart);
   }
-  k_finalize_noalloc<<<1, 128, 0, s>>>(scratch, nwarps, ppart, npw, g, nr, out_dev);
+  k_finalize_noalloc<<<nr + 1, 256, 0, s>>>(scratch, nwarps, ppart, npw, g, nr, out_dev);
   count_launches(3);
   return cudaGetLastError() == cudaSuccess ? ML_OK : ML_ECUDA;
 }
