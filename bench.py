@@ -10,10 +10,22 @@ sweeps) before the warm-up steps.
 
 Metric: link updates per second over whole steps (every heatbath and
 overrelaxation link update of the step, divided by the step's device time),
-with multilevel measurements per second beside it.  L2 is flushed (a 512 MB
-write) before every timed step.  With --gpus N > 1 (torchrun) every rank runs
+with multilevel measurements per second beside it.  The K timed steps are one
+call of K measurements (CUDA events around it), so each measurement's
+products overlap the next one's sweeps as in any run of measurements; L2 is
+flushed (a 512 MB write) before that call, and the slab sums the step streams
+through (1.05 GB) are larger than L2.  `isolated_ms_per_step` is one
+measurement per call with L2 flushed before each.  With --gpus N > 1 (torchrun) every rank runs
 its own lattice (independent Markov chains, weak scaling) and the value is the
 sum over ranks divided by the slowest rank's time.
+
+The same JSON line carries the other configured workloads: the 8^3 x 4 FP64
+plain multilevel run (its 5 measurements) and one 48^3 x 16 two-level
+measurement (20 outer x 200 inner sub-updates) under `configs`, each with its
+kernel classes, roofline and the oracle beside it (truncated for 48^3 x 16);
+the 64-lattice batch (`batched`); and serving (10 000 seeded requests with
+Poisson arrivals at 80% of the measured capacity, p50/p99 latency per lattice
+size, `serving`).
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (one sub-update per step) on the host cores.
@@ -74,7 +86,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except (OSError, ValueError):
@@ -177,24 +189,154 @@ def run_reference(args, w, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU arm
-def algorithmic_bytes(w, kernel, n_batch=1):
+def kernel_classes(ml, lat, w, ms_step):
+    """Per-launch device time of each kernel class (ml_kernel_timing) and its
+    share of a measurement step: the k0 full sweeps run as one launch of
+    k_between compound sweeps; a slab sub-update is one launch of the sweep
+    kernel with the record fused (the resident kernel runs a ring buffer of
+    sub-updates per launch and its folds overlap on the SMs it leaves free, so
+    shares can sum past 1)."""
+    nB = lat.batch_slots
+    n_outer = w.n_sub_outer if w.outer_slab else 1
+    per_step = {
+        "subupdate": (ml.ML_K_SUBUPDATE, w.n_sub * n_outer),
+        "full_sweeps": (ml.ML_K_FULLSWEEP, w.k_between),
+        "accumulate": (ml.ML_K_ACCUMULATE, n_outer * -(-w.n_sub // nB)),
+        "products": (ml.ML_K_PRODUCTS, 1),
+    }
+    kms = {name: lat.kernel_ms(kid, reps=20 if name != "products" else 3) for name, (kid, _) in per_step.items()}
+    share = {name: kms[name] * per_step[name][1] / ms_step for name in per_step}
+    return kms, share
+
+
+def hbm_roofline(ml, lat, w, kms, share, peak, peak_kind):
+    """HBM roofline of the step's dominant kernel class (sub-updates or folds):
+    algorithmic bytes per launch over the event-timed launch."""
+    nB = lat.batch_slots
+    dominant = max(("subupdate", "accumulate"), key=share.get)
+    resident = lat.sweep_mode == ml.ML_SWEEP_RESIDENT
+    per_launch = nB if (dominant == "subupdate" and resident) else 1  # sub-updates per launch
+    nbytes = algorithmic_bytes(w, "sweep" if dominant == "subupdate" else dominant, nB) * per_launch
+    launch_ms = kms[dominant] * per_launch
+    achieved = nbytes / (launch_ms * 1e-3) / 1e9
+    impl = ["k_sweeps_table (persistent, record fused)", "k_pass_table + k_record_table",
+            "k_sweeps_resident (cluster-resident slabs, record fused)"][lat.sweep_mode]
+    return {"kernel": {"subupdate": impl, "accumulate": "k_accum_T_table + k_accum_O_table"}[dominant],
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
+            "launch_ms": launch_ms, "sub_updates_per_launch": per_launch, "batch_slots": nB}
+
+
+def config_point(ml, w, n_meas, warmup, peak, peak_kind):
+    """One configured workload: n_meas measurements in one call after warm-up
+    (L2 flushed before), link updates/s, measurements/s, kernel classes and
+    the roofline of the dominant one."""
+    import torch
+
+    p = ml.Params.from_workload(w)
+    with ml.Lattice(p) as lat:
+        lat.thermalize(w.n_therm)
+        rec = torch.empty((n_meas, lat.rec_len), dtype=torch.float64, device=lat.device)
+        for _ in range(warmup):
+            lat.measure_device(1, rec[:1])
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=lat.device)
+        with torch.cuda.stream(lat.stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(lat.stream)
+        lat.measure_device(n_meas, rec)
+        e1.record(lat.stream)
+        lat.sync()
+        ms = e0.elapsed_time(e1) / n_meas
+        del flush
+        kms, share = kernel_classes(ml, lat, w, ms)
+        roof = hbm_roofline(ml, lat, w, kms, share, peak, peak_kind)
+        mode = ["persistent", "per-pass", "resident"][lat.sweep_mode]
+    upd = link_updates_per_step(w)
+    return {"workload": w.name, "dtype": "f64" if w.fp64 else "f32 links; f64 slab sums, products, reductions",
+            "ms_per_measurement": ms, "measurements_per_s": 1e3 / ms, "link_updates_per_s": upd / (ms * 1e-3),
+            "link_updates_per_measurement": upd, "measurements_timed": n_meas, "sweep_impl": mode,
+            "kernel_ms": kms, "kernel_share": share, "roofline": roof}
+
+
+def oracle_small_point(w):
+    """The oracle on the whole 8^3 x 4 FP64 workload: thermalisation, then its
+    n_meas measurements timed."""
+    import oracle
+
+    po = oracle.Params(L=w.L, Nt=w.Nt, beta=w.beta, seed=w.seed, n_or=w.n_or, slab=w.slab, n_sub=w.n_sub,
+                       k_between=w.k_between, r=w.r, rf=w.rf, probes=w.probes, comp_mask=w.comp_mask,
+                       threads=os.cpu_count())
+    th = oracle.hot_start(po)
+    c = oracle.thermalize(po, th, 0, w.n_therm)
+    t0 = time.perf_counter()
+    oracle.measure(po, th, c, w.n_meas)
+    dt = time.perf_counter() - t0
+    upd = link_updates_per_step(w) * w.n_meas
+    return {"kind": "oracle", "cores": os.cpu_count(), "ms_per_measurement": 1e3 * dt / w.n_meas,
+            "link_updates_per_s": upd / dt, "sample": f"the whole workload: {w.n_meas} measurements"}
+
+
+def oracle_large_point(w):
+    """The oracle on the 48^3 x 16 two-level workload, truncated: one slab
+    sub-update (a compound sweep with the inner mask), extrapolated to a whole
+    measurement by its link updates (the oracle's accumulations, whose slab
+    sums for this workload's probe set would hold 6.6 GB, are left out, so
+    the extrapolation is a lower bound on the oracle's time)."""
+    import oracle
+
+    po = oracle.Params(L=w.L, Nt=w.Nt, beta=w.beta, seed=w.seed, n_or=w.n_or, draws=1, slab=w.slab, n_sub=1,
+                       k_between=0, r=w.r, threads=os.cpu_count())
+    th = oracle.hot_start(po)
+    t0 = time.perf_counter()
+    oracle.compound_sweep(po, th, 0, w.slab)
+    dt = time.perf_counter() - t0
+    V = w.V
+    upd = (V + 3 * V * (w.slab - 1) // w.slab) * (1 + w.n_or)
+    rate = upd / dt
+    return {"kind": "oracle", "cores": os.cpu_count(), "link_updates_per_s": rate,
+            "ms_per_measurement_extrapolated": 1e3 * link_updates_per_step(w) / rate,
+            "sample": f"truncated: one slab sub-update of the 48^3 x 16 lattice ({dt:.1f} s), extrapolated to a "
+                      "whole measurement by its link updates, accumulations left out (a lower bound)"}
+
+
+def pass_bytes(V, mu, d, tsz):
+    """Bytes one (mu, parity) pass must move at minimum.
+
+    Without frozen links (d = 0) a pass updates V/2 links: it reads U_mu at
+    both parities (V angles; the staples reach the other parity), the three
+    other directions everywhere (3V) and writes V/2: 4.5 V angles.  With the
+    slab mask d a temporal pass is the same; a spatial pass updates the links
+    on d - 1 of every d time slices (V (d - 1) / (2d) of them) and reads U_mu
+    everywhere (its staples reach the frozen slices at t +- 1), the other two
+    spatial directions on the updated slices only and U_0 at t and t - 1 (all
+    slices): 2 V + 2.5 V (d - 1) / d angles (3.25 V for d = 2)."""
+    if d == 0 or mu == 0:
+        return 4.5 * V * tsz
+    if d == 1:
+        return 0.0  # every spatial link is frozen: the pass moves nothing
+    return (2.0 * V + 2.5 * V * (d - 1) / d) * tsz
+
+
+def sweep_bytes(V, d, n_or, tsz):
+    """Compound sweep: 1 + n_or sweeps of the four directions at both parities."""
+    return (1 + n_or) * 2 * sum(pass_bytes(V, mu, d, tsz) for mu in range(4))
+
+
+def algorithmic_bytes(w, kernel, n_batch=1, d=None):
     """Bytes one launch of a kernel class must move at minimum.
 
-    update pass: a (mu, parity) pass reads U_mu at both parities (V angles),
-    the other three directions everywhere (3V) and writes V/2: 4.5 V angles;
-    the persistent kernel runs 4 (1 + n_or) ... = 8 (1 + n_or) passes per
-    compound sweep.  fold: every slab accumulator (16 bytes per complex sum:
-    two doubles, or two float pairs) is read and written once (32 bytes) and
-    every record of the batch is read once."""
+    sweep: the compound sweep's passes (pass_bytes) with the slab mask d
+    (default: the workload's inner slab).  fold: every slab accumulator (16
+    bytes per complex sum) is read and written once (32 bytes) and every
+    record of the batch is read once."""
     tsz = 8 if w.fp64 else 4
     Ns, V = w.L ** 3, w.V
     nslab = w.Nt // w.slab
     nR = len(set(w.r) | set(w.rf))
     nc = bin(w.comp_mask).count("1")
-    if kernel == "pass":
-        return int(4.5 * V * tsz)
     if kernel == "sweep":
-        return int(8 * (1 + w.n_or) * 4.5 * V * tsz)
+        return int(sweep_bytes(V, w.slab if d is None else d, w.n_or, tsz))
     if kernel == "accumulate":
         acc_o = nslab * len(w.rf) * len(w.probes) * nc * 2 * Ns
         acc_t = nslab * nR * Ns
@@ -203,25 +345,70 @@ def algorithmic_bytes(w, kernel, n_batch=1):
     raise ValueError(kernel)
 
 
+# Warp instructions per link update of the global-memory pass kernel
+# (k_update_pass_pair<float, KIND>, ncu on a 64^4 FP32 lattice): heatbath 688
+# and overrelaxation 222 per 32 links.  The cluster-resident kernel runs the
+# same link update on shared memory; these counts give its issue bound.
+INSTR_PER_LINK = {"heatbath": 688 / 32, "overrelax": 222 / 32}
+
+
+def issue_roofline(w, launch_ms, sub_updates, sms, sm_mhz):
+    """Issue bound of the cluster-resident sub-updates: warp instructions of
+    the launch's link updates over (SMs x 4 schedulers x clock)."""
+    V, d = w.V, w.slab
+    links = V + 3 * V * (d - 1) // d  # per sweep: temporal links all, spatial on d - 1 of d slices
+    instr = sub_updates * links * (INSTR_PER_LINK["heatbath"] + w.n_or * INSTR_PER_LINK["overrelax"])
+    bound_ms = instr / (sms * 4 * sm_mhz * 1e6) * 1e3
+    return {"bound": "issue", "kernel": "k_sweeps_resident", "warp_instructions_per_launch": instr,
+            "instr_per_link": INSTR_PER_LINK, "sms": sms, "sm_mhz": sm_mhz, "issue_bound_ms": bound_ms,
+            "launch_ms": launch_ms, "frac": bound_ms / launch_ms,
+            "source": "instruction counts of k_update_pass_pair<float> (ncu, 64^4 FP32); SMs = 16-CTA clusters x slabs"}
+
+
+def _timed_passes(ml, lat, mu, kind, reps=10):
+    """Average event time of `reps` unmasked (mu, even) passes through
+    ml_update_pass (one kernel launch each)."""
+    import torch
+
+    lat.update_pass(mu, 0, 0, 10 ** 6, kind)
+    lat.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    for i in range(reps):
+        lat.update_pass(mu, 0, 0, 10 ** 6 + i, kind)
+    e1.record(lat.stream)
+    lat.sync()
+    return e0.elapsed_time(e1) / reps
+
+
 def hbm_sweep_point(ml, peak):
-    """Persistent compound sweep on a 64^4 FP32 lattice (268 MB of angles,
-    beyond L2): link updates/s and effective bandwidth against HBM."""
+    """A 64^4 FP32 lattice (268 MB of angles, beyond L2): the compound sweep
+    without frozen links (as in thermalisation), its heatbath and
+    overrelaxation passes separately, and the slab-masked sweep with the bytes
+    its passes need (pass_bytes)."""
     p = ml.Params(L=64, Nt=64, beta=0.98, seed=5, fp64=False, slab=2, n_sub=1, r=(1,))
     with ml.Lattice(p) as lat:
         lat.thermalize(2)
-        ms_sweep = lat.kernel_ms(ml.ML_K_SWEEP, reps=5)
-        ms_or = lat.kernel_ms(ml.ML_K_OVERRELAX, reps=10)
-        ms_hb = lat.kernel_ms(ml.ML_K_HEATBATH, reps=10)
+        ms_full = lat.kernel_ms(ml.ML_K_FULLSWEEP, reps=5)
+        ms_masked = lat.kernel_ms(ml.ML_K_SWEEP, reps=5)
+        passes = {(kind, mu): _timed_passes(ml, lat, mu, kind) for kind in (0, 1) for mu in (0, 1)}
     V = p.V
-    # slab mask 2: temporal links all move, spatial links on half the slices
-    moved = (V + 3 * V // 2) * 4
-    pass_bytes = 4.5 * V * 4
-    return {"workload": "sweep-64x64x64x64-fp32", "angle_bytes": 16 * V,
-            "compound_sweep_ms": ms_sweep, "link_updates_per_s": moved / (ms_sweep * 1e-3),
-            "sweep_achieved_gbs": 32 * pass_bytes / (ms_sweep * 1e-3) / 1e9,
-            "sweep_frac": 32 * pass_bytes / (ms_sweep * 1e-3) / 1e9 / peak,
-            "or_pass_ms": ms_or, "or_pass_gbs": pass_bytes / (ms_or * 1e-3) / 1e9,
-            "hb_pass_ms": ms_hb, "hb_pass_gbs": pass_bytes / (ms_hb * 1e-3) / 1e9}
+    full_bytes = sweep_bytes(V, 0, 3, 4)
+    masked_bytes = sweep_bytes(V, 2, 3, 4)
+    pb = pass_bytes(V, 0, 0, 4)
+    gbs = lambda nbytes, ms: nbytes / (ms * 1e-3) / 1e9  # noqa: E731
+    out = {"workload": "sweep-64x64x64x64-fp32", "angle_bytes": 16 * V,
+           "full_sweep_ms": ms_full, "full_sweep_link_updates_per_s": 16 * V / (ms_full * 1e-3),
+           "sweep_achieved_gbs": gbs(full_bytes, ms_full), "sweep_frac": gbs(full_bytes, ms_full) / peak,
+           "masked_sweep_ms": ms_masked, "masked_sweep_gbs": gbs(masked_bytes, ms_masked),
+           "masked_sweep_frac": gbs(masked_bytes, ms_masked) / peak,
+           "note": "sweep_frac: unmasked compound sweep (1 heatbath + 3 overrelaxation sweeps), 4.5 V angles per "
+                   "pass; masked: slab mask 2, spatial passes charged 3.25 V"}
+    for (kind, mu), ms in passes.items():
+        name = ("hb" if kind == 0 else "or") + f"_pass_mu{mu}"
+        out[name + "_ms"] = ms
+        out[name + "_frac"] = gbs(pb, ms) / peak
+    return out
 
 
 def batch_params(ml, n=64):
@@ -370,6 +557,33 @@ def fp64_point(ml, w, steps=3):
             "sweep_impl": mode}
 
 
+def pair_sums_point(ml, w, steps=5):
+    """The step's workload with float-pair slab sums (ml_params.pair_sums = 1)
+    instead of double-precision ones, on the same chain: the device-time cost
+    of keeping the slab sums in FP64 on this GPU's double-precision pipe."""
+    import torch
+
+    p = ml.Params.from_workload(w, pair_sums=1)
+    with ml.Lattice(p) as lat:
+        lat.thermalize(w.n_therm)
+        rec = torch.empty((1, lat.rec_len), dtype=torch.float64, device=lat.device)
+        for _ in range(2):
+            lat.measure_device(1, rec)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(lat.stream)
+        for _ in range(steps):
+            lat.measure_device(1, rec)
+        e1.record(lat.stream)
+        lat.sync()
+        ms = e0.elapsed_time(e1) / steps
+        fold_ms = lat.kernel_ms(ml.ML_K_ACCUMULATE, reps=20)
+        prod_ms = lat.kernel_ms(ml.ML_K_PRODUCTS, reps=3)
+    return {"workload": w.name + "-pair-sums", "ms_per_step": ms, "fold_ms": fold_ms, "products_ms": prod_ms,
+            "link_updates_per_s": link_updates_per_step(w) / (ms * 1e-3),
+            "slab_sums": "float pairs (about 47 bits), products and reductions in double"}
+
+
 def replay_point(ml, w, steps=3):
     """The step's workload with the field insertions by replay: the inner
     loop runs twice, and no per-site insertion sums are kept."""
@@ -429,29 +643,38 @@ def run_gpu(args, w, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # The K timed steps run as one call of K measurements, as a run of
+    # measurements streams on the device: each measurement's products (on the
+    # accumulation stream) overlap the next one's sweeps.  L2 is flushed
+    # before the call; the step's working set (the slab sums, about 1 GB at
+    # 24^3 x 8) is larger than L2.  With --profile each step is one call
+    # bracketed for the profiler.
+    recs = torch.empty((args.steps, lat.rec_len), dtype=torch.float64, device=lat.device)
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     launches0 = ml.kernel_launches()
     with ClockSampler(torch.cuda.current_device()) as clk:
         t_wall0 = time.perf_counter()
-        for k in range(args.steps):
-            with torch.cuda.stream(st):
-                flush.fill_(float(k))
-            if args.profile and k == 0:
+        with torch.cuda.stream(st):
+            flush.fill_(0.0)
+        if args.profile:
+            e_start.record(st)
+            for k in range(args.steps):
                 torch.cuda.synchronize()
                 torch.cuda.cudart().cudaProfilerStart()
-            starts[k].record(st)
-            lat.measure_device(1, rec)
-            ends[k].record(st)
-            if args.profile and k == 0:
+                lat.measure_device(1, recs[k:k + 1])
                 torch.cuda.synchronize()
                 torch.cuda.cudart().cudaProfilerStop()
+            e_end.record(st)
+        else:
+            e_start.record(st)
+            lat.measure_device(args.steps, recs)
+            e_end.record(st)
         lat.sync()
         barrier()
         t_wall = time.perf_counter() - t_wall0
     launches = ml.kernel_launches() - launches0
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    ms = e_start.elapsed_time(e_end)
     if dist is not None:
         t = torch.tensor([ms], dtype=torch.float64, device=lat.device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -459,39 +682,27 @@ def run_gpu(args, w, rank, world):
     upd = link_updates_per_step(w)
     value = world * upd * args.steps / (ms * 1e-3)
 
-    # kernel classes: per-launch device time and launches per step
-    nB = lat.batch_slots
-    n_folds = -(-w.n_sub // nB)
-    # the k0 full sweeps run as one launch of k_between compound sweeps; a
-    # slab sub-update is one launch of the sweep kernel with the record fused
-    # (the resident kernel runs a ring buffer of nB sub-updates per launch and
-    # its folds overlap on the SMs it leaves free, so shares can sum past 1)
-    per_step = {
-        "subupdate": (ml.ML_K_SUBUPDATE, w.n_sub),
-        "full_sweeps": (ml.ML_K_FULLSWEEP, w.k_between),
-        "accumulate": (ml.ML_K_ACCUMULATE, n_folds),
-        "products": (ml.ML_K_PRODUCTS, 1),
-    }
-    kms = {name: lat.kernel_ms(kid, reps=20 if name != "products" else 3) for name, (kid, _) in per_step.items()}
-    share = {name: kms[name] * per_step[name][1] / (ms / args.steps) for name in per_step}
-    dominant = max(("subupdate", "accumulate"), key=share.get)
+    # one measurement per call, L2 flushed before each (nothing overlaps the
+    # products): reported beside the streamed step time
+    iso = []
+    for k in range(3):
+        with torch.cuda.stream(st):
+            flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lat.measure_device(1, rec)
+        e1.record(st)
+        lat.sync()
+        iso.append(e0.elapsed_time(e1))
+    kms, share = kernel_classes(ml, lat, w, ms / args.steps)
     peak, peak_kind = measured_peaks()
-    resident = lat.sweep_mode == ml.ML_SWEEP_RESIDENT
-    per_launch = nB if (dominant == "subupdate" and resident) else 1  # sub-updates per launch
-    nbytes = algorithmic_bytes(w, "sweep" if dominant == "subupdate" else dominant, nB) * per_launch
-    launch_ms = kms[dominant] * per_launch
-    achieved = nbytes / (launch_ms * 1e-3) / 1e9
-    impl = ["k_sweeps_table (persistent, record fused)", "k_pass_table + k_record_table",
-            "k_sweeps_resident (cluster-resident slabs, record fused)"][lat.sweep_mode]
-    roof = {"kernel": {"subupdate": impl, "accumulate": "k_accum_T_table + k_accum_O_table"}[dominant], "bound": "hbm",
-            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": nbytes,
-            "launch_ms": launch_ms, "sub_updates_per_launch": per_launch, "batch_slots": nB}
+    roof = hbm_roofline(ml, lat, w, kms, share, peak, peak_kind)
     hbm_point = hbm_sweep_point(ml, peak) if rank == 0 and not args.no_extra else None
     batch_point = batched_point(ml) if rank == 0 and not args.no_extra else None
     mh_point = multihit_point(ml, w) if rank == 0 and not args.no_extra else None
     rp_point = replay_point(ml, w) if rank == 0 and not args.no_extra and not w.outer_slab else None
     f64_point = fp64_point(ml, w) if rank == 0 and not args.no_extra and not w.fp64 else None
+    pair_point = pair_sums_point(ml, w) if rank == 0 and not args.no_extra and not w.fp64 else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -509,9 +720,27 @@ def run_gpu(args, w, rank, world):
     e2e_s = time.perf_counter() - t0
     e2e_value = world * upd * e2e_steps / e2e_s
 
+    clocks = clk.summary()
+    roof_issue = None
+    if lat.sweep_mode == ml.ML_SWEEP_RESIDENT and clocks["sm_mhz"]:
+        nslab = w.Nt // w.slab
+        roof_issue = issue_roofline(w, kms["subupdate"] * lat.batch_slots, lat.batch_slots, 16 * nslab,
+                                    clocks["sm_mhz"])
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
+    # the other configured workloads: 8^3 x 4 FP64 plain multilevel and the
+    # 48^3 x 16 two-level measurement, each with the oracle beside it
+    configs = None
+    if rank == 0 and not args.no_configs:
+        small = config_point(ml, workloads.SMALL_FP64, workloads.SMALL_FP64.n_meas, 1, peak, peak_kind)
+        large = config_point(ml, workloads.LARGE_48, 1, 1, peak, peak_kind)
+        large["fold_share"] = large["kernel_share"]["accumulate"]
+        if world == 1 and not args.no_cpu_baseline:
+            small["oracle"] = oracle_small_point(workloads.SMALL_FP64)
+            large["oracle"] = oracle_large_point(workloads.LARGE_48)
+        configs = {"plain-8x8x8x4-fp64": small, "two-level-48x48x48x16-fp32": large}
     serving = None
     if rank == 0 and args.serving_requests > 0:
         serving = serving_point(ml, n_requests=args.serving_requests)
@@ -519,27 +748,34 @@ def run_gpu(args, w, rank, world):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if w.fp64 else "f32 (float-pair slab sums, FP64 products)",
+        "vs_baseline": None,
+        "dtype": "f64" if w.fp64 else "f32 links and update; f64 slab sums, averages, products and reductions",
         "data": "synthetic (hot start from the Philox stream, thermalised)",
         "config": {"workload": w.name, "L": w.L, "Nt": w.Nt, "beta": w.beta, "n_sub": w.n_sub,
                    "k_between": w.k_between, "n_or": w.n_or, "r": f"{w.r[0]}..{w.r[-1]}",
                    "field_r": f"{w.rf[0]}..{w.rf[-1]}", "probes": len(w.probes), "components": 6,
-                   "link_updates_per_step": upd, "l2": "flushed (512 MB write) before every timed step",
+                   "link_updates_per_step": upd,
+                   "l2": "flushed (512 MB write) before the timed call of K measurements; the step's working set "
+                         "(slab sums, 1.05 GB) is larger than L2",
                    "parallelism": f"{world} independent lattice(s)"},
         "measurements_per_s": world * args.steps / (ms * 1e-3),
+        "isolated_ms_per_step": float(np.median(iso)),
         "roofline": roof,
+        "roofline_issue": roof_issue,
         "kernel_ms": kms, "kernel_share": share,
         "sweep_hbm_point": hbm_point,
         "batched": batch_point,
         "multihit": mh_point,
         "replay": rp_point,
         "fp64_path": f64_point,
+        "pair_sums": pair_point,
         "vs_fp64_path": (f64_point["ms_per_step"] / (ms / args.steps)) if f64_point else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "cpu_baseline": cpu,
+        "configs": configs,
         "serving": serving,
         "wall_s": t_wall,
     }
@@ -568,8 +804,10 @@ def main():
     ap.add_argument("--sweep-mode", default="auto", choices=["auto", "persistent", "passes", "resident"],
                     help="force the single lattice's sweep implementation (default: autotuned; resident: "
                          "sub-updates cluster-resident, full sweeps persistent)")
-    ap.add_argument("--serving-requests", type=int, default=1000,
+    ap.add_argument("--serving-requests", type=int, default=10000,
                     help="requests of the serving measurement (0 skips it)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 8^3 x 4 FP64 and 48^3 x 16 two-level workloads")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
