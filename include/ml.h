@@ -224,6 +224,76 @@ int ml_observe(ml_lattice *h, double *out_host, size_t out_len);
 int ml_sync(ml_lattice *h);
 
 /* ------------------------------------------------------------------------ */
+/* Time-slab partition of one lattice over several processes                 */
+/* ------------------------------------------------------------------------ */
+
+/* Section II.C: with the spatial links of the slab boundaries frozen, the
+ * slabs' sub-updates are independent of one another.  A lattice can
+ * therefore be split by time slices over R processes (one GPU each), every
+ * process holding the whole lattice but moving only the links of its own
+ * slices [t_lo, t_hi).  One measurement then runs as:
+ *   1. k0 full compound sweeps, pass by pass (ml_update_pass), from
+ *      boundary slices refreshed in every direction and parity (the previous
+ *      measurement's sub-updates moved the neighbours' boundary links), each
+ *      pass followed by the exchange of the moved links on the two boundary
+ *      slices with the neighbouring processes (ML_PART_LINKS);
+ *   2. the owned slices of every process gathered into every copy, so each
+ *      copy is the whole configuration (ML_PART_LINKS);
+ *   3. ml_measure_inner: naive correlator and plaquette of that
+ *      configuration, the slab sub-updates, records and folds of the owned
+ *      slabs (no exchange at all);
+ *   4. the top-level [T] slab sums (ML_PART_SLAB_SUMS) of every process
+ *      gathered into every copy (each process's products multiply by the
+ *      other slabs' averages), the vacuum block sums (ML_PART_VACUUM) into
+ *      the copy of the process with the last slabs;
+ *   5. ml_measure_products in process order: each adds its slabs' field
+ *      insertions to the per-site sums it receives and passes them on
+ *      (ML_PART_W_SUMS bytes); the last reduces them into the record.
+ * The records are bit-identical to those of one process running ml_measure
+ * (the same kernels add the same terms in the same order).  The exchanges
+ * are the caller's (the Python binding's partition module uses
+ * torch.distributed).  While a range other than the whole lattice is set,
+ * ml_thermalize and ml_measure return ML_ESTATE. */
+
+/* Own the time slices [t_lo, t_hi): t_lo and t_hi multiples of the top-level
+ * slab thickness (outer_slab for two levels, else slab), 0 <= t_lo < t_hi <=
+ * Nt; (0, Nt) restores the whole lattice.  Handles with replay: ML_EINVAL.
+ * Blocking (re-plans the sweeps and re-captures the graphs). */
+int ml_set_time_range(ml_lattice *h, int t_lo, int t_hi);
+
+typedef enum {
+  ML_PART_LINKS = 0,     /* one time slice of the links of one direction and parity:
+                            L^3 / 2 angles in the lattice's precision           */
+  ML_PART_SLAB_SUMS = 1, /* one top-level slab's [T] sums: nR L^3 complex values of
+                            16 bytes (nR: the distinct separations of r and rf)  */
+  ML_PART_VACUUM = 2,    /* one inner slab's vacuum block sums (doubles)          */
+  ML_PART_W_SUMS = 3     /* the per-site field-insertion sums passed between
+                            processes: nrf nprobe nc 2 L^3 complex values of 16 bytes
+                            (nc: selected components); ml_part_size only        */
+} ml_part_block;
+
+/* Bytes of one unit of block `what` (a slice, a slab; for ML_PART_W_SUMS the
+ * whole array). */
+int ml_part_size(ml_lattice *h, int what, size_t *bytes);
+
+/* Copies units [begin, begin + count) of block `what` (for ML_PART_LINKS
+ * direction mu and parity `parity`, slices begin.. of that array) between the
+ * lattice and the device buffer buf_dev (to_lattice = 1: buffer -> lattice),
+ * on the handle's stream after its accumulation work.  Asynchronous. */
+int ml_part_copy(ml_lattice *h, int what, int mu, int parity, int begin, int count, void *buf_dev, int to_lattice);
+
+/* Step 3 above; rec_dev (rec_len >= ml_record_len doubles of device memory)
+ * receives the naive and plaquette blocks.  Asynchronous. */
+int ml_measure_inner(ml_lattice *h, double *rec_dev, size_t rec_len);
+
+/* Step 5 above: w_in_dev (NULL: zero; ML_PART_W_SUMS bytes) are the sums of
+ * the preceding processes.  With w_out_dev the sums after this process's
+ * slabs go there and rec_dev is not touched; with w_out_dev = NULL the
+ * record's P, Pf, W and vacuum blocks are completed in rec_dev.  ML_ESTATE
+ * without a preceding ml_measure_inner.  Asynchronous. */
+int ml_measure_products(ml_lattice *h, const void *w_in_dev, void *w_out_dev, double *rec_dev, size_t rec_len);
+
+/* ------------------------------------------------------------------------ */
 /* Utilities                                                                  */
 /* ------------------------------------------------------------------------ */
 
@@ -329,22 +399,29 @@ int ml_batch_set_sweep_mode(ml_batch *b, int mode);
 /* Serving: measurement requests with continuous batching                     */
 /* ------------------------------------------------------------------------ */
 
-/* A server owns one device allocation of budget_bytes (the HBM budget) and a
- * worker thread.  Requests (one lattice each: create, n_therm thermalisation
- * sweeps, n_meas measurements) are admitted first-in first-out whenever their
- * memory fits the budget and fewer than max_active (0: 1024) are running.
- * All admitted lattices advance together: each worker tick is one compound
- * sweep of every lattice in one launch (each with the slab mask of its own
- * phase), one record and one fold launch over the lattices that need them,
- * and the per-lattice steps of Algorithm 1.  Requests that arrive while others
- * run join at the next tick; finished ones leave and free their memory.  Each
- * request's records are identical to the same parameters run with ml_create.
- * All requests of a server share prec and n_or. */
+/* A server owns one device allocation of budget_bytes (the HBM budget) and
+ * `lanes` size lanes, each with its own stream and worker thread; a request
+ * goes to the lane of its lattice volume V = L^3 Nt (with three lanes: V below
+ * 2^16 sites, below 2^18, and the rest), so small requests do not wait on the
+ * ticks of large ones and the lanes' launches overlap on the GPU.  Requests
+ * (one lattice each: create, n_therm thermalisation sweeps, n_meas
+ * measurements) are admitted first-in first-out within a lane whenever their
+ * memory fits the budget and fewer than max_active (0: 1024) are running in
+ * all lanes.  The admitted lattices of a lane advance together: each worker
+ * tick is one launch in which every lattice advances by its share of compound
+ * sweeps (the lane's largest volume over its own, at most 2, within its
+ * phase; inner sub-updates recorded into consecutive ring slots), one fold
+ * launch over the lattices that need it, and the per-lattice steps of
+ * Algorithm 1.  Requests that arrive while others run join at the next tick;
+ * finished ones leave and free their memory.  Each request's records are
+ * identical to the same parameters run with ml_create.  All requests of a
+ * server share prec and n_or. */
 typedef struct {
   int prec;            /* ml_precision of every request                      */
   int n_or;            /* overrelaxation sweeps per heatbath sweep           */
   size_t budget_bytes; /* device memory for all resident requests (>= 1 MiB) */
   int max_active;      /* bound on simultaneously resident requests (0: 1024) */
+  int lanes;           /* size lanes, 1..8 (0: 3)                            */
 } ml_server_config;
 
 typedef struct {

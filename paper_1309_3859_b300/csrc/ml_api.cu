@@ -192,8 +192,8 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
     if (any_mh) L->mh_rec[b] = lat_alloc(e, L, 2 * L->trec_bytes);
   }
   L->nparts = vac_part_count(g, p->slab);
-  L->vac_part = static_cast<double*>(lat_alloc(e, L, static_cast<size_t>(L->nparts) * 2 * nc * sizeof(double)));
-  L->vac_acc = static_cast<double*>(lat_alloc(e, L, 12 * sizeof(double)));
+  L->vac_bytes = static_cast<size_t>(L->nparts) * 2 * nc * sizeof(double);
+  L->vac_part = static_cast<double*>(lat_alloc(e, L, L->vac_bytes));
   const size_t nw = static_cast<size_t>(product_partial_count(g));
   const size_t nout = static_cast<size_t>(nr) + nrf + static_cast<size_t>(nrf) * np * nc * 2;
   const size_t nvw = static_cast<size_t>((g.V + 255) / 256) * 8;
@@ -204,7 +204,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   L->naive_theta = lat_alloc(e, L, 4ull * g.V * tsz);
   const bool ok = L->theta && L->naive_theta && L->d_n && L->d_lists && L->accT && (L->accO || !L->accO_bytes) && L->osum[0] &&
                   L->osum[1] && (!p->replay || (L->replay_theta && L->replay_n)) &&
-                  L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->vac_acc && L->partial &&
+                  L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->partial &&
                   L->partial_naive && L->scratch_n && (!nslab_out || (L->acc4T && L->acc4O)) &&
                   (!any_mh || (L->mh_rec[0] && L->mh_rec[1]));
   if (!ok) return ML_ENOMEM;
@@ -254,14 +254,13 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   d.accO = L->accO;
   d.vac_part = L->vac_part;
   d.nparts = L->nparts;
-  d.vac_acc = L->vac_acc;
 
   cudaStream_t s = e->stream;
   cudaError_t ce = cudaSuccess;
   if (!lists.empty())
     ce = cudaMemcpyAsync(L->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L->d_n, 0, sizeof(unsigned long long), s);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(L->vac_part, 0, L->vac_bytes, s);
   // ring slots not yet written in a batch are multiplied by zero: keep them finite
   for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
     ce = cudaMemsetAsync(L->osum[b], 0, L->osum_bytes, s);
@@ -515,7 +514,7 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       LatState* L = e->lats[li];
       launch_naive_and_plaquette(e->fp64, L->naive_theta, L->g, L->meas, L->partial_naive, out[li], e->side);
     }
-    for (LatState* L : e->lats) ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->side));
+    for (LatState* L : e->lats) ML_CUDA(cudaMemsetAsync(L->vac_part, 0, L->vac_bytes, e->side));
     int ncfg = 0;
     if (e->replay) {
       // Replay (one level): pass 1 forms the slab averages from the inner
@@ -583,9 +582,98 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       ncfg = e->n_sub * e->n_sub_outer;
     }
     for (int li = 0; li < nlat; ++li)
-      launch_write_vac(e->lats[li]->vac_acc, 1.0 / ncfg, e->lats[li]->meas, out[li], e->side);
+      launch_write_vac(e->lats[li]->vac_part, e->lats[li]->nparts, 1.0 / ncfg, e->lats[li]->meas, e->lats[li]->g,
+                       out[li], e->side);
   }
   st = join(e->side, e->stream, e->ev_side);  // results complete in stream order on the main stream
+  if (st) return st;
+  return cuda_status(cudaGetLastError());
+}
+
+// ---- time-slab partition of one lattice over processes (Section II.C: with
+// the spatial links of the slab boundaries frozen, the slabs' sub-updates are
+// independent).  The process that owns time slices [t_lo, t_hi) runs a
+// measurement in two phases around the exchanges its caller makes.
+
+bool partitioned(const Engine* e) {
+  const Geom& g = e->lats[0]->g;
+  return g.t_lo != 0 || g.t_hi != g.Nt;
+}
+
+// First phase: the record is cleared; the naive correlator and the plaquette
+// of the current configuration (which the caller has made whole) go into it;
+// the inner loop (one level) or the outer iterations with their level
+// combinations (two levels) run on the owned slabs.  The slab sums and the
+// vacuum block sums are complete when the call's work is.
+int part_measure_inner(Engine* e, double* rec) {
+  LatState* L = e->lats[0];
+  int st = join(e->stream, e->side, e->ev_main);
+  if (st) return st;
+  ML_CUDA(cudaMemsetAsync(rec, 0, L->meas.rec_len * sizeof(double), e->stream));
+  ML_CUDA(cudaMemcpyAsync(L->naive_theta, L->theta, 4ull * L->g.V * (e->fp64 ? 8 : 4), cudaMemcpyDeviceToDevice,
+                          e->stream));
+  st = join(e->stream, e->side, e->ev_main);
+  if (st) return st;
+  launch_naive_and_plaquette(e->fp64, L->naive_theta, L->g, L->meas, L->partial_naive, rec, e->side);
+  ML_CUDA(cudaMemsetAsync(L->vac_part, 0, L->vac_bytes, e->side));
+  if (e->outer_slab == 0) {
+    int tb = 0, tn = 0;
+    bool tfirst = false;
+    st = run_inner_loop(e, &tb, &tn, &tfirst);
+    if (st) return st;
+    e->part_tail_buf = tb;
+    e->part_tail_nrec = tn;
+    e->part_tail_first = tfirst;
+  } else {
+    ML_CUDA(cudaMemsetAsync(L->acc4T, 0, L->acc4T_bytes, e->side));
+    if (L->acc4O_bytes) ML_CUDA(cudaMemsetAsync(L->acc4O, 0, L->acc4O_bytes, e->side));
+    for (int o = 0; o < e->n_sub_outer; ++o) {
+      st = launch_graph(e, e->g_outer);
+      if (!st) st = run_inner_loop(e);
+      if (st) return st;
+      launch_combine(L->g, L->g.Nt / e->outer_slab, e->outer_slab / e->slab, L->meas, e->pairs, L->accT, L->accO,
+                     1.0 / e->n_sub, L->acc4T, L->acc4O, e->side);
+    }
+    e->part_tail_nrec = 0;
+  }
+  e->part_open = true;
+  return join(e->side, e->stream, e->ev_side);
+}
+
+// Second phase: the field insertions of the owned top-level slabs are added
+// to the per-site sums w_in (null: zero).  With w_out the sums are written
+// there for the process holding the next slabs; without it (the last slabs)
+// they are reduced into the record together with P(r) from the top-level
+// [T] sums of every slab (the caller has gathered the other processes'
+// slabs) and the vacuum from the block sums (likewise gathered).
+int part_measure_products(Engine* e, const double2* w_in, double2* w_out, double* rec) {
+  if (!e->part_open) return ML_ESTATE;
+  LatState* L = e->lats[0];
+  int st = join(e->stream, e->side, e->ev_main);
+  if (st) return st;
+  const int top = e->outer_slab ? e->outer_slab : e->slab;
+  ProductRange pr;
+  pr.s_lo = L->g.t_lo / top;
+  pr.s_hi = L->g.t_hi / top;
+  pr.w_in = w_in;
+  pr.w_out = w_out;
+  int ncfg;
+  if (e->outer_slab == 0) {
+    const int tb = e->part_tail_buf;
+    launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
+                    rec, e->side,
+                    ProductTail{L->theta_rec[tb], L->osum[tb], e->part_tail_nrec, e->part_tail_first ? 1 : 0}, false,
+                    pr);
+    ML_CUDA(cudaEventRecord(e->ev_fold[tb], e->side));  // the tail buffer is free after the products
+    ncfg = e->n_sub;
+  } else {
+    launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, e->fp64, e->pairs, L->acc4T, L->acc4O,
+                    1.0 / e->n_sub_outer, L->partial, rec, e->side, ProductTail{}, false, pr);
+    ncfg = e->n_sub * e->n_sub_outer;
+  }
+  if (!w_out) launch_write_vac(L->vac_part, L->nparts, 1.0 / ncfg, L->meas, L->g, rec, e->side);
+  e->part_open = false;
+  st = join(e->side, e->stream, e->ev_side);
   if (st) return st;
   return cuda_status(cudaGetLastError());
 }
@@ -994,6 +1082,7 @@ int ml_sync(ml_lattice* h) {
 
 int ml_thermalize(ml_lattice* h, int n_sweeps) {
   if (!h) return ML_EINVAL;
+  if (partitioned(&h->e)) return ML_ESTATE;  // full sweeps need the neighbours' halo after every pass
   return thermalize_engine(&h->e, n_sweeps);
 }
 
@@ -1014,13 +1103,107 @@ int ml_update_pass(ml_lattice* h, int mu, int parity, int slab_d, uint64_t n, in
 
 int ml_measure_device(ml_lattice* h, int n_meas, double* out_dev, size_t out_len) {
   if (!h || n_meas < 0 || (n_meas > 0 && !out_dev)) return ML_EINVAL;
+  if (partitioned(&h->e)) return ML_ESTATE;
   if (out_len < total_len(&h->e, n_meas)) return ML_EINVAL;
   return enqueue_measurements(&h->e, n_meas, out_dev);
 }
 
 int ml_measure(ml_lattice* h, int n_meas, double* out_host, size_t out_len) {
   if (!h) return ML_EINVAL;
+  if (partitioned(&h->e)) return ML_ESTATE;
   return measure_host(&h->e, n_meas, out_host, out_len);
+}
+
+int ml_set_time_range(ml_lattice* h, int t_lo, int t_hi) {
+  if (!h) return ML_EINVAL;
+  Engine* e = &h->e;
+  LatState* L = h->L();
+  const int top = e->outer_slab ? e->outer_slab : e->slab;
+  if (t_lo < 0 || t_hi > L->g.Nt || t_lo >= t_hi || t_lo % top != 0 || t_hi % top != 0) return ML_EINVAL;
+  if (e->replay || e->part_open) return ML_EINVAL;
+  int st = check_errors(e);
+  if (st) return st;
+  L->g.t_lo = t_lo;
+  L->g.t_hi = t_hi;
+  L->desc.g = L->g;
+  ML_CUDA(cudaMemcpyAsync(e->d_desc, &L->desc, sizeof(LatDesc), cudaMemcpyHostToDevice, e->stream));
+  if (e->d_desc_scratch) {
+    LatDesc d = L->desc;
+    d.theta = L->scratch_theta;
+    d.n_dev = L->scratch_n;
+    ML_CUDA(cudaMemcpyAsync(e->d_desc_scratch, &d, sizeof(LatDesc), cudaMemcpyHostToDevice, e->stream));
+  }
+  ML_CUDA(cudaStreamSynchronize(e->stream));
+  // the resident units of the owned slabs only, and graphs with the new geometry
+  destroy_graphs(e);
+  st = plan_resident_sweeps(e);
+  if (!st && e->sweep_mode == ML_SWEEP_RESIDENT && !resident_plan(e, e->slab)) e->sweep_mode = e->full_mode;
+  if (!st) st = capture_graphs(e);
+  return st;
+}
+
+int ml_part_size(ml_lattice* h, int what, size_t* bytes) {
+  if (!h || !bytes) return ML_EINVAL;
+  Engine* e = &h->e;
+  LatState* L = h->L();
+  const Geom& g = L->g;
+  const MeasLayout& m = L->meas;
+  switch (what) {
+    case ML_PART_LINKS: *bytes = static_cast<size_t>(g.Ns / 2) * (e->fp64 ? 8 : 4); break;
+    case ML_PART_SLAB_SUMS: *bytes = static_cast<size_t>(m.nR) * g.Ns * 16; break;
+    case ML_PART_VACUUM: *bytes = L->vac_bytes / static_cast<size_t>(g.Nt / e->slab); break;
+    case ML_PART_W_SUMS: *bytes = static_cast<size_t>(m.nrf) * m.np * m.nc * 2 * g.Ns * 16; break;
+    default: return ML_EINVAL;
+  }
+  return ML_OK;
+}
+
+int ml_part_copy(ml_lattice* h, int what, int mu, int parity, int begin, int count, void* buf_dev, int to_lattice) {
+  if (!h || !buf_dev || begin < 0 || count < 0) return ML_EINVAL;
+  Engine* e = &h->e;
+  LatState* L = h->L();
+  const Geom& g = L->g;
+  size_t unit = 0;
+  int st = ml_part_size(h, what, &unit);
+  if (st) return st;
+  char* base = nullptr;
+  switch (what) {
+    case ML_PART_LINKS:
+      if (mu < 0 || mu > 3 || parity < 0 || parity > 1 || begin + count > g.Nt) return ML_EINVAL;
+      base = static_cast<char*>(L->theta) + static_cast<size_t>(mu * 2 + parity) * g.Vh * (e->fp64 ? 8 : 4);
+      break;
+    case ML_PART_SLAB_SUMS:
+      if (begin + count > g.Nt / (e->outer_slab ? e->outer_slab : e->slab)) return ML_EINVAL;
+      base = reinterpret_cast<char*>(e->outer_slab ? L->acc4T : L->accT);
+      break;
+    case ML_PART_VACUUM:
+      if (begin + count > g.Nt / e->slab) return ML_EINVAL;
+      base = reinterpret_cast<char*>(L->vac_part);
+      break;
+    default: return ML_EINVAL;
+  }
+  base += static_cast<size_t>(begin) * unit;
+  st = join(e->side, e->stream, e->ev_side);  // the accumulation stream's sums are complete first
+  if (st) return st;
+  if (count > 0)
+    ML_CUDA(cudaMemcpyAsync(to_lattice ? base : buf_dev, to_lattice ? buf_dev : base, static_cast<size_t>(count) * unit,
+                            cudaMemcpyDeviceToDevice, e->stream));
+  return ML_OK;
+}
+
+int ml_measure_inner(ml_lattice* h, double* rec_dev, size_t rec_len) {
+  if (!h || !rec_dev) return ML_EINVAL;
+  Engine* e = &h->e;
+  if (e->replay || e->part_open) return e->replay ? ML_EINVAL : ML_ESTATE;
+  if (rec_len < static_cast<size_t>(h->L()->meas.rec_len)) return ML_EINVAL;
+  return part_measure_inner(e, rec_dev);
+}
+
+int ml_measure_products(ml_lattice* h, const void* w_in_dev, void* w_out_dev, double* rec_dev, size_t rec_len) {
+  if (!h || (!w_out_dev && !rec_dev)) return ML_EINVAL;
+  if (!w_out_dev && rec_len < static_cast<size_t>(h->L()->meas.rec_len)) return ML_EINVAL;
+  return part_measure_products(&h->e, static_cast<const double2*>(w_in_dev), static_cast<double2*>(w_out_dev),
+                               rec_dev);
 }
 
 int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
@@ -1038,7 +1221,7 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
   ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
   ML_CUDA(cudaMemsetAsync(out, 0, m.rec_len * sizeof(double), e->stream));
   launch_naive_and_plaquette(e->fp64, L->theta, L->g, m, L->partial_naive, out, e->stream);
-  ML_CUDA(cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->stream));
+  ML_CUDA(cudaMemsetAsync(L->vac_part, 0, L->vac_bytes, e->stream));
   launch_record_table(e->fp64, e->d_desc, e->td, nullptr, buf, 0, e->stream);
   if (e->replay) {
     // no stored insertion sums: the products take the one record as their tail
@@ -1049,7 +1232,7 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
     launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, buf, 1, e->stream, false, true);
     launch_products(L->g, L->g.Nt / e->slab, m, e->fp64, e->pairs, L->accT, L->accO, 1.0, L->partial, out, e->stream);
   }
-  launch_write_vac(L->vac_acc, 1.0, m, out, e->stream);
+  launch_write_vac(L->vac_part, L->nparts, 1.0, m, L->g, out, e->stream);
   ML_CUDA(cudaGetLastError());
   ML_CUDA(cudaMemcpyAsync(out_host, out, m.rec_len * sizeof(double), cudaMemcpyDeviceToHost, e->stream));
   return check_errors(e);

@@ -72,6 +72,7 @@ struct Geom {
   int V;   // Ns * Nt
   int Vh;  // V / 2
   unsigned long long m_L, m_hx;  // division magics of L and L / 2 (div_magic)
+  int t_lo, t_hi;  // time slices whose links this handle moves: [t_lo, t_hi) (all: 0, Nt)
 };
 
 // Division by an invariant d >= 1 as a 64-bit multiply-high: for 0 <= x <
@@ -105,6 +106,8 @@ __host__ __device__ inline Geom make_geom(int L, int Nt) {
   g.Vh = g.V / 2;
   g.m_L = div_magic(L);
   g.m_hx = div_magic(L / 2);
+  g.t_lo = 0;
+  g.t_hi = Nt;
   return g;
 }
 

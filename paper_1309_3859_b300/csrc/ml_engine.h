@@ -32,9 +32,9 @@ struct LatState {
   void* theta_rec[2] = {nullptr, nullptr};  // record ring [nslab][slots][Ns]
   void* mh_rec[2] = {nullptr, nullptr};     // multihit ring [nslab][2][slots][Ns], or none
   size_t osum_bytes = 0, trec_bytes = 0;
-  double* vac_part = nullptr;
+  double* vac_part = nullptr;  // [nparts][nc * 2] vacuum block sums of the current measurement
   int nparts = 0;
-  double* vac_acc = nullptr;
+  size_t vac_bytes = 0;
   double2* partial = nullptr;        // product partials (accumulation stream)
   double2* partial_naive = nullptr;  // naive / plaquette partials (accumulation stream)
   void* naive_theta = nullptr;       // the configuration the naive correlator and plaquette read
@@ -75,6 +75,11 @@ struct Engine {
   Graph g_full, g_outer, g_one_full, g_sub[2][kBatchMax];
   double* rec_buf = nullptr;
   size_t rec_cap = 0;
+  // time-slab partition: a measurement split into ml_measure_inner and
+  // ml_measure_products, with the last ring buffer's records as the products' tail
+  bool part_open = false;
+  int part_tail_buf = 0, part_tail_nrec = 0;
+  bool part_tail_first = false;
 };
 
 int cuda_status(cudaError_t e);

@@ -47,9 +47,9 @@ struct LatDesc {
   void* osum[2];              // [nslab][nc][2][slots][Ns], slots = rec_batch(fp64)
   double2* accT;              // inner slab sums: double2 (re, im), or for FP32
   double2* accO;              //   lattices with float-pair sums float4 (re_hi, re_lo, im_hi, im_lo)
-  double* vac_part;           // [nc * 2][nparts] block partials of the vacuum sums of a fold
-  int nparts;                 // vacuum blocks per part (vac_part_count)
-  double* vac_acc;            // [12] vacuum sums of the folded configurations
+  double* vac_part;           // [nparts][nc * 2] vacuum sums of the measurement's folds per block of
+                              //   (slab, site) pairs (blocks never straddle a slab)
+  int nparts;                 // vacuum blocks (vac_part_count): nslab x blocks per slab
 };
 
 // Update of the first sweep of a compound sweep, per lattice.
@@ -66,8 +66,11 @@ __host__ __device__ inline UpdateRule update_rule(const LatDesc& L) {
 // that advance every lattice of a table in lockstep pass null and uniform
 // arguments instead.
 struct LatCtl {
-  int mask;    // slab thickness of this step's sweep (0: no frozen links)
-  int record;  // 1: record the configuration into slot `slot` of buffer `buf`
+  int mask;    // slab thickness of this step's sweeps (0: no frozen links)
+  int sweeps;  // compound sweeps of this lattice in this step: it takes part in
+               // iterations c < sweeps of the launch (0: none)
+  int record;  // 1: record the configuration after each of its sweeps c into
+               // slot `slot` + c of buffer `buf`
   int buf, slot;
   int fold;    // 1: fold slots 0 .. nrec-1 of buffer `fold_buf`
   int fold_buf, nrec;
@@ -111,14 +114,15 @@ int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int*
                         cudaStream_t s, bool record = false, int rec_buf = 0, int rec_slot = 0,
                         const LatDesc* single = nullptr);
 // record of each lattice's configuration into ring slot (buf, slot), with
-// the multihit record of the multihit lattices
+// the multihit record of the multihit lattices; with ctl, the record after
+// the lattice's sweep c of a step (slot ctl.slot + c; none when c >= ctl.sweeps)
 void launch_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
-                         cudaStream_t s);
+                         cudaStream_t s, int c = 0);
 // the multihit record alone (after a sweep launch that recorded the rest)
 void launch_mh_record_table(bool fp64, const LatDesc* d, const TableDims& td, const LatCtl* ctl, int buf, int slot,
-                            cudaStream_t s);
+                            cudaStream_t s, int c = 0);
 // fold slots 0 .. nrec-1 of ring buffer buf into each lattice's slab sums,
-// and their vacuum sums into vac_acc (pairs: FP32 lattices with float-pair
+// and their vacuum sums into vac_part (pairs: FP32 lattices with float-pair
 // slab sums; skip_O: leave the field-insertion sums to a products launch with
 // that buffer as its tail; overwrite: the slab sums start from zero instead of
 // their stored values)
@@ -162,12 +166,21 @@ struct ProductTail {
   int overwrite = 0;  // the stored field-insertion sums are not yet written: start from zero
   int add = 0;        // add the W partials to the stored ones (later batches of a replay)
 };
+// Time-slab partition of the products: the field insertions of slabs
+// [s_lo, s_hi) (s_hi < 0: all) are added to the per-site sums, which start
+// from w_in (null: zero; layout [nrf][nW][Ns] double2) and, with w_out set,
+// are written there unreduced instead of reduced into the record (no P).
+struct ProductRange {
+  int s_lo = 0, s_hi = -1;
+  const double2* w_in = nullptr;
+  double2* w_out = nullptr;
+};
 // cross-slab products of the averages sum / n, in double precision, reduced
 // over x into the record's P, Pf and W blocks (fp64: the lattice's precision;
 // pairs: as for launch_fold_table)
-void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT, const void* accO,
-                     double inv_n, double2* partial, double* rec, cudaStream_t s, const ProductTail& tail = {},
-                     bool W_done = false);
+void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
+                     const void* accO, double inv_n, double2* partial, double* rec, cudaStream_t s,
+                     const ProductTail& tail = {}, bool W_done = false, const ProductRange& pr = {});
 // replay: the W partials of one ring buffer's records (tail.nrec of them)
 // times the final slab averages, stored (tail.add = 0) or added to the stored
 // partials; W_done in the final launch_products then only adds P and finalises
@@ -176,7 +189,10 @@ void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool fp64, b
 // naive P+P and mean plaquette of the current configuration
 void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,
                                 double* rec, cudaStream_t s);
-void launch_write_vac(const double* vac_acc, double inv_ncfg, const MeasLayout& m, double* rec, cudaStream_t s);
+// the record's vacuum block from the block sums vac_part[nparts][nc * 2],
+// divided by V and by the number of folded configurations (1 / inv_ncfg)
+void launch_write_vac(const double* vac_part, int nparts, double inv_ncfg, const MeasLayout& m, const Geom& g,
+                      double* rec, cudaStream_t s);
 void launch_connected(const double* recs, int n_meas, const MeasLayout& m, double beta, double* out,
                       cudaStream_t s);
 

@@ -652,7 +652,9 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, Resi
       continue;
     }
     for (int i = 0; i < nlat; ++i)
-      for (int s = 0; s < geoms[i].Nt / mask; ++s) units->push_back(make_int4(i, s, split[i].ny, split[i].nz));
+      for (int s = 0; s < geoms[i].Nt / mask; ++s)
+        if (s * mask >= geoms[i].t_lo && (s + 1) * mask <= geoms[i].t_hi)  // the handle's own slabs
+          units->push_back(make_int4(i, s, split[i].ny, split[i].nz));
     p->cs = cs;
     p->smem = smem;
     p->nunits = static_cast<int>(units->size());

@@ -2,15 +2,21 @@
 // probes) arrive at any time, are admitted while their memory fits an HBM
 // budget, and are advanced together (continuous batching).
 //
-// A worker thread runs ticks.  One tick is one compound sweep of every
-// admitted lattice in a single launch over the descriptor table (each lattice
-// with the slab mask of its own phase: thermalisation, k0 sweeps, outer or
-// inner sub-update of Algorithm 1), then one record launch and one fold
-// launch over the lattices that need them, then each lattice's phase
-// transitions (naive correlator at the start of a measurement, level
-// combination, products and vacuum at its end).  Jobs that finish leave the
-// table and free their memory; queued jobs join it between ticks.  Every
-// lattice runs the same kernels, in the same order, as it would alone.
+// Requests are split by lattice volume into size lanes.  Each lane has its
+// own stream and worker thread and runs ticks over its own admitted lattices,
+// so a small request's ticks are short, and the lanes' launches overlap on
+// the GPU.  One tick is one launch over the lane's descriptor table in which
+// every lattice advances by its share of compound sweeps (each with the slab
+// mask of its own phase: thermalisation, k0 sweeps, outer or inner sub-update
+// of Algorithm 1; the share is the lane's largest volume over the lattice's
+// own, at most 2, so that lattices of a lane do about the same work per tick),
+// with the inner loop's records, then one fold launch over the lattices that
+// need it, then each lattice's phase transitions (naive correlator at the
+// start of a measurement, level combination, products and vacuum at its end).
+// Jobs that finish leave the table and free their memory; queued jobs join it
+// between ticks.  Every lattice runs the same kernels, in the same order, as
+// it would alone.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -26,6 +32,8 @@
 
 using namespace ml;
 using namespace ml::eng;
+
+struct Lane;  // a size lane of the server (below)
 
 namespace {
 
@@ -117,6 +125,8 @@ struct Job {
   double* rec_dev = nullptr;
   std::vector<double> result;
   int phase = kTherm, left = 0, meas = 0, sub = 0, outer = 0;
+  int tick_sweeps = 1;  // compound sweeps of the current tick
+  Lane* lane = nullptr;  // the size lane that runs it
   int status = ML_OK;
   bool done = false;
   double t_submit = 0, t_admit = -1, t_done = -1;
@@ -129,22 +139,18 @@ double now_s() {
 
 }  // namespace
 
-struct ml_server {
-  Engine e;  // streams, error word, barrier counter, precision, n_or, arena allocator
-  Arena arena;
-  int device = 0;
-  int max_active = 0;
-  double t0 = 0;
+// One size lane: its own engine (stream, error word, barrier counter), queue,
+// admitted lattices, descriptor tables and worker thread.
+struct Lane {
+  int index = 0;
+  Engine e;
   std::thread worker;
-  std::mutex m;
-  std::condition_variable cv_work, cv_done;
-  bool stop = false;
-  std::deque<Job*> queue;
-  std::unordered_map<uint64_t, Job*> jobs;
-  uint64_t next_id = 1;
+  std::deque<Job*> queue;  // guarded by the server's mutex
   // worker-owned
   std::vector<Job*> active;
-  bool dirty = true, freed_since_fail = true;
+  bool dirty = true;
+  uint64_t mem_gen_at_fail = 0;  // the server's release count when admission last ran out of memory
+  bool mem_blocked = false;
   LatDesc* d_desc = nullptr;
   int* d_tile_lat = nullptr;
   LatCtl* d_ctl = nullptr;
@@ -154,21 +160,38 @@ struct ml_server {
   std::vector<LatCtl> h_ctl;
   TableDims td{};
   int coresident_tiles = 0;
-  uint64_t ticks = 0, completed = 0, failed = 0;
+  std::atomic<uint64_t> ticks{0};
   std::atomic<int> n_active{0};
-  int worker_status = ML_OK;
+};
+
+struct ml_server {
+  Arena arena;
+  int device = 0;
+  int max_active = 0;
+  bool fp64 = false;
+  int n_or = 3;
+  double t0 = 0;
+  std::mutex m;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  std::unordered_map<uint64_t, Job*> jobs;
+  uint64_t next_id = 1;
+  std::vector<Lane*> lanes;
+  std::atomic<uint64_t> mem_gen{0};  // memory releases so far
+  std::atomic<int> n_active{0};
+  uint64_t completed = 0, failed = 0;
 };
 
 namespace {
 
 // --------------------------------------------------------------------------- per-job schedule
-void launch_start_of_measurement(ml_server* s, Job* j) {
-  Engine* e = &s->e;
+void launch_start_of_measurement(Job* j) {
+  Engine* e = &j->lane->e;
   LatState* L = j->L;
   double* out = j->rec_dev + static_cast<size_t>(j->meas) * L->meas.rec_len;
   cudaMemsetAsync(out, 0, L->meas.rec_len * sizeof(double), e->stream);
   launch_naive_and_plaquette(e->fp64, L->theta, L->g, L->meas, L->partial_naive, out, e->stream);
-  cudaMemsetAsync(L->vac_acc, 0, 12 * sizeof(double), e->stream);
+  cudaMemsetAsync(L->vac_part, 0, L->vac_bytes, e->stream);
   if (j->p.outer_slab) {
     cudaMemsetAsync(L->acc4T, 0, L->acc4T_bytes, e->stream);
     if (L->acc4O_bytes) cudaMemsetAsync(L->acc4O, 0, L->acc4O_bytes, e->stream);
@@ -182,14 +205,14 @@ void launch_start_of_measurement(ml_server* s, Job* j) {
   }
 }
 
-void begin_measurement(ml_server* s, Job* j) {
+void begin_measurement(Job* j) {
   j->phase = kK0;
   j->left = j->p.k_between;
-  if (j->left == 0) launch_start_of_measurement(s, j);
+  if (j->left == 0) launch_start_of_measurement(j);
 }
 
-void end_of_measurement(ml_server* s, Job* j) {
-  Engine* e = &s->e;
+void end_of_measurement(Job* j) {
+  Engine* e = &j->lane->e;
   LatState* L = j->L;
   double* out = j->rec_dev + static_cast<size_t>(j->meas) * L->meas.rec_len;
   int ncfg;
@@ -202,23 +225,23 @@ void end_of_measurement(ml_server* s, Job* j) {
                     out, e->stream);
     ncfg = j->p.n_sub;
   }
-  launch_write_vac(L->vac_acc, 1.0 / ncfg, L->meas, out, e->stream);
+  launch_write_vac(L->vac_part, L->nparts, 1.0 / ncfg, L->meas, L->g, out, e->stream);
   if (++j->meas < j->n_meas)
-    begin_measurement(s, j);
+    begin_measurement(j);
   else
     j->phase = kDone;
 }
 
 // transitions after the tick's sweep, record and fold
-void advance(ml_server* s, Job* j) {
-  Engine* e = &s->e;
+void advance(Job* j) {
+  Engine* e = &j->lane->e;
   LatState* L = j->L;
   switch (j->phase) {
     case kTherm:
-      if (--j->left <= 0) begin_measurement(s, j);
+      if ((j->left -= j->tick_sweeps) <= 0) begin_measurement(j);
       break;
     case kK0:
-      if (--j->left <= 0) launch_start_of_measurement(s, j);
+      if ((j->left -= j->tick_sweeps) <= 0) launch_start_of_measurement(j);
       break;
     case kOuter:
       cudaMemsetAsync(L->accT, 0, L->accT_bytes, e->stream);
@@ -227,16 +250,16 @@ void advance(ml_server* s, Job* j) {
       j->sub = 0;
       break;
     case kInner:
-      if (++j->sub == j->p.n_sub) {
+      if ((j->sub += j->tick_sweeps) == j->p.n_sub) {
         if (j->p.outer_slab) {
           launch_combine(L->g, L->g.Nt / j->p.outer_slab, j->p.outer_slab / j->p.slab, L->meas, e->pairs,
                          L->accT, L->accO, 1.0 / j->p.n_sub, L->acc4T, L->acc4O, e->stream);
           if (++j->outer < j->p.n_sub_outer)
             j->phase = kOuter;
           else
-            end_of_measurement(s, j);
+            end_of_measurement(j);
         } else {
-          end_of_measurement(s, j);
+          end_of_measurement(j);
         }
       }
       break;
@@ -245,32 +268,53 @@ void advance(ml_server* s, Job* j) {
   }
 }
 
-LatCtl control_of(const Job* j, int nB) {
+// Compound sweeps per tick of a lattice of volume V when the lane's largest
+// admitted one has volume Vmax: about the same work per lattice and tick.
+// Capped at 2: later iterations of a tick hold only the smaller lattices, and
+// each costs its grid barriers or launches whatever its work (a cap of 8 on a
+// single lane cut the steady-state throughput below the arrival rate).
+constexpr int kMaxTickSweeps = 2;
+int tick_share(long long V, long long Vmax) {
+  return static_cast<int>(std::min<long long>(kMaxTickSweeps, std::max<long long>(1, Vmax / V)));
+}
+
+// The tick's control of one lattice: thermalisation and k0 sweeps advance by
+// up to `share` sweeps; the inner loop by up to `share` sub-updates, each
+// recorded into the next ring slot, within one ring buffer (multihit lattices
+// one per tick: their record follows the launch); outer sweeps one.
+LatCtl control_of(Job* j, int nB, int share) {
   LatCtl c{};
+  c.sweeps = 1;
+  if (j->phase == kTherm || j->phase == kK0) c.sweeps = std::max(1, std::min(j->left, share));
   if (j->phase == kOuter) c.mask = j->p.outer_slab;
   if (j->phase == kInner) {
     c.mask = j->p.slab;
     c.record = 1;
     c.slot = j->sub % nB;
-    c.fold = (c.slot == nB - 1 || j->sub == j->p.n_sub - 1) ? 1 : 0;
-    c.nrec = c.slot + 1;
+    int n = std::min(share, std::min(j->p.n_sub - j->sub, nB - c.slot));
+    if (j->L->mh_rec[0]) n = 1;
+    c.sweeps = std::max(1, n);
+    c.fold = (c.slot + c.sweeps == nB || j->sub + c.sweeps == j->p.n_sub) ? 1 : 0;
+    c.nrec = c.slot + c.sweeps;
   }
+  j->tick_sweeps = c.sweeps;
   return c;
 }
 
 // --------------------------------------------------------------------------- admission and tables
 void release_job_memory(ml_server* s, Job* j) {
-  if (j->L) free_lattice(&s->e, j->L);
+  if (j->L) free_lattice(&j->lane->e, j->L);
   j->L = nullptr;
   if (j->rec_dev) s->arena.release(j->rec_dev);
   j->rec_dev = nullptr;
-  s->freed_since_fail = true;
+  s->mem_gen.fetch_add(1);
 }
 
 // returns true when admitted (or failed for good), false when it must wait
-bool try_admit(ml_server* s, Job* j) {
+bool try_admit(ml_server* s, Lane* ln, Job* j) {
   LatState* L = nullptr;
-  int st = make_lattice(&s->e, &j->p, &L);
+  const uint64_t gen = s->mem_gen.load();
+  int st = make_lattice(&ln->e, &j->p, &L);
   j->L = L;
   if (st == ML_OK) {
     j->rec_dev = static_cast<double*>(s->arena.alloc(static_cast<size_t>(j->n_meas) * L->meas.rec_len * sizeof(double)));
@@ -280,12 +324,15 @@ bool try_admit(ml_server* s, Job* j) {
     j->t_admit = now_s() - s->t0;
     j->phase = kTherm;
     j->left = j->n_therm;
-    if (j->left == 0) begin_measurement(s, j);
+    if (j->left == 0) begin_measurement(j);
     return true;
   }
   release_job_memory(s, j);
-  if (st == ML_ENOMEM && !s->active.empty()) {
-    s->freed_since_fail = false;  // retry once memory has been released
+  // out of memory while some lattice (of any lane) holds memory: retry once
+  // memory has been released
+  if (st == ML_ENOMEM && s->n_active.load() > 0) {
+    ln->mem_blocked = true;
+    ln->mem_gen_at_fail = gen + 1;  // this failure's own release above
     return false;
   }
   std::lock_guard<std::mutex> g(s->m);  // cannot ever fit, or failed: report it
@@ -297,7 +344,7 @@ bool try_admit(ml_server* s, Job* j) {
   return true;
 }
 
-int rebuild_tables(ml_server* s) {
+int rebuild_tables(Lane* s) {
   const size_t n = s->active.size();
   s->h_desc.clear();
   s->h_tile_lat.clear();
@@ -357,7 +404,7 @@ int rebuild_tables(ml_server* s) {
   return ML_OK;
 }
 
-int run_tick(ml_server* s) {
+int run_tick(ml_server* srv, Lane* s) {
   Engine* e = &s->e;
   if (s->dirty) {
     int st = rebuild_tables(s);
@@ -365,15 +412,21 @@ int run_tick(ml_server* s) {
   }
   const size_t n = s->active.size();
   s->h_ctl.resize(n);
-  for (size_t i = 0; i < n; ++i) s->h_ctl[i] = control_of(s->active[i], rec_batch(e->fp64));
+  long long vmax = 1;
+  for (Job* j : s->active) vmax = std::max<long long>(vmax, j->L->g.V);
+  int n_compound = 1;
+  for (size_t i = 0; i < n; ++i) {
+    s->h_ctl[i] = control_of(s->active[i], rec_batch(e->fp64), tick_share(s->active[i]->L->g.V, vmax));
+    n_compound = std::max(n_compound, s->h_ctl[i].sweeps);
+  }
   SRV_CUDA(cudaMemcpyAsync(s->d_ctl, s->h_ctl.data(), n * sizeof(LatCtl), cudaMemcpyHostToDevice, e->stream));
   const bool persistent = s->td.total_tiles <= s->coresident_tiles;
   if (persistent) SRV_CUDA(cudaMemsetAsync(e->bar, 0, sizeof(unsigned long long), e->stream));
-  if (launch_sweeps_table(e->fp64, persistent, s->d_desc, s->d_tile_lat, s->td, s->d_ctl, 0, e->n_or, 1, e->d_err,
-                          e->bar, e->stream, true, 0, 0))
+  if (launch_sweeps_table(e->fp64, persistent, s->d_desc, s->d_tile_lat, s->td, s->d_ctl, 0, e->n_or, n_compound,
+                          e->d_err, e->bar, e->stream, true, 0, 0))
     return ML_ECUDA;
   launch_fold_table(e->fp64, e->pairs, s->d_desc, s->td, s->d_ctl, 0, 0, e->stream);
-  for (Job* j : s->active) advance(s, j);
+  for (Job* j : s->active) advance(j);
   SRV_CUDA(cudaGetLastError());
   // finished jobs: read their records back, then release their memory
   bool any_done = false;
@@ -387,78 +440,106 @@ int run_tick(ml_server* s) {
   SRV_CUDA(cudaStreamSynchronize(e->stream));
   int err = 0;
   SRV_CUDA(cudaMemcpy(&err, e->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  ++s->ticks;
+  s->ticks.fetch_add(1);
   if (any_done) {
     std::vector<Job*> keep;
     std::vector<Job*> fin;
     for (Job* j : s->active) (j->phase == kDone ? fin : keep).push_back(j);
     s->active.swap(keep);
     s->n_active = static_cast<int>(s->active.size());
-    for (Job* j : fin) release_job_memory(s, j);
-    std::lock_guard<std::mutex> g(s->m);
-    const double t = now_s() - s->t0;
+    srv->n_active.fetch_sub(static_cast<int>(fin.size()));
+    for (Job* j : fin) release_job_memory(srv, j);
+    std::lock_guard<std::mutex> g(srv->m);
+    const double t = now_s() - srv->t0;
     for (Job* j : fin) {
       j->done = true;
       j->t_done = t;
-      ++s->completed;
+      ++srv->completed;
     }
     s->dirty = true;
-    s->cv_done.notify_all();
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();  // lanes waiting for memory may retry
   }
   if (err) return (err & kErrTimeout) ? ML_ETIMEOUT : ML_EREJECT;
   return ML_OK;
 }
 
-void worker_main(ml_server* s) {
+void worker_main(ml_server* s, Lane* ln) {
   cudaSetDevice(s->device);
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->m);
-      if (s->active.empty() && s->queue.empty()) {
-        if (s->stop) break;
+      const bool can_admit =
+          !ln->queue.empty() && (!ln->mem_blocked || s->mem_gen.load() != ln->mem_gen_at_fail);
+      if (ln->active.empty() && !can_admit) {
+        if (s->stop && ln->queue.empty()) break;
         s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
         continue;
       }
     }
-    // admission (FIFO) while memory and the active-set limit allow
+    // admission (FIFO within the lane) while memory and the active-set limit allow
     for (;;) {
       Job* j = nullptr;
       {
         std::lock_guard<std::mutex> g(s->m);
-        if (s->queue.empty() || static_cast<int>(s->active.size()) >= s->max_active) break;
-        if (!s->freed_since_fail && !s->active.empty()) break;
-        j = s->queue.front();
+        if (ln->queue.empty() || s->n_active.load() >= s->max_active) break;
+        if (ln->mem_blocked && s->mem_gen.load() == ln->mem_gen_at_fail) break;
+        j = ln->queue.front();
       }
-      if (!try_admit(s, j)) break;
+      ln->mem_blocked = false;
+      if (!try_admit(s, ln, j)) break;
       {
         std::lock_guard<std::mutex> g(s->m);
-        s->queue.pop_front();
+        ln->queue.pop_front();
       }
       if (!j->done) {
-        s->active.push_back(j);
-        s->dirty = true;
+        ln->active.push_back(j);
+        s->n_active.fetch_add(1);
+        ln->dirty = true;
       }
     }
-    if (s->active.empty()) continue;
-    s->n_active = static_cast<int>(s->active.size());
-    const int st = run_tick(s);
+    if (ln->active.empty()) continue;
+    ln->n_active = static_cast<int>(ln->active.size());
+    const int st = run_tick(s, ln);
     if (st) {
-      // a device error ends every job in flight; the server stays usable
+      // a device error ends every job in flight in this lane; the server stays usable
       std::lock_guard<std::mutex> g(s->m);
-      for (Job* j : s->active) {
+      for (Job* j : ln->active) {
         j->status = st;
         j->done = true;
         j->t_done = now_s() - s->t0;
         ++s->failed;
       }
-      s->worker_status = st;
       s->cv_done.notify_all();
-      for (Job* j : s->active) release_job_memory(s, j);
-      s->active.clear();
-      s->dirty = true;
-      cudaMemset(s->e.d_err, 0, sizeof(int));
+      for (Job* j : ln->active) release_job_memory(s, j);
+      s->n_active.fetch_sub(static_cast<int>(ln->active.size()));
+      ln->active.clear();
+      ln->n_active = 0;
+      ln->dirty = true;
+      cudaMemset(ln->e.d_err, 0, sizeof(int));
     }
   }
+}
+
+// Size lane of a lattice of volume V among `lanes`: volumes below 2^16
+// sites, below 2^18, and above (one lane: everything together).
+int lane_of(long long V, int lanes) {
+  int b = 0;
+  while ((1ll << (b + 1)) <= V) ++b;  // floor(log2 V)
+  return std::min(lanes - 1, std::max(0, (b - 14) / 2));
+}
+
+void destroy_lane(Lane* ln) {
+  cudaFree(ln->d_desc);
+  cudaFree(ln->d_tile_lat);
+  cudaFree(ln->d_ctl);
+  cudaFree(ln->e.d_err);
+  cudaFree(ln->e.bar);
+  ln->e.d_err = nullptr;
+  ln->e.bar = nullptr;
+  if (ln->e.stream) cudaStreamDestroy(ln->e.stream);
+  ln->e.stream = nullptr;
+  delete ln;
 }
 
 }  // namespace
@@ -468,7 +549,8 @@ extern "C" {
 int ml_server_create(const ml_server_config* cfg, ml_server** out) {
   if (!cfg || !out) return ML_EINVAL;
   *out = nullptr;
-  if ((cfg->prec != ML_FP64 && cfg->prec != ML_FP32) || cfg->n_or < 0 || cfg->budget_bytes < (1u << 20))
+  if ((cfg->prec != ML_FP64 && cfg->prec != ML_FP32) || cfg->n_or < 0 || cfg->budget_bytes < (1u << 20) ||
+      cfg->lanes < 0 || cfg->lanes > 8)
     return ML_EINVAL;
   ml_server* s = new (std::nothrow) ml_server();
   if (!s) return ML_ENOMEM;
@@ -478,32 +560,42 @@ int ml_server_create(const ml_server_config* cfg, ml_server** out) {
     return st;
   }
   cudaGetDevice(&s->device);
-  s->e.fp64 = cfg->prec == ML_FP64;
-  s->e.n_or = cfg->n_or;
-  s->e.alloc.alloc = arena_alloc;
-  s->e.alloc.free = arena_free;
-  s->e.alloc.ctx = &s->arena;
-  s->e.use_alloc = true;
+  s->fp64 = cfg->prec == ML_FP64;
+  s->n_or = cfg->n_or;
   s->max_active = cfg->max_active > 0 ? cfg->max_active : 1024;
+  const int nlanes = cfg->lanes > 0 ? cfg->lanes : 3;
   cudaError_t ce = prepare_measure_kernels() ? cudaErrorUnknown : cudaSuccess;
-  if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s->e.stream, cudaStreamNonBlocking);
-  if (ce == cudaSuccess) s->e.own_stream = true;
-  if (ce == cudaSuccess) ce = cudaMalloc(&s->e.d_err, sizeof(int));
-  if (ce == cudaSuccess) ce = cudaMalloc(&s->e.bar, sizeof(unsigned long long));
-  if (ce == cudaSuccess) ce = cudaMemset(s->e.d_err, 0, sizeof(int));
   int sms = 0, per_sm = 0;
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-  if (ce == cudaSuccess) per_sm = sweep_blocks_per_sm(s->e.fp64);
+  if (ce == cudaSuccess) per_sm = sweep_blocks_per_sm(s->fp64);
+  for (int k = 0; k < nlanes && ce == cudaSuccess; ++k) {
+    Lane* ln = new (std::nothrow) Lane();
+    if (!ln) {
+      ce = cudaErrorMemoryAllocation;
+      break;
+    }
+    s->lanes.push_back(ln);
+    ln->index = k;
+    ln->e.fp64 = s->fp64;
+    ln->e.n_or = s->n_or;
+    ln->e.alloc.alloc = arena_alloc;
+    ln->e.alloc.free = arena_free;
+    ln->e.alloc.ctx = &s->arena;
+    ln->e.use_alloc = true;
+    ln->coresident_tiles = sms * per_sm;
+    ce = cudaStreamCreateWithFlags(&ln->e.stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ln->e.own_stream = true;
+    if (ce == cudaSuccess) ce = cudaMalloc(&ln->e.d_err, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMalloc(&ln->e.bar, sizeof(unsigned long long));
+    if (ce == cudaSuccess) ce = cudaMemset(ln->e.d_err, 0, sizeof(int));
+  }
   if (ce != cudaSuccess) {
-    if (s->e.stream) cudaStreamDestroy(s->e.stream);
-    cudaFree(s->e.d_err);
-    cudaFree(s->e.bar);
+    for (Lane* ln : s->lanes) destroy_lane(ln);
     delete s;
     return ML_ECUDA;
   }
-  s->coresident_tiles = sms * per_sm;
   s->t0 = now_s();
-  s->worker = std::thread(worker_main, s);
+  for (Lane* ln : s->lanes) ln->worker = std::thread(worker_main, s, ln);
   *out = s;
   return ML_OK;
 }
@@ -514,7 +606,7 @@ int ml_submit(ml_server* s, const ml_params* p, int n_therm, int n_meas, uint64_
   if (st) return st;
   // the server's step machine folds every record as it comes: no replay;
   // its slab sums are double precision: no float-pair sums
-  if ((p->prec == ML_FP64) != s->e.fp64 || p->n_or != s->e.n_or || p->replay || p->pair_sums) return ML_EINVAL;
+  if ((p->prec == ML_FP64) != s->fp64 || p->n_or != s->n_or || p->replay || p->pair_sums) return ML_EINVAL;
   Job* j = new (std::nothrow) Job();
   if (!j) return ML_ENOMEM;
   j->p = *p;
@@ -535,9 +627,11 @@ int ml_submit(ml_server* s, const ml_params* p, int n_therm, int n_meas, uint64_
     j->id = s->next_id++;
     j->t_submit = now_s() - s->t0;
     s->jobs[j->id] = j;
-    s->queue.push_back(j);
+    const long long V = static_cast<long long>(p->L) * p->L * p->L * p->Nt;
+    j->lane = s->lanes[lane_of(V, static_cast<int>(s->lanes.size()))];
+    j->lane->queue.push_back(j);
   }
-  s->cv_work.notify_one();
+  s->cv_work.notify_all();
   *job = j->id;
   return ML_OK;
 }
@@ -593,11 +687,15 @@ int ml_job_release(ml_server* s, uint64_t job) {
 int ml_server_stats(ml_server* s, ml_server_info* out) {
   if (!s || !out) return ML_EINVAL;
   std::lock_guard<std::mutex> g(s->m);
-  out->queued = static_cast<int>(s->queue.size());
+  out->queued = 0;
+  out->ticks = 0;
+  for (Lane* ln : s->lanes) {
+    out->queued += static_cast<int>(ln->queue.size());
+    out->ticks += ln->ticks.load();
+  }
   out->active = s->n_active.load();
   out->completed = s->completed;
   out->failed = s->failed;
-  out->ticks = s->ticks;
   out->budget_bytes = s->arena.size();
   out->used_bytes = s->arena.used();
   return ML_OK;
@@ -608,28 +706,26 @@ int ml_server_destroy(ml_server* s) {
   {
     std::lock_guard<std::mutex> g(s->m);
     s->stop = true;
-    for (Job* j : s->queue) {  // never started
-      j->status = ML_ESTATE;
-      j->done = true;
+    for (Lane* ln : s->lanes) {
+      for (Job* j : ln->queue) {  // never started
+        j->status = ML_ESTATE;
+        j->done = true;
+      }
+      ln->queue.clear();
     }
-    s->queue.clear();
   }
   s->cv_work.notify_all();
-  if (s->worker.joinable()) s->worker.join();
-  cudaStreamSynchronize(s->e.stream);
-  for (Job* j : s->active) release_job_memory(s, j);
-  s->active.clear();
+  for (Lane* ln : s->lanes)
+    if (ln->worker.joinable()) ln->worker.join();
+  for (Lane* ln : s->lanes) {
+    cudaStreamSynchronize(ln->e.stream);
+    for (Job* j : ln->active) release_job_memory(s, j);
+    ln->active.clear();
+  }
   for (auto& kv : s->jobs) delete kv.second;
   s->jobs.clear();
-  cudaFree(s->d_desc);
-  cudaFree(s->d_tile_lat);
-  cudaFree(s->d_ctl);
-  cudaFree(s->e.d_err);
-  cudaFree(s->e.bar);
-  s->e.d_err = nullptr;
-  s->e.bar = nullptr;
-  cudaStreamDestroy(s->e.stream);
-  s->e.stream = nullptr;
+  for (Lane* ln : s->lanes) destroy_lane(ln);
+  s->lanes.clear();
   delete s;
   return ML_OK;
 }

@@ -44,6 +44,7 @@ __device__ __forceinline__ void update_link_mu(T* th, const Geom& g, int parity,
   int c[4];
   half_site_coords(g, h, parity, c);
   if (slab_d > 0 && mu != 0 && small_mod(c[0], slab_d) == 0) return;  // frozen boundary link
+  if (c[0] < g.t_lo || c[0] >= g.t_hi) return;  // another rank's time slice
   const int i = site_index(g, c[0], c[1], c[2], c[3]);
   const int op = parity ^ 1;
   const int ipmu = step_index(g, i, c, mu, +1);
@@ -123,6 +124,7 @@ __device__ __forceinline__ void update_pair_mu(T* th, const Geom& g, int parity,
   int c0[4];
   half_site_coords(g, h0, parity, c0);
   if (slab_d > 0 && mu != 0 && small_mod(c0[0], slab_d) == 0) return;  // frozen boundary links (same t)
+  if (c0[0] < g.t_lo || c0[0] >= g.t_hi) return;  // another rank's time slice (both links)
   const int c1[4] = {c0[0], c0[1] + 2, c0[2], c0[3]};
   const int i0 = site_index(g, c0[0], c0[1], c0[2], c0[3]);
   const int i1 = i0 + 2;
@@ -256,6 +258,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
   T c_beta = T(0);
   UpdateRule c_rule{};
   unsigned long long c_base = 0;
+  int c_sweeps = 0;
   if (one_tile && static_cast<int>(blockIdx.x) < total_tiles) {
     const int i = tile_lat[blockIdx.x];
     const LatDesc& L = d[i];
@@ -268,13 +271,14 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
     c_beta = static_cast<T>(L.beta);
     c_rule = update_rule(L);
     c_base = *L.n_dev;
+    c_sweeps = ctl ? ctl[i].sweeps : n_compound;
   }
   for (int c = 0; c < n_compound; ++c) {
     for (int sweep = 0; sweep <= n_or; ++sweep)
       for (int mu = 0; mu < 4; ++mu)
         for (int par = 0; par < 2; ++par) {
           if (one_tile) {
-            if (c_theta && c_h < c_g.Vh) {
+            if (c_theta && c_h < c_g.Vh && c < c_sweeps) {
               if (sweep == 0)
                 update_link<T, 0>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err,
                                   c_rule);
@@ -289,6 +293,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
               const int h = (t - L.tile_start) * kSweepTile + threadIdx.x;
               const Geom g = L.g;  // registers, not loads from the table
               if (h >= g.Vh) continue;
+              if (ctl && c >= ctl[i].sweeps) continue;  // this lattice's sweeps of the step are done
               const int md = ctl ? ctl[i].mask : mask;
               const unsigned long long n = *L.n_dev + 1 + c;
               if (sweep == 0)
@@ -301,27 +306,34 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
           }
           if (!grid_barrier(bar, err)) return;
         }
-  }
-  if (record) {
-    // record of the new configurations (the work of k_record_table, warp for
-    // warp)
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int li = 0; li < nlat; ++li) {
-      int buf = rec_buf, slot = rec_slot;
-      if (ctl) {
-        if (!ctl[li].record) continue;
-        buf = ctl[li].buf;
-        slot = ctl[li].slot;
+    if (record) {
+      // record of the new configurations (the work of k_record_table, warp
+      // for warp): with ctl after each of a lattice's sweeps of the step
+      // (slot + c), without it after the last sweep
+      const int lane = threadIdx.x & 31;
+      const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+      const int nwarps = (gridDim.x * blockDim.x) >> 5;
+      bool any = false;
+      for (int li = 0; li < nlat; ++li) {
+        int buf = rec_buf, slot = rec_slot;
+        if (ctl) {
+          if (!ctl[li].record || c >= ctl[li].sweeps) continue;
+          buf = ctl[li].buf;
+          slot = ctl[li].slot + c;
+        } else if (c != n_compound - 1) {
+          continue;
+        }
+        any = true;
+        const LatDesc& L = d[li];
+        const int nw = record_warps(L), items = (L.m.nc + 1) * nw;
+        for (int it = gw; it < items; it += nwarps) record_warp<T>(L, buf, slot, it / nw, it - (it / nw) * nw, lane);
       }
-      const LatDesc& L = d[li];
-      const int nw = record_warps(L), items = (L.m.nc + 1) * nw;
-      for (int it = gw; it < items; it += nwarps) record_warp<T>(L, buf, slot, it / nw, it - (it / nw) * nw, lane);
+      // the record reads the configuration the next sweep moves
+      if (any && c + 1 < n_compound && !grid_barrier(bar, err)) return;
     }
   }
   if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < nlat; i += blockDim.x) *d[i].n_dev += n_compound;
+    for (int i = threadIdx.x; i < nlat; i += blockDim.x) *d[i].n_dev += ctl ? ctl[i].sweeps : n_compound;
 }
 
 // One (mu, parity) pass of every lattice of a table, one tile per block; the
@@ -330,7 +342,7 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(kSweepThreads, 4) k_pass_table(const LatDesc* __restrict__ d,
                                                               const int* __restrict__ tile_lat,
                                                               const LatCtl* __restrict__ ctl, int mask, int mu,
-                                                              int parity, int* __restrict__ err) {
+                                                              int parity, int* __restrict__ err, int c) {
   const int i = tile_lat[blockIdx.x];
   const LatDesc& L = d[i];
   const int h = (blockIdx.x - L.tile_start) * kSweepTile + threadIdx.x;
@@ -338,6 +350,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_pass_table(const LatDesc* 
   // would be a load from the table in global memory
   const Geom g = L.g;
   if (h >= g.Vh) return;
+  if (ctl && c >= ctl[i].sweeps) return;  // this lattice's sweeps of the step are done
   const int md = ctl ? ctl[i].mask : mask;
   T* const th = static_cast<T*>(L.theta);
   const unsigned long long n = *L.n_dev;
@@ -353,19 +366,22 @@ template <typename T, int KIND>
 __global__ void __launch_bounds__(kSweepThreads / 2) k_pass_table_pair(const LatDesc* __restrict__ d,
                                                                        const int* __restrict__ tile_lat,
                                                                        const LatCtl* __restrict__ ctl, int mask,
-                                                                       int mu, int parity, int* __restrict__ err) {
+                                                                       int mu, int parity, int* __restrict__ err,
+                                                                       int c) {
   const int i = tile_lat[blockIdx.x];
   const LatDesc& L = d[i];
   const Geom g = L.g;
   const int hp = (blockIdx.x - L.tile_start) * (kSweepTile / 2) + threadIdx.x;
   if (2 * hp >= g.Vh) return;
+  if (ctl && c >= ctl[i].sweeps) return;
   const int md = ctl ? ctl[i].mask : mask;
   update_pair<T, KIND>(static_cast<T*>(L.theta), g, mu, parity, md, hp, *L.n_dev, L.k0, L.k1,
                        static_cast<T>(L.beta), err, update_rule(L));
 }
 
-__global__ void k_sweep_begin_table(const LatDesc* __restrict__ d, int nlat) {
-  for (int i = threadIdx.x; i < nlat; i += blockDim.x) *d[i].n_dev += 1ull;
+__global__ void k_sweep_begin_table(const LatDesc* __restrict__ d, int nlat, const LatCtl* __restrict__ ctl, int c) {
+  for (int i = threadIdx.x; i < nlat; i += blockDim.x)
+    if (!ctl || c < ctl[i].sweeps) *d[i].n_dev += 1ull;
 }
 
 template <typename T>
@@ -511,10 +527,9 @@ static cudaError_t launch_sweeps_table_t(const LatDesc* d, const int* tile_lat, 
 
 template <typename T>
 static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const TableDims& td, const LatCtl* ctl,
-                                  int mask, int n_or, int n_compound, int* err, cudaStream_t s,
-                                  const LatDesc* single) {
-  for (int c = 0; c < n_compound; ++c) {
-    k_sweep_begin_table<<<1, 128, 0, s>>>(d, td.nlat);
+                                  int mask, int n_or, int c, int* err, cudaStream_t s, const LatDesc* single) {
+  {
+    k_sweep_begin_table<<<1, 128, 0, s>>>(d, td.nlat, ctl, c);
     count_launches(1);
     for (int sweep = 0; sweep <= n_or; ++sweep)
       for (int mu = 0; mu < 4; ++mu)
@@ -535,14 +550,14 @@ static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const T
           if (td.all_l4) {  // two links per thread
             if (sweep == 0)
               k_pass_table_pair<T, 0><<<td.total_tiles, kSweepThreads / 2, 0, s>>>(d, tile_lat, ctl, mask, mu, par,
-                                                                                    err);
+                                                                                    err, c);
             else
               k_pass_table_pair<T, 1><<<td.total_tiles, kSweepThreads / 2, 0, s>>>(d, tile_lat, ctl, mask, mu, par,
-                                                                                    err);
+                                                                                    err, c);
           } else if (sweep == 0) {
-            k_pass_table<T, 0><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
+            k_pass_table<T, 0><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err, c);
           } else {
-            k_pass_table<T, 1><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err);
+            k_pass_table<T, 1><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err, c);
           }
           count_launches(1);
         }
@@ -563,11 +578,14 @@ int launch_sweeps_table(bool fp64, bool persistent, const LatDesc* d, const int*
     count_launches(1);
     if (record) launch_mh_record_table(fp64, d, td, ctl, rec_buf, rec_slot, s);
   } else {
-    if (fp64)
-      launch_passes_table_t<double>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s, single);
-    else
-      launch_passes_table_t<float>(d, tile_lat, td, ctl, mask, n_or, n_compound, err, s, single);
-    if (record) launch_record_table(fp64, d, td, ctl, rec_buf, rec_slot, s);
+    for (int c = 0; c < n_compound; ++c) {
+      if (fp64)
+        launch_passes_table_t<double>(d, tile_lat, td, ctl, mask, n_or, c, err, s, single);
+      else
+        launch_passes_table_t<float>(d, tile_lat, td, ctl, mask, n_or, c, err, s, single);
+      // with ctl a record after each of a lattice's sweeps, without it after the last
+      if (record && (ctl || c == n_compound - 1)) launch_record_table(fp64, d, td, ctl, rec_buf, rec_slot, s, c);
+    }
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? 0 : -1;

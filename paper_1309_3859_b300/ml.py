@@ -22,6 +22,7 @@ ML_FP64, ML_FP32 = 0, 1
 ML_SWEEP_PERSISTENT, ML_SWEEP_PASSES, ML_SWEEP_RESIDENT = 0, 1, 2
 ML_FOLD_SITE, ML_FOLD_TILE = 0, 1
 ML_UPDATE_HEATBATH, ML_UPDATE_METROPOLIS = 0, 1
+ML_PART_LINKS, ML_PART_SLAB_SUMS, ML_PART_VACUUM, ML_PART_W_SUMS = 0, 1, 2, 3
 (ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP, ML_K_SUBUPDATE,
  ML_K_FULLSWEEP) = range(8)
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
@@ -114,6 +115,12 @@ SIGNATURES = {
     "ml_job_release": (ctypes.c_int, [_H, ctypes.c_uint64]),
     "ml_server_stats": (ctypes.c_int, [_H, ctypes.c_void_p]),
     "ml_server_destroy": (ctypes.c_int, [_H]),
+    "ml_set_time_range": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int]),
+    "ml_part_size": (ctypes.c_int, [_H, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "ml_part_copy": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_void_p, ctypes.c_int]),
+    "ml_measure_inner": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_size_t]),
+    "ml_measure_products": (ctypes.c_int, [_H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "ml_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ml_kernel_launches": (ctypes.c_uint64, []),
 }
@@ -376,6 +383,49 @@ class Lattice:
     def sync(self):
         _check(lib().ml_sync(self.h), "ml_sync")
 
+    # -- time-slab partition (ml_set_time_range ... ml_measure_products)
+    def set_time_range(self, t_lo: int, t_hi: int):
+        _check(lib().ml_set_time_range(self.h, int(t_lo), int(t_hi)), "ml_set_time_range")
+
+    def part_size(self, what: int) -> int:
+        n = ctypes.c_size_t()
+        _check(lib().ml_part_size(self.h, int(what), ctypes.byref(n)), "ml_part_size")
+        return n.value
+
+    def part_read(self, what: int, begin: int, count: int, mu: int = 0, parity: int = 0):
+        """Units [begin, begin + count) of a partition block as a new uint8 device tensor."""
+        torch = self._torch
+        with torch.cuda.stream(self.stream):
+            buf = torch.empty(count * self.part_size(what), dtype=torch.uint8, device=self.device)
+        _check(lib().ml_part_copy(self.h, int(what), int(mu), int(parity), int(begin), int(count),
+                                  ctypes.c_void_p(buf.data_ptr()), 0), "ml_part_copy")
+        # the copy is on the lattice's stream: work the caller queues on its
+        # current stream waits for it, and the memory is kept until then
+        cur = torch.cuda.current_stream(self.device)
+        cur.wait_stream(self.stream)
+        buf.record_stream(cur)
+        return buf
+
+    def part_write(self, what: int, begin: int, count: int, buf, mu: int = 0, parity: int = 0):
+        """Copy a uint8 device tensor into units [begin, begin + count) of a partition block."""
+        assert buf.is_cuda and buf.is_contiguous() and buf.numel() == count * self.part_size(what)
+        self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+        buf.record_stream(self.stream)  # its memory is not reused before the copy is done
+        _check(lib().ml_part_copy(self.h, int(what), int(mu), int(parity), int(begin), int(count),
+                                  ctypes.c_void_p(buf.data_ptr()), 1), "ml_part_copy")
+
+    def measure_inner(self, rec):
+        assert rec.is_cuda and rec.dtype == self._torch.float64 and rec.numel() >= self.rec_len
+        _check(lib().ml_measure_inner(self.h, ctypes.c_void_p(rec.data_ptr()), rec.numel()), "ml_measure_inner")
+
+    def measure_products(self, w_in=None, w_out=None, rec=None):
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        if w_in is not None:
+            self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+            w_in.record_stream(self.stream)
+        _check(lib().ml_measure_products(self.h, ptr(w_in), ptr(w_out), ptr(rec),
+                                         rec.numel() if rec is not None else 0), "ml_measure_products")
+
 
 def _torch_allocator(torch, dev, st):
     def _alloc(size, ctx):
@@ -489,7 +539,7 @@ class Batch:
 
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("n_or", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
-                ("max_active", ctypes.c_int)]
+                ("max_active", ctypes.c_int), ("lanes", ctypes.c_int)]
 
 
 class _ServerStats(ctypes.Structure):
@@ -501,11 +551,11 @@ class _ServerStats(ctypes.Structure):
 class Server:
     """Request server with continuous batching (``ml_server_*``, ``ml_submit``)."""
 
-    def __init__(self, budget_bytes: int, fp64: bool = False, n_or: int = 3, max_active: int = 0):
+    def __init__(self, budget_bytes: int, fp64: bool = False, n_or: int = 3, max_active: int = 0, lanes: int = 0):
         import torch
 
         torch.cuda.init()
-        cfg = _ServerConfig(ML_FP64 if fp64 else ML_FP32, n_or, int(budget_bytes), int(max_active))
+        cfg = _ServerConfig(ML_FP64 if fp64 else ML_FP32, n_or, int(budget_bytes), int(max_active), int(lanes))
         h = ctypes.c_void_p()
         _check(lib().ml_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ml_server_create")
         self.h = h

@@ -4,6 +4,8 @@
   with requests arriving while others run (different phases share ticks),
   mixed sizes, couplings, schedules and two-level requests.
 * Multihit and Metropolis requests in the mix, bit-identical to alone.
+* Size lanes: requests of different volumes tick in separate lanes (own
+  streams and workers), records still as alone; one lane also works.
 * Admission by HBM budget: requests queue until memory frees up, all finish,
   usage never exceeds the budget; a request larger than the budget fails with
   ML_ENOMEM; mismatched precision is rejected.
@@ -112,3 +114,37 @@ def test_server_budget_admission_and_limits():
         with pytest.raises(ml.MLError) as exc:
             srv.submit(job_params(0, fp64=True), 0, 1)
         assert exc.value.status == ml.ML_EINVAL
+
+
+def test_server_lanes_match_alone():
+    """Requests of different volumes go to different size lanes (below 2^16
+    sites, below 2^18, above), which tick on their own streams at the same
+    time; every request's records are still those of the same parameters run
+    alone, and a lane of one lattice still advances small lattices by up to
+    two sweeps per tick."""
+    specs = [dict(L=4, Nt=4, n_sub=5, k_between=1), dict(L=16, Nt=16, n_sub=3, k_between=1),
+             dict(L=24, Nt=20, n_sub=2, k_between=0), dict(L=6, Nt=8, n_sub=17, k_between=2),
+             dict(L=16, Nt=12, n_sub=4, k_between=1)]
+    ps = [ml.Params(beta=0.97, seed=700 + i, fp64=False, slab=2, r=(1, 2), rf=(2,), probes=((0, 0), (1, 0)),
+                    comp_mask=0x09, **kw) for i, kw in enumerate(specs)]
+    sched = [(5, 2), (3, 1), (1, 1), (4, 1), (2, 1)]
+    with ml.Server(budget_bytes=2 << 30, fp64=False) as srv:
+        jobs = []
+        for p, sc in zip(ps, sched):
+            jobs.append(srv.submit(p, *sc))
+            time.sleep(0.01)
+        results = [srv.wait(j, timeout_s=300) for j in jobs]
+        st = srv.stats()
+        assert st["completed"] == len(ps) and st["failed"] == 0 and st["used_bytes"] == 0
+    for i, p in enumerate(ps):
+        assert np.array_equal(results[i], run_alone(p, *sched[i])), i
+
+
+def test_server_one_lane():
+    """lanes = 1: every request in one tick loop, records as alone."""
+    ps = [job_params(i, False) for i in range(3)]
+    with ml.Server(budget_bytes=256 << 20, fp64=False, lanes=1) as srv:
+        jobs = [srv.submit(p, 2, 1) for p in ps]
+        results = [srv.wait(j, timeout_s=120) for j in jobs]
+    for i, p in enumerate(ps):
+        assert np.array_equal(results[i], run_alone(p, 2, 1)), i
