@@ -424,30 +424,74 @@ def batch_params(ml, n=64):
 
 
 def batched_point(ml, steps=3, warmup=1):
+    """The 64-lattice batch in the autotuned sweep implementation, and each
+    implementation forced (the same chains: the implementations are
+    bit-identical), ms per measurement of every lattice."""
     import torch
 
     ps = batch_params(ml)
+    names = ["persistent", "per-pass", "resident"]
+    forced = {}
     with ml.Batch(ps) as b:
         b.thermalize(200)
-        for _ in range(warmup):
-            b.measure_device(1)
-        b.sync()
-        st = b.stream
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(steps):
-            b.measure_device(1)
-        e1.record(st)
-        b.sync()
-        ms = e0.elapsed_time(e1) / steps
-        mode = b.sweep_mode
+        auto = b.sweep_mode
+
+        def timed():
+            for _ in range(warmup):
+                b.measure_device(1)
+            b.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(b.stream)
+            for _ in range(steps):
+                b.measure_device(1)
+            e1.record(b.stream)
+            b.sync()
+            return e0.elapsed_time(e1) / steps
+
+        ms = timed()
+        for mode in (ml.ML_SWEEP_PERSISTENT, ml.ML_SWEEP_PASSES, ml.ML_SWEEP_RESIDENT):
+            try:
+                b.sweep_mode = mode
+            except ml.MLError:
+                continue
+            forced[names[mode]] = timed()
+        b.sweep_mode = auto
     upd = 0
     for p in ps:
         V = p.L ** 3 * p.Nt
         upd += (p.k_between * 4 * V + p.n_sub * (V + 3 * V * (p.slab - 1) // p.slab)) * (1 + p.n_or)
     return {"workload": "batched-64-lattices-fp32", "lattices": len(ps), "ms_per_step": ms,
             "link_updates_per_s": upd / (ms * 1e-3), "measurements_per_s": len(ps) / (ms * 1e-3),
-            "sweep_impl": ["persistent", "per-pass", "resident"][mode], "step": "one measurement of every lattice"}
+            "sweep_impl": names[auto], "ms_per_step_by_impl": forced,
+            "step": "one measurement of every lattice"}
+
+
+def step_breakdown(ml, w, n_meas=20):
+    """Where the step goes, from the public API: streamed ms per measurement
+    of the workload, without the k0 sweeps, without the field insertions
+    (no rf, probes or components), and without both."""
+    import torch
+
+    variants = {"step": {}, "no_k0": dict(k_between=0), "no_field": dict(rf=(), probes=(), comp_mask=0),
+                "no_k0_no_field": dict(k_between=0, rf=(), probes=(), comp_mask=0)}
+    out = {}
+    for name, kw in variants.items():
+        p = ml.Params.from_workload(w, **kw)
+        with ml.Lattice(p) as lat:
+            lat.thermalize(50)
+            recs = torch.empty((n_meas, lat.rec_len), dtype=torch.float64, device=lat.device)
+            lat.measure_device(3, recs[:3])
+            lat.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(lat.stream)
+            lat.measure_device(n_meas, recs)
+            e1.record(lat.stream)
+            lat.sync()
+            out[name + "_ms"] = e0.elapsed_time(e1) / n_meas
+    out["k0_sweeps_ms"] = out["step_ms"] - out["no_k0_ms"]
+    out["field_insertions_ms"] = out["step_ms"] - out["no_field_ms"]
+    out["note"] = "streamed measurements (one call of 20); differences of whole steps, so overlap is accounted"
+    return out
 
 
 def serving_request(ml, L, Nt, beta, seed):
@@ -494,7 +538,10 @@ def serving_point(ml, n_requests=1000, load=0.8, budget_gb=160):
             "capacity_req_per_s": capacity, "arrival_rate_per_s": rate, "throughput_req_per_s": n_requests / span,
             "link_updates_per_s": upd / span, "latency_s": {"p50": q(lat, 50), "p99": q(lat, 99)},
             "latency_by_L_s": {str(L): {"n": len(v), "p50": q(v, 50), "p99": q(v, 99)} for L, v in sorted(by_L.items())},
-            "budget_gb": budget_gb, "ticks": stats["ticks"],
+            # link updates x 36 B (the unmasked per-pass bytes of an FP32 update): an upper bound on the sweeps'
+            # algorithmic traffic, as a fraction of the measured HBM bandwidth
+            "sweep_gbs_at_36B": 36 * upd / span / 1e9, "sweep_frac_at_36B": 36 * upd / span / 1e9 / measured_peaks()[0],
+            "budget_gb": budget_gb, "ticks": stats["ticks"], "lanes": 3,
             "request": "100 thermalisation sweeps + 1 measurement (50 sub-updates), L in 12..32, Nt in 4..12"}
 
 
@@ -703,6 +750,7 @@ def run_gpu(args, w, rank, world):
     rp_point = replay_point(ml, w) if rank == 0 and not args.no_extra and not w.outer_slab else None
     f64_point = fp64_point(ml, w) if rank == 0 and not args.no_extra and not w.fp64 else None
     pair_point = pair_sums_point(ml, w) if rank == 0 and not args.no_extra and not w.fp64 else None
+    breakdown = step_breakdown(ml, w) if rank == 0 and not args.no_extra else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -769,6 +817,7 @@ def run_gpu(args, w, rank, world):
         "replay": rp_point,
         "fp64_path": f64_point,
         "pair_sums": pair_point,
+        "step_breakdown": breakdown,
         "vs_fp64_path": (f64_point["ms_per_step"] / (ms / args.steps)) if f64_point else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
