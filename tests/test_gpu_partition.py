@@ -98,3 +98,34 @@ def test_partition_two_ranks_matches_one_process(case, tmp_path):
         own = slice(lo * Ns, hi * Ns)
         assert np.array_equal(d["th"][:, own], th_ref[:, own]), rank
         assert int(d["n"]) == n_ref
+
+
+def test_partition_api_refusals():
+    """ml_set_time_range validates its range (whole top-level slabs inside the
+    lattice); with a partial range the whole-lattice schedules refuse
+    (ML_ESTATE), as do products without a preceding inner phase; replay
+    handles cannot be partitioned; (0, Nt) restores the whole lattice."""
+    import torch
+
+    p = ml.Params(**CASES["two-level-fp64"])  # Nt 8, outer slabs of 4
+    with ml.Lattice(p) as lat:
+        for lo, hi in [(0, 2), (2, 6), (-4, 4), (4, 12), (4, 4)]:
+            with pytest.raises(ml.MLError) as e:
+                lat.set_time_range(lo, hi)
+            assert e.value.status == ml.ML_EINVAL, (lo, hi)
+        lat.set_time_range(4, 8)
+        for call in (lambda: lat.measure(1), lambda: lat.thermalize(1)):
+            with pytest.raises(ml.MLError) as e:
+                call()
+            assert e.value.status == ml.ML_ESTATE
+        rec = torch.zeros(lat.rec_len, dtype=torch.float64, device=lat.device)
+        with pytest.raises(ml.MLError) as e:
+            lat.measure_products(rec=rec)
+        assert e.value.status == ml.ML_ESTATE
+        lat.set_time_range(0, 8)
+        assert np.all(np.isfinite(lat.measure(1)))
+    q = ml.Params(**dict(CASES["one-level-fp32"], replay=1))
+    with ml.Lattice(q) as lat:
+        with pytest.raises(ml.MLError) as e:
+            lat.set_time_range(0, 4)
+        assert e.value.status == ml.ML_EINVAL
