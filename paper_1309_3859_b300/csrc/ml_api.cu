@@ -198,13 +198,15 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   const size_t nout = static_cast<size_t>(nr) + nrf + static_cast<size_t>(nrf) * np * nc * 2;
   const size_t nvw = static_cast<size_t>((g.V + 255) / 256) * 8;
   L->partial = static_cast<double2*>(lat_alloc(e, L, nout * nw * sizeof(double2)));
+  L->rest_bytes = static_cast<size_t>(nrf) * nslab_in * g.Ns * sizeof(double2);
+  L->rest = L->rest_bytes ? static_cast<double2*>(lat_alloc(e, L, L->rest_bytes)) : nullptr;
   L->partial_naive =
       static_cast<double2*>(lat_alloc(e, L, (static_cast<size_t>(nr) * nw + nvw / 2 + 1) * sizeof(double2)));
   L->scratch_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
   L->naive_theta = lat_alloc(e, L, 4ull * g.V * tsz);
   const bool ok = L->theta && L->naive_theta && L->d_n && L->d_lists && L->accT && (L->accO || !L->accO_bytes) && L->osum[0] &&
                   L->osum[1] && (!p->replay || (L->replay_theta && L->replay_n)) &&
-                  L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->partial &&
+                  L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->partial && (L->rest || !L->rest_bytes) &&
                   L->partial_naive && L->scratch_n && (!nslab_out || (L->acc4T && L->acc4O)) &&
                   (!any_mh || (L->mh_rec[0] && L->mh_rec[1]));
   if (!ok) return ML_ENOMEM;
@@ -261,6 +263,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
     ce = cudaMemcpyAsync(L->d_lists, lists.data(), lists.size() * sizeof(int), cudaMemcpyHostToDevice, s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L->d_n, 0, sizeof(unsigned long long), s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L->vac_part, 0, L->vac_bytes, s);
+  if (ce == cudaSuccess && L->rest) ce = cudaMemsetAsync(L->rest, 0, L->rest_bytes, s);
   // ring slots not yet written in a batch are multiplied by zero: keep them finite
   for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
     ce = cudaMemsetAsync(L->osum[b], 0, L->osum_bytes, s);
@@ -391,9 +394,14 @@ int hand_over(Engine* e, int buf, int nrec, bool defer_O, bool first) {
   if (e->pass == 2) {
     // replay: this buffer's field insertions times the final slab averages
     // straight into the products' partial sums
-    for (LatState* L : e->lats)
-      launch_replay_W(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, 1.0 / e->n_sub, L->partial,
+    for (LatState* L : e->lats) {
+      // the other slabs' products of the final averages, once per pass
+      if (first)
+        launch_products_rest(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, 1.0 / e->n_sub, L->rest,
+                             e->side);
+      launch_replay_W(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->rest, L->partial,
                       ProductTail{L->theta_rec[buf], L->osum[buf], nrec, 1, first ? 0 : 1}, e->side);
+    }
     ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
     return ML_OK;
   }
@@ -545,7 +553,7 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
         launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, nullptr, 1.0 / e->n_sub, L->partial,
-                        out[li], e->side, ProductTail{}, true);
+                        L->rest, out[li], e->side, ProductTail{}, true);
       }
       ncfg = e->n_sub;
     } else if (e->outer_slab == 0) {
@@ -557,7 +565,7 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
         launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
-                        out[li], e->side, ProductTail{L->theta_rec[tb], L->osum[tb], tn, tfirst ? 1 : 0});
+                        L->rest, out[li], e->side, ProductTail{L->theta_rec[tb], L->osum[tb], tn, tfirst ? 1 : 0});
       }
       ML_CUDA(cudaEventRecord(e->ev_fold[tb], e->side));  // the tail buffer is free after the products
       ncfg = e->n_sub;
@@ -577,7 +585,7 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
         launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, e->fp64, e->pairs, L->acc4T, L->acc4O,
-                        1.0 / e->n_sub_outer, L->partial, out[li], e->side);
+                        1.0 / e->n_sub_outer, L->partial, L->rest, out[li], e->side);
       }
       ncfg = e->n_sub * e->n_sub_outer;
     }
@@ -661,14 +669,14 @@ int part_measure_products(Engine* e, const double2* w_in, double2* w_out, double
   if (e->outer_slab == 0) {
     const int tb = e->part_tail_buf;
     launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
-                    rec, e->side,
+                    L->rest, rec, e->side,
                     ProductTail{L->theta_rec[tb], L->osum[tb], e->part_tail_nrec, e->part_tail_first ? 1 : 0}, false,
                     pr);
     ML_CUDA(cudaEventRecord(e->ev_fold[tb], e->side));  // the tail buffer is free after the products
     ncfg = e->n_sub;
   } else {
     launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, e->fp64, e->pairs, L->acc4T, L->acc4O,
-                    1.0 / e->n_sub_outer, L->partial, rec, e->side, ProductTail{}, false, pr);
+                    1.0 / e->n_sub_outer, L->partial, L->rest, rec, e->side, ProductTail{}, false, pr);
     ncfg = e->n_sub * e->n_sub_outer;
   }
   if (!w_out) launch_write_vac(L->vac_part, L->nparts, 1.0 / ncfg, L->meas, L->g, rec, e->side);
@@ -1226,11 +1234,13 @@ int ml_observe(ml_lattice* h, double* out_host, size_t out_len) {
   if (e->replay) {
     // no stored insertion sums: the products take the one record as their tail
     launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, buf, 1, e->stream, true, true);
-    launch_products(L->g, L->g.Nt / e->slab, m, e->fp64, e->pairs, L->accT, nullptr, 1.0, L->partial, out, e->stream,
+    launch_products(L->g, L->g.Nt / e->slab, m, e->fp64, e->pairs, L->accT, nullptr, 1.0, L->partial, L->rest, out,
+                    e->stream,
                     ProductTail{L->theta_rec[buf], L->osum[buf], 1, 1, 0});
   } else {
     launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, buf, 1, e->stream, false, true);
-    launch_products(L->g, L->g.Nt / e->slab, m, e->fp64, e->pairs, L->accT, L->accO, 1.0, L->partial, out, e->stream);
+    launch_products(L->g, L->g.Nt / e->slab, m, e->fp64, e->pairs, L->accT, L->accO, 1.0, L->partial, L->rest, out,
+                    e->stream);
   }
   launch_write_vac(L->vac_part, L->nparts, 1.0, m, L->g, out, e->stream);
   ML_CUDA(cudaGetLastError());
@@ -1376,11 +1386,11 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
         launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, 0, e->nB, e->stream);
         if (e->replay)
           for (LatState* Lr : e->lats)
-            launch_replay_W(Lr->g, Lr->g.Nt / e->slab, Lr->meas, e->fp64, e->pairs, Lr->accT, 1.0, Lr->partial,
+            launch_replay_W(Lr->g, Lr->g.Nt / e->slab, Lr->meas, e->fp64, e->pairs, Lr->rest, Lr->partial,
                             ProductTail{Lr->theta_rec[0], Lr->osum[0], e->nB, 1, 1}, e->stream);
         break;
       case ML_K_PRODUCTS:
-        launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0, L->partial, e->rec_buf,
+        launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0, L->partial, L->rest, e->rec_buf,
                         e->stream, ProductTail{}, e->replay);
         break;
       case ML_K_SWEEP:

@@ -21,30 +21,36 @@ __host__ __device__ __forceinline__ double exact_double(float f) {
   uint32_t u;
   memcpy(&u, &f, sizeof u);
 #endif
-  const uint32_t e = (u >> 23) & 0xFFu;
-  const uint32_t m = u & 0x7FFFFFu;
-  const uint64_t sign = static_cast<uint64_t>(u >> 31) << 63;
-  uint64_t bits;
-  if (e - 1u < 254u) {  // normal
-    bits = sign | (static_cast<uint64_t>(e + 896u) << 52) | (static_cast<uint64_t>(m) << 29);
-  } else if (e == 0u) {
-    if (m == 0u) {
-      bits = sign;  // signed zero
-    } else {        // subnormal: m 2^-149 with its top bit at position p
+  const uint32_t a = u & 0x7FFFFFFFu;
+  uint32_t hi, lo;
+  if (a - 0x00800000u < 0x7F000000u) {
+    // normal (biased exponent 1..254): the exponent and fraction move down
+    // three places as one field, which adds 1023 - 127 = 896 to the exponent
+    // when 896 << 20 is added; the fraction's low three bits start the low word
+    hi = ((a >> 3) + 0x38000000u) | (u & 0x80000000u);
+    lo = u << 29;
+  } else {
+    const uint32_t e = a >> 23, m = a & 0x7FFFFFu;
+    hi = u & 0x80000000u;
+    lo = 0u;
+    if (e == 0xFFu) {  // infinity or NaN: the fraction keeps its payload
+      hi |= 0x7FF00000u | (m >> 3);
+      lo = m << 29;
+    } else if (m != 0u) {  // subnormal: m 2^-149 with its top bit at position p
 #ifdef __CUDA_ARCH__
       const int p = 31 - __clz(static_cast<int>(m));
 #else
       const int p = 31 - __builtin_clz(m);
 #endif
-      bits = sign | (static_cast<uint64_t>(p + 874) << 52) |
-             ((static_cast<uint64_t>(m) << (52 - p)) & 0xFFFFFFFFFFFFFull);
-    }
-  } else {  // infinity or NaN
-    bits = sign | (0x7FFull << 52) | (static_cast<uint64_t>(m) << 29);
+      const uint64_t frac = (static_cast<uint64_t>(m) << (52 - p)) & 0xFFFFFFFFFFFFFull;
+      hi |= (static_cast<uint32_t>(p + 874) << 20) | static_cast<uint32_t>(frac >> 32);
+      lo = static_cast<uint32_t>(frac);
+    }  // else a signed zero
   }
 #ifdef __CUDA_ARCH__
-  return __longlong_as_double(static_cast<long long>(bits));
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
 #else
+  const uint64_t bits = (static_cast<uint64_t>(hi) << 32) | lo;
   double d;
   memcpy(&d, &bits, sizeof d);
   return d;

@@ -36,6 +36,8 @@ struct LatState {
   int nparts = 0;
   size_t vac_bytes = 0;
   double2* partial = nullptr;        // product partials (accumulation stream)
+  double2* rest = nullptr;           // other-slab products of the W products [nrf][nslab][Ns]
+  size_t rest_bytes = 0;
   double2* partial_naive = nullptr;  // naive / plaquette partials (accumulation stream)
   void* naive_theta = nullptr;       // the configuration the naive correlator and plaquette read
   double* staging = nullptr;         // canonical angles for get / set

@@ -177,15 +177,20 @@ struct ProductRange {
 };
 // cross-slab products of the averages sum / n, in double precision, reduced
 // over x into the record's P, Pf and W blocks (fp64: the lattice's precision;
-// pairs: as for launch_fold_table)
+// pairs: as for launch_fold_table); rest: the table of the other slabs'
+// products [nrf][nslab][Ns] the W products read (written here)
 void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
-                     const void* accO, double inv_n, double2* partial, double* rec, cudaStream_t s,
+                     const void* accO, double inv_n, double2* partial, double2* rest, double* rec, cudaStream_t s,
                      const ProductTail& tail = {}, bool W_done = false, const ProductRange& pr = {});
+// the table rest alone (the replay's insertions need it before the products)
+void launch_products_rest(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
+                          double inv_n, double2* rest, cudaStream_t s);
 // replay: the W partials of one ring buffer's records (tail.nrec of them)
-// times the final slab averages, stored (tail.add = 0) or added to the stored
-// partials; W_done in the final launch_products then only adds P and finalises
-void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
-                     double inv_n, double2* partial, const ProductTail& tail, cudaStream_t s);
+// times the final slab averages (the table rest), stored (tail.add = 0) or
+// added to the stored partials, unscaled; W_done in the final launch_products
+// then only adds P and finalises with the 1/n of the sums
+void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const double2* rest,
+                     double2* partial, const ProductTail& tail, cudaStream_t s);
 // naive P+P and mean plaquette of the current configuration
 void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,
                                 double* rec, cudaStream_t s);

@@ -593,133 +593,157 @@ __global__ void __launch_bounds__(256) k_combine(Geom g, int n_outer, int q, Mea
 //   o in [nr+nrf, ...)      W(f, j)   = sum_x sum_s [TO]_s(x, f, j) R_s(x, f),
 //                           R_s = prod_{s' != s} [T]_{s'} (prefix x suffix),
 //                           j = (b * nc + ci) * 2 + k
-// k_products_P: grid (sites, nr + nrf); k_products_W: grid (sites, nrf,
-// chunks of kWChunk values of j).  All in double precision: every [T] factor
-// is the average sum / n (scaled as it is read, so no product of many slabs
-// over- or underflows), [TO] is scaled by 1/n once at the end.
+// k_products_P: grid (sites, outputs from o0), and for the field separations
+// the table R[f][s][x] the W products read; k_products_W: grid (sites /
+// kWSites, nrf, chunks of kWChunk values of j).  All in double precision:
+// every [T] factor is the average sum / n (scaled as it is read, so no
+// product of many slabs over- or underflows); the [TO] sums enter unscaled
+// and the finalisation applies their 1/n with the site average.
 // ---------------------------------------------------------------------------
-constexpr int kWChunk = 6;         // values of j per thread
-constexpr int kProdMinBlocks = 3;  // launch bound of the products without a tail: blocks per SM
+constexpr int kWChunk = 4;         // values of j per thread
+constexpr int kWSites = 4;         // sites per thread, summed before the warp reduction
 
 template <typename A>
 __global__ void __launch_bounds__(256) k_products_P(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT,
-                                                    double inv_n, double2* __restrict__ partial, int nwarps) {
+                                                    double inv_n, double2* __restrict__ partial, int nwarps, int o0,
+                                                    double2* __restrict__ rest) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = x < g.Ns;
-  const int o = blockIdx.y;
-  const int a = o < m.nr ? m.r_idx[o] : m.rf_idx[o - m.nr];
+  const int o = o0 + blockIdx.y;
+  const bool field = o >= m.nr;
+  const int a = field ? m.rf_idx[o - m.nr] : m.r_idx[o];
   double2 prod = make_double2(live ? 1.0 : 0.0, 0.0);
-  if (live)
-    for (int s = 0; s < nslab; ++s)
-      prod = cmul(prod, cscale(acc_value(accT[(static_cast<size_t>(s) * m.nR + a) * g.Ns + x]), inv_n));
+  if (live) {
+    const A* col = accT + static_cast<size_t>(a) * g.Ns + x;
+    const size_t tstride = static_cast<size_t>(m.nR) * g.Ns;  // slab stride of accT
+    if (field && rest) {
+      // R_s = (prod_{s' < s}) x (prod_{s' > s}): the suffixes go into the
+      // table first, from the top slab down, then each is multiplied by the
+      // running prefix, which ends as the full product
+      double2* rcol = rest + static_cast<size_t>(o - m.nr) * nslab * g.Ns + x;
+      double2 suf = make_double2(1.0, 0.0);
+      for (int s = nslab - 1; s >= 0; --s) {
+        rcol[static_cast<size_t>(s) * g.Ns] = suf;
+        suf = cmul(suf, cscale(acc_value(col[s * tstride]), inv_n));
+      }
+      for (int s = 0; s < nslab; ++s) {
+        double2* r = rcol + static_cast<size_t>(s) * g.Ns;
+        *r = cmul(prod, *r);
+        prod = cmul(prod, cscale(acc_value(col[s * tstride]), inv_n));
+      }
+    } else {
+      for (int s = 0; s < nslab; ++s) prod = cmul(prod, cscale(acc_value(col[s * tstride]), inv_n));
+    }
+  }
+  if (!partial) return;  // the table alone (uniform over the grid)
   prod = warp_sum(prod);
   if ((threadIdx.x & 31) == 0) partial[static_cast<size_t>(o) * nwarps + (x >> 5)] = prod;
 }
 
-// One thread: site x, field separation f, kWChunk values of j.  Suffix
-// products are formed once from the top slab down; the loop over slabs then
-// keeps the prefix product running and reads the kWChunk [TO] sums of each
-// slab together.  With TAIL, the [TO] sums first take in the last nrec
-// records of ring buffer (trec, osum) exactly as k_accum_O_table would have
-// (same batch sum, same accumulator update), without writing them back: the
-// measurement's final fold of the field insertions and the products in one
-// pass over the slab sums.  T: the records' type; A: the slab sums' type.
+// One thread: kWSites sites x (a grid stride apart, so a warp reads
+// consecutive sites), field separation f, kWChunk values of j.  Per site the
+// sum over slabs is formed completely (from w_in, in slab order) before it
+// is added to the thread's sum over its sites, so a time-slab partition,
+// which carries the per-site sums from process to process, adds the same
+// terms in the same order.  With TAIL, the [TO] sums first take in the last
+// nrec records of ring buffer (trec, osum) exactly as k_accum_O_table would
+// have (same batch sum, same accumulator update), without writing them back:
+// the measurement's final fold of the field insertions and the products in
+// one pass over the slab sums.  T: the records' type; A: the slab sums' type.
 // TB: 0 without a tail, else the ring slots read (nrec rounded up to 4, 8 or
 // 16; the slots beyond nrec add exact zeros, so fewer of them leave every sum
-// unchanged).
+// unchanged).  partial rows are nwarps apart; this kernel writes the first
+// gridDim.x * blockDim.x / 32 of each.
 template <typename T, typename A, int TB>
-__global__ void __launch_bounds__(256, TB == 0 ? kProdMinBlocks : 2)
-    k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accT, const A* __restrict__ accO,
-                 double inv_n, double2* __restrict__ partial, int nwarps, ProductTail tail, ProductRange pr) {
+__global__ void __launch_bounds__(256, 2)
+    k_products_W(Geom g, int nslab, MeasLayout m, const A* __restrict__ accO, const double2* __restrict__ rest,
+                 double2* __restrict__ partial, int nwarps, ProductTail tail, ProductRange pr) {
   constexpr bool TAIL = TB > 0;
   constexpr int B = TAIL ? TB : 1;
   static_assert(B <= RecBatch<T>::n, "a tail holds at most one ring buffer");
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = x < g.Ns;
+  const int xt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nthr = gridDim.x * blockDim.x;
   const int f = blockIdx.y;
   const int nW = m.np * m.nc * 2;
   const int j0 = blockIdx.z * kWChunk;
   const int nj = min(nW - j0, kWChunk);
-  double2 sum[kWChunk];
-#pragma unroll
-  for (int q = 0; q < kWChunk; ++q)
-    sum[q] = (pr.w_in && live && q < nj) ? pr.w_in[static_cast<size_t>(f * nW + j0 + q) * g.Ns + x]
-                                         : make_double2(0.0, 0.0);
-  if (live) {
-    const size_t tstride = static_cast<size_t>(m.nR) * g.Ns;  // slab stride of accT
-    const A* tcol = accT + static_cast<size_t>(m.rf_idx[f]) * g.Ns + x;
-    double2 suf[kMaxSlabs];  // suf[s] = prod_{s' > s} [T]_{s'}
-    double2 run = make_double2(1.0, 0.0);
-    for (int s = nslab - 1; s >= 0; --s) {
-      suf[s] = run;
-      run = cmul(run, cscale(acc_value(tcol[s * tstride]), inv_n));
-    }
-    // tail: the partner site x + rf of the phases, and per value q its
-    // insertion site x0 (probe b) and osum row (ci, k) within a slab, all
-    // independent of the slab
-    int xr = 0, x0q[kWChunk], rowq[kWChunk];
-    if constexpr (TAIL) {
-      int cx, cy, cz;
-      spatial_coords(g, x, &cx, &cy, &cz);
-      xr = wrapc(cx + m.rf[f], g.L) + g.L * (cy + g.L * cz);
-      const int x0x = wrapc(cx + m.rf[f] / 2, g.L);
-#pragma unroll
-      for (int q = 0; q < kWChunk; ++q) {
-        const int j = min(j0 + q, nW - 1), b = j / (2 * m.nc);
-        rowq[q] = j - b * (2 * m.nc);  // ci * 2 + k
-        x0q[q] = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
-      }
-    }
-    run = make_double2(1.0, 0.0);  // prod_{s' < s} [T]_{s'}
-    for (int s = 0; s < nslab; ++s) {
-      if (s < pr.s_lo || s >= pr.s_hi) {  // another process's slab: its insertions are not here
-        run = cmul(run, cscale(acc_value(tcol[s * tstride]), inv_n));
-        continue;
-      }
-      const double2 rest = cmul(run, suf[s]);
-      const bool fresh = TAIL && tail.overwrite;  // no stored sums (replay: accO is null)
-      const A* ocol = fresh ? nullptr : accO + (static_cast<size_t>(s * m.nrf + f) * nW + j0) * g.Ns + x;
-      A o[kWChunk];
-#pragma unroll
-      for (int q = 0; q < kWChunk; ++q)
-        if (q < nj) o[q] = fresh ? A{} : __ldcs(ocol + static_cast<size_t>(q) * g.Ns);
-      if constexpr (TAIL) {
-        const T* trec = static_cast<const T*>(tail.trec);
-        const T* osum = static_cast<const T*>(tail.osum);
-        T er[B], ei[B];
-        batch_phases<T, B>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, tail.nrec, er, ei);
-#pragma unroll
-        for (int q = 0; q < kWChunk; ++q) {
-          if (q >= nj) break;
-          T ov[B];
-          load_batch<T, B>(osum + rec_index(g, static_cast<size_t>(s * m.nc) * 2 + rowq[q], x0q[q], 0), g.Ns, ov);
-          T sr = T(0), si = T(0);
-#pragma unroll
-          for (int r = 0; r < B; ++r) {
-            sr += er[r] * ov[r];
-            si += ei[r] * ov[r];
-          }
-          acc_add(o[q], sr, si);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kWChunk; ++q)
-        if (q < nj) sum[q] = cmac(sum[q], acc_value(o[q]), rest);
-      run = cmul(run, cscale(acc_value(tcol[s * tstride]), inv_n));
-    }
-  }
-  if (pr.w_out) {  // the per-site sums go on to the process holding the next slabs
+  const double2* rtab = rest + static_cast<size_t>(f) * nslab * g.Ns;
+  double2 tot[kWChunk];
+#pragma unroll 1
+  for (int i = 0; i < kWSites; ++i) {
+    const int x = xt + i * nthr;
+    const bool live = x < g.Ns;
+    double2 sum[kWChunk];
 #pragma unroll
     for (int q = 0; q < kWChunk; ++q)
-      if (q < nj && live) pr.w_out[static_cast<size_t>(f * nW + j0 + q) * g.Ns + x] = sum[q];
-    return;
+      sum[q] = (pr.w_in && live && q < nj) ? pr.w_in[static_cast<size_t>(f * nW + j0 + q) * g.Ns + x]
+                                           : make_double2(0.0, 0.0);
+    if (live) {
+      // tail: the partner site x + rf of the phases, and per value q its
+      // insertion site x0 (probe b) and osum row (ci, k) within a slab, all
+      // independent of the slab
+      int xr = 0, x0q[kWChunk], rowq[kWChunk];
+      if constexpr (TAIL) {
+        int cx, cy, cz;
+        spatial_coords(g, x, &cx, &cy, &cz);
+        xr = wrapc(cx + m.rf[f], g.L) + g.L * (cy + g.L * cz);
+        const int x0x = wrapc(cx + m.rf[f] / 2, g.L);
+#pragma unroll
+        for (int q = 0; q < kWChunk; ++q) {
+          const int j = min(j0 + q, nW - 1), b = j / (2 * m.nc);
+          rowq[q] = j - b * (2 * m.nc);  // ci * 2 + k
+          x0q[q] = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
+        }
+      }
+      // slabs of another process: their insertions are not here
+      for (int s = pr.s_lo; s < pr.s_hi; ++s) {
+        const double2 R = rtab[static_cast<size_t>(s) * g.Ns + x];
+        const bool fresh = TAIL && tail.overwrite;  // no stored sums (replay: accO is null)
+        const A* ocol = fresh ? nullptr : accO + (static_cast<size_t>(s * m.nrf + f) * nW + j0) * g.Ns + x;
+        A o[kWChunk];
+#pragma unroll
+        for (int q = 0; q < kWChunk; ++q)
+          if (q < nj) o[q] = fresh ? A{} : __ldcs(ocol + static_cast<size_t>(q) * g.Ns);
+        if constexpr (TAIL) {
+          const T* trec = static_cast<const T*>(tail.trec);
+          const T* osum = static_cast<const T*>(tail.osum);
+          T er[B], ei[B];
+          batch_phases<T, B>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, tail.nrec, er, ei);
+#pragma unroll
+          for (int q = 0; q < kWChunk; ++q) {
+            if (q >= nj) break;
+            T ov[B];
+            load_batch<T, B>(osum + rec_index(g, static_cast<size_t>(s * m.nc) * 2 + rowq[q], x0q[q], 0), g.Ns, ov);
+            T sr = T(0), si = T(0);
+#pragma unroll
+            for (int r = 0; r < B; ++r) {
+              sr += er[r] * ov[r];
+              si += ei[r] * ov[r];
+            }
+            acc_add(o[q], sr, si);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kWChunk; ++q)
+          if (q < nj) sum[q] = cmac(sum[q], acc_value(o[q]), R);
+      }
+    }
+    if (pr.w_out) {  // the per-site sums go on to the process holding the next slabs
+#pragma unroll
+      for (int q = 0; q < kWChunk; ++q)
+        if (q < nj && live) pr.w_out[static_cast<size_t>(f * nW + j0 + q) * g.Ns + x] = sum[q];
+      continue;
+    }
+#pragma unroll
+    for (int q = 0; q < kWChunk; ++q) tot[q] = i == 0 ? sum[q] : cadd(tot[q], sum[q]);
   }
+  if (pr.w_out) return;
 #pragma unroll
   for (int q = 0; q < kWChunk; ++q) {
     if (q >= nj) break;
-    const double2 w = warp_sum(cscale(sum[q], inv_n));
+    const double2 w = warp_sum(tot[q]);
     if ((threadIdx.x & 31) == 0) {
-      double2* p = partial + static_cast<size_t>(m.nr + m.nrf + f * nW + j0 + q) * nwarps + (x >> 5);
+      double2* p = partial + static_cast<size_t>(m.nr + m.nrf + f * nW + j0 + q) * nwarps + (xt >> 5);
       *p = (TAIL && tail.add) ? cadd(*p, w) : w;
     }
   }
@@ -727,14 +751,18 @@ __global__ void __launch_bounds__(256, TB == 0 ? kProdMinBlocks : 2)
 
 // Fixed-order sum of the warp partials of each output into the record: one
 // warp per output, lane l adding partials l, l + 32, ..., then a shuffle tree.
-__global__ void __launch_bounds__(256) k_finalize_products(const double2* __restrict__ partial, int nwarps, Geom g,
-                                                           MeasLayout m, double* __restrict__ rec) {
+// nwarps: the row stride and P's warp count; nwarps_w: W's; w_inv_n: the 1/n
+// of the [TO] sums.
+__global__ void __launch_bounds__(256) k_finalize_products(const double2* __restrict__ partial, int nwarps,
+                                                           int nwarps_w, double w_inv_n, Geom g, MeasLayout m,
+                                                           double* __restrict__ rec) {
   const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int nW = m.np * m.nc * 2;
   const int nout = m.nr + m.nrf + m.nrf * nW;
   if (o >= nout) return;  // whole warp
+  const int nw = o < m.nr + m.nrf ? nwarps : nwarps_w;
   double2 s = make_double2(0.0, 0.0);
-  for (int w = lane; w < nwarps; w += 32) s = cadd(s, partial[static_cast<size_t>(o) * nwarps + w]);
+  for (int w = lane; w < nw; w += 32) s = cadd(s, partial[static_cast<size_t>(o) * nwarps + w]);
   s = warp_sum(s);
   if (lane != 0) return;
   size_t off;
@@ -750,7 +778,7 @@ __global__ void __launch_bounds__(256) k_finalize_products(const double2* __rest
     const int f = q / nW, j = q - f * nW;
     const int b = j / (m.nc * 2), ci = (j / 2) % m.nc, k = j & 1;
     off = m.off_W + ((((static_cast<size_t>(f) * m.np + b) * 6 + m.comp[ci]) * 2 + k) * 2);
-    scale = 1.0 / (static_cast<double>(g.Ns) * g.Nt);
+    scale = w_inv_n / (static_cast<double>(g.Ns) * g.Nt);
   }
   rec[off] = s.x * scale;
   rec[off + 1] = s.y * scale;
@@ -980,63 +1008,76 @@ void launch_combine(const Geom& g, int n_outer, int q, const MeasLayout& m, bool
 
 // k_products_W with the tail's slot count
 template <typename T, typename A>
-static void launch_products_W(dim3 grid, const Geom& g, int nslab, const MeasLayout& m, const A* accT, const A* accO,
-                              double inv_n, double2* partial, int nwarps, const ProductTail& tail, cudaStream_t s,
+static void launch_products_W(const Geom& g, int nslab, const MeasLayout& m, const A* accO, const double2* rest,
+                              double2* partial, int nwarps, const ProductTail& tail, cudaStream_t s,
                               ProductRange pr = {}) {
   if (pr.s_hi < 0) pr.s_hi = nslab;
+  const int nW = m.np * m.nc * 2;
+  const dim3 grid(blocks_for(blocks_for(g.Ns, kWSites), 256), m.nrf, (nW + kWChunk - 1) / kWChunk);
   if (tail.nrec <= 0)
-    k_products_W<T, A, 0><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail, pr);
+    k_products_W<T, A, 0><<<grid, 256, 0, s>>>(g, nslab, m, accO, rest, partial, nwarps, tail, pr);
   else if (tail.nrec <= 4)
-    k_products_W<T, A, 4><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail, pr);
+    k_products_W<T, A, 4><<<grid, 256, 0, s>>>(g, nslab, m, accO, rest, partial, nwarps, tail, pr);
   else if (tail.nrec <= 8)
-    k_products_W<T, A, 8><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail, pr);
+    k_products_W<T, A, 8><<<grid, 256, 0, s>>>(g, nslab, m, accO, rest, partial, nwarps, tail, pr);
   else
-    k_products_W<T, A, RecBatch<T>::n><<<grid, 256, 0, s>>>(g, nslab, m, accT, accO, inv_n, partial, nwarps, tail,
-                                                            pr);
+    k_products_W<T, A, RecBatch<T>::n><<<grid, 256, 0, s>>>(g, nslab, m, accO, rest, partial, nwarps, tail, pr);
+  count_launches(1);
+}
+
+// warps of the W products' partials (per output row)
+static int w_warps(const Geom& g) { return blocks_for(blocks_for(g.Ns, kWSites), 256) * 8; }
+
+void launch_products_rest(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
+                          double inv_n, double2* rest, cudaStream_t s) {
+  if (m.nrf == 0) return;
+  with_sum_types(fp64, pairs, [&](auto, auto a) {
+    using A = decltype(a);
+    k_products_P<A><<<dim3(blocks_for(g.Ns, 256), m.nrf), 256, 0, s>>>(g, nslab, m, static_cast<const A*>(accT),
+                                                                        inv_n, nullptr, 0, m.nr, rest);
+  });
+  count_launches(1);
 }
 
 void launch_products(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
-                     const void* accO, double inv_n, double2* partial, double* rec, cudaStream_t s,
+                     const void* accO, double inv_n, double2* partial, double2* rest, double* rec, cudaStream_t s,
                      const ProductTail& tail, bool W_done, const ProductRange& pr) {
   const int nb = blocks_for(g.Ns, 256);
   const int nwarps = nb * 8;
   const int nW = m.np * m.nc * 2;
+  const bool W = m.nrf > 0 && nW > 0 && !W_done;
   with_sum_types(fp64, pairs, [&](auto t, auto a) {
     using T = decltype(t);
     using A = decltype(a);
     if (!pr.w_out) {
+      // P and Pf, and for the W products the table of other-slab products
       k_products_P<A><<<dim3(nb, m.nr + m.nrf), 256, 0, s>>>(g, nslab, m, static_cast<const A*>(accT), inv_n,
-                                                             partial, nwarps);
+                                                             partial, nwarps, 0, W ? rest : nullptr);
       count_launches(1);
+    } else if (W) {
+      launch_products_rest(g, nslab, m, fp64, pairs, accT, inv_n, rest, s);
     }
-    if (m.nrf > 0 && nW > 0 && !W_done) {
-      const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
-      launch_products_W<T, A>(grid, g, nslab, m, static_cast<const A*>(accT), static_cast<const A*>(accO), inv_n,
-                              partial, nwarps, tail, s, pr);
-      count_launches(1);
-    }
+    if (W)
+      launch_products_W<T, A>(g, nslab, m, static_cast<const A*>(accO), rest, partial, nwarps, tail, s, pr);
   });
   if (pr.w_out) return;  // per-site sums only: the process holding the last slabs finishes the record
   const int nout = m.nr + m.nrf + m.nrf * nW;
-  k_finalize_products<<<blocks_for(32ll * nout, 256), 256, 0, s>>>(partial, nwarps, g, m, rec);
+  k_finalize_products<<<blocks_for(32ll * nout, 256), 256, 0, s>>>(partial, nwarps, w_warps(g), inv_n, g, m, rec);
   count_launches(1);
 }
 
-void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const void* accT,
-                     double inv_n, double2* partial, const ProductTail& tail, cudaStream_t s) {
+void launch_replay_W(const Geom& g, int nslab, const MeasLayout& m, bool fp64, bool pairs, const double2* rest,
+                     double2* partial, const ProductTail& tail, cudaStream_t s) {
   const int nW = m.np * m.nc * 2;
   if (m.nrf == 0 || nW == 0 || tail.nrec <= 0) return;
-  const int nb = blocks_for(g.Ns, 256);
-  const dim3 grid(nb, m.nrf, (nW + kWChunk - 1) / kWChunk);
   ProductTail tl = tail;
   tl.overwrite = 1;  // this buffer's records alone
   with_sum_types(fp64, pairs, [&](auto t, auto a) {
     using T = decltype(t);
     using A = decltype(a);
-    launch_products_W<T, A>(grid, g, nslab, m, static_cast<const A*>(accT), static_cast<const A*>(nullptr), inv_n,
-                            partial, nb * 8, tl, s);
+    launch_products_W<T, A>(g, nslab, m, static_cast<const A*>(nullptr), rest, partial, blocks_for(g.Ns, 256) * 8,
+                            tl, s);
   });
-  count_launches(1);
 }
 
 void launch_naive_and_plaquette(bool fp64, const void* theta, const Geom& g, const MeasLayout& m, double2* partial,

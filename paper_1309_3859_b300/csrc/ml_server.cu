@@ -218,11 +218,11 @@ void end_of_measurement(Job* j) {
   int ncfg;
   if (j->p.outer_slab) {
     launch_products(L->g, L->g.Nt / j->p.outer_slab, L->meas, e->fp64, e->pairs, L->acc4T, L->acc4O,
-                    1.0 / j->p.n_sub_outer, L->partial, out, e->stream);
+                    1.0 / j->p.n_sub_outer, L->partial, L->rest, out, e->stream);
     ncfg = j->p.n_sub * j->p.n_sub_outer;
   } else {
     launch_products(L->g, L->g.Nt / j->p.slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0 / j->p.n_sub, L->partial,
-                    out, e->stream);
+                    L->rest, out, e->stream);
     ncfg = j->p.n_sub;
   }
   launch_write_vac(L->vac_part, L->nparts, 1.0 / ncfg, L->meas, L->g, out, e->stream);
