@@ -49,14 +49,40 @@ __device__ __forceinline__ double2 unit_phase(double phi) {
 //                                    (FP32: summed in single precision and
 //                                    reduced to [-pi, pi); slab_phase_sum)
 //   osum[s][ci][k][slots][x]         sum_{t in slab} (Re, Im) P_c(x, t)
-// A site's batch: the slots at p, p + Ns, p + 2 Ns, ... (p = rec_index(.., 0)),
-// each load coalesced over a warp's consecutive sites.
+// A site's batch: NB / G 16-byte vectors at p, p + G Ns, p + 2 G Ns, ...
+// (p = rec_index<T>(.., 0)), each load coalesced over a warp's consecutive sites.
 // ---------------------------------------------------------------------------
-// (the first NB slots: a batch known to hold fewer records loads fewer)
+template <typename T>
+struct Vec16;  // the 16-byte vector of G record slots
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+// (the first NB slots, a multiple of G: a batch known to hold fewer records
+// loads fewer)
 template <typename T, int NB = RecBatch<T>::n>
-__device__ __forceinline__ void load_batch(const T* __restrict__ p, int stride, T v[NB]) {
+__device__ __forceinline__ void load_batch(const T* __restrict__ p, int ns, T v[NB]) {
+  using V = typename Vec16<T>::type;
+  constexpr int G = 16 / static_cast<int>(sizeof(T));
+  static_assert(NB % G == 0, "whole 16-byte groups of slots");
+  const V* q = reinterpret_cast<const V*>(p);
 #pragma unroll
-  for (int j = 0; j < NB; ++j) v[j] = __ldg(p + static_cast<size_t>(j) * stride);
+  for (int k = 0; k < NB / G; ++k) {
+    const V a = __ldg(q + static_cast<size_t>(k) * ns);
+    if constexpr (G == 4) {
+      v[4 * k] = a.x;
+      v[4 * k + 1] = a.y;
+      v[4 * k + 2] = a.z;
+      v[4 * k + 3] = a.w;
+    } else {
+      v[2 * k] = a.x;
+      v[2 * k + 1] = a.y;
+    }
+  }
 }
 
 // Record of each lattice's configuration into ring slot `slot` of buffer
@@ -143,7 +169,7 @@ __global__ void __launch_bounds__(256) k_vac_partial_table(const LatDesc* __rest
   const T* osum = static_cast<const T*>(L.osum[buf]);
   double v = 0.0;
   for (int x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
-    const T* o = osum + rec_index(L.g, static_cast<size_t>((sl * L.m.nc + ci) * 2 + k), x, 0);
+    const T* o = osum + rec_index<T>(L.g, static_cast<size_t>((sl * L.m.nc + ci) * 2 + k), x, 0);
     T a[B];
     load_batch<T>(o, L.g.Ns, a);
     T t = T(0);
@@ -240,6 +266,42 @@ __device__ __forceinline__ void batch_phases(const T* __restrict__ rec_x, const 
   }
 }
 
+// The batch sum of a field insertion, sum_j e^{i phi_j} o_j over NB slots,
+// in the records' precision.  Every kernel that forms it (the folds and the
+// products' tail) calls this, so they agree bit for bit.
+template <typename T, int NB>
+__device__ __forceinline__ void batch_dot(const T er[NB], const T ei[NB], const T o[NB], T& sr, T& si) {
+  sr = T(0);
+  si = T(0);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    sr += er[j] * o[j];
+    si += ei[j] * o[j];
+  }
+}
+
+// a site's batch from a shared-memory tile laid out as the ring ([group][..]
+// cells of 16 bytes, `cells` apart between groups)
+template <typename T, int NB = RecBatch<T>::n>
+__device__ __forceinline__ void tile_batch(const T* p, int cells, T v[NB]) {
+  using V = typename Vec16<T>::type;
+  constexpr int G = 16 / static_cast<int>(sizeof(T));
+  const V* q = reinterpret_cast<const V*>(p);
+#pragma unroll
+  for (int k = 0; k < NB / G; ++k) {
+    const V a = q[static_cast<size_t>(k) * cells];
+    if constexpr (G == 4) {
+      v[4 * k] = a.x;
+      v[4 * k + 1] = a.y;
+      v[4 * k + 2] = a.z;
+      v[4 * k + 3] = a.w;
+    } else {
+      v[2 * k] = a.x;
+      v[2 * k + 1] = a.y;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Fold of nrec <= slots records into the slab sums (type A); with
 // `overwrite` the sums start from zero (the first fold of an inner loop), so
@@ -288,7 +350,7 @@ __global__ void __launch_bounds__(256) k_accum_T_table(const LatDesc* __restrict
     }
   } else {
     const T* rec = static_cast<const T*>(L.theta_rec[buf]);
-    batch_phases<T>(rec + rec_index(g, s, x, 0), rec + rec_index(g, s, xr, 0), g.Ns, nrec, er, ei);
+    batch_phases<T>(rec + rec_index<T>(g, s, x, 0), rec + rec_index<T>(g, s, xr, 0), g.Ns, nrec, er, ei);
   }
   T sr = T(0), si = T(0);
 #pragma unroll
@@ -339,7 +401,7 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
   const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
   A* __restrict__ acc = reinterpret_cast<A*>(L.accO);
   T er[B], ei[B];
-  batch_phases<T>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, nrec, er, ei);
+  batch_phases<T>(trec + rec_index<T>(g, s, x, 0), trec + rec_index<T>(g, s, xr, 0), g.Ns, nrec, er, ei);
   const int x0x = wrapc(cx + rf / 2, g.L);
   const int nck = 2 * m.nc;
   const int b_end = min(m.np, (bg + 1) * kProbesPerThread);
@@ -359,13 +421,9 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
         if (q >= nck) break;
         const int ci = q >> 1, k = q & 1;
         T o[B];
-        load_batch<T>(osum + rec_index(g, static_cast<size_t>(s * m.nc + ci) * 2 + k, x0, 0), g.Ns, o);
-        T sr = T(0), si = T(0);
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-          sr += er[j] * o[j];
-          si += ei[j] * o[j];
-        }
+        load_batch<T>(osum + rec_index<T>(g, static_cast<size_t>(s * m.nc + ci) * 2 + k, x0, 0), g.Ns, o);
+        T sr, si;
+        batch_dot<T, B>(er, ei, o, sr, si);
         acc_add(a[i], sr, si);
       }
 #pragma unroll
@@ -459,19 +517,19 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
   const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
   A* __restrict__ acc = reinterpret_cast<A*>(L.accO);
   T er[B], ei[B];
-  batch_phases<T>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, nrec, er, ei);
+  batch_phases<T>(trec + rec_index<T>(g, s, x, 0), trec + rec_index<T>(g, s, xr, 0), g.Ns, nrec, er, ei);
   const int col = wrapc(xx + rf / 2, g.L);
-  const int row_chunks = g.L / CH;                    // 16-byte chunks of an x row (L a multiple of CH)
-  const int copies = B * trows * row_chunks;          // per component
+  constexpr int NG = B / CH;                          // 16-byte cells of a site's batch
+  const int copies = NG * trows * g.L;                // per component
   for (int q = 0; q < nck; ++q) {
     const size_t rowck = static_cast<size_t>(s * m.nc + (q >> 1)) * 2 + (q & 1);
-    for (int c = tid; c < copies; c += blockDim.x) {  // chunk c: slot j, tile row r, chunk u of the row
-      const int u = c % row_chunks, jr = c / row_chunks;
-      const int r = jr % trows, j = jr / trows;
+    for (int c = tid; c < copies; c += blockDim.x) {  // cell c: slot group k, tile row r, site u of the row
+      const int u = c % g.L, kr = c / g.L;
+      const int r = kr % trows, k = kr / trows;
       const int tz = r / tyn, ty = r - tz * tyn;
       const int yg = wrapc(y0 + pb.dymin + ty, g.L), zg = wrapc(z0 + pb.dzmin + tz, g.L);
-      cp_async16(tile + (static_cast<size_t>(j) * trows + r) * g.L + u * CH,
-                 osum + rec_index(g, rowck, g.L * (yg + g.L * zg), j) + u * CH);
+      cp_async16(tile + ((static_cast<size_t>(k) * trows + r) * g.L + u) * CH,
+                 osum + rec_index<T>(g, rowck, u + g.L * (yg + g.L * zg), k * CH));
     }
     cp_async_commit();
     cp_async_wait_all();
@@ -489,15 +547,10 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
           const int b = b0 + i;
           if (b >= m.np) break;
           const int r = (yy + m.pdy[b] - pb.dymin) + tyn * (m.pdz[b] - pb.dzmin);
-          const T* o_s = tile + static_cast<size_t>(r) * g.L + col;
-          const size_t jstride = static_cast<size_t>(trows) * g.L;
-          T sr = T(0), si = T(0);
-#pragma unroll
-          for (int j = 0; j < B; ++j) {
-            const T o = o_s[j * jstride];
-            sr += er[j] * o;
-            si += ei[j] * o;
-          }
+          T o[B];
+          tile_batch<T>(tile + (static_cast<size_t>(r) * g.L + col) * CH, trows * g.L, o);
+          T sr, si;
+          batch_dot<T, B>(er, ei, o, sr, si);
           acc_add(a[i], sr, si);
         }
 #pragma unroll
@@ -511,8 +564,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
 }
 
 // Tile plan of a lattice for k_accum_O_tile: false when it does not apply
-// (L above the block or not a whole number of 16-byte chunks of a row, or a
-// tile above kTileSmemMax).
+// (L above the block, or a tile above kTileSmemMax).
 bool fold_tile_plan(bool fp64, int L, const int* pdy, const int* pdz, int np, int* blocks_x, size_t* smem) {
   if (np <= 0) {
     *blocks_x = 0;
@@ -520,7 +572,7 @@ bool fold_tile_plan(bool fp64, int L, const int* pdy, const int* pdz, int np, in
     return true;
   }
   const int tsz = fp64 ? 8 : 4;
-  if (L > kTileThreads || (L * tsz) % 16 != 0) return false;
+  if (L > kTileThreads) return false;
   const ProbeBox pb = probe_box(pdy, pdz, np);
   const size_t bytes = static_cast<size_t>(RecBatch<float>::n) * tile_rows(L, pb) * L * tsz;
   if (bytes > kTileSmemMax) return false;
@@ -708,18 +760,14 @@ __global__ void __launch_bounds__(256, 2)
           const T* trec = static_cast<const T*>(tail.trec);
           const T* osum = static_cast<const T*>(tail.osum);
           T er[B], ei[B];
-          batch_phases<T, B>(trec + rec_index(g, s, x, 0), trec + rec_index(g, s, xr, 0), g.Ns, tail.nrec, er, ei);
+          batch_phases<T, B>(trec + rec_index<T>(g, s, x, 0), trec + rec_index<T>(g, s, xr, 0), g.Ns, tail.nrec, er, ei);
 #pragma unroll
           for (int q = 0; q < kWChunk; ++q) {
             if (q >= nj) break;
             T ov[B];
-            load_batch<T, B>(osum + rec_index(g, static_cast<size_t>(s * m.nc) * 2 + rowq[q], x0q[q], 0), g.Ns, ov);
-            T sr = T(0), si = T(0);
-#pragma unroll
-            for (int r = 0; r < B; ++r) {
-              sr += er[r] * ov[r];
-              si += ei[r] * ov[r];
-            }
+            load_batch<T, B>(osum + rec_index<T>(g, static_cast<size_t>(s * m.nc) * 2 + rowq[q], x0q[q], 0), g.Ns, ov);
+            T sr, si;
+            batch_dot<T, B>(er, ei, ov, sr, si);
             acc_add(o[q], sr, si);
           }
         }

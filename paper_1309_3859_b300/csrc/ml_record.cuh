@@ -97,19 +97,24 @@ __device__ __forceinline__ void temporal_staples(const T* th, const Geom& g, con
   v[5] = th[soa(g, nu, shifted(g, c, nu, -1, 0, 0), op)];
 }
 
-// Ring of sub-update records, slot-major: row r of a ring buffer (a slab of
-// theta_rec, a (slab, component, Re/Im) of osum, a (slab, part) of mh_rec)
-// holds its RecBatch::n slots one after another, each a run of Ns sites, so
-// the record of one sub-update is written by consecutive threads at
-// consecutive addresses and a site's batch is read with stride Ns.
+// Ring of sub-update records: row r of a ring buffer (a slab of theta_rec,
+// a (slab, component, Re/Im) of osum, a (slab, part) of mh_rec) holds its
+// RecBatch::n slots in groups of G = 16 / sizeof(T) (four floats, two
+// doubles): group k is a run of Ns 16-byte cells, one per site x, holding
+// slots kG .. kG + G - 1 of that site.  A sub-update's record writes one
+// element of each cell (consecutive threads, consecutive cells); a fold reads
+// a site's batch as n / G 16-byte vectors Ns cells apart.
+template <typename T>
 __host__ __device__ __forceinline__ size_t rec_index(const Geom& g, size_t row, int x, int slot) {
-  return (row * RecBatch<float>::n + slot) * static_cast<size_t>(g.Ns) + x;
+  constexpr int G = 16 / static_cast<int>(sizeof(T));
+  constexpr int NG = RecBatch<T>::n / G;
+  return ((row * NG + slot / G) * static_cast<size_t>(g.Ns) + x) * G + slot % G;
 }
 
 // Multihit ring slot of slab s, site x: modulus at part 0, phase at part 1.
 template <typename T>
 __device__ __forceinline__ size_t mh_index(const Geom& g, int s, int part, int x, int slot) {
-  return rec_index(g, static_cast<size_t>(s) * 2 + part, x, slot);
+  return rec_index<T>(g, static_cast<size_t>(s) * 2 + part, x, slot);
 }
 
 // Warps of the record of one slab: warp xw covers the spatial sites
@@ -135,7 +140,7 @@ __device__ __forceinline__ void record_warp(const LatDesc& L, int buf, int slot,
   spatial_coords(g, x, &c[1], &c[2], &c[3]);
   if (y == nc) {
     if (live) {
-      static_cast<T*>(L.theta_rec[buf])[rec_index(g, s, x, slot)] = slab_phase_sum<T>(d, [&](int tl) {
+      static_cast<T*>(L.theta_rec[buf])[rec_index<T>(g, s, x, slot)] = slab_phase_sum<T>(d, [&](int tl) {
         const int t = s * d + tl;
         const int i = c[1] + g.L * (c[2] + g.L * (c[3] + g.L * t));
         return th[soa(g, 0, i, (c[1] + c[2] + c[3] + t) & 1)];
@@ -156,8 +161,8 @@ __device__ __forceinline__ void record_warp(const LatDesc& L, int buf, int slot,
       im += sn;
     }
     T* osum = static_cast<T*>(L.osum[buf]);
-    osum[rec_index(g, static_cast<size_t>(s * nc + y) * 2 + 0, x, slot)] = re;
-    osum[rec_index(g, static_cast<size_t>(s * nc + y) * 2 + 1, x, slot)] = im;
+    osum[rec_index<T>(g, static_cast<size_t>(s * nc + y) * 2 + 0, x, slot)] = re;
+    osum[rec_index<T>(g, static_cast<size_t>(s * nc + y) * 2 + 1, x, slot)] = im;
   }
 }
 

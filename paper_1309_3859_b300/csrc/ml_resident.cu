@@ -515,7 +515,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
         const int x = cx + g.L * (b.y0 + ry + g.L * (b.z0 + rz));
         const int bi = b.cell(cx, ry + 1, rz + 1);
         const int xp = b.xplus(cx), xm = b.xminus(cx);
-        static_cast<T*>(Ld.theta_rec[rec_buf])[rec_index(g, s, x, slot)] =
+        static_cast<T*>(Ld.theta_rec[rec_buf])[rec_index<T>(g, s, x, slot)] =
             slab_phase_sum<T>(d, [&](int tl) { return buf[tl * b.vol + bi]; });
         if (MH && Ld.mh_rec[rec_buf]) {
           T mod, ph;
@@ -537,8 +537,8 @@ __global__ void __launch_bounds__(kResThreads, 1)
             re += cs;
             im += sn;
           }
-          osum[rec_index(g, static_cast<size_t>(s * nc + y) * 2 + 0, x, slot)] = re;
-          osum[rec_index(g, static_cast<size_t>(s * nc + y) * 2 + 1, x, slot)] = im;
+          osum[rec_index<T>(g, static_cast<size_t>(s * nc + y) * 2 + 0, x, slot)] = re;
+          osum[rec_index<T>(g, static_cast<size_t>(s * nc + y) * 2 + 1, x, slot)] = im;
         };
         if (nc == 6) {  // all six components, rows in component order: planes known at compile time
           plane_sums(0, 1, 0);

@@ -537,7 +537,8 @@ def test_sweep_implementations_agree(fp64, geom):
 @pytest.mark.parametrize("geom", [dict(L=8, Nt=4, n_sub=20, probes=((0, 0), (1, 0), (-2, 1), (3, -2))),
                                   dict(L=8, Nt=8, n_sub=18, outer_slab=4, n_sub_outer=2,
                                        probes=((0, 0), (2, 0), (-3, 3))),
-                                  dict(L=12, Nt=4, n_sub=3, probes=tuple((d, 0) for d in range(7)))])
+                                  dict(L=12, Nt=4, n_sub=3, probes=tuple((d, 0) for d in range(7))),
+                                  dict(L=6, Nt=4, n_sub=5, probes=((0, 0), (1, -1)))])
 def test_fold_implementations_agree(fp64, geom):
     """The per-site fold and the shared-memory tiled fold form the same sums
     operation for operation: identical records.  The probe sets reach both
@@ -553,11 +554,12 @@ def test_fold_implementations_agree(fp64, geom):
     assert np.array_equal(out[ml.ML_FOLD_SITE], out[ml.ML_FOLD_TILE])
 
 
-def test_tiled_fold_refused_when_rows_are_not_whole_chunks():
-    """FP32 rows of L = 6 sites are not a whole number of 16-byte chunks: the
-    tiled fold is refused and the handle keeps the per-site fold."""
-    p = ml.Params(L=6, Nt=4, beta=0.95, seed=8, fp64=False, slab=2, n_sub=2, r=(1,), rf=(2,), probes=((0, 0),),
-                  comp_mask=0x3F)
+def test_tiled_fold_refused_when_the_tile_does_not_fit():
+    """Probes six z planes apart on a 64^3 lattice need a tile of 28 rows x 64
+    sites x 16 slots (112 KB) per block, above the tiled fold's shared-memory
+    limit: the tiled fold is refused and the handle keeps the per-site fold."""
+    p = ml.Params(L=64, Nt=4, beta=0.95, seed=8, fp64=False, slab=2, n_sub=2, r=(1,), rf=(2,),
+                  probes=((0, 0), (0, 6)), comp_mask=0x01)
     with ml.Lattice(p) as lat:
         assert lat.fold_mode == ml.ML_FOLD_SITE
         with pytest.raises(ml.MLError) as exc:
