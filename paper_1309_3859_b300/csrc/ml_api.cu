@@ -186,7 +186,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   const int nB = rec_batch(e->fp64);
   L->osum_bytes = static_cast<size_t>(nslab_in) * nc * 2 * g.Ns * nB * tsz;
   L->trec_bytes = static_cast<size_t>(nslab_in) * g.Ns * nB * tsz;
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < e->ring_bufs; ++b) {
     L->osum[b] = lat_alloc(e, L, L->osum_bytes);
     L->theta_rec[b] = lat_alloc(e, L, L->trec_bytes);
     if (any_mh) L->mh_rec[b] = lat_alloc(e, L, 2 * L->trec_bytes);
@@ -204,11 +204,12 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
       static_cast<double2*>(lat_alloc(e, L, (static_cast<size_t>(nr) * nw + nvw / 2 + 1) * sizeof(double2)));
   L->scratch_n = static_cast<unsigned long long*>(lat_alloc(e, L, sizeof(unsigned long long)));
   L->naive_theta = lat_alloc(e, L, 4ull * g.V * tsz);
-  const bool ok = L->theta && L->naive_theta && L->d_n && L->d_lists && L->accT && (L->accO || !L->accO_bytes) && L->osum[0] &&
-                  L->osum[1] && (!p->replay || (L->replay_theta && L->replay_n)) &&
-                  L->theta_rec[0] && L->theta_rec[1] && L->vac_part && L->partial && (L->rest || !L->rest_bytes) &&
-                  L->partial_naive && L->scratch_n && (!nslab_out || (L->acc4T && L->acc4O)) &&
-                  (!any_mh || (L->mh_rec[0] && L->mh_rec[1]));
+  bool rings = true;
+  for (int b = 0; b < e->ring_bufs; ++b) rings = rings && L->osum[b] && L->theta_rec[b] && (!any_mh || L->mh_rec[b]);
+  const bool ok = L->theta && L->naive_theta && L->d_n && L->d_lists && L->accT && (L->accO || !L->accO_bytes) &&
+                  rings && (!p->replay || (L->replay_theta && L->replay_n)) && L->vac_part && L->partial &&
+                  (L->rest || !L->rest_bytes) && L->partial_naive && L->scratch_n &&
+                  (!nslab_out || (L->acc4T && L->acc4O));
   if (!ok) return ML_ENOMEM;
 
   MeasLayout& m = L->meas;
@@ -247,7 +248,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   d.slab = p->slab;
   d.nslab = nslab_in;
   d.tiles = (g.Vh + kSweepTile - 1) / kSweepTile;
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kRingBufs; ++b) {
     d.theta_rec[b] = L->theta_rec[b];
     d.mh_rec[b] = L->mh_rec[b];
     d.osum[b] = L->osum[b];
@@ -265,7 +266,7 @@ int make_lattice(Engine* e, const ml_params* p, LatState** out) {
   if (ce == cudaSuccess) ce = cudaMemsetAsync(L->vac_part, 0, L->vac_bytes, s);
   if (ce == cudaSuccess && L->rest) ce = cudaMemsetAsync(L->rest, 0, L->rest_bytes, s);
   // ring slots not yet written in a batch are multiplied by zero: keep them finite
-  for (int b = 0; b < 2 && ce == cudaSuccess; ++b) {
+  for (int b = 0; b < e->ring_bufs && ce == cudaSuccess; ++b) {
     ce = cudaMemsetAsync(L->osum[b], 0, L->osum_bytes, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(L->theta_rec[b], 0, L->trec_bytes, s);
     if (ce == cudaSuccess && L->mh_rec[b]) ce = cudaMemsetAsync(L->mh_rec[b], 0, 2 * L->trec_bytes, s);
@@ -374,7 +375,7 @@ int check_errors(Engine* e) {
 
 void destroy_graphs(Engine* e) {
   std::vector<Graph*> all = {&e->g_full, &e->g_outer, &e->g_one_full};
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < kRingBufs; ++b)
     for (int j = 0; j < kBatchMax; ++j) all.push_back(&e->g_sub[b][j]);
   for (Graph* gr : all)
     if (gr->exec) {
@@ -412,29 +413,34 @@ int hand_over(Engine* e, int buf, int nrec, bool defer_O, bool first) {
   return ML_OK;
 }
 
+// The last ring buffer of an inner loop, whose field insertions the
+// products fold (its first-fold flag with it).
+struct InnerTail {
+  int buf = -1, nrec = 0;
+  bool first = false;
+};
+
 // inner loop of n_sub slab sub-updates (main stream), folding every nB
 // records on the accumulation stream while the sweeps continue; a ring
-// buffer is reused only after its previous fold has finished.  With tail_buf,
+// buffer is reused only after its previous fold has finished.  With tail,
 // the last buffer's field-insertion fold is deferred to the products and
-// (*tail_buf, *tail_nrec) name it.
-int run_inner_loop(Engine* e, int* tail_buf = nullptr, int* tail_nrec = nullptr, bool* tail_first = nullptr) {
-  int buf = e->cur_buf, slot = 0;
+// tail names it.
+int run_inner_loop(Engine* e, InnerTail* tail = nullptr) {
+  const int nbufs = (e->n_sub + e->nB - 1) / e->nB;
+  int buf = e->cur_buf, slot = 0, done = 0;
   bool first = true;  // the slab sums are not cleared: the first fold starts them from zero
-  auto fold = [&](int buf_, int nrec_) {
-    const int st = hand_over(e, buf_, nrec_, false, first);
-    first = false;
-    return st;
-  };
-  auto last = [&](int buf_, int nrec_) {
-    if (tail_buf) {
-      *tail_buf = buf_;
-      *tail_nrec = nrec_;
-      *tail_first = first;
+  auto complete = [&](int buf_, int nrec_) -> int {
+    const bool last = done++ == nbufs - 1;
+    if (last && tail) {
+      tail->buf = buf_;
+      tail->nrec = nrec_;
+      tail->first = first;
     }
-    const int st = hand_over(e, buf_, nrec_, tail_buf != nullptr, first);
+    const int st = hand_over(e, buf_, nrec_, last && tail, first);
     first = false;
     return st;
   };
+  auto next = [&](int b) { return (b + 1) % e->ring_bufs; };
   if (const ResidentPlan* p = e->sweep_mode == ML_SWEEP_RESIDENT ? resident_plan(e, e->slab) : nullptr) {
     // one cluster-resident launch per ring buffer: the sweeps keep their
     // SMs, the previous buffer's fold runs on the others
@@ -444,9 +450,9 @@ int run_inner_loop(Engine* e, int* tail_buf = nullptr, int* tail_nrec = nullptr,
       if (launch_sweeps_resident(e->fp64, *p, e->d_desc, e->td.nlat, e->n_or, 1, e->d_err, e->stream, true, buf, 0,
                                  cnt))
         return ML_ECUDA;
-      int st = i + cnt == e->n_sub ? last(buf, cnt) : fold(buf, cnt);
+      const int st = complete(buf, cnt);
       if (st) return st;
-      buf ^= 1;
+      buf = next(buf);
       i += cnt;
     }
     e->cur_buf = buf;
@@ -457,17 +463,17 @@ int run_inner_loop(Engine* e, int* tail_buf = nullptr, int* tail_nrec = nullptr,
     int st = launch_graph(e, e->g_sub[buf][slot]);
     if (st) return st;
     if (++slot == e->nB) {
-      st = i + 1 == e->n_sub ? last(buf, slot) : fold(buf, slot);
+      st = complete(buf, slot);
       if (st) return st;
-      buf ^= 1;
+      buf = next(buf);
       slot = 0;
       if (i + 1 < e->n_sub) ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
     }
   }
   if (slot > 0) {
-    int st = last(buf, slot);
+    const int st = complete(buf, slot);
     if (st) return st;
-    buf ^= 1;
+    buf = next(buf);
   }
   e->cur_buf = buf;
   return ML_OK;
@@ -558,16 +564,15 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       ncfg = e->n_sub;
     } else if (e->outer_slab == 0) {
       // the last ring buffer's field insertions are folded by the products
-      int tb = 0, tn = 0;
-      bool tfirst = false;
-      st = run_inner_loop(e, &tb, &tn, &tfirst);
+      InnerTail t;
+      st = run_inner_loop(e, &t);
       if (st) return st;
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
         launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
-                        L->rest, out[li], e->side, ProductTail{L->theta_rec[tb], L->osum[tb], tn, tfirst ? 1 : 0});
+                        L->rest, out[li], e->side, ProductTail{L->theta_rec[t.buf], L->osum[t.buf], t.nrec, t.first ? 1 : 0});
       }
-      ML_CUDA(cudaEventRecord(e->ev_fold[tb], e->side));  // the tail buffer is free after the products
+      ML_CUDA(cudaEventRecord(e->ev_fold[t.buf], e->side));  // the tail buffer is free after the products
       ncfg = e->n_sub;
     } else {
       for (LatState* L : e->lats) {
@@ -625,13 +630,12 @@ int part_measure_inner(Engine* e, double* rec) {
   launch_naive_and_plaquette(e->fp64, L->naive_theta, L->g, L->meas, L->partial_naive, rec, e->side);
   ML_CUDA(cudaMemsetAsync(L->vac_part, 0, L->vac_bytes, e->side));
   if (e->outer_slab == 0) {
-    int tb = 0, tn = 0;
-    bool tfirst = false;
-    st = run_inner_loop(e, &tb, &tn, &tfirst);
+    InnerTail t;
+    st = run_inner_loop(e, &t);
     if (st) return st;
-    e->part_tail_buf = tb;
-    e->part_tail_nrec = tn;
-    e->part_tail_first = tfirst;
+    e->part_tail_buf = t.buf;
+    e->part_tail_nrec = t.nrec;
+    e->part_tail_first = t.first;
   } else {
     ML_CUDA(cudaMemsetAsync(L->acc4T, 0, L->acc4T_bytes, e->side));
     if (L->acc4O_bytes) ML_CUDA(cudaMemsetAsync(L->acc4O, 0, L->acc4O_bytes, e->side));
@@ -691,7 +695,7 @@ int capture_graphs(Engine* e) {
   int st = ML_OK;
   if (e->k_between > 0) st = capture(e, &e->g_full, [&] { return enqueue_sweeps(e, e->k_between, 0); });
   if (!st) st = capture(e, &e->g_one_full, [&] { return enqueue_sweeps(e, 1, 0); });
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < e->ring_bufs; ++b) {
     for (int j = 0; j < e->nB && !st; ++j)
       st = capture(e, &e->g_sub[b][j], [&] { return enqueue_sub_update(e, b, j); });
   }
@@ -856,11 +860,20 @@ int choose_sweep_mode(Engine* e) {
   return check_errors(e);
 }
 
+std::vector<cudaEvent_t*> engine_events(Engine* e) {
+  std::vector<cudaEvent_t*> v = {&e->ev_main, &e->ev_side};
+  for (int b = 0; b < kRingBufs; ++b) {
+    v.push_back(&e->ev_rec[b]);
+    v.push_back(&e->ev_fold[b]);
+  }
+  return v;
+}
+
 void destroy_engine(Engine* e) {
   if (e->side) cudaStreamSynchronize(e->side);
   if (e->stream) cudaStreamSynchronize(e->stream);
   destroy_graphs(e);
-  for (cudaEvent_t* x : {&e->ev_rec[0], &e->ev_rec[1], &e->ev_fold[0], &e->ev_fold[1], &e->ev_main, &e->ev_side})
+  for (cudaEvent_t* x : engine_events(e))
     if (*x) cudaEventDestroy(*x);
   if (e->side) cudaStreamDestroy(e->side);
   for (LatState* L : e->lats) free_lattice(e, L);
@@ -910,8 +923,7 @@ int init_engine(Engine* e, const ml_params* ps, int n, const ml_allocator* alloc
     e->own_stream = true;
   }
   ML_CUDA(cudaStreamCreateWithPriority(&e->side, cudaStreamNonBlocking, lo));
-  for (cudaEvent_t* x : {&e->ev_rec[0], &e->ev_rec[1], &e->ev_fold[0], &e->ev_fold[1], &e->ev_main, &e->ev_side})
-    ML_CUDA(cudaEventCreateWithFlags(x, cudaEventDisableTiming));
+  for (cudaEvent_t* x : engine_events(e)) ML_CUDA(cudaEventCreateWithFlags(x, cudaEventDisableTiming));
   e->d_err = static_cast<int*>(dev_alloc(e, sizeof(int)));
   e->bar = static_cast<unsigned long long*>(dev_alloc(e, sizeof(unsigned long long)));
   if (!e->d_err || !e->bar) return ML_ENOMEM;

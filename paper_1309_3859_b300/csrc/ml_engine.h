@@ -28,9 +28,9 @@ struct LatState {
   int* d_lists = nullptr;
   double2 *accT = nullptr, *accO = nullptr, *acc4T = nullptr, *acc4O = nullptr;
   size_t accT_bytes = 0, accO_bytes = 0, acc4T_bytes = 0, acc4O_bytes = 0;
-  void* osum[2] = {nullptr, nullptr};       // record ring [nslab][nc][2][slots][Ns]
-  void* theta_rec[2] = {nullptr, nullptr};  // record ring [nslab][slots][Ns]
-  void* mh_rec[2] = {nullptr, nullptr};     // multihit ring [nslab][2][slots][Ns], or none
+  void* osum[kRingBufs] = {};       // record ring [nslab][nc][2][slots][Ns]
+  void* theta_rec[kRingBufs] = {};  // record ring [nslab][slots][Ns]
+  void* mh_rec[kRingBufs] = {};     // multihit ring [nslab][2][slots][Ns], or none
   size_t osum_bytes = 0, trec_bytes = 0;
   double* vac_part = nullptr;  // [nparts][nc * 2] vacuum block sums of the current measurement
   int nparts = 0;
@@ -72,9 +72,10 @@ struct Engine {
   int full_mode = ML_SWEEP_PERSISTENT;   // of sweeps the resident kernels cannot run (no frozen links)
   ResidentPlan res_inner, res_outer;     // cluster-resident plans for slab and outer_slab
   int nB = kBatchMax, cur_buf = 0;  // ring slots (rec_batch of the precision)
-  cudaEvent_t ev_rec[2] = {nullptr, nullptr}, ev_fold[2] = {nullptr, nullptr};
+  int ring_bufs = kRingBufs;        // ring buffers per lattice (the server's tick folds in place: 1)
+  cudaEvent_t ev_rec[kRingBufs] = {}, ev_fold[kRingBufs] = {};
   cudaEvent_t ev_main = nullptr, ev_side = nullptr;
-  Graph g_full, g_outer, g_one_full, g_sub[2][kBatchMax];
+  Graph g_full, g_outer, g_one_full, g_sub[kRingBufs][kBatchMax];
   double* rec_buf = nullptr;
   size_t rec_cap = 0;
   // time-slab partition: a measurement split into ml_measure_inner and

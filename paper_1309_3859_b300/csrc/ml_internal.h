@@ -30,6 +30,10 @@ struct MeasLayout {
 // Per-lattice descriptor read by the multi-lattice ("table") kernels.  A
 // table holds one or more lattices of one precision; one launch covers all of
 // them, each with its own geometry, coupling, seed and buffers.
+// Record ring buffers per lattice: one is folded while the sub-updates fill
+// the other.
+constexpr int kRingBufs = 2;
+
 struct LatDesc {
   Geom g;
   MeasLayout m;
@@ -42,9 +46,9 @@ struct LatDesc {
   double metro_width;         // Metropolis proposal half-width
   int slab, nslab;            // inner slab thickness d and Nt / d
   int tile_start, tiles;      // sweep tiles of kSweepTile links
-  void* theta_rec[2];         // record ring buffers [nslab][slots][Ns]
-  void* mh_rec[2];            // multihit ring [nslab][2][slots][Ns] (modulus, phase); null: none
-  void* osum[2];              // [nslab][nc][2][slots][Ns], slots = rec_batch(fp64)
+  void* theta_rec[kRingBufs];  // record ring buffers [nslab][slots][Ns]
+  void* mh_rec[kRingBufs];     // multihit ring [nslab][2][slots][Ns] (modulus, phase); null: none
+  void* osum[kRingBufs];       // [nslab][nc][2][slots][Ns], slots = rec_batch(fp64)
   double2* accT;              // inner slab sums: double2 (re, im), or for FP32
   double2* accO;              //   lattices with float-pair sums float4 (re_hi, re_lo, im_hi, im_lo)
   double* vac_part;           // [nparts][nc * 2] vacuum sums of the measurement's folds per block of

@@ -578,6 +578,7 @@ int ml_server_create(const ml_server_config* cfg, ml_server** out) {
     ln->index = k;
     ln->e.fp64 = s->fp64;
     ln->e.n_or = s->n_or;
+    ln->e.ring_bufs = 1;  // each tick folds its records before the next tick writes
     ln->e.alloc.alloc = arena_alloc;
     ln->e.alloc.free = arena_free;
     ln->e.alloc.ctx = &s->arena;
