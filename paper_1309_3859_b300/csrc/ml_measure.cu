@@ -519,44 +519,64 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
   T er[B], ei[B];
   batch_phases<T>(trec + rec_index<T>(g, s, x, 0), trec + rec_index<T>(g, s, xr, 0), g.Ns, nrec, er, ei);
   const int col = wrapc(xx + rf / 2, g.L);
-  constexpr int NG = B / CH;                          // 16-byte cells of a site's batch
-  const int copies = NG * trows * g.L;                // per component
+  constexpr int NG = B / CH;  // 16-byte cells of a site's batch
+  // block tables after the tile: the first site of each tile row, and each
+  // probe's tile row relative to the thread's own (yy)
+  int* const row_site = reinterpret_cast<int*>(tile + static_cast<size_t>(NG) * trows * g.L * CH);
+  int* const probe_row = row_site + trows;
+  for (int r = tid; r < trows; r += blockDim.x) {
+    const int tz = r / tyn, ty = r - tz * tyn;
+    row_site[r] = g.L * (wrapc(y0 + pb.dymin + ty, g.L) + g.L * wrapc(z0 + pb.dzmin + tz, g.L));
+  }
+  for (int b = tid; b < m.np; b += blockDim.x) probe_row[b] = (m.pdy[b] - pb.dymin) + tyn * (m.pdz[b] - pb.dzmin);
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
+  const int nrows = NG * trows;  // staged rows: slot group k, tile row r
+  // the thread's slab sums of (probe b, value q): arow + (b * nck + q) * Ns
+  A* const arow = reinterpret_cast<A*>(L.accO) + (static_cast<size_t>(s) * m.nrf + f) * m.np * nck * g.Ns + x;
+  const size_t bstride = static_cast<size_t>(nck) * g.Ns;
   for (int q = 0; q < nck; ++q) {
-    const size_t rowck = static_cast<size_t>(s * m.nc + (q >> 1)) * 2 + (q & 1);
-    for (int c = tid; c < copies; c += blockDim.x) {  // cell c: slot group k, tile row r, site u of the row
-      const int u = c % g.L, kr = c / g.L;
-      const int r = kr % trows, k = kr / trows;
-      const int tz = r / tyn, ty = r - tz * tyn;
-      const int yg = wrapc(y0 + pb.dymin + ty, g.L), zg = wrapc(z0 + pb.dzmin + tz, g.L);
-      cp_async16(tile + ((static_cast<size_t>(k) * trows + r) * g.L + u) * CH,
-                 osum + rec_index<T>(g, rowck, u + g.L * (yg + g.L * zg), k * CH));
+    // each warp copies whole rows (a row is L consecutive 16-byte cells in
+    // the ring and in the tile), rows warp, warp + nwarps, ...
+    const T* qsrc = osum + rec_index<T>(g, static_cast<size_t>(s * m.nc + (q >> 1)) * 2 + (q & 1), 0, 0);
+    int k = 0, r = warp;
+    while (r >= trows) {
+      r -= trows;
+      ++k;
+    }
+    for (int kr = warp; kr < nrows; kr += nwarps) {
+      const T* src = qsrc + (static_cast<size_t>(k) * g.Ns + row_site[r]) * CH;
+      T* dst = tile + static_cast<size_t>(kr) * g.L * CH;
+      for (int u = lane; u < g.L; u += 32) cp_async16(dst + u * CH, src + u * CH);
+      r += nwarps;
+      while (r >= trows) {
+        r -= trows;
+        ++k;
+      }
     }
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
     if (live) {
+      A* ap = arow + static_cast<size_t>(q) * g.Ns;
       for (int b0 = 0; b0 < m.np; b0 += kTileProbes) {
         A a[kTileProbes];
 #pragma unroll
         for (int i = 0; i < kTileProbes; ++i)
-          if (b0 + i < m.np)
-            a[i] = overwrite ? A{}
-                             : __ldcs(acc + (((static_cast<size_t>(s) * m.nrf + f) * m.np + b0 + i) * nck + q) * g.Ns + x);
+          if (b0 + i < m.np) a[i] = overwrite ? A{} : __ldcs(ap + (b0 + i) * bstride);
 #pragma unroll
         for (int i = 0; i < kTileProbes; ++i) {
           const int b = b0 + i;
           if (b >= m.np) break;
-          const int r = (yy + m.pdy[b] - pb.dymin) + tyn * (m.pdz[b] - pb.dzmin);
           T o[B];
-          tile_batch<T>(tile + (static_cast<size_t>(r) * g.L + col) * CH, trows * g.L, o);
+          tile_batch<T>(tile + (static_cast<size_t>(yy + probe_row[b]) * g.L + col) * CH, trows * g.L, o);
           T sr, si;
           batch_dot<T, B>(er, ei, o, sr, si);
           acc_add(a[i], sr, si);
         }
 #pragma unroll
         for (int i = 0; i < kTileProbes; ++i)
-          if (b0 + i < m.np)
-            __stcs(acc + (((static_cast<size_t>(s) * m.nrf + f) * m.np + b0 + i) * nck + q) * g.Ns + x, a[i]);
+          if (b0 + i < m.np) __stcs(ap + (b0 + i) * bstride, a[i]);
       }
     }
     __syncthreads();  // the tile is read before the next component's copies
@@ -574,7 +594,9 @@ bool fold_tile_plan(bool fp64, int L, const int* pdy, const int* pdz, int np, in
   const int tsz = fp64 ? 8 : 4;
   if (L > kTileThreads) return false;
   const ProbeBox pb = probe_box(pdy, pdz, np);
-  const size_t bytes = static_cast<size_t>(RecBatch<float>::n) * tile_rows(L, pb) * L * tsz;
+  // the tile, then the row and probe tables (ints)
+  const size_t bytes = static_cast<size_t>(RecBatch<float>::n) * tile_rows(L, pb) * L * tsz +
+                       (static_cast<size_t>(tile_rows(L, pb)) + np) * sizeof(int);
   if (bytes > kTileSmemMax) return false;
   const int ry = tile_rows_per_block(L);
   *blocks_x = (L + ry - 1) / ry * L;
