@@ -386,49 +386,56 @@ __global__ void __launch_bounds__(256, fold_min_blocks<T>())
   const LatDesc& L = desc[li];
   const Geom g = L.g;
   const MeasLayout& m = L.m;
-  const int nbg = (m.np + kProbesPerThread - 1) / kProbesPerThread;
+  // the layout's counts in registers: the slab-sum stores below may alias the
+  // descriptor as far as the compiler knows
+  const int np = m.np, nc = m.nc, nrf = m.nrf;
+  const int nbg = (np + kProbesPerThread - 1) / kProbesPerThread;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= g.Ns || m.nrf == 0 || nbg == 0 || m.nc == 0 || static_cast<int>(blockIdx.y) >= L.nslab * m.nrf * nbg)
-    return;
+  if (x >= g.Ns || nrf == 0 || nbg == 0 || nc == 0 || static_cast<int>(blockIdx.y) >= L.nslab * nrf * nbg) return;
   const int bg = blockIdx.y % nbg;
   const int sf = blockIdx.y / nbg;
-  const int s = sf / m.nrf, f = sf - s * m.nrf;
+  const int s = sf / nrf, f = sf - s * nrf;
   int cx, cy, cz;
   spatial_coords(g, x, &cx, &cy, &cz);
   const int rf = m.rf[f];
   const int xr = wrapc(cx + rf, g.L) + g.L * (cy + g.L * cz);
   const T* __restrict__ trec = static_cast<const T*>(L.theta_rec[buf]);
   const T* __restrict__ osum = static_cast<const T*>(L.osum[buf]);
-  A* __restrict__ acc = reinterpret_cast<A*>(L.accO);
   T er[B], ei[B];
   batch_phases<T>(trec + rec_index<T>(g, s, x, 0), trec + rec_index<T>(g, s, xr, 0), g.Ns, nrec, er, ei);
   const int x0x = wrapc(cx + rf / 2, g.L);
-  const int nck = 2 * m.nc;
-  const int b_end = min(m.np, (bg + 1) * kProbesPerThread);
-  for (int b = bg * kProbesPerThread; b < b_end; ++b) {
+  const int nck = 2 * nc;
+  const int b_begin = bg * kProbesPerThread, b_end = min(np, b_begin + kProbesPerThread);
+  constexpr int G = 16 / static_cast<int>(sizeof(T));
+  const size_t ring_row = static_cast<size_t>(B) * g.Ns;  // elements of one ring row (value q -> q + 1)
+  // value q = (ci, k) of slab s: ring row s * nck + q; slab sum (b, q): acc
+  // row ((s * nrf + f) * np + b) * nck + q
+  const T* const orow = osum + rec_index<T>(g, static_cast<size_t>(s) * nck, 0, 0);
+  A* ap = reinterpret_cast<A*>(L.accO) + ((static_cast<size_t>(s) * nrf + f) * np + b_begin) * nck * g.Ns + x;
+  for (int b = b_begin; b < b_end; ++b) {
     const int x0 = x0x + g.L * (wrapc(cy + m.pdy[b], g.L) + g.L * wrapc(cz + m.pdz[b], g.L));
-    const size_t abase = (((static_cast<size_t>(s) * m.nrf + f) * m.np + b) * nck) * g.Ns + x;
+    const T* op = orow + static_cast<size_t>(x0) * G;
     // the slab sums of a group are read before its arithmetic, so their
     // loads are in flight together
     for (int q0 = 0; q0 < nck; q0 += kAccGroup) {
       A a[kAccGroup];
 #pragma unroll
       for (int i = 0; i < kAccGroup; ++i)
-        if (q0 + i < nck) a[i] = overwrite ? A{} : __ldcs(acc + abase + static_cast<size_t>(q0 + i) * g.Ns);
+        if (q0 + i < nck) a[i] = overwrite ? A{} : __ldcs(ap + static_cast<size_t>(i) * g.Ns);
 #pragma unroll
       for (int i = 0; i < kAccGroup; ++i) {
-        const int q = q0 + i;
-        if (q >= nck) break;
-        const int ci = q >> 1, k = q & 1;
+        if (q0 + i >= nck) break;
         T o[B];
-        load_batch<T>(osum + rec_index<T>(g, static_cast<size_t>(s * m.nc + ci) * 2 + k, x0, 0), g.Ns, o);
+        load_batch<T>(op, g.Ns, o);
+        op += ring_row;
         T sr, si;
         batch_dot<T, B>(er, ei, o, sr, si);
         acc_add(a[i], sr, si);
       }
 #pragma unroll
       for (int i = 0; i < kAccGroup; ++i)
-        if (q0 + i < nck) __stcs(acc + abase + static_cast<size_t>(q0 + i) * g.Ns, a[i]);
+        if (q0 + i < nck) __stcs(ap + static_cast<size_t>(i) * g.Ns, a[i]);
+      ap += static_cast<size_t>(kAccGroup) * g.Ns;
     }
   }
 }
@@ -496,7 +503,10 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
   const LatDesc& L = desc[li];
   const Geom g = L.g;
   const MeasLayout& m = L.m;
-  if (m.nrf == 0 || m.np == 0 || m.nc == 0 || static_cast<int>(blockIdx.y) >= L.nslab * m.nrf) return;
+  // the layout's counts in registers: the slab-sum stores below may alias the
+  // descriptor as far as the compiler knows
+  const int np = m.np, nrf = m.nrf;
+  if (nrf == 0 || np == 0 || m.nc == 0 || static_cast<int>(blockIdx.y) >= L.nslab * nrf) return;
   const int ry = tile_rows_per_block(g.L);
   const int nrb = (g.L + ry - 1) / ry;  // row blocks per z plane
   if (static_cast<int>(blockIdx.x) >= nrb * g.L) return;
@@ -505,7 +515,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
   const ProbeBox pb = probe_box(m.pdy, m.pdz, m.np);
   const int tyn = ry + pb.dymax - pb.dymin;
   const int trows = tyn * (pb.dzmax - pb.dzmin + 1);
-  const int s = blockIdx.y / m.nrf, f = blockIdx.y - s * m.nrf;
+  const int s = blockIdx.y / nrf, f = blockIdx.y - s * nrf;
   const int nck = 2 * m.nc;
   const int tid = threadIdx.x, yy = tid / g.L, xx = tid - yy * g.L;
   const bool live = yy < rows;
@@ -528,17 +538,18 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
     const int tz = r / tyn, ty = r - tz * tyn;
     row_site[r] = g.L * (wrapc(y0 + pb.dymin + ty, g.L) + g.L * wrapc(z0 + pb.dzmin + tz, g.L));
   }
-  for (int b = tid; b < m.np; b += blockDim.x) probe_row[b] = (m.pdy[b] - pb.dymin) + tyn * (m.pdz[b] - pb.dzmin);
+  for (int b = tid; b < np; b += blockDim.x) probe_row[b] = (m.pdy[b] - pb.dymin) + tyn * (m.pdz[b] - pb.dzmin);
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
   const int nrows = NG * trows;  // staged rows: slot group k, tile row r
   // the thread's slab sums of (probe b, value q): arow + (b * nck + q) * Ns
-  A* const arow = reinterpret_cast<A*>(L.accO) + (static_cast<size_t>(s) * m.nrf + f) * m.np * nck * g.Ns + x;
+  A* const arow = reinterpret_cast<A*>(L.accO) + (static_cast<size_t>(s) * nrf + f) * np * nck * g.Ns + x;
   const size_t bstride = static_cast<size_t>(nck) * g.Ns;
+  const int cells = trows * g.L;  // tile cells between slot groups
   for (int q = 0; q < nck; ++q) {
     // each warp copies whole rows (a row is L consecutive 16-byte cells in
     // the ring and in the tile), rows warp, warp + nwarps, ...
-    const T* qsrc = osum + rec_index<T>(g, static_cast<size_t>(s * m.nc + (q >> 1)) * 2 + (q & 1), 0, 0);
+    const T* qsrc = osum + rec_index<T>(g, static_cast<size_t>(s) * nck + q, 0, 0);
     int k = 0, r = warp;
     while (r >= trows) {
       r -= trows;
@@ -558,25 +569,27 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<T>()) k_accum_O_
     cp_async_wait_all();
     __syncthreads();
     if (live) {
-      A* ap = arow + static_cast<size_t>(q) * g.Ns;
-      for (int b0 = 0; b0 < m.np; b0 += kTileProbes) {
+      A* ap = arow + static_cast<size_t>(q) * g.Ns;  // probe b0's slab sum; probe b0 + i's at + i * bstride
+      const T* const trow = tile + static_cast<size_t>(yy * g.L + col) * CH;
+      for (int b0 = 0; b0 < np; b0 += kTileProbes) {
         A a[kTileProbes];
 #pragma unroll
         for (int i = 0; i < kTileProbes; ++i)
-          if (b0 + i < m.np) a[i] = overwrite ? A{} : __ldcs(ap + (b0 + i) * bstride);
+          if (b0 + i < np) a[i] = overwrite ? A{} : __ldcs(ap + i * bstride);
 #pragma unroll
         for (int i = 0; i < kTileProbes; ++i) {
           const int b = b0 + i;
-          if (b >= m.np) break;
+          if (b >= np) break;
           T o[B];
-          tile_batch<T>(tile + (static_cast<size_t>(yy + probe_row[b]) * g.L + col) * CH, trows * g.L, o);
+          tile_batch<T>(trow + probe_row[b] * g.L * CH, cells, o);
           T sr, si;
           batch_dot<T, B>(er, ei, o, sr, si);
           acc_add(a[i], sr, si);
         }
 #pragma unroll
         for (int i = 0; i < kTileProbes; ++i)
-          if (b0 + i < m.np) __stcs(ap + (b0 + i) * bstride, a[i]);
+          if (b0 + i < np) __stcs(ap + i * bstride, a[i]);
+        ap += kTileProbes * bstride;
       }
     }
     __syncthreads();  // the tile is read before the next component's copies
