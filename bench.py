@@ -839,6 +839,26 @@ def run_gpu(args, w, rank, world):
 SWEEP_MODES = {"persistent": 0, "passes": 1, "resident": 2}
 
 
+def fold_case(impl, reps=3):
+    """The fold of the two-level 48^3 workload's field insertions (probes at y
+    offsets 0..12, six components) on a 48^3 x 8 lattice with one field
+    separation: the same blocks and tiles as the 48^3 x 16 workload with 1.1
+    GB of slab sums instead of 6.6 GB.  Prints one JSON line."""
+    from paper_1309_3859_b300 import ml
+
+    w = workloads.LARGE_48
+    p = ml.Params(L=w.L, Nt=8, beta=w.beta, seed=w.seed, fp64=False, slab=w.slab, n_sub=32, k_between=1, r=(2, 4),
+                  rf=(16,), probes=w.probes, comp_mask=w.comp_mask)
+    with ml.Lattice(p) as lat:
+        lat.thermalize(1)
+        lat.fold_mode = ml.ML_FOLD_TILE if impl == "tile" else ml.ML_FOLD_SITE
+        nslab, nrf, nq = p.Nt // p.slab, 1, 2 * bin(w.comp_mask).count("1")
+        print(json.dumps({"workload": "fold-48x48x48x8-fp32", "fold": impl,
+                          "slab_sum_bytes": nslab * nrf * len(w.probes) * nq * w.L ** 3 * 16,
+                          "fold_ms": lat.kernel_ms(ml.ML_K_ACCUMULATE, reps=reps)}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -857,7 +877,13 @@ def main():
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 8^3 x 4 FP64 and 48^3 x 16 two-level workloads")
+    ap.add_argument("--fold-case", choices=["tile", "site"],
+                    help="only time the fold of the two-level workload's probes on a 48^3 x 8 lattice (one "
+                         "field separation, 1.1 GB of sums) in the given implementation, and exit; a small case "
+                         "for profiling the 48^3 folds")
     args = ap.parse_args()
+    if args.fold_case:
+        return fold_case(args.fold_case)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus))
     w = workloads.WORKLOADS[args.workload]
