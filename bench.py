@@ -751,6 +751,7 @@ def run_gpu(args, w, rank, world):
     f64_point = fp64_point(ml, w) if rank == 0 and not args.no_extra and not w.fp64 else None
     pair_point = pair_sums_point(ml, w) if rank == 0 and not args.no_extra and not w.fp64 else None
     breakdown = step_breakdown(ml, w) if rank == 0 and not args.no_extra else None
+    tl = step_timeline(ml, lat, w) if rank == 0 and not args.no_extra else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -818,6 +819,7 @@ def run_gpu(args, w, rank, world):
         "fp64_path": f64_point,
         "pair_sums": pair_point,
         "step_breakdown": breakdown,
+        "timeline": tl,
         "vs_fp64_path": (f64_point["ms_per_step"] / (ms / args.steps)) if f64_point else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
@@ -837,6 +839,41 @@ def run_gpu(args, w, rank, world):
 
 
 SWEEP_MODES = {"persistent": 0, "passes": 1, "resident": 2}
+
+
+def step_timeline(ml, lat, w, n_meas=4):
+    """Launch timeline of n_meas streamed measurements (ml_timeline_read):
+    mean durations of the full sweeps, the sub-update groups (a whole ring
+    buffer), the folds and the products, and how much of the span the main
+    stream's work covers (the step's critical path: full sweeps, then
+    sub-updates)."""
+    import torch
+
+    rec = torch.empty((n_meas, lat.rec_len), dtype=torch.float64, device=lat.device)
+    lat.timeline_enable(64 * n_meas)
+    lat.measure_device(n_meas, rec)
+    marks = lat.timeline()
+    lat.timeline_enable(0)
+    spans = {}
+    open_at = {}
+    for tag, ms in marks:
+        kind, end = tag // 2, tag % 2
+        if not end:
+            open_at[kind] = ms
+        elif kind in open_at:
+            spans.setdefault(kind, []).append(ms - open_at.pop(kind))
+    names = {0: "full_sweeps", 1: "sub_update_group", 2: "fold", 3: "products"}
+    main = [ms for tag, ms in marks if tag // 2 in (0, 1)]
+    span = main[-1] - main[0] if len(main) > 1 else 0.0
+    busy = sum(spans.get(0, [])) + sum(spans.get(1, []))
+    nB = lat.batch_slots
+    full_groups = [d for i, d in enumerate(spans.get(1, [])) if (i + 1) % -(-w.n_sub // nB) != 0]
+    return {"measurements": n_meas, "ms_per_measurement": span / n_meas if n_meas else None,
+            **{names[k] + "_ms": float(np.mean(v)) for k, v in spans.items()},
+            "full_ring_group_ms": float(np.mean(full_groups)) if full_groups else None,
+            "sub_updates_per_group": nB, "main_stream_busy_frac": busy / span if span else None,
+            "note": "CUDA events around each launch group (ml_timeline_read); main stream: full sweeps and "
+                    "sub-update groups back to back; accumulation stream: folds and products beside them"}
 
 
 def fold_case(impl, reps=3):

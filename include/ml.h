@@ -326,6 +326,34 @@ typedef enum {
  * left undefined (every measurement clears them first).  Blocking. */
 int ml_kernel_timing(ml_lattice *h, int kernel, int reps, double *avg_ms);
 
+/* Launch timeline of the measurement schedule (Algorithm 1 as ml_measure and
+ * ml_measure_device enqueue it): with a capacity set, CUDA events are
+ * recorded around the full sweeps between measurements, every sub-update
+ * group (one cluster-resident launch of a ring buffer of sub-updates, or a
+ * ring buffer's worth of per-pass or persistent sub-update graphs) and the
+ * loop's last group, on the main stream, and around every fold of a ring
+ * buffer and the products, on the accumulation stream, until the capacity is
+ * used up.  The events only time: the schedule and the results are
+ * unchanged.  ml_timeline_enable(h, 0) turns it off; a new capacity discards
+ * earlier marks. */
+typedef enum {
+  ML_TL_FULL_BEGIN = 0, /* k0 full sweeps of a measurement (main stream)   */
+  ML_TL_FULL_END = 1,
+  ML_TL_SUB_BEGIN = 2,  /* a group of slab sub-updates (main stream)        */
+  ML_TL_SUB_END = 3,
+  ML_TL_FOLD_BEGIN = 4, /* the fold of a ring buffer (accumulation stream)  */
+  ML_TL_FOLD_END = 5,
+  ML_TL_PROD_BEGIN = 6, /* the products of a measurement, with the last
+                           buffer's field insertions (accumulation stream)  */
+  ML_TL_PROD_END = 7
+} ml_timeline_tag;
+int ml_timeline_enable(ml_lattice *h, int capacity);
+/* Waits for the handle's streams, then writes up to cap marks in recording
+ * order: tags[i] (ml_timeline_tag) and ms[i], the device time of mark i
+ * after the first mark; *n = the number written.  The marks are then
+ * discarded (the capacity stays). */
+int ml_timeline_read(ml_lattice *h, int *tags, float *ms, int cap, int *n);
+
 /* Implementations of the compound sweep.  ml_create times the available
  * ones on the handle's lattices and keeps the fastest; results are
  * bit-identical. */

@@ -333,6 +333,14 @@ int join(cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
   return ML_OK;
 }
 
+// a timeline mark on stream s (nothing when the timeline is off or full;
+// never inside a graph capture, where events would become graph nodes)
+void tl_mark(Engine* e, cudaStream_t s, int tag) {
+  if (tl_capturing || e->tl_n >= static_cast<int>(e->tl_ev.size())) return;
+  if (cudaEventRecord(e->tl_ev[e->tl_n], s) != cudaSuccess) return;
+  e->tl_tag[e->tl_n++] = tag;
+}
+
 template <typename F>
 int capture(Engine* e, Graph* out, F&& body) {
   cudaGraph_t graph = nullptr;
@@ -408,7 +416,9 @@ int hand_over(Engine* e, int buf, int nrec, bool defer_O, bool first) {
   }
   // the replay's first pass forms the slab averages [T] (and the vacuum) only
   const bool skip_O = defer_O || e->pass == 1;
+  tl_mark(e, e->side, ML_TL_FOLD_BEGIN);
   launch_fold_table(e->fp64, e->pairs, e->d_desc, e->td, nullptr, buf, nrec, e->side, skip_O, first);
+  tl_mark(e, e->side, ML_TL_FOLD_END);
   if (!defer_O) ML_CUDA(cudaEventRecord(e->ev_fold[buf], e->side));
   return ML_OK;
 }
@@ -447,9 +457,11 @@ int run_inner_loop(Engine* e, InnerTail* tail = nullptr) {
     for (int i = 0; i < e->n_sub;) {
       const int cnt = std::min(e->nB, e->n_sub - i);
       ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
+      tl_mark(e, e->stream, ML_TL_SUB_BEGIN);
       if (launch_sweeps_resident(e->fp64, *p, e->d_desc, e->td.nlat, e->n_or, 1, e->d_err, e->stream, true, buf, 0,
                                  cnt))
         return ML_ECUDA;
+      tl_mark(e, e->stream, ML_TL_SUB_END);
       const int st = complete(buf, cnt);
       if (st) return st;
       buf = next(buf);
@@ -460,9 +472,11 @@ int run_inner_loop(Engine* e, InnerTail* tail = nullptr) {
   }
   ML_CUDA(cudaStreamWaitEvent(e->stream, e->ev_fold[buf], 0));
   for (int i = 0; i < e->n_sub; ++i) {
+    if (slot == 0) tl_mark(e, e->stream, ML_TL_SUB_BEGIN);
     int st = launch_graph(e, e->g_sub[buf][slot]);
     if (st) return st;
-    if (++slot == e->nB) {
+    if (++slot == e->nB || i + 1 == e->n_sub) tl_mark(e, e->stream, ML_TL_SUB_END);
+    if (slot == e->nB) {
       st = complete(buf, slot);
       if (st) return st;
       buf = next(buf);
@@ -514,8 +528,10 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       ML_CUDA(cudaMemsetAsync(out[li], 0, L->meas.rec_len * sizeof(double), e->stream));
     }
     if (e->k_between > 0) {
+      tl_mark(e, e->stream, ML_TL_FULL_BEGIN);
       st = launch_graph(e, e->g_full);
       if (st) return st;
+      tl_mark(e, e->stream, ML_TL_FULL_END);
     }
     // the naive correlator and plaquette of this configuration run on the
     // accumulation stream, from a copy, while the inner loop starts
@@ -567,11 +583,13 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
       InnerTail t;
       st = run_inner_loop(e, &t);
       if (st) return st;
+      tl_mark(e, e->side, ML_TL_PROD_BEGIN);
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
         launch_products(L->g, L->g.Nt / e->slab, L->meas, e->fp64, e->pairs, L->accT, L->accO, 1.0 / e->n_sub, L->partial,
                         L->rest, out[li], e->side, ProductTail{L->theta_rec[t.buf], L->osum[t.buf], t.nrec, t.first ? 1 : 0});
       }
+      tl_mark(e, e->side, ML_TL_PROD_END);
       ML_CUDA(cudaEventRecord(e->ev_fold[t.buf], e->side));  // the tail buffer is free after the products
       ncfg = e->n_sub;
     } else {
@@ -587,11 +605,13 @@ int enqueue_measurements(Engine* e, int n_meas, double* rec) {
           launch_combine(L->g, L->g.Nt / e->outer_slab, e->outer_slab / e->slab, L->meas, e->pairs, L->accT,
                          L->accO, 1.0 / e->n_sub, L->acc4T, L->acc4O, e->side);
       }
+      tl_mark(e, e->side, ML_TL_PROD_BEGIN);
       for (int li = 0; li < nlat; ++li) {
         LatState* L = e->lats[li];
         launch_products(L->g, L->g.Nt / e->outer_slab, L->meas, e->fp64, e->pairs, L->acc4T, L->acc4O,
                         1.0 / e->n_sub_outer, L->partial, L->rest, out[li], e->side);
       }
+      tl_mark(e, e->side, ML_TL_PROD_END);
       ncfg = e->n_sub * e->n_sub_outer;
     }
     for (int li = 0; li < nlat; ++li)
@@ -869,10 +889,18 @@ std::vector<cudaEvent_t*> engine_events(Engine* e) {
   return v;
 }
 
+void destroy_timeline(Engine* e) {
+  for (cudaEvent_t ev : e->tl_ev) cudaEventDestroy(ev);
+  e->tl_ev.clear();
+  e->tl_tag.clear();
+  e->tl_n = 0;
+}
+
 void destroy_engine(Engine* e) {
   if (e->side) cudaStreamSynchronize(e->side);
   if (e->stream) cudaStreamSynchronize(e->stream);
   destroy_graphs(e);
+  destroy_timeline(e);
   for (cudaEvent_t* x : engine_events(e))
     if (*x) cudaEventDestroy(*x);
   if (e->side) cudaStreamDestroy(e->side);
@@ -1337,6 +1365,39 @@ int ml_set_fold_mode(ml_lattice* h, int mode) {
 int ml_batch_slots(ml_lattice* h, int* n) {
   if (!h || !n) return ML_EINVAL;
   *n = h->e.nB;
+  return ML_OK;
+}
+
+int ml_timeline_enable(ml_lattice* h, int capacity) {
+  if (!h || capacity < 0 || capacity > (1 << 20)) return ML_EINVAL;
+  Engine* e = &h->e;
+  if (e->side) ML_CUDA(cudaStreamSynchronize(e->side));
+  ML_CUDA(cudaStreamSynchronize(e->stream));
+  destroy_timeline(e);
+  for (int i = 0; i < capacity; ++i) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      destroy_timeline(e);
+      return ML_ECUDA;
+    }
+    e->tl_ev.push_back(ev);
+  }
+  e->tl_tag.assign(capacity, 0);
+  return ML_OK;
+}
+
+int ml_timeline_read(ml_lattice* h, int* tags, float* ms, int cap, int* n) {
+  if (!h || !n || cap < 0 || (cap > 0 && (!tags || !ms))) return ML_EINVAL;
+  Engine* e = &h->e;
+  if (e->side) ML_CUDA(cudaStreamSynchronize(e->side));
+  ML_CUDA(cudaStreamSynchronize(e->stream));
+  const int m = std::min(cap, e->tl_n);
+  for (int i = 0; i < m; ++i) {
+    tags[i] = e->tl_tag[i];
+    ML_CUDA(cudaEventElapsedTime(&ms[i], e->tl_ev[0], e->tl_ev[i]));
+  }
+  *n = m;
+  e->tl_n = 0;
   return ML_OK;
 }
 

@@ -83,6 +83,11 @@ struct Engine {
   bool part_open = false;
   int part_tail_buf = 0, part_tail_nrec = 0;
   bool part_tail_first = false;
+  // launch timeline (ml_timeline_enable): a pool of timing events, the marks
+  // recorded so far and their tags
+  std::vector<cudaEvent_t> tl_ev;
+  std::vector<int> tl_tag;
+  int tl_n = 0;
 };
 
 int cuda_status(cudaError_t e);

@@ -25,6 +25,8 @@ ML_UPDATE_HEATBATH, ML_UPDATE_METROPOLIS = 0, 1
 ML_PART_LINKS, ML_PART_SLAB_SUMS, ML_PART_VACUUM, ML_PART_W_SUMS = 0, 1, 2, 3
 (ML_K_HEATBATH, ML_K_OVERRELAX, ML_K_RECORD, ML_K_ACCUMULATE, ML_K_PRODUCTS, ML_K_SWEEP, ML_K_SUBUPDATE,
  ML_K_FULLSWEEP) = range(8)
+(ML_TL_FULL_BEGIN, ML_TL_FULL_END, ML_TL_SUB_BEGIN, ML_TL_SUB_END, ML_TL_FOLD_BEGIN, ML_TL_FOLD_END,
+ ML_TL_PROD_BEGIN, ML_TL_PROD_END) = range(8)
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
@@ -85,6 +87,9 @@ SIGNATURES = {
     "ml_sync": (ctypes.c_int, [_H]),
     "ml_philox": (ctypes.c_int, [_U32, _U32, ctypes.c_size_t, _U32]),
     "ml_kernel_timing": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "ml_timeline_enable": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ml_timeline_read": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
+                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ml_batch_slots": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     "ml_sweep_mode": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
     "ml_set_sweep_mode": (ctypes.c_int, [_H, ctypes.c_int]),
@@ -347,6 +352,20 @@ class Lattice:
 
     def compound_sweeps(self, n: int, slab_d: int = 0):
         _check(lib().ml_compound_sweeps(self.h, int(n), int(slab_d)), "ml_compound_sweeps")
+
+    def timeline_enable(self, capacity: int):
+        """Record up to `capacity` launch marks of the measurement schedule
+        (ml_timeline_enable; 0 turns it off)."""
+        _check(lib().ml_timeline_enable(self.h, int(capacity)), "ml_timeline_enable")
+
+    def timeline(self, cap: int = 1 << 16) -> list:
+        """The marks recorded so far as (ML_TL_* tag, ms after the first mark),
+        in recording order (ml_timeline_read); they are then discarded."""
+        tags = (ctypes.c_int * cap)()
+        ms = (ctypes.c_float * cap)()
+        n = ctypes.c_int()
+        _check(lib().ml_timeline_read(self.h, tags, ms, int(cap), ctypes.byref(n)), "ml_timeline_read")
+        return [(tags[i], ms[i]) for i in range(n.value)]
 
     def kernel_ms(self, kernel: int, reps: int = 20) -> float:
         """Average event-timed duration of one kernel class (ml_kernel_timing)."""
