@@ -752,6 +752,7 @@ def run_gpu(args, w, rank, world):
     pair_point = pair_sums_point(ml, w) if rank == 0 and not args.no_extra and not w.fp64 else None
     breakdown = step_breakdown(ml, w) if rank == 0 and not args.no_extra else None
     tl = step_timeline(ml, lat, w) if rank == 0 and not args.no_extra else None
+    rprof = resident_profile_point(ml, lat, w) if rank == 0 and not args.no_extra else None
 
     # end to end through the public API with host buffers: upload this
     # step's configuration from pinned memory, measure, read the record
@@ -820,6 +821,7 @@ def run_gpu(args, w, rank, world):
         "pair_sums": pair_point,
         "step_breakdown": breakdown,
         "timeline": tl,
+        "resident_profile": rprof,
         "vs_fp64_path": (f64_point["ms_per_step"] / (ms / args.steps)) if f64_point else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(theta_host.numel() * 8),
                 "d2h_bytes_per_step": int(lat.rec_len * 8), "steps": e2e_steps},
@@ -839,6 +841,38 @@ def run_gpu(args, w, rank, world):
 
 
 SWEEP_MODES = {"persistent": 0, "passes": 1, "resident": 2}
+
+
+def resident_profile_point(ml, lat, w):
+    """Where one cluster-resident launch spends its time (ml_resident_profile:
+    SM clock cycles per phase, thread 0 of each CTA), in microseconds at the
+    GPU's maximum SM clock (the bench's clock samples show it is held), and
+    each phase's share of a sub-update."""
+    if lat.sweep_mode != ml.ML_SWEEP_RESIDENT:
+        return None
+    pr = lat.resident_profile()
+    mhz = 2032.0
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=10).stdout.split()
+        mhz = float(out[0])
+    except Exception:  # noqa: BLE001 - the bench also runs where nvidia-smi is absent
+        pass
+    us = {k: v / mhz for k, v in pr.items() if k not in ("sub_updates", "ctas")}
+    n_or = w.n_or
+    counts = {"heatbath_t": 2, "heatbath_s": 6, "overrelax_t": 2 * n_or, "overrelax_s": 6 * n_or}
+    per_sub = {"update": sum(counts[c] * us["update_" + c] for c in counts),
+               "exchange": sum(counts[c] * us["exchange_" + c] for c in counts), "record": us["record"]}
+    total = sum(per_sub.values())
+    return {"us_per_pass": {k: round(v, 3) for k, v in us.items() if k.startswith(("update_", "exchange_"))},
+            "us_per_sub_update": {k: round(v, 2) for k, v in per_sub.items()},
+            "share_of_sub_update": {k: round(v / total, 3) for k, v in per_sub.items()},
+            "launch_us": round(us["launch"], 1), "setup_us": round(us["setup"], 1),
+            "write_back_us": round(us["write_back"], 1), "sub_updates_per_launch": pr["sub_updates"],
+            "sm_mhz_assumed": mhz,
+            "note": "timed variant of the launch (thread 0 of each CTA reads the SM clock; a block barrier splits "
+                    "each pass into own updates and exchange); pass classes: heatbath/overrelaxation, t = temporal "
+                    "links (both slices), s = spatial links (inner slice)"}
 
 
 def step_timeline(ml, lat, w, n_meas=4):

@@ -354,6 +354,28 @@ int ml_timeline_enable(ml_lattice *h, int capacity);
  * discarded (the capacity stays). */
 int ml_timeline_read(ml_lattice *h, int *tags, float *ms, int cap, int *n);
 
+/* Where the cluster-resident sub-updates spend their time: one launch as a
+ * measurement runs it (a ring buffer of sub-updates with their records, on
+ * the timing copy of the angles, so the chain is unchanged) in a variant in
+ * which thread 0 of every CTA reads the SM clock around its phases, with a
+ * block barrier between a pass's own link updates and its exchange.  out
+ * (ML_RESIDENT_PROFILE_LEN doubles, SM clock cycles averaged over the CTAs):
+ *   [0..3]  own link updates per pass, pass classes heatbath mu = 0,
+ *           heatbath mu > 0, overrelaxation mu = 0, overrelaxation mu > 0
+ *   [4..7]  exchange per pass (waiting for the neighbours' mirror stores and
+ *           tokens of the pass, and the block barrier after it), same classes
+ *   [8]     record of one sub-update (phase and plaquette sums, with its
+ *           cluster barriers)
+ *   [9]     launch set-up (box load, mirror lists, cluster barriers)
+ *   [10]    write-back of the links
+ *   [11]    the whole launch
+ *   [12]    sub-updates in the launch
+ *   [13]    CTAs
+ * ML_EINVAL when the handle's sub-updates are not cluster-resident.
+ * Blocking. */
+#define ML_RESIDENT_PROFILE_LEN 14
+int ml_resident_profile(ml_lattice *h, double *out, int n);
+
 /* Implementations of the compound sweep.  ml_create times the available
  * ones on the handle's lattices and keeps the fastest; results are
  * bit-identical. */

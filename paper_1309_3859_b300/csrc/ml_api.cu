@@ -1488,6 +1488,44 @@ int ml_kernel_timing(ml_lattice* h, int kernel, int reps, double* avg_ms) {
   return check_errors(e);
 }
 
+int ml_resident_profile(ml_lattice* h, double* out, int n) {
+  if (!h || !out || n < ML_RESIDENT_PROFILE_LEN) return ML_EINVAL;
+  Engine* e = &h->e;
+  const ResidentPlan* res = e->sweep_mode == ML_SWEEP_RESIDENT ? resident_plan(e, e->slab) : nullptr;
+  if (!res) return ML_EINVAL;
+  int st = ensure_scratch(e);
+  if (!st) st = join(e->side, e->stream, e->ev_side);
+  if (!st) st = refresh_scratch(e);
+  if (st) return st;
+  constexpr int kSlots = 17;
+  unsigned long long* d_prof = nullptr;
+  ML_CUDA(cudaMalloc(&d_prof, kSlots * sizeof(unsigned long long)));
+  unsigned long long p[kSlots] = {};
+  cudaError_t ce = cudaMemsetAsync(d_prof, 0, sizeof p, e->stream);
+  // one launch as a measurement runs it (a ring buffer of sub-updates with
+  // their records) on the timing copy of the angles
+  if (ce == cudaSuccess && launch_sweeps_resident(e->fp64, *res, e->d_desc_scratch, e->td.nlat, e->n_or, 1, e->d_err,
+                                                  e->stream, true, 0, 0, e->nB, d_prof))
+    ce = cudaErrorLaunchFailure;
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(p, d_prof, sizeof p, cudaMemcpyDeviceToHost, e->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+  cudaFree(d_prof);
+  if (ce != cudaSuccess) return cuda_status(ce);
+  const double ctas = static_cast<double>(p[16] ? p[16] : 1);
+  for (int c = 0; c < 4; ++c) {
+    const double passes = static_cast<double>(p[8 + c] ? p[8 + c] : 1);
+    out[c] = static_cast<double>(p[c]) / passes;
+    out[4 + c] = static_cast<double>(p[4 + c]) / passes;
+  }
+  out[8] = static_cast<double>(p[12]) / (ctas * e->nB);
+  out[9] = static_cast<double>(p[13]) / ctas;
+  out[10] = static_cast<double>(p[14]) / ctas;
+  out[11] = static_cast<double>(p[15]) / ctas;
+  out[12] = e->nB;
+  out[13] = static_cast<double>(p[16]);
+  return check_errors(e);
+}
+
 int ml_philox(const uint32_t* ctr, const uint32_t* key, size_t n, uint32_t* out) {
   if (!ctr || !key || !out) return ML_EINVAL;
   if (n == 0) return ML_OK;

@@ -225,8 +225,11 @@ void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, bool mh, Re
 // lattice of the table, each optionally followed by the record into ring slot
 // (rec_buf, rec_slot + round): n_rec sub-updates as n_rec calls of
 // launch_sweeps_table would run them, in one launch.  Returns 0 or -1.
+// prof: the timed variant, adding its per-CTA clock sums into prof (17
+// counters, see ml_resident_profile)
 int launch_sweeps_resident(bool fp64, const ResidentPlan& p, const LatDesc* d, int nlat, int n_or, int n_compound,
-                           int* err, cudaStream_t s, bool record, int rec_buf, int rec_slot, int n_rec = 1);
+                           int* err, cudaStream_t s, bool record, int rec_buf, int rec_slot, int n_rec = 1,
+                           unsigned long long* prof = nullptr);
 
 // kernels launched so far (process-wide)
 void count_launches(uint64_t n);

@@ -52,6 +52,7 @@
 namespace ml {
 
 constexpr int kResThreads = 512;
+constexpr int kResProfSlots = 17;  // counters of a timed launch: 16 clock sums + the CTA count
 constexpr size_t kResSmemMax = 200 * 1024;  // per CTA
 
 // x / div for x div < 2^40 with mdiv = floor(2^40 / div) + 1
@@ -258,12 +259,25 @@ __device__ __forceinline__ void box_or_pair(const Box& b, T* buf, const uint2* m
 // record into ring slot rec_slot + round.  done: counter of finished units;
 // the last one advances every lattice's sweep counter by n_rec n_compound and
 // resets it.
-template <typename T, bool MH>
+// TIMED: the same launch with thread 0 of every CTA reading the SM clock
+// around its phases (and a block barrier between a pass's own updates and its
+// exchange, so that the two are split), summed over the CTAs into prof
+// (kResProfSlots counters); the arithmetic and the results are unchanged.
+template <typename T, bool MH, bool TIMED = false>
 __global__ void __launch_bounds__(kResThreads, 1)
     k_sweeps_resident(const LatDesc* __restrict__ desc, const int4* __restrict__ units, int nunits, int nlat, int d,
                       int n_or, int n_compound, int* __restrict__ err, unsigned long long* __restrict__ done,
-                      int record, int rec_buf, int rec_slot, int n_rec) {
+                      int record, int rec_buf, int rec_slot, int n_rec,
+                      unsigned long long* __restrict__ prof = nullptr) {
   using P = Prec<T>;
+  // per-CTA clock sums of the timed launch (thread 0): pass classes c =
+  // (mu > 0) + 2 (overrelaxation): own updates [c], exchange [4 + c], passes
+  // [8 + c]; records [12]; set-up [13]; write-back [14]; whole CTA [15]
+  long long tp[16] = {};
+  long long t_kernel = 0, t_mark = 0;
+  if constexpr (TIMED) {
+    if (threadIdx.x == 0) t_kernel = t_mark = clock64();
+  }
   extern __shared__ __align__(16) unsigned char res_smem[];
   const int rank = static_cast<int>(cluster_rank());
   const int u = static_cast<int>(cluster_index());
@@ -477,6 +491,13 @@ __global__ void __launch_bounds__(kResThreads, 1)
     }
   };
   uint32_t q = 0;  // passes of this launch so far
+  if constexpr (TIMED) {
+    if (threadIdx.x == 0) {
+      const long long t = clock64();
+      tp[13] += t - t_mark;
+      t_mark = t;
+    }
+  }
   for (int round = 0; round < n_rec; ++round) {
     for (int c = 0; c < n_compound; ++c) {
       const unsigned long long n = nbase + 1 + static_cast<unsigned long long>(round) * n_compound + c;
@@ -495,12 +516,29 @@ __global__ void __launch_bounds__(kResThreads, 1)
               case 2: pass(std::integral_constant<int, 2>{}, sweep, par, n, bar); break;
               default: pass(std::integral_constant<int, 3>{}, sweep, par, n, bar); break;
             }
+            const int pc = (mu > 0 ? 1 : 0) + (sweep > 0 ? 2 : 0);
+            if constexpr (TIMED) {
+              __syncthreads();
+              if (threadIdx.x == 0) {
+                const long long t = clock64();
+                tp[pc] += t - t_mark;
+                t_mark = t;
+              }
+            }
             // this CTA's incoming mirror stores of the pass have landed, and
             // its own threads' updates are done
             if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, xbytes[mu > 0][par]);
             mbar_wait_bounded(bar, (q >> 1) & 1u, err);
             __syncthreads();
             ++q;
+            if constexpr (TIMED) {
+              if (threadIdx.x == 0) {
+                const long long t = clock64();
+                tp[4 + pc] += t - t_mark;
+                tp[8 + pc] += 1;
+                t_mark = t;
+              }
+            }
           }
     }
     if (record) {
@@ -559,6 +597,13 @@ __global__ void __launch_bounds__(kResThreads, 1)
     // records read mirrored cells: no CTA stores into them before every
     // record of this round is done
     cluster_sync();
+    if constexpr (TIMED) {
+      if (threadIdx.x == 0) {
+        const long long t = clock64();
+        tp[12] += t - t_mark;
+        t_mark = t;
+      }
+    }
   }
 
   // write back the updated links (U_0 at tl in [0, d), U_i at tl in [1, d))
@@ -575,6 +620,16 @@ __global__ void __launch_bounds__(kResThreads, 1)
     const int cy = b.y0 + ry, cz = b.z0 + rz, t = t0 + tl;
     th[soa(g, rho, cx + g.L * (cy + g.L * cz) + g.Ns * t, (cx + cy + cz + t) & 1)] =
         buf[sl * b.vol + b.cell(cx, ry + 1, rz + 1)];
+  }
+  if constexpr (TIMED) {
+    __syncthreads();
+    if (threadIdx.x == 0 && prof) {
+      const long long t = clock64();
+      tp[14] += t - t_mark;
+      tp[15] += t - t_kernel;
+      for (int i = 0; i < kResProfSlots - 1; ++i) atomicAdd(prof + i, static_cast<unsigned long long>(tp[i]));
+      atomicAdd(prof + kResProfSlots - 1, 1ull);  // CTAs
+    }
   }
   // every CTA of every unit read the sweep counters before its cluster's
   // barriers; the last unit to arrive advances them
@@ -605,10 +660,12 @@ static cudaLaunchConfig_t resident_config(int cs, size_t smem, int clusters, cud
   return cfg;
 }
 
-// the multihit variant records the multihit products too (more registers)
+// the multihit variant records the multihit products too (more registers);
+// the timed ones read the clock (ml_resident_profile)
 template <typename T>
-static auto resident_kernel(bool mh) {
-  return mh ? k_sweeps_resident<T, true> : k_sweeps_resident<T, false>;
+static auto resident_kernel(bool mh, bool timed = false) {
+  if (timed) return mh ? k_sweeps_resident<T, true, true> : k_sweeps_resident<T, false, true>;
+  return mh ? k_sweeps_resident<T, true, false> : k_sweeps_resident<T, false, false>;
 }
 
 template <typename T>
@@ -620,13 +677,17 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, Resi
   units->clear();
   if (mask < 1) return;
   auto kern = resident_kernel<T>(mh);
+  auto timed = resident_kernel<T>(mh, true);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kResSmemMax)) !=
-      cudaSuccess) {
+          cudaSuccess ||
+      cudaFuncSetAttribute(timed, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kResSmemMax)) !=
+          cudaSuccess) {
     cudaGetLastError();
     return;
   }
   for (int cs : {16, 8}) {
-    if (cs > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    if (cs > 8 && (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+                   cudaFuncSetAttribute(timed, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
       cudaGetLastError();
       continue;
     }
@@ -671,20 +732,22 @@ void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, bool mh, Re
 }
 
 int launch_sweeps_resident(bool fp64, const ResidentPlan& p, const LatDesc* d, int nlat, int n_or, int n_compound,
-                           int* err, cudaStream_t s, bool record, int rec_buf, int rec_slot, int n_rec) {
+                           int* err, cudaStream_t s, bool record, int rec_buf, int rec_slot, int n_rec,
+                           unsigned long long* prof) {
   if (n_compound <= 0 || n_rec <= 0) return 0;
   if (p.cs == 0 || !p.units || !p.done) return -1;
   cudaLaunchAttribute at[1];
   cudaError_t e;
   const int rec = record ? 1 : 0;
+  const bool timed = prof != nullptr;
   if (fp64) {
     cudaLaunchConfig_t cfg = resident_config<double>(p.cs, p.smem, p.nunits, s, at);
-    e = cudaLaunchKernelEx(&cfg, resident_kernel<double>(p.mh), d, p.units, p.nunits, nlat, p.mask, n_or, n_compound,
-                           err, p.done, rec, rec_buf, rec_slot, n_rec);
+    e = cudaLaunchKernelEx(&cfg, resident_kernel<double>(p.mh, timed), d, p.units, p.nunits, nlat, p.mask, n_or,
+                           n_compound, err, p.done, rec, rec_buf, rec_slot, n_rec, prof);
   } else {
     cudaLaunchConfig_t cfg = resident_config<float>(p.cs, p.smem, p.nunits, s, at);
-    e = cudaLaunchKernelEx(&cfg, resident_kernel<float>(p.mh), d, p.units, p.nunits, nlat, p.mask, n_or, n_compound, err,
-                           p.done, rec, rec_buf, rec_slot, n_rec);
+    e = cudaLaunchKernelEx(&cfg, resident_kernel<float>(p.mh, timed), d, p.units, p.nunits, nlat, p.mask, n_or,
+                           n_compound, err, p.done, rec, rec_buf, rec_slot, n_rec, prof);
   }
   count_launches(1);
   return e == cudaSuccess ? 0 : -1;

@@ -88,6 +88,7 @@ SIGNATURES = {
     "ml_philox": (ctypes.c_int, [_U32, _U32, ctypes.c_size_t, _U32]),
     "ml_kernel_timing": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ml_timeline_enable": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ml_resident_profile": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
     "ml_timeline_read": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float),
                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "ml_batch_slots": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int)]),
@@ -352,6 +353,20 @@ class Lattice:
 
     def compound_sweeps(self, n: int, slab_d: int = 0):
         _check(lib().ml_compound_sweeps(self.h, int(n), int(slab_d)), "ml_compound_sweeps")
+
+    def resident_profile(self) -> dict:
+        """SM clock cycles of one cluster-resident launch by phase
+        (ml_resident_profile): own updates and exchange per pass of each
+        class, record per sub-update, set-up, write-back, whole launch."""
+        n = 14
+        out = (ctypes.c_double * n)()
+        _check(lib().ml_resident_profile(self.h, out, n), "ml_resident_profile")
+        cls = ("heatbath_t", "heatbath_s", "overrelax_t", "overrelax_s")
+        d = {f"update_{c}": out[i] for i, c in enumerate(cls)}
+        d.update({f"exchange_{c}": out[4 + i] for i, c in enumerate(cls)})
+        d.update(record=out[8], setup=out[9], write_back=out[10], launch=out[11], sub_updates=int(out[12]),
+                 ctas=int(out[13]))
+        return d
 
     def timeline_enable(self, capacity: int):
         """Record up to `capacity` launch marks of the measurement schedule

@@ -65,3 +65,37 @@ def test_timeline_capacity_and_off():
         with pytest.raises(ml.MLError) as e:
             lat.timeline_enable(-1)
         assert e.value.status == ml.ML_EINVAL
+
+
+def test_resident_profile():
+    """The timed cluster-resident launch (ml_resident_profile): every phase
+    takes time, the passes and records account for most of the launch, the
+    chain is unchanged (the launch runs on the timing copy), and handles whose
+    sub-updates are not cluster-resident are refused."""
+    p = ml.Params(**KW)
+    with ml.Lattice(p) as lat:
+        lat.sweep_mode = ml.ML_SWEEP_RESIDENT
+        lat.thermalize(1)
+        before = lat.get_angles()
+        prof = lat.resident_profile()
+        assert np.array_equal(lat.get_angles(), before)
+        assert prof["sub_updates"] == lat.batch_slots and prof["ctas"] > 0
+        for k in ("update_heatbath_t", "update_heatbath_s", "update_overrelax_t", "update_overrelax_s",
+                  "exchange_heatbath_t", "exchange_overrelax_s", "record", "setup", "write_back"):
+            assert prof[k] > 0, k
+        n_or = p.n_or
+        per_sub = (2 * (prof["update_heatbath_t"] + prof["exchange_heatbath_t"])
+                   + 6 * (prof["update_heatbath_s"] + prof["exchange_heatbath_s"])
+                   + 2 * n_or * (prof["update_overrelax_t"] + prof["exchange_overrelax_t"])
+                   + 6 * n_or * (prof["update_overrelax_s"] + prof["exchange_overrelax_s"]) + prof["record"])
+        parts = per_sub * prof["sub_updates"] + prof["setup"] + prof["write_back"]
+        assert 0.8 * prof["launch"] < parts <= 1.01 * prof["launch"]
+        ref = lat.measure(1)
+    with ml.Lattice(p) as lat:
+        lat.sweep_mode = ml.ML_SWEEP_RESIDENT
+        lat.thermalize(1)
+        assert np.array_equal(lat.measure(1), ref)
+        lat.sweep_mode = ml.ML_SWEEP_PASSES
+        with pytest.raises(ml.MLError) as e:
+            lat.resident_profile()
+        assert e.value.status == ml.ML_EINVAL
