@@ -52,13 +52,27 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 
 // Open-interval uniforms: 52-bit u = (k + 1/2) 2^-52 with k = (a << 20) |
 // (b >> 12); 23-bit u = (k + 1/2) 2^-23 with k = a >> 9.  Both are exact in
-// their precision and lie strictly inside (0, 1).
+// their precision and lie strictly inside (0, 1).  k goes into the mantissa
+// of 1 + k 2^-p (no integer-to-float conversion), and subtracting 1 - 2^-(p+1)
+// is exact (the operands are within a factor of two of each other), so the
+// value is exactly (k + 1/2) 2^-p.
 __device__ __forceinline__ double uniform52(uint32_t a, uint32_t b) {
   const uint64_t k = (static_cast<uint64_t>(a) << 20) | static_cast<uint64_t>(b >> 12);
-  return (static_cast<double>(k) + 0.5) * 0x1p-52;
+  return __longlong_as_double(static_cast<long long>(0x3FF0000000000000ull | k)) - 0x1.fffffffffffffp-1;
 }
 __device__ __forceinline__ float uniform23(uint32_t a) {
-  return (static_cast<float>(a >> 9) + 0.5f) * 0x1p-23f;
+  return __uint_as_float(0x3F800000u | (a >> 9)) - 0x1.fffffep-1f;
+}
+
+// Round-to-nearest-even and floor of a float of magnitude below 2^22 on the
+// FP32 pipe: adding and subtracting 1.5 2^23 leaves the nearest integer
+// (ties to even, as rintf); floor steps that down by one where it lies above
+// y.  The _rn intrinsics keep the compiler from fusing the additions with a
+// preceding product.  Bit-identical to rintf / floorf in that range.
+__device__ __forceinline__ float rint_small(float y) { return __fsub_rn(__fadd_rn(y, 12582912.0f), 12582912.0f); }
+__device__ __forceinline__ float floor_small(float y) {
+  const float n = rint_small(y);
+  return n > y ? n - 1.0f : n;
 }
 
 // ---------------------------------------------------------------------------
@@ -182,7 +196,7 @@ template <>
 struct Prec<float> {
   static constexpr bool fp64 = false;
   __device__ static __forceinline__ void sincos_(float a, float* s, float* c) {
-    const float r = fmaf(-kTwoPiF, rintf(a * kInvTwoPiF), a);
+    const float r = fmaf(-kTwoPiF, rint_small(__fmul_rn(a, kInvTwoPiF)), a);
     __sincosf(r, s, c);
   }
   __device__ static __forceinline__ float atan2_(float y, float x) { return atan2f(y, x); }
@@ -190,7 +204,9 @@ struct Prec<float> {
   __device__ static __forceinline__ float log_(float a) { return __logf(a); }
   __device__ static __forceinline__ float acos_(float a) { return acosf(a); }
   __device__ static __forceinline__ float cos_pi_u(float u) { return __cosf(kPiF * u); }
-  __device__ static __forceinline__ float wrap(float a) { return fmaf(-kTwoPiF, floorf((a + kPiF) * kInvTwoPiF), a); }
+  __device__ static __forceinline__ float wrap(float a) {
+    return fmaf(-kTwoPiF, floor_small(__fmul_rn(__fadd_rn(a, kPiF), kInvTwoPiF)), a);
+  }
   __device__ static __forceinline__ float pi() { return kPiF; }
   __device__ static __forceinline__ float bessel_ratio(float x) { return cyl_bessel_i1f(x) / cyl_bessel_i0f(x); }
   static constexpr float kappa_tiny = 1e-15f;

@@ -77,12 +77,41 @@ __device__ __forceinline__ bool bf_trial(float kappa, float s, uint32_t a, uint3
   return false;
 }
 
+// The acceptance test of bf_trial with both of its tests evaluated (no
+// branch): the same boolean, so that trials can be computed side by side.
+__device__ __forceinline__ bool bf_accept(float kappa, float s, uint32_t a, uint32_t b, float* f_out) {
+  const float u1 = uniform23(a), u2 = uniform23(b);
+  const float z = Prec<float>::cos_pi_u(u1);
+  float f = __fdividef(fmaf(s, z, 1.0f), s + z);
+  f = fminf(fmaxf(f, -1.0f), 1.0f);
+  const float c = kappa * (s - f);
+  *f_out = f;
+  return (c * (2.0f - c) - u2 > 0.0f) | (__logf(c) - __logf(u2) + 1.0f - c >= 0.0f);
+}
+// Trials 4j .. 4j + 3 (Philox blocks 2j and 2j + 1) as four independent
+// chains; the first accepted one in trial order gives f and the sign.
+__device__ __forceinline__ bool bf_four(float kappa, float s, const U4& oa, const U4& ob, float* f, bool* neg) {
+  float f0, f1, f2, f3;
+  const bool a0 = bf_accept(kappa, s, oa.x, oa.y, &f0);
+  const bool a1 = bf_accept(kappa, s, oa.z, oa.w, &f1);
+  const bool a2 = bf_accept(kappa, s, ob.x, ob.y, &f2);
+  const bool a3 = bf_accept(kappa, s, ob.z, ob.w, &f3);
+  const uint32_t w = a0 ? oa.x : (a1 ? oa.z : (a2 ? ob.x : ob.z));
+  *f = a0 ? f0 : (a1 ? f1 : (a2 ? f2 : f3));
+  *neg = ((w >> 8) & 1u) == 0u;
+  return a0 | a1 | a2 | a3;
+}
+
 // Best & Fisher (Applied Statistics 28 (1979) 152): psi with density
 // exp(kappa cos psi) / (2 pi I0(kappa)).  Returns false at the trial cap.
 // EAGER (FP32): Philox blocks 0 and 1 are drawn together before the first
 // trial, so their two dependent round chains overlap; the trials are still
 // taken in order, so the angle is the one-at-a-time sampler's.  For
-// latency-bound callers with idle issue slots.
+// latency-bound callers with idle issue slots.  EAGER = 2 also evaluates the
+// four trials of two blocks side by side (and draws later blocks in pairs):
+// a pass ends with its slowest link, and with one link per thread that is
+// the rare link needing five or more trials, whose trials would otherwise
+// run one after another.
 // pre: EAGER > 0 only, the link's blocks 0 and 1 when the caller drew them
 // before its staple sum (so the rounds overlap that work too).
 template <typename T, int EAGER = 0>
@@ -121,7 +150,20 @@ __device__ __forceinline__ bool von_mises(T kappa, uint32_t site, int mu, unsign
       return true;
     }
     const float s = bf_envelope(kappa);
-    static_assert(kMaxTrials % 2 == 0, "trials come in pairs per Philox block");
+    static_assert(kMaxTrials % 4 == 0, "trials come in pairs per Philox block, blocks in pairs");
+    if constexpr (EAGER == 2) {
+      float f;
+      bool neg;
+      bool ok = bf_four(kappa, s, pre ? pre[0] : Draws<float>::block(site, mu, n, 0, k0, k1),
+                        pre ? pre[1] : Draws<float>::block(site, mu, n, 1, k0, k1), &f, &neg);
+      for (int j = 2; !ok && j < kMaxTrials / 2; j += 2)
+        ok = bf_four(kappa, s, Draws<float>::block(site, mu, n, j, k0, k1),
+                     Draws<float>::block(site, mu, n, j + 1, k0, k1), &f, &neg);
+      if (!ok) return false;
+      const float a = acosf(f);
+      *psi = neg ? -a : a;
+      return true;
+    }
     int j0 = 0;
     if constexpr (EAGER > 0) {
       const U4 o0 = pre ? pre[0] : Draws<float>::block(site, mu, n, 0, k0, k1);

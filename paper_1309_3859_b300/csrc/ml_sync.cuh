@@ -8,17 +8,20 @@
 namespace ml {
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident), on a
-// monotonic 64-bit arrival counter: block b's k-th arrival returns old, and
-// the barrier opens when the counter reaches the next multiple of the grid
-// size.  Arrival is a release atomic, polling an acquire load.  The spin is
-// bounded: after kSpinLimit polls the block records kErrTimeout and reports
-// failure, so a lost block cannot hang the device.
+// monotonic 64-bit arrival counter that is a multiple of the grid size
+// between launches.  Thread 0 of each block keeps the count at which the
+// next barrier opens (grid_barrier_base at kernel start: the counter rounded
+// down to a multiple of the grid size, which it cannot pass before every
+// block has arrived at the first barrier, so every block reads the same
+// base).  Arrival is a release reduction with no reply (the block goes
+// straight to polling, one round trip to L2 fewer than a returning atomic),
+// polling an acquire load.  The spin is bounded: after kSpinLimit polls the
+// block records kErrTimeout and reports failure, so a lost block cannot hang
+// the device.
 constexpr unsigned kSpinLimit = 1u << 28;
 
-__device__ __forceinline__ unsigned long long atom_add_release(unsigned long long* p, unsigned long long v) {
-  unsigned long long old;
-  asm volatile("atom.release.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
-  return old;
+__device__ __forceinline__ void red_add_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
@@ -27,15 +30,20 @@ __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long lon
   return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(unsigned long long* count, int* err) {
+__device__ __forceinline__ unsigned long long grid_barrier_base(const unsigned long long* count) {
+  const unsigned long long v = ld_acquire(count);
+  return v - v % gridDim.x;
+}
+
+// target: thread 0's opening count (from grid_barrier_base); unused elsewhere
+__device__ __forceinline__ bool grid_barrier(unsigned long long* count, unsigned long long* target, int* err) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
-    const unsigned long long nb = gridDim.x;
-    const unsigned long long old = atom_add_release(count, 1ull);
-    const unsigned long long target = (old / nb + 1ull) * nb;
+    *target += gridDim.x;
+    red_add_release(count, 1ull);
     unsigned polls = 0;
-    while (ld_acquire(count) < target) {
+    while (ld_acquire(count) < *target) {
       if (++polls > kSpinLimit) {
         atomicOr(err, kErrTimeout);
         ok = 0;

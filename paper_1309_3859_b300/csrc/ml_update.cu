@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
     c_base = *L.n_dev;
     c_sweeps = ctl ? ctl[i].sweeps : n_compound;
   }
+  unsigned long long bar_target = threadIdx.x == 0 ? grid_barrier_base(bar) : 0ull;
   for (int c = 0; c < n_compound; ++c) {
     for (int sweep = 0; sweep <= n_or; ++sweep)
       for (int mu = 0; mu < 4; ++mu)
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
                                   static_cast<T>(L.beta), err, update_rule(L));
             }
           }
-          if (!grid_barrier(bar, err)) return;
+          if (!grid_barrier(bar, &bar_target, err)) return;
         }
     if (record) {
       // record of the new configurations (the work of k_record_table, warp
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
         for (int it = gw; it < items; it += nwarps) record_warp<T>(L, buf, slot, it / nw, it - (it / nw) * nw, lane);
       }
       // the record reads the configuration the next sweep moves
-      if (any && c + 1 < n_compound && !grid_barrier(bar, err)) return;
+      if (any && c + 1 < n_compound && !grid_barrier(bar, &bar_target, err)) return;
     }
   }
   if (blockIdx.x == 0)
