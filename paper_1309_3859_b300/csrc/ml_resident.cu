@@ -186,23 +186,27 @@ __device__ __forceinline__ void box_staples(const Box& b, const T* buf, int mu, 
   w[5] = at(nu, tl - dt, bi + ob);   // theta_nu(x - nu)
 }
 
+// Mirror entry (cluster address of the slot-0 cell, cluster address of the
+// receiver's exchange barrier of even passes), or kOwnMirror in place of the
+// barrier for a ghost cell of this CTA's own box.
+constexpr uint32_t kOwnMirror = 0xFFFFFFFFu;
+
 // Store a link's angle v (slot sl, cell bi): into its own cell when it moved,
-// and into every mirror mirror[m0 .. m1) ((cluster address of the slot-0
-// cell, CTA rank)): st.async onto the receiver's exchange barrier `bar` (a
-// local address, the same in every CTA), or a plain store into this CTA's
-// (rank `own`) ghost rows.  Every mirror is stored, moved or not, so that the
-// receivers' byte counts are fixed.
+// and into every mirror mirror[m0 .. m1): st.async onto the receiver's
+// exchange barrier of the pass (the even passes' barrier + boff), or a plain
+// store into this CTA's ghost rows.  Every mirror is stored, moved or not, so
+// that the receivers' byte counts are fixed.
 template <typename T>
-__device__ __forceinline__ void box_commit(const Box& b, T* buf, const uint2* mirror, uint32_t own, uint32_t bar,
-                                           int m0, int m1, int sl, int bi, bool moved, T v) {
+__device__ __forceinline__ void box_commit(const Box& b, T* buf, const uint2* mirror, uint32_t boff, int m0, int m1,
+                                           int sl, int bi, bool moved, T v) {
   if (moved) buf[sl * b.vol + bi] = v;
   const uint32_t soff = static_cast<uint32_t>(sl * b.vol * sizeof(T));
   for (int m = m0; m < m1; ++m) {
     const uint2 e = mirror[m];
-    if (e.y == own)
+    if (e.y == kOwnMirror)
       st_cluster(e.x + soff, v);
     else
-      st_async(e.x + soff, v, map_to_rank(bar, e.y));
+      st_async(e.x + soff, v, e.y + boff);
   }
 }
 
@@ -211,8 +215,7 @@ __device__ __forceinline__ void box_commit(const Box& b, T* buf, const uint2* mi
 // template parameter, so the staple offsets and slots of every plane resolve
 // at compile time.
 template <typename T, int KIND, int MU>
-__device__ __forceinline__ void box_link(const Box& b, T* buf, const uint2* mirror, uint32_t own, uint32_t bar,
-                                         int m0, int m1, int tl, int bi, int xp, int xm, uint32_t site,
+__device__ __forceinline__ void box_link(const Box& b, T* buf, const uint2* mirror, uint32_t boff, int m0, int m1, int tl, int bi, int xp, int xm, uint32_t site,
                                          unsigned long long n, uint32_t k0, uint32_t k1, T beta, int* err,
                                          const UpdateRule& rule) {
   constexpr int mu = MU;
@@ -226,7 +229,7 @@ __device__ __forceinline__ void box_link(const Box& b, T* buf, const uint2* mirr
           ? new_link_angle<T, 2>(mu, staples, cur, site, n, k0, k1, beta, err, &out, static_cast<T>(rule.width),
                                  rule.hits)
           : new_link_angle<T, KIND, 2>(mu, staples, cur, site, n, k0, k1, beta, err, &out);
-  box_commit<T>(b, buf, mirror, own, bar, m0, m1, sl, bi, moved, moved ? out : *self);
+  box_commit<T>(b, buf, mirror, boff, m0, m1, sl, bi, moved, moved ? out : *self);
 }
 
 // A link of a pass: mirrors [m0, m1), local time, box cell, x offsets, site.
@@ -240,8 +243,7 @@ struct BoxLink {
 // staple loads and arithmetic interleave; the angles are those of two
 // box_link calls.
 template <typename T, int MU>
-__device__ __forceinline__ void box_or_pair(const Box& b, T* buf, const uint2* mirror, uint32_t own, uint32_t bar,
-                                            const BoxLink& la, const BoxLink& lb, int* err) {
+__device__ __forceinline__ void box_or_pair(const Box& b, T* buf, const uint2* mirror, uint32_t boff, const BoxLink& la, const BoxLink& lb, int* err) {
   auto sa = [&](int nu, T w[6]) { box_staples<T>(b, buf, MU, la.tl, la.bi, la.xp, la.xm, nu, w); };
   auto sb = [&](int nu, T w[6]) { box_staples<T>(b, buf, MU, lb.tl, lb.bi, lb.xp, lb.xm, nu, w); };
   const int sla = b.slot(MU, la.tl), slb = b.slot(MU, lb.tl);
@@ -249,8 +251,8 @@ __device__ __forceinline__ void box_or_pair(const Box& b, T* buf, const uint2* m
   T oa, ob;
   const bool ma = new_link_angle<T, 1, 2>(MU, sa, [&] { return ca; }, la.site, 0ull, 0u, 0u, T(0), err, &oa);
   const bool mb = new_link_angle<T, 1, 2>(MU, sb, [&] { return cb; }, lb.site, 0ull, 0u, 0u, T(0), err, &ob);
-  box_commit<T>(b, buf, mirror, own, bar, la.m0, la.m1, sla, la.bi, ma, ma ? oa : ca);
-  box_commit<T>(b, buf, mirror, own, bar, lb.m0, lb.m1, slb, lb.bi, mb, mb ? ob : cb);
+  box_commit<T>(b, buf, mirror, boff, la.m0, la.m1, sla, la.bi, ma, ma ? oa : ca);
+  box_commit<T>(b, buf, mirror, boff, lb.m0, lb.m1, slb, lb.bi, mb, mb ? ob : cb);
 }
 
 // Grid: one cluster of cs CTAs per unit (lattice, slab); mask d is the slab
@@ -417,7 +419,8 @@ __global__ void __launch_bounds__(kResThreads, 1)
     const uint32_t cnt = shared_addr(&xcnt[(cx + cy + cz) & 1]);
     for_each_mirror(g.L, b.ny, nz, b.yl_full, b.zl_full, bry, brz, cx, cy, cz, [&](int r, int cell) {
       const uint32_t ur = static_cast<uint32_t>(r);
-      mirror[m++] = make_uint2(map_to_rank(base + static_cast<uint32_t>(cell * sizeof(T)), ur), ur);
+      mirror[m++] = make_uint2(map_to_rank(base + static_cast<uint32_t>(cell * sizeof(T)), ur),
+                               r == rank ? kOwnMirror : map_to_rank(shared_addr(&xbar[0]), ur));
       if (r != rank) {
         red_add_cluster(map_to_rank(cnt, ur), 1u);
         xflag[r] = 1;
@@ -454,40 +457,43 @@ __global__ void __launch_bounds__(kResThreads, 1)
     }
   const uint32_t xtok_addr = shared_addr(&xtok);
   const uint32_t xbar0 = shared_addr(&xbar[0]);
-  const uint32_t urank = static_cast<uint32_t>(rank);
+  // link item k of a pass of the links at local times tl >= tl_lo (0:
+  // temporal, 1: spatial, whose links at tl = 0 are frozen) on sites of
+  // parity par: local time, then rows, then site pairs along x
+  auto item_at = [&](int tl_lo, int par, int k) {
+    const int q = fdiv(k, m_half);
+    const int tl = tl_lo + q, t = t0 + tl;
+    const int j = k - q * half;
+    const int row = fdiv(j, m_hx);
+    const int cx0 = 2 * (j - row * hx);  // even
+    const int rz = fdiv(row, m_yl), ry = row - rz * b.ylen;
+    const int cy = b.y0 + ry, cz = b.z0 + rz;
+    const int cx = cx0 + (((cy + cz + t) & 1) ^ par);
+    const int jo = cx + g.L * row;  // owned-site index
+    return BoxLink{mstart[jo], mstart[jo + 1], tl, b.cell(cx, ry + 1, rz + 1), b.xplus(cx), b.xminus(cx),
+                   static_cast<uint32_t>(cx + g.L * (cy + g.L * cz) + g.Ns * t)};
+  };
   // one (mu, parity) pass of this CTA's links, mu a compile-time constant;
   // bar: the pass's exchange barrier
   auto pass = [&](auto mu_c, int sweep, int par, unsigned long long n, uint32_t bar) {
     constexpr int mu = decltype(mu_c)::value;
     constexpr int tl_lo = mu == 0 ? 0 : 1;  // spatial links at tl = 0 are frozen
     const int items = (d - tl_lo) * half;
-    // link item k of the pass
-    auto item = [&](int k) {
-      const int q = fdiv(k, m_half);
-      const int tl = tl_lo + q, t = t0 + tl;
-      const int j = k - q * half;
-      const int row = fdiv(j, m_hx);
-      const int cx0 = 2 * (j - row * hx);  // even
-      const int rz = fdiv(row, m_yl), ry = row - rz * b.ylen;
-      const int cy = b.y0 + ry, cz = b.z0 + rz;
-      const int cx = cx0 + (((cy + cz + t) & 1) ^ par);
-      const int jo = cx + g.L * row;  // owned-site index
-      return BoxLink{mstart[jo], mstart[jo + 1], tl, b.cell(cx, ry + 1, rz + 1), b.xplus(cx), b.xminus(cx),
-                     static_cast<uint32_t>(cx + g.L * (cy + g.L * cz) + g.Ns * t)};
-    };
+    auto item = [&](int k) { return item_at(tl_lo, par, k); };
+    const uint32_t boff = bar - xbar0;  // the odd passes' barrier is the next 8 bytes
     int k = threadIdx.x;
     // the temporal overrelaxation passes give threads two links: taken as pairs
     if (mu == 0 && sweep > 0)
       for (; k + static_cast<int>(blockDim.x) < items; k += 2 * blockDim.x)
-        box_or_pair<T, mu>(b, buf, mirror, urank, bar, item(k), item(k + blockDim.x), err);
+        box_or_pair<T, mu>(b, buf, mirror, boff, item(k), item(k + blockDim.x), err);
     for (; k < items; k += blockDim.x) {
       const BoxLink l = item(k);
       if (sweep == 0)
-        box_link<T, 0, mu>(b, buf, mirror, urank, bar, l.m0, l.m1, l.tl, l.bi, l.xp, l.xm, l.site, n, k0, k1, beta,
-                           err, rule);
+        box_link<T, 0, mu>(b, buf, mirror, boff, l.m0, l.m1, l.tl, l.bi, l.xp, l.xm, l.site, n, k0, k1, beta, err,
+                           rule);
       else
-        box_link<T, 1, mu>(b, buf, mirror, urank, bar, l.m0, l.m1, l.tl, l.bi, l.xp, l.xm, l.site, n, k0, k1, beta,
-                           err, rule);
+        box_link<T, 1, mu>(b, buf, mirror, boff, l.m0, l.m1, l.tl, l.bi, l.xp, l.xm, l.site, n, k0, k1, beta, err,
+                           rule);
     }
   };
   uint32_t q = 0;  // passes of this launch so far

@@ -36,7 +36,7 @@ __device__ __forceinline__ int step_index(const Geom& g, int i, const int c[4], 
 // The direction is a template parameter so that the loop over the planes
 // (mu, nu) unrolls with constant nu: coordinate and neighbour selects
 // resolve at compile time; update_link dispatches on the runtime direction.
-template <typename T, int KIND, int MU>
+template <typename T, int KIND, int MU, int EAGER = 1>
 __device__ __forceinline__ void update_link_mu(T* th, const Geom& g, int parity, int slab_d, int h,
                                                unsigned long long n, uint32_t k0, uint32_t k1, T beta,
                                                int* __restrict__ err, const UpdateRule& rule) {
@@ -70,27 +70,29 @@ __device__ __forceinline__ void update_link_mu(T* th, const Geom& g, int parity,
     if (new_link_angle<T, 2>(mu, staples, cur, static_cast<uint32_t>(i), n, k0, k1, beta, err, &out,
                              static_cast<T>(rule.width), rule.hits))
       *self = out;
-  } else if (new_link_angle<T, KIND, 1>(mu, staples, cur, static_cast<uint32_t>(i), n, k0, k1, beta, err, &out)) {
+  } else if (new_link_angle<T, KIND, EAGER>(mu, staples, cur, static_cast<uint32_t>(i), n, k0, k1, beta, err, &out)) {
     *self = out;
   }
 }
 
-template <typename T, int KIND>
+// EAGER: the Philox draws of the heatbath (new_link_angle); 2 for kernels
+// with one link per thread that are bound by the latency of the update
+template <typename T, int KIND, int EAGER = 1>
 __device__ __forceinline__ void update_link(T* th, const Geom& g, int mu, int parity, int slab_d, int h,
                                             unsigned long long n, uint32_t k0, uint32_t k1, T beta,
                                             int* __restrict__ err, const UpdateRule& rule) {
   switch (mu) {
     case 0:
-      update_link_mu<T, KIND, 0>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
+      update_link_mu<T, KIND, 0, EAGER>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
       break;
     case 1:
-      update_link_mu<T, KIND, 1>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
+      update_link_mu<T, KIND, 1, EAGER>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
       break;
     case 2:
-      update_link_mu<T, KIND, 2>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
+      update_link_mu<T, KIND, 2, EAGER>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
       break;
     default:
-      update_link_mu<T, KIND, 3>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
+      update_link_mu<T, KIND, 3, EAGER>(th, g, parity, slab_d, h, n, k0, k1, beta, err, rule);
       break;
   }
 }
@@ -281,10 +283,10 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
           if (one_tile) {
             if (c_theta && c_h < c_g.Vh && c < c_sweeps) {
               if (sweep == 0)
-                update_link<T, 0>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err,
+                update_link<T, 0, 2>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err,
                                   c_rule);
               else
-                update_link<T, 1>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err,
+                update_link<T, 1, 2>(c_theta, c_g, mu, par, c_mask, c_h, c_base + 1 + c, c_k0, c_k1, c_beta, err,
                                   c_rule);
             }
           } else {
