@@ -346,10 +346,10 @@ def algorithmic_bytes(w, kernel, n_batch=1, d=None):
 
 
 # Warp instructions per link update of the global-memory pass kernel
-# (k_update_pass_pair<float, KIND>, ncu on a 64^4 FP32 lattice): heatbath 688
-# and overrelaxation 222 per 32 links.  The cluster-resident kernel runs the
+# (k_update_pass_pair<float, KIND>, ncu on a 64^4 FP32 lattice): heatbath 622
+# and overrelaxation 233 per 32 links.  The cluster-resident kernel runs the
 # same link update on shared memory; these counts give its issue bound.
-INSTR_PER_LINK = {"heatbath": 688 / 32, "overrelax": 222 / 32}
+INSTR_PER_LINK = {"heatbath": 622 / 32, "overrelax": 233 / 32}
 
 
 def issue_roofline(w, launch_ms, sub_updates, sms, sm_mhz):
