@@ -216,6 +216,7 @@ struct ResidentPlan {
   const int4* units = nullptr;         // device [nunits] (lattice, slab, ny, nz bricks)
   unsigned long long* done = nullptr;  // finished-unit counter (zero between launches)
   bool mh = false;                     // the records include the multihit products
+  bool l24 = false;                    // FP32 24^3 lattices, thickness 2, 16-CTA clusters: the constant-shape kernel
 };
 // Fills everything but the device pointers; the host list of units goes to
 // `units` (empty when cs = 0).  mh: the table has multihit lattices.

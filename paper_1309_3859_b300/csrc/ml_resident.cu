@@ -265,7 +265,10 @@ __device__ __forceinline__ void box_or_pair(const Box& b, T* buf, const uint2* m
 // around its phases (and a block barrier between a pass's own updates and its
 // exchange, so that the two are split), summed over the CTAs into prof
 // (kResProfSlots counters); the arithmetic and the results are unchanged.
-template <typename T, bool MH, bool TIMED = false>
+// L24: the shape of a 24^3 lattice in slabs of thickness 2 on 16-CTA
+// clusters (4 x 4 bricks), its extents compile-time constants (the plan
+// selects it only for such tables); 0: any shape.
+template <typename T, bool MH, bool TIMED = false, int L24 = 0>
 __global__ void __launch_bounds__(kResThreads, 1)
     k_sweeps_resident(const LatDesc* __restrict__ desc, const int4* __restrict__ units, int nunits, int nlat, int d,
                       int n_or, int n_compound, int* __restrict__ err, unsigned long long* __restrict__ done,
@@ -285,12 +288,19 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const int u = static_cast<int>(cluster_index());
   const int li = units[u].x, s = units[u].y;
   const LatDesc& Ld = desc[li];
-  const Geom g = Ld.g;
+  Geom g = Ld.g;
+  if constexpr (L24 != 0) {
+    d = 2;
+    g.L = 24;
+    g.Ns = 24 * 24 * 24;
+    g.m_L = div_magic(24);
+    g.m_hx = div_magic(12);
+  }
   Box b;
   b.L = g.L;
   b.d = d;
-  b.ny = units[u].z;
-  const int nz = units[u].w;
+  b.ny = L24 ? 4 : units[u].z;
+  const int nz = L24 ? 4 : units[u].w;
   b.yl_full = (g.L + b.ny - 1) / b.ny;
   b.zl_full = (g.L + nz - 1) / nz;
   b.bx = g.L;
@@ -668,8 +678,15 @@ static cudaLaunchConfig_t resident_config(int cs, size_t smem, int clusters, cud
 
 // the multihit variant records the multihit products too (more registers);
 // the timed ones read the clock (ml_resident_profile)
+// l24: the 24^3, thickness-2, 16-CTA shape (FP32 only)
 template <typename T>
-static auto resident_kernel(bool mh, bool timed = false) {
+static auto resident_kernel(bool mh, bool timed = false, bool l24 = false) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (l24) {
+      if (timed) return mh ? k_sweeps_resident<T, true, true, 1> : k_sweeps_resident<T, false, true, 1>;
+      return mh ? k_sweeps_resident<T, true, false, 1> : k_sweeps_resident<T, false, false, 1>;
+    }
+  }
   if (timed) return mh ? k_sweeps_resident<T, true, true> : k_sweeps_resident<T, false, true>;
   return mh ? k_sweeps_resident<T, true, false> : k_sweeps_resident<T, false, false>;
 }
@@ -683,17 +700,20 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, Resi
   units->clear();
   if (mask < 1) return;
   auto kern = resident_kernel<T>(mh);
-  auto timed = resident_kernel<T>(mh, true);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kResSmemMax)) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(timed, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kResSmemMax)) !=
-          cudaSuccess) {
-    cudaGetLastError();
-    return;
-  }
+  const decltype(kern) all[4] = {kern, resident_kernel<T>(mh, true), resident_kernel<T>(mh, false, true),
+                                 resident_kernel<T>(mh, true, true)};
+  for (auto k : all)
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kResSmemMax)) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
   for (int cs : {16, 8}) {
-    if (cs > 8 && (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-                   cudaFuncSetAttribute(timed, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    bool big_ok = true;
+    for (auto k : all)
+      if (cs > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        big_ok = false;
+    if (!big_ok) {
       cudaGetLastError();
       continue;
     }
@@ -725,6 +745,10 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, Resi
     p->cs = cs;
     p->smem = smem;
     p->nunits = static_cast<int>(units->size());
+    // the compile-time shape when every lattice has it
+    p->l24 = std::is_same<T, float>::value && cs == 16 && mask == 2;
+    for (int i = 0; i < nlat; ++i)
+      p->l24 = p->l24 && geoms[i].L == 24 && split[i].ny == 4 && split[i].nz == 4;
     return;
   }
 }
@@ -748,12 +772,12 @@ int launch_sweeps_resident(bool fp64, const ResidentPlan& p, const LatDesc* d, i
   const bool timed = prof != nullptr;
   if (fp64) {
     cudaLaunchConfig_t cfg = resident_config<double>(p.cs, p.smem, p.nunits, s, at);
-    e = cudaLaunchKernelEx(&cfg, resident_kernel<double>(p.mh, timed), d, p.units, p.nunits, nlat, p.mask, n_or,
-                           n_compound, err, p.done, rec, rec_buf, rec_slot, n_rec, prof);
+    e = cudaLaunchKernelEx(&cfg, resident_kernel<double>(p.mh, timed, p.l24), d, p.units, p.nunits, nlat, p.mask,
+                           n_or, n_compound, err, p.done, rec, rec_buf, rec_slot, n_rec, prof);
   } else {
     cudaLaunchConfig_t cfg = resident_config<float>(p.cs, p.smem, p.nunits, s, at);
-    e = cudaLaunchKernelEx(&cfg, resident_kernel<float>(p.mh, timed), d, p.units, p.nunits, nlat, p.mask, n_or,
-                           n_compound, err, p.done, rec, rec_buf, rec_slot, n_rec, prof);
+    e = cudaLaunchKernelEx(&cfg, resident_kernel<float>(p.mh, timed, p.l24), d, p.units, p.nunits, nlat, p.mask,
+                           n_or, n_compound, err, p.done, rec, rec_buf, rec_slot, n_rec, prof);
   }
   count_launches(1);
   return e == cudaSuccess ? 0 : -1;

@@ -502,7 +502,7 @@ def test_full_size_observe_fp32_single_24(multihit):
                                   dict(L=8, Nt=4, n_sub=3, **METRO), dict(L=6, Nt=4, n_sub=18, multihit=1),
                                   dict(L=6, Nt=4, n_sub=18, replay=1), dict(L=6, Nt=4, n_sub=5, slab=1),
                                   dict(L=8, Nt=8, n_sub=3, slab=4), dict(L=10, Nt=4, n_sub=3),
-                                  dict(L=4, Nt=4, n_sub=17)])
+                                  dict(L=4, Nt=4, n_sub=17), dict(L=24, Nt=8, n_sub=17)])
 def test_sweep_implementations_agree(fp64, geom):
     """The persistent kernel, the per-pass kernels and the cluster-resident
     kernels run the same link updates with the same random numbers: identical
@@ -511,7 +511,8 @@ def test_sweep_implementations_agree(fp64, geom):
     two-level run uses the resident kernels for both slab thicknesses.  In the
     resident kernel: slab thickness 1 (spatial passes that move no link, so
     CTAs exchange only their per-pass tokens) and 4, ragged bricks (L = 10 on
-    3 x 5 bricks) and bricks one site thick (L = 4)."""
+    3 x 5 bricks) and bricks one site thick (L = 4); L = 24 in slabs of
+    thickness 2 runs, in FP32, the resident kernel compiled for that shape."""
     kw = dict(beta=0.95, seed=5, fp64=fp64, slab=2, k_between=1, r=(1, 2), rf=(2,), probes=((0, 0), (1, 0)),
               comp_mask=0x3F)
     kw.update(geom)
