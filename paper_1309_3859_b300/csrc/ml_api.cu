@@ -758,11 +758,16 @@ int refresh_scratch(Engine* e) {
 // their unit lists and finished-unit counters on the device.
 int plan_resident_sweeps(Engine* e) {
   std::vector<Geom> geoms;
-  for (LatState* L : e->lats) geoms.push_back(L->g);
+  bool heatbath3 = e->n_or == 3;
+  for (LatState* L : e->lats) {
+    geoms.push_back(L->g);
+    heatbath3 = heatbath3 && L->desc.update == 0;
+  }
   for (ResidentPlan* p : {&e->res_inner, &e->res_outer}) {
     const int mask = p == &e->res_inner ? e->slab : e->outer_slab;
     std::vector<int4> units;
-    plan_resident(e->fp64, geoms.data(), static_cast<int>(geoms.size()), mask, e->td.max_blocks_mh > 0, p, &units);
+    plan_resident(e->fp64, geoms.data(), static_cast<int>(geoms.size()), mask, e->td.max_blocks_mh > 0, p, &units,
+                  heatbath3);
     if (p->cs == 0) continue;
     int4* d_units = static_cast<int4*>(dev_alloc(e, units.size() * sizeof(int4)));
     p->done = static_cast<unsigned long long*>(dev_alloc(e, sizeof(unsigned long long)));

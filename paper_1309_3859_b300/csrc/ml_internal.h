@@ -216,12 +216,15 @@ struct ResidentPlan {
   const int4* units = nullptr;         // device [nunits] (lattice, slab, ny, nz bricks)
   unsigned long long* done = nullptr;  // finished-unit counter (zero between launches)
   bool mh = false;                     // the records include the multihit products
-  bool l24 = false;                    // FP32 24^3 lattices, thickness 2, 16-CTA clusters: the constant-shape kernel
+  bool l24 = false;                    // FP32 24^3 lattices, thickness 2, 16-CTA clusters, heatbath + 3
+                                       // overrelaxation sweeps: the constant-shape kernel
 };
 // Fills everything but the device pointers; the host list of units goes to
 // `units` (empty when cs = 0).  mh: the table has multihit lattices.
+// heatbath3: every lattice takes the heatbath with 3 overrelaxation sweeps
+// (a condition of the constant-shape kernel).
 void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, bool mh, ResidentPlan* p,
-                   std::vector<int4>* units);
+                   std::vector<int4>* units, bool heatbath3 = false);
 // n_rec rounds of n_compound compound slab sweeps (mask p.mask) of every
 // lattice of the table, each optionally followed by the record into ring slot
 // (rec_buf, rec_slot + round): n_rec sub-updates as n_rec calls of

@@ -266,8 +266,9 @@ __device__ __forceinline__ void box_or_pair(const Box& b, T* buf, const uint2* m
 // exchange, so that the two are split), summed over the CTAs into prof
 // (kResProfSlots counters); the arithmetic and the results are unchanged.
 // L24: the shape of a 24^3 lattice in slabs of thickness 2 on 16-CTA
-// clusters (4 x 4 bricks), its extents compile-time constants (the plan
-// selects it only for such tables); 0: any shape.
+// clusters (4 x 4 bricks), its extents, the update rule (heatbath) and the 3
+// overrelaxation sweeps compile-time constants (the plan selects it only for
+// such tables); 0: any shape.
 template <typename T, bool MH, bool TIMED = false, int L24 = 0>
 __global__ void __launch_bounds__(kResThreads, 1)
     k_sweeps_resident(const LatDesc* __restrict__ desc, const int4* __restrict__ units, int nunits, int nlat, int d,
@@ -369,7 +370,9 @@ __global__ void __launch_bounds__(kResThreads, 1)
   const unsigned long long nbase = *Ld.n_dev;
   const uint32_t k0 = Ld.k0, k1 = Ld.k1;
   const T beta = static_cast<T>(Ld.beta);
-  const UpdateRule rule = update_rule(Ld);
+  // the constant-shape kernel runs heatbath + 3 overrelaxation sweeps only
+  const UpdateRule rule = L24 ? UpdateRule{0, 0, 0.0} : update_rule(Ld);
+  if constexpr (L24 != 0) n_or = 3;
   const unsigned long long m_yl = fdiv_magic(max(b.ylen, 1));
 
   // mirror lists: counts, an exclusive scan over the owned sites (one chunk
@@ -693,7 +696,7 @@ static auto resident_kernel(bool mh, bool timed = false, bool l24 = false) {
 
 template <typename T>
 static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, ResidentPlan* p,
-                            std::vector<int4>* units) {
+                            std::vector<int4>* units, bool heatbath3) {
   *p = ResidentPlan{};
   p->mask = mask;
   p->mh = mh;
@@ -746,7 +749,7 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, Resi
     p->smem = smem;
     p->nunits = static_cast<int>(units->size());
     // the compile-time shape when every lattice has it
-    p->l24 = std::is_same<T, float>::value && cs == 16 && mask == 2;
+    p->l24 = std::is_same<T, float>::value && cs == 16 && mask == 2 && heatbath3;
     for (int i = 0; i < nlat; ++i)
       p->l24 = p->l24 && geoms[i].L == 24 && split[i].ny == 4 && split[i].nz == 4;
     return;
@@ -754,11 +757,11 @@ static void plan_resident_t(const Geom* geoms, int nlat, int mask, bool mh, Resi
 }
 
 void plan_resident(bool fp64, const Geom* geoms, int nlat, int mask, bool mh, ResidentPlan* p,
-                   std::vector<int4>* units) {
+                   std::vector<int4>* units, bool heatbath3) {
   if (fp64)
-    plan_resident_t<double>(geoms, nlat, mask, mh, p, units);
+    plan_resident_t<double>(geoms, nlat, mask, mh, p, units, heatbath3);
   else
-    plan_resident_t<float>(geoms, nlat, mask, mh, p, units);
+    plan_resident_t<float>(geoms, nlat, mask, mh, p, units, heatbath3);
 }
 
 int launch_sweeps_resident(bool fp64, const ResidentPlan& p, const LatDesc* d, int nlat, int n_or, int n_compound,
