@@ -16,6 +16,30 @@ namespace ml {
 
 constexpr int kSweepThreads = kSweepTile;  // block size of the sweep kernels
 
+// Programmatic dependent launch of the per-pass kernels: a pass is launched
+// with programmatic stream serialization, so its blocks may be scheduled
+// while the previous pass drains; each thread first waits until the
+// previous kernel of the stream has completed and its memory is visible
+// (griddepcontrol.wait; a no-op when the kernel was launched without the
+// attribute), then allows the next pass's blocks to be scheduled.
+__device__ __forceinline__ void pass_prologue() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... Params, typename... Args>
+static void launch_pass_pdl(void (*kernel)(Params...), int grid, int block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<Params>(args)...);
+}
+
 // Site index of the neighbour one step along direction mu (sign +1 or -1)
 // of the site with index i and coordinates c = (t, x, y, z).  No division:
 // the wrap is a compare.
@@ -219,6 +243,7 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update_pass_pair(T* __restri
                                                                      unsigned long long n_fixed, uint32_t k0,
                                                                      uint32_t k1, T beta, int* __restrict__ err,
                                                                      UpdateRule rule) {
+  pass_prologue();
   const int hp = blockIdx.x * blockDim.x + threadIdx.x;
   if (hp >= (g.Vh >> 1)) return;
   const unsigned long long n = n_dev ? *n_dev : n_fixed;
@@ -230,6 +255,7 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update_pass(T* __restrict__ 
                                                       const unsigned long long* __restrict__ n_dev,
                                                       unsigned long long n_fixed, uint32_t k0, uint32_t k1, T beta,
                                                       int* __restrict__ err, UpdateRule rule) {
+  pass_prologue();
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= g.Vh) return;
   const unsigned long long n = n_dev ? *n_dev : n_fixed;
@@ -346,6 +372,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) k_pass_table(const LatDesc* 
                                                               const int* __restrict__ tile_lat,
                                                               const LatCtl* __restrict__ ctl, int mask, int mu,
                                                               int parity, int* __restrict__ err, int c) {
+  pass_prologue();
   const int i = tile_lat[blockIdx.x];
   const LatDesc& L = d[i];
   const int h = (blockIdx.x - L.tile_start) * kSweepTile + threadIdx.x;
@@ -371,6 +398,7 @@ __global__ void __launch_bounds__(kSweepThreads / 2) k_pass_table_pair(const Lat
                                                                        const LatCtl* __restrict__ ctl, int mask,
                                                                        int mu, int parity, int* __restrict__ err,
                                                                        int c) {
+  pass_prologue();
   const int i = tile_lat[blockIdx.x];
   const LatDesc& L = d[i];
   const Geom g = L.g;
@@ -453,12 +481,12 @@ static void launch_pass_t(T* th, const Geom& g, int mu, int parity, int slab_d, 
                           const UpdateRule& rule, cudaStream_t s) {
   if ((g.L & 3) == 0) {
     const int nb = blocks_for(g.Vh / 2, kUpdateThreads);
-    k_update_pass_pair<T, KIND><<<nb, kUpdateThreads, 0, s>>>(th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1,
-                                                               beta, err, rule);
+    launch_pass_pdl(k_update_pass_pair<T, KIND>, nb, kUpdateThreads, s, th, g, mu, parity, slab_d, n_dev, n_fixed,
+                    k0, k1, beta, err, rule);
   } else {
     const int nb = blocks_for(g.Vh, kUpdateThreads);
-    k_update_pass<T, KIND><<<nb, kUpdateThreads, 0, s>>>(th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1, beta,
-                                                          err, rule);
+    launch_pass_pdl(k_update_pass<T, KIND>, nb, kUpdateThreads, s, th, g, mu, parity, slab_d, n_dev, n_fixed, k0, k1,
+                    beta, err, rule);
   }
   count_launches(1);
 }
@@ -552,15 +580,17 @@ static void launch_passes_table_t(const LatDesc* d, const int* tile_lat, const T
           }
           if (td.all_l4) {  // two links per thread
             if (sweep == 0)
-              k_pass_table_pair<T, 0><<<td.total_tiles, kSweepThreads / 2, 0, s>>>(d, tile_lat, ctl, mask, mu, par,
-                                                                                    err, c);
+              launch_pass_pdl(k_pass_table_pair<T, 0>, td.total_tiles, kSweepThreads / 2, s, d, tile_lat, ctl, mask,
+                              mu, par, err, c);
             else
-              k_pass_table_pair<T, 1><<<td.total_tiles, kSweepThreads / 2, 0, s>>>(d, tile_lat, ctl, mask, mu, par,
-                                                                                    err, c);
+              launch_pass_pdl(k_pass_table_pair<T, 1>, td.total_tiles, kSweepThreads / 2, s, d, tile_lat, ctl, mask,
+                              mu, par, err, c);
           } else if (sweep == 0) {
-            k_pass_table<T, 0><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err, c);
+            launch_pass_pdl(k_pass_table<T, 0>, td.total_tiles, kSweepThreads, s, d, tile_lat, ctl, mask, mu, par, err,
+                            c);
           } else {
-            k_pass_table<T, 1><<<td.total_tiles, kSweepThreads, 0, s>>>(d, tile_lat, ctl, mask, mu, par, err, c);
+            launch_pass_pdl(k_pass_table<T, 1>, td.total_tiles, kSweepThreads, s, d, tile_lat, ctl, mask, mu, par, err,
+                            c);
           }
           count_launches(1);
         }
