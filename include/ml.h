@@ -302,6 +302,20 @@ int ml_measure_products(ml_lattice *h, const void *w_in_dev, void *w_out_dev, do
  * Blocking.  Used to check the device generator bit for bit. */
 int ml_philox(const uint32_t *ctr, const uint32_t *key, size_t n, uint32_t *out);
 
+/* Self-check of the single-precision link update's own rounding (no
+ * counterpart in the paper: an implementation detail).  The FP32 update
+ * rounds its range reductions and its wrap to [-pi, pi) by adding and
+ * subtracting 1.5 2^23 on the FP32 pipe instead of rintf / floorf, and builds
+ * its uniforms (k + 1/2) 2^-p in the mantissa instead of converting k.  This
+ * counts, on the device, the values where they differ from the conversions:
+ * mismatches[0] rint and mismatches[1] floor over every float of magnitude
+ * below 2^22, mismatches[2] every 23-bit uniform, mismatches[3] 2^24 52-bit
+ * uniforms spread over the range (a zero result of either sign counts as
+ * equal to the other).  All four are 0 on a correct build.
+ * mismatches: host array of 4.  Blocking; allocates 32 bytes on the current
+ * device.  ML_ECUDA on a CUDA error. */
+int ml_check_rounding(unsigned long long *mismatches);
+
 /* Kernel classes of ml_kernel_timing. */
 typedef enum {
   ML_K_HEATBATH = 0,   /* one heatbath pass kernel (mu = 1, even sites, slab mask) */

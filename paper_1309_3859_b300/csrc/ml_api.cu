@@ -1551,6 +1551,20 @@ int ml_philox(const uint32_t* ctr, const uint32_t* key, size_t n, uint32_t* out)
   return ce == cudaSuccess ? ML_OK : ML_ECUDA;
 }
 
+int ml_check_rounding(unsigned long long* mismatches) {
+  if (!mismatches) return ML_EINVAL;
+  unsigned long long* d = nullptr;
+  cudaError_t ce = cudaMalloc(&d, 4 * sizeof(unsigned long long));
+  if (ce == cudaSuccess) ce = cudaMemset(d, 0, 4 * sizeof(unsigned long long));
+  if (ce == cudaSuccess) {
+    launch_check_rounding(d, nullptr);
+    ce = cudaGetLastError();
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpy(mismatches, d, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return ce == cudaSuccess ? ML_OK : ML_ECUDA;
+}
+
 // --------------------------------------------------------------------------- batches
 int ml_batch_create(const ml_params* ps, int n, const ml_allocator* alloc, void* cuda_stream, ml_batch** out) {
   if (!out || !ps || n < 1) return ML_EINVAL;

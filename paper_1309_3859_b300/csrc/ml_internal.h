@@ -153,6 +153,7 @@ void launch_hot_start(bool fp64, void* theta, const Geom& g, uint64_t seed, cuda
 void launch_angles_to_soa(bool fp64, const double* canon, void* theta, const Geom& g, cudaStream_t s);
 void launch_angles_from_soa(bool fp64, const void* theta, double* canon, const Geom& g, cudaStream_t s);
 void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size_t n, cudaStream_t s);
+void launch_check_rounding(unsigned long long* bad, cudaStream_t s);
 
 // ---- measurement (ml_measure.cu) ----
 int vac_part_count(const Geom& g, int d);

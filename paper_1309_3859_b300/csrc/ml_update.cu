@@ -658,4 +658,45 @@ void launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, size
   count_launches(1);
 }
 
+// Self-check of the FP32-pipe rounding and the mantissa-built uniforms
+// against the conversions they replace: over every float of magnitude below
+// 2^22 (every 32-bit pattern, the others skipped), rint_small against rintf
+// and floor_small against floorf; every 23-bit uniform against
+// ((float)(a >> 9) + 0.5) 2^-23; and 2^24 52-bit uniforms with k spread over
+// [0, 2^52) (both ends included) against ((double)k + 0.5) 2^-52.
+// Mismatches counted into bad[0..3].
+__global__ void k_check_rounding(unsigned long long* __restrict__ bad) {
+  unsigned long long n[4] = {0, 0, 0, 0};
+  const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * blockDim.x;
+  const unsigned long long tid = blockIdx.x * static_cast<unsigned long long>(blockDim.x) + threadIdx.x;
+  for (unsigned long long v = tid; v < (1ull << 32); v += stride) {
+    const float y = __uint_as_float(static_cast<uint32_t>(v));
+    if (!(fabsf(y) < 4194304.0f)) continue;  // NaN or |y| >= 2^22
+    if (__float_as_uint(rint_small(y)) != __float_as_uint(rintf(y)) && rint_small(y) != rintf(y)) ++n[0];
+    if (floor_small(y) != floorf(y)) ++n[1];
+  }
+  for (unsigned long long k = tid; k < (1ull << 23); k += stride) {
+    const uint32_t a = static_cast<uint32_t>(k) << 9;
+    const float ref = (static_cast<float>(a >> 9) + 0.5f) * 0x1p-23f;
+    if (__float_as_uint(uniform23(a)) != __float_as_uint(ref)) ++n[2];
+  }
+  for (unsigned long long j = tid; j < (1ull << 24); j += stride) {
+    // k = j 2^28 + (j * 2654435761 mod 2^28): every 2^28-wide cell, a spread low part
+    const unsigned long long k = (j << 28) | ((j * 2654435761ull) & ((1ull << 28) - 1ull));
+    const uint32_t a = static_cast<uint32_t>(k >> 20), b = static_cast<uint32_t>((k & 0xFFFFFull) << 12);
+    const double ref = (static_cast<double>(k) + 0.5) * 0x1p-52;
+    if (__double_as_longlong(uniform52(a, b)) != __double_as_longlong(ref)) ++n[3];
+  }
+  for (int i = 0; i < 4; ++i)
+    if (n[i]) atomicAdd(bad + i, n[i]);
+}
+
+void launch_check_rounding(unsigned long long* bad, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_check_rounding<<<sms * 8, 256, 0, s>>>(bad);
+  count_launches(1);
+}
+
 }  // namespace ml

@@ -86,6 +86,7 @@ SIGNATURES = {
     "ml_observe": (ctypes.c_int, [_H, _D, ctypes.c_size_t]),
     "ml_sync": (ctypes.c_int, [_H]),
     "ml_philox": (ctypes.c_int, [_U32, _U32, ctypes.c_size_t, _U32]),
+    "ml_check_rounding": (ctypes.c_int, [ctypes.POINTER(ctypes.c_ulonglong)]),
     "ml_kernel_timing": (ctypes.c_int, [_H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "ml_timeline_enable": (ctypes.c_int, [_H, ctypes.c_int]),
     "ml_resident_profile": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int]),
@@ -242,6 +243,15 @@ def philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
     _check(lib().ml_philox(ctr.ctypes.data_as(_U32), key.ctypes.data_as(_U32), ctr.shape[0],
                            out.ctypes.data_as(_U32)), "ml_philox")
     return out
+
+
+def check_rounding() -> list:
+    """Mismatch counts of the FP32 update's own rounding and uniforms against
+    the conversions they replace (ml_check_rounding): rint, floor, 23-bit and
+    52-bit uniforms."""
+    out = (ctypes.c_ulonglong * 4)()
+    _check(lib().ml_check_rounding(out), "ml_check_rounding")
+    return [int(v) for v in out]
 
 
 def kernel_launches() -> int:

@@ -648,3 +648,11 @@ def test_pair_sums_refused_for_fp64():
     with pytest.raises(ml.MLError) as e:
         ml.Lattice(p)
     assert e.value.status == ml.ML_EINVAL
+
+
+def test_fp32_rounding_matches_conversions():
+    """The FP32 update rounds its range reductions and wrap on the FP32 pipe
+    and builds its uniforms in the mantissa; on the device these equal rintf,
+    floorf and the integer-to-float uniform formulas for every float of
+    magnitude below 2^22, every 23-bit uniform and 2^24 52-bit uniforms."""
+    assert ml.check_rounding() == [0, 0, 0, 0]
