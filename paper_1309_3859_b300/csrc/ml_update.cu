@@ -274,11 +274,13 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
                                                                 int nlat, const LatCtl* __restrict__ ctl, int mask,
                                                                 int n_or, int n_compound, int* __restrict__ err,
                                                                 unsigned long long* __restrict__ bar, int record,
-                                                                int rec_buf, int rec_slot) {
+                                                                int rec_buf, int rec_slot, int sub) {
   // When every tile has its own block (the latency-bound case), the block's
   // lattice parameters are read once into registers: the barrier's acquire
   // fence would otherwise send each pass's descriptor loads back to L2.
-  const bool one_tile = total_tiles <= static_cast<int>(gridDim.x);
+  // sub > 1 (tables of a few tiles): each tile is split over sub blocks of
+  // kSweepTile / sub threads, so that its links spread over more SMs.
+  const bool one_tile = total_tiles * sub <= static_cast<int>(gridDim.x);
   T* c_theta = nullptr;
   Geom c_g{};
   int c_h = 0, c_mask = 0;
@@ -287,12 +289,13 @@ __global__ void __launch_bounds__(kSweepThreads, 2) k_sweeps_table(const LatDesc
   UpdateRule c_rule{};
   unsigned long long c_base = 0;
   int c_sweeps = 0;
-  if (one_tile && static_cast<int>(blockIdx.x) < total_tiles) {
-    const int i = tile_lat[blockIdx.x];
+  if (one_tile && static_cast<int>(blockIdx.x) < total_tiles * sub) {
+    const int tile = static_cast<int>(blockIdx.x) / sub;
+    const int i = tile_lat[tile];
     const LatDesc& L = d[i];
     c_theta = static_cast<T*>(L.theta);
     c_g = L.g;
-    c_h = (static_cast<int>(blockIdx.x) - L.tile_start) * kSweepTile + threadIdx.x;
+    c_h = (tile - L.tile_start) * kSweepTile + (static_cast<int>(blockIdx.x) - tile * sub) * blockDim.x + threadIdx.x;
     c_mask = ctl ? ctl[i].mask : mask;
     c_k0 = L.k0;
     c_k1 = L.k1;
@@ -546,6 +549,29 @@ static cudaError_t launch_sweeps_table_t(const LatDesc* d, const int* tile_lat, 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(sweeps_grid<T>(td.total_tiles));
   cfg.blockDim = dim3(kSweepThreads);
+  // a table of a few tiles (no per-lattice control): each tile split over
+  // sub blocks (a divisor of kSweepTile / 32) so that the grid covers about
+  // one block per SM; the grid is fixed per table, as the barrier requires
+  static_assert(kSweepTile % (32 * 12) == 0, "sub-tiles of whole warps");
+  int sub = 1;
+  if (!ctl) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int c : {12, 6, 4, 3, 2}) {
+      if (td.total_tiles * c > sms) continue;
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweeps_table<T>, kSweepTile / c, 0);
+      if (per_sm >= 1) {
+        sub = c;
+        break;
+      }
+    }
+    if (sub > 1) {
+      cfg.gridDim = dim3(td.total_tiles * sub);
+      cfg.blockDim = dim3(kSweepTile / sub);
+    }
+  }
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -553,7 +579,7 @@ static cudaError_t launch_sweeps_table_t(const LatDesc* d, const int* tile_lat, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k_sweeps_table<T>, d, tile_lat, td.total_tiles, td.nlat, ctl, mask, n_or,
-                            n_compound, err, bar, record, rec_buf, rec_slot);
+                            n_compound, err, bar, record, rec_buf, rec_slot, sub);
 }
 
 template <typename T>
