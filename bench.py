@@ -352,6 +352,17 @@ def algorithmic_bytes(w, kernel, n_batch=1, d=None):
 INSTR_PER_LINK = {"heatbath": 622 / 32, "overrelax": 233 / 32}
 
 
+def l2_note(w):
+    """How the timed steps treat L2: flushed before the timed call, and
+    whether the step's slab sums (16 bytes per complex value) exceed L2."""
+    nslab, Ns, nc = w.Nt // w.slab, w.L ** 3, 6
+    sums = 16 * nslab * Ns * (len(w.r) + len(w.rf) * len(w.probes) * nc * 2)
+    size = f"{sums / 1e9:.2f} GB" if sums >= 1e8 else f"{sums / 1e6:.1f} MB"
+    rel = "larger than L2" if sums > 126e6 else "within L2; the flush makes each timed call start cold"
+    return (f"flushed ({L2_FLUSH_BYTES >> 20} MB write) before the timed call of K measurements; the step's "
+            f"slab sums ({size}) are {rel}")
+
+
 def issue_roofline(w, launch_ms, sub_updates, sms, sm_mhz):
     """Issue bound of the cluster-resident sub-updates: warp instructions of
     the launch's link updates over (SMs x 4 schedulers x clock)."""
@@ -805,8 +816,7 @@ def run_gpu(args, w, rank, world):
                    "k_between": w.k_between, "n_or": w.n_or, "r": f"{w.r[0]}..{w.r[-1]}",
                    "field_r": f"{w.rf[0]}..{w.rf[-1]}", "probes": len(w.probes), "components": 6,
                    "link_updates_per_step": upd,
-                   "l2": "flushed (512 MB write) before the timed call of K measurements; the step's working set "
-                         "(slab sums, 1.05 GB) is larger than L2",
+                   "l2": l2_note(w),
                    "parallelism": f"{world} independent lattice(s)"},
         "measurements_per_s": world * args.steps / (ms * 1e-3),
         "isolated_ms_per_step": float(np.median(iso)),
